@@ -1,0 +1,360 @@
+"""Pins of the FP64 oracle against closed forms, invariants, brute force and
+hand-worked values (no GPU). Each test names the passage it instantiates and
+the mistake it would catch."""
+import math
+import os
+from fractions import Fraction
+from types import SimpleNamespace
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import operators, observe, posterior, spectrum, timefactors
+from oracle.problem import Problem
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _spec(**kw):
+    base = dict(dim=2, n=7, nt=12, T=1.0, prior_alpha=0.1, sigma=0.05, obs_every=3,
+                sensors=synth.uniform_sensors(5, 2, 3), kappa=None)
+    base.update(kw)
+    return SimpleNamespace(**base)
+
+
+def _read_golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+# ---------------------------------------------------------------- operators
+@pytest.mark.parametrize("dim,n,modes", [(1, 15, (3,)), (2, 7, (1, 2)), (2, 15, (4, 1)),
+                                          (3, 7, (2, 1, 3))])
+def test_laplacian_sine_modes(dim, n, modes):
+    """Sec. 5: sine modes are eigenfunctions of the Dirichlet Laplacian; the
+    discrete eigenvalue is sum (4/h^2) sin^2(m pi h/2). Catches a wrong h
+    scaling, a missing boundary term or a wrong neighbour index."""
+    L = operators.laplacian(n, dim)
+    phi = operators.sine_mode(n, dim, modes)
+    mu = operators.sine_eigenvalue(n, modes)
+    np.testing.assert_allclose(L @ phi, mu * phi, rtol=0, atol=1e-10 * mu)
+
+
+def test_laplacian_golden_1d():
+    rows = _read_golden("laplace1d_n3.txt")
+    L = operators.laplacian(3, 1).toarray()
+    lam = np.sort(np.linalg.eigvalsh(L))
+    want = np.array([float(r[1]) for r in rows])
+    np.testing.assert_allclose(lam, want, rtol=1e-14)
+
+
+def test_laplacian_flux_form_faces():
+    """Variable kappa (flux form): for u = x-coordinate at an interior node,
+    (L u)_p = (kappa_west - kappa_east)/h exactly. Catches swapped faces, a
+    sign error or faces read along the wrong axis."""
+    n, dim = 9, 2
+    kap = synth.kappa_faces(n, dim, seed=5)
+    L = operators.laplacian(n, dim, kap)
+    h = 1.0 / (n + 1)
+    x = np.tile((np.arange(n) + 1.0) * h, n)          # first coordinate fastest
+    y = np.repeat((np.arange(n) + 1.0) * h, n)
+    kx, ky = kap
+    Lx, Ly = L @ x, L @ y
+    for (i, j) in [(3, 4), (1, 1), (5, 7)]:
+        p = i + n * j
+        assert abs(Lx[p] - (kx[j, i] - kx[j, i + 1]) / h) < 1e-9
+        assert abs(Ly[p] - (ky[j, i] - ky[j + 1, i]) / h) < 1e-9
+    assert abs(L - L.T).max() < 1e-12
+
+
+def test_laplacian_constant_kappa_scales():
+    n, dim = 5, 3
+    kap = [np.full(s.shape, 2.5) for s in synth.kappa_faces(n, dim, seed=1)]
+    L = operators.laplacian(n, dim, kap)
+    L0 = operators.laplacian(n, dim)
+    assert abs(L - 2.5 * L0).max() < 1e-9
+
+
+def test_kappa_field_statistics():
+    """Input recipe check: log(kappa) has mean ~0 and std ~0.5."""
+    kap = synth.kappa_faces(31, 2, seed=11)
+    g = np.log(np.concatenate([k.ravel() for k in kap]))
+    assert abs(g.mean()) < 0.5
+    assert 0.2 < g.std() < 0.9
+
+
+# ---------------------------------------------------------------- time stepping
+@pytest.mark.parametrize("dim,n,modes", [(1, 31, (2,)), (2, 7, (2, 3)), (3, 7, (1, 1, 2))])
+def test_modal_decay(dim, n, modes):
+    """Implicit Euler on a sine mode: y_n = (1 + tau mu)^{-n} phi exactly.
+    Catches an explicit-Euler step, an off-by-one step count or a wrong tau."""
+    P = Problem(_spec(dim=dim, n=n, nt=9, sensors=synth.uniform_sensors(3, dim, 1)))
+    phi = operators.sine_mode(n, dim, modes)
+    mu = operators.sine_eigenvalue(n, modes)
+    Y = P.trajectory(phi)
+    for k in range(P.nt):
+        np.testing.assert_allclose(Y[:, k], (1 + P.tau * mu) ** -(k + 1) * phi,
+                                   rtol=1e-12, atol=1e-14)
+
+
+def test_heat_1d_continuum_decay():
+    """1D heat equation u_t = u_xx, u(0)=sin(pi x): the exact solution decays
+    as exp(-pi^2 t). The implicit-Euler/FD error is O(tau + h^2): halving tau
+    (h fixed and small) must roughly halve the error."""
+    errs = []
+    for nt in (200, 400, 800):
+        P = Problem(_spec(dim=1, n=255, nt=nt, sensors=synth.uniform_sensors(2, 1, 1)))
+        phi = operators.sine_mode(255, 1, (1,))
+        y = P.trajectory(phi)[:, -1]
+        errs.append(np.max(np.abs(y - math.exp(-math.pi ** 2) * phi)))
+    assert errs[0] < 5e-4
+    assert 1.8 < errs[0] / errs[1] < 2.2 and 1.8 < errs[1] / errs[2] < 2.2
+
+
+# ---------------------------------------------------------------- observation
+def test_lattice_sensors_select_nodes():
+    """The tiny workload's 7x7 lattice (i/8, j/8) on the 31-grid hits nodes
+    (4i-1, 4j-1) exactly: B is a 0/1 selection."""
+    B = observe.observation_matrix(31, 2, synth.lattice_sensors(7, 2)).toarray()
+    assert B.shape == (49, 961)
+    for s in range(49):
+        i, j = s % 7 + 1, s // 7 + 1
+        row = np.zeros(961)
+        row[(4 * i - 1) + 31 * (4 * j - 1)] = 1.0
+        np.testing.assert_array_equal(B[s], row)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_interpolation_reproduces_multilinear(dim):
+    """Bilinear/trilinear interpolation reproduces f = prod_a x_a exactly
+    (it vanishes on the faces x_a = 0, so cells touching those faces count
+    too); weights of interior cells sum to 1."""
+    n = 9
+    h = 1.0 / (n + 1)
+    r = synth.rng(3)
+    pts = r.uniform(0.0, 0.6, size=(40, dim))
+    B = observe.observation_matrix(n, dim, pts)
+    coords = np.meshgrid(*[(np.arange(n) + 1.0) * h] * dim, indexing="ij")
+    f_nodes = np.ones([n] * dim)
+    for c in coords:
+        f_nodes = f_nodes * c
+    f_nodes = f_nodes.transpose(tuple(range(dim))[::-1]).ravel()   # first coord fastest
+    np.testing.assert_allclose(B @ f_nodes, np.prod(pts, axis=1), rtol=1e-12, atol=1e-15)
+    inner = np.all((pts > h) & (pts < 1 - h), axis=1)
+    np.testing.assert_allclose(np.asarray(B.sum(axis=1)).ravel()[inner], 1.0, rtol=1e-14)
+
+
+# ---------------------------------------------------------------- forward / adjoint
+@pytest.mark.parametrize("dim,kappa", [(2, False), (3, True)])
+def test_adjoint_identity(dim, kappa):
+    """<F u, w> = <u, F^T w> to 1e-12: F (forward stepping) and F^T (backward
+    recursion) are written independently."""
+    n = 7 if dim == 2 else 5
+    spec = _spec(dim=dim, n=n, nt=10, obs_every=2, sensors=synth.uniform_sensors(6, dim, 2),
+                 kappa=synth.kappa_faces(n, dim, 4) if kappa else None)
+    P = Problem(spec)
+    r = synth.rng(9)
+    u = r.standard_normal((P.nx, 3))
+    w = r.standard_normal((P.n_data, 3))
+    lhs = np.sum(P.forward(u) * w, axis=0)
+    rhs = np.sum(u * P.adjoint(w), axis=0)
+    np.testing.assert_allclose(lhs, rhs, rtol=1e-12)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_forward_brute_force(dim):
+    """F from dense matrix powers B (I + tau L)^{-n} on an n=3 grid."""
+    spec = _spec(dim=dim, n=3, nt=6, obs_every=2, sensors=synth.uniform_sensors(4, dim, 6),
+                 kappa=synth.kappa_faces(3, dim, 8))
+    P = Problem(spec)
+    L = operators.laplacian(3, dim, spec.kappa).toarray()
+    Sinv = np.linalg.inv(np.eye(P.nx) + P.tau * L)
+    B = observe.observation_matrix(3, dim, spec.sensors).toarray()
+    rows = [B @ np.linalg.matrix_power(Sinv, s) for s in (2, 4, 6)]
+    np.testing.assert_allclose(P.forward_explicit(), np.vstack(rows), rtol=1e-12, atol=1e-15)
+
+
+def test_hessian_matrix_free_symmetric():
+    """Htilde applied column by column (matrix-free path) is symmetric to 1e-12."""
+    P = Problem(_spec(n=5, nt=8, obs_every=2, sensors=synth.uniform_sensors(4, 2, 12)))
+    H = P.hessian_apply(np.eye(P.nx))
+    assert np.max(np.abs(H - H.T)) <= 1e-12 * np.max(np.abs(H))
+
+
+def test_hessian_modal_closed_form():
+    """Full observation (a sensor on every node, every step) and constant
+    kappa: a sine mode is an exact eigenvector of Htilde with eigenvalue
+    (1+alpha mu)^-2 sigma^-2 sum_n (1+tau mu)^-2n (discrete analogue of the
+    Sec. 5 modal analysis). Catches a missing prior factor, sigma^-1 instead
+    of sigma^-2, or a mis-indexed observed step."""
+    n = 7
+    spec = _spec(n=n, nt=10, obs_every=1, sensors=synth.lattice_sensors(n, 2),
+                 sigma=0.3, prior_alpha=0.02)
+    P = Problem(spec)
+    assert np.allclose(P.B.toarray(), np.eye(P.nx))
+    for modes in [(1, 1), (2, 3), (5, 2)]:
+        phi = operators.sine_mode(n, 2, modes)
+        mu = operators.sine_eigenvalue(n, modes)
+        lam = (1 + P.alpha * mu) ** -2 / P.sigma ** 2 * sum(
+            (1 + P.tau * mu) ** (-2 * k) for k in range(1, P.nt + 1))
+        np.testing.assert_allclose(P.hessian_apply(phi), lam * phi, rtol=1e-11, atol=1e-14)
+
+
+def test_one_node_golden():
+    rows = {r[0]: Fraction(r[1]) for r in _read_golden("one_node_problem.txt")}
+    spec = _spec(n=1, nt=2, prior_alpha=1 / 16, sigma=1.0, obs_every=1,
+                 sensors=np.array([[0.5, 0.5]]))
+    P = Problem(spec)
+    assert abs(P.misfit_explicit()[0, 0] - float(rows["H_mis"])) < 1e-16
+    assert abs(P.hessian_explicit()[0, 0] - float(rows["Htilde"])) < 1e-16
+    assert abs(posterior.post_cov_exact(P)[0, 0] - float(rows["Gamma_post"])) < 1e-15
+    m = posterior.mean_exact(P, np.array([1.0, 1.0]))
+    assert abs(m[0] - float(rows["mean"])) < 1e-15
+
+
+# ---------------------------------------------------------------- spectrum
+def test_sigma_rescaling():
+    """Gamma_noise = sigma^2 I: eigenvalues scale as 1/sigma^2."""
+    s1 = _spec(n=5, nt=6, obs_every=2, sigma=1.0, sensors=synth.uniform_sensors(4, 2, 1))
+    s2 = _spec(n=5, nt=6, obs_every=2, sigma=0.01, sensors=synth.uniform_sensors(4, 2, 1))
+    l1, _ = spectrum.eig_dense(Problem(s1).hessian_explicit())
+    l2, _ = spectrum.eig_dense(Problem(s2).hessian_explicit())
+    np.testing.assert_allclose(l2, l1 / 0.01 ** 2, rtol=1e-9, atol=1e-9 * l2[0])
+
+
+def test_arnoldi_matches_dense():
+    """Algorithm 1 (Arnoldi + MGS) recovers the leading eigenvalues of the
+    explicit Htilde (the check of Sec. 6.1 against a dense eigensolver)."""
+    P = Problem(_spec(n=7, nt=12, obs_every=3, sensors=synth.uniform_sensors(6, 2, 5)))
+    lam, _ = spectrum.eig_dense(P.hessian_explicit())
+    v1 = synth.normal_block(P.nx, 1, 3)[:, 0]
+    V, H = spectrum.arnoldi_mgs(P.hessian_apply, v1, 30)
+    ritz, Y = spectrum.ritz_from_arnoldi(V, H, 5)
+    np.testing.assert_allclose(ritz, lam[:5], rtol=1e-10)
+    for i in range(3):
+        r = P.hessian_apply(Y[:, i]) - ritz[i] * Y[:, i]
+        assert np.linalg.norm(r) < 1e-8 * lam[0]
+
+
+# ---------------------------------------------------------------- posterior
+def _tiny_problem():
+    return Problem(_spec(n=5, nt=8, obs_every=2, sensors=synth.uniform_sensors(5, 2, 21),
+                         sigma=0.02, prior_alpha=0.05))
+
+
+def test_smw_full_rank_equals_exact():
+    """With all nx eigenpairs the low-rank form equals the exact inverse
+    (Sherman-Morrison-Woodbury, Sec. 2)."""
+    P = _tiny_problem()
+    lam, V = spectrum.eig_dense(P.hessian_explicit())
+    G_lr = posterior.post_cov_lowrank(P, lam, V)
+    G_ex = posterior.post_cov_exact(P)
+    assert np.max(np.abs(G_lr - G_ex)) <= 1e-10 * np.max(np.abs(G_ex))
+    Ht = P.hessian_explicit()
+    np.testing.assert_allclose(posterior.smw_inner(lam, V), np.linalg.inv(np.eye(P.nx) + Ht),
+                               rtol=1e-9, atol=1e-12)
+
+
+def test_mean_is_map_point():
+    """The exact mean zeroes the gradient of the MAP objective
+    1/2 u^T Gamma_prior^{-1} u + 1/2 |y - F u|^2 / sigma^2 (Sec. 2), and the
+    full-rank low-rank mean equals it."""
+    P = _tiny_problem()
+    y = synth.normal_block(P.n_data, 1, 4)[:, 0]
+    m = posterior.mean_exact(P, y)
+    R = P.R.toarray()
+    grad = R @ (R @ m) - P.adjoint(y - P.forward(m)) / P.sigma ** 2
+    assert np.linalg.norm(grad) <= 1e-9 * np.linalg.norm(P.adjoint(y)) / P.sigma ** 2
+    lam, V = spectrum.eig_dense(P.hessian_explicit())
+    np.testing.assert_allclose(posterior.mean_lowrank(P, lam, V, y), m, rtol=1e-8,
+                               atol=1e-10 * np.abs(m).max())
+
+
+def test_sample_map_covariance():
+    """M = R^{-1}(I + V((1+lam)^-1/2 - 1)V^T) satisfies M M^T = low-rank
+    Gamma_post for a partial spectrum too."""
+    P = _tiny_problem()
+    lam, V = spectrum.eig_dense(P.hessian_explicit())
+    k = 6
+    mean = np.zeros(P.nx)
+    M = posterior.samples_lowrank(P, lam[:k], V[:, :k], mean, np.eye(P.nx))
+    np.testing.assert_allclose(M @ M.T, posterior.post_cov_lowrank(P, lam[:k], V[:, :k]),
+                               rtol=1e-10, atol=1e-14)
+
+
+def test_variance_matches_dense_diag():
+    P = _tiny_problem()
+    lam, V = spectrum.eig_dense(P.hessian_explicit())
+    nodes = np.array([0, 3, 12, 24])
+    want = np.diag(posterior.post_cov_lowrank(P, lam[:5], V[:, :5]))[nodes]
+    np.testing.assert_allclose(posterior.variance_lowrank(P, lam[:5], V[:, :5], nodes), want,
+                               rtol=1e-11)
+
+
+@pytest.mark.parametrize("dim,n", [(2, 7), (3, 5)])
+def test_prior_diag_dst_closed_form(dim, n):
+    """(Gamma_prior)_ii for the constant-coefficient prior equals the
+    spectral sum over orthonormal discrete sine vectors
+    sum_m prod_a s_{m_a}(i_a)^2 / (1 + alpha mu_m)^2."""
+    alpha = 0.07
+    P = Problem(_spec(dim=dim, n=n, prior_alpha=alpha, sensors=synth.uniform_sensors(2, dim, 1)))
+    nodes = np.arange(P.nx)
+    got = posterior.prior_diag(P, nodes)
+    x = np.arange(1, n + 1)
+    S = np.sqrt(2.0 / (n + 1)) * np.sin(np.outer(np.arange(1, n + 1), x) * np.pi / (n + 1))
+    h = 1.0 / (n + 1)
+    mu1 = 4 / h ** 2 * np.sin(np.arange(1, n + 1) * np.pi * h / 2) ** 2
+    want = np.zeros(P.nx)
+    for p in range(P.nx):
+        idx = [(p // n ** a) % n for a in range(dim)]
+        tot = 0.0
+        for m in np.ndindex(*([n] * dim)):
+            mu = sum(mu1[mi] for mi in m)
+            w = np.prod([S[m[a], idx[a]] ** 2 for a in range(dim)])
+            tot += w / (1 + alpha * mu) ** 2
+        want[p] = tot
+    np.testing.assert_allclose(got, want, rtol=1e-12)
+
+
+# ---------------------------------------------------------------- time factors
+def test_truncate_known_spectrum():
+    """Eckart-Young on a matrix with prescribed singular values: the chosen
+    rank is the smallest meeting the tail bound and the error is the tail."""
+    r = synth.rng(2)
+    U, _ = np.linalg.qr(r.standard_normal((60, 12)))
+    Z, _ = np.linalg.qr(r.standard_normal((40, 12)))
+    s = 10.0 ** -np.arange(12)
+    Y = (U * s) @ Z.T
+    W, V, err = timefactors.truncate(Y, 3e-6, 40)
+    fro = np.linalg.norm(Y)
+    # tail from s_6 = 1e-6 on is ~1.005e-6 <= 3e-6 |Y|; from s_5 it is ~1e-5 > 3e-6 |Y|
+    assert W.shape[1] == 6
+    assert abs(err - np.sqrt(np.sum(s[6:] ** 2))) < 1e-12
+    assert np.linalg.norm(Y - W @ V.T) <= 3e-6 * fro
+
+
+def test_streaming_exact_low_rank():
+    r = synth.rng(3)
+    Y = r.standard_normal((50, 3)) @ r.standard_normal((3, 37))
+    W, V, ranks = timefactors.streaming(Y, 8, 1e-10, 40)
+    assert W.shape[1] == 3 and max(ranks) == 3
+    np.testing.assert_allclose(W @ V.T, Y, rtol=0, atol=1e-10 * np.abs(Y).max())
+
+
+def test_streaming_trajectory_error_bound():
+    """Low-rank-in-time factors of a real heat trajectory meet the tolerance
+    and their rank stays close to the optimal SVD rank (Sec. 3)."""
+    P = Problem(_spec(n=15, nt=120, sensors=synth.uniform_sensors(3, 2, 1)))
+    u = P.prior_half(synth.normal_block(P.nx, 1, 8)[:, 0])
+    Y = P.trajectory(u)
+    tol = 1e-8
+    W, V, ranks = timefactors.streaming(Y, 20, tol, 40)
+    assert np.linalg.norm(Y - W @ V.T) <= tol * np.linalg.norm(Y)
+    Wo, Vo, _ = timefactors.truncate(Y, tol, 40)
+    assert Wo.shape[1] <= W.shape[1] <= Wo.shape[1] + 6
