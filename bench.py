@@ -1,0 +1,354 @@
+"""Benchmark: low-rank posterior covariance hot path on the 2D heat workload
+(127x127 interior, nx = 16129, nt = 500, 400 uniform sensors observed at
+every step, sigma = 1e-3, prior (I + 0.05 L)^-2, rank k = 100).
+
+One step = one pass of the whole hot path over one batch of synthetic input:
+block Lanczos (block 16, full re-orthogonalisation) on the prior-
+preconditioned misfit Hessian until the k = 100 Ritz pairs meet
+||Htilde v - theta v|| <= 1e-6 theta_1 — every Hessian apply being a prior
+solve, a 500-step forward and a 500-step adjoint implicit-Euler sweep of
+multigrid-preconditioned CG solves — then the posterior factors, then one
+posterior query (mean, pointwise variance at 1024 nodes, 8 samples).
+
+value = Hessian matvecs (Htilde applied to one vector) per second over the
+whole step; s_to_rank_k is the Lanczos part alone. Inputs are resident in
+HBM; L2 is flushed (256 MB write) before every timed step. e2e repeats the
+step through the C ABI with host buffers (copies inside the timed region).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank runs an independent replica of the workload on its
+own GPU (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "Hessian matvecs/s (s to rank-k Gamma_post at 1e-6 rel. Ritz residual reported beside)"
+UNIT = "matvec/s"
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "sweep_kernel_heat2d_127.json")
+KERNEL_SOURCES = ["lrp_sweep_kernel.cuh", "lrp_team.cuh", "lrp_sweep.cu"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1703_05638_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(seconds: float = 15.0):
+    """The FP64 oracle (SciPy sparse LU per operator, single-threaded
+    triangular solves) applying Htilde to single vectors on this host."""
+    from oracle.problem import Problem as OProblem
+    spec = synth.workload("heat2d_127")
+    P = OProblem(spec)
+    x = synth.normal_block(P.nx, 1, 77)[:, 0]
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        P.hessian_apply(x)
+        n += 1
+        dt = time.perf_counter() - t0
+        if dt >= seconds:
+            break
+    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} single-vector Htilde applies on heat2d_127 (nx=16129, nt=500) in {dt:.1f} s"}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle.problem import Problem as OProblem
+    spec = synth.workload("heat2d_127")
+    P = OProblem(spec)
+    x = synth.normal_block(P.nx, 1, 77)[:, 0]
+    per_step = 2  # a bounded sample per step: two single-vector applies
+    for _ in range(args.warmup):
+        P.hessian_apply(x)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for _ in range(per_step):
+            P.hessian_apply(x)
+    dt = time.perf_counter() - t0
+    value = args.steps * per_step / dt
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "heat2d_127: 2D heat 127x127, nt=500, 400 sensors every step, sigma=1e-3, "
+                                   "prior (I-0.05 Lap)^-2, k=100", "l2": "n/a (host)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step} single-vector Htilde applies per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--k", type=int, default=100)
+    ap.add_argument("--block", type=int, default=16)
+    ap.add_argument("--nt", type=int, default=0, help="override nt (profiling of small cases only)")
+    ap.add_argument("--team-ctas", type=int, default=0)
+    ap.add_argument("--team-cols", type=int, default=0)
+    ap.add_argument("--mg-nu", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_1703_05638_gb300 as lrp
+    from paper_1703_05638_gb300 import build as lrp_build
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or ws == 1:
+        lrp_build.build()
+    if dist:
+        dist.barrier()
+    lrp.load()
+
+    spec = synth.workload("heat2d_127")
+    if args.nt:
+        spec.nt = args.nt
+    precision = lrp.LRP_MIXED if args.precision == "mixed" else lrp.LRP_FP64
+    stream = torch.cuda.current_stream()
+    tuning = {}
+    if args.team_ctas:
+        tuning["team_ctas"] = args.team_ctas
+    if args.team_cols:
+        tuning["team_cols"] = args.team_cols
+    if args.mg_nu:
+        tuning["mg_nu"] = args.mg_nu
+    G = lrp.lrp_setup_problem(spec, precision=precision, stream=stream, **tuning)
+    nx = G.nx
+    seed = spec.seed + 101 * rank
+    # synthetic inputs, resident in HBM: Lanczos start block, data, query nodes, sample draws
+    start_h = synth.normal_block(nx, args.block, seed)
+    u_true_h = synth.normal_block(nx, 1, seed + 1)
+    u_true = lrp.lrp_prior_half(G, torch.from_numpy(u_true_h).cuda())[0]
+    d_clean = lrp.lrp_forward_observe(G, u_true)[0]
+    noise = torch.from_numpy(synth.normal_block(G.n_data, 1, seed + 2)).cuda()
+    y_obs = (d_clean + spec.sigma * noise).reshape(-1).contiguous()
+    nodes_h = synth.query_nodes(nx, 1024, seed + 3)
+    xi_h = synth.normal_block(nx, 8, seed + 4)
+    start_d = torch.from_numpy(start_h).cuda()
+    nodes_d = torch.from_numpy(nodes_h).cuda()
+    xi_d = torch.from_numpy(xi_h).cuda()
+    y_obs_h = y_obs.cpu().numpy()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    kind = lrp.LRP_Q_MEAN | lrp.LRP_Q_VARIANCE | lrp.LRP_Q_SAMPLES
+
+    def step(device=True):
+        if device:
+            post, st = lrp.lrp_lowrank_posterior(G, k=args.k, block=args.block, eig_tol=1e-6, start=start_d)
+            out = lrp.lrp_posterior_query(post, kind, y_obs=y_obs, points=nodes_d, xi=xi_d, device=True)
+        else:
+            post, st = lrp.lrp_lowrank_posterior(G, k=args.k, block=args.block, eig_tol=1e-6, start=start_h)
+            out = lrp.lrp_posterior_query(post, kind, y_obs=y_obs_h, points=nodes_h, xi=xi_h, device=False)
+            out["lambda"] = post.eigs()
+        post.close()
+        return st, out
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    launches0 = lrp.lrp_kernel_launches()
+    lrp.lrp_sweep_profile(G, 1)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        st, _ = step()
+        ev[i][1].record(stream)
+        stats.append(st)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    sweep_ms, sweep_launches, sweep_bytes = lrp.lrp_sweep_profile(G, 0)
+    launches = lrp.lrp_kernel_launches() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    matvecs = sum(s["n_matvec"] for s in stats)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        m = torch.tensor([matvecs], device="cuda", dtype=torch.float64)
+        dist.all_reduce(m, op=dist.ReduceOp.SUM)
+        matvecs = int(m.item())
+    value = matvecs / (total_ms / 1e3)
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        h2d = start_h.nbytes + y_obs_h.nbytes + nodes_h.nbytes + xi_h.nbytes
+        d2h = 8 * (args.k + nx + nodes_h.size + nx * xi_h.shape[1])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mv = 0
+        for _ in range(args.steps):
+            st, _ = step(device=False)
+            mv += st["n_matvec"]
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        e2e = {"value": mv * max(ws, 1) / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    peaks, peak_kind = measured_peaks()
+    achieved = (sweep_bytes / sweep_launches) / (sweep_ms / sweep_launches / 1e3) / 1e9 if sweep_ms > 0 else 0.0
+    traffic = None
+    try:
+        with open(PROFILE_SUMMARY) as f:
+            prof = json.load(f)
+        if prof.get("kernel_hash") == kernel_hash() and prof.get("dram_bytes_per_launch_full"):
+            traffic = prof["dram_bytes_per_launch_full"]
+    except (OSError, ValueError):
+        pass
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                "kernel": "sweep_kernel<float,2,mixed> (persistent MG-PCG forward/adjoint sweeps)",
+                "peak_kind": f"{peak_kind} copy bandwidth",
+                "algo_bytes_per_launch": sweep_bytes / max(sweep_launches, 1),
+                "ms_per_launch": sweep_ms / max(sweep_launches, 1), "launches": sweep_launches}
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        cpu = cpu_baseline()
+    lan = stats[-1]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": max(ws, 1), "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 multigrid-PCG in f64 refinement; f64 Lanczos/QR/eig/posterior" if precision else "f64",
+        "data": "synthetic",
+        "config": {"workload": f"heat2d_127: 2D heat eq 127x127 interior (nx=16129), nt={spec.nt}, 400 uniform "
+                               "sensors at every step, sigma=1e-3, prior (I-0.05 Lap)^-2",
+                   "k": args.k, "block": args.block, "eig_tol": 1e-6, "query": "mean + variance@1024 + 8 samples",
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": f"replicas x{max(ws, 1)}"},
+        "s_to_rank_k": statistics.mean(s["ms"] for s in stats) / 1e3,
+        "lanczos": {"n_iter": lan["n_iter"], "n_matvec": lan["n_matvec"], "k_converged": lan["k_converged"],
+                    "max_ritz_resid": lan["max_ritz_resid"], "ms_apply": lan["ms_apply"]},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,248 @@
+/*
+ * lrp.h — C ABI of the GB300 low-rank posterior-covariance library.
+ *
+ * The library computes, on one GPU, the hot path of the low-rank posterior
+ * covariance method for a linear Bayesian inverse problem whose parameter is
+ * the initial condition u of a parabolic PDE (Benner, Qiu, Stoll,
+ * "Low-rank computation of posterior covariance matrices in Bayesian inverse
+ * problems", Sec. 6 Eq. (pde)):
+ *
+ *   y_t - div(kappa grad y) = 0 on the unit square/cube, y = 0 on the
+ *   boundary, y(0) = u; finite differences with n interior nodes per axis
+ *   (h = 1/(n+1)), implicit Euler with tau = T/nt:
+ *   (I + tau L) y_n = y_{n-1}  (block row of Sec. 6.1 Eq. (st_pde), M = I).
+ *   Data: point sensors read the bilinear/trilinear interpolant of y at the
+ *   observed steps obs_every, 2*obs_every, ..., nt (Sec. 6 Eq. (obj),
+ *   Eq. (dis_obj)). Gamma_noise = sigma^2 I.
+ *   Prior: Gamma_prior = R^-2, R = I + alpha L0 (L0 the constant-coefficient
+ *   Laplacian), so Gamma_prior^{1/2} = R^{-1}.
+ *   F = parameter-to-observable map; H_mis = F^T F / sigma^2;
+ *   Htilde = R^{-1} H_mis R^{-1}  (Sec. 2 Eq. (prior_pre), Sec. 6.1 Eq. (misfit)).
+ *
+ * Conventions (all entry points):
+ *  - Grid vectors have nx = n^dim entries, node (i0,i1,i2) at flat index
+ *    i0 + n*i1 + n*n*i2 (first coordinate fastest).
+ *  - Blocks of vectors are column-major: column j of a block X with leading
+ *    dimension ldx starts at X + j*ldx.
+ *  - Observation vectors (one per column) have n_data = n_obs * n_steps
+ *    entries, step-major: (k-th observed step, sensor s) at k*n_obs + s.
+ *  - Array arguments may be host or device pointers; the library detects
+ *    which with cudaPointerGetAttributes and stages host arrays through the
+ *    device. The caller owns every array it passes. Device arrays must be
+ *    on the problem's device.
+ *  - All work is ordered on the problem's CUDA stream; every call returns
+ *    after that work has completed (synchronous).
+ *  - Errors: a call returns a status; on error the outputs are undefined and
+ *    lrp_last_error() describes the failure. A solve that misses its
+ *    tolerance within its iteration cap still fills its outputs and stats
+ *    and returns LRP_ENOCONV.
+ *  - Handles are not thread-safe: one host thread per handle at a time.
+ */
+#ifndef LRP_H
+#define LRP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LRP_OK = 0,
+  LRP_EINVAL = 1,     /* invalid argument */
+  LRP_ENOMEM = 2,     /* device or host allocation failed */
+  LRP_ENOCONV = 3,    /* a solve or the eigensolver missed its tolerance */
+  LRP_ENONFINITE = 4, /* NaN or Inf in an input */
+  LRP_ETIMEOUT = 5,   /* a bounded device-side wait gave up */
+  LRP_EBUDGET = 6,    /* request exceeds the configured memory budget */
+  LRP_ECUDA = 7       /* CUDA runtime error */
+} lrp_status;
+
+/* precision of the inner (PCG / multigrid) arithmetic */
+enum {
+  LRP_FP64 = 0,  /* everything in FP64 */
+  LRP_MIXED = 1  /* FP32 multigrid-PCG corrections inside FP64 iterative refinement */
+};
+
+/* flags of lrp_hessian_apply */
+enum {
+  LRP_PRIOR_PRECOND = 0,      /* default: Y = Htilde X */
+  LRP_MISFIT_ONLY = 1u << 0,  /* Y = H_mis X (no prior factors) */
+  LRP_KEEP_TRAJ_FACTORS = 1u << 1 /* also compress the forward trajectory of
+                                     each column to low-rank-in-time factors
+                                     Y ~ W V^T (Sec. 3); ranks in the stats */
+};
+
+typedef struct lrp_problem lrp_problem;     /* opaque, library-owned */
+typedef struct lrp_posterior lrp_posterior; /* opaque, library-owned, device-resident factors */
+
+typedef struct {
+  int dim;                  /* 2 or 3 */
+  int n;                    /* interior nodes per axis; n = 2^L - 1, 3 <= n <= 511 */
+  int nt;                   /* time steps */
+  double T;                 /* final time */
+  const double* kappa_faces;/* host; NULL -> kappa = 1. Else the face values of kappa:
+                               faces normal to axis 0, then axis 1 (then 2); along
+                               their own axis a face index runs 0..n (face i lies
+                               between nodes i-1 and i), along the other axes 0..n-1;
+                               first coordinate fastest within each block. */
+  double prior_alpha;       /* R = I + alpha*L0 */
+  int n_obs;                /* number of sensors (>= 1) */
+  const double* obs_xyz;    /* host, n_obs*dim sensor coordinates in (0,1)^dim, point-major */
+  int obs_every;            /* observed steps obs_every, 2*obs_every, ..., <= nt */
+  double sigma;             /* noise standard deviation */
+  int precision;            /* LRP_FP64 or LRP_MIXED */
+  double time_trunc_tol;    /* relative Frobenius tolerance of the time factors (e.g. 1e-8) */
+  int time_rank_max;        /* rank cap of the time factors (e.g. 40) */
+  int time_chunk;           /* steps buffered between recompressions (0 -> 32) */
+  double solve_rtol;        /* relative residual per spatial solve (0 -> 1e-13 FP64, 1e-11 mixed) */
+  int pcg_maxit;            /* PCG iteration cap per solve (0 -> 200) */
+  /* tuning (0 -> autotuned or default) */
+  int team_ctas;            /* CTAs per thread-block cluster working on one column group */
+  int team_cols;            /* columns per cluster: 1, 2, 4, 8 or 16 */
+  int mg_nu;                /* Jacobi sweeps before and after each coarse correction */
+  double inner_rtol;        /* LRP_MIXED: FP32 inner relative tolerance (0 -> 1e-4) */
+} lrp_problem_desc;
+
+typedef struct {
+  int n_solves;             /* spatial solves performed (per column) */
+  int pcg_iters_max;        /* largest PCG iteration count of any solve */
+  double pcg_iters_mean;    /* mean PCG iterations per solve */
+  int refine_max;           /* LRP_MIXED: largest number of refinement sweeps of any solve */
+  double max_rel_residual;  /* largest final relative residual of any solve */
+  int time_rank_max;        /* largest time rank of the kept trajectory factors (0 if not kept) */
+  double time_trunc_err;    /* largest certified relative truncation error bound of the factors */
+  double ms;                /* wall time of the call */
+} lrp_apply_stats;
+
+typedef struct {
+  int n_iter;               /* Lanczos block steps */
+  int n_matvec;             /* Htilde applications to single vectors */
+  int k_converged;          /* Ritz pairs meeting the residual test */
+  double max_ritz_resid;    /* max over the returned pairs of ||Htilde v - theta v|| / theta_1 */
+  double ms;                /* wall time */
+  double ms_apply;          /* of which Hessian applications */
+} lrp_lanczos_stats;
+
+/* query kinds */
+enum { LRP_Q_MEAN = 1, LRP_Q_VARIANCE = 2, LRP_Q_SAMPLES = 4 };
+
+typedef struct {
+  unsigned kind;            /* mask of LRP_Q_* */
+  const double* y_obs;      /* n_data observations (host or device); needed for MEAN and SAMPLES */
+  double sigma;             /* noise level of this request; 0 -> the problem's sigma */
+  int n_points;             /* VARIANCE: number of query nodes */
+  const int* points;        /* VARIANCE: flat node indices (host or device) */
+  int n_samples;            /* SAMPLES: number of samples */
+  const double* xi;         /* SAMPLES: nx*n_samples standard normals, column-major (host or device) */
+} lrp_query;
+
+typedef struct {
+  double* mean;             /* nx (host or device), written for MEAN and SAMPLES requests if non-NULL */
+  double* variance;         /* n_points (host or device) */
+  double* samples;          /* nx*n_samples column-major (host or device) */
+  double ms;                /* wall time */
+} lrp_query_result;
+
+/* ---------------------------------------------------------------------------
+ * Problem setup (Sec. 6: grid, operators, sensors, prior).
+ * Builds the multigrid hierarchy of I + tau*L and I + alpha*L0, the sensor
+ * interpolation lists and their transpose, and uploads them. cuda_stream: a
+ * cudaStream_t (NULL = the default stream); the current device at this call
+ * becomes the problem's device. On success *out owns all device memory of
+ * the problem until lrp_problem_destroy.
+ * Errors: LRP_EINVAL (bad sizes: n not 2^L-1, dim not 2/3, nt < 1, sensor
+ * outside (0,1)^dim, ...), LRP_ENONFINITE, LRP_ENOMEM, LRP_ECUDA. */
+lrp_status lrp_setup_problem(const lrp_problem_desc* desc, void* cuda_stream, lrp_problem** out);
+void lrp_problem_destroy(lrp_problem* p);
+
+/* Basic sizes of a problem: nx, n_obs, number of observed steps, n_data. */
+lrp_status lrp_problem_sizes(const lrp_problem* p, int* nx, int* n_obs, int* n_steps, int* n_data);
+
+/* ---------------------------------------------------------------------------
+ * Y = Htilde X (Sec. 2 Eq. (prior_pre); Sec. 6.1 Eq. (misfit)) for nvec
+ * columns: prior half-apply, forward implicit-Euler sweep with the fused
+ * observation and 1/sigma^2 weighting, adjoint sweep with the fused
+ * B^T source, prior half-apply. With LRP_MISFIT_ONLY: Y = H_mis X.
+ * X: nx x nvec (ldx >= nx), Y: nx x nvec (ldy >= nx); X and Y may not overlap.
+ * st may be NULL. */
+lrp_status lrp_hessian_apply(lrp_problem* p, int nvec, const double* X, int ldx,
+                             double* Y, int ldy, unsigned flags, lrp_apply_stats* st);
+
+/* D = F U (no noise weighting): forward sweep and observation.
+ * U: nx x nvec, D: n_data x nvec. */
+lrp_status lrp_forward_observe(lrp_problem* p, int nvec, const double* U, int ldu,
+                               double* D, int ldd, lrp_apply_stats* st);
+
+/* U = F^T D: adjoint sweep (backward recursion with the B^T source).
+ * D: n_data x nvec, U: nx x nvec. */
+lrp_status lrp_adjoint(lrp_problem* p, int nvec, const double* D, int ldd,
+                       double* U, int ldu, lrp_apply_stats* st);
+
+/* Y = Gamma_prior^{1/2} X = (I + alpha L0)^{-1} X. */
+lrp_status lrp_prior_half(lrp_problem* p, int nvec, const double* X, int ldx,
+                          double* Y, int ldy, lrp_apply_stats* st);
+
+/* Forward trajectory of each column of U in low-rank-in-time form (Sec. 3):
+ * Y = [y_1 .. y_nt] ~ W V^T with W: nx x r and V: nt x r (column j's factors
+ * at W + j*nx*rmax and V + j*nt*rmax, column-major, ld nx and nt).
+ * ranks[j] receives r for column j (<= time_rank_max). W, V must hold
+ * nvec*nx*time_rank_max and nvec*nt*time_rank_max doubles. */
+lrp_status lrp_trajectory_factors(lrp_problem* p, int nvec, const double* U, int ldu,
+                                  double* W, double* V, int* ranks, lrp_apply_stats* st);
+
+/* ---------------------------------------------------------------------------
+ * Low-rank posterior (Sec. 4 Algorithm 1, as block Lanczos with full
+ * reorthogonalisation on the symmetric Htilde; Sec. 2 SMW form).
+ * Computes the k leading eigenpairs of Htilde with blocks of `block`
+ * columns (1..16) until every returned Ritz pair has
+ * ||Htilde v - theta v|| <= eig_tol * theta_1 (eig_tol 0 -> 1e-6), or the
+ * Krylov space reaches max_basis columns (0 -> min(nx, 4k+2*block)).
+ * eig_threshold > 0 keeps only eigenvalues >= eig_threshold (the paper's
+ * threshold epsilon) among the k. start: optional nx x block start block
+ * (host or device), NULL -> a fixed pseudo-random block.
+ * The posterior keeps V_k, G = R^{-1} V_k and lambda on the device.
+ * Returns LRP_ENOCONV (with a usable posterior) if the basis cap is hit. */
+lrp_status lrp_lowrank_posterior(lrp_problem* p, int k, int block, double eig_tol,
+                                 double eig_threshold, int max_basis, const double* start,
+                                 lrp_posterior** out, lrp_lanczos_stats* st);
+void lrp_posterior_destroy(lrp_posterior* post);
+
+/* Copies the r <= k eigenvalues (decreasing) and optionally the eigenvectors
+ * (nx x r column-major, ld ldv) out of a posterior. *r receives the count. */
+lrp_status lrp_posterior_eigs(const lrp_posterior* post, int* r, double* lambda,
+                              double* V, int ldv);
+
+/* Posterior queries (Sec. 2: posterior mean = MAP point, pointwise variance
+ * diag(Gamma_post), samples u_mean + R^{-1}(I + V Lambda V^T)^{-1/2} xi),
+ * with the eigenvalues rescaled to the request's sigma
+ * (lambda(sigma) = lambda(sigma0) sigma0^2 / sigma^2). */
+lrp_status lrp_posterior_query(lrp_posterior* post, const lrp_query* q, lrp_query_result* r);
+
+/* Checkpoint: write / read the posterior factors and a hash of the problem. */
+lrp_status lrp_posterior_save(const lrp_posterior* post, const char* path);
+lrp_status lrp_posterior_load(lrp_problem* p, const char* path, lrp_posterior** out);
+
+/* Message of the last error on this host thread (never NULL). */
+const char* lrp_last_error(void);
+
+/* Library version string. */
+const char* lrp_version(void);
+
+/* Sweep-kernel ledger. mode 1: reset and start recording, for every launch
+ * of the persistent sweep kernel on this problem, its CUDA-event duration and
+ * its algorithmic bytes (passes over the fine-level vectors implied by the
+ * solver's iteration counts); mode 0: reset and stop; mode -1: read only.
+ * The accumulated values before the reset are returned in *ms, *launches and
+ * *algo_bytes (each may be NULL). */
+lrp_status lrp_sweep_profile(lrp_problem* p, int mode, double* ms, unsigned long long* launches,
+                             double* algo_bytes);
+
+/* Diagnostics: number of CUDA kernels this library has launched in this
+ * process so far (all problems, all threads). */
+unsigned long long lrp_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LRP_H */

@@ -1,0 +1,394 @@
+"""Python binding of the GB300 low-rank posterior library (C ABI in include/lrp.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library ``liblrp.so`` built in-tree for sm_103a. Importing this package does
+not load the library; the first call does, and raises if it is missing.
+
+Function names mirror the C entry points (``lrp_setup_problem``,
+``lrp_hessian_apply``, ...). Arrays may be NumPy arrays (host memory) or
+CUDA torch tensors (device memory); blocks of vectors have shape (rows, ncols)
+and are passed column-major, as the C ABI expects.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblrp.so")
+
+LRP_OK, LRP_EINVAL, LRP_ENOMEM, LRP_ENOCONV, LRP_ENONFINITE, LRP_ETIMEOUT, LRP_EBUDGET, LRP_ECUDA = range(8)
+LRP_FP64, LRP_MIXED = 0, 1
+LRP_PRIOR_PRECOND, LRP_MISFIT_ONLY, LRP_KEEP_TRAJ_FACTORS = 0, 1, 2
+LRP_Q_MEAN, LRP_Q_VARIANCE, LRP_Q_SAMPLES = 1, 2, 4
+STATUS_NAMES = {0: "LRP_OK", 1: "LRP_EINVAL", 2: "LRP_ENOMEM", 3: "LRP_ENOCONV", 4: "LRP_ENONFINITE",
+                5: "LRP_ETIMEOUT", 6: "LRP_EBUDGET", 7: "LRP_ECUDA"}
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+
+
+class lrp_problem_desc(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int), ("nt", C.c_int), ("T", C.c_double),
+                ("kappa_faces", C.c_void_p), ("prior_alpha", C.c_double), ("n_obs", C.c_int),
+                ("obs_xyz", C.c_void_p), ("obs_every", C.c_int), ("sigma", C.c_double),
+                ("precision", C.c_int), ("time_trunc_tol", C.c_double), ("time_rank_max", C.c_int),
+                ("time_chunk", C.c_int), ("solve_rtol", C.c_double), ("pcg_maxit", C.c_int),
+                ("team_ctas", C.c_int), ("team_cols", C.c_int), ("mg_nu", C.c_int),
+                ("inner_rtol", C.c_double)]
+
+
+class lrp_apply_stats(C.Structure):
+    _fields_ = [("n_solves", C.c_int), ("pcg_iters_max", C.c_int), ("pcg_iters_mean", C.c_double),
+                ("refine_max", C.c_int), ("max_rel_residual", C.c_double), ("time_rank_max", C.c_int),
+                ("time_trunc_err", C.c_double), ("ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class lrp_lanczos_stats(C.Structure):
+    _fields_ = [("n_iter", C.c_int), ("n_matvec", C.c_int), ("k_converged", C.c_int),
+                ("max_ritz_resid", C.c_double), ("ms", C.c_double), ("ms_apply", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class lrp_query(C.Structure):
+    _fields_ = [("kind", C.c_uint), ("y_obs", C.c_void_p), ("sigma", C.c_double), ("n_points", C.c_int),
+                ("points", C.c_void_p), ("n_samples", C.c_int), ("xi", C.c_void_p)]
+
+
+class lrp_query_result(C.Structure):
+    _fields_ = [("mean", C.c_void_p), ("variance", C.c_void_p), ("samples", C.c_void_p), ("ms", C.c_double)]
+
+
+EXPORTS = {
+    "lrp_setup_problem": (C.c_int, [C.POINTER(lrp_problem_desc), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "lrp_problem_destroy": (None, [C.c_void_p]),
+    "lrp_problem_sizes": (C.c_int, [C.c_void_p, _ip, _ip, _ip, _ip]),
+    "lrp_hessian_apply": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_uint,
+                                    C.POINTER(lrp_apply_stats)]),
+    "lrp_forward_observe": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int,
+                                      C.POINTER(lrp_apply_stats)]),
+    "lrp_adjoint": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int,
+                              C.POINTER(lrp_apply_stats)]),
+    "lrp_prior_half": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int,
+                                 C.POINTER(lrp_apply_stats)]),
+    "lrp_trajectory_factors": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+                                         C.c_void_p, C.POINTER(lrp_apply_stats)]),
+    "lrp_lowrank_posterior": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
+                                        C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(lrp_lanczos_stats)]),
+    "lrp_posterior_destroy": (None, [C.c_void_p]),
+    "lrp_posterior_eigs": (C.c_int, [C.c_void_p, _ip, C.c_void_p, C.c_void_p, C.c_int]),
+    "lrp_posterior_query": (C.c_int, [C.c_void_p, C.POINTER(lrp_query), C.POINTER(lrp_query_result)]),
+    "lrp_posterior_save": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "lrp_posterior_load": (C.c_int, [C.c_void_p, C.c_char_p, C.POINTER(C.c_void_p)]),
+    "lrp_last_error": (C.c_char_p, []),
+    "lrp_version": (C.c_char_p, []),
+    "lrp_kernel_launches": (C.c_ulonglong, []),
+    "lrp_sweep_profile": (C.c_int, [C.c_void_p, C.c_int, _dp, C.POINTER(C.c_ulonglong), _dp]),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: Optional[str] = None):
+    """Load liblrp.so (building nothing). Raises if the library is missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError(f"CUDA library {p} is missing: run __graft_entry__.build() "
+                                   "(or python paper_1703_05638_gb300/build.py) first")
+            lib = C.CDLL(p)
+            for name, (res, args) in EXPORTS.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+class LrpError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(status, allow=(LRP_OK,)):
+    if status not in allow:
+        raise LrpError(status, load().lrp_last_error().decode())
+    return status
+
+
+# --------------------------------------------------------------------------- arrays
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+class _Arg:
+    """A column-major view of a (rows, ncols) block as a raw pointer."""
+
+    def __init__(self, x, rows: int, dtype=np.float64):
+        self.keep = None
+        if x is None:
+            self.ptr, self.ld, self.ncols, self.kind = None, rows, 0, "none"
+            return
+        if _is_torch(x):
+            import torch
+            t = x if x.dim() == 2 else x.reshape(-1, 1)
+            assert t.shape[0] == rows, (tuple(t.shape), rows)
+            tdt = torch.float64 if dtype == np.float64 else torch.int32
+            ct = t.t().contiguous().to(tdt)  # (ncols, rows) row-major == column-major block
+            self.keep = ct
+            self.ptr, self.ld, self.ncols, self.kind = ct.data_ptr(), rows, t.shape[1], "torch"
+        else:
+            a = np.asarray(x, dtype=dtype)
+            if a.ndim == 1:
+                a = a.reshape(-1, 1)
+            assert a.shape[0] == rows, (a.shape, rows)
+            a = np.asfortranarray(a)
+            self.keep = a
+            self.ptr, self.ld, self.ncols, self.kind = a.ctypes.data, rows, a.shape[1], "numpy"
+
+
+def _out_like(arg: _Arg, rows: int, ncols: int, like):
+    if arg.kind == "torch":
+        import torch
+        t = torch.empty((ncols, rows), dtype=torch.float64, device=like.device)
+        return t, t.data_ptr(), lambda: t.t()
+    a = np.empty((rows, ncols), dtype=np.float64, order="F")
+    return a, a.ctypes.data, lambda: a
+
+
+# --------------------------------------------------------------------------- problem
+class Problem:
+    """Owner of one lrp_problem handle."""
+
+    def __init__(self, handle, desc):
+        self.handle = handle
+        self.desc = desc
+        nx, no, ns, nd = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        _check(load().lrp_problem_sizes(handle, C.byref(nx), C.byref(no), C.byref(ns), C.byref(nd)))
+        self.nx, self.n_obs, self.n_steps, self.n_data = nx.value, no.value, ns.value, nd.value
+
+    def close(self):
+        if self.handle:
+            load().lrp_problem_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lrp_setup_problem(spec, precision: int = LRP_FP64, stream=None, **tuning) -> Problem:
+    """Set up a problem from an object with the attributes of synth.ProblemSpec
+    (dim, n, nt, T, prior_alpha, sigma, obs_every, sensors, kappa)."""
+    lib = load()
+    d = lrp_problem_desc()
+    d.dim, d.n, d.nt, d.T = int(spec.dim), int(spec.n), int(spec.nt), float(spec.T)
+    kap = getattr(spec, "kappa", None)
+    keep = []
+    if kap is not None:
+        k = np.ascontiguousarray(np.concatenate([np.asarray(f, dtype=np.float64).ravel() for f in kap]))
+        keep.append(k)
+        d.kappa_faces = k.ctypes.data
+    d.prior_alpha = float(spec.prior_alpha)
+    sens = np.ascontiguousarray(np.asarray(spec.sensors, dtype=np.float64))
+    keep.append(sens)
+    d.n_obs = sens.shape[0]
+    d.obs_xyz = sens.ctypes.data
+    d.obs_every = int(spec.obs_every)
+    d.sigma = float(spec.sigma)
+    d.precision = int(precision)
+    d.time_trunc_tol = float(getattr(spec, "time_trunc_tol", 1e-8) or 1e-8)
+    d.time_rank_max = int(getattr(spec, "time_rank_max", 40) or 40)
+    for key, val in tuning.items():
+        setattr(d, key, val)
+    h = C.c_void_p()
+    s = 0 if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(lib.lrp_setup_problem(C.byref(d), C.c_void_p(s), C.byref(h)))
+    return Problem(h, d)
+
+
+def _sweep(fn, prob: Problem, X, rows_in, rows_out, *extra):
+    a = _Arg(X, rows_in)
+    out, optr, view = _out_like(a, rows_out, a.ncols, X)
+    st = lrp_apply_stats()
+    status = fn(prob.handle, a.ncols, C.c_void_p(a.ptr), a.ld, C.c_void_p(optr), rows_out, *extra, C.byref(st))
+    _check(status, allow=(LRP_OK, LRP_ENOCONV))
+    return view(), st.as_dict()
+
+
+def lrp_hessian_apply(prob: Problem, X, flags: int = 0):
+    """Y = Htilde X (or H_mis X with LRP_MISFIT_ONLY). Returns (Y, stats)."""
+    return _sweep(load().lrp_hessian_apply, prob, X, prob.nx, prob.nx, C.c_uint(flags))
+
+
+def lrp_forward_observe(prob: Problem, U):
+    """D = F U. Returns (D, stats), D of shape (n_data, ncols)."""
+    return _sweep(load().lrp_forward_observe, prob, U, prob.nx, prob.n_data)
+
+
+def lrp_adjoint(prob: Problem, D):
+    """U = F^T D. Returns (U, stats)."""
+    return _sweep(load().lrp_adjoint, prob, D, prob.n_data, prob.nx)
+
+
+def lrp_prior_half(prob: Problem, X):
+    """Y = Gamma_prior^{1/2} X = (I + alpha L0)^{-1} X. Returns (Y, stats)."""
+    return _sweep(load().lrp_prior_half, prob, X, prob.nx, prob.nx)
+
+
+def lrp_trajectory_factors(prob: Problem, U):
+    """Low-rank-in-time factors of the forward trajectories of the columns of
+    U (host arrays): returns (list of (W, V) with Y_j ~ W V^T, stats)."""
+    a = _Arg(np.asarray(U), prob.nx)
+    rmax = prob.desc.time_rank_max
+    nt = prob.desc.nt
+    W = np.zeros((a.ncols, rmax, prob.nx))
+    V = np.zeros((a.ncols, rmax, nt))
+    ranks = np.zeros(a.ncols, dtype=np.int32)
+    st = lrp_apply_stats()
+    status = load().lrp_trajectory_factors(prob.handle, a.ncols, C.c_void_p(a.ptr), a.ld,
+                                           C.c_void_p(W.ctypes.data), C.c_void_p(V.ctypes.data),
+                                           C.c_void_p(ranks.ctypes.data), C.byref(st))
+    _check(status, allow=(LRP_OK, LRP_ENOCONV))
+    out = [(W[j, :ranks[j]].T.copy(), V[j, :ranks[j]].T.copy()) for j in range(a.ncols)]
+    return out, st.as_dict()
+
+
+class Posterior:
+    def __init__(self, handle, prob: Problem):
+        self.handle = handle
+        self.prob = prob
+
+    def eigs(self, vectors: bool = False):
+        r = C.c_int()
+        lib = load()
+        _check(lib.lrp_posterior_eigs(self.handle, C.byref(r), None, None, 0))
+        lam = np.zeros(max(r.value, 1))
+        V = np.zeros((self.prob.nx, max(r.value, 1)), order="F") if vectors else None
+        _check(lib.lrp_posterior_eigs(self.handle, C.byref(r), C.c_void_p(lam.ctypes.data),
+                                      C.c_void_p(V.ctypes.data) if vectors else None, self.prob.nx))
+        lam = lam[:r.value]
+        return (lam, V[:, :r.value]) if vectors else lam
+
+    def close(self):
+        if self.handle:
+            load().lrp_posterior_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lrp_lowrank_posterior(prob: Problem, k: int, block: int = 1, eig_tol: float = 1e-6,
+                          eig_threshold: float = 0.0, max_basis: int = 0, start=None):
+    """Block Lanczos for the k leading eigenpairs of Htilde; returns (Posterior, stats)."""
+    lib = load()
+    a = _Arg(start, prob.nx) if start is not None else None
+    h = C.c_void_p()
+    st = lrp_lanczos_stats()
+    status = lib.lrp_lowrank_posterior(prob.handle, int(k), int(block), float(eig_tol), float(eig_threshold),
+                                       int(max_basis), C.c_void_p(a.ptr) if a else None, C.byref(h),
+                                       C.byref(st))
+    _check(status, allow=(LRP_OK, LRP_ENOCONV))
+    return Posterior(h, prob), st.as_dict()
+
+
+def lrp_posterior_query(post: Posterior, kind: int, y_obs=None, sigma: float = 0.0, points=None, xi=None,
+                        device: bool = False):
+    """Mean / pointwise variance / samples. Inputs may be NumPy (host) or CUDA
+    torch tensors; outputs are NumPy arrays, or CUDA torch tensors if device.
+    Returns a dict with 'mean', 'variance', 'samples', 'ms'."""
+    lib = load()
+    nx = post.prob.nx
+    q = lrp_query()
+    res = lrp_query_result()
+    keep = []
+    out = {}
+    q.kind = kind
+    q.sigma = float(sigma)
+
+    def alloc(shape):
+        if device:
+            import torch
+            t = torch.empty(shape[::-1] if len(shape) == 2 else shape, dtype=torch.float64, device="cuda")
+            return (t.t() if len(shape) == 2 else t), t.data_ptr()
+        a = np.zeros(shape, order="F")
+        return a, a.ctypes.data
+
+    def inp(x, dtype):
+        if _is_torch(x):
+            t = x.contiguous()
+            keep.append(t)
+            return t.data_ptr(), t.numel()
+        a = np.ascontiguousarray(np.asarray(x, dtype=dtype).ravel())
+        keep.append(a)
+        return a.ctypes.data, a.size
+
+    if y_obs is not None:
+        q.y_obs, _ = inp(y_obs, np.float64)
+    if kind & (LRP_Q_MEAN | LRP_Q_SAMPLES):
+        out["mean"], res.mean = alloc((nx,))
+    if kind & LRP_Q_VARIANCE:
+        q.points, q.n_points = inp(points, np.int32)
+        out["variance"], res.variance = alloc((q.n_points,))
+    if kind & LRP_Q_SAMPLES:
+        if _is_torch(xi):
+            a = _Arg(xi, nx)
+            keep.append(a)
+            q.xi, q.n_samples = a.ptr, a.ncols
+        else:
+            x = np.asfortranarray(np.asarray(xi, dtype=np.float64).reshape(nx, -1))
+            keep.append(x)
+            q.xi, q.n_samples = x.ctypes.data, x.shape[1]
+        out["samples"], res.samples = alloc((nx, q.n_samples))
+    _check(lib.lrp_posterior_query(post.handle, C.byref(q), C.byref(res)), allow=(LRP_OK, LRP_ENOCONV))
+    out["ms"] = res.ms
+    return out
+
+
+def lrp_posterior_save(post: Posterior, path: str):
+    _check(load().lrp_posterior_save(post.handle, path.encode()))
+
+
+def lrp_posterior_load(prob: Problem, path: str) -> Posterior:
+    h = C.c_void_p()
+    _check(load().lrp_posterior_load(prob.handle, path.encode(), C.byref(h)))
+    return Posterior(h, prob)
+
+
+def lrp_last_error() -> str:
+    return load().lrp_last_error().decode()
+
+
+def lrp_version() -> str:
+    return load().lrp_version().decode()
+
+
+def lrp_sweep_profile(prob: "Problem", mode: int = -1):
+    """Sweep-kernel ledger: returns (ms, launches, algorithmic bytes) accumulated
+    so far; mode 1 resets and starts recording, 0 resets and stops, -1 reads."""
+    ms, n, b = C.c_double(), C.c_ulonglong(), C.c_double()
+    _check(load().lrp_sweep_profile(prob.handle, int(mode), C.byref(ms), C.byref(n), C.byref(b)))
+    return ms.value, int(n.value), b.value
+
+
+def lrp_kernel_launches() -> int:
+    return int(load().lrp_kernel_launches())

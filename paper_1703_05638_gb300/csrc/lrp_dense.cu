@@ -1,0 +1,733 @@
+// FP64 dense kernels of the Lanczos / posterior stage:
+//  * gemm_tn: C = A^T B for tall-skinny A (nx x m) and B (nx x nb), split over
+//    row chunks with a fixed-order second-stage reduction (deterministic);
+//  * gemm_nn: Y = beta Y + alpha A M for A (nx x m) and a small M (m x nc);
+//  * Cholesky of a small Gram matrix (CholQR) with a rank-deficiency test;
+//  * symmetric eigensolver for the (block) tridiagonal Lanczos matrix:
+//    Householder reduction to tridiagonal form with accumulated reflections,
+//    then implicit QL iterations with Wilkinson shifts; one CTA;
+//  * small elementwise helpers (column norms, scaling, gathers, fills).
+// FP64 throughout: the Lanczos eigensolve, re-orthogonalisation and the
+// posterior factors stay in FP64.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "lrp_dense.h"
+#include "lrp_internal.h"
+
+namespace lrp {
+
+// ---------------------------------------------------------------- gemm_tn
+#define TN_TI 16
+#define TN_TR 64
+
+__global__ void __launch_bounds__(256) k_gemm_tn(int nx, int m, int nb, const double* __restrict__ A,
+                                                  int lda, const double* __restrict__ B, int ldb,
+                                                  double* __restrict__ part, int rows_per_chunk) {
+  __shared__ double As[TN_TI][TN_TR + 1];
+  __shared__ double Bs[16][TN_TR + 1];
+  const int i0 = blockIdx.x * TN_TI;
+  const int chunk = blockIdx.y;
+  const int r0 = chunk * rows_per_chunk;
+  const int r1 = min(nx, r0 + rows_per_chunk);
+  const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
+  double acc = 0.0;
+  for (int rb = r0; rb < r1; rb += TN_TR) {
+    for (int e = threadIdx.x; e < TN_TI * TN_TR; e += 256) {
+      const int ci = e / TN_TR, rr = e % TN_TR;
+      const int i = i0 + ci, r = rb + rr;
+      As[ci][rr] = (i < m && r < r1) ? A[(size_t)i * lda + r] : 0.0;
+    }
+    for (int e = threadIdx.x; e < 16 * TN_TR; e += 256) {
+      const int cj = e / TN_TR, rr = e % TN_TR;
+      const int r = rb + rr;
+      Bs[cj][rr] = (cj < nb && r < r1) ? B[(size_t)cj * ldb + r] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int rr = 0; rr < TN_TR; ++rr) acc += As[ti][rr] * Bs[tj][rr];
+    __syncthreads();
+  }
+  const int i = i0 + ti;
+  if (i < m && tj < nb) part[((size_t)chunk * m + i) * 16 + tj] = acc;
+}
+
+__global__ void k_reduce_parts(int m, int nb, int nchunk, const double* __restrict__ part,
+                               double* __restrict__ C, int ldc, double alpha, double beta) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * nb) return;
+  const int i = e / nb, j = e % nb;
+  double s = 0.0;
+  for (int c = 0; c < nchunk; ++c) s += part[((size_t)c * m + i) * 16 + j];
+  double* out = C + (size_t)j * ldc + i;
+  *out = (beta == 0.0 ? 0.0 : beta * *out) + alpha * s;
+}
+
+// ---------------------------------------------------------------- gemm_nn
+#define NN_TI 128
+
+__global__ void __launch_bounds__(256) k_gemm_nn(int nx, int m, int nc, double alpha,
+                                                  const double* __restrict__ A, int lda,
+                                                  const double* __restrict__ M, int ldm, double beta,
+                                                  double* Y, int ldy) {
+  __shared__ double Ms[NN_TI][16];
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j0 = blockIdx.y * 16;
+  const int ncl = min(16, nc - j0);
+  double acc[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) acc[j] = 0.0;
+  for (int ib = 0; ib < m; ib += NN_TI) {
+    const int ni = min(NN_TI, m - ib);
+    __syncthreads();
+    for (int e = threadIdx.x; e < NN_TI * 16; e += blockDim.x) {
+      const int ii = e >> 4, jj = e & 15;
+      Ms[ii][jj] = (ii < ni && jj < ncl) ? M[(size_t)(j0 + jj) * ldm + ib + ii] : 0.0;
+    }
+    __syncthreads();
+    if (p < nx) {
+      for (int ii = 0; ii < ni; ++ii) {
+        const double a = A[(size_t)(ib + ii) * lda + p];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[j] += a * Ms[ii][j];
+      }
+    }
+  }
+  if (p < nx) {
+    for (int j = 0; j < ncl; ++j) {
+      double* y = Y + (size_t)(j0 + j) * ldy + p;
+      *y = (beta == 0.0 ? 0.0 : beta * *y) + alpha * acc[j];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- small Cholesky
+// G (nb x nb, ld nb) -> R upper triangular with R^T R = G, Rinv = R^{-1}.
+// A pivot below tol * G_cc marks the column deficient: its R column is set
+// to the unit column (so Rinv stays finite) and flags[c] = 1.
+__global__ void k_chol_small(int nb, const double* __restrict__ G, double* __restrict__ R,
+                             double* __restrict__ Rinv, int* __restrict__ flags, double tol) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double r[16][16];
+  for (int i = 0; i < nb; ++i)
+    for (int j = 0; j < nb; ++j) r[i][j] = 0.0;
+  for (int c = 0; c < nb; ++c) {
+    double d = G[c * nb + c];
+    for (int i = 0; i < c; ++i) d -= r[i][c] * r[i][c];
+    const double gcc = G[c * nb + c];
+    if (!(d > tol * gcc) || !(gcc > 0.0) || !isfinite(d)) {
+      flags[c] = 1;
+      r[c][c] = 1.0;
+      for (int e = c + 1; e < nb; ++e) r[c][e] = 0.0;
+      continue;
+    }
+    flags[c] = 0;
+    r[c][c] = sqrt(d);
+    for (int e = c + 1; e < nb; ++e) {
+      double v = G[e * nb + c];
+      for (int i = 0; i < c; ++i) v -= r[i][c] * r[i][e];
+      r[c][e] = v / r[c][c];
+    }
+  }
+  // inverse of the upper triangular r by columns
+  double ri[16][16];
+  for (int i = 0; i < nb; ++i)
+    for (int j = 0; j < nb; ++j) ri[i][j] = 0.0;
+  for (int j = 0; j < nb; ++j) {
+    ri[j][j] = 1.0 / r[j][j];
+    for (int i = j - 1; i >= 0; --i) {
+      double s = 0.0;
+      for (int k = i + 1; k <= j; ++k) s += r[i][k] * ri[k][j];
+      ri[i][j] = -s / r[i][i];
+    }
+  }
+  // column-major outputs
+  for (int i = 0; i < nb; ++i)
+    for (int j = 0; j < nb; ++j) {
+      R[j * nb + i] = r[i][j];
+      Rinv[j * nb + i] = ri[i][j];
+    }
+}
+
+// C = A B for small upper-triangular nb x nb column-major matrices.
+__global__ void k_small_mm(int nb, const double* A, const double* B, double* C) {
+  const int e = threadIdx.x;
+  if (e >= nb * nb) return;
+  const int i = e % nb, j = e / nb;
+  double s = 0.0;
+  for (int k = 0; k < nb; ++k) s += A[k * nb + i] * B[j * nb + k];
+  C[j * nb + i] = s;
+}
+
+// ---------------------------------------------------------------- eigensolver
+// Symmetric eigendecomposition of the n x n matrix A (column-major, ld lda,
+// destroyed) into theta (decreasing) and Z (n x n, ld ldz), one CTA.
+// Step 1: Householder reflections H_k = I - 2 v v^T zero column k below the
+// subdiagonal; A <- H_k A H_k, Z <- Z H_k.
+// Step 2: implicit QL on the tridiagonal (d, e): repeatedly pick the
+// unreduced block [l, m], shift by the eigenvalue of the leading 2x2 closest
+// to d_l, chase the bulge with plane rotations from m-1 down to l. The
+// rotation angles depend only on (d, e): thread 0 computes a whole chase,
+// then all threads apply it to their rows of Z.
+// Step 3: sort by decreasing eigenvalue.
+#define EIG_NT 512
+
+__global__ void __launch_bounds__(EIG_NT) k_eig_sym(int n, double* A, int lda, double* Z, int ldz,
+                                                     double* theta, double* work, int* status,
+                                                     const int* n_batch, size_t strideA, size_t strideZ,
+                                                     size_t strideT, size_t strideW) {
+  // batched mode: block b works on matrix b (its size in n_batch[b])
+  if (n_batch) {
+    const int b = blockIdx.x;
+    n = n_batch[b];
+    lda = ldz = n;
+    A += b * strideA;
+    Z += b * strideZ;
+    theta += b * strideT;
+    work += b * strideW;
+    if (status) status += b;
+  }
+  __shared__ double s_red[EIG_NT / 32];
+  __shared__ double s_scal[4];
+  __shared__ double s_c[1024], s_s[1024];
+  __shared__ int s_int[4];
+  const int tid = threadIdx.x;
+  double* v = work;          // n
+  double* pvec = work + n;   // n
+  double* d = work + 2 * n;  // n
+  double* e = work + 3 * n;  // n
+  auto At = [&](int i, int j) -> double& { return A[(size_t)j * lda + i]; };
+  auto Zt = [&](int i, int j) -> double& { return Z[(size_t)j * ldz + i]; };
+  auto block_sum = [&](double x) -> double {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((tid & 31) == 0) s_red[tid >> 5] = x;
+    __syncthreads();
+    double s = 0.0;
+    for (int w = 0; w < EIG_NT / 32; ++w) s += s_red[w];
+    __syncthreads();
+    return s;
+  };
+  for (int i = tid; i < n * n; i += EIG_NT) Zt(i % n, i / n) = (i % n == i / n) ? 1.0 : 0.0;
+  __syncthreads();
+  // ---- Householder tridiagonalisation
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m0 = k + 1, len = n - m0;
+    double part = 0.0;
+    for (int i = tid; i < len; i += EIG_NT) {
+      const double x = At(m0 + i, k);
+      part += x * x;
+    }
+    const double xnorm2 = block_sum(part);
+    const double x0 = At(m0, k);
+    const double xnorm = sqrt(xnorm2);
+    const double tail2 = xnorm2 - x0 * x0;
+    if (!(tail2 > 1e-300)) continue;  // column already reduced
+    const double alpha = x0 > 0 ? -xnorm : xnorm;
+    // v = x - alpha e1, normalised
+    const double v0 = x0 - alpha;
+    const double vnorm = sqrt(tail2 + v0 * v0);
+    for (int i = tid; i < len; i += EIG_NT) v[i] = (i == 0 ? v0 : At(m0 + i, k)) / vnorm;
+    __syncthreads();
+    // p = 2 B v on the trailing block B = A[m0:, m0:]
+    for (int i = tid; i < len; i += EIG_NT) {
+      double s = 0.0;
+      for (int j = 0; j < len; ++j) s += At(m0 + i, m0 + j) * v[j];
+      pvec[i] = 2.0 * s;
+    }
+    __syncthreads();
+    double kp = 0.0;
+    for (int i = tid; i < len; i += EIG_NT) kp += v[i] * pvec[i];
+    const double K = block_sum(kp);
+    // q = p - K v; B <- B - v q^T - q v^T
+    for (int i = tid; i < len; i += EIG_NT) pvec[i] -= K * v[i];
+    __syncthreads();
+    for (int idx = tid; idx < len * len; idx += EIG_NT) {
+      const int i = idx % len, j = idx / len;
+      At(m0 + i, m0 + j) -= v[i] * pvec[j] + pvec[i] * v[j];
+    }
+    for (int i = tid; i < len; i += EIG_NT) {
+      At(m0 + i, k) = (i == 0) ? alpha : 0.0;
+      At(k, m0 + i) = (i == 0) ? alpha : 0.0;
+    }
+    // Z[:, m0:] <- Z[:, m0:] (I - 2 v v^T)
+    for (int r = tid; r < n; r += EIG_NT) {
+      double s = 0.0;
+      for (int j = 0; j < len; ++j) s += Zt(r, m0 + j) * v[j];
+      s *= 2.0;
+      for (int j = 0; j < len; ++j) Zt(r, m0 + j) -= s * v[j];
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < n; i += EIG_NT) {
+    d[i] = At(i, i);
+    e[i] = (i + 1 < n) ? At(i + 1, i) : 0.0;
+  }
+  __syncthreads();
+  // ---- implicit QL with Wilkinson shifts
+  if (tid == 0) s_int[0] = 0;
+  __syncthreads();
+  for (int l = 0; l < n; ++l) {
+    int iter = 0;
+    for (;;) {
+      // thread 0 finds the block end and computes the rotation chase
+      if (tid == 0) {
+        int m = l;
+        for (; m < n - 1; ++m) {
+          const double dd = fabs(d[m]) + fabs(d[m + 1]);
+          if (fabs(e[m]) <= 2.220446049250313e-16 * dd) break;
+        }
+        s_int[1] = m;
+        s_int[2] = 0;
+        if (m != l) {
+          if (iter >= 60) {
+            s_int[0] = 1;  // no convergence; leave as is
+            s_int[1] = l;
+          } else {
+            double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+            double r = hypot(g, 1.0);
+            g = d[m] - d[l] + e[l] / (g + (g >= 0 ? fabs(r) : -fabs(r)));
+            double s = 1.0, c = 1.0, p = 0.0;
+            int i = m - 1;
+            int cnt = 0;
+            bool early = false;
+            for (; i >= l; --i) {
+              const double f = s * e[i];
+              const double b = c * e[i];
+              r = hypot(f, g);
+              e[i + 1] = r;
+              if (r == 0.0) {
+                d[i + 1] -= p;
+                e[m] = 0.0;
+                early = true;
+                break;
+              }
+              s = f / r;
+              c = g / r;
+              g = d[i + 1] - p;
+              r = (d[i] - g) * s + 2.0 * c * b;
+              p = s * r;
+              d[i + 1] = g + p;
+              g = c * r - b;
+              s_c[cnt] = c;
+              s_s[cnt] = s;
+              ++cnt;
+            }
+            if (!early) {
+              d[l] -= p;
+              e[l] = g;
+              e[m] = 0.0;
+            }
+            s_int[2] = cnt;
+          }
+        }
+      }
+      __syncthreads();
+      const int m = s_int[1];
+      const int cnt = s_int[2];
+      if (m == l) break;
+      // apply the chase to the rows of Z: rotation t acts on columns (i, i+1), i = m-1-t
+      for (int r = tid; r < n; r += EIG_NT) {
+        for (int t = 0; t < cnt; ++t) {
+          const int i = m - 1 - t;
+          const double c = s_c[t], s = s_s[t];
+          const double zi = Zt(r, i), zi1 = Zt(r, i + 1);
+          Zt(r, i + 1) = s * zi + c * zi1;
+          Zt(r, i) = c * zi - s * zi1;
+        }
+      }
+      __syncthreads();
+      ++iter;
+    }
+  }
+  // ---- sort decreasing (selection sort by thread 0 on indices, then permute)
+  int* perm = (int*)(work + 4 * n);
+  if (tid == 0) {
+    for (int i = 0; i < n; ++i) perm[i] = i;
+    for (int i = 0; i < n; ++i) {
+      int best = i;
+      for (int j = i + 1; j < n; ++j)
+        if (d[perm[j]] > d[perm[best]]) best = j;
+      const int tmp = perm[i];
+      perm[i] = perm[best];
+      perm[best] = tmp;
+    }
+    if (status) *status = s_int[0];
+  }
+  __syncthreads();
+  for (int i = tid; i < n; i += EIG_NT) theta[i] = d[perm[i]];
+  // permute columns of Z into A (as scratch), then copy back
+  for (int idx = tid; idx < n * n; idx += EIG_NT) {
+    const int r = idx % n, c = idx / n;
+    At(r, c) = Zt(r, perm[c]);
+  }
+  __syncthreads();
+  for (int idx = tid; idx < n * n; idx += EIG_NT) {
+    const int r = idx % n, c = idx / n;
+    Zt(r, c) = At(r, c);
+  }
+}
+
+// resid[i] = || B (nb x nb upper, col-major) * Z[row0:row0+nb, i] ||, i < k
+__global__ void k_ritz_resid(int k, int nb, const double* B, const double* Z, int ldz, int row0,
+                             double* resid) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= k) return;
+  double s2 = 0.0;
+  for (int r = 0; r < nb; ++r) {
+    double s = 0.0;
+    for (int c = 0; c < nb; ++c) s += B[c * nb + r] * Z[(size_t)i * ldz + row0 + c];
+    s2 += s * s;
+  }
+  resid[i] = sqrt(s2);
+}
+
+// T[r0:r0+nb, c0:c0+nb] = S (and optionally the transpose block), S col-major nb x nb
+__global__ void k_set_block(double* T, int ldt, int r0, int c0, int nb, const double* S, int lds,
+                            int symmetrize, int also_transpose) {
+  const int e = threadIdx.x;
+  if (e >= nb * nb) return;
+  const int i = e % nb, j = e / nb;
+  double v = S[(size_t)j * lds + i];
+  if (symmetrize) v = 0.5 * (v + S[(size_t)i * lds + j]);
+  T[(size_t)(c0 + j) * ldt + r0 + i] = v;
+  if (also_transpose) T[(size_t)(r0 + i) * ldt + c0 + j] = v;
+}
+
+// zero the columns c of an nb x nb col-major matrix with flags[c] != 0
+__global__ void k_zero_flagged_cols(int nb, double* M, const int* flags) {
+  const int e = threadIdx.x;
+  if (e >= nb * nb) return;
+  const int j = e / nb;
+  if (flags[j]) M[e] = 0.0;
+}
+
+// Pseudo-random values in [-1, 1) from a counter-based hash (splitmix64 of
+// seed, column and row); fills columns with flags[c] != 0 (flags NULL = all).
+__device__ __forceinline__ double hash_uniform(unsigned long long seed, int col, int row) {
+  unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(col + 1) +
+                         0xD1B54A32D192ED03ull * (unsigned long long)(row + 1);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
+__global__ void k_fill_random(int nx, int nb, double* W, int ldw, const int* flags,
+                              unsigned long long seed) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  if (p >= nx || c >= nb) return;
+  if (flags && !flags[c]) return;
+  W[(size_t)c * ldw + p] = hash_uniform(seed, c, p);
+}
+
+__global__ void k_copy_cols(int nx, int nb, const double* S, int lds, double* D, int ldd) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  if (p >= nx || c >= nb) return;
+  D[(size_t)c * ldd + p] = S[(size_t)c * lds + p];
+}
+
+// y[j] = scale * x[j] * f(lambda_j): mode 0 -> d = lam/(lam+1); mode 1 -> (1+lam)^{-1/2} - 1
+__global__ void k_diag_scale(int k, int ncols, const double* lam, double lam_scale, int mode,
+                             double* C, int ldc) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= k * ncols) return;
+  const int i = e % k, j = e / k;
+  const double l = lam[i] * lam_scale;
+  const double f = (mode == 0) ? l / (l + 1.0) : 1.0 / sqrt(1.0 + l) - 1.0;
+  C[(size_t)j * ldc + i] *= f;
+}
+
+// var[i] = pdiag[i] - sum_j d_j G[node_i, j]^2
+__global__ void k_variance(int np, const int* nodes, const double* pdiag, int k, const double* lam,
+                           double lam_scale, const double* G, int ldg, double* var) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  const int node = nodes[i];
+  double s = 0.0;
+  for (int j = 0; j < k; ++j) {
+    const double l = lam[j] * lam_scale;
+    const double g = G[(size_t)j * ldg + node];
+    s += (l / (l + 1.0)) * g * g;
+  }
+  var[i] = pdiag[i] - s;
+}
+
+// E[:, i] = e_{nodes[i]} (columns i0..i0+nc)
+__global__ void k_unit_cols(int nx, int nc, const int* nodes, int i0, double* E, int lde) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  if (p >= nx || c >= nc) return;
+  E[(size_t)c * lde + p] = (nodes[i0 + c] == p) ? 1.0 : 0.0;
+}
+
+// out[i] = sum_p X[i][p]^2 for columns i < nc (one block per column)
+__global__ void k_col_norm2(int nx, int nc, const double* X, int ldx, double* out) {
+  __shared__ double s_red[32];
+  const int c = blockIdx.x;
+  if (c >= nc) return;
+  double s = 0.0;
+  for (int p = threadIdx.x; p < nx; p += blockDim.x) {
+    const double x = X[(size_t)c * ldx + p];
+    s += x * x;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_red[w];
+    out[c] = t;
+  }
+}
+
+__global__ void k_axpby(size_t n, double a, const double* x, double b, double* y) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = a * x[i] + (b == 0.0 ? 0.0 : b * y[i]);
+}
+
+// Y[:, j] += m (broadcast a vector into every column)
+__global__ void k_add_vec_cols(int nx, int nc, const double* m, double* Y, int ldy) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  if (p >= nx || c >= nc) return;
+  Y[(size_t)c * ldy + p] += m[p];
+}
+
+// ---------------------------------------------------------------- block Gram-Schmidt
+// Rank-revealing orthonormalisation of the s <= 16 columns of B (nx x s, ld
+// ldb) in place, one CTA per matrix (blockIdx.x selects B + b*strideB and
+// R + b*strideR): column c is orthogonalised against columns 0..c-1 by
+// classical Gram-Schmidt twice (a third pass when the norm fell below 1/10),
+// then normalised. A column whose remaining norm is at most drop_tol times
+// its norm on entry lies numerically in the span of the previous ones: it is
+// set to zero and its diagonal entry of R is 0. Output: B = Q R with R
+// (s x s, col-major) upper triangular; zero columns of Q have zero rows in R.
+#define GS_NT 512
+__global__ void __launch_bounds__(GS_NT) k_block_gs(int nx, int s, double* B, size_t strideB, int ldb,
+                                                     double* R, size_t strideR, double drop_tol,
+                                                     int* ndrop) {
+  __shared__ double s_part[GS_NT / 32][17];
+  __shared__ double s_tot[17];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  double* Bb = B + blockIdx.x * strideB;
+  double* Rb = R + blockIdx.x * strideR;
+  // reduce acc[0..16] over the CTA into s_tot
+  auto reduce17 = [&](double* acc) {
+#pragma unroll
+    for (int i = 0; i < 17; ++i) {
+      double v = acc[i];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) s_part[wid][i] = v;
+    }
+    __syncthreads();
+    if (tid < 17) {
+      double t = 0.0;
+      for (int w = 0; w < GS_NT / 32; ++w) t += s_part[w][tid];
+      s_tot[tid] = t;
+    }
+    __syncthreads();
+  };
+  int dropped = 0;
+  for (int c = 0; c < s; ++c) {
+    double* w = Bb + (size_t)c * ldb;
+    double rc[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) rc[i] = 0.0;
+    double n0 = 0.0, nprev = 0.0, ncur = 0.0;
+    for (int pass = 0; pass < 4; ++pass) {
+      // h = Q[:, :c]^T w and |w|^2
+      double acc[17];
+#pragma unroll
+      for (int i = 0; i < 17; ++i) acc[i] = 0.0;
+      for (int p = tid; p < nx; p += GS_NT) {
+        const double wp = w[p];
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          if (i < c) acc[i] += Bb[(size_t)i * ldb + p] * wp;
+        acc[16] += wp * wp;
+      }
+      reduce17(acc);
+      ncur = s_tot[16];
+      if (pass == 0) n0 = ncur;
+      // stop after two projections, or a third one if the norm collapsed
+      const bool more = (c > 0) && (pass < 2 || (pass == 2 && ncur < 1e-2 * nprev));
+      if (!more) break;
+      double h[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        h[i] = (i < c) ? s_tot[i] : 0.0;
+        rc[i] += h[i];
+      }
+      __syncthreads();
+      for (int p = tid; p < nx; p += GS_NT) {
+        double v = w[p];
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          if (i < c) v -= h[i] * Bb[(size_t)i * ldb + p];
+        w[p] = v;
+      }
+      __syncthreads();
+      nprev = ncur;
+    }
+    const double nrm = sqrt(ncur);
+    const bool drop = !(nrm > drop_tol * sqrt(n0)) || !(nrm > 0.0);
+    const double scale = drop ? 0.0 : 1.0 / nrm;
+    for (int p = tid; p < nx; p += GS_NT) w[p] *= scale;
+    if (tid == 0) {
+      for (int i = 0; i < s; ++i) Rb[(size_t)c * s + i] = (i < c) ? rc[i] : (i == c ? (drop ? 0.0 : nrm) : 0.0);
+    }
+    dropped += drop ? 1 : 0;
+    __syncthreads();
+  }
+  if (tid == 0 && ndrop) ndrop[blockIdx.x] = dropped;
+}
+
+// --------------------------------------------------------------------------- host wrappers
+
+cudaError_t gemm_tn(cudaStream_t s, int nx, int m, int nb, const double* A, int lda, const double* B,
+                    int ldb, double* C, int ldc, double alpha, double beta, double* part, size_t part_cap) {
+  int nchunk = std::min(128, std::max(1, (nx + 4095) / 4096));
+  while ((size_t)nchunk * m * 16 > part_cap && nchunk > 1) nchunk /= 2;
+  const int rows = ((nx + nchunk - 1) / nchunk + TN_TR - 1) / TN_TR * TN_TR;
+  nchunk = (nx + rows - 1) / rows;
+  for (int j0 = 0; j0 < nb; j0 += 16) {
+    const int nbl = std::min(16, nb - j0);
+    dim3 grid((m + TN_TI - 1) / TN_TI, nchunk);
+    note_launch();
+    k_gemm_tn<<<grid, 256, 0, s>>>(nx, m, nbl, A, lda, B + (size_t)j0 * ldb, ldb, part, rows);
+    note_launch();
+    k_reduce_parts<<<(m * nbl + 255) / 256, 256, 0, s>>>(m, nbl, nchunk, part, C + (size_t)j0 * ldc,
+                                                         ldc, alpha, beta);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t gemm_nn(cudaStream_t s, int nx, int m, int nc, double alpha, const double* A, int lda,
+                    const double* M, int ldm, double beta, double* Y, int ldy) {
+  if (m == 0) {
+    if (beta == 1.0) return cudaSuccess;
+  }
+  dim3 grid((nx + 255) / 256, (nc + 15) / 16);
+  note_launch();
+  k_gemm_nn<<<grid, 256, 0, s>>>(nx, m, nc, alpha, A, lda, M, ldm, beta, Y, ldy);
+  return cudaGetLastError();
+}
+
+cudaError_t chol_small(cudaStream_t s, int nb, const double* G, double* R, double* Rinv, int* flags,
+                       double tol) {
+  note_launch();
+  k_chol_small<<<1, 32, 0, s>>>(nb, G, R, Rinv, flags, tol);
+  return cudaGetLastError();
+}
+
+cudaError_t small_mm(cudaStream_t s, int nb, const double* A, const double* B, double* C) {
+  note_launch();
+  k_small_mm<<<1, 256, 0, s>>>(nb, A, B, C);
+  return cudaGetLastError();
+}
+
+cudaError_t eig_sym(cudaStream_t s, int n, double* A, int lda, double* Z, int ldz, double* theta,
+                    double* work, int* status) {
+  if (n > 1024) return cudaErrorInvalidValue;
+  note_launch();
+  k_eig_sym<<<1, EIG_NT, 0, s>>>(n, A, lda, Z, ldz, theta, work, status, nullptr, 0, 0, 0, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t ritz_resid(cudaStream_t s, int k, int nb, const double* B, const double* Z, int ldz, int row0,
+                       double* resid) {
+  note_launch();
+  k_ritz_resid<<<(k + 127) / 128, 128, 0, s>>>(k, nb, B, Z, ldz, row0, resid);
+  return cudaGetLastError();
+}
+
+cudaError_t set_block(cudaStream_t s, double* T, int ldt, int r0, int c0, int nb, const double* S, int lds,
+                      bool symmetrize, bool also_transpose) {
+  note_launch();
+  k_set_block<<<1, 256, 0, s>>>(T, ldt, r0, c0, nb, S, lds, symmetrize ? 1 : 0, also_transpose ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t zero_flagged_cols(cudaStream_t s, int nb, double* M, const int* flags) {
+  note_launch();
+  k_zero_flagged_cols<<<1, 256, 0, s>>>(nb, M, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t fill_random(cudaStream_t s, int nx, int nb, double* W, int ldw, const int* flags,
+                        unsigned long long seed) {
+  dim3 grid((nx + 255) / 256, nb);
+  note_launch();
+  k_fill_random<<<grid, 256, 0, s>>>(nx, nb, W, ldw, flags, seed);
+  return cudaGetLastError();
+}
+
+cudaError_t copy_cols(cudaStream_t s, int nx, int nb, const double* S, int lds, double* D, int ldd) {
+  dim3 grid((nx + 255) / 256, nb);
+  note_launch();
+  k_copy_cols<<<grid, 256, 0, s>>>(nx, nb, S, lds, D, ldd);
+  return cudaGetLastError();
+}
+
+cudaError_t diag_scale(cudaStream_t s, int k, int ncols, const double* lam, double lam_scale, int mode,
+                       double* C, int ldc) {
+  note_launch();
+  k_diag_scale<<<(k * ncols + 255) / 256, 256, 0, s>>>(k, ncols, lam, lam_scale, mode, C, ldc);
+  return cudaGetLastError();
+}
+
+cudaError_t variance(cudaStream_t s, int np, const int* nodes, const double* pdiag, int k, const double* lam,
+                     double lam_scale, const double* G, int ldg, double* var) {
+  note_launch();
+  k_variance<<<(np + 127) / 128, 128, 0, s>>>(np, nodes, pdiag, k, lam, lam_scale, G, ldg, var);
+  return cudaGetLastError();
+}
+
+cudaError_t unit_cols(cudaStream_t s, int nx, int nc, const int* nodes, int i0, double* E, int lde) {
+  dim3 grid((nx + 255) / 256, nc);
+  note_launch();
+  k_unit_cols<<<grid, 256, 0, s>>>(nx, nc, nodes, i0, E, lde);
+  return cudaGetLastError();
+}
+
+cudaError_t col_norm2(cudaStream_t s, int nx, int nc, const double* X, int ldx, double* out) {
+  note_launch();
+  k_col_norm2<<<nc, 256, 0, s>>>(nx, nc, X, ldx, out);
+  return cudaGetLastError();
+}
+
+cudaError_t axpby(cudaStream_t s, size_t n, double a, const double* x, double b, double* y) {
+  note_launch();
+  k_axpby<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, a, x, b, y);
+  return cudaGetLastError();
+}
+
+cudaError_t add_vec_cols(cudaStream_t s, int nx, int nc, const double* m, double* Y, int ldy) {
+  dim3 grid((nx + 255) / 256, nc);
+  note_launch();
+  k_add_vec_cols<<<grid, 256, 0, s>>>(nx, nc, m, Y, ldy);
+  return cudaGetLastError();
+}
+
+cudaError_t block_gs(cudaStream_t s, int batch, int nx, int ncols, double* B, size_t strideB, int ldb, double* R,
+                     size_t strideR, double drop_tol, int* ndrop) {
+  if (ncols > 16) return cudaErrorInvalidValue;
+  note_launch();
+  k_block_gs<<<batch, GS_NT, 0, s>>>(nx, ncols, B, strideB, ldb, R, strideR, drop_tol, ndrop);
+  return cudaGetLastError();
+}
+
+cudaError_t eig_sym_batched(cudaStream_t s, int batch, const int* n_dev, int nmax, double* A, size_t strideA,
+                            double* Z, size_t strideZ, double* theta, size_t strideT, double* work,
+                            size_t strideW, int* status) {
+  if (nmax > 1024) return cudaErrorInvalidValue;
+  note_launch();
+  k_eig_sym<<<batch, EIG_NT, 0, s>>>(nmax, A, nmax, Z, nmax, theta, work, status, n_dev, strideA, strideZ,
+                                     strideT, strideW);
+  return cudaGetLastError();
+}
+
+}  // namespace lrp

@@ -1,0 +1,204 @@
+// Internal structures of the GB300 low-rank posterior library.
+//
+// Layout in HBM (per problem):
+//  * geometry of the multigrid hierarchy: n_l = (n+1)/2^l - 1 nodes per axis,
+//    level 0 the finest; face diffusivities per level (FP64 and FP32 copies)
+//    for the time-step operator I + tau L; the prior operator I + alpha L0 has
+//    kappa = 1 and needs no arrays;
+//  * sensors: per sensor 2^dim (node, weight) pairs (node -1 = unused) and the
+//    transpose as CSR over fine nodes (sensor, weight) for the adjoint source;
+//  * solver workspace: one slab per "team" (a thread-block cluster owning a
+//    group of BV columns); inside a slab every grid vector stores BV columns
+//    interleaved, element (p, j) at p*BV + j, so a thread reading item
+//    (p, j) and its neighbours reads whole BV-wide rows.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "lrp.h"
+
+#define LRP_MAXLEV 10
+#define LRP_MAXBV 16
+
+namespace lrp {
+
+// Division by a runtime constant d (dividend < 2^31): q = (umulhi(x,m)+x) >> s.
+struct FastDiv {
+  uint32_t d, m, s;
+};
+
+inline FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f;
+  f.d = d;
+  uint32_t l = 0;
+  while ((1ull << l) < d) ++l;
+  f.s = l;
+  f.m = (uint32_t)((((uint64_t)1 << 32) * (((uint64_t)1 << l) - d)) / d + 1);
+  return f;
+}
+
+// One multigrid level of one operator I + c L_l.
+struct OpLevel {
+  int n;        // nodes per axis
+  int N;        // n^dim
+  FastDiv dn;   // division by n
+  double ch2;   // c / h_l^2
+  const double* kd[3];  // face diffusivity (NULL -> 1), see kappa layout in lrp.h
+  const float* kf[3];
+};
+
+struct Op {
+  int L;        // number of levels
+  int Lt;       // levels worked by the whole team (the rest by CTA rank 0 alone)
+  int has_kappa;
+  OpLevel lv[LRP_MAXLEV];
+};
+
+// Stage mask of one sweep-kernel launch.
+enum : unsigned {
+  ST_LOAD_X = 1u << 0,      // load column-major X into the start buffer
+  ST_PRIOR_IN = 1u << 1,    // solve (I + alpha L0) z = x
+  ST_FORWARD = 1u << 2,     // forward implicit-Euler sweep with observation
+  ST_LOAD_D = 1u << 3,      // load column-major D (observations) into the team's D buffer
+  ST_ADJOINT = 1u << 4,     // adjoint sweep with the B^T source
+  ST_PRIOR_OUT = 1u << 5,   // solve (I + alpha L0) y = q
+  ST_STORE_Y = 1u << 6,     // store the result buffer to column-major Y
+  ST_STORE_D = 1u << 7,     // store the observations (unweighted) to column-major D
+  ST_TRAJ = 1u << 8         // copy every forward state into the trajectory chunk buffer
+};
+
+enum : int { STAT_NOCONV = 1, STAT_NONFINITE = 2 };
+
+struct SolveCfg {
+  double rtol;        // outer relative residual
+  double inner_rtol;  // mixed: FP32 inner relative residual
+  int maxit;          // PCG iterations per (inner) solve
+  int maxref;         // mixed: refinement sweeps
+  int nu;             // Jacobi sweeps pre and post
+  double omega;       // Jacobi damping
+};
+
+struct Stats {
+  unsigned long long solves;
+  unsigned long long iters;
+  unsigned long long refines;
+  int iters_max;
+  int refine_max;
+  unsigned long long max_rel_res_bits;  // double bits (non-negative)
+  int status;
+};
+
+struct SweepParams {
+  Op step, prior;
+  int dim;
+  int nt;             // steps of the forward sweep (last observed step unless the trajectory is kept)
+  int t_begin, t_end; // forward steps handled by this launch: t_begin+1 .. t_end
+  int adj_begin;      // adjoint: first (largest) step
+  int obs_every, n_obs, n_steps;
+  double inv_sigma2;
+  const int* obs_node;     // [n_obs][8]
+  const double* obs_w;     // [n_obs][8]
+  const int* bt_ptr;       // [N0+1]
+  const int* bt_idx;       // sensor index
+  const double* bt_w;
+  // launch geometry
+  int C, NT, BV, bv_shift, nvec, n_teams;
+  unsigned stages;
+  // column-major inputs/outputs
+  const double* X; int ldx;
+  double* Y; int ldy;
+  const double* Din; int lddin;
+  double* Dout; int lddout;
+  double* traj; int traj_ld; int traj_cols;  // trajectory chunk buffer: [team col][step in chunk][nx]
+  // workspace
+  char* ws;
+  size_t team_bytes;
+  size_t off_dbuf[3], off_bd, off_obs;        // double vectors
+  size_t off_r, off_p, off_q, off_c, off_e0[2];  // inner vectors (T)
+  size_t off_e[LRP_MAXLEV][2], off_f[LRP_MAXLEV]; // coarse levels (T)
+  int start_buf;      // index of the buffer that holds the sweep state at launch
+  int* end_buf;       // device: buffer index holding the state at exit (per team)
+  SolveCfg cfg;
+  Stats* stats;
+};
+
+// host-side helpers shared by the translation units
+struct DeviceBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace lrp
+
+// The opaque problem handle.
+struct lrp_problem {
+  lrp_problem_desc desc;
+  int dim, n, nx, nt, L;
+  int n_obs, n_steps, n_data, last_obs;
+  double tau, h;
+  cudaStream_t stream;
+  int device;
+  // device arrays
+  std::vector<void*> allocs;
+  lrp::Op step, prior;
+  int* obs_node;
+  double* obs_w;
+  int* bt_ptr;
+  int* bt_idx;
+  double* bt_w;
+  // solver workspace (grown on demand)
+  char* ws;
+  size_t ws_bytes;
+  lrp::Stats* stats;
+  int* end_buf;
+  int sm_count;
+  // tuned launch parameters
+  int team_ctas, team_cols, nthreads, coarse_items;
+  lrp::SolveCfg cfg;
+  uint64_t hash;
+  // sweep-kernel ledger (lrp_sweep_profile): CUDA-event time and algorithmic
+  // bytes of every sweep launch while enabled
+  int prof_on;
+  cudaEvent_t prof_ev[2];
+  double prof_ms;
+  double prof_bytes;
+  unsigned long long prof_launches;
+};
+
+struct lrp_posterior {
+  lrp_problem* prob;
+  int k;             // number of eigenpairs kept
+  int nx;
+  double sigma0;
+  double* lambda;    // device [k]
+  double* V;         // device nx x k
+  double* G;         // device nx x k, R^{-1} V
+  std::vector<double> lambda_host;
+  // cached prior diagonal at the last variance node set
+  std::vector<int> diag_nodes;
+  double* diag;      // device
+  int diag_cap;
+};
+
+namespace lrp {
+void note_launch(unsigned n = 1);
+void set_error(const std::string& msg);
+lrp_status cuda_status(cudaError_t e, const char* where);
+bool is_device_ptr(const void* p);
+
+// sweep launcher (lrp_sweep.cu)
+lrp_status run_sweep(lrp_problem* P, unsigned stages, int nvec, const double* X, int ldx,
+                     double* Y, int ldy, const double* Din, int lddin, double* Dout,
+                     int lddout, lrp_apply_stats* st, bool misfit_only);
+lrp_status run_sweep_ex(lrp_problem* Pr, unsigned stages, int nvec, const double* X, int ldx, double* Y,
+                        int ldy, const double* Din, int lddin, double* Dout, int lddout, lrp_apply_stats* st,
+                        int t_begin, int t_end, double* traj, int traj_cols);
+lrp_status trajectory_factors_impl(lrp_problem* P, int nvec, const double* U, int ldu, double* Wout,
+                                   double* Vout, int* ranks, lrp_apply_stats* stats, bool with_hessian,
+                                   double* Yout, int ldy);
+lrp_status ensure_workspace(lrp_problem* P, size_t bytes);
+}  // namespace lrp

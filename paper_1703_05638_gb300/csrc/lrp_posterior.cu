@@ -1,0 +1,486 @@
+// Low-rank posterior: block Lanczos with full re-orthogonalisation on the
+// prior-preconditioned misfit Hessian (Sec. 4 Algorithm 1 in its symmetric
+// form), Ritz pairs, the Sherman-Morrison-Woodbury factors (Sec. 2), and the
+// posterior queries (mean, pointwise variance, samples). Host code drives
+// the iteration; every arithmetic step runs in the library's kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lrp_dense.h"
+#include "lrp_internal.h"
+
+namespace lrp {
+
+lrp_status sweep_call(lrp_problem* P, unsigned stages, int nvec, const double* in, int ldin, int rows_in,
+                      double* out, int ldout, int rows_out, bool in_is_d, bool out_is_d,
+                      lrp_apply_stats* st, bool misfit_only);
+
+template <typename T>
+struct DArr {
+  T* p = nullptr;
+  size_t n = 0;
+  DArr() = default;
+  DArr(const DArr&) = delete;
+  DArr& operator=(const DArr&) = delete;
+  ~DArr() {
+    if (p) cudaFree(p);
+  }
+  cudaError_t alloc(size_t count) {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = count;
+    return cudaMalloc((void**)&p, std::max<size_t>(count, 1) * sizeof(T));
+  }
+  T* release() {
+    T* r = p;
+    p = nullptr;
+    return r;
+  }
+};
+
+#define CK(call)                                             \
+  do {                                                       \
+    cudaError_t _e = (call);                                 \
+    if (_e != cudaSuccess) return cuda_status(_e, #call);    \
+  } while (0)
+
+static const unsigned HESS_STAGES = ST_LOAD_X | ST_PRIOR_IN | ST_FORWARD | ST_ADJOINT | ST_PRIOR_OUT | ST_STORE_Y;
+
+// Scratch of one Lanczos run.
+struct LanczosWS {
+  DArr<double> part, G, R1, R2, Ri1, Ri2, R, C1, C2;
+  DArr<int> flags;
+  size_t part_cap = 0;
+};
+
+// Orthonormalise the nb columns of Wn (nx x nb, ld nx) against Q[:, :nprev]
+// (already orthonormal) by block CGS2 when nprev > 0 (coefficients added to
+// Cacc), then within the block by rank-revealing CGS2: Wn = Qn R with R upper
+// triangular in ws.R. A column numerically inside the span of the others
+// becomes zero with a zero diagonal in R (block-Lanczos deflation).
+static lrp_status block_orth(lrp_problem* P, int nx, int nb, double* Wn, const double* Q, int nprev,
+                             LanczosWS& ws, double* Cacc) {
+  cudaStream_t s = P->stream;
+  for (int pass = 0; pass < 2 && nprev > 0; ++pass) {
+    CK(gemm_tn(s, nx, nprev, nb, Q, nx, Wn, nx, ws.C1.p, nprev, 1.0, 0.0, ws.part.p, ws.part_cap));
+    CK(gemm_nn(s, nx, nprev, nb, -1.0, Q, nx, ws.C1.p, nprev, 1.0, Wn, nx));
+    if (Cacc) CK(axpby(s, (size_t)nprev * nb, 1.0, ws.C1.p, 1.0, Cacc));
+  }
+  CK(block_gs(s, 1, nx, nb, Wn, 0, nx, ws.R.p, 0, 1e-13, nullptr));
+  return LRP_OK;
+}
+
+}  // namespace lrp
+
+using namespace lrp;
+
+extern "C" {
+
+lrp_status lrp_lowrank_posterior(lrp_problem* P, int k, int block, double eig_tol, double eig_threshold,
+                                 int max_basis, const double* start, lrp_posterior** out,
+                                 lrp_lanczos_stats* stats) {
+  if (!P || !out) {
+    set_error("NULL argument");
+    return LRP_EINVAL;
+  }
+  *out = nullptr;
+  const int nx = P->nx;
+  if (block < 1 || block > 16 || k < 1 || k > nx) {
+    set_error("need 1 <= block <= 16 and 1 <= k <= nx");
+    return LRP_EINVAL;
+  }
+  cudaSetDevice(P->device);
+  auto t0 = std::chrono::steady_clock::now();
+  double ms_apply = 0.0;
+  const int nb = block;
+  if (!(eig_tol > 0)) eig_tol = 1e-6;
+  int mmax = max_basis > 0 ? max_basis : std::min(nx, 3 * k + 4 * nb);
+  mmax = std::min(mmax, nx);
+  mmax = std::min(mmax, 1024);
+  mmax = std::max(nb, mmax / nb * nb);
+  cudaStream_t s = P->stream;
+  DArr<double> Q, W, T, Tw, Z, theta, work, resid;
+  DArr<int> estat;
+  LanczosWS ws;
+  CK(Q.alloc((size_t)nx * (mmax + nb)));
+  CK(W.alloc((size_t)nx * nb));
+  CK(T.alloc((size_t)(mmax + nb) * (mmax + nb)));
+  CK(Tw.alloc((size_t)mmax * mmax));
+  CK(Z.alloc((size_t)mmax * mmax));
+  CK(theta.alloc(mmax));
+  CK(work.alloc(6 * (size_t)mmax + 8));
+  CK(resid.alloc(mmax));
+  CK(estat.alloc(1));
+  ws.part_cap = (size_t)std::max(mmax + nb, 16) * 16 * 128;
+  CK(ws.part.alloc(ws.part_cap));
+  CK(ws.G.alloc(nb * nb));
+  CK(ws.R1.alloc(nb * nb));
+  CK(ws.R2.alloc(nb * nb));
+  CK(ws.Ri1.alloc(nb * nb));
+  CK(ws.Ri2.alloc(nb * nb));
+  CK(ws.R.alloc(nb * nb));
+  CK(ws.C1.alloc((size_t)(mmax + nb) * nb));
+  CK(ws.C2.alloc((size_t)(mmax + nb) * nb));
+  CK(ws.flags.alloc(nb));
+  CK(cudaMemsetAsync(T.p, 0, T.n * sizeof(double), s));
+  // start block
+  if (start) {
+    if (is_device_ptr(start)) {
+      CK(copy_cols(s, nx, nb, start, nx, Q.p, nx));
+    } else {
+      CK(cudaMemcpyAsync(Q.p, start, (size_t)nx * nb * sizeof(double), cudaMemcpyHostToDevice, s));
+    }
+  } else {
+    CK(fill_random(s, nx, nb, Q.p, nx, nullptr, 0x5EEDull));
+  }
+  lrp_status st = block_orth(P, nx, nb, Q.p, Q.p, 0, ws, nullptr);
+  if (st != LRP_OK) return st;
+  int n_iter = 0, n_matvec = 0, cols = 0, kk = 0;
+  bool converged = false;
+  double max_res = 0.0;
+  std::vector<double> h_theta, h_res;
+  for (int j = 0;; ++j) {
+    const int c0 = j * nb;
+    cols = c0 + nb;
+    auto ta = std::chrono::steady_clock::now();
+    st = run_sweep(P, HESS_STAGES, nb, Q.p + (size_t)c0 * nx, nx, W.p, nx, nullptr, 0, nullptr, 0, nullptr,
+                   false);
+    ms_apply += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ta).count();
+    if (st != LRP_OK && st != LRP_ENOCONV) return st;
+    n_matvec += nb;
+    ++n_iter;
+    // full re-orthogonalisation (CGS2 against the whole basis), the
+    // coefficients of block j give A_j; block CGS2 of the remainder gives B_j
+    CK(cudaMemsetAsync(ws.C2.p, 0, (size_t)cols * nb * sizeof(double), s));
+    st = block_orth(P, nx, nb, W.p, Q.p, cols, ws, ws.C2.p);
+    if (st != LRP_OK) return st;
+    CK(set_block(s, T.p, mmax + nb, c0, c0, nb, ws.C2.p + c0, cols, true, false));
+    CK(set_block(s, T.p, mmax + nb, cols, c0, nb, ws.R.p, nb, false, true));
+    if (cols < mmax) CK(copy_cols(s, nx, nb, W.p, nx, Q.p + (size_t)cols * nx, nx));
+    const bool last = cols + nb > mmax;
+    if (cols >= std::min(k, mmax) || last) {
+      kk = std::min(k, cols);
+      // eigenpairs of T_j (copied: the solver destroys its input)
+      CK(cudaMemcpy2DAsync(Tw.p, (size_t)cols * sizeof(double), T.p, (size_t)(mmax + nb) * sizeof(double),
+                           (size_t)cols * sizeof(double), cols, cudaMemcpyDeviceToDevice, s));
+      CK(eig_sym(s, cols, Tw.p, cols, Z.p, cols, theta.p, work.p, estat.p));
+      CK(ritz_resid(s, kk, nb, ws.R.p, Z.p, cols, c0, resid.p));
+      h_theta.resize(kk);
+      h_res.resize(kk);
+      CK(cudaMemcpyAsync(h_theta.data(), theta.p, kk * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(h_res.data(), resid.p, kk * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      const double th0 = std::max(h_theta[0], 1e-300);
+      bool ok = kk == k || cols >= nx;
+      max_res = 0.0;
+      for (int i = 0; i < kk; ++i) {
+        if (eig_threshold > 0 && h_theta[i] < eig_threshold) continue;
+        max_res = std::max(max_res, h_res[i] / th0);
+        if (h_res[i] > eig_tol * th0) ok = false;
+      }
+      if (ok) {
+        converged = true;
+        break;
+      }
+      if (last) break;
+    }
+  }
+  // Ritz vectors V_k = Q_m S_k, eigenvalues theta_k
+  int kout = kk;
+  if (eig_threshold > 0) {
+    kout = 0;
+    for (int i = 0; i < kk; ++i)
+      if (h_theta[i] >= eig_threshold) ++kout;
+  }
+  lrp_posterior* post = new lrp_posterior();
+  post->prob = P;
+  post->k = kout;
+  post->nx = nx;
+  post->sigma0 = P->desc.sigma;
+  post->diag = nullptr;
+  post->diag_cap = 0;
+  post->lambda_host.assign(h_theta.begin(), h_theta.begin() + kout);
+  DArr<double> V, G, lam;
+  CK(V.alloc((size_t)nx * std::max(kout, 1)));
+  CK(G.alloc((size_t)nx * std::max(kout, 1)));
+  CK(lam.alloc(std::max(kout, 1)));
+  if (kout > 0) {
+    CK(gemm_nn(s, nx, cols, kout, 1.0, Q.p, nx, Z.p, cols, 0.0, V.p, nx));
+    CK(cudaMemcpyAsync(lam.p, theta.p, kout * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    lrp_apply_stats ast;
+    st = run_sweep(P, ST_LOAD_X | ST_PRIOR_IN | ST_STORE_Y, kout, V.p, nx, G.p, nx, nullptr, 0, nullptr, 0,
+                   &ast, false);
+    if (st != LRP_OK && st != LRP_ENOCONV) {
+      delete post;
+      return st;
+    }
+  }
+  CK(cudaStreamSynchronize(s));
+  post->V = V.release();
+  post->G = G.release();
+  post->lambda = lam.release();
+  *out = post;
+  if (stats) {
+    stats->n_iter = n_iter;
+    stats->n_matvec = n_matvec;
+    stats->k_converged = converged ? kout : 0;
+    stats->max_ritz_resid = max_res;
+    stats->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    stats->ms_apply = ms_apply;
+  }
+  if (!converged) {
+    set_error("Lanczos reached its basis cap before all Ritz pairs converged");
+    return LRP_ENOCONV;
+  }
+  return LRP_OK;
+}
+
+void lrp_posterior_destroy(lrp_posterior* post) {
+  if (!post) return;
+  if (post->V) cudaFree(post->V);
+  if (post->G) cudaFree(post->G);
+  if (post->lambda) cudaFree(post->lambda);
+  if (post->diag) cudaFree(post->diag);
+  delete post;
+}
+
+lrp_status lrp_posterior_eigs(const lrp_posterior* post, int* r, double* lambda, double* V, int ldv) {
+  if (!post || !r) {
+    set_error("NULL argument");
+    return LRP_EINVAL;
+  }
+  *r = post->k;
+  if (lambda) std::memcpy(lambda, post->lambda_host.data(), post->k * sizeof(double));
+  if (V && post->k > 0) {
+    if (ldv < post->nx) {
+      set_error("ldv < nx");
+      return LRP_EINVAL;
+    }
+    const cudaMemcpyKind kind = is_device_ptr(V) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    cudaError_t e = cudaMemcpy2D(V, (size_t)ldv * sizeof(double), post->V, (size_t)post->nx * sizeof(double),
+                                 (size_t)post->nx * sizeof(double), post->k, kind);
+    if (e != cudaSuccess) return cuda_status(e, "posterior_eigs copy");
+  }
+  return LRP_OK;
+}
+
+lrp_status lrp_posterior_query(lrp_posterior* post, const lrp_query* q, lrp_query_result* r) {
+  if (!post || !q || !r) {
+    set_error("NULL argument");
+    return LRP_EINVAL;
+  }
+  lrp_problem* P = post->prob;
+  cudaSetDevice(P->device);
+  cudaStream_t s = P->stream;
+  auto t0 = std::chrono::steady_clock::now();
+  const int nx = P->nx, k = post->k;
+  const double sigma = q->sigma > 0 ? q->sigma : P->desc.sigma;
+  const double lam_scale = (post->sigma0 * post->sigma0) / (sigma * sigma);
+  const bool want_mean = (q->kind & (LRP_Q_MEAN | LRP_Q_SAMPLES)) != 0;
+  lrp_status st;
+  DArr<double> mean, tmp, coef;
+  if (want_mean) {
+    if (!q->y_obs) {
+      set_error("query: y_obs required for MEAN/SAMPLES");
+      return LRP_EINVAL;
+    }
+    // g = F^T y / sigma^2 ; z = R^{-1} g (one adjoint sweep + prior solve)
+    DArr<double> y;
+    CK(y.alloc(P->n_data));
+    const cudaMemcpyKind kind = is_device_ptr(q->y_obs) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(y.p, q->y_obs, P->n_data * sizeof(double), kind, s));
+    CK(axpby(s, P->n_data, 1.0 / (sigma * sigma), y.p, 0.0, y.p));
+    CK(mean.alloc(nx));
+    CK(tmp.alloc(nx));
+    st = run_sweep(P, ST_LOAD_D | ST_ADJOINT | ST_PRIOR_OUT | ST_STORE_Y, 1, nullptr, 0, tmp.p, nx, y.p,
+                   P->n_data, nullptr, 0, nullptr, false);
+    if (st != LRP_OK && st != LRP_ENOCONV) return st;
+    // z <- z - V (d .* V^T z)
+    if (k > 0) {
+      CK(coef.alloc(k));
+      DArr<double> part;
+      CK(part.alloc((size_t)k * 16 * 128));
+      CK(gemm_tn(s, nx, k, 1, post->V, nx, tmp.p, nx, coef.p, k, 1.0, 0.0, part.p, part.n));
+      CK(diag_scale(s, k, 1, post->lambda, lam_scale, 0, coef.p, k));
+      CK(gemm_nn(s, nx, k, 1, -1.0, post->V, nx, coef.p, k, 1.0, tmp.p, nx));
+    }
+    st = run_sweep(P, ST_LOAD_X | ST_PRIOR_IN | ST_STORE_Y, 1, tmp.p, nx, mean.p, nx, nullptr, 0, nullptr, 0,
+                   nullptr, false);
+    if (st != LRP_OK && st != LRP_ENOCONV) return st;
+    if (r->mean) {
+      const cudaMemcpyKind k2 = is_device_ptr(r->mean) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+      CK(cudaMemcpyAsync(r->mean, mean.p, nx * sizeof(double), k2, s));
+    }
+  }
+  if (q->kind & LRP_Q_VARIANCE) {
+    const int np = q->n_points;
+    if (np < 1 || !q->points || !r->variance) {
+      set_error("query: VARIANCE needs points and a variance buffer");
+      return LRP_EINVAL;
+    }
+    std::vector<int> nodes(np);
+    if (is_device_ptr(q->points)) {
+      CK(cudaMemcpy(nodes.data(), q->points, np * sizeof(int), cudaMemcpyDeviceToHost));
+    } else {
+      std::memcpy(nodes.data(), q->points, np * sizeof(int));
+    }
+    for (int v : nodes)
+      if (v < 0 || v >= nx) {
+        set_error("query: node index out of range");
+        return LRP_EINVAL;
+      }
+    DArr<int> dnodes;
+    CK(dnodes.alloc(np));
+    CK(cudaMemcpyAsync(dnodes.p, nodes.data(), np * sizeof(int), cudaMemcpyHostToDevice, s));
+    if (post->diag_nodes != nodes) {
+      // prior diagonal ||R^{-1} e_i||^2 at the nodes by batched prior solves
+      if (post->diag) cudaFree(post->diag);
+      post->diag = nullptr;
+      CK(cudaMalloc(&post->diag, np * sizeof(double)));
+      const int chunk = 256;
+      DArr<double> E, X;
+      CK(E.alloc((size_t)nx * chunk));
+      CK(X.alloc((size_t)nx * chunk));
+      for (int i0 = 0; i0 < np; i0 += chunk) {
+        const int nc = std::min(chunk, np - i0);
+        CK(unit_cols(s, nx, nc, dnodes.p, i0, E.p, nx));
+        st = run_sweep(P, ST_LOAD_X | ST_PRIOR_IN | ST_STORE_Y, nc, E.p, nx, X.p, nx, nullptr, 0, nullptr, 0,
+                       nullptr, false);
+        if (st != LRP_OK && st != LRP_ENOCONV) return st;
+        CK(col_norm2(s, nx, nc, X.p, nx, post->diag + i0));
+      }
+      post->diag_nodes = nodes;
+    }
+    DArr<double> var;
+    CK(var.alloc(np));
+    CK(variance(s, np, dnodes.p, post->diag, k, post->lambda, lam_scale, post->G, nx, var.p));
+    const cudaMemcpyKind k2 = is_device_ptr(r->variance) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CK(cudaMemcpyAsync(r->variance, var.p, np * sizeof(double), k2, s));
+  }
+  if (q->kind & LRP_Q_SAMPLES) {
+    const int ns = q->n_samples;
+    if (ns < 1 || !q->xi || !r->samples) {
+      set_error("query: SAMPLES needs xi and a samples buffer");
+      return LRP_EINVAL;
+    }
+    DArr<double> Xi, Sm;
+    CK(Xi.alloc((size_t)nx * ns));
+    CK(Sm.alloc((size_t)nx * ns));
+    const cudaMemcpyKind kind = is_device_ptr(q->xi) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(Xi.p, q->xi, (size_t)nx * ns * sizeof(double), kind, s));
+    if (k > 0) {
+      DArr<double> Cc, part;
+      CK(Cc.alloc((size_t)k * ns));
+      CK(part.alloc((size_t)k * 16 * 128));
+      CK(gemm_tn(s, nx, k, ns, post->V, nx, Xi.p, nx, Cc.p, k, 1.0, 0.0, part.p, part.n));
+      CK(diag_scale(s, k, ns, post->lambda, lam_scale, 1, Cc.p, k));
+      CK(gemm_nn(s, nx, k, ns, 1.0, post->V, nx, Cc.p, k, 1.0, Xi.p, nx));
+    }
+    st = run_sweep(P, ST_LOAD_X | ST_PRIOR_IN | ST_STORE_Y, ns, Xi.p, nx, Sm.p, nx, nullptr, 0, nullptr, 0,
+                   nullptr, false);
+    if (st != LRP_OK && st != LRP_ENOCONV) return st;
+    CK(add_vec_cols(s, nx, ns, mean.p, Sm.p, nx));
+    const cudaMemcpyKind k2 = is_device_ptr(r->samples) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CK(cudaMemcpyAsync(r->samples, Sm.p, (size_t)nx * ns * sizeof(double), k2, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  r->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return LRP_OK;
+}
+
+lrp_status lrp_posterior_save(const lrp_posterior* post, const char* path) {
+  if (!post || !path) {
+    set_error("NULL argument");
+    return LRP_EINVAL;
+  }
+  FILE* f = std::fopen(path, "wb");
+  if (!f) {
+    set_error(std::string("cannot open ") + path);
+    return LRP_EINVAL;
+  }
+  const size_t nx = post->nx, k = post->k;
+  std::vector<double> V(nx * k), G(nx * k);
+  if (k) {
+    cudaMemcpy(V.data(), post->V, V.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaMemcpy(G.data(), post->G, G.size() * sizeof(double), cudaMemcpyDeviceToHost);
+  }
+  const char magic[8] = {'L', 'R', 'P', 'O', 'S', 'T', '0', '1'};
+  const uint64_t hdr[3] = {post->prob->hash, (uint64_t)nx, (uint64_t)k};
+  bool ok = std::fwrite(magic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof(uint64_t), 3, f) == 3 &&
+            std::fwrite(&post->sigma0, sizeof(double), 1, f) == 1 &&
+            std::fwrite(post->lambda_host.data(), sizeof(double), k, f) == k &&
+            std::fwrite(V.data(), sizeof(double), V.size(), f) == V.size() &&
+            std::fwrite(G.data(), sizeof(double), G.size(), f) == G.size();
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) {
+    set_error("write failed");
+    return LRP_EINVAL;
+  }
+  return LRP_OK;
+}
+
+lrp_status lrp_posterior_load(lrp_problem* P, const char* path, lrp_posterior** out) {
+  if (!P || !path || !out) {
+    set_error("NULL argument");
+    return LRP_EINVAL;
+  }
+  *out = nullptr;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) {
+    set_error(std::string("cannot open ") + path);
+    return LRP_EINVAL;
+  }
+  char magic[8];
+  uint64_t hdr[3];
+  double sigma0;
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "LRPOST01", 8) == 0 &&
+            std::fread(hdr, sizeof(uint64_t), 3, f) == 3 && std::fread(&sigma0, sizeof(double), 1, f) == 1;
+  if (!ok || hdr[0] != P->hash || hdr[1] != (uint64_t)P->nx) {
+    std::fclose(f);
+    set_error("checkpoint does not match this problem");
+    return LRP_EINVAL;
+  }
+  const size_t nx = hdr[1], k = hdr[2];
+  std::vector<double> lam(k), V(nx * k), G(nx * k);
+  ok = std::fread(lam.data(), sizeof(double), k, f) == k && std::fread(V.data(), sizeof(double), V.size(), f) == V.size() &&
+       std::fread(G.data(), sizeof(double), G.size(), f) == G.size();
+  std::fclose(f);
+  if (!ok) {
+    set_error("truncated checkpoint");
+    return LRP_EINVAL;
+  }
+  cudaSetDevice(P->device);
+  lrp_posterior* post = new lrp_posterior();
+  post->prob = P;
+  post->k = (int)k;
+  post->nx = (int)nx;
+  post->sigma0 = sigma0;
+  post->lambda_host = lam;
+  post->diag = nullptr;
+  post->diag_cap = 0;
+  post->V = post->G = post->lambda = nullptr;
+  cudaError_t e = cudaMalloc(&post->V, std::max<size_t>(1, V.size()) * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&post->G, std::max<size_t>(1, G.size()) * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&post->lambda, std::max<size_t>(1, k) * sizeof(double));
+  if (e == cudaSuccess && k) {
+    cudaMemcpy(post->V, V.data(), V.size() * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(post->G, G.data(), G.size() * sizeof(double), cudaMemcpyHostToDevice);
+    e = cudaMemcpy(post->lambda, lam.data(), k * sizeof(double), cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) {
+    lrp_posterior_destroy(post);
+    return cuda_status(e, "posterior_load");
+  }
+  *out = post;
+  return LRP_OK;
+}
+
+}  // extern "C"

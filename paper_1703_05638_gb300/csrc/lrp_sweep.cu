@@ -1,0 +1,193 @@
+// Host launcher of the persistent sweep kernel (lrp_sweep_kernel.cuh): team
+// workspace layout, levels worked by the whole team, cluster launch, stats.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+
+#include "lrp_internal.h"
+
+namespace lrp {
+
+template <typename T, int DIM, bool MIXED>
+cudaError_t launch_sweep(const SweepParams& prm, cudaStream_t stream);
+extern template cudaError_t launch_sweep<double, 2, false>(const SweepParams&, cudaStream_t);
+extern template cudaError_t launch_sweep<double, 3, false>(const SweepParams&, cudaStream_t);
+extern template cudaError_t launch_sweep<float, 2, true>(const SweepParams&, cudaStream_t);
+extern template cudaError_t launch_sweep<float, 3, true>(const SweepParams&, cudaStream_t);
+
+
+static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Algorithmic bytes of one sweep launch from the solver's own counts: the
+// passes over fine-level vectors each phase makes (coarse levels add 1/3 in
+// 2D, 1/7 in 3D), per point and column:
+//   PCG iteration: phase A 5, phase B 7, V-cycle 3(nu-1) pre-sweeps +
+//     2.5 restriction + 2.25 prolongation + 3 nu post-sweeps + 1 (r.z),
+//     in words of the inner type;
+//   solve set-up: 3 FP64 + 2 inner words; FP64 refinement: 3 FP64 + 3 inner.
+double algorithmic_bytes(const lrp_problem* Pr, const Stats& hs, int BV, bool mixed) {
+  const double T = mixed ? 4.0 : 8.0, D = 8.0;
+  const double nu = Pr->cfg.nu;
+  const double g = Pr->dim == 2 ? 4.0 / 3.0 : 8.0 / 7.0;
+  const double c_it = 12.0 + (3.0 * (nu - 1.0) + 2.5 + 2.25 + 3.0 * nu + 1.0) * g;
+  const double per_point = (double)hs.iters * c_it * T + (double)hs.refines * (3.0 * D + 3.0 * T) +
+                           (double)hs.solves * (3.0 * D + 2.0 * T);
+  return per_point * (double)Pr->nx * BV;
+}
+
+lrp_status run_sweep(lrp_problem* Pr, unsigned stages, int nvec, const double* X, int ldx,
+                     double* Y, int ldy, const double* Din, int lddin, double* Dout, int lddout,
+                     lrp_apply_stats* st, bool misfit_only) {
+  (void)misfit_only;
+  return run_sweep_ex(Pr, stages, nvec, X, ldx, Y, ldy, Din, lddin, Dout, lddout, st, 0, -1, nullptr, 0);
+}
+
+// t_end < 0: the forward sweep runs to the last observed step.
+lrp_status run_sweep_ex(lrp_problem* Pr, unsigned stages, int nvec, const double* X, int ldx,
+                        double* Y, int ldy, const double* Din, int lddin, double* Dout, int lddout,
+                        lrp_apply_stats* st, int t_begin, int t_end, double* traj, int traj_cols) {
+  auto t0 = std::chrono::steady_clock::now();
+  const bool mixed = Pr->desc.precision == LRP_MIXED;
+  const int BV = Pr->team_cols;
+  int bvs = 0;
+  while ((1 << bvs) < BV) ++bvs;
+  const int n_teams = (nvec + BV - 1) / BV;
+  const size_t tsz = mixed ? sizeof(float) : sizeof(double);
+  const size_t N0 = (size_t)Pr->nx;
+  SweepParams prm;
+  std::memset(&prm, 0, sizeof(prm));
+  size_t off = 0;
+  for (int k = 0; k < 3; ++k) {
+    prm.off_dbuf[k] = off;
+    off = align_up(off + N0 * BV * sizeof(double));
+  }
+  prm.off_bd = off;
+  off = align_up(off + (mixed ? N0 * BV * sizeof(double) : 0));
+  prm.off_obs = off;
+  off = align_up(off + (size_t)Pr->n_obs * Pr->n_steps * BV * sizeof(double));
+  prm.off_r = off;
+  off = align_up(off + N0 * BV * tsz);
+  prm.off_p = off;
+  off = align_up(off + N0 * BV * tsz);
+  prm.off_q = off;
+  off = align_up(off + N0 * BV * tsz);
+  prm.off_c = off;
+  off = align_up(off + (mixed ? N0 * BV * tsz : 0));
+  prm.off_e0[0] = off;
+  off = align_up(off + N0 * BV * tsz);
+  prm.off_e0[1] = off;
+  off = align_up(off + N0 * BV * tsz);
+  for (int l = 1; l < Pr->L; ++l) {
+    const size_t Nl = (size_t)Pr->step.lv[l].N;
+    prm.off_e[l][0] = off;
+    off = align_up(off + Nl * BV * tsz);
+    prm.off_e[l][1] = off;
+    off = align_up(off + Nl * BV * tsz);
+    prm.off_f[l] = off;
+    off = align_up(off + Nl * BV * tsz);
+  }
+  prm.team_bytes = off;
+  lrp_status s = ensure_workspace(Pr, off * n_teams);
+  if (s != LRP_OK) return s;
+  prm.ws = Pr->ws;
+  prm.step = Pr->step;
+  prm.prior = Pr->prior;
+  // levels worked by the whole team: those with at least coarse_items items
+  auto team_levels = [&](Op& op) {
+    int Lt = 0;
+    if (Pr->team_ctas > 1) {
+      for (int l = 0; l < op.L; ++l)
+        if ((long long)op.lv[l].N * BV >= Pr->coarse_items) Lt = l + 1;
+      if (Lt < 1) Lt = 1;
+    }
+    op.Lt = Lt;
+  };
+  team_levels(prm.step);
+  team_levels(prm.prior);
+  prm.dim = Pr->dim;
+  prm.nt = Pr->nt;
+  prm.t_begin = t_begin;
+  prm.t_end = t_end >= 0 ? t_end : Pr->last_obs;
+  prm.traj = traj;
+  prm.traj_ld = Pr->nx;
+  prm.traj_cols = traj_cols;
+  prm.adj_begin = Pr->last_obs;
+  prm.obs_every = Pr->desc.obs_every;
+  prm.n_obs = Pr->n_obs;
+  prm.n_steps = Pr->n_steps;
+  prm.inv_sigma2 = 1.0 / (Pr->desc.sigma * Pr->desc.sigma);
+  prm.obs_node = Pr->obs_node;
+  prm.obs_w = Pr->obs_w;
+  prm.bt_ptr = Pr->bt_ptr;
+  prm.bt_idx = Pr->bt_idx;
+  prm.bt_w = Pr->bt_w;
+  prm.C = Pr->team_ctas;
+  prm.NT = Pr->nthreads;
+  prm.BV = BV;
+  prm.bv_shift = bvs;
+  prm.nvec = nvec;
+  prm.n_teams = n_teams;
+  prm.stages = stages;
+  prm.X = X;
+  prm.ldx = ldx;
+  prm.Y = Y;
+  prm.ldy = ldy;
+  prm.Din = Din;
+  prm.lddin = lddin;
+  prm.Dout = Dout;
+  prm.lddout = lddout;
+  prm.end_buf = Pr->end_buf;
+  prm.cfg = Pr->cfg;
+  prm.stats = Pr->stats;
+  cudaError_t e = cudaMemsetAsync(Pr->stats, 0, sizeof(Stats), Pr->stream);
+  if (e != cudaSuccess) return cuda_status(e, "stats reset");
+  if (Pr->prof_on) cudaEventRecord(Pr->prof_ev[0], Pr->stream);
+  if (Pr->dim == 2) {
+    e = mixed ? launch_sweep<float, 2, true>(prm, Pr->stream)
+              : launch_sweep<double, 2, false>(prm, Pr->stream);
+  } else {
+    e = mixed ? launch_sweep<float, 3, true>(prm, Pr->stream)
+              : launch_sweep<double, 3, false>(prm, Pr->stream);
+  }
+  if (e != cudaSuccess) return cuda_status(e, "sweep launch");
+  note_launch();
+  if (Pr->prof_on) cudaEventRecord(Pr->prof_ev[1], Pr->stream);
+  Stats hs;
+  e = cudaMemcpyAsync(&hs, Pr->stats, sizeof(Stats), cudaMemcpyDeviceToHost, Pr->stream);
+  if (e != cudaSuccess) return cuda_status(e, "stats copy");
+  e = cudaStreamSynchronize(Pr->stream);
+  if (e != cudaSuccess) return cuda_status(e, "sweep");
+  if (Pr->prof_on) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, Pr->prof_ev[0], Pr->prof_ev[1]);
+    Pr->prof_ms += ms;
+    Pr->prof_launches += 1;
+    Pr->prof_bytes += algorithmic_bytes(Pr, hs, BV, mixed);
+  }
+  if (st) {
+    std::memset(st, 0, sizeof(*st));
+    const double nteams_cols = (double)n_teams;
+    st->n_solves = (int)(hs.solves / (unsigned long long)std::max(1, n_teams));
+    st->pcg_iters_max = hs.iters_max;
+    st->pcg_iters_mean = hs.solves ? (double)hs.iters / (double)hs.solves : 0.0;
+    (void)nteams_cols;
+    st->refine_max = hs.refine_max;
+    double mr;
+    std::memcpy(&mr, &hs.max_rel_res_bits, sizeof(double));
+    st->max_rel_residual = mr;
+    st->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (hs.status & STAT_NONFINITE) {
+    set_error("non-finite value in a spatial solve");
+    return LRP_ENONFINITE;
+  }
+  if (hs.status & STAT_NOCONV) {
+    set_error("a spatial solve missed its tolerance within the iteration cap");
+    return LRP_ENOCONV;
+  }
+  return LRP_OK;
+}
+
+}  // namespace lrp

@@ -1,0 +1,545 @@
+#pragma once
+// Persistent sweep kernel: one launch runs, for every group of BV columns,
+// the prior half-apply, the forward implicit-Euler sweep with the fused
+// observation, the adjoint sweep with the fused B^T source and the second
+// prior half-apply (the Hessian apply of Sec. 2 Eq. (prior_pre) /
+// Sec. 6.1 Eq. (misfit)), or any subset of these stages.
+//
+// Work decomposition: a "team" is one thread-block cluster of C CTAs that owns
+// BV columns; it steps through all 2*nt spatial solves on its own, separated
+// from its phases by hardware cluster barriers, and never waits on another
+// team. Each spatial solve is preconditioned CG on I + c L with one V-cycle
+// per iteration; LRP_MIXED runs the PCG in FP32 inside FP64 iterative
+// refinement (residual and solution in FP64).
+#include <cuda_runtime.h>
+
+#include "lrp_team.cuh"
+
+namespace lrp {
+
+template <typename T>
+struct WSV {
+  double* dbuf[3];
+  double* bd;
+  double* obs;
+  T* r;
+  T* p;
+  T* q;
+  T* c;
+  T* e[LRP_MAXLEV][2];  // level 0: the two finest smoother buffers
+  T* f[LRP_MAXLEV];     // level 0: r
+};
+
+struct Ctr {
+  long long iters = 0, refines = 0, solves = 0;
+  int iters_max = 0, refine_max = 0;
+  double max_res = 0.0;
+  int status = 0;
+};
+
+// V-cycle: z = M r. On entry f[0] = r is complete and e[0][0] holds the first
+// (pointwise) smoother sweep of level 0. On exit z = e[0][ecur0] and the
+// team total r.z is in slot SL_RZ.
+template <typename T, int DIM, bool KAPPA>
+__device__ int vcycle(const Team& t, const Op& op, const WSV<T>& w, T omega, int nu) {
+  int ecur[LRP_MAXLEV];
+  for (int l = 0; l < LRP_MAXLEV; ++l) ecur[l] = 0;
+  const int L = op.L;
+  const int Lt = min(op.Lt, L - 1);
+  double rz = 0.0;
+  if (L == 1) return 0;  // z = r/d was formed exactly in the fused phase (rz too)
+  // down, team levels
+  for (int l = 0; l < Lt; ++l) {
+    for (int s = 1; s < nu; ++s) {
+      mg_sweep<T, DIM, KAPPA>(op.lv[l], w.e[l][ecur[l] ^ 1], w.e[l][ecur[l]], w.f[l], t.g, t.S,
+                              t.bvs, t.col, omega, (const T*)nullptr, rz);
+      ecur[l] ^= 1;
+      team_sync(t);
+    }
+    const T sc = (l + 1 == L - 1) ? T(1) : omega;
+    mg_restrict<T, DIM, KAPPA>(op.lv[l], op.lv[l + 1], w.e[l][ecur[l]], w.f[l], w.f[l + 1],
+                               w.e[l + 1][0], t.g, t.S, t.bvs, t.col, sc);
+    ecur[l + 1] = 0;
+    team_sync(t);
+  }
+  // levels below the team levels: CTA rank 0 alone, __syncthreads between phases
+  if (Lt < L - 1) {
+    const bool me = (t.rank == 0);
+    for (int l = Lt; l < L - 1; ++l) {
+      for (int s = 1; s < nu; ++s) {
+        if (me) {
+          mg_sweep<T, DIM, KAPPA>(op.lv[l], w.e[l][ecur[l] ^ 1], w.e[l][ecur[l]], w.f[l], t.tid,
+                                  t.NT, t.bvs, t.col, omega, (const T*)nullptr, rz);
+          __syncthreads();
+        }
+        ecur[l] ^= 1;
+      }
+      const T sc = (l + 1 == L - 1) ? T(1) : omega;
+      if (me) {
+        mg_restrict<T, DIM, KAPPA>(op.lv[l], op.lv[l + 1], w.e[l][ecur[l]], w.f[l], w.f[l + 1],
+                                   w.e[l + 1][0], t.tid, t.NT, t.bvs, t.col, sc);
+        __syncthreads();
+      }
+      ecur[l + 1] = 0;
+    }
+    for (int l = L - 2; l >= Lt; --l) {
+      if (me) {
+        mg_prolong<T, DIM>(op.lv[l], op.lv[l + 1], w.e[l][ecur[l]], w.e[l + 1][ecur[l + 1]], t.tid,
+                           t.NT, t.bvs, t.col);
+        __syncthreads();
+      }
+      for (int s = 0; s < nu; ++s) {
+        if (me) {
+          mg_sweep<T, DIM, KAPPA>(op.lv[l], w.e[l][ecur[l] ^ 1], w.e[l][ecur[l]], w.f[l], t.tid,
+                                  t.NT, t.bvs, t.col, omega, (const T*)nullptr, rz);
+          __syncthreads();
+        }
+        ecur[l] ^= 1;
+      }
+    }
+    team_sync(t);
+  }
+  // up, team levels
+  for (int l = Lt - 1; l >= 0; --l) {
+    mg_prolong<T, DIM>(op.lv[l], op.lv[l + 1], w.e[l][ecur[l]], w.e[l + 1][ecur[l + 1]], t.g, t.S,
+                       t.bvs, t.col);
+    team_sync(t);
+    for (int s = 0; s < nu; ++s) {
+      const bool last = (l == 0 && s == nu - 1);
+      mg_sweep<T, DIM, KAPPA>(op.lv[l], w.e[l][ecur[l] ^ 1], w.e[l][ecur[l]], w.f[l], t.g, t.S,
+                              t.bvs, t.col, omega, last ? (const T*)w.f[0] : (const T*)nullptr, rz);
+      ecur[l] ^= 1;
+      if (last) contribute(t, SL_RZ, rz);
+      team_sync(t);
+    }
+  }
+  if (Lt == 0) {
+    // every level was worked by rank 0 (C == 1 teams): r.z from level 0 sweeps
+    // is accumulated here over the whole CTA
+    double acc = 0.0;
+    const int items = op.lv[0].N << t.bvs;
+    const T* z = w.e[0][ecur[0]];
+    for (int it = t.g; it < items; it += t.S) acc += (double)(w.f[0][it] * z[it]);
+    contribute(t, SL_RZ, acc);
+    team_sync(t);
+  }
+  return ecur[0];
+}
+
+// PCG iterations on (I + c L) x = b from a prepared state: f[0] = r holds the
+// initial residual, e[0][0] its first smoother sweep, `done` whether this
+// thread's column is already converged. Updates xt (+= alpha p; = alpha p on
+// the first iteration if zero_init).
+template <typename T, typename TX, int DIM, bool KAPPA>
+__device__ void pcg_iterate(const Team& t, const Op& op, const WSV<T>& w, TX* xt, bool zero_init,
+                            double tol2bb, bool& done, const SolveCfg& cfg, T omega, T scale0,
+                            Ctr& ctr, double& rr_last) {
+  const OpLevel& l0 = op.lv[0];
+  const int items = l0.N << t.bvs;
+  int it_count = 0;
+  double rz_old = 0.0;
+  bool all = __syncthreads_and(done);
+  while (!all) {
+    const int zc = vcycle<T, DIM, KAPPA>(t, op, w, omega, cfg.nu);
+    const T* z = w.e[0][zc];
+    const double rz = total(t, SL_RZ);
+    const T beta = (T)((it_count == 0 || done || !(rz_old > 0.0)) ? 0.0 : rz / rz_old);
+    // phase A: p = z + beta p, q = A z + beta q, accumulate p.q
+    double pq = 0.0;
+    {
+      Ld<T> ld{z, t.bvs, t.col};
+      for (int it = t.g; it < items; it += t.S) {
+        const int p = it >> t.bvs;
+        int i0, i1, i2;
+        decomp<DIM>(l0, p, i0, i1, i2);
+        T d;
+        const T az = op_at<T, DIM, KAPPA>(l0, ld, p, i0, i1, i2, d);
+        T pv, qv;
+        if (it_count == 0) {
+          pv = z[it];
+          qv = az;
+        } else {
+          pv = z[it] + beta * w.p[it];
+          qv = az + beta * w.q[it];
+        }
+        w.p[it] = pv;
+        w.q[it] = qv;
+        pq += (double)(pv * qv);
+      }
+    }
+    contribute(t, SL_PQ, pq);
+    team_sync(t);
+    const double pqt = total(t, SL_PQ);
+    const T alpha = (T)((done || !(pqt > 0.0)) ? 0.0 : rz / pqt);
+    // phase B: x += alpha p, r -= alpha q, first smoother sweep of the next V-cycle
+    double rr = 0.0, rz1 = 0.0;
+    for (int it = t.g; it < items; it += t.S) {
+      const int p = it >> t.bvs;
+      if (zero_init && it_count == 0)
+        xt[it] = (TX)(alpha * w.p[it]);
+      else
+        xt[it] += (TX)(alpha * w.p[it]);
+      const T rv = w.f[0][it] - alpha * w.q[it];
+      w.f[0][it] = rv;
+      rr += (double)(rv * rv);
+      int i0, i1, i2;
+      decomp<DIM>(l0, p, i0, i1, i2);
+      const T e = scale0 * rv / diag_at<T, DIM, KAPPA>(l0, p, i0, i1, i2);
+      w.e[0][0][it] = e;
+      if (op.L == 1) rz1 += (double)(rv * e);
+    }
+    contribute(t, SL_RR, rr);
+    if (op.L == 1) contribute(t, SL_RZ, rz1);
+    team_sync(t);
+    const double rrt = total(t, SL_RR);
+    if (!isfinite(rrt)) {
+      ctr.status |= STAT_NONFINITE;
+      done = true;
+    }
+    if (!done) rr_last = rrt;
+    done = done || (rrt <= tol2bb);
+    ++it_count;
+    rz_old = rz;
+    const bool capped = it_count >= cfg.maxit;
+    all = __syncthreads_and(done) || capped;
+    if (capped && !__syncthreads_and(done)) ctr.status |= STAT_NOCONV;
+  }
+  ctr.iters += it_count;
+  ctr.iters_max = max(ctr.iters_max, it_count);
+}
+
+// Right-hand side at node p: bsrc (or 0) plus the adjoint source B^T d.
+__device__ __forceinline__ double rhs_at(const SweepParams& P, const Team& t, const double* bsrc,
+                                         const double* dsrc, int p, int it) {
+  double b = bsrc ? bsrc[it] : 0.0;
+  if (dsrc) {
+    const int e0 = P.bt_ptr[p], e1 = P.bt_ptr[p + 1];
+    for (int e = e0; e < e1; ++e) b += P.bt_w[e] * dsrc[(P.bt_idx[e] << t.bvs) + t.col];
+  }
+  return b;
+}
+
+// Solve (I + c L) x = b in FP64 (x0 = warm start or NULL = 0). Returns the
+// index (in w.dbuf) of the solution buffer X1.
+template <int DIM, bool KAPPA>
+__device__ double* solve_fp64(const Team& t, const SweepParams& P, const Op& op,
+                              const WSV<double>& w, const double* bsrc, const double* dsrc,
+                              const double* x0, double* X1, Ctr& ctr) {
+  const OpLevel& l0 = op.lv[0];
+  const int items = l0.N << t.bvs;
+  const double omega = P.cfg.omega;
+  const double scale0 = (op.L == 1) ? 1.0 : omega;
+  double rr = 0.0, bb = 0.0, rz1 = 0.0;
+  Ld<double> ld{x0, t.bvs, t.col};
+  for (int it = t.g; it < items; it += t.S) {
+    const int p = it >> t.bvs;
+    int i0, i1, i2;
+    decomp<DIM>(l0, p, i0, i1, i2);
+    const double bp = rhs_at(P, t, bsrc, dsrc, p, it);
+    double d, ax = 0.0;
+    if (x0)
+      ax = op_at<double, DIM, KAPPA>(l0, ld, p, i0, i1, i2, d);
+    else
+      d = diag_at<double, DIM, KAPPA>(l0, p, i0, i1, i2);
+    const double rv = bp - ax;
+    w.f[0][it] = rv;
+    X1[it] = x0 ? x0[it] : 0.0;
+    const double e = scale0 * rv / d;
+    w.e[0][0][it] = e;
+    rr += rv * rv;
+    bb += bp * bp;
+    if (op.L == 1) rz1 += rv * e;
+  }
+  contribute(t, SL_RR, rr);
+  contribute(t, SL_BB, bb);
+  if (op.L == 1) contribute(t, SL_RZ, rz1);
+  team_sync(t);
+  const double rrt = total(t, SL_RR), bbt = total(t, SL_BB);
+  const double tol2bb = P.cfg.rtol * P.cfg.rtol * bbt;
+  bool done = rrt <= tol2bb;
+  if (!(bbt > 0.0)) {
+    for (int it = t.g; it < items; it += t.S) X1[it] = 0.0;
+    done = true;
+  }
+  if (!isfinite(rrt) || !isfinite(bbt)) {
+    ctr.status |= STAT_NONFINITE;
+    done = true;
+  }
+  double rr_last = rrt;
+  pcg_iterate<double, double, DIM, KAPPA>(t, op, w, X1, false, tol2bb, done, P.cfg, omega,
+                                          scale0, ctr, rr_last);
+  ctr.max_res = fmax(ctr.max_res, bbt > 0.0 ? sqrt(rr_last / bbt) : 0.0);
+  ctr.solves += 1;
+  return X1;
+}
+
+// Solve (I + c L) x = b by FP64 iterative refinement around FP32 MG-PCG.
+template <int DIM, bool KAPPA>
+__device__ double* solve_mixed(const Team& t, const SweepParams& P, const Op& op,
+                               const WSV<float>& w, const double* bsrc, const double* dsrc,
+                               const double* x0, double* X1, double* X2, Ctr& ctr) {
+  const OpLevel& l0 = op.lv[0];
+  const int items = l0.N << t.bvs;
+  const float omega = (float)P.cfg.omega;
+  const float scale0 = (op.L == 1) ? 1.f : omega;
+  const double* xa = x0;
+  double* tgt = X1;
+  double* oth = X2;
+  bool done = false;
+  double bbt = 0.0;
+  int ref = 0;
+  for (;; ++ref) {
+    const bool first = (ref == 0);
+    double rr = 0.0, bb = 0.0, rz1 = 0.0;
+    LdSum<float> ls{xa, first ? (const float*)nullptr : w.c, t.bvs, t.col};
+    for (int it = t.g; it < items; it += t.S) {
+      const int p = it >> t.bvs;
+      int i0, i1, i2;
+      decomp<DIM>(l0, p, i0, i1, i2);
+      double bp;
+      if (first) {
+        bp = rhs_at(P, t, bsrc, dsrc, p, it);
+        if (dsrc) w.bd[it] = bp;
+        bb += bp * bp;
+      } else {
+        bp = dsrc ? w.bd[it] : (bsrc ? bsrc[it] : 0.0);
+      }
+      double d, ax = 0.0;
+      if (xa || !first)
+        ax = op_at<double, DIM, KAPPA>(l0, ls, p, i0, i1, i2, d);
+      const double rd = bp - ax;
+      tgt[it] = ls(p);
+      const float rf = (float)rd;
+      w.f[0][it] = rf;
+      const float e = scale0 * rf / diag_at<float, DIM, KAPPA>(l0, p, i0, i1, i2);
+      w.e[0][0][it] = e;
+      rr += rd * rd;
+      if (op.L == 1) rz1 += (double)(rf * e);
+    }
+    contribute(t, SL_RRD, rr);
+    if (first) contribute(t, SL_BBD, bb);
+    if (op.L == 1) contribute(t, SL_RZ, rz1);
+    team_sync(t);
+    const double rrt = total(t, SL_RRD);
+    if (first) {
+      bbt = total(t, SL_BBD);
+      if (!(bbt > 0.0)) {
+        for (int it = t.g; it < items; it += t.S) tgt[it] = 0.0;
+        done = true;
+      }
+    }
+    if (!isfinite(rrt)) {
+      ctr.status |= STAT_NONFINITE;
+      done = true;
+    }
+    done = done || (rrt <= P.cfg.rtol * P.cfg.rtol * bbt);
+    if (done) ctr.max_res = fmax(ctr.max_res, bbt > 0.0 ? sqrt(rrt / bbt) : 0.0);
+    const bool all = __syncthreads_and(done);
+    if (all) break;
+    if (ref >= P.cfg.maxref) {
+      ctr.status |= STAT_NOCONV;
+      break;
+    }
+    bool idone = done;
+    const double itol2 = P.cfg.inner_rtol * P.cfg.inner_rtol * rrt;
+    double rr_in = rrt;
+    pcg_iterate<float, float, DIM, KAPPA>(t, op, w, w.c, true, itol2, idone, P.cfg, omega, scale0,
+                                          ctr, rr_in);
+    xa = tgt;
+    double* tmp = tgt;
+    tgt = oth;
+    oth = tmp;
+  }
+  ctr.refines += ref;
+  ctr.refine_max = max(ctr.refine_max, ref);
+  ctr.solves += 1;
+  return tgt;
+}
+
+template <typename T, int DIM, bool MIXED>
+__device__ __forceinline__ double* solve_any(const Team& t, const SweepParams& P, const Op& op,
+                                             const WSV<T>& w, const double* bsrc,
+                                             const double* dsrc, const double* x0, double* X1,
+                                             double* X2, Ctr& ctr) {
+  if constexpr (MIXED) {
+    if (op.has_kappa)
+      return solve_mixed<DIM, true>(t, P, op, w, bsrc, dsrc, x0, X1, X2, ctr);
+    return solve_mixed<DIM, false>(t, P, op, w, bsrc, dsrc, x0, X1, X2, ctr);
+  } else {
+    if (op.has_kappa) return solve_fp64<DIM, true>(t, P, op, w, bsrc, dsrc, x0, X1, ctr);
+    return solve_fp64<DIM, false>(t, P, op, w, bsrc, dsrc, x0, X1, ctr);
+  }
+}
+
+__device__ __forceinline__ int buf_index(const double* const* b, const double* x) {
+  return x == b[0] ? 0 : (x == b[1] ? 1 : 2);
+}
+
+template <typename T, int DIM, bool MIXED>
+__global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
+  __shared__ double s_red[NSLOT * LRP_MAXBV];
+  __shared__ double s_redw[32 * LRP_MAXBV];
+  Team t;
+  t.C = P.C;
+  t.rank = (P.C > 1) ? (int)cg::this_cluster().block_rank() : 0;
+  t.NT = blockDim.x;
+  t.tid = threadIdx.x;
+  t.g = t.rank * t.NT + t.tid;
+  t.S = t.C * t.NT;
+  t.BV = P.BV;
+  t.bvs = P.bv_shift;
+  t.col = t.g & (P.BV - 1);
+  t.red = s_red;
+  t.redw = s_redw;
+  const int team = blockIdx.x / P.C;
+  char* base = P.ws + (size_t)team * P.team_bytes;
+  WSV<T> w;
+  for (int k = 0; k < 3; ++k) w.dbuf[k] = (double*)(base + P.off_dbuf[k]);
+  w.bd = (double*)(base + P.off_bd);
+  w.obs = (double*)(base + P.off_obs);
+  w.r = (T*)(base + P.off_r);
+  w.p = (T*)(base + P.off_p);
+  w.q = (T*)(base + P.off_q);
+  w.c = (T*)(base + P.off_c);
+  w.e[0][0] = (T*)(base + P.off_e0[0]);
+  w.e[0][1] = (T*)(base + P.off_e0[1]);
+  w.f[0] = w.r;
+  for (int l = 1; l < LRP_MAXLEV; ++l) {
+    w.e[l][0] = (T*)(base + P.off_e[l][0]);
+    w.e[l][1] = (T*)(base + P.off_e[l][1]);
+    w.f[l] = (T*)(base + P.off_f[l]);
+  }
+  const int gcol = team * P.BV + t.col;
+  const bool valid = gcol < P.nvec;
+  const int N0 = P.step.lv[0].N;
+  const int items0 = N0 << t.bvs;
+  Ctr ctr;
+  int cur = (P.stages & ST_LOAD_X) ? 0 : min(max(P.end_buf[team], 0), 2);
+
+  if (P.stages & ST_LOAD_X) {
+    for (int it = t.g; it < items0; it += t.S) {
+      const int p = it >> t.bvs;
+      w.dbuf[0][it] = valid ? P.X[(size_t)gcol * P.ldx + p] : 0.0;
+    }
+    team_sync(t);
+  }
+  if (P.stages & ST_LOAD_D) {
+    const int nd = (P.n_obs * P.n_steps) << t.bvs;
+    for (int it = t.g; it < nd; it += t.S) {
+      const int e = it >> t.bvs;
+      w.obs[it] = valid ? P.Din[(size_t)gcol * P.lddin + e] : 0.0;
+    }
+    team_sync(t);
+  }
+  if (P.stages & ST_PRIOR_IN) {
+    double* X1 = w.dbuf[(cur + 1) % 3];
+    double* X2 = w.dbuf[(cur + 2) % 3];
+    double* res = solve_any<T, DIM, MIXED>(t, P, P.prior, w, w.dbuf[cur], nullptr, nullptr, X1,
+                                           X2, ctr);
+    cur = buf_index(w.dbuf, res);
+  }
+  if (P.stages & ST_FORWARD) {
+    for (int n = P.t_begin + 1; n <= P.t_end; ++n) {
+      double* X1 = w.dbuf[(cur + 1) % 3];
+      double* X2 = w.dbuf[(cur + 2) % 3];
+      double* res = solve_any<T, DIM, MIXED>(t, P, P.step, w, w.dbuf[cur], nullptr, w.dbuf[cur],
+                                             X1, X2, ctr);
+      cur = buf_index(w.dbuf, res);
+      // fused observation d_n = B y_n (/ sigma^2 for the Hessian); no barrier
+      // needed: the next phase only reads y_n as well
+      if ((P.stages & ST_FORWARD) && P.n_steps > 0 && (n % P.obs_every) == 0 &&
+          n / P.obs_every <= P.n_steps) {
+        const int k = n / P.obs_every - 1;
+        const int no = P.n_obs << t.bvs;
+        for (int it = t.g; it < no; it += t.S) {
+          const int s = it >> t.bvs;
+          double y = 0.0;
+          for (int c = 0; c < 8; ++c) {
+            const int node = P.obs_node[s * 8 + c];
+            if (node >= 0) y += P.obs_w[s * 8 + c] * res[(node << t.bvs) + t.col];
+          }
+          w.obs[((size_t)k * P.n_obs << t.bvs) + it] = y * P.inv_sigma2;
+          if ((P.stages & ST_STORE_D) && valid) P.Dout[(size_t)gcol * P.lddout + k * P.n_obs + s] = y;
+        }
+      }
+      if (P.stages & ST_TRAJ) {
+        const int chunk_pos = n - P.t_begin - 1;
+        if (valid) {
+          double* dst = P.traj + ((size_t)gcol * P.traj_cols + chunk_pos) * P.traj_ld;
+          for (int it = t.g; it < items0; it += t.S) dst[it >> t.bvs] = res[it];
+        }
+      }
+    }
+  }
+  if (P.stages & ST_ADJOINT) {
+    const double* q = nullptr;  // q_{nt+1} = 0
+    for (int n = P.adj_begin; n >= 1; --n) {
+      const bool obs = (n % P.obs_every) == 0 && n / P.obs_every <= P.n_steps;
+      if (!q && !obs) continue;
+      const double* dsrc = obs ? w.obs + ((size_t)(n / P.obs_every - 1) * P.n_obs << t.bvs) : nullptr;
+      const int qi = q ? buf_index(w.dbuf, q) : cur;
+      double* X1 = w.dbuf[(qi + 1) % 3];
+      double* X2 = w.dbuf[(qi + 2) % 3];
+      double* res = solve_any<T, DIM, MIXED>(t, P, P.step, w, q, dsrc, q, X1, X2, ctr);
+      q = res;
+    }
+    if (q) {
+      cur = buf_index(w.dbuf, q);
+    } else {
+      for (int it = t.g; it < items0; it += t.S) w.dbuf[cur][it] = 0.0;
+      team_sync(t);
+    }
+  }
+  if (P.stages & ST_PRIOR_OUT) {
+    double* X1 = w.dbuf[(cur + 1) % 3];
+    double* X2 = w.dbuf[(cur + 2) % 3];
+    double* res = solve_any<T, DIM, MIXED>(t, P, P.prior, w, w.dbuf[cur], nullptr, nullptr, X1,
+                                           X2, ctr);
+    cur = buf_index(w.dbuf, res);
+  }
+  if ((P.stages & ST_STORE_Y) && valid) {
+    for (int it = t.g; it < items0; it += t.S) P.Y[(size_t)gcol * P.ldy + (it >> t.bvs)] = w.dbuf[cur][it];
+  }
+  // keep every CTA's shared memory alive until all DSMEM readers are done
+  team_sync(t);
+  if (t.rank == 0 && t.tid == 0) {
+    P.end_buf[team] = cur;
+    atomicAdd(&P.stats->solves, (unsigned long long)ctr.solves);
+    atomicAdd(&P.stats->iters, (unsigned long long)ctr.iters);
+    atomicAdd(&P.stats->refines, (unsigned long long)ctr.refines);
+    atomicMax(&P.stats->iters_max, ctr.iters_max);
+    atomicMax(&P.stats->refine_max, ctr.refine_max);
+    if (ctr.status) atomicOr(&P.stats->status, ctr.status);
+  }
+  if (t.rank == 0 && t.tid < t.BV && valid) {
+    atomicMax(&P.stats->max_rel_res_bits, (unsigned long long)__double_as_longlong(ctr.max_res));
+  }
+}
+
+template <typename T, int DIM, bool MIXED>
+cudaError_t launch_sweep(const SweepParams& prm, cudaStream_t stream) {
+  auto kern = sweep_kernel<T, DIM, MIXED>;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(prm.n_teams * prm.C);
+  cfg.blockDim = dim3(prm.NT);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  int na = 0;
+  if (prm.C > 1) {
+    if (prm.C > 8) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) return e;
+    }
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = prm.C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    na = 1;
+  }
+  cfg.attrs = attr;
+  cfg.numAttrs = na;
+  return cudaLaunchKernelEx(&cfg, kern, prm);
+}
+
+}  // namespace lrp

@@ -1,0 +1,276 @@
+// Device building blocks of the persistent sweep kernel: the team (a
+// thread-block cluster of C CTAs owning BV interleaved columns), its barrier
+// and deterministic reductions, the finite-difference operator I + c L_l, and
+// the multigrid transfer operators.
+//
+// Operator (Sec. 6 Eq. (pde), implicit Euler block row of Eq. (st_pde), M = I):
+//   ((I + c L) v)_p = d_p v_p - (c/h^2) sum_faces kappa_f v_nbr(f),
+//   d_p = 1 + (c/h^2) sum_faces kappa_f,  v = 0 outside the grid.
+// Multigrid (preconditioner of PCG on I + c L): damped Jacobi smoothing,
+// full-weighting restriction (1D stencil [1/4 1/2 1/4]), bi/trilinear
+// prolongation (= 2^dim x restriction^T), rediscretised coarse operators,
+// exact solve on the single-node coarsest level. With equal pre and post
+// sweep counts the V-cycle is a fixed symmetric positive definite operator.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "lrp_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace lrp {
+
+enum { SL_RR = 0, SL_BB = 1, SL_RZ = 2, SL_PQ = 3, SL_RRD = 4, SL_BBD = 5, NSLOT = 8 };
+
+struct Team {
+  int C, rank, NT, tid, g, S, BV, bvs, col;
+  double* red;   // [NSLOT][LRP_MAXBV] CTA totals (shared memory)
+  double* redw;  // [32][LRP_MAXBV] warp partials (shared memory)
+};
+
+__device__ __forceinline__ void team_sync(const Team& t) {
+  if (t.C > 1) {
+    cg::this_cluster().sync();  // barrier.cluster arrive(release) + wait(acquire)
+  } else {
+    __syncthreads();
+  }
+}
+
+// Sum v over the CTA per column (lanes with equal col), store the CTA total
+// in slot. Deterministic order. Must be called by every thread of the CTA.
+__device__ __forceinline__ void contribute(const Team& t, int slot, double v) {
+  for (int off = 16; off >= t.BV; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  const int lane = t.tid & 31, w = t.tid >> 5;
+  if (lane < t.BV) t.redw[w * LRP_MAXBV + lane] = v;
+  __syncthreads();
+  if (t.tid < t.BV) {
+    double s = 0.0;
+    const int nw = t.NT >> 5;
+    for (int i = 0; i < nw; ++i) s += t.redw[i * LRP_MAXBV + t.tid];
+    t.red[slot * LRP_MAXBV + t.tid] = s;
+  }
+  __syncthreads();
+}
+
+// Team-wide total of slot for this thread's column; valid after a team_sync
+// that followed the contribute. Every CTA sums the ranks in the same order,
+// so all CTAs obtain bit-identical totals (and take identical branches).
+__device__ __forceinline__ double total(const Team& t, int slot) {
+  const int idx = slot * LRP_MAXBV + t.col;
+  if (t.C == 1) return t.red[idx];
+  cg::cluster_group cl = cg::this_cluster();
+  double s = 0.0;
+  for (int r = 0; r < t.C; ++r) s += *cl.map_shared_rank(t.red + idx, r);
+  return s;
+}
+
+__device__ __forceinline__ uint32_t fdiv(uint32_t x, const FastDiv& f) {
+  return (__umulhi(x, f.m) + x) >> f.s;
+}
+
+template <int DIM>
+__device__ __forceinline__ void decomp(const OpLevel& lv, int p, int& i0, int& i1, int& i2) {
+  const uint32_t q = fdiv((uint32_t)p, lv.dn);
+  i0 = p - (int)q * lv.n;
+  if (DIM == 3) {
+    const uint32_t q2 = fdiv(q, lv.dn);
+    i1 = (int)q - (int)q2 * lv.n;
+    i2 = (int)q2;
+  } else {
+    i1 = (int)q;
+    i2 = 0;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ const T* kap(const OpLevel& lv, int a);
+template <>
+__device__ __forceinline__ const double* kap<double>(const OpLevel& lv, int a) { return lv.kd[a]; }
+template <>
+__device__ __forceinline__ const float* kap<float>(const OpLevel& lv, int a) { return lv.kf[a]; }
+
+// Loader of one interleaved column of a team vector.
+template <typename T>
+struct Ld {
+  const T* v;
+  int bvs, col;
+  __device__ __forceinline__ T operator()(int q) const { return v[(q << bvs) + col]; }
+};
+
+// Loader of (x + c) for the refinement residual (x double, c inner type).
+template <typename TI>
+struct LdSum {
+  const double* x;  // may be NULL (zero)
+  const TI* c;      // may be NULL (zero)
+  int bvs, col;
+  __device__ __forceinline__ double operator()(int q) const {
+    const int i = (q << bvs) + col;
+    double s = x ? x[i] : 0.0;
+    if (c) s += (double)c[i];
+    return s;
+  }
+};
+
+// ((I + c L) v)_p and the diagonal d_p at node p = (i0,i1,i2).
+template <typename T, int DIM, bool KAPPA, class LD>
+__device__ __forceinline__ T op_at(const OpLevel& lv, const LD& ld, int p, int i0, int i1, int i2,
+                                   T& diag) {
+  const int n = lv.n;
+  T s, kd;
+  if (KAPPA) {
+    const T* kx = kap<T>(lv, 0);
+    const T* ky = kap<T>(lv, 1);
+    const int fx = p + (DIM == 3 ? (i2 * n + i1) : i1);
+    const T kw = kx[fx], ke = kx[fx + 1];
+    const int fy = p + (DIM == 3 ? i2 * n : 0);
+    const T ks = ky[fy], kn = ky[fy + n];
+    kd = kw + ke + ks + kn;
+    s = (i0 > 0 ? kw * ld(p - 1) : T(0)) + (i0 < n - 1 ? ke * ld(p + 1) : T(0)) +
+        (i1 > 0 ? ks * ld(p - n) : T(0)) + (i1 < n - 1 ? kn * ld(p + n) : T(0));
+    if (DIM == 3) {
+      const T* kz = kap<T>(lv, 2);
+      const int nn = n * n;
+      const T kdn = kz[p], kup = kz[p + nn];
+      kd += kdn + kup;
+      s += (i2 > 0 ? kdn * ld(p - nn) : T(0)) + (i2 < n - 1 ? kup * ld(p + nn) : T(0));
+    }
+  } else {
+    s = (i0 > 0 ? ld(p - 1) : T(0)) + (i0 < n - 1 ? ld(p + 1) : T(0)) +
+        (i1 > 0 ? ld(p - n) : T(0)) + (i1 < n - 1 ? ld(p + n) : T(0));
+    if (DIM == 3) {
+      const int nn = n * n;
+      s += (i2 > 0 ? ld(p - nn) : T(0)) + (i2 < n - 1 ? ld(p + nn) : T(0));
+    }
+    kd = T(2 * DIM);
+  }
+  const T ch2 = (T)lv.ch2;
+  diag = T(1) + ch2 * kd;
+  return diag * ld(p) - ch2 * s;
+}
+
+template <typename T, int DIM, bool KAPPA>
+__device__ __forceinline__ T diag_at(const OpLevel& lv, int p, int i0, int i1, int i2) {
+  const int n = lv.n;
+  T kd;
+  if (KAPPA) {
+    const T* kx = kap<T>(lv, 0);
+    const T* ky = kap<T>(lv, 1);
+    const int fx = p + (DIM == 3 ? (i2 * n + i1) : i1);
+    const int fy = p + (DIM == 3 ? i2 * n : 0);
+    kd = kx[fx] + kx[fx + 1] + ky[fy] + ky[fy + n];
+    if (DIM == 3) {
+      const T* kz = kap<T>(lv, 2);
+      kd += kz[p] + kz[p + n * n];
+    }
+  } else {
+    kd = T(2 * DIM);
+  }
+  return T(1) + (T)lv.ch2 * kd;
+}
+
+// ---------------------------------------------------------------------------
+// Multigrid phases. Each works over items [start, N*BV) with the given
+// stride; the caller ends the phase with a team barrier (team levels) or
+// __syncthreads (levels worked by CTA rank 0 alone).
+
+// One damped Jacobi sweep e_out = e_in + omega (f - A e_in) / d. If rz_r is
+// non-NULL, accumulates rz_r * e_out into rz (used for r.z after the last
+// post-smoothing sweep on the finest level).
+template <typename T, int DIM, bool KAPPA>
+__device__ __forceinline__ void mg_sweep(const OpLevel& lv, T* __restrict__ eo,
+                                         const T* __restrict__ ei, const T* __restrict__ f,
+                                         int start, int stride, int bvs, int col, T omega,
+                                         const T* rz_r, double& rz) {
+  const int items = lv.N << bvs;
+  Ld<T> ld{ei, bvs, col};
+  for (int it = start; it < items; it += stride) {
+    const int p = it >> bvs;
+    int i0, i1, i2;
+    decomp<DIM>(lv, p, i0, i1, i2);
+    T d;
+    const T ae = op_at<T, DIM, KAPPA>(lv, ld, p, i0, i1, i2, d);
+    const T e = ei[it] + omega * (f[it] - ae) / d;
+    eo[it] = e;
+    if (rz_r) rz += (double)(rz_r[it] * e);
+  }
+}
+
+// Restrict the residual f - A e of level l (fine) to level l+1 (coarse) by
+// full weighting, and start the coarse smoother: e_c = scale * f_c / d_c
+// (scale = omega, or 1 on the single-node coarsest level: exact solve).
+template <typename T, int DIM, bool KAPPA>
+__device__ __forceinline__ void mg_restrict(const OpLevel& lf, const OpLevel& lc,
+                                            const T* __restrict__ ef, const T* __restrict__ ff,
+                                            T* __restrict__ fc, T* __restrict__ ec, int start,
+                                            int stride, int bvs, int col, T scale) {
+  const int items = lc.N << bvs;
+  Ld<T> ld{ef, bvs, col};
+  const int nf = lf.n;
+  for (int it = start; it < items; it += stride) {
+    const int P = it >> bvs;
+    int c0, c1, c2;
+    decomp<DIM>(lc, P, c0, c1, c2);
+    T acc = T(0);
+    const int z0 = (DIM == 3) ? -1 : 0, z1 = (DIM == 3) ? 1 : 0;
+    for (int dz = z0; dz <= z1; ++dz) {
+      for (int dy = -1; dy <= 1; ++dy) {
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int F0 = 2 * c0 + 1 + dx, F1 = 2 * c1 + 1 + dy;
+          const int F2 = (DIM == 3) ? 2 * c2 + 1 + dz : 0;
+          const int pf = F0 + nf * (F1 + nf * F2);
+          T d;
+          const T res = ff[(pf << bvs) + col] - op_at<T, DIM, KAPPA>(lf, ld, pf, F0, F1, F2, d);
+          T w = (dx == 0 ? T(0.5) : T(0.25)) * (dy == 0 ? T(0.5) : T(0.25));
+          if (DIM == 3) w *= (dz == 0 ? T(0.5) : T(0.25));
+          acc += w * res;
+        }
+      }
+    }
+    fc[it] = acc;
+    ec[it] = scale * acc / diag_at<T, DIM, KAPPA>(lc, P, c0, c1, c2);
+  }
+}
+
+// e_f += P e_c (bi/trilinear interpolation, zero boundary).
+template <typename T, int DIM>
+__device__ __forceinline__ void mg_prolong(const OpLevel& lf, const OpLevel& lc,
+                                           T* __restrict__ ef, const T* __restrict__ ec,
+                                           int start, int stride, int bvs, int col) {
+  const int items = lf.N << bvs;
+  const int nc = lc.n;
+  for (int it = start; it < items; it += stride) {
+    const int p = it >> bvs;
+    int F[3];
+    decomp<DIM>(lf, p, F[0], F[1], F[2]);
+    int ci[3][2], cnt[3];
+    T cw[3][2];
+    for (int a = 0; a < DIM; ++a) {
+      if (F[a] & 1) {
+        ci[a][0] = (F[a] - 1) >> 1;
+        cw[a][0] = T(1);
+        cnt[a] = 1;
+      } else {
+        cnt[a] = 0;
+        const int lo = (F[a] >> 1) - 1, hi = F[a] >> 1;
+        if (lo >= 0) { ci[a][cnt[a]] = lo; cw[a][cnt[a]] = T(0.5); ++cnt[a]; }
+        if (hi < nc) { ci[a][cnt[a]] = hi; cw[a][cnt[a]] = T(0.5); ++cnt[a]; }
+      }
+    }
+    T acc = T(0);
+    const int n2 = (DIM == 3) ? cnt[2] : 1;
+    for (int c = 0; c < n2; ++c) {
+      const int z = (DIM == 3) ? ci[2][c] : 0;
+      const T wz = (DIM == 3) ? cw[2][c] : T(1);
+      for (int b = 0; b < cnt[1]; ++b) {
+        for (int a = 0; a < cnt[0]; ++a) {
+          const int P = ci[0][a] + nc * (ci[1][b] + nc * z);
+          acc += wz * cw[1][b] * cw[0][a] * ec[(P << bvs) + col];
+        }
+      }
+    }
+    ef[it] += acc;
+  }
+}
+
+}  // namespace lrp

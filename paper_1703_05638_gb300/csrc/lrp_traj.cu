@@ -1,0 +1,356 @@
+// Low-rank-in-time trajectory factors (Sec. 3: Y = [y_1 .. y_nt] ~ W V^T with
+// small rank; Sec. 4: rank control of factored sums by skinny QR and
+// truncated SVD).
+//
+// The forward sweep runs in chunks of s steps; each chunk's states land in a
+// buffer B (nx x s per column). Streaming recompression per column, with the
+// current factors Y_old ~ Qw diag(sig) V^T (Qw, V orthonormal columns):
+//   C = Qw^T B, B' = B - Qw C (twice: CGS2), B' = Q2 R2 (CholQR2),
+//   core = [[diag(sig), C], [0, R2]] = U S Zt (SVD),
+//   keep the r' leading triplets whose discarded Frobenius tail is at most
+//   (tol / K) ||core||_F (K = number of chunks; by the triangle inequality the
+//   accumulated error is at most tol ||Y||_F), capped at time_rank_max,
+//   Qw <- [Qw Q2] U[:, :r'], V <- blockdiag(V, I_s) Zt^T[:, :r'], sig <- S[:r'].
+// The SVD of the small core comes from the symmetric eigenproblem of
+// [[0, core], [core^T, 0]] (eigenvalues +-s_i, eigenvectors [u; v]/sqrt 2),
+// which keeps absolute accuracy eps*||core|| without squaring the core.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "lrp_dense.h"
+#include "lrp_internal.h"
+
+namespace lrp {
+
+// Aug_b (2m x 2m, col-major, m = r_b + s) = [[0, core], [core^T, 0]] with
+// core = [[diag(sig_b), C_b], [0, R_b]]; one CTA per column b.
+__global__ void k_build_aug(const int* r_arr, int s, const double* sig, size_t sig_stride, const double* C,
+                            size_t c_stride, const double* R, size_t r_stride, double* Aug, size_t aug_stride) {
+  const int b = blockIdx.x;
+  const int r = r_arr[b];
+  const int m = r + s, n2 = 2 * m;
+  const double* sg = sig + b * sig_stride;
+  const double* Cb = C + b * c_stride;  // r x s, ld r
+  const double* Rb = R + b * r_stride;  // s x s, ld s
+  double* A = Aug + b * aug_stride;
+  for (int e = threadIdx.x; e < n2 * n2; e += blockDim.x) {
+    const int i = e % n2, j = e / n2;
+    double v = 0.0;
+    int a = -1, c = -1;
+    if (i < m && j >= m) {
+      a = i;
+      c = j - m;
+    } else if (i >= m && j < m) {
+      a = j;
+      c = i - m;
+    }
+    if (a >= 0) {
+      if (a < r && c < r) v = (a == c) ? sg[a] : 0.0;
+      else if (a < r && c >= r) v = Cb[(size_t)(c - r) * r + a];
+      else if (a >= r && c >= r) v = Rb[(size_t)(c - r) * s + (a - r)];
+    }
+    A[e] = v;
+  }
+}
+
+// From the eigenvectors Zaug (2m x 2m, sorted decreasing) take U (m x rn) and
+// Zv (m x rn): U = sqrt2 * Zaug[0:m, 0:rn], Zv = sqrt2 * Zaug[m:2m, 0:rn].
+__global__ void k_split_uv(int m, int rn, const double* Zaug, double* U, double* Zv) {
+  const int e = threadIdx.x + blockIdx.x * blockDim.x;
+  if (e >= m * rn) return;
+  const int i = e % m, j = e / m;
+  const double sq2 = 1.4142135623730951;
+  U[(size_t)j * m + i] = sq2 * Zaug[(size_t)j * 2 * m + i];
+  Zv[(size_t)j * m + i] = sq2 * Zaug[(size_t)j * 2 * m + m + i];
+}
+
+// Vn[rows n0..n0+s, :] = Zv[r:r+s, :rn]; (rows 0..n0 come from a GEMM)
+__global__ void k_tail_rows(int n0, int s, int r, int m, int rn, const double* Zv, double* Vn, int ldv) {
+  const int e = threadIdx.x + blockIdx.x * blockDim.x;
+  if (e >= s * rn) return;
+  const int i = e % s, j = e / s;
+  Vn[(size_t)j * ldv + n0 + i] = Zv[(size_t)j * m + r + i];
+}
+
+__global__ void k_scale_cols(int nx, int r, const double* sig, double* W, int ldw) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  if (p >= nx || c >= r) return;
+  W[(size_t)c * ldw + p] *= sig[c];
+}
+
+#define CKT(call)                                          \
+  do {                                                     \
+    cudaError_t _e = (call);                               \
+    if (_e != cudaSuccess) return cuda_status(_e, #call);  \
+  } while (0)
+
+struct DBuf {
+  double* p = nullptr;
+  ~DBuf() {
+    if (p) cudaFree(p);
+  }
+  cudaError_t alloc(size_t n) { return cudaMalloc((void**)&p, std::max<size_t>(n, 1) * sizeof(double)); }
+};
+
+// Factor state of one column: Y_absorbed ~ Qw diag(sig) V^T.
+struct TrajCol {
+  DBuf Qa, Qb;  // nx x rmax (orthonormal columns)
+  DBuf V, Vn;   // nt x rmax
+  int r = 0;
+  int nrows = 0;  // time steps absorbed
+  double err_abs = 0.0;
+  double fro2 = 0.0;
+};
+
+// Scratch shared by all columns (batched over columns b with fixed strides).
+struct TrajWS {
+  int nvec, s, rmax, m;  // m = rmax + s
+  DBuf traj;             // nvec x s x nx: the chunk's states, orthonormalised in place
+  DBuf C, C2;            // nvec x (rmax*s)
+  DBuf R;                // nvec x s*s
+  DBuf part;             // gemm_tn scratch
+  size_t part_cap = 0;
+  DBuf Aug, Zaug;        // nvec x (2m)^2
+  DBuf th, work;         // nvec x 2m, nvec x 12m
+  DBuf U, Zv;            // m x m (per column, reused)
+  DBuf sig;              // nvec x rmax singular values of the current factors
+  int* iarr = nullptr;   // device: [0, nvec) ranks, [nvec, 2nvec) eig sizes
+  ~TrajWS() {
+    if (iarr) cudaFree(iarr);
+  }
+};
+
+// Absorb one chunk (sk steps, all columns) into the factors.
+static lrp_status absorb_chunk(lrp_problem* P, std::vector<TrajCol>& cols, TrajWS& ws, int sk, double tol_k) {
+  cudaStream_t st = P->stream;
+  const int nx = P->nx, nt = P->nt, nvec = ws.nvec, s = ws.s, rmax = ws.rmax, M = ws.m;
+  // 1. project the chunk onto the complement of each column's Qw (CGS2)
+  for (int b = 0; b < nvec; ++b) {
+    TrajCol& tc = cols[b];
+    const int r = tc.r;
+    double* B = ws.traj.p + (size_t)b * s * nx;
+    double* C = ws.C.p + (size_t)b * rmax * s;
+    if (r == 0) continue;
+    CKT(cudaMemsetAsync(C, 0, (size_t)r * sk * sizeof(double), st));
+    for (int pass = 0; pass < 2; ++pass) {
+      CKT(gemm_tn(st, nx, r, sk, tc.Qa.p, nx, B, nx, ws.C2.p, r, 1.0, 0.0, ws.part.p, ws.part_cap));
+      CKT(gemm_nn(st, nx, r, sk, -1.0, tc.Qa.p, nx, ws.C2.p, r, 1.0, B, nx));
+      CKT(axpby(st, (size_t)r * sk, 1.0, ws.C2.p, 1.0, C));
+    }
+  }
+  // 2. rank-revealing thin QR of the remainders (one CTA per column)
+  CKT(block_gs(st, nvec, nx, sk, ws.traj.p, (size_t)s * nx, nx, ws.R.p, (size_t)s * s, 1e-13, nullptr));
+  // 3. SVD of every column's small core via the augmented symmetric eigenproblem
+  std::vector<int> iarr(2 * nvec);
+  for (int b = 0; b < nvec; ++b) {
+    iarr[b] = cols[b].r;
+    iarr[nvec + b] = 2 * (cols[b].r + sk);
+  }
+  CKT(cudaMemcpyAsync(ws.iarr, iarr.data(), 2 * nvec * sizeof(int), cudaMemcpyHostToDevice, st));
+  note_launch();
+  // R of a short last chunk has leading dimension sk
+  k_build_aug<<<nvec, 256, 0, st>>>(ws.iarr, sk, ws.sig.p, (size_t)rmax, ws.C.p, (size_t)rmax * s, ws.R.p, (size_t)s * s,
+                                   ws.Aug.p, (size_t)4 * M * M);
+  CKT(cudaGetLastError());
+  CKT(eig_sym_batched(st, nvec, ws.iarr + nvec, 2 * M, ws.Aug.p, (size_t)4 * M * M, ws.Zaug.p, (size_t)4 * M * M,
+                      ws.th.p, (size_t)2 * M, ws.work.p, (size_t)12 * M, nullptr));
+  std::vector<double> th((size_t)nvec * 2 * M);
+  CKT(cudaMemcpyAsync(th.data(), ws.th.p, th.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CKT(cudaStreamSynchronize(st));
+  // 4. per column: truncation rank, new space factor, new time factor
+  for (int b = 0; b < nvec; ++b) {
+    TrajCol& tc = cols[b];
+    const int r = tc.r, m = r + sk;
+    std::vector<double> sv(m);
+    for (int i = 0; i < m; ++i) sv[i] = std::max(th[(size_t)b * 2 * M + i], 0.0);
+    double fro2 = 0.0;
+    for (double x : sv) fro2 += x * x;
+    std::vector<double> tail(m + 1, 0.0);
+    for (int i = m - 1; i >= 0; --i) tail[i] = tail[i + 1] + sv[i] * sv[i];
+    int rn = 0;
+    while (rn < m && tail[rn] > tol_k * tol_k * fro2) ++rn;
+    if (rn == 0 && m > 0 && sv[0] > 0) rn = 1;
+    rn = std::min(rn, rmax);
+    tc.err_abs += std::sqrt(tail[rn]);
+    tc.fro2 = fro2;
+    if (rn == 0) {
+      tc.r = 0;
+      tc.nrows += sk;
+      continue;
+    }
+    const double* Zb = ws.Zaug.p + (size_t)b * 4 * M * M;
+    note_launch();
+    k_split_uv<<<(m * rn + 255) / 256, 256, 0, st>>>(m, rn, Zb, ws.U.p, ws.Zv.p);
+    CKT(cudaGetLastError());
+    // Qw <- [Qw Q2] U
+    const double* Q2 = ws.traj.p + (size_t)b * s * nx;
+    if (r > 0) {
+      CKT(gemm_nn(st, nx, r, rn, 1.0, tc.Qa.p, nx, ws.U.p, m, 0.0, tc.Qb.p, nx));
+      CKT(gemm_nn(st, nx, sk, rn, 1.0, Q2, nx, ws.U.p + r, m, 1.0, tc.Qb.p, nx));
+    } else {
+      CKT(gemm_nn(st, nx, sk, rn, 1.0, Q2, nx, ws.U.p, m, 0.0, tc.Qb.p, nx));
+    }
+    std::swap(tc.Qa.p, tc.Qb.p);
+    // V <- blockdiag(V, I) Zv
+    if (r == 0 && tc.nrows > 0) CKT(cudaMemsetAsync(tc.Vn.p, 0, (size_t)nt * rn * sizeof(double), st));
+    if (r > 0) CKT(gemm_nn(st, tc.nrows, r, rn, 1.0, tc.V.p, nt, ws.Zv.p, m, 0.0, tc.Vn.p, nt));
+    note_launch();
+    k_tail_rows<<<(sk * rn + 255) / 256, 256, 0, st>>>(tc.nrows, sk, r, m, rn, ws.Zv.p, tc.Vn.p, nt);
+    CKT(cudaGetLastError());
+    std::swap(tc.V.p, tc.Vn.p);
+    CKT(cudaMemcpyAsync(ws.sig.p + (size_t)b * rmax, ws.th.p + (size_t)b * 2 * M, rn * sizeof(double),
+                        cudaMemcpyDeviceToDevice, st));
+    tc.r = rn;
+    tc.nrows += sk;
+  }
+  return LRP_OK;
+}
+
+lrp_status trajectory_factors_impl(lrp_problem* P, int nvec, const double* U, int ldu, double* Wout,
+                                   double* Vout, int* ranks, lrp_apply_stats* stats, bool with_hessian,
+                                   double* Yout, int ldy) {
+  auto t0 = std::chrono::steady_clock::now();
+  const int nx = P->nx, nt = P->nt;
+  const int s = std::min(16, std::max(1, P->desc.time_chunk));
+  const int rmax = P->desc.time_rank_max;
+  const int K = (nt + s - 1) / s;
+  const double tol_k = P->desc.time_trunc_tol / K;
+  std::vector<TrajCol> cols(nvec);
+  for (auto& c : cols) {
+    CKT(c.Qa.alloc((size_t)nx * rmax));
+    CKT(c.Qb.alloc((size_t)nx * rmax));
+    CKT(c.V.alloc((size_t)nt * rmax));
+    CKT(c.Vn.alloc((size_t)nt * rmax));
+  }
+  TrajWS ws;
+  ws.nvec = nvec;
+  ws.s = s;
+  ws.rmax = rmax;
+  ws.m = rmax + s;
+  const int M = ws.m;
+  CKT(ws.traj.alloc((size_t)nvec * s * nx));
+  CKT(ws.C.alloc((size_t)nvec * rmax * s));
+  CKT(ws.C2.alloc((size_t)rmax * s));
+  CKT(ws.R.alloc((size_t)nvec * s * s));
+  ws.part_cap = (size_t)std::max(M, 16) * 16 * 128;
+  CKT(ws.part.alloc(ws.part_cap));
+  CKT(ws.Aug.alloc((size_t)nvec * 4 * M * M));
+  CKT(ws.Zaug.alloc((size_t)nvec * 4 * M * M));
+  CKT(ws.th.alloc((size_t)nvec * 2 * M));
+  CKT(ws.work.alloc((size_t)nvec * 12 * M + 8));
+  CKT(ws.U.alloc((size_t)M * M));
+  CKT(ws.Zv.alloc((size_t)M * M));
+  CKT(ws.sig.alloc((size_t)nvec * rmax));
+  CKT(cudaMalloc(&ws.iarr, 2 * nvec * sizeof(int)));
+  lrp_apply_stats acc;
+  std::memset(&acc, 0, sizeof(acc));
+  lrp_status result = LRP_OK;
+  double iters_sum = 0.0;
+  long long solves = 0;
+  auto fold = [&](const lrp_apply_stats& st) {
+    acc.pcg_iters_max = std::max(acc.pcg_iters_max, st.pcg_iters_max);
+    acc.refine_max = std::max(acc.refine_max, st.refine_max);
+    acc.max_rel_residual = std::max(acc.max_rel_residual, st.max_rel_residual);
+    iters_sum += st.pcg_iters_mean * st.n_solves;
+    solves += st.n_solves;
+  };
+  for (int c0 = 0; c0 < nt; c0 += s) {
+    const int c1 = std::min(nt, c0 + s);
+    unsigned stages = ST_FORWARD | ST_TRAJ;
+    if (c0 == 0) stages |= ST_LOAD_X | (with_hessian ? ST_PRIOR_IN : 0);
+    lrp_apply_stats st;
+    lrp_status sres = run_sweep_ex(P, stages, nvec, U, ldu, nullptr, 0, nullptr, 0, nullptr, 0, &st, c0, c1,
+                                   ws.traj.p, s);
+    if (sres != LRP_OK && sres != LRP_ENOCONV) return sres;
+    if (sres == LRP_ENOCONV) result = sres;
+    fold(st);
+    lrp_status a = absorb_chunk(P, cols, ws, c1 - c0, tol_k);
+    if (a != LRP_OK) return a;
+  }
+  if (with_hessian) {
+    lrp_apply_stats st;
+    lrp_status sres = run_sweep_ex(P, ST_ADJOINT | ST_PRIOR_OUT | ST_STORE_Y, nvec, nullptr, 0, Yout, ldy,
+                                   nullptr, 0, nullptr, 0, &st, 0, 0, nullptr, 0);
+    if (sres != LRP_OK && sres != LRP_ENOCONV) return sres;
+    if (sres == LRP_ENOCONV) result = sres;
+    fold(st);
+  }
+  int rank_max = 0;
+  double err_max = 0.0;
+  for (int j = 0; j < nvec; ++j) {
+    TrajCol& tc = cols[j];
+    rank_max = std::max(rank_max, tc.r);
+    const double fro = std::sqrt(tc.fro2);
+    err_max = std::max(err_max, fro > 0 ? tc.err_abs / fro : 0.0);
+    if (ranks) ranks[j] = tc.r;
+    if (Wout && tc.r > 0) {
+      double* W = Wout + (size_t)j * nx * rmax;
+      CKT(cudaMemcpyAsync(W, tc.Qa.p, (size_t)nx * tc.r * sizeof(double), cudaMemcpyDeviceToDevice, P->stream));
+      dim3 grid((nx + 255) / 256, tc.r);
+      note_launch();
+      k_scale_cols<<<grid, 256, 0, P->stream>>>(nx, tc.r, ws.sig.p + (size_t)j * rmax, W, nx);
+      CKT(cudaGetLastError());
+    }
+    if (Vout && tc.r > 0)
+      CKT(cudaMemcpyAsync(Vout + (size_t)j * nt * rmax, tc.V.p, (size_t)nt * tc.r * sizeof(double),
+                          cudaMemcpyDeviceToDevice, P->stream));
+  }
+  CKT(cudaStreamSynchronize(P->stream));
+  if (stats) {
+    *stats = acc;
+    stats->n_solves = (int)solves;
+    stats->pcg_iters_mean = solves ? iters_sum / solves : 0.0;
+    stats->time_rank_max = rank_max;
+    stats->time_trunc_err = err_max;
+    stats->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return result;
+}
+
+}  // namespace lrp
+
+using namespace lrp;
+
+extern "C" lrp_status lrp_trajectory_factors(lrp_problem* P, int nvec, const double* U, int ldu, double* W,
+                                             double* V, int* ranks, lrp_apply_stats* st) {
+  if (!P || !U || !W || !V || !ranks || nvec < 0 || ldu < (P ? P->nx : 0)) {
+    set_error("lrp_trajectory_factors: invalid argument");
+    return LRP_EINVAL;
+  }
+  if (nvec == 0) return LRP_OK;
+  cudaSetDevice(P->device);
+  if (!is_device_ptr(U) || !is_device_ptr(W) || !is_device_ptr(V)) {
+    // stage through the device
+    const size_t nx = P->nx, nt = P->nt, rmax = P->desc.time_rank_max;
+    double *dU = nullptr, *dW = nullptr, *dV = nullptr;
+    cudaError_t e = cudaMalloc(&dU, nx * nvec * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&dW, nx * rmax * nvec * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&dV, nt * rmax * nvec * sizeof(double));
+    if (e != cudaSuccess) {
+      cudaFree(dU);
+      cudaFree(dW);
+      cudaFree(dV);
+      return cuda_status(e, "trajectory staging");
+    }
+    const cudaMemcpyKind ku = is_device_ptr(U) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaMemcpy2D(dU, nx * sizeof(double), U, (size_t)ldu * sizeof(double), nx * sizeof(double), nvec, ku);
+    cudaMemset(dW, 0, nx * rmax * nvec * sizeof(double));
+    cudaMemset(dV, 0, nt * rmax * nvec * sizeof(double));
+    lrp_status s = trajectory_factors_impl(P, nvec, dU, (int)nx, dW, dV, ranks, st, false, nullptr, 0);
+    const cudaMemcpyKind kw = is_device_ptr(W) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const cudaMemcpyKind kv = is_device_ptr(V) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    cudaMemcpy(W, dW, nx * rmax * nvec * sizeof(double), kw);
+    cudaMemcpy(V, dV, nt * rmax * nvec * sizeof(double), kv);
+    cudaFree(dU);
+    cudaFree(dW);
+    cudaFree(dV);
+    return s;
+  }
+  return trajectory_factors_impl(P, nvec, U, ldu, W, V, ranks, st, false, nullptr, 0);
+}

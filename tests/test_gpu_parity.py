@@ -1,0 +1,226 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Tolerances (relative, max-norm over the compared block): 1e-10 on the FP64
+path and 1e-6 on the mixed FP32/FP64-refinement path (the targets stated for
+this method); eigenvalues compared as sorted multisets with
+|lam_i - lam*_i| <= tol * lam*_1 for all i, plus relative error <= tol for the
+resolvable ones (lam*_i >= 1e-6 lam*_1 for FP64, 1e-3 lam*_1 for mixed).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import posterior as opost
+from oracle import spectrum as ospec
+from oracle import timefactors as otf
+from oracle.problem import Problem as OProblem
+
+lrp = pytest.importorskip("paper_1703_05638_gb300")
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+TOL = {lrp.LRP_FP64: 1e-10, lrp.LRP_MIXED: 1e-6}
+
+
+def relerr(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1703_05638_gb300 import build
+    build.build()
+    lrp.load()
+
+
+def _pair(spec, precision, **tuning):
+    return OProblem(spec), lrp.lrp_setup_problem(spec, precision=precision, **tuning)
+
+
+SMALL = [
+    dict(dim=2, n=15, nt=20, obs_every=3, n_obs=7, with_kappa=False),
+    dict(dim=2, n=31, nt=16, obs_every=1, n_obs=12, with_kappa=True),
+    dict(dim=3, n=7, nt=10, obs_every=2, n_obs=9, with_kappa=True),
+]
+TEAMS = [dict(team_ctas=1, team_cols=1), dict(team_ctas=2, team_cols=4), dict(team_ctas=4, team_cols=2)]
+
+
+@pytest.mark.parametrize("precision", [lrp.LRP_FP64, lrp.LRP_MIXED])
+@pytest.mark.parametrize("case", range(len(SMALL)))
+@pytest.mark.parametrize("team", range(len(TEAMS)))
+def test_sweeps_match_oracle(precision, case, team):
+    spec = synth.small_spec(**SMALL[case], seed=11 + case)
+    P, G = _pair(spec, precision, **TEAMS[team])
+    tol = TOL[precision]
+    nvec = 5  # ragged against every team width
+    U = synth.normal_block(P.nx, nvec, 21 + case)
+    D, st = lrp.lrp_forward_observe(G, U)
+    assert relerr(D, P.forward(U)) < tol, st
+    W = synth.normal_block(P.n_data, nvec, 31 + case)
+    X, st = lrp.lrp_adjoint(G, W)
+    assert relerr(X, P.adjoint(W)) < tol, st
+    Y, st = lrp.lrp_prior_half(G, U)
+    assert relerr(Y, P.prior_half(U)) < tol, st
+    H, st = lrp.lrp_hessian_apply(G, U)
+    assert relerr(H, P.hessian_apply(U)) < tol, st
+    M, st = lrp.lrp_hessian_apply(G, U, flags=lrp.LRP_MISFIT_ONLY)
+    assert relerr(M, P.misfit_apply(U)) < tol, st
+
+
+@pytest.mark.parametrize("precision", [lrp.LRP_FP64, lrp.LRP_MIXED])
+def test_tiny_workload_hessian(precision):
+    """The 31x31, nt=100 workload (lattice sensors every 10th step)."""
+    spec = synth.workload("tiny")
+    P, G = _pair(spec, precision)
+    X = synth.normal_block(P.nx, 3, 5)
+    H, st = lrp.lrp_hessian_apply(G, X)
+    assert relerr(H, P.hessian_apply(X)) < TOL[precision], st
+    # device (torch) inputs and outputs give the same result as host arrays
+    Xd = torch.from_numpy(X).cuda()
+    Hd, _ = lrp.lrp_hessian_apply(G, Xd)
+    assert relerr(Hd.cpu().numpy(), H) < TOL[precision]
+
+
+def test_edge_cases():
+    spec = synth.small_spec(dim=2, n=7, nt=6, obs_every=2, n_obs=3)
+    P, G = _pair(spec, lrp.LRP_FP64, team_ctas=2, team_cols=2)
+    # zero input -> zero output
+    Z, _ = lrp.lrp_hessian_apply(G, np.zeros((P.nx, 3)))
+    assert np.all(Z == 0.0)
+    # a single column, then a block with a zero column among nonzero ones
+    X = synth.normal_block(P.nx, 3, 2)
+    X[:, 1] = 0.0
+    H, _ = lrp.lrp_hessian_apply(G, X)
+    np.testing.assert_allclose(H, P.hessian_apply(X), rtol=0, atol=1e-10 * np.abs(H).max())
+    assert np.all(H[:, 1] == 0.0)
+    H1, _ = lrp.lrp_hessian_apply(G, X[:, :1])
+    assert relerr(H1, H[:, :1]) < 1e-12
+    # invalid setups are rejected with LRP_EINVAL
+    bad = synth.small_spec(dim=2, n=6, nt=4)
+    with pytest.raises(lrp.LrpError) as e:
+        lrp.lrp_setup_problem(bad)
+    assert e.value.status == lrp.LRP_EINVAL
+    bad = synth.small_spec(dim=2, n=7, nt=4)
+    bad.sensors = np.array([[0.5, 1.2]])
+    with pytest.raises(lrp.LrpError) as e:
+        lrp.lrp_setup_problem(bad)
+    assert e.value.status == lrp.LRP_EINVAL
+    # non-finite input is reported
+    Xn = X.copy()
+    Xn[3, 0] = np.nan
+    with pytest.raises(lrp.LrpError) as e:
+        lrp.lrp_hessian_apply(G, Xn)
+    assert e.value.status == lrp.LRP_ENONFINITE
+
+
+def _check_eigs(lam, lam_ref, tol, resolvable):
+    k = len(lam)
+    assert k == len(lam_ref)
+    assert np.max(np.abs(lam - lam_ref)) <= tol * lam_ref[0]
+    big = lam_ref >= resolvable * lam_ref[0]
+    assert np.max(np.abs(lam[big] - lam_ref[big]) / lam_ref[big]) <= tol
+
+
+@pytest.mark.parametrize("block", [1, 2, 4])
+def test_lanczos_tiny_fp64(block):
+    spec = synth.workload("tiny")
+    P, G = _pair(spec, lrp.LRP_FP64)
+    lam_ref, V_ref = ospec.eig_dense(P.hessian_explicit())
+    post, st = lrp.lrp_lowrank_posterior(G, k=30, block=block, eig_tol=1e-11)
+    lam, V = post.eigs(vectors=True)
+    _check_eigs(lam, lam_ref[:30], 1e-10, 1e-6)
+    # eigenvectors through an invariant: the projector on the top-3 space
+    # (lam_3 > lam_4 strictly)
+    Pg = V[:, :3] @ V[:, :3].T
+    Pr = V_ref[:, :3] @ V_ref[:, :3].T
+    assert np.max(np.abs(Pg - Pr)) < 1e-8
+    assert st["n_matvec"] <= 4 * 30 + 8 * block
+
+
+def test_lanczos_and_queries_mixed_medium():
+    """Block Lanczos on a 63^2 problem in the mixed path, then mean, variance
+    and samples against the oracle's low-rank formulas with oracle eigenpairs
+    at the same k (k chosen at a spectral gap so the rank-k projector is
+    unique)."""
+    spec = synth.small_spec(dim=2, n=31, nt=40, obs_every=4, n_obs=16, sigma=1e-2, alpha=0.05, seed=3)
+    P, G = _pair(spec, lrp.LRP_MIXED)
+    lam_ref, V_ref = ospec.eig_dense(P.hessian_explicit())
+    gaps = lam_ref[:40] / lam_ref[1:41]
+    k = int(np.argmax(gaps[8:30]) + 8) + 1
+    post, st = lrp.lrp_lowrank_posterior(G, k=k, block=4, eig_tol=1e-9)
+    lam = post.eigs()
+    _check_eigs(lam, lam_ref[:k], 1e-6, 1e-3)
+    u_true = P.prior_half(synth.normal_block(P.nx, 1, 8)[:, 0])
+    y = P.forward(u_true) + spec.sigma * synth.normal_block(P.n_data, 1, 9)[:, 0]
+    nodes = synth.query_nodes(P.nx, 64, 10)
+    xi = synth.normal_block(P.nx, 3, 12)
+    for sigma in (0.0, 3e-2):
+        s_eff = sigma or spec.sigma
+        out = lrp.lrp_posterior_query(post, lrp.LRP_Q_MEAN | lrp.LRP_Q_VARIANCE | lrp.LRP_Q_SAMPLES,
+                                      y_obs=y, sigma=sigma, points=nodes, xi=xi)
+        m_ref = opost.mean_lowrank(P, lam_ref[:k], V_ref[:, :k], y, sigma=s_eff)
+        v_ref = opost.variance_lowrank(P, lam_ref[:k], V_ref[:, :k], nodes, sigma=s_eff)
+        s_ref = opost.samples_lowrank(P, lam_ref[:k], V_ref[:, :k], m_ref, xi, sigma=s_eff)
+        assert relerr(out["mean"], m_ref) < 1e-6
+        assert relerr(out["variance"], v_ref) < 1e-6
+        assert relerr(out["samples"], s_ref) < 1e-6
+
+
+def test_checkpoint_roundtrip(tmp_path):
+    spec = synth.small_spec(dim=2, n=15, nt=10, obs_every=2, n_obs=6)
+    _, G = _pair(spec, lrp.LRP_FP64)
+    post, _ = lrp.lrp_lowrank_posterior(G, k=6, block=2, eig_tol=1e-10)
+    path = str(tmp_path / "post.bin")
+    lrp.lrp_posterior_save(post, path)
+    post2 = lrp.lrp_posterior_load(G, path)
+    l1, V1 = post.eigs(vectors=True)
+    l2, V2 = post2.eigs(vectors=True)
+    np.testing.assert_array_equal(l1, l2)
+    np.testing.assert_array_equal(V1, V2)
+
+
+@pytest.mark.parametrize("precision", [lrp.LRP_FP64, lrp.LRP_MIXED])
+def test_trajectory_factors(precision):
+    """Low-rank-in-time factors: ||Y - W V^T||_F <= tol ||Y||_F (plus the
+    solver error) and the rank is near the optimal SVD rank (Sec. 3)."""
+    spec = synth.small_spec(dim=2, n=31, nt=70, obs_every=5, n_obs=8, seed=4)
+    spec.time_trunc_tol = 1e-8
+    P, G = _pair(spec, precision)
+    U = P.prior_half(synth.normal_block(P.nx, 2, 6))
+    facs, st = lrp.lrp_trajectory_factors(G, U)
+    for j, (W, V) in enumerate(facs):
+        Y = P.trajectory(U[:, j])
+        err = np.linalg.norm(Y - W @ V.T) / np.linalg.norm(Y)
+        assert err <= 1e-8 + 10 * TOL[precision], (err, st)
+        r_opt = otf.truncate(Y, 1e-8, 40)[0].shape[1]
+        assert r_opt <= W.shape[1] <= r_opt + 8
+    assert st["time_trunc_err"] <= 1e-8
+
+
+def test_hessian_with_trajectory_factors_matches_plain():
+    spec = synth.small_spec(dim=2, n=15, nt=40, obs_every=4, n_obs=6, seed=5)
+    P, G = _pair(spec, lrp.LRP_FP64)
+    X = synth.normal_block(P.nx, 3, 7)
+    H1, _ = lrp.lrp_hessian_apply(G, X)
+    H2, st = lrp.lrp_hessian_apply(G, X, flags=lrp.LRP_KEEP_TRAJ_FACTORS)
+    assert relerr(H2, H1) < 1e-12
+    assert 1 <= st["time_rank_max"] <= 40
+
+
+@pytest.mark.parametrize("precision", [lrp.LRP_FP64, lrp.LRP_MIXED])
+def test_full_size_heat2d_sampled(precision):
+    """The 127^2, nt=500 workload in the launch configuration the benchmark
+    uses: one Hessian apply on two columns against the oracle."""
+    spec = synth.workload("heat2d_127")
+    P, G = _pair(spec, precision)
+    X = synth.normal_block(P.nx, 2, 41)
+    H, st = lrp.lrp_hessian_apply(G, X)
+    assert relerr(H, P.hessian_apply(X)) < TOL[precision], st
