@@ -102,6 +102,8 @@ typedef struct {
   int team_cols;            /* columns per cluster: 1, 2, 4, 8 or 16 */
   int mg_nu;                /* Jacobi sweeps before and after each coarse correction */
   double inner_rtol;        /* LRP_MIXED: FP32 inner relative tolerance (0 -> 1e-4) */
+  int coarse_items;         /* multigrid levels with at most this many points x columns are
+                               solved by every CTA of a team in shared memory (0 -> 1024) */
 } lrp_problem_desc;
 
 typedef struct {

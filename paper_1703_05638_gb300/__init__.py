@@ -39,7 +39,7 @@ class lrp_problem_desc(C.Structure):
                 ("precision", C.c_int), ("time_trunc_tol", C.c_double), ("time_rank_max", C.c_int),
                 ("time_chunk", C.c_int), ("solve_rtol", C.c_double), ("pcg_maxit", C.c_int),
                 ("team_ctas", C.c_int), ("team_cols", C.c_int), ("mg_nu", C.c_int),
-                ("inner_rtol", C.c_double)]
+                ("inner_rtol", C.c_double), ("coarse_items", C.c_int)]
 
 
 class lrp_apply_stats(C.Structure):

@@ -8,6 +8,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -72,6 +73,7 @@ lrp_status ensure_workspace(lrp_problem* P, size_t bytes) {
   cudaError_t e = cudaMalloc((void**)&P->ws, want);
   if (e != cudaSuccess) return cuda_status(e, "workspace cudaMalloc");
   P->ws_bytes = want;
+  if (P->poison) cudaMemset(P->ws, P->poison & 0xFF, want);  // 0xFF bytes: NaN in FP32 and FP64
   return LRP_OK;
 }
 
@@ -116,7 +118,7 @@ static std::vector<double> coarsen_faces(const std::vector<double>& kf, int nf, 
 
 static void default_tuning(lrp_problem* P) {
   const lrp_problem_desc& d = P->desc;
-  P->nthreads = 256;
+  P->nthreads = 512;
   P->team_cols = d.team_cols > 0 ? d.team_cols : 1;
   if (d.team_ctas > 0) {
     P->team_ctas = d.team_ctas;
@@ -127,7 +129,8 @@ static void default_tuning(lrp_problem* P) {
   } else {
     P->team_ctas = 1;
   }
-  P->coarse_items = 4 * P->nthreads;
+  P->coarse_items = d.coarse_items > 0 ? d.coarse_items : 1024;
+  P->smem_cap = 160 * 1024;
 }
 
 }  // namespace lrp
@@ -215,6 +218,10 @@ lrp_status lrp_setup_problem(const lrp_problem_desc* desc, void* cuda_stream, lr
   P->prof_ev[0] = P->prof_ev[1] = nullptr;
   P->prof_ms = P->prof_bytes = 0.0;
   P->prof_launches = 0;
+  {
+    const char* pz = std::getenv("LRP_POISON");  // byte value to fill new workspace with (1 -> 0xFF)
+    P->poison = pz ? (std::atoi(pz) == 1 ? 0xFF : (std::atoi(pz) | 0x100)) : 0;
+  }
   auto fail = [&](lrp_status s) {
     lrp_problem_destroy(P);
     return s;
@@ -261,6 +268,10 @@ lrp_status lrp_setup_problem(const lrp_problem_desc* desc, void* cuda_stream, lr
     }
     P->step.lv[l].ch2 = P->tau * h2inv;
     P->prior.lv[l].ch2 = d.prior_alpha * h2inv;
+    P->step.lv[l].dinv = 1.0 / (1.0 + P->step.lv[l].ch2 * 2 * d.dim);
+    P->prior.lv[l].dinv = 1.0 / (1.0 + P->prior.lv[l].ch2 * 2 * d.dim);
+    P->step.lv[l].dinvd = P->prior.lv[l].dinvd = nullptr;
+    P->step.lv[l].dinvf = P->prior.lv[l].dinvf = nullptr;
     if (has_kappa) {
       for (int a = 0; a < d.dim; ++a) {
         if (l > 0) kcur[a] = coarsen_faces(kcur[a], ((d.n + 1) >> (l - 1)) - 1, d.dim, a);
@@ -275,6 +286,32 @@ lrp_status lrp_setup_problem(const lrp_problem_desc* desc, void* cuda_stream, lr
         P->step.lv[l].kd[a] = kd;
         P->step.lv[l].kf[a] = kf;
       }
+      // per-node inverse diagonal 1 / (1 + (tau/h^2) sum of the node's face kappas)
+      const int nl = P->step.lv[l].n, Nl = P->step.lv[l].N;
+      std::vector<double> dinv(Nl);
+      for (int p = 0; p < Nl; ++p) {
+        int ii[3] = {p % nl, (p / nl) % nl, p / (nl * nl)};
+        double ks = 0.0;
+        for (int a = 0; a < d.dim; ++a) {
+          int ext[3];
+          for (int b = 0; b < 3; ++b) ext[b] = (b < d.dim) ? (b == a ? nl + 1 : nl) : 1;
+          int f[3] = {ii[0], ii[1], d.dim == 3 ? ii[2] : 0};
+          const size_t lo = (size_t)f[0] + (size_t)ext[0] * ((size_t)f[1] + (size_t)ext[1] * f[2]);
+          f[a] += 1;
+          const size_t hi = (size_t)f[0] + (size_t)ext[0] * ((size_t)f[1] + (size_t)ext[1] * f[2]);
+          ks += kcur[a][lo] + kcur[a][hi];
+        }
+        dinv[p] = 1.0 / (1.0 + P->step.lv[l].ch2 * ks);
+      }
+      double* dd = nullptr;
+      float* df = nullptr;
+      lrp_status s2 = upload(P, &dd, dinv);
+      if (s2 != LRP_OK) return fail(s2);
+      std::vector<float> dinv32(dinv.begin(), dinv.end());
+      s2 = upload(P, &df, dinv32);
+      if (s2 != LRP_OK) return fail(s2);
+      P->step.lv[l].dinvd = dd;
+      P->step.lv[l].dinvf = df;
     }
   }
   P->hash = hash;

@@ -47,13 +47,16 @@ struct OpLevel {
   int N;        // n^dim
   FastDiv dn;   // division by n
   double ch2;   // c / h_l^2
+  double dinv;  // 1 / diagonal when kappa = 1
   const double* kd[3];  // face diffusivity (NULL -> 1), see kappa layout in lrp.h
   const float* kf[3];
+  const double* dinvd;  // per-node 1 / diagonal when kappa is given
+  const float* dinvf;
 };
 
 struct Op {
   int L;        // number of levels
-  int Lt;       // levels worked by the whole team (the rest by CTA rank 0 alone)
+  int Ls;       // levels Ls..L-1 are solved by every CTA of a team in its shared memory
   int has_kappa;
   OpLevel lv[LRP_MAXLEV];
 };
@@ -120,6 +123,9 @@ struct SweepParams {
   size_t off_dbuf[3], off_bd, off_obs;        // double vectors
   size_t off_r, off_p, off_q, off_c, off_e0[2];  // inner vectors (T)
   size_t off_e[LRP_MAXLEV][2], off_f[LRP_MAXLEV]; // coarse levels (T)
+  size_t smem_off[LRP_MAXLEV][3];  // shared-memory coarse levels: e0, e1, f offsets (bytes)
+  size_t smem_bytes;
+  int poison;         // fill the dynamic shared memory with NaN first (read-before-write check)
   int start_buf;      // index of the buffer that holds the sweep state at launch
   int* end_buf;       // device: buffer index holding the state at exit (per team)
   SolveCfg cfg;
@@ -157,7 +163,8 @@ struct lrp_problem {
   int* end_buf;
   int sm_count;
   // tuned launch parameters
-  int team_ctas, team_cols, nthreads, coarse_items;
+  int team_ctas, team_cols, nthreads, coarse_items, smem_cap;
+  int poison;  // LRP_POISON set: new workspace and shared memory start as NaN
   lrp::SolveCfg cfg;
   uint64_t hash;
   // sweep-kernel ledger (lrp_sweep_profile): CUDA-event time and algorithmic

@@ -9,6 +9,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -178,6 +179,13 @@ lrp_status lrp_lowrank_posterior(lrp_problem* P, int k, int block, double eig_to
       CK(cudaMemcpyAsync(h_res.data(), resid.p, kk * sizeof(double), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       const double th0 = std::max(h_theta[0], 1e-300);
+      if (std::getenv("LRP_VERBOSE")) {
+        double mr = 0.0;
+        for (int i = 0; i < kk; ++i) mr = std::max(mr, h_res[i] / th0);
+        std::fprintf(stderr, "[lrp] lanczos j=%d cols=%d theta1=%.6e max_resid=%.3e apply_ms=%.1f total_ms=%.1f\n", j,
+                     cols, h_theta[0], mr, ms_apply,
+                     std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
+      }
       bool ok = kk == k || cols >= nx;
       max_res = 0.0;
       for (int i = 0; i < kk; ++i) {

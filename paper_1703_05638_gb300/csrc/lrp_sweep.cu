@@ -16,6 +16,20 @@ extern template cudaError_t launch_sweep<double, 2, false>(const SweepParams&, c
 extern template cudaError_t launch_sweep<double, 3, false>(const SweepParams&, cudaStream_t);
 extern template cudaError_t launch_sweep<float, 2, true>(const SweepParams&, cudaStream_t);
 extern template cudaError_t launch_sweep<float, 3, true>(const SweepParams&, cudaStream_t);
+template <typename T, int DIM, bool MIXED>
+int max_resident_teams(int C, int NT, size_t smem, int sm_count);
+extern template int max_resident_teams<double, 2, false>(int, int, size_t, int);
+extern template int max_resident_teams<double, 3, false>(int, int, size_t, int);
+extern template int max_resident_teams<float, 2, true>(int, int, size_t, int);
+extern template int max_resident_teams<float, 3, true>(int, int, size_t, int);
+
+static int resident_teams(bool mixed, int dim, int C, int NT, size_t smem, int sm_count) {
+  if (dim == 2)
+    return mixed ? max_resident_teams<float, 2, true>(C, NT, smem, sm_count)
+                 : max_resident_teams<double, 2, false>(C, NT, smem, sm_count);
+  return mixed ? max_resident_teams<float, 3, true>(C, NT, smem, sm_count)
+               : max_resident_teams<double, 3, false>(C, NT, smem, sm_count);
+}
 
 
 static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -94,18 +108,33 @@ lrp_status run_sweep_ex(lrp_problem* Pr, unsigned stages, int nvec, const double
   prm.ws = Pr->ws;
   prm.step = Pr->step;
   prm.prior = Pr->prior;
-  // levels worked by the whole team: those with at least coarse_items items
-  auto team_levels = [&](Op& op) {
-    int Lt = 0;
-    if (Pr->team_ctas > 1) {
-      for (int l = 0; l < op.L; ++l)
-        if ((long long)op.lv[l].N * BV >= Pr->coarse_items) Lt = l + 1;
-      if (Lt < 1) Lt = 1;
+  // coarse levels solved redundantly in every CTA's shared memory: the first
+  // level l >= 1 with at most coarse_items items whose levels l..L-1 fit the
+  // shared-memory budget
+  int Ls = Pr->L > 1 ? Pr->L - 1 : 1;
+  for (int l = Pr->L - 1; l >= 1; --l) {
+    size_t bytes = 0;
+    for (int c = l; c < Pr->L; ++c) bytes += 3 * (((size_t)Pr->step.lv[c].N * BV * tsz + 15) & ~(size_t)15);
+    if ((long long)Pr->step.lv[l].N * BV <= Pr->coarse_items && bytes <= (size_t)Pr->smem_cap) Ls = l;
+  }
+  size_t soff = 0;
+  for (int l = 0; l < LRP_MAXLEV; ++l) {
+    for (int k = 0; k < 3; ++k) prm.smem_off[l][k] = 0;
+    if (l >= Ls && l < Pr->L) {
+      const size_t b = ((size_t)Pr->step.lv[l].N * BV * tsz + 15) & ~(size_t)15;
+      for (int k = 0; k < 3; ++k) {
+        prm.smem_off[l][k] = soff;
+        soff += b;
+      }
     }
-    op.Lt = Lt;
-  };
-  team_levels(prm.step);
-  team_levels(prm.prior);
+  }
+  prm.smem_bytes = soff;
+  prm.poison = Pr->poison;
+  prm.step.Ls = Ls;
+  prm.prior.Ls = Ls;
+  // team size: the largest C <= the requested one whose teams all stay resident
+  int C = Pr->team_ctas;
+  while (C > 1 && resident_teams(mixed, Pr->dim, C, Pr->nthreads, soff, Pr->sm_count) < n_teams) C >>= 1;
   prm.dim = Pr->dim;
   prm.nt = Pr->nt;
   prm.t_begin = t_begin;
@@ -123,7 +152,7 @@ lrp_status run_sweep_ex(lrp_problem* Pr, unsigned stages, int nvec, const double
   prm.bt_ptr = Pr->bt_ptr;
   prm.bt_idx = Pr->bt_idx;
   prm.bt_w = Pr->bt_w;
-  prm.C = Pr->team_ctas;
+  prm.C = C;
   prm.NT = Pr->nthreads;
   prm.BV = BV;
   prm.bv_shift = bvs;

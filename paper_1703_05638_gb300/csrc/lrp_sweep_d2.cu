@@ -4,4 +4,5 @@
 
 namespace lrp {
 template cudaError_t launch_sweep<double, 2, false>(const SweepParams&, cudaStream_t);
+template int max_resident_teams<double, 2, false>(int, int, size_t, int);
 }  // namespace lrp

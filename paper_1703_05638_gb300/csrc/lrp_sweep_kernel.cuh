@@ -35,74 +35,105 @@ struct Ctr {
   int iters_max = 0, refine_max = 0;
   double max_res = 0.0;
   int status = 0;
+  double mix_scale = 1.0;  // power-of-two scale of the next FP32 inner problem (this column)
+};
+
+// 2^-round(log2(x)) for x > 0 (exact power of two; 1 for x = 0 or non-finite)
+__device__ __forceinline__ double pow2_inv(double x) {
+  if (!(x > 0.0) || !isfinite(x)) return 1.0;
+  int e;
+  frexp(x, &e);
+  return ldexp(1.0, -e);
+}
+
+// Pointers of the shared-memory copies of the coarse levels Ls..L-1.
+template <typename T>
+struct SmemLv {
+  T* e[LRP_MAXLEV][2];
+  T* f[LRP_MAXLEV];
 };
 
 // V-cycle: z = M r. On entry f[0] = r is complete and e[0][0] holds the first
-// (pointwise) smoother sweep of level 0. On exit z = e[0][ecur0] and the
-// team total r.z is in slot SL_RZ.
+// (pointwise) smoother sweep of level 0. Levels 0..Ls-1 live in global memory
+// and are worked by the whole team (phases separated by team barriers);
+// levels Ls..L-1 are small: every CTA restricts level Ls-1 into its own
+// shared-memory copy of level Ls and runs the rest of the cycle there with
+// block barriers only, so no CTA idles and no team barrier is needed before
+// the prolongation back to level Ls-1 (all copies are bit-identical). On exit
+// z = e[0][returned index] and the team total r.z is in slot SL_RZ.
 template <typename T, int DIM, bool KAPPA>
-__device__ int vcycle(const Team& t, const Op& op, const WSV<T>& w, T omega, int nu) {
+__device__ int vcycle(const Team& t, const Op& op, const WSV<T>& w, const SmemLv<T>& sm, T omega, int nu) {
   int ecur[LRP_MAXLEV];
   for (int l = 0; l < LRP_MAXLEV; ++l) ecur[l] = 0;
   const int L = op.L;
-  const int Lt = min(op.Lt, L - 1);
-  double rz = 0.0;
   if (L == 1) return 0;  // z = r/d was formed exactly in the fused phase (rz too)
-  // down, team levels
-  for (int l = 0; l < Lt; ++l) {
+  const int Ls = op.Ls;  // 1 <= Ls <= L-1
+  double rz = 0.0;
+  // down: team levels 0..Ls-2 (pre-smoothing, restriction in global memory)
+  for (int l = 0; l < Ls - 1; ++l) {
     for (int s = 1; s < nu; ++s) {
       mg_sweep<T, DIM, KAPPA>(op.lv[l], w.e[l][ecur[l] ^ 1], w.e[l][ecur[l]], w.f[l], t.g, t.S,
                               t.bvs, t.col, omega, (const T*)nullptr, rz);
       ecur[l] ^= 1;
       team_sync(t);
     }
-    const T sc = (l + 1 == L - 1) ? T(1) : omega;
     mg_restrict<T, DIM, KAPPA>(op.lv[l], op.lv[l + 1], w.e[l][ecur[l]], w.f[l], w.f[l + 1],
-                               w.e[l + 1][0], t.g, t.S, t.bvs, t.col, sc);
+                               w.e[l + 1][0], t.g, t.S, t.bvs, t.col, omega);
     ecur[l + 1] = 0;
     team_sync(t);
   }
-  // levels below the team levels: CTA rank 0 alone, __syncthreads between phases
-  if (Lt < L - 1) {
-    const bool me = (t.rank == 0);
-    for (int l = Lt; l < L - 1; ++l) {
-      for (int s = 1; s < nu; ++s) {
-        if (me) {
-          mg_sweep<T, DIM, KAPPA>(op.lv[l], w.e[l][ecur[l] ^ 1], w.e[l][ecur[l]], w.f[l], t.tid,
-                                  t.NT, t.bvs, t.col, omega, (const T*)nullptr, rz);
-          __syncthreads();
-        }
-        ecur[l] ^= 1;
-      }
-      const T sc = (l + 1 == L - 1) ? T(1) : omega;
-      if (me) {
-        mg_restrict<T, DIM, KAPPA>(op.lv[l], op.lv[l + 1], w.e[l][ecur[l]], w.f[l], w.f[l + 1],
-                                   w.e[l + 1][0], t.tid, t.NT, t.bvs, t.col, sc);
-        __syncthreads();
-      }
-      ecur[l + 1] = 0;
+  // level Ls-1: pre-smoothing by the team
+  {
+    const int l = Ls - 1;
+    for (int s = 1; s < nu; ++s) {
+      mg_sweep<T, DIM, KAPPA>(op.lv[l], w.e[l][ecur[l] ^ 1], w.e[l][ecur[l]], w.f[l], t.g, t.S,
+                              t.bvs, t.col, omega, (const T*)nullptr, rz);
+      ecur[l] ^= 1;
+      team_sync(t);
     }
-    for (int l = L - 2; l >= Lt; --l) {
-      if (me) {
-        mg_prolong<T, DIM>(op.lv[l], op.lv[l + 1], w.e[l][ecur[l]], w.e[l + 1][ecur[l + 1]], t.tid,
-                           t.NT, t.bvs, t.col);
-        __syncthreads();
-      }
-      for (int s = 0; s < nu; ++s) {
-        if (me) {
-          mg_sweep<T, DIM, KAPPA>(op.lv[l], w.e[l][ecur[l] ^ 1], w.e[l][ecur[l]], w.f[l], t.tid,
-                                  t.NT, t.bvs, t.col, omega, (const T*)nullptr, rz);
-          __syncthreads();
-        }
-        ecur[l] ^= 1;
-      }
-    }
-    team_sync(t);
   }
-  // up, team levels
-  for (int l = Lt - 1; l >= 0; --l) {
-    mg_prolong<T, DIM>(op.lv[l], op.lv[l + 1], w.e[l][ecur[l]], w.e[l + 1][ecur[l + 1]], t.g, t.S,
-                       t.bvs, t.col);
+  // every CTA: restriction into its shared-memory level Ls, coarse cycle there
+  {
+    const int l = Ls - 1;
+    mg_restrict<T, DIM, KAPPA>(op.lv[l], op.lv[Ls], w.e[l][ecur[l]], w.f[l], sm.f[Ls], sm.e[Ls][0], t.tid,
+                               t.NT, t.bvs, t.col, (Ls == L - 1) ? T(1) : omega);
+    ecur[Ls] = 0;
+    __syncthreads();
+    for (int c = Ls; c < L - 1; ++c) {
+      for (int s = 1; s < nu; ++s) {
+        mg_sweep<T, DIM, KAPPA>(op.lv[c], sm.e[c][ecur[c] ^ 1], sm.e[c][ecur[c]], sm.f[c], t.tid, t.NT,
+                                t.bvs, t.col, omega, (const T*)nullptr, rz);
+        ecur[c] ^= 1;
+        __syncthreads();
+      }
+      mg_restrict<T, DIM, KAPPA>(op.lv[c], op.lv[c + 1], sm.e[c][ecur[c]], sm.f[c], sm.f[c + 1],
+                                 sm.e[c + 1][0], t.tid, t.NT, t.bvs, t.col, (c + 1 == L - 1) ? T(1) : omega);
+      ecur[c + 1] = 0;
+      __syncthreads();
+    }
+    for (int c = L - 2; c >= Ls; --c) {
+      mg_prolong<T, DIM>(op.lv[c], op.lv[c + 1], sm.e[c][ecur[c]], sm.e[c + 1][ecur[c + 1]], t.tid, t.NT,
+                         t.bvs, t.col);
+      __syncthreads();
+      for (int s = 0; s < nu; ++s) {
+        mg_sweep<T, DIM, KAPPA>(op.lv[c], sm.e[c][ecur[c] ^ 1], sm.e[c][ecur[c]], sm.f[c], t.tid, t.NT,
+                                t.bvs, t.col, omega, (const T*)nullptr, rz);
+        ecur[c] ^= 1;
+        __syncthreads();
+      }
+    }
+  }
+  // up: prolongation from the CTA's own shared-memory level Ls, then the team levels
+  for (int l = Ls - 1; l >= 0; --l) {
+    if (l == Ls - 1) {
+      // out of place: other CTAs may still be restricting from e[l][ecur]
+      mg_prolong<T, DIM>(op.lv[l], op.lv[l + 1], w.e[l][ecur[l] ^ 1], sm.e[Ls][ecur[Ls]], t.g, t.S, t.bvs,
+                         t.col, w.e[l][ecur[l]]);
+      ecur[l] ^= 1;
+    } else {
+      mg_prolong<T, DIM>(op.lv[l], op.lv[l + 1], w.e[l][ecur[l]], w.e[l + 1][ecur[l + 1]], t.g, t.S, t.bvs,
+                         t.col);
+    }
     team_sync(t);
     for (int s = 0; s < nu; ++s) {
       const bool last = (l == 0 && s == nu - 1);
@@ -113,16 +144,6 @@ __device__ int vcycle(const Team& t, const Op& op, const WSV<T>& w, T omega, int
       team_sync(t);
     }
   }
-  if (Lt == 0) {
-    // every level was worked by rank 0 (C == 1 teams): r.z from level 0 sweeps
-    // is accumulated here over the whole CTA
-    double acc = 0.0;
-    const int items = op.lv[0].N << t.bvs;
-    const T* z = w.e[0][ecur[0]];
-    for (int it = t.g; it < items; it += t.S) acc += (double)(w.f[0][it] * z[it]);
-    contribute(t, SL_RZ, acc);
-    team_sync(t);
-  }
   return ecur[0];
 }
 
@@ -131,7 +152,8 @@ __device__ int vcycle(const Team& t, const Op& op, const WSV<T>& w, T omega, int
 // thread's column is already converged. Updates xt (+= alpha p; = alpha p on
 // the first iteration if zero_init).
 template <typename T, typename TX, int DIM, bool KAPPA>
-__device__ void pcg_iterate(const Team& t, const Op& op, const WSV<T>& w, TX* xt, bool zero_init,
+__device__ void pcg_iterate(const Team& t, const Op& op, const WSV<T>& w, const SmemLv<T>& sm, TX* xt,
+                            bool zero_init,
                             double tol2bb, bool& done, const SolveCfg& cfg, T omega, T scale0,
                             Ctr& ctr, double& rr_last) {
   const OpLevel& l0 = op.lv[0];
@@ -140,7 +162,7 @@ __device__ void pcg_iterate(const Team& t, const Op& op, const WSV<T>& w, TX* xt
   double rz_old = 0.0;
   bool all = __syncthreads_and(done);
   while (!all) {
-    const int zc = vcycle<T, DIM, KAPPA>(t, op, w, omega, cfg.nu);
+    const int zc = vcycle<T, DIM, KAPPA>(t, op, w, sm, omega, cfg.nu);
     const T* z = w.e[0][zc];
     const double rz = total(t, SL_RZ);
     const T beta = (T)((it_count == 0 || done || !(rz_old > 0.0)) ? 0.0 : rz / rz_old);
@@ -182,9 +204,7 @@ __device__ void pcg_iterate(const Team& t, const Op& op, const WSV<T>& w, TX* xt
       const T rv = w.f[0][it] - alpha * w.q[it];
       w.f[0][it] = rv;
       rr += (double)(rv * rv);
-      int i0, i1, i2;
-      decomp<DIM>(l0, p, i0, i1, i2);
-      const T e = scale0 * rv / diag_at<T, DIM, KAPPA>(l0, p, i0, i1, i2);
+      const T e = scale0 * rv * dinv_at<T, KAPPA>(l0, p);
       w.e[0][0][it] = e;
       if (op.L == 1) rz1 += (double)(rv * e);
     }
@@ -223,8 +243,8 @@ __device__ __forceinline__ double rhs_at(const SweepParams& P, const Team& t, co
 // index (in w.dbuf) of the solution buffer X1.
 template <int DIM, bool KAPPA>
 __device__ double* solve_fp64(const Team& t, const SweepParams& P, const Op& op,
-                              const WSV<double>& w, const double* bsrc, const double* dsrc,
-                              const double* x0, double* X1, Ctr& ctr) {
+                              const WSV<double>& w, const SmemLv<double>& sm, const double* bsrc,
+                              const double* dsrc, const double* x0, double* X1, Ctr& ctr) {
   const OpLevel& l0 = op.lv[0];
   const int items = l0.N << t.bvs;
   const double omega = P.cfg.omega;
@@ -237,14 +257,11 @@ __device__ double* solve_fp64(const Team& t, const SweepParams& P, const Op& op,
     decomp<DIM>(l0, p, i0, i1, i2);
     const double bp = rhs_at(P, t, bsrc, dsrc, p, it);
     double d, ax = 0.0;
-    if (x0)
-      ax = op_at<double, DIM, KAPPA>(l0, ld, p, i0, i1, i2, d);
-    else
-      d = diag_at<double, DIM, KAPPA>(l0, p, i0, i1, i2);
+    if (x0) ax = op_at<double, DIM, KAPPA>(l0, ld, p, i0, i1, i2, d);
     const double rv = bp - ax;
     w.f[0][it] = rv;
     X1[it] = x0 ? x0[it] : 0.0;
-    const double e = scale0 * rv / d;
+    const double e = scale0 * rv * dinv_at<double, KAPPA>(l0, p);
     w.e[0][0][it] = e;
     rr += rv * rv;
     bb += bp * bp;
@@ -266,7 +283,7 @@ __device__ double* solve_fp64(const Team& t, const SweepParams& P, const Op& op,
     done = true;
   }
   double rr_last = rrt;
-  pcg_iterate<double, double, DIM, KAPPA>(t, op, w, X1, false, tol2bb, done, P.cfg, omega,
+  pcg_iterate<double, double, DIM, KAPPA>(t, op, w, sm, X1, false, tol2bb, done, P.cfg, omega,
                                           scale0, ctr, rr_last);
   ctr.max_res = fmax(ctr.max_res, bbt > 0.0 ? sqrt(rr_last / bbt) : 0.0);
   ctr.solves += 1;
@@ -274,10 +291,17 @@ __device__ double* solve_fp64(const Team& t, const SweepParams& P, const Op& op,
 }
 
 // Solve (I + c L) x = b by FP64 iterative refinement around FP32 MG-PCG.
+// Each FP32 inner problem is scaled by an exact power of two chosen so that
+// its entries are O(1): deep in a sweep the state has decayed by many orders
+// and the refinement residual by more, and unscaled FP32 products of such
+// values underflow. The scale of refinement k is predicted from the residual
+// of refinement k-1 (the inner solve reduces it by about inner_rtol); that of
+// the first refinement from the previous solve's right-hand side.
 template <int DIM, bool KAPPA>
 __device__ double* solve_mixed(const Team& t, const SweepParams& P, const Op& op,
-                               const WSV<float>& w, const double* bsrc, const double* dsrc,
-                               const double* x0, double* X1, double* X2, Ctr& ctr) {
+                               const WSV<float>& w, const SmemLv<float>& sm, const double* bsrc,
+                               const double* dsrc, const double* x0, double* X1, double* X2,
+                               Ctr& ctr) {
   const OpLevel& l0 = op.lv[0];
   const int items = l0.N << t.bvs;
   const float omega = (float)P.cfg.omega;
@@ -288,10 +312,13 @@ __device__ double* solve_mixed(const Team& t, const SweepParams& P, const Op& op
   bool done = false;
   double bbt = 0.0;
   int ref = 0;
+  const double inv_n = 1.0 / (double)l0.N;
+  double sc = ctr.mix_scale;  // scale of the float residual written in this refinement
+  double inv_sc_c = 1.0;      // 1 / scale of the current inner correction c
   for (;; ++ref) {
     const bool first = (ref == 0);
     double rr = 0.0, bb = 0.0, rz1 = 0.0;
-    LdSum<float> ls{xa, first ? (const float*)nullptr : w.c, t.bvs, t.col};
+    LdSum<float> ls{xa, first ? (const float*)nullptr : w.c, t.bvs, t.col, inv_sc_c};
     for (int it = t.g; it < items; it += t.S) {
       const int p = it >> t.bvs;
       int i0, i1, i2;
@@ -309,9 +336,9 @@ __device__ double* solve_mixed(const Team& t, const SweepParams& P, const Op& op
         ax = op_at<double, DIM, KAPPA>(l0, ls, p, i0, i1, i2, d);
       const double rd = bp - ax;
       tgt[it] = ls(p);
-      const float rf = (float)rd;
+      const float rf = (float)(rd * sc);
       w.f[0][it] = rf;
-      const float e = scale0 * rf / diag_at<float, DIM, KAPPA>(l0, p, i0, i1, i2);
+      const float e = scale0 * rf * dinv_at<float, KAPPA>(l0, p);
       w.e[0][0][it] = e;
       rr += rd * rd;
       if (op.L == 1) rz1 += (double)(rf * e);
@@ -327,6 +354,7 @@ __device__ double* solve_mixed(const Team& t, const SweepParams& P, const Op& op
         for (int it = t.g; it < items; it += t.S) tgt[it] = 0.0;
         done = true;
       }
+      ctr.mix_scale = pow2_inv(sqrt(bbt * inv_n));
     }
     if (!isfinite(rrt)) {
       ctr.status |= STAT_NONFINITE;
@@ -341,14 +369,16 @@ __device__ double* solve_mixed(const Team& t, const SweepParams& P, const Op& op
       break;
     }
     bool idone = done;
-    const double itol2 = P.cfg.inner_rtol * P.cfg.inner_rtol * rrt;
-    double rr_in = rrt;
-    pcg_iterate<float, float, DIM, KAPPA>(t, op, w, w.c, true, itol2, idone, P.cfg, omega, scale0,
+    const double itol2 = P.cfg.inner_rtol * P.cfg.inner_rtol * rrt * sc * sc;
+    double rr_in = rrt * sc * sc;
+    pcg_iterate<float, float, DIM, KAPPA>(t, op, w, sm, w.c, true, itol2, idone, P.cfg, omega, scale0,
                                           ctr, rr_in);
     xa = tgt;
     double* tmp = tgt;
     tgt = oth;
     oth = tmp;
+    inv_sc_c = 1.0 / sc;
+    sc = pow2_inv(P.cfg.inner_rtol * sqrt(rrt * inv_n));
   }
   ctr.refines += ref;
   ctr.refine_max = max(ctr.refine_max, ref);
@@ -358,16 +388,16 @@ __device__ double* solve_mixed(const Team& t, const SweepParams& P, const Op& op
 
 template <typename T, int DIM, bool MIXED>
 __device__ __forceinline__ double* solve_any(const Team& t, const SweepParams& P, const Op& op,
-                                             const WSV<T>& w, const double* bsrc,
+                                             const WSV<T>& w, const SmemLv<T>& sm, const double* bsrc,
                                              const double* dsrc, const double* x0, double* X1,
                                              double* X2, Ctr& ctr) {
   if constexpr (MIXED) {
     if (op.has_kappa)
-      return solve_mixed<DIM, true>(t, P, op, w, bsrc, dsrc, x0, X1, X2, ctr);
-    return solve_mixed<DIM, false>(t, P, op, w, bsrc, dsrc, x0, X1, X2, ctr);
+      return solve_mixed<DIM, true>(t, P, op, w, sm, bsrc, dsrc, x0, X1, X2, ctr);
+    return solve_mixed<DIM, false>(t, P, op, w, sm, bsrc, dsrc, x0, X1, X2, ctr);
   } else {
-    if (op.has_kappa) return solve_fp64<DIM, true>(t, P, op, w, bsrc, dsrc, x0, X1, ctr);
-    return solve_fp64<DIM, false>(t, P, op, w, bsrc, dsrc, x0, X1, ctr);
+    if (op.has_kappa) return solve_fp64<DIM, true>(t, P, op, w, sm, bsrc, dsrc, x0, X1, ctr);
+    return solve_fp64<DIM, false>(t, P, op, w, sm, bsrc, dsrc, x0, X1, ctr);
   }
 }
 
@@ -377,8 +407,9 @@ __device__ __forceinline__ int buf_index(const double* const* b, const double* x
 
 template <typename T, int DIM, bool MIXED>
 __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
-  __shared__ double s_red[NSLOT * LRP_MAXBV];
+  __shared__ double s_red[2 * NSLOT * LRP_MAXBV];
   __shared__ double s_redw[32 * LRP_MAXBV];
+  extern __shared__ __align__(16) unsigned char s_dyn[];
   Team t;
   t.C = P.C;
   t.rank = (P.C > 1) ? (int)cg::this_cluster().block_rank() : 0;
@@ -391,6 +422,7 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
   t.col = t.g & (P.BV - 1);
   t.red = s_red;
   t.redw = s_redw;
+  t.phase = 0;
   const int team = blockIdx.x / P.C;
   char* base = P.ws + (size_t)team * P.team_bytes;
   WSV<T> w;
@@ -408,6 +440,16 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
     w.e[l][0] = (T*)(base + P.off_e[l][0]);
     w.e[l][1] = (T*)(base + P.off_e[l][1]);
     w.f[l] = (T*)(base + P.off_f[l]);
+  }
+  if (P.poison) {
+    for (size_t i = t.tid; i < P.smem_bytes / sizeof(T); i += t.NT) ((T*)s_dyn)[i] = T(NAN);
+    __syncthreads();
+  }
+  SmemLv<T> sm;
+  for (int l = 0; l < LRP_MAXLEV; ++l) {
+    sm.e[l][0] = (T*)(s_dyn + P.smem_off[l][0]);
+    sm.e[l][1] = (T*)(s_dyn + P.smem_off[l][1]);
+    sm.f[l] = (T*)(s_dyn + P.smem_off[l][2]);
   }
   const int gcol = team * P.BV + t.col;
   const bool valid = gcol < P.nvec;
@@ -434,7 +476,7 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
   if (P.stages & ST_PRIOR_IN) {
     double* X1 = w.dbuf[(cur + 1) % 3];
     double* X2 = w.dbuf[(cur + 2) % 3];
-    double* res = solve_any<T, DIM, MIXED>(t, P, P.prior, w, w.dbuf[cur], nullptr, nullptr, X1,
+    double* res = solve_any<T, DIM, MIXED>(t, P, P.prior, w, sm, w.dbuf[cur], nullptr, nullptr, X1,
                                            X2, ctr);
     cur = buf_index(w.dbuf, res);
   }
@@ -442,7 +484,7 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
     for (int n = P.t_begin + 1; n <= P.t_end; ++n) {
       double* X1 = w.dbuf[(cur + 1) % 3];
       double* X2 = w.dbuf[(cur + 2) % 3];
-      double* res = solve_any<T, DIM, MIXED>(t, P, P.step, w, w.dbuf[cur], nullptr, w.dbuf[cur],
+      double* res = solve_any<T, DIM, MIXED>(t, P, P.step, w, sm, w.dbuf[cur], nullptr, w.dbuf[cur],
                                              X1, X2, ctr);
       cur = buf_index(w.dbuf, res);
       // fused observation d_n = B y_n (/ sigma^2 for the Hessian); no barrier
@@ -471,6 +513,11 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
       }
     }
   }
+  if (P.stages & ST_FORWARD) {
+    // the last observation phase has no barrier of its own: the adjoint
+    // source reads those values next
+    team_sync(t);
+  }
   if (P.stages & ST_ADJOINT) {
     const double* q = nullptr;  // q_{nt+1} = 0
     for (int n = P.adj_begin; n >= 1; --n) {
@@ -480,7 +527,7 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
       const int qi = q ? buf_index(w.dbuf, q) : cur;
       double* X1 = w.dbuf[(qi + 1) % 3];
       double* X2 = w.dbuf[(qi + 2) % 3];
-      double* res = solve_any<T, DIM, MIXED>(t, P, P.step, w, q, dsrc, q, X1, X2, ctr);
+      double* res = solve_any<T, DIM, MIXED>(t, P, P.step, w, sm, q, dsrc, q, X1, X2, ctr);
       q = res;
     }
     if (q) {
@@ -493,7 +540,7 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
   if (P.stages & ST_PRIOR_OUT) {
     double* X1 = w.dbuf[(cur + 1) % 3];
     double* X2 = w.dbuf[(cur + 2) % 3];
-    double* res = solve_any<T, DIM, MIXED>(t, P, P.prior, w, w.dbuf[cur], nullptr, nullptr, X1,
+    double* res = solve_any<T, DIM, MIXED>(t, P, P.prior, w, sm, w.dbuf[cur], nullptr, nullptr, X1,
                                            X2, ctr);
     cur = buf_index(w.dbuf, res);
   }
@@ -517,20 +564,26 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
 }
 
 template <typename T, int DIM, bool MIXED>
+static cudaError_t prepare_sweep(size_t smem) {
+  auto kern = sweep_kernel<T, DIM, MIXED>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <typename T, int DIM, bool MIXED>
 cudaError_t launch_sweep(const SweepParams& prm, cudaStream_t stream) {
   auto kern = sweep_kernel<T, DIM, MIXED>;
+  cudaError_t e = prepare_sweep<T, DIM, MIXED>(prm.smem_bytes);
+  if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(prm.n_teams * prm.C);
   cfg.blockDim = dim3(prm.NT);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = prm.smem_bytes;
   cfg.stream = stream;
   cudaLaunchAttribute attr[1];
   int na = 0;
   if (prm.C > 1) {
-    if (prm.C > 8) {
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-      if (e != cudaSuccess) return e;
-    }
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = prm.C;
     attr[0].val.clusterDim.y = 1;
@@ -540,6 +593,43 @@ cudaError_t launch_sweep(const SweepParams& prm, cudaStream_t stream) {
   cfg.attrs = attr;
   cfg.numAttrs = na;
   return cudaLaunchKernelEx(&cfg, kern, prm);
+}
+
+// How many teams of C CTAs (NT threads, smem dynamic bytes each) can be
+// resident at once: the sweep keeps every team resident for its whole
+// lifetime, so a launch with more teams than this runs in waves.
+template <typename T, int DIM, bool MIXED>
+int max_resident_teams(int C, int NT, size_t smem, int sm_count) {
+  auto kern = sweep_kernel<T, DIM, MIXED>;
+  if (prepare_sweep<T, DIM, MIXED>(smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (C == 1) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    return per_sm * sm_count;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C * 64);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
 }
 
 }  // namespace lrp

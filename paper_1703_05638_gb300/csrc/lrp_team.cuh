@@ -25,8 +25,13 @@ enum { SL_RR = 0, SL_BB = 1, SL_RZ = 2, SL_PQ = 3, SL_RRD = 4, SL_BBD = 5, NSLOT
 
 struct Team {
   int C, rank, NT, tid, g, S, BV, bvs, col;
-  double* red;   // [NSLOT][LRP_MAXBV] CTA totals (shared memory)
+  double* red;   // [2][NSLOT][LRP_MAXBV] CTA totals, two banks (shared memory)
   double* redw;  // [32][LRP_MAXBV] warp partials (shared memory)
+  // Team barriers passed so far (identical in every thread of the team).
+  // A total is contributed before barrier k into bank k&1 and read after it;
+  // its bank is next written before barrier k+2, which no CTA reaches before
+  // every CTA has finished reading it (the reads precede barrier k+1).
+  mutable unsigned phase;
 };
 
 __device__ __forceinline__ void team_sync(const Team& t) {
@@ -35,6 +40,7 @@ __device__ __forceinline__ void team_sync(const Team& t) {
   } else {
     __syncthreads();
   }
+  ++t.phase;
 }
 
 // Sum v over the CTA per column (lanes with equal col), store the CTA total
@@ -48,7 +54,7 @@ __device__ __forceinline__ void contribute(const Team& t, int slot, double v) {
     double s = 0.0;
     const int nw = t.NT >> 5;
     for (int i = 0; i < nw; ++i) s += t.redw[i * LRP_MAXBV + t.tid];
-    t.red[slot * LRP_MAXBV + t.tid] = s;
+    t.red[((t.phase & 1) * NSLOT + slot) * LRP_MAXBV + t.tid] = s;
   }
   __syncthreads();
 }
@@ -57,7 +63,7 @@ __device__ __forceinline__ void contribute(const Team& t, int slot, double v) {
 // that followed the contribute. Every CTA sums the ranks in the same order,
 // so all CTAs obtain bit-identical totals (and take identical branches).
 __device__ __forceinline__ double total(const Team& t, int slot) {
-  const int idx = slot * LRP_MAXBV + t.col;
+  const int idx = (((t.phase - 1) & 1) * NSLOT + slot) * LRP_MAXBV + t.col;
   if (t.C == 1) return t.red[idx];
   cg::cluster_group cl = cg::this_cluster();
   double s = 0.0;
@@ -98,16 +104,18 @@ struct Ld {
   __device__ __forceinline__ T operator()(int q) const { return v[(q << bvs) + col]; }
 };
 
-// Loader of (x + c) for the refinement residual (x double, c inner type).
+// Loader of (x + c * c_scale) for the refinement residual (x double, c the
+// inner correction in the inner type, c_scale undoing its power-of-two scale).
 template <typename TI>
 struct LdSum {
   const double* x;  // may be NULL (zero)
   const TI* c;      // may be NULL (zero)
   int bvs, col;
+  double c_scale;
   __device__ __forceinline__ double operator()(int q) const {
     const int i = (q << bvs) + col;
     double s = x ? x[i] : 0.0;
-    if (c) s += (double)c[i];
+    if (c) s += (double)c[i] * c_scale;
     return s;
   }
 };
@@ -149,6 +157,18 @@ __device__ __forceinline__ T op_at(const OpLevel& lv, const LD& ld, int p, int i
   return diag * ld(p) - ch2 * s;
 }
 
+// 1 / diagonal of (I + c L) at node p (precomputed; no division in the kernel)
+template <typename T, bool KAPPA>
+__device__ __forceinline__ T dinv_at(const OpLevel& lv, int p);
+template <>
+__device__ __forceinline__ double dinv_at<double, true>(const OpLevel& lv, int p) { return lv.dinvd[p]; }
+template <>
+__device__ __forceinline__ float dinv_at<float, true>(const OpLevel& lv, int p) { return lv.dinvf[p]; }
+template <>
+__device__ __forceinline__ double dinv_at<double, false>(const OpLevel& lv, int) { return lv.dinv; }
+template <>
+__device__ __forceinline__ float dinv_at<float, false>(const OpLevel& lv, int) { return (float)lv.dinv; }
+
 template <typename T, int DIM, bool KAPPA>
 __device__ __forceinline__ T diag_at(const OpLevel& lv, int p, int i0, int i1, int i2) {
   const int n = lv.n;
@@ -171,15 +191,18 @@ __device__ __forceinline__ T diag_at(const OpLevel& lv, int p, int i0, int i1, i
 
 // ---------------------------------------------------------------------------
 // Multigrid phases. Each works over items [start, N*BV) with the given
-// stride; the caller ends the phase with a team barrier (team levels) or
-// __syncthreads (levels worked by CTA rank 0 alone).
+// stride; the caller ends the phase with a team barrier (global levels) or
+// __syncthreads (shared-memory levels). The vectors are written by other
+// phases of the same launch, so their pointers must not be declared
+// __restrict__ read-only: that would allow the non-coherent read-only load
+// path, which can return stale lines.
 
 // One damped Jacobi sweep e_out = e_in + omega (f - A e_in) / d. If rz_r is
 // non-NULL, accumulates rz_r * e_out into rz (used for r.z after the last
 // post-smoothing sweep on the finest level).
 template <typename T, int DIM, bool KAPPA>
-__device__ __forceinline__ void mg_sweep(const OpLevel& lv, T* __restrict__ eo,
-                                         const T* __restrict__ ei, const T* __restrict__ f,
+__device__ __forceinline__ void mg_sweep(const OpLevel& lv, T* eo,
+                                         const T* ei, const T* f,
                                          int start, int stride, int bvs, int col, T omega,
                                          const T* rz_r, double& rz) {
   const int items = lv.N << bvs;
@@ -190,7 +213,7 @@ __device__ __forceinline__ void mg_sweep(const OpLevel& lv, T* __restrict__ eo,
     decomp<DIM>(lv, p, i0, i1, i2);
     T d;
     const T ae = op_at<T, DIM, KAPPA>(lv, ld, p, i0, i1, i2, d);
-    const T e = ei[it] + omega * (f[it] - ae) / d;
+    const T e = ei[it] + omega * (f[it] - ae) * dinv_at<T, KAPPA>(lv, p);
     eo[it] = e;
     if (rz_r) rz += (double)(rz_r[it] * e);
   }
@@ -201,8 +224,8 @@ __device__ __forceinline__ void mg_sweep(const OpLevel& lv, T* __restrict__ eo,
 // (scale = omega, or 1 on the single-node coarsest level: exact solve).
 template <typename T, int DIM, bool KAPPA>
 __device__ __forceinline__ void mg_restrict(const OpLevel& lf, const OpLevel& lc,
-                                            const T* __restrict__ ef, const T* __restrict__ ff,
-                                            T* __restrict__ fc, T* __restrict__ ec, int start,
+                                            const T* ef, const T* ff,
+                                            T* fc, T* ec, int start,
                                             int stride, int bvs, int col, T scale) {
   const int items = lc.N << bvs;
   Ld<T> ld{ef, bvs, col};
@@ -228,15 +251,16 @@ __device__ __forceinline__ void mg_restrict(const OpLevel& lf, const OpLevel& lc
       }
     }
     fc[it] = acc;
-    ec[it] = scale * acc / diag_at<T, DIM, KAPPA>(lc, P, c0, c1, c2);
+    ec[it] = scale * acc * dinv_at<T, KAPPA>(lc, P);
   }
 }
 
-// e_f += P e_c (bi/trilinear interpolation, zero boundary).
+// e_out = e_in + P e_c (bi/trilinear interpolation, zero boundary); e_out
+// may equal e_in (in place).
 template <typename T, int DIM>
-__device__ __forceinline__ void mg_prolong(const OpLevel& lf, const OpLevel& lc,
-                                           T* __restrict__ ef, const T* __restrict__ ec,
-                                           int start, int stride, int bvs, int col) {
+__device__ __forceinline__ void mg_prolong(const OpLevel& lf, const OpLevel& lc, T* ef,
+                                           const T* ec, int start, int stride, int bvs,
+                                           int col, const T* ein = nullptr) {
   const int items = lf.N << bvs;
   const int nc = lc.n;
   for (int it = start; it < items; it += stride) {
@@ -269,7 +293,7 @@ __device__ __forceinline__ void mg_prolong(const OpLevel& lf, const OpLevel& lc,
         }
       }
     }
-    ef[it] += acc;
+    ef[it] = (ein ? ein[it] : ef[it]) + acc;
   }
 }
 
