@@ -171,6 +171,26 @@ lrp_status lrp_problem_sizes(const lrp_problem* p, int* nx, int* n_obs, int* n_s
 lrp_status lrp_hessian_apply(lrp_problem* p, int nvec, const double* X, int ldx,
                              double* Y, int ldy, unsigned flags, lrp_apply_stats* st);
 
+/* Allocation-free variant of lrp_hessian_apply (the paper has no
+ * counterpart; this is an interface for callers that cannot allocate device
+ * memory while they run, e.g. a process whose device memory is reserved up
+ * front by another allocator, or a loop where a cudaMalloc would synchronise
+ * the device). Computes Y = Htilde X exactly as lrp_hessian_apply does, but
+ * the solver workspace is a fixed 64 MiB array in device memory that the
+ * library holds on every GPU that loads it until the process exits; the call
+ * makes no cudaMalloc or cudaFree. X and Y must be device arrays (host arrays
+ * are rejected: staging them would allocate). A call whose workspace would
+ * exceed 64 MiB (it grows with nvec, the grid and the number of observations)
+ * returns LRP_EINVAL with the required size in lrp_last_error(); split the
+ * columns into smaller calls. The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture. All calls share the one
+ * array, so calls that overlap on the GPU (different threads or streams,
+ * any problems) race: serialise them. The array keeps the previous call's
+ * contents; nothing in the computation reads it before writing it. */
+lrp_status lrp_hessian_apply_noalloc(lrp_problem* p, int nvec, const double* X, int ldx,
+                                     double* Y, int ldy, lrp_apply_stats* st);
+
 /* D = F U (no noise weighting): forward sweep and observation.
  * U: nx x nvec, D: n_data x nvec. */
 lrp_status lrp_forward_observe(lrp_problem* p, int nvec, const double* U, int ldu,

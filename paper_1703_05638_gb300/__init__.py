@@ -74,6 +74,8 @@ EXPORTS = {
     "lrp_problem_sizes": (C.c_int, [C.c_void_p, _ip, _ip, _ip, _ip]),
     "lrp_hessian_apply": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_uint,
                                     C.POINTER(lrp_apply_stats)]),
+    "lrp_hessian_apply_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int,
+                                            C.POINTER(lrp_apply_stats)]),
     "lrp_forward_observe": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int,
                                       C.POINTER(lrp_apply_stats)]),
     "lrp_adjoint": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int,
@@ -234,6 +236,16 @@ def _sweep(fn, prob: Problem, X, rows_in, rows_out, *extra):
 def lrp_hessian_apply(prob: Problem, X, flags: int = 0):
     """Y = Htilde X (or H_mis X with LRP_MISFIT_ONLY). Returns (Y, stats)."""
     return _sweep(load().lrp_hessian_apply, prob, X, prob.nx, prob.nx, C.c_uint(flags))
+
+
+def lrp_hessian_apply_noalloc(prob: Problem, X):
+    """Y = Htilde X with the library's fixed workspace (no device allocation
+    by the call). X must be a CUDA torch tensor (nx, ncols); returns (Y, stats)
+    with Y a CUDA tensor. The output tensor is allocated here, by the caller
+    side, not by the library."""
+    if not _is_torch(X) or not X.is_cuda:
+        raise ValueError("lrp_hessian_apply_noalloc needs a CUDA tensor")
+    return _sweep(load().lrp_hessian_apply_noalloc, prob, X, prob.nx, prob.nx)
 
 
 def lrp_forward_observe(prob: Problem, U):

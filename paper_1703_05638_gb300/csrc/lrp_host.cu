@@ -222,6 +222,8 @@ lrp_status lrp_setup_problem(const lrp_problem_desc* desc, void* cuda_stream, lr
     const char* pz = std::getenv("LRP_POISON");  // byte value to fill new workspace with (1 -> 0xFF)
     P->poison = pz ? (std::atoi(pz) == 1 ? 0xFF : (std::atoi(pz) | 0x100)) : 0;
   }
+  P->ws_fixed = nullptr;
+  P->ws_fixed_bytes = 0;
   auto fail = [&](lrp_status s) {
     lrp_problem_destroy(P);
     return s;

@@ -165,6 +165,10 @@ struct lrp_problem {
   // tuned launch parameters
   int team_ctas, team_cols, nthreads, coarse_items, smem_cap;
   int poison;  // LRP_POISON set: new workspace and shared memory start as NaN
+  // caller-provided sweep workspace (set only for the duration of an
+  // allocation-free call; NULL otherwise)
+  char* ws_fixed;
+  size_t ws_fixed_bytes;
   lrp::SolveCfg cfg;
   uint64_t hash;
   // sweep-kernel ledger (lrp_sweep_profile): CUDA-event time and algorithmic

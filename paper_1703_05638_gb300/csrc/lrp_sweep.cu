@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cstring>
+#include <string>
 
 #include "lrp_internal.h"
 
@@ -103,9 +104,18 @@ lrp_status run_sweep_ex(lrp_problem* Pr, unsigned stages, int nvec, const double
     off = align_up(off + Nl * BV * tsz);
   }
   prm.team_bytes = off;
-  lrp_status s = ensure_workspace(Pr, off * n_teams);
-  if (s != LRP_OK) return s;
-  prm.ws = Pr->ws;
+  if (Pr->ws_fixed) {
+    if (off * n_teams > Pr->ws_fixed_bytes) {
+      set_error("the fixed workspace holds " + std::to_string(Pr->ws_fixed_bytes) + " bytes; this call needs " +
+                std::to_string(off * n_teams));
+      return LRP_EINVAL;
+    }
+    prm.ws = Pr->ws_fixed;
+  } else {
+    lrp_status s = ensure_workspace(Pr, off * n_teams);
+    if (s != LRP_OK) return s;
+    prm.ws = Pr->ws;
+  }
   prm.step = Pr->step;
   prm.prior = Pr->prior;
   // coarse levels solved redundantly in every CTA's shared memory: the first
