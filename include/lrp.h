@@ -100,10 +100,15 @@ typedef struct {
   /* tuning (0 -> autotuned or default) */
   int team_ctas;            /* CTAs per thread-block cluster working on one column group */
   int team_cols;            /* columns per cluster: 1, 2, 4, 8 or 16 */
-  int mg_nu;                /* Jacobi sweeps before and after each coarse correction */
+  int mg_nu;                /* Jacobi sweeps before and after the coarse correction (finest level) */
   double inner_rtol;        /* LRP_MIXED: FP32 inner relative tolerance (0 -> 1e-4) */
   int coarse_items;         /* multigrid levels with at most this many points x columns are
                                solved by every CTA of a team in shared memory (0 -> 1024) */
+  int kernel_variant;       /* 0 auto; 1 the generic sweep kernel; 2 the band kernel (2D, kappa = 1,
+                               LRP_MIXED, team_cols 1: each CTA keeps its band of rows of the finest
+                               grid in shared memory), LRP_EINVAL if it does not apply */
+  int mg_nu_coarse;         /* Jacobi sweeps before and after on the coarser levels of the band
+                               kernel (0 -> mg_nu) */
 } lrp_problem_desc;
 
 typedef struct {
@@ -190,6 +195,14 @@ lrp_status lrp_hessian_apply(lrp_problem* p, int nvec, const double* X, int ldx,
  * contents; nothing in the computation reads it before writing it. */
 lrp_status lrp_hessian_apply_noalloc(lrp_problem* p, int nvec, const double* X, int ldx,
                                      double* Y, int ldy, lrp_apply_stats* st);
+
+/* Autotuner: for blocks of nvec columns, times a short forward sweep (steps
+ * implicit-Euler steps, 0 -> 4) for each candidate cluster size, columns per
+ * cluster, smoothing sweeps and (LRP_MIXED) inner tolerance, and keeps the
+ * fastest in the problem handle for later calls. All candidates iterate to
+ * the same tolerances. *best_ms (may be NULL) receives the winning time.
+ * Allocates a temporary nx x nvec block. No counterpart in the paper. */
+lrp_status lrp_autotune(lrp_problem* p, int nvec, int steps, double* best_ms);
 
 /* D = F U (no noise weighting): forward sweep and observation.
  * U: nx x nvec, D: n_data x nvec. */

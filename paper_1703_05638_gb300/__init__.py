@@ -39,7 +39,8 @@ class lrp_problem_desc(C.Structure):
                 ("precision", C.c_int), ("time_trunc_tol", C.c_double), ("time_rank_max", C.c_int),
                 ("time_chunk", C.c_int), ("solve_rtol", C.c_double), ("pcg_maxit", C.c_int),
                 ("team_ctas", C.c_int), ("team_cols", C.c_int), ("mg_nu", C.c_int),
-                ("inner_rtol", C.c_double), ("coarse_items", C.c_int)]
+                ("inner_rtol", C.c_double), ("coarse_items", C.c_int), ("kernel_variant", C.c_int),
+                ("mg_nu_coarse", C.c_int)]
 
 
 class lrp_apply_stats(C.Structure):
@@ -76,6 +77,7 @@ EXPORTS = {
                                     C.POINTER(lrp_apply_stats)]),
     "lrp_hessian_apply_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int,
                                             C.POINTER(lrp_apply_stats)]),
+    "lrp_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _dp]),
     "lrp_forward_observe": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int,
                                       C.POINTER(lrp_apply_stats)]),
     "lrp_adjoint": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int,
@@ -246,6 +248,14 @@ def lrp_hessian_apply_noalloc(prob: Problem, X):
     if not _is_torch(X) or not X.is_cuda:
         raise ValueError("lrp_hessian_apply_noalloc needs a CUDA tensor")
     return _sweep(load().lrp_hessian_apply_noalloc, prob, X, prob.nx, prob.nx)
+
+
+def lrp_autotune(prob: Problem, nvec: int, steps: int = 4) -> float:
+    """Pick the fastest launch shape / multigrid setting for blocks of nvec
+    columns (kept in the problem); returns the winning time in ms."""
+    ms = C.c_double()
+    _check(load().lrp_autotune(prob.handle, int(nvec), int(steps), C.byref(ms)))
+    return ms.value
 
 
 def lrp_forward_observe(prob: Problem, U):

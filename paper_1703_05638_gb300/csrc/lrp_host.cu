@@ -13,6 +13,7 @@
 #include <string>
 #include <vector>
 
+#include "lrp_dense.h"
 #include "lrp_internal.h"
 
 namespace lrp {
@@ -130,6 +131,7 @@ static void default_tuning(lrp_problem* P) {
     P->team_ctas = 1;
   }
   P->coarse_items = d.coarse_items > 0 ? d.coarse_items : 1024;
+  P->kernel_variant = d.kernel_variant;
   P->smem_cap = 160 * 1024;
 }
 
@@ -377,6 +379,7 @@ lrp_status lrp_setup_problem(const lrp_problem_desc* desc, void* cuda_stream, lr
   c.maxit = d.pcg_maxit > 0 ? d.pcg_maxit : 200;
   c.maxref = 30;
   c.nu = d.mg_nu > 0 ? d.mg_nu : 2;
+  c.nu_coarse = d.mg_nu_coarse > 0 ? d.mg_nu_coarse : c.nu;
   c.omega = d.dim == 2 ? 0.8 : 6.0 / 7.0;
   if (P->desc.time_chunk <= 0) P->desc.time_chunk = 32;
   if (P->desc.time_rank_max <= 0) P->desc.time_rank_max = 40;
@@ -553,6 +556,92 @@ static lrp_status hessian_with_factors(lrp_problem* P, int nvec, const double* X
 }  // namespace lrp
 
 extern "C" {
+
+// Autotuner: times a short forward sweep (steps implicit-Euler steps on a
+// pseudo-random block of nvec columns) for each candidate launch shape and
+// multigrid setting and keeps the fastest. Every candidate iterates to the
+// same tolerances, so the choice changes the speed, not the result beyond
+// rounding.
+lrp_status lrp_autotune(lrp_problem* P, int nvec, int steps, double* best_ms) {
+  if (!P || nvec < 1 || nvec > 4096) {
+    set_error("lrp_autotune: invalid argument");
+    return LRP_EINVAL;
+  }
+  cudaSetDevice(P->device);
+  if (steps < 1) steps = 4;
+  steps = std::min(steps, P->nt);
+  double* X = nullptr;
+  cudaError_t e = cudaMalloc(&X, (size_t)P->nx * nvec * sizeof(double));
+  if (e != cudaSuccess) return cuda_status(e, "autotune cudaMalloc");
+  e = fill_random(P->stream, P->nx, nvec, X, P->nx, nullptr, 0xA070ull);
+  if (e != cudaSuccess) {
+    cudaFree(X);
+    return cuda_status(e, "autotune fill");
+  }
+  struct Cand {
+    int C, BV, nu, nuc;
+    double inner;
+  };
+  std::vector<Cand> cands;
+  const bool mixed = P->desc.precision == LRP_MIXED;
+  const int Cs[] = {1, 2, 4, 8, 16};
+  const int BVs[] = {1, 2, 4};
+  for (int C : Cs)
+    for (int BV : BVs) {
+      if (BV > nvec && BV > 1) continue;
+      if (C > 1 && (long long)P->nx / C < 256) continue;
+      for (int nu : {1, 2})
+        for (double inner : (mixed ? std::vector<double>{1e-4, 1e-5} : std::vector<double>{0.0}))
+          cands.push_back({C, BV, nu, nu, inner});
+    }
+  const int save_C = P->team_ctas, save_BV = P->team_cols;
+  const SolveCfg save_cfg = P->cfg;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best = 1e300;
+  Cand bestc = {save_C, save_BV, save_cfg.nu, save_cfg.nu_coarse, save_cfg.inner_rtol};
+  for (const Cand& c : cands) {
+    P->team_ctas = c.C;
+    P->team_cols = c.BV;
+    P->cfg.nu = c.nu;
+    P->cfg.nu_coarse = c.nuc;
+    if (mixed) P->cfg.inner_rtol = c.inner;
+    double ms_run = 1e300;
+    for (int rep = 0; rep < 2; ++rep) {
+      cudaEventRecord(e0, P->stream);
+      lrp_status st = run_sweep_ex(P, ST_LOAD_X | ST_FORWARD, nvec, X, P->nx, nullptr, 0, nullptr, 0, nullptr, 0,
+                                   nullptr, 0, steps, nullptr, 0);
+      cudaEventRecord(e1, P->stream);
+      cudaEventSynchronize(e1);
+      if (st != LRP_OK) {
+        ms_run = 1e300;
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms_run = std::min(ms_run, (double)ms);
+    }
+    if (ms_run < best) {
+      best = ms_run;
+      bestc = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(X);
+  P->team_ctas = bestc.C;
+  P->team_cols = bestc.BV;
+  P->cfg = save_cfg;
+  P->cfg.nu = bestc.nu;
+  P->cfg.nu_coarse = bestc.nuc;
+  if (mixed) P->cfg.inner_rtol = bestc.inner;
+  if (best_ms) *best_ms = best;
+  if (std::getenv("LRP_VERBOSE"))
+    std::fprintf(stderr, "[lrp] autotune nvec=%d: C=%d BV=%d nu=%d inner=%.0e (%.2f ms per %d steps)\n", nvec,
+                 bestc.C, bestc.BV, bestc.nu, bestc.inner, best, steps);
+  return best < 1e300 ? LRP_OK : LRP_ECUDA;
+}
 
 lrp_status lrp_hessian_apply(lrp_problem* P, int nvec, const double* X, int ldx, double* Y, int ldy,
                              unsigned flags, lrp_apply_stats* st) {

@@ -81,7 +81,8 @@ struct SolveCfg {
   double inner_rtol;  // mixed: FP32 inner relative residual
   int maxit;          // PCG iterations per (inner) solve
   int maxref;         // mixed: refinement sweeps
-  int nu;             // Jacobi sweeps pre and post
+  int nu;             // Jacobi sweeps pre and post (finest level)
+  int nu_coarse;      // Jacobi sweeps pre and post on the coarser levels
   double omega;       // Jacobi damping
 };
 
@@ -125,6 +126,8 @@ struct SweepParams {
   size_t off_e[LRP_MAXLEV][2], off_f[LRP_MAXLEV]; // coarse levels (T)
   size_t smem_off[LRP_MAXLEV][3];  // shared-memory coarse levels: e0, e1, f offsets (bytes)
   size_t smem_bytes;
+  int fast_band_len;  // band kernel: floats per band array (halos and padding included)
+  unsigned long long* section_cycles;  // optional section timers (LRP_SECTION_TIMERS builds)
   int poison;         // fill the dynamic shared memory with NaN first (read-before-write check)
   int start_buf;      // index of the buffer that holds the sweep state at launch
   int* end_buf;       // device: buffer index holding the state at exit (per team)
@@ -163,7 +166,7 @@ struct lrp_problem {
   int* end_buf;
   int sm_count;
   // tuned launch parameters
-  int team_ctas, team_cols, nthreads, coarse_items, smem_cap;
+  int team_ctas, team_cols, nthreads, coarse_items, smem_cap, kernel_variant;
   int poison;  // LRP_POISON set: new workspace and shared memory start as NaN
   // caller-provided sweep workspace (set only for the duration of an
   // allocation-free call; NULL otherwise)

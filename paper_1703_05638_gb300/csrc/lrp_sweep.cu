@@ -4,12 +4,15 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cstdio>
 #include <cstring>
 #include <string>
 
 #include "lrp_internal.h"
 
 namespace lrp {
+
+constexpr int FAST_HALO_ROWS = 2;  // halo rows of the band kernel
 
 template <typename T, int DIM, bool MIXED>
 cudaError_t launch_sweep(const SweepParams& prm, cudaStream_t stream);
@@ -23,6 +26,9 @@ extern template int max_resident_teams<double, 2, false>(int, int, size_t, int);
 extern template int max_resident_teams<double, 3, false>(int, int, size_t, int);
 extern template int max_resident_teams<float, 2, true>(int, int, size_t, int);
 extern template int max_resident_teams<float, 3, true>(int, int, size_t, int);
+
+cudaError_t launch_fast2d(const SweepParams& prm, cudaStream_t stream);
+int fast2d_resident_teams(int C, int NT, size_t smem, int sm_count);
 
 static int resident_teams(bool mixed, int dim, int C, int NT, size_t smem, int sm_count) {
   if (dim == 2)
@@ -144,7 +150,40 @@ lrp_status run_sweep_ex(lrp_problem* Pr, unsigned stages, int nvec, const double
   prm.prior.Ls = Ls;
   // team size: the largest C <= the requested one whose teams all stay resident
   int C = Pr->team_ctas;
-  while (C > 1 && resident_teams(mixed, Pr->dim, C, Pr->nthreads, soff, Pr->sm_count) < n_teams) C >>= 1;
+  // Band kernel (2D, kappa = 1, one column per team, FP32 inner): every CTA
+  // keeps its band of the finest level and all coarse levels in shared memory.
+  bool fast = false;
+  if (Pr->kernel_variant != 1 && Pr->dim == 2 && mixed && BV == 1 && !Pr->step.has_kappa && Pr->L >= 2) {
+    const int n = Pr->n;
+    for (int Cf = C; Cf >= 1; Cf >>= 1) {
+      if (n / Cf < FAST_HALO_ROWS) continue;
+      const int rows_max = (n + Cf - 1) / Cf;
+      const int band_len = (rows_max + 2 * FAST_HALO_ROWS) * (n + 1) + 2;
+      size_t bytes = ((size_t)6 * band_len * sizeof(float) + 15) & ~(size_t)15;
+      size_t offs[LRP_MAXLEV][3] = {};
+      for (int l = 1; l < Pr->L; ++l)
+        for (int k = 0; k < 3; ++k) {
+          offs[l][k] = bytes;
+          const size_t nl = Pr->step.lv[l].n;  // padded copy: (n+2) rows of pitch n+1, plus 2
+          bytes += (((nl + 2) * (nl + 1) + 2) * sizeof(float) + 15) & ~(size_t)15;
+        }
+      if (bytes > (size_t)215 * 1024) continue;
+      if (fast2d_resident_teams(Cf, Pr->nthreads, bytes, Pr->sm_count) < n_teams && Cf > 1) continue;
+      fast = true;
+      C = Cf;
+      prm.fast_band_len = band_len;
+      prm.smem_bytes = bytes;
+      for (int l = 0; l < LRP_MAXLEV; ++l)
+        for (int k = 0; k < 3; ++k) prm.smem_off[l][k] = offs[l][k];
+      break;
+    }
+    if (!fast && Pr->kernel_variant == 2) {
+      set_error("the band kernel does not apply to or fit this problem");
+      return LRP_EINVAL;
+    }
+  }
+  if (!fast)
+    while (C > 1 && resident_teams(mixed, Pr->dim, C, Pr->nthreads, soff, Pr->sm_count) < n_teams) C >>= 1;
   prm.dim = Pr->dim;
   prm.nt = Pr->nt;
   prm.t_begin = t_begin;
@@ -183,7 +222,15 @@ lrp_status run_sweep_ex(lrp_problem* Pr, unsigned stages, int nvec, const double
   cudaError_t e = cudaMemsetAsync(Pr->stats, 0, sizeof(Stats), Pr->stream);
   if (e != cudaSuccess) return cuda_status(e, "stats reset");
   if (Pr->prof_on) cudaEventRecord(Pr->prof_ev[0], Pr->stream);
-  if (Pr->dim == 2) {
+#ifdef LRP_SECTION_TIMERS
+  static unsigned long long* sec_buf = nullptr;
+  if (!sec_buf) cudaMalloc(&sec_buf, 8 * sizeof(unsigned long long));
+  cudaMemsetAsync(sec_buf, 0, 8 * sizeof(unsigned long long), Pr->stream);
+  prm.section_cycles = sec_buf;
+#endif
+  if (fast) {
+    e = launch_fast2d(prm, Pr->stream);
+  } else if (Pr->dim == 2) {
     e = mixed ? launch_sweep<float, 2, true>(prm, Pr->stream)
               : launch_sweep<double, 2, false>(prm, Pr->stream);
   } else {
@@ -218,6 +265,14 @@ lrp_status run_sweep_ex(lrp_problem* Pr, unsigned stages, int nvec, const double
     st->max_rel_residual = mr;
     st->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
+#ifdef LRP_SECTION_TIMERS
+  if (fast) {
+    unsigned long long sc[8];
+    cudaMemcpy(sc, prm.section_cycles, sizeof(sc), cudaMemcpyDeviceToHost);
+    std::fprintf(stderr, "[sections] band %.3e sync %.3e coarse %.3e refine %.3e reduce %.3e total %.3e cycles\n",
+                 (double)sc[0], (double)sc[1], (double)sc[2], (double)sc[3], (double)sc[4], (double)sc[7]);
+  }
+#endif
   if (hs.status & STAT_NONFINITE) {
     set_error("non-finite value in a spatial solve");
     return LRP_ENONFINITE;

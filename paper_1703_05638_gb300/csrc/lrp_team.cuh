@@ -50,9 +50,16 @@ __device__ __forceinline__ void contribute(const Team& t, int slot, double v) {
   const int lane = t.tid & 31, w = t.tid >> 5;
   if (lane < t.BV) t.redw[w * LRP_MAXBV + lane] = v;
   __syncthreads();
-  if (t.tid < t.BV) {
+  const int nw = t.NT >> 5;
+  if (t.BV == 1) {
+    // one column: warp 0 combines the warp partials with a shuffle tree
+    if (w == 0) {
+      double s = lane < nw ? t.redw[lane * LRP_MAXBV] : 0.0;
+      for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+      if (lane == 0) t.red[((t.phase & 1) * NSLOT + slot) * LRP_MAXBV] = s;
+    }
+  } else if (t.tid < t.BV) {
     double s = 0.0;
-    const int nw = t.NT >> 5;
     for (int i = 0; i < nw; ++i) s += t.redw[i * LRP_MAXBV + t.tid];
     t.red[((t.phase & 1) * NSLOT + slot) * LRP_MAXBV + t.tid] = s;
   }
@@ -66,6 +73,14 @@ __device__ __forceinline__ double total(const Team& t, int slot) {
   const int idx = (((t.phase - 1) & 1) * NSLOT + slot) * LRP_MAXBV + t.col;
   if (t.C == 1) return t.red[idx];
   cg::cluster_group cl = cg::this_cluster();
+  if (t.BV == 1) {
+    // one column: lane r loads rank r's partial, a fixed shuffle tree sums
+    // them (the same tree in every warp of every CTA: identical results)
+    const int lane = t.tid & 31;
+    double s = lane < t.C ? *cl.map_shared_rank(t.red + idx, lane) : 0.0;
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    return s;
+  }
   double s = 0.0;
   for (int r = 0; r < t.C; ++r) s += *cl.map_shared_rank(t.red + idx, r);
   return s;

@@ -41,14 +41,14 @@ def test_struct_layouts_match_c(tmp_path):
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "lrp.h"\n'
                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n",'
                    'sizeof(lrp_problem_desc), sizeof(lrp_apply_stats), sizeof(lrp_lanczos_stats),'
-                   'sizeof(lrp_query), sizeof(lrp_query_result), offsetof(lrp_problem_desc, coarse_items),'
+                   'sizeof(lrp_query), sizeof(lrp_query_result), offsetof(lrp_problem_desc, mg_nu_coarse),'
                    'offsetof(lrp_query, xi));return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     want = [ctypes.sizeof(lrp.lrp_problem_desc), ctypes.sizeof(lrp.lrp_apply_stats),
             ctypes.sizeof(lrp.lrp_lanczos_stats), ctypes.sizeof(lrp.lrp_query),
-            ctypes.sizeof(lrp.lrp_query_result), lrp.lrp_problem_desc.coarse_items.offset,
+            ctypes.sizeof(lrp.lrp_query_result), lrp.lrp_problem_desc.mg_nu_coarse.offset,
             lrp.lrp_query.xi.offset]
     assert got == want
 

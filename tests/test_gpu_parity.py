@@ -224,3 +224,39 @@ def test_full_size_heat2d_sampled(precision):
     X = synth.normal_block(P.nx, 2, 41)
     H, st = lrp.lrp_hessian_apply(G, X)
     assert relerr(H, P.hessian_apply(X)) < TOL[precision], st
+
+
+@pytest.mark.parametrize("C", [1, 2, 4, 8])
+def test_band_kernel_matches_oracle(C):
+    """The shared-memory band kernel (2D, mixed precision, one column per
+    cluster) against the oracle and against the generic kernel, for several
+    cluster sizes (bands of 31/C rows with two halo rows each)."""
+    spec = synth.small_spec(dim=2, n=31, nt=24, obs_every=2, n_obs=9, sigma=0.02, seed=31)
+    P = OProblem(spec)
+    Gb = lrp.lrp_setup_problem(spec, precision=lrp.LRP_MIXED, team_ctas=C, team_cols=1, kernel_variant=2)
+    Gg = lrp.lrp_setup_problem(spec, precision=lrp.LRP_MIXED, team_ctas=C, team_cols=1, kernel_variant=1)
+    U = synth.normal_block(P.nx, 3, 5)
+    for fn, ref in ((lrp.lrp_hessian_apply, P.hessian_apply(U)), (lrp.lrp_prior_half, P.prior_half(U)),
+                    (lrp.lrp_forward_observe, P.forward(U))):
+        Yb, sb = fn(Gb, U)
+        Yg, _ = fn(Gg, U)
+        assert relerr(Yb, ref) < 1e-6, sb
+        assert relerr(Yb, Yg) < 1e-6
+    W = synth.normal_block(P.n_data, 3, 6)
+    Xb, _ = lrp.lrp_adjoint(Gb, W)
+    assert relerr(Xb, P.adjoint(W)) < 1e-6
+    Z, _ = lrp.lrp_hessian_apply(Gb, np.zeros((P.nx, 2)))
+    assert np.all(Z == 0.0)
+
+
+@pytest.mark.parametrize("precision", [lrp.LRP_FP64, lrp.LRP_MIXED])
+def test_autotune_keeps_results(precision):
+    """Whatever launch shape and multigrid setting the autotuner picks, the
+    Hessian apply still matches the oracle to the path's tolerance."""
+    spec = synth.small_spec(dim=2, n=31, nt=16, obs_every=2, n_obs=9, with_kappa=True, seed=17)
+    P, G = _pair(spec, precision)
+    ms = lrp.lrp_autotune(G, 4, steps=3)
+    assert 0.0 < ms < 1e4
+    U = synth.normal_block(P.nx, 4, 9)
+    H, st = lrp.lrp_hessian_apply(G, U)
+    assert relerr(H, P.hessian_apply(U)) < TOL[precision], st
