@@ -40,13 +40,23 @@ import synth  # noqa: E402
 
 METRIC = "Hessian matvecs/s (s to rank-k Gamma_post at 1e-6 rel. Ritz residual reported beside)"
 UNIT = "matvec/s"
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "sweep_kernel_heat2d_127.json")
-KERNEL_SOURCES = ["lrp_sweep_kernel.cuh", "lrp_team.cuh", "lrp_sweep.cu"]
+# The two sweep kernels, the sources their device code comes from, and the
+# committed ncu summary (DRAM traffic per launch) for this workload.
+KERNELS = {
+    1: ("sweep_kernel", "persistent cluster-team MG-PCG forward/adjoint sweeps",
+        ["lrp_sweep_kernel.cuh", "lrp_team.cuh", "lrp_sweep.cu"]),
+    2: ("fast2d_kernel", "2D band kernel: shared-memory MG-PCG forward/adjoint sweeps",
+        ["lrp_fast2d.cuh", "lrp_team.cuh", "lrp_sweep_fast.cu", "lrp_sweep.cu"]),
+}
 
 
-def kernel_hash() -> str:
+def profile_summary(name: str) -> str:
+    return os.path.join(ROOT, "profiles", f"{name}_heat2d_127.json")
+
+
+def kernel_hash(sources) -> str:
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in sources:
         with open(os.path.join(ROOT, "paper_1703_05638_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -136,6 +146,87 @@ def cpu_baseline(seconds: float = 15.0):
             "sample": f"{n} single-vector Htilde applies on heat2d_127 (nx=16129, nt=500) in {dt:.1f} s"}
 
 
+def serve_bench(lrp, count: int, rate_hz: float, budget_gib: float, slots: int, max_batch: int):
+    """The serving workload: Poisson arrivals of posterior queries (mean,
+    variance at 1024 nodes, 8 samples) over a 2D 127^2 and two 3D problems,
+    through the library's server (continuous batching, factors resident,
+    admission by memory budget). Factors (k=50) are computed before the
+    stream starts and reported separately. Latency = result on the host
+    minus the scheduled arrival."""
+    import torch
+    reqs = synth.serving_requests(count=count, rate_hz=rate_hz)
+    sizes = sorted({r["size"] for r in reqs})
+    srv = lrp.Server(hbm_budget=int(budget_gib * (1 << 30)), slots=slots, max_batch=max_batch, max_samples=8,
+                     max_points=1024)
+    t0 = time.perf_counter()
+    mids, pools, setup = {}, {}, {}
+    for size in sizes:
+        spec = synth.serving_model_spec(size)
+        ts = time.perf_counter()
+        mid, lst = srv.add_model(spec, k=50, precision=lrp.LRP_MIXED, block=16, eig_tol=1e-6)
+        mids[size] = mid
+        setup[f"{size[0]}_{size[1]}"] = {"s": time.perf_counter() - ts, "n_matvec": lst["n_matvec"],
+                                         "k_converged": lst["k_converged"]}
+        # noise-free data of 8 seeded prior draws, and 2 blocks of sample draws
+        G = lrp.lrp_setup_problem(spec, precision=lrp.LRP_MIXED)
+        u = lrp.lrp_prior_half(G, torch.from_numpy(synth.normal_block(G.nx, 8, spec.seed + 11)).cuda())[0]
+        d = lrp.lrp_forward_observe(G, u)[0].cpu().numpy()
+        pools[size] = (d, [synth.normal_block(G.nx, 8, spec.seed + 13 + j) for j in range(2)], G.nx, G.n_data)
+        G.close()
+    warm_s = time.perf_counter() - t0
+    kind = lrp.LRP_Q_MEAN | lrp.LRP_Q_VARIANCE | lrp.LRP_Q_SAMPLES
+    # inputs of every request prepared before the clock starts
+    prepared = []
+    for r in reqs:
+        d, xis, nx, nd = pools[r["size"]]
+        g = synth.rng(r["seed"])
+        y = d[:, r["index"] % d.shape[1]] + r["sigma"] * g.standard_normal(nd)
+        prepared.append((mids[r["size"]], y, r["sigma"], synth.query_nodes(nx, r["n_query"], r["seed"]),
+                         xis[r["index"] % 2]))
+    tickets = [None] * len(reqs)
+    lag = [0.0] * len(reqs)
+    start = time.perf_counter() + 0.05
+
+    def submitter():
+        for i, r in enumerate(reqs):
+            due = start + r["arrival_s"]
+            while True:
+                now = time.perf_counter()
+                if now >= due:
+                    break
+                time.sleep(min(due - now, 0.002))
+            mid, y, sig, pts, xi = prepared[i]
+            tickets[i] = srv.submit(mid, kind, y_obs=y, sigma=sig, points=pts, xi=xi)
+            lag[i] = (time.perf_counter() - due) * 1e3
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    lat, batch = [], []
+    for i in range(len(reqs)):
+        while tickets[i] is None:
+            time.sleep(0.0005)
+        out = srv.wait(tickets[i], timeout=600.0)
+        lat.append(out["latency_ms"] + lag[i])
+        batch.append(out["stats"]["batch"])
+    th.join()
+    t_end = time.perf_counter()
+    info = srv.info()
+    srv.close()
+    lat_a = np.asarray(lat)
+    by_size = {}
+    for size in sizes:
+        sel = [j for j, r in enumerate(reqs) if r["size"] == size]
+        by_size[f"{size[0]}_{size[1]}"] = {"n": len(sel), "p50_ms": float(np.percentile(lat_a[sel], 50)),
+                                           "p99_ms": float(np.percentile(lat_a[sel], 99))}
+    return {"p50_ms": float(np.percentile(lat_a, 50)), "p99_ms": float(np.percentile(lat_a, 99)),
+            "requests": len(reqs), "rate_hz": rate_hz,
+            "throughput_rps": len(reqs) / (t_end - start), "mean_batch": float(np.mean(batch)),
+            "batches": info["batches"], "admissions": info["admissions"], "evictions": info["evictions"],
+            "device_gib_held": info["device_bytes"] / (1 << 30), "budget_gib": budget_gib, "slots": slots,
+            "max_batch": max_batch, "by_size": by_size, "factor_setup": setup, "warmup_s": warm_s,
+            "query": "mean + variance@1024 + 8 samples, sigma log-uniform [1e-4, 1e-2], k=50"}
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -186,6 +277,17 @@ def main():
     ap.add_argument("--team-ctas", type=int, default=0)
     ap.add_argument("--team-cols", type=int, default=0)
     ap.add_argument("--mg-nu", type=int, default=0)
+    ap.add_argument("--mode", default="posterior", choices=["posterior", "apply"],
+                    help="posterior: the whole hot path per step; apply: one Hessian apply per step "
+                         "(kernel-level measurement and profiling)")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-budget-gib", type=float, default=24.0)
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-batch", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -221,6 +323,8 @@ def main():
     if args.mg_nu:
         tuning["mg_nu"] = args.mg_nu
     G = lrp.lrp_setup_problem(spec, precision=precision, stream=stream, **tuning)
+    if not args.no_autotune and not tuning:
+        lrp.lrp_autotune(G, args.block)
     nx = G.nx
     seed = spec.seed + 101 * rank
     # synthetic inputs, resident in HBM: Lanczos start block, data, query nodes, sample draws
@@ -240,6 +344,11 @@ def main():
     kind = lrp.LRP_Q_MEAN | lrp.LRP_Q_VARIANCE | lrp.LRP_Q_SAMPLES
 
     def step(device=True):
+        if args.mode == "apply":
+            # kernel-level case: one Hessian apply to the Lanczos-sized block
+            _, ast = lrp.lrp_hessian_apply(G, start_d if device else start_h)
+            return {"n_matvec": args.block, "ms": ast["ms"], "n_iter": 1, "k_converged": 0,
+                    "max_ritz_resid": 0.0, "ms_apply": ast["ms"]}, None
         if device:
             post, st = lrp.lrp_lowrank_posterior(G, k=args.k, block=args.block, eig_tol=1e-6, start=start_d)
             out = lrp.lrp_posterior_query(post, kind, y_obs=y_obs, points=nodes_d, xi=xi_d, device=True)
@@ -273,7 +382,11 @@ def main():
     if dist:
         dist.barrier()
     clocks = sampler.stop()
-    sweep_ms, sweep_launches, sweep_bytes = lrp.lrp_sweep_profile(G, 0)
+    ledger = {kv: lrp.lrp_sweep_profile(G, -1, kv) for kv in (1, 2)}
+    lrp.lrp_sweep_profile(G, 0)
+    # the dominant sweep kernel of the timed region (most device time)
+    kdom = max(ledger, key=lambda kv: ledger[kv][0])
+    sweep_ms, sweep_launches, sweep_bytes = ledger[kdom]
     launches = lrp.lrp_kernel_launches() - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = float(sum(step_ms))
@@ -290,8 +403,11 @@ def main():
     # end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
-        h2d = start_h.nbytes + y_obs_h.nbytes + nodes_h.nbytes + xi_h.nbytes
-        d2h = 8 * (args.k + nx + nodes_h.size + nx * xi_h.shape[1])
+        if args.mode == "apply":
+            h2d, d2h = start_h.nbytes, start_h.nbytes
+        else:
+            h2d = start_h.nbytes + y_obs_h.nbytes + nodes_h.nbytes + xi_h.nbytes
+            d2h = 8 * (args.k + nx + nodes_h.size + nx * xi_h.shape[1])
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         mv = 0
@@ -303,26 +419,58 @@ def main():
         e2e = {"value": mv * max(ws, 1) / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
+    # the plain FP64 GPU method on the same workload and GPU: one full
+    # time-to-rank-k run (the same Lanczos, every solve in FP64)
+    fp64 = None
+    if not args.no_fp64_compare and precision == lrp.LRP_MIXED and rank == 0 and args.mode == "posterior":
+        G64 = lrp.lrp_setup_problem(spec, precision=lrp.LRP_FP64, stream=stream)
+        lrp.lrp_hessian_apply(G64, start_d[:, :2])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        post64, st64 = lrp.lrp_lowrank_posterior(G64, k=args.k, block=args.block, eig_tol=1e-6, start=start_d)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        lam64 = post64.eigs()
+        post64.close()
+        post_m, _ = lrp.lrp_lowrank_posterior(G, k=args.k, block=args.block, eig_tol=1e-6, start=start_d)
+        lam_m = post_m.eigs()
+        post_m.close()
+        kk = min(len(lam64), len(lam_m))
+        ms64 = e0.elapsed_time(e1)
+        fp64 = {"value": st64["n_matvec"] / (ms64 / 1e3), "unit": UNIT, "s_to_rank_k": ms64 / 1e3,
+                "n_matvec": st64["n_matvec"], "tuning": lrp.lrp_problem_tuning(G64),
+                "max_rel_eig_diff_vs_mixed": float(np.max(np.abs(lam_m[:kk] - lam64[:kk]) / lam64[0]))}
+        G64.close()
+
+    serve = None
+    if not args.no_serve and args.mode == "posterior":
+        serve = serve_bench(lrp, args.serve_requests, args.serve_rate, args.serve_budget_gib, args.serve_slots,
+                            args.serve_batch)
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return 0
     peaks, peak_kind = measured_peaks()
+    tune = lrp.lrp_problem_tuning(G)
+    kname, kdesc, ksources = KERNELS[kdom]
     achieved = (sweep_bytes / sweep_launches) / (sweep_ms / sweep_launches / 1e3) / 1e9 if sweep_ms > 0 else 0.0
     traffic = None
     try:
-        with open(PROFILE_SUMMARY) as f:
+        with open(profile_summary(kname)) as f:
             prof = json.load(f)
-        if prof.get("kernel_hash") == kernel_hash() and prof.get("dram_bytes_per_launch_full"):
+        if prof.get("kernel_hash") == kernel_hash(ksources) and prof.get("dram_bytes_per_launch_full"):
             traffic = prof["dram_bytes_per_launch_full"]
     except (OSError, ValueError):
         pass
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                "kernel": "sweep_kernel<float,2,mixed> (persistent MG-PCG forward/adjoint sweeps)",
+                "kernel": f"{kname} ({kdesc})", "kernel_hash": kernel_hash(ksources),
                 "peak_kind": f"{peak_kind} copy bandwidth",
                 "algo_bytes_per_launch": sweep_bytes / max(sweep_launches, 1),
-                "ms_per_launch": sweep_ms / max(sweep_launches, 1), "launches": sweep_launches}
+                "ms_per_launch": sweep_ms / max(sweep_launches, 1), "launches": sweep_launches,
+                "sweep_ms_by_kernel": {KERNELS[kv][0]: ledger[kv][0] for kv in ledger}}
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         cpu = cpu_baseline()
@@ -331,17 +479,23 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": max(ws, 1), "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 multigrid-PCG in f64 refinement; f64 Lanczos/QR/eig/posterior" if precision else "f64",
+        "dtype": "f32/f64" if precision == lrp.LRP_MIXED else "f64",
         "data": "synthetic",
         "config": {"workload": f"heat2d_127: 2D heat eq 127x127 interior (nx=16129), nt={spec.nt}, 400 uniform "
                                "sensors at every step, sigma=1e-3, prior (I-0.05 Lap)^-2",
+                   "step": ("block Lanczos to rank k + posterior factors + one query" if args.mode == "posterior"
+                            else "one Hessian apply to a block of columns"),
                    "k": args.k, "block": args.block, "eig_tol": 1e-6, "query": "mean + variance@1024 + 8 samples",
                    "l2": "flushed (256 MB write) before every timed step",
+                   "precision": "f32 MG-PCG inside f64 iterative refinement; f64 Lanczos, re-orthogonalisation, "
+                                "eigensolve and posterior" if precision == lrp.LRP_MIXED else "f64 throughout",
+                   "launch": tune, "autotuned": not args.no_autotune and not tuning,
                    "parallelism": f"replicas x{max(ws, 1)}"},
         "s_to_rank_k": statistics.mean(s["ms"] for s in stats) / 1e3,
         "lanczos": {"n_iter": lan["n_iter"], "n_matvec": lan["n_matvec"], "k_converged": lan["k_converged"],
                     "max_ritz_resid": lan["max_ritz_resid"], "ms_apply": lan["ms_apply"]},
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "fp64_gpu": fp64, "serve": serve,
+        "gpu_launches": int(launches),
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)

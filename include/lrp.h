@@ -196,12 +196,14 @@ lrp_status lrp_hessian_apply(lrp_problem* p, int nvec, const double* X, int ldx,
 lrp_status lrp_hessian_apply_noalloc(lrp_problem* p, int nvec, const double* X, int ldx,
                                      double* Y, int ldy, lrp_apply_stats* st);
 
-/* Autotuner: for blocks of nvec columns, times a short forward sweep (steps
- * implicit-Euler steps, 0 -> 4) for each candidate cluster size, columns per
- * cluster, smoothing sweeps and (LRP_MIXED) inner tolerance, and keeps the
- * fastest in the problem handle for later calls. All candidates iterate to
- * the same tolerances. *best_ms (may be NULL) receives the winning time.
- * Allocates a temporary nx x nvec block. No counterpart in the paper. */
+/* Autotuner for blocks of nvec columns. Round 1 times, for each candidate
+ * cluster size, columns per cluster, smoothing sweeps and (LRP_MIXED) inner
+ * tolerance, the prior solve and the first `steps` forward implicit-Euler
+ * steps (0 -> 16); round 2 times one whole Hessian apply for the three
+ * fastest. The winner stays in the problem handle for later calls. All
+ * candidates iterate to the same tolerances. *best_ms (may be NULL) receives
+ * the winner's Hessian-apply time. Allocates two nx x nvec blocks for the
+ * duration of the call. No counterpart in the paper. */
 lrp_status lrp_autotune(lrp_problem* p, int nvec, int steps, double* best_ms);
 
 /* D = F U (no noise weighting): forward sweep and observation.
@@ -265,13 +267,90 @@ const char* lrp_last_error(void);
 const char* lrp_version(void);
 
 /* Sweep-kernel ledger. mode 1: reset and start recording, for every launch
- * of the persistent sweep kernel on this problem, its CUDA-event duration and
- * its algorithmic bytes (passes over the fine-level vectors implied by the
+ * of a sweep kernel on this problem, its CUDA-event duration and its
+ * algorithmic bytes (passes over the fine-level vectors implied by the
  * solver's iteration counts); mode 0: reset and stop; mode -1: read only.
- * The accumulated values before the reset are returned in *ms, *launches and
- * *algo_bytes (each may be NULL). */
-lrp_status lrp_sweep_profile(lrp_problem* p, int mode, double* ms, unsigned long long* launches,
+ * kernel selects what is returned: 0 all sweep launches, 1 the generic team
+ * kernel, 2 the 2D band kernel. The accumulated values before the reset are
+ * returned in *ms, *launches and *algo_bytes (each may be NULL). */
+lrp_status lrp_sweep_profile(lrp_problem* p, int mode, int kernel, double* ms, unsigned long long* launches,
                              double* algo_bytes);
+
+/* Current launch/multigrid settings of a problem (set by lrp_setup_problem's
+ * descriptor or chosen by lrp_autotune) and what the last sweep launch used:
+ * last_kernel 1 = generic team kernel, 2 = 2D band kernel, 0 = none yet;
+ * last_team_ctas = the cluster size it ran with (the requested size is
+ * halved until every team is resident). No counterpart in the paper. */
+typedef struct lrp_tuning {
+  int team_ctas, team_cols, mg_nu, mg_nu_coarse;
+  double inner_rtol;
+  int last_kernel, last_team_ctas;
+} lrp_tuning;
+lrp_status lrp_problem_tuning(const lrp_problem* p, lrp_tuning* out);
+
+/* ---------------------------------------------------------------------------
+ * Posterior-query server (no counterpart in the paper; it serves the
+ * low-rank posterior of Sec. 2 to a stream of requests).
+ *
+ * A model is a problem with its rank-k factors, computed by
+ * lrp_lowrank_posterior when the model is added (or read from a checkpoint).
+ * Requests (lrp_query: mean, pointwise variance, samples; each with its own
+ * data and noise level, the stored eigenvalues being rescaled by
+ * sigma0^2/sigma^2) are queued by lrp_server_submit and served by `slots`
+ * worker threads, each with its own CUDA stream: a free worker takes the
+ * model of the oldest pending request and serves up to max_batch of its
+ * pending requests in one batch (one adjoint sweep and one prior sweep over
+ * all the batch's columns). Requests arriving while batches run join the
+ * next batch a worker forms, and batches overlap on the device.
+ * Memory: factors, per-worker problem handles and batch scratch are counted
+ * against hbm_budget; a model whose factors are not on the device is admitted
+ * by evicting least recently used idle models (factors kept in pinned host
+ * memory); a request whose model cannot fit even alone fails with
+ * LRP_EBUDGET. A result does not depend on the batch it was served in beyond
+ * the solver tolerance. The device current at lrp_server_create is used.
+ * Thread safety: submit, wait and info may be called from any threads. */
+typedef struct lrp_server lrp_server;
+
+typedef struct {
+  size_t hbm_budget;  /* device bytes the server may hold; 0 -> 16 GiB */
+  int slots;          /* worker threads / streams (batches in flight); 0 -> 4, <= 64 */
+  int max_batch;      /* requests per batch; 0 -> 16, <= 256 */
+  int max_samples;    /* largest n_samples of a request; 0 -> 8, <= 64 */
+  int max_points;     /* largest n_points of a request; 0 -> 1024 */
+} lrp_server_config;
+
+typedef struct {
+  double t_submit_ms;  /* milliseconds since lrp_server_create */
+  double t_start_ms;   /* its batch was formed */
+  double t_done_ms;    /* its results were on the host */
+  int batch;           /* requests in that batch */
+  int slot;            /* worker that served it */
+  int admitted;        /* 1 if the model's factors were brought onto the device for this batch */
+} lrp_request_stats;
+
+typedef struct {
+  size_t device_bytes;  /* accounted device bytes held now */
+  int models, resident;
+  long long admissions, evictions, batches, served, pending;
+} lrp_server_stats;
+
+lrp_status lrp_server_create(const lrp_server_config* cfg, lrp_server** out);
+/* Adds a model: sets the problem up from d, computes its rank-k factors
+ * (block, eig_tol as in lrp_lowrank_posterior) or, if factors_path names an
+ * existing checkpoint of the same problem, reads them (a non-NULL path that
+ * does not exist yet receives the computed factors). *model receives its id. */
+lrp_status lrp_server_add_model(lrp_server* s, const lrp_problem_desc* d, int k, int block, double eig_tol,
+                                const char* factors_path, int* model, lrp_lanczos_stats* st);
+/* Queues a request (its inputs are copied; q's arrays may be reused at once). */
+lrp_status lrp_server_submit(lrp_server* s, int model, const lrp_query* q, unsigned long long* ticket);
+/* Waits for a request (timeout_s <= 0: no limit; LRP_ETIMEOUT otherwise),
+ * copies its results into r's HOST buffers (each may be NULL) and releases
+ * the ticket. Returns the request's own status. */
+lrp_status lrp_server_wait(lrp_server* s, unsigned long long ticket, double timeout_s, lrp_query_result* r,
+                           lrp_request_stats* st);
+lrp_status lrp_server_info(lrp_server* s, lrp_server_stats* out);
+/* Finishes the queued requests, stops the workers, frees everything. */
+void lrp_server_destroy(lrp_server* s);
 
 /* Diagnostics: number of CUDA kernels this library has launched in this
  * process so far (all problems, all threads). */

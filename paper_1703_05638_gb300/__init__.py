@@ -69,6 +69,33 @@ class lrp_query_result(C.Structure):
     _fields_ = [("mean", C.c_void_p), ("variance", C.c_void_p), ("samples", C.c_void_p), ("ms", C.c_double)]
 
 
+class lrp_server_config(C.Structure):
+    _fields_ = [("hbm_budget", C.c_size_t), ("slots", C.c_int), ("max_batch", C.c_int),
+                ("max_samples", C.c_int), ("max_points", C.c_int)]
+
+
+class lrp_request_stats(C.Structure):
+    _fields_ = [("t_submit_ms", C.c_double), ("t_start_ms", C.c_double), ("t_done_ms", C.c_double),
+                ("batch", C.c_int), ("slot", C.c_int), ("admitted", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class lrp_server_stats(C.Structure):
+    _fields_ = [("device_bytes", C.c_size_t), ("models", C.c_int), ("resident", C.c_int),
+                ("admissions", C.c_longlong), ("evictions", C.c_longlong), ("batches", C.c_longlong),
+                ("served", C.c_longlong), ("pending", C.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class lrp_tuning(C.Structure):
+    _fields_ = [("team_ctas", C.c_int), ("team_cols", C.c_int), ("mg_nu", C.c_int), ("mg_nu_coarse", C.c_int),
+                ("inner_rtol", C.c_double), ("last_kernel", C.c_int), ("last_team_ctas", C.c_int)]
+
+
 EXPORTS = {
     "lrp_setup_problem": (C.c_int, [C.POINTER(lrp_problem_desc), C.c_void_p, C.POINTER(C.c_void_p)]),
     "lrp_problem_destroy": (None, [C.c_void_p]),
@@ -96,7 +123,16 @@ EXPORTS = {
     "lrp_last_error": (C.c_char_p, []),
     "lrp_version": (C.c_char_p, []),
     "lrp_kernel_launches": (C.c_ulonglong, []),
-    "lrp_sweep_profile": (C.c_int, [C.c_void_p, C.c_int, _dp, C.POINTER(C.c_ulonglong), _dp]),
+    "lrp_sweep_profile": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _dp, C.POINTER(C.c_ulonglong), _dp]),
+    "lrp_problem_tuning": (C.c_int, [C.c_void_p, C.POINTER(lrp_tuning)]),
+    "lrp_server_create": (C.c_int, [C.POINTER(lrp_server_config), C.POINTER(C.c_void_p)]),
+    "lrp_server_add_model": (C.c_int, [C.c_void_p, C.POINTER(lrp_problem_desc), C.c_int, C.c_int, C.c_double,
+                                       C.c_char_p, C.POINTER(C.c_int), C.POINTER(lrp_lanczos_stats)]),
+    "lrp_server_submit": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(lrp_query), C.POINTER(C.c_ulonglong)]),
+    "lrp_server_wait": (C.c_int, [C.c_void_p, C.c_ulonglong, C.c_double, C.POINTER(lrp_query_result),
+                                  C.POINTER(lrp_request_stats)]),
+    "lrp_server_info": (C.c_int, [C.c_void_p, C.POINTER(lrp_server_stats)]),
+    "lrp_server_destroy": (None, [C.c_void_p]),
 }
 
 _lib = None
@@ -196,14 +232,10 @@ class Problem:
             pass
 
 
-def lrp_setup_problem(spec, precision: int = LRP_FP64, stream=None, **tuning) -> Problem:
-    """Set up a problem from an object with the attributes of synth.ProblemSpec
-    (dim, n, nt, T, prior_alpha, sigma, obs_every, sensors, kappa)."""
-    lib = load()
+def _desc(spec, precision, tuning, keep):
     d = lrp_problem_desc()
     d.dim, d.n, d.nt, d.T = int(spec.dim), int(spec.n), int(spec.nt), float(spec.T)
     kap = getattr(spec, "kappa", None)
-    keep = []
     if kap is not None:
         k = np.ascontiguousarray(np.concatenate([np.asarray(f, dtype=np.float64).ravel() for f in kap]))
         keep.append(k)
@@ -220,6 +252,15 @@ def lrp_setup_problem(spec, precision: int = LRP_FP64, stream=None, **tuning) ->
     d.time_rank_max = int(getattr(spec, "time_rank_max", 40) or 40)
     for key, val in tuning.items():
         setattr(d, key, val)
+    return d
+
+
+def lrp_setup_problem(spec, precision: int = LRP_FP64, stream=None, **tuning) -> Problem:
+    """Set up a problem from an object with the attributes of synth.ProblemSpec
+    (dim, n, nt, T, prior_alpha, sigma, obs_every, sensors, kappa)."""
+    lib = load()
+    keep = []
+    d = _desc(spec, precision, tuning, keep)
     h = C.c_void_p()
     s = 0 if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
     _check(lib.lrp_setup_problem(C.byref(d), C.c_void_p(s), C.byref(h)))
@@ -250,9 +291,10 @@ def lrp_hessian_apply_noalloc(prob: Problem, X):
     return _sweep(load().lrp_hessian_apply_noalloc, prob, X, prob.nx, prob.nx)
 
 
-def lrp_autotune(prob: Problem, nvec: int, steps: int = 4) -> float:
+def lrp_autotune(prob: Problem, nvec: int, steps: int = 16) -> float:
     """Pick the fastest launch shape / multigrid setting for blocks of nvec
-    columns (kept in the problem); returns the winning time in ms."""
+    columns (kept in the problem); returns the winner's Hessian-apply time
+    in ms."""
     ms = C.c_double()
     _check(load().lrp_autotune(prob.handle, int(nvec), int(steps), C.byref(ms)))
     return ms.value
@@ -404,12 +446,110 @@ def lrp_version() -> str:
     return load().lrp_version().decode()
 
 
-def lrp_sweep_profile(prob: "Problem", mode: int = -1):
+def lrp_sweep_profile(prob: "Problem", mode: int = -1, kernel: int = 0):
     """Sweep-kernel ledger: returns (ms, launches, algorithmic bytes) accumulated
-    so far; mode 1 resets and starts recording, 0 resets and stops, -1 reads."""
+    so far for kernel (0 all sweep launches, 1 generic team kernel, 2 band
+    kernel); mode 1 resets and starts recording, 0 resets and stops, -1 reads."""
     ms, n, b = C.c_double(), C.c_ulonglong(), C.c_double()
-    _check(load().lrp_sweep_profile(prob.handle, int(mode), C.byref(ms), C.byref(n), C.byref(b)))
+    _check(load().lrp_sweep_profile(prob.handle, int(mode), int(kernel), C.byref(ms), C.byref(n), C.byref(b)))
     return ms.value, int(n.value), b.value
+
+
+class Server:
+    """Posterior-query server (continuous batching over several models on one
+    GPU; see lrp_server_* in lrp.h). Results come back as NumPy arrays."""
+
+    def __init__(self, hbm_budget: int = 0, slots: int = 0, max_batch: int = 0, max_samples: int = 0,
+                 max_points: int = 0):
+        cfg = lrp_server_config(int(hbm_budget), int(slots), int(max_batch), int(max_samples), int(max_points))
+        h = C.c_void_p()
+        _check(load().lrp_server_create(C.byref(cfg), C.byref(h)))
+        self.handle = h
+        self._nx = {}
+        self._shape = {}
+
+    def add_model(self, spec, k: int, precision: int = LRP_MIXED, block: int = 16, eig_tol: float = 1e-6,
+                  factors_path=None, **tuning):
+        """Returns (model id, Lanczos stats)."""
+        keep = []
+        d = _desc(spec, precision, tuning, keep)
+        mid = C.c_int()
+        st = lrp_lanczos_stats()
+        path = factors_path.encode() if factors_path else None
+        _check(load().lrp_server_add_model(self.handle, C.byref(d), int(k), int(block), float(eig_tol), path,
+                                           C.byref(mid), C.byref(st)), allow=(LRP_OK, LRP_ENOCONV))
+        self._nx[mid.value] = int(spec.n) ** int(spec.dim)
+        return mid.value, st.as_dict()
+
+    def submit(self, model: int, kind: int, y_obs=None, sigma: float = 0.0, points=None, xi=None) -> int:
+        q = lrp_query()
+        q.kind = kind
+        q.sigma = float(sigma)
+        keep = []
+        nx = self._nx[model]
+        if y_obs is not None:
+            y = np.ascontiguousarray(np.asarray(y_obs, dtype=np.float64).ravel())
+            keep.append(y)
+            q.y_obs = y.ctypes.data
+        npts = ns = 0
+        if points is not None:
+            pt = np.ascontiguousarray(np.asarray(points, dtype=np.int32).ravel())
+            keep.append(pt)
+            q.points, q.n_points = pt.ctypes.data, pt.size
+            npts = pt.size
+        if xi is not None:
+            x = np.asfortranarray(np.asarray(xi, dtype=np.float64).reshape(nx, -1))
+            keep.append(x)
+            q.xi, q.n_samples = x.ctypes.data, x.shape[1]
+            ns = x.shape[1]
+        t = C.c_ulonglong()
+        _check(load().lrp_server_submit(self.handle, int(model), C.byref(q), C.byref(t)))
+        self._shape[t.value] = (kind, nx, npts, ns)
+        return t.value
+
+    def wait(self, ticket: int, timeout: float = 0.0) -> dict:
+        kind, nx, npts, ns = self._shape.pop(ticket)
+        res = lrp_query_result()
+        out = {}
+        if kind & (LRP_Q_MEAN | LRP_Q_SAMPLES):
+            out["mean"] = np.zeros(nx)
+            res.mean = out["mean"].ctypes.data
+        if kind & LRP_Q_VARIANCE:
+            out["variance"] = np.zeros(npts)
+            res.variance = out["variance"].ctypes.data
+        if kind & LRP_Q_SAMPLES:
+            out["samples"] = np.zeros((nx, ns), order="F")
+            res.samples = out["samples"].ctypes.data
+        st = lrp_request_stats()
+        _check(load().lrp_server_wait(self.handle, C.c_ulonglong(ticket), float(timeout), C.byref(res),
+                                      C.byref(st)))
+        out["stats"] = st.as_dict()
+        out["latency_ms"] = st.t_done_ms - st.t_submit_ms
+        return out
+
+    def info(self) -> dict:
+        st = lrp_server_stats()
+        _check(load().lrp_server_info(self.handle, C.byref(st)))
+        return st.as_dict()
+
+    def close(self):
+        if self.handle:
+            load().lrp_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lrp_problem_tuning(prob: "Problem") -> dict:
+    """Current launch/multigrid settings and what the last sweep launch used
+    (last_kernel: 1 generic team kernel, 2 band kernel, 0 none yet)."""
+    t = lrp_tuning()
+    _check(load().lrp_problem_tuning(prob.handle, C.byref(t)))
+    return {f: getattr(t, f) for f, _ in lrp_tuning._fields_}
 
 
 def lrp_kernel_launches() -> int:

@@ -47,6 +47,7 @@ static lrp_status dev_alloc(lrp_problem* P, T** out, size_t count) {
   cudaError_t e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
   if (e != cudaSuccess) return cuda_status(e, "cudaMalloc");
   P->allocs.push_back(p);
+  P->dev_bytes += std::max<size_t>(count, 1) * sizeof(T);
   *out = (T*)p;
   return LRP_OK;
 }
@@ -218,8 +219,6 @@ lrp_status lrp_setup_problem(const lrp_problem_desc* desc, void* cuda_stream, lr
   P->ws_bytes = 0;
   P->prof_on = 0;
   P->prof_ev[0] = P->prof_ev[1] = nullptr;
-  P->prof_ms = P->prof_bytes = 0.0;
-  P->prof_launches = 0;
   {
     const char* pz = std::getenv("LRP_POISON");  // byte value to fill new workspace with (1 -> 0xFF)
     P->poison = pz ? (std::atoi(pz) == 1 ? 0xFF : (std::atoi(pz) | 0x100)) : 0;
@@ -391,25 +390,42 @@ lrp_status lrp_setup_problem(const lrp_problem_desc* desc, void* cuda_stream, lr
   return LRP_OK;
 }
 
-lrp_status lrp_sweep_profile(lrp_problem* P, int mode, double* ms, unsigned long long* launches,
+lrp_status lrp_sweep_profile(lrp_problem* P, int mode, int kernel, double* ms, unsigned long long* launches,
                              double* algo_bytes) {
-  if (!P) {
-    set_error("NULL problem");
+  if (!P || kernel < 0 || kernel > 2) {
+    set_error("lrp_sweep_profile: NULL problem or kernel not in 0..2");
     return LRP_EINVAL;
   }
-  if (ms) *ms = P->prof_ms;
-  if (launches) *launches = P->prof_launches;
-  if (algo_bytes) *algo_bytes = P->prof_bytes;
+  if (ms) *ms = P->prof_ms[kernel];
+  if (launches) *launches = P->prof_launches[kernel];
+  if (algo_bytes) *algo_bytes = P->prof_bytes[kernel];
   if (mode >= 0) {
     if (mode == 1 && !P->prof_ev[0]) {
       cudaEventCreate(&P->prof_ev[0]);
       cudaEventCreate(&P->prof_ev[1]);
     }
     P->prof_on = (mode == 1) && P->prof_ev[0];
-    P->prof_ms = 0.0;
-    P->prof_bytes = 0.0;
-    P->prof_launches = 0;
+    for (int v = 0; v < 3; ++v) {
+      P->prof_ms[v] = 0.0;
+      P->prof_bytes[v] = 0.0;
+      P->prof_launches[v] = 0;
+    }
   }
+  return LRP_OK;
+}
+
+lrp_status lrp_problem_tuning(const lrp_problem* P, lrp_tuning* out) {
+  if (!P || !out) {
+    set_error("lrp_problem_tuning: NULL argument");
+    return LRP_EINVAL;
+  }
+  out->team_ctas = P->team_ctas;
+  out->team_cols = P->team_cols;
+  out->mg_nu = P->cfg.nu;
+  out->mg_nu_coarse = P->cfg.nu_coarse;
+  out->inner_rtol = P->cfg.inner_rtol;
+  out->last_kernel = P->last_kernel;
+  out->last_team_ctas = P->last_team_ctas;
   return LRP_OK;
 }
 
@@ -557,90 +573,106 @@ static lrp_status hessian_with_factors(lrp_problem* P, int nvec, const double* X
 
 extern "C" {
 
-// Autotuner: times a short forward sweep (steps implicit-Euler steps on a
-// pseudo-random block of nvec columns) for each candidate launch shape and
-// multigrid setting and keeps the fastest. Every candidate iterates to the
-// same tolerances, so the choice changes the speed, not the result beyond
-// rounding.
+// Autotuner, in two rounds on a pseudo-random block of nvec columns:
+// (1) every candidate launch shape and multigrid setting times the prior
+// solve and the first `steps` implicit-Euler steps of the forward sweep
+// (the smooth start the Hessian apply sees); (2) the three fastest time one
+// whole Hessian apply each, and the fastest of those is kept. Every
+// candidate iterates to the same tolerances, so the choice changes the
+// speed, not the result beyond rounding.
 lrp_status lrp_autotune(lrp_problem* P, int nvec, int steps, double* best_ms) {
   if (!P || nvec < 1 || nvec > 4096) {
     set_error("lrp_autotune: invalid argument");
     return LRP_EINVAL;
   }
   cudaSetDevice(P->device);
-  if (steps < 1) steps = 4;
+  if (steps < 1) steps = 16;
   steps = std::min(steps, P->nt);
-  double* X = nullptr;
+  double *X = nullptr, *Y = nullptr;
   cudaError_t e = cudaMalloc(&X, (size_t)P->nx * nvec * sizeof(double));
-  if (e != cudaSuccess) return cuda_status(e, "autotune cudaMalloc");
-  e = fill_random(P->stream, P->nx, nvec, X, P->nx, nullptr, 0xA070ull);
+  if (e == cudaSuccess) e = cudaMalloc(&Y, (size_t)P->nx * nvec * sizeof(double));
+  if (e == cudaSuccess) e = fill_random(P->stream, P->nx, nvec, X, P->nx, nullptr, 0xA070ull);
   if (e != cudaSuccess) {
     cudaFree(X);
-    return cuda_status(e, "autotune fill");
+    cudaFree(Y);
+    return cuda_status(e, "autotune buffers");
   }
   struct Cand {
-    int C, BV, nu, nuc;
-    double inner;
+    int C, BV, nu;
+    double inner, t1, t2;
   };
   std::vector<Cand> cands;
   const bool mixed = P->desc.precision == LRP_MIXED;
-  const int Cs[] = {1, 2, 4, 8, 16};
-  const int BVs[] = {1, 2, 4};
-  for (int C : Cs)
-    for (int BV : BVs) {
+  for (int C : {1, 2, 4, 8, 16})
+    for (int BV : {1, 2, 4}) {
       if (BV > nvec && BV > 1) continue;
       if (C > 1 && (long long)P->nx / C < 256) continue;
       for (int nu : {1, 2})
         for (double inner : (mixed ? std::vector<double>{1e-4, 1e-5} : std::vector<double>{0.0}))
-          cands.push_back({C, BV, nu, nu, inner});
+          cands.push_back({C, BV, nu, inner, 1e300, 1e300});
     }
   const int save_C = P->team_ctas, save_BV = P->team_cols;
   const SolveCfg save_cfg = P->cfg;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  double best = 1e300;
-  Cand bestc = {save_C, save_BV, save_cfg.nu, save_cfg.nu_coarse, save_cfg.inner_rtol};
-  for (const Cand& c : cands) {
+  auto apply_cand = [&](const Cand& c) {
     P->team_ctas = c.C;
     P->team_cols = c.BV;
+    P->cfg = save_cfg;
     P->cfg.nu = c.nu;
-    P->cfg.nu_coarse = c.nuc;
+    P->cfg.nu_coarse = c.nu;
     if (mixed) P->cfg.inner_rtol = c.inner;
-    double ms_run = 1e300;
+  };
+  auto time_it = [&](unsigned stages, int t_end, double* out) {
+    double best_t = 1e300;
     for (int rep = 0; rep < 2; ++rep) {
       cudaEventRecord(e0, P->stream);
-      lrp_status st = run_sweep_ex(P, ST_LOAD_X | ST_FORWARD, nvec, X, P->nx, nullptr, 0, nullptr, 0, nullptr, 0,
-                                   nullptr, 0, steps, nullptr, 0);
+      lrp_status st = run_sweep_ex(P, stages, nvec, X, P->nx, Y, P->nx, nullptr, 0, nullptr, 0, nullptr, 0, t_end,
+                                   nullptr, 0);
       cudaEventRecord(e1, P->stream);
       cudaEventSynchronize(e1);
-      if (st != LRP_OK) {
-        ms_run = 1e300;
-        break;
-      }
+      if (st != LRP_OK) return;
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
-      ms_run = std::min(ms_run, (double)ms);
+      best_t = std::min(best_t, (double)ms);
     }
-    if (ms_run < best) {
-      best = ms_run;
-      bestc = c;
-    }
+    *out = best_t;
+  };
+  for (Cand& c : cands) {
+    apply_cand(c);
+    time_it(ST_LOAD_X | ST_PRIOR_IN | ST_FORWARD, steps, &c.t1);
+  }
+  std::sort(cands.begin(), cands.end(), [](const Cand& a, const Cand& b) { return a.t1 < b.t1; });
+  const unsigned hess = ST_LOAD_X | ST_PRIOR_IN | ST_FORWARD | ST_ADJOINT | ST_PRIOR_OUT | ST_STORE_Y;
+  const int n2 = std::min<int>(3, (int)cands.size());
+  for (int i = 0; i < n2; ++i) {
+    if (!(cands[i].t1 < 1e300)) continue;
+    apply_cand(cands[i]);
+    time_it(hess, -1, &cands[i].t2);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(X);
-  P->team_ctas = bestc.C;
-  P->team_cols = bestc.BV;
-  P->cfg = save_cfg;
-  P->cfg.nu = bestc.nu;
-  P->cfg.nu_coarse = bestc.nuc;
-  if (mixed) P->cfg.inner_rtol = bestc.inner;
-  if (best_ms) *best_ms = best;
+  cudaFree(Y);
+  int bi = -1;
+  for (int i = 0; i < n2; ++i)
+    if (cands[i].t2 < 1e300 && (bi < 0 || cands[i].t2 < cands[bi].t2)) bi = i;
+  if (bi < 0) {
+    P->team_ctas = save_C;
+    P->team_cols = save_BV;
+    P->cfg = save_cfg;
+    set_error("lrp_autotune: no candidate ran");
+    return LRP_ECUDA;
+  }
+  apply_cand(cands[bi]);
+  if (best_ms) *best_ms = cands[bi].t2;
   if (std::getenv("LRP_VERBOSE"))
-    std::fprintf(stderr, "[lrp] autotune nvec=%d: C=%d BV=%d nu=%d inner=%.0e (%.2f ms per %d steps)\n", nvec,
-                 bestc.C, bestc.BV, bestc.nu, bestc.inner, best, steps);
-  return best < 1e300 ? LRP_OK : LRP_ECUDA;
+    for (int i = 0; i < n2; ++i)
+      std::fprintf(stderr, "[lrp] autotune nvec=%d: C=%d BV=%d nu=%d inner=%.0e screen %.2f ms, apply %.2f ms%s\n",
+                   nvec, cands[i].C, cands[i].BV, cands[i].nu, cands[i].inner, cands[i].t1, cands[i].t2,
+                   i == bi ? " <- kept" : "");
+  return LRP_OK;
 }
 
 lrp_status lrp_hessian_apply(lrp_problem* P, int nvec, const double* X, int ldx, double* Y, int ldy,

@@ -167,6 +167,7 @@ struct lrp_problem {
   int sm_count;
   // tuned launch parameters
   int team_ctas, team_cols, nthreads, coarse_items, smem_cap, kernel_variant;
+  int last_kernel = 0, last_team_ctas = 0;  // what the last sweep launch used
   int poison;  // LRP_POISON set: new workspace and shared memory start as NaN
   // caller-provided sweep workspace (set only for the duration of an
   // allocation-free call; NULL otherwise)
@@ -176,11 +177,13 @@ struct lrp_problem {
   uint64_t hash;
   // sweep-kernel ledger (lrp_sweep_profile): CUDA-event time and algorithmic
   // bytes of every sweep launch while enabled
+  // (index 0: all launches; 1: generic team kernel; 2: band kernel)
   int prof_on;
   cudaEvent_t prof_ev[2];
-  double prof_ms;
-  double prof_bytes;
-  unsigned long long prof_launches;
+  double prof_ms[3];
+  double prof_bytes[3];
+  unsigned long long prof_launches[3];
+  size_t dev_bytes = 0;  // device bytes of the problem's own arrays (not the workspace)
 };
 
 struct lrp_posterior {

@@ -184,6 +184,8 @@ lrp_status run_sweep_ex(lrp_problem* Pr, unsigned stages, int nvec, const double
   }
   if (!fast)
     while (C > 1 && resident_teams(mixed, Pr->dim, C, Pr->nthreads, soff, Pr->sm_count) < n_teams) C >>= 1;
+  Pr->last_kernel = fast ? 2 : 1;
+  Pr->last_team_ctas = C;
   prm.dim = Pr->dim;
   prm.nt = Pr->nt;
   prm.t_begin = t_begin;
@@ -248,9 +250,12 @@ lrp_status run_sweep_ex(lrp_problem* Pr, unsigned stages, int nvec, const double
   if (Pr->prof_on) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, Pr->prof_ev[0], Pr->prof_ev[1]);
-    Pr->prof_ms += ms;
-    Pr->prof_launches += 1;
-    Pr->prof_bytes += algorithmic_bytes(Pr, hs, BV, mixed);
+    const double ab = algorithmic_bytes(Pr, hs, BV, mixed);
+    for (int v : {0, fast ? 2 : 1}) {
+      Pr->prof_ms[v] += ms;
+      Pr->prof_launches[v] += 1;
+      Pr->prof_bytes[v] += ab;
+    }
   }
   if (st) {
     std::memset(st, 0, sizeof(*st));

@@ -218,6 +218,21 @@ def serving_requests(count: int = 1000, rate_hz: float = 200.0,
     return reqs
 
 
+def serving_model_spec(size) -> ProblemSpec:
+    """The fixed problem behind each request size of the serving workload:
+    ("2d", 127) is the 127^2 workload (nt=500, 400 uniform sensors observed
+    at every step); ("3d", n) is the 3D workload's setting on an n^3 grid
+    (kappa field, 400 uniform sensors every 10th step) with nt=100. The
+    factors are computed at sigma0 = 1e-3 and rescaled per request."""
+    dim, n = size
+    if dim == "2d":
+        return workload("heat2d_127")
+    seed = 1000 + WORKLOAD_INDEX["serving"] + n
+    return ProblemSpec(name=f"serve3d_n{n}", dim=3, n=n, nt=100, T=1.0, prior_alpha=0.05, sigma=1e-3,
+                       obs_every=10, sensors=uniform_sensors(400, 3, seed), kappa=kappa_faces(n, 3, seed + 7),
+                       k=50, block=16, seed=seed)
+
+
 def query_nodes(nx: int, count: int, seed: int) -> np.ndarray:
     """count distinct grid-node indices drawn uniformly (sorted, int32)."""
     count = min(count, nx)

@@ -39,17 +39,18 @@ def test_every_declared_symbol_is_exported(lib):
 def test_struct_layouts_match_c(tmp_path):
     src = tmp_path / "sz.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "lrp.h"\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n",'
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",'
                    'sizeof(lrp_problem_desc), sizeof(lrp_apply_stats), sizeof(lrp_lanczos_stats),'
                    'sizeof(lrp_query), sizeof(lrp_query_result), offsetof(lrp_problem_desc, mg_nu_coarse),'
-                   'offsetof(lrp_query, xi));return 0;}\n')
+                   'offsetof(lrp_query, xi), sizeof(lrp_tuning), offsetof(lrp_tuning, last_team_ctas));'
+                   'return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     want = [ctypes.sizeof(lrp.lrp_problem_desc), ctypes.sizeof(lrp.lrp_apply_stats),
             ctypes.sizeof(lrp.lrp_lanczos_stats), ctypes.sizeof(lrp.lrp_query),
             ctypes.sizeof(lrp.lrp_query_result), lrp.lrp_problem_desc.mg_nu_coarse.offset,
-            lrp.lrp_query.xi.offset]
+            lrp.lrp_query.xi.offset, ctypes.sizeof(lrp.lrp_tuning), lrp.lrp_tuning.last_team_ctas.offset]
     assert got == want
 
 
@@ -64,3 +65,14 @@ def test_sources_have_no_host_fallback():
     src = open(os.path.join(ROOT, "paper_1703_05638_gb300", "__init__.py")).read()
     assert "oracle" not in src.replace("the oracle", "")
     assert "import scipy" not in src
+
+
+def test_server_struct_layouts_match_c(tmp_path):
+    names = ["lrp_server_config", "lrp_request_stats", "lrp_server_stats", "lrp_tuning"]
+    src = tmp_path / "sz2.c"
+    body = "".join(f'printf("%zu\\n", sizeof({n}));' for n in names)
+    src.write_text('#include <stdio.h>\n#include "lrp.h"\nint main(void){' + body + 'return 0;}\n')
+    exe = tmp_path / "sz2"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert got == [ctypes.sizeof(getattr(lrp, n)) for n in names]
