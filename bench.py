@@ -277,9 +277,9 @@ def main():
     ap.add_argument("--team-ctas", type=int, default=0)
     ap.add_argument("--team-cols", type=int, default=0)
     ap.add_argument("--mg-nu", type=int, default=0)
-    ap.add_argument("--mode", default="posterior", choices=["posterior", "apply"],
+    ap.add_argument("--mode", default="posterior", choices=["posterior", "apply", "serve"],
                     help="posterior: the whole hot path per step; apply: one Hessian apply per step "
-                         "(kernel-level measurement and profiling)")
+                         "(kernel-level measurement and profiling); serve: the serving workload alone")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
@@ -310,6 +310,17 @@ def main():
         dist.barrier()
     lrp.load()
 
+    if args.mode == "serve":
+        if rank == 0:
+            sv = serve_bench(lrp, args.serve_requests, args.serve_rate, args.serve_budget_gib, args.serve_slots,
+                             args.serve_batch)
+            print(json.dumps({"metric": "serve latency p50 (p99 beside)", "value": sv["p50_ms"], "unit": "ms",
+                              "n_gpus": 1, "higher_is_better": False, "data": "synthetic", "dtype": "f32/f64",
+                              "config": {"workload": "serving: Poisson stream over 2D 127^2 and 3D 31^3/63^3"},
+                              "serve": sv}), flush=True)
+        if dist:
+            dist.destroy_process_group()
+        return 0
     spec = synth.workload("heat2d_127")
     if args.nt:
         spec.nt = args.nt

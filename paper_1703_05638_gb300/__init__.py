@@ -486,7 +486,7 @@ class Server:
         q.kind = kind
         q.sigma = float(sigma)
         keep = []
-        nx = self._nx[model]
+        nx = self._nx.get(model, 1)  # an unknown model is rejected by the library
         if y_obs is not None:
             y = np.ascontiguousarray(np.asarray(y_obs, dtype=np.float64).ravel())
             keep.append(y)

@@ -730,4 +730,67 @@ cudaError_t eig_sym_batched(cudaStream_t s, int batch, const int* n_dev, int nma
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Diagonal of the prior covariance R^-2, R = I + alpha L0, with L0 the
+// constant-coefficient finite-difference Laplacian on the n^dim interior
+// grid of the unit square/cube (zero Dirichlet data). L0 is diagonalised by
+// the orthonormal sine transform: S_ik = sqrt(2/(n+1)) sin(pi i k/(n+1)) per
+// axis, eigenvalues mu_k = (4/h^2) sin^2(pi k h/2), h = 1/(n+1), summed over
+// the axes. Hence diag_i = sum_k w(k) prod_d S_{i_d k_d}^2 with
+// w(k) = (1 + alpha sum_d mu_{k_d})^-2, evaluated by contracting one axis at
+// a time (dim n^(dim+1) multiply-adds).
+__global__ void k_dst_sq(int n, double* A) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * n) return;
+  const int i = e / n, k = e % n;
+  const double s = sinpi((double)((i + 1) * (k + 1)) / (double)(n + 1));
+  A[e] = 2.0 / (double)(n + 1) * s * s;
+}
+
+__global__ void k_dst_weight(int dim, int n, double alpha, double* W) {
+  const int total = dim == 2 ? n * n : n * n * n;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const double h = 1.0 / (double)(n + 1);
+  int k[3] = {e % n, (e / n) % n, dim == 3 ? e / (n * n) : 0};
+  double mu = 0.0;
+  for (int d = 0; d < dim; ++d) {
+    const double sv = sinpi(0.5 * (double)(k[d] + 1) * h);
+    mu += 4.0 / (h * h) * sv * sv;
+  }
+  const double r = 1.0 + alpha * mu;
+  W[e] = 1.0 / (r * r);
+}
+
+// out(.., i_axis, ..) = sum_k A(i_axis, k) in(.., k, ..); axis 0 is the fastest index.
+__global__ void k_dst_contract(int dim, int n, int axis, const double* A, const double* in, double* out) {
+  const int total = dim == 2 ? n * n : n * n * n;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const int stride = axis == 0 ? 1 : (axis == 1 ? n : n * n);
+  const int ia = (e / stride) % n;
+  const int base = e - ia * stride;
+  double acc = 0.0;
+  for (int k = 0; k < n; ++k) acc += A[ia * n + k] * in[base + k * stride];
+  out[e] = acc;
+}
+
+cudaError_t prior_diag_dst(cudaStream_t s, int dim, int n, double alpha, double* out, double* work) {
+  const int total = dim == 2 ? n * n : n * n * n;
+  double* A = work;
+  double* W = work + (size_t)n * n;
+  double* T = W + total;
+  note_launch(2);
+  k_dst_sq<<<(n * n + 255) / 256, 256, 0, s>>>(n, A);
+  k_dst_weight<<<(total + 255) / 256, 256, 0, s>>>(dim, n, alpha, W);
+  const double* src = W;
+  for (int axis = 0; axis < dim; ++axis) {
+    double* dst = (axis == dim - 1) ? out : (src == W ? T : W);
+    note_launch();
+    k_dst_contract<<<(total + 255) / 256, 256, 0, s>>>(dim, n, axis, A, src, dst);
+    src = dst;
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace lrp

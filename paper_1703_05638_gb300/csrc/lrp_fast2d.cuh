@@ -20,6 +20,14 @@
 // is being overwritten.
 // The FP64 state of the implicit-Euler sweep (solution, right-hand side,
 // observations) stays in global memory: it is touched once per refinement.
+//
+// Addressing: every shared-memory array is an offset (in floats) into the
+// kernel's dynamic shared memory, so local accesses are 32-bit shared-window
+// accesses, and the neighbours' copies are 32-bit cluster-window addresses
+// (mapa); this keeps the register footprint small enough for the hot loops to
+// load all inputs of a group of column chunks before their first store (a
+// store could alias the next point's inputs, so the compiler would otherwise
+// issue one point's loads at a time).
 #pragma once
 
 #include "lrp_sweep_kernel.cuh"
@@ -27,6 +35,30 @@
 namespace lrp {
 
 constexpr int FAST_HALO = 2;
+constexpr int FAST_NJ = 4;  // column chunks per row a lane handles (col = lane + 32 j): n <= 128
+#ifndef LRP_FAST_G
+#define LRP_FAST_G 2
+#endif
+constexpr int FAST_G = LRP_FAST_G;  // chunks whose loads are issued together
+#ifndef LRP_FAST_THREADS
+#define LRP_FAST_THREADS 512
+#endif
+constexpr int FAST_THREADS = LRP_FAST_THREADS;
+
+extern __shared__ __align__(16) float s_fb[];  // the band kernel's dynamic shared memory
+
+__device__ __forceinline__ unsigned smem_addr(int off) {
+  return (unsigned)__cvta_generic_to_shared(s_fb + off);
+}
+// Address of the same shared-memory location in CTA `rank` of the cluster.
+__device__ __forceinline__ unsigned cluster_addr(unsigned local, int rank) {
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_cluster(unsigned addr, float v) {
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
 
 // Optional section timers (build with -DLRP_SECTION_TIMERS): thread 0 of each
 // CTA accumulates clock64() cycles per section into shared memory; CTA 0 of
@@ -57,68 +89,83 @@ struct Band {
   int warp, lane, nwarp;
 };
 
-// Address of (row, col) in a band array whose band starts at row b0.
+// Index of (row, col) in a band array whose band starts at row b0.
 __device__ __forceinline__ int bidx(const Band& b, int b0, int row, int col) {
   return (row - b0 + FAST_HALO) * b.pitch + col;
 }
 
-// A band array with the addresses of the same array in the previous and next
-// CTA of the team (NULL at the ends), for halo stores.
+// A band array (offset of its element 0) with the cluster addresses of the
+// same array in the previous and next CTA of the team, for halo stores.
 struct BArr {
-  float* a;
-  float* prev;
-  float* next;
+  int a;
+  unsigned prev, next;
 };
 
-__device__ __forceinline__ BArr barr(const Band& b, float* A) {
+__device__ __forceinline__ BArr barr(const Band& b, int A) {
   BArr r;
   r.a = A;
-  r.prev = b.rank > 0 ? cg::this_cluster().map_shared_rank(A, b.rank - 1) : nullptr;
-  r.next = b.rank < b.C - 1 ? cg::this_cluster().map_shared_rank(A, b.rank + 1) : nullptr;
+  const unsigned loc = smem_addr(A);
+  r.prev = b.rank > 0 ? cluster_addr(loc, b.rank - 1) : 0u;
+  r.next = b.rank < b.C - 1 ? cluster_addr(loc, b.rank + 1) : 0u;
   return r;
 }
 
 // Store v at (row, col) locally and, for boundary rows, into the halo of the
 // neighbour that needs it.
 __device__ __forceinline__ void bstore(const Band& b, const BArr& A, int row, int col, float v) {
-  A.a[bidx(b, b.r0, row, col)] = v;
-  if (A.prev && row < b.r0 + FAST_HALO) A.prev[bidx(b, b.r0p, row, col)] = v;
-  if (A.next && row >= b.r1 - FAST_HALO) A.next[bidx(b, b.r0n, row, col)] = v;
+  s_fb[A.a + bidx(b, b.r0, row, col)] = v;
+  if (b.rank > 0 && row < b.r0 + FAST_HALO) st_cluster(A.prev + 4u * (unsigned)bidx(b, b.r0p, row, col), v);
+  if (b.rank < b.C - 1 && row >= b.r1 - FAST_HALO)
+    st_cluster(A.next + 4u * (unsigned)bidx(b, b.r0n, row, col), v);
 }
 
-// (I + c L) v at (row, col) for a band array (kappa = 1).
-__device__ __forceinline__ float band_op(const Band& b, const float* A, int row, int col, float ch2,
-                                         float d) {
-  const int i = bidx(b, b.r0, row, col);
-  return d * A[i] - ch2 * (A[i - 1] + A[i + 1] + A[i - b.pitch] + A[i + b.pitch]);
-}
-
-template <class F>
-__device__ __forceinline__ void for_own(const Band& b, F f) {
-  for (int row = b.r0 + b.warp; row < b.r1; row += b.nwarp)
-    for (int col = b.lane; col < b.n; col += 32) f(row, col);
+// Sum of the four neighbours of index i of a band array.
+__device__ __forceinline__ float bnb(const Band& b, int A, int i) {
+  return s_fb[A + i - 1] + s_fb[A + i + 1] + s_fb[A + i - b.pitch] + s_fb[A + i + b.pitch];
 }
 
 struct FastVec {
-  float* E[2];
-  float* R;
-  float* P;
-  float* Q;
-  float* X;
+  int E[2];
+  int R, P, Q, X;
+};
+
+// Coarse levels: offsets of the two smoother buffers and the right-hand side.
+struct CLv {
+  int e[LRP_MAXLEV][2];
+  int f[LRP_MAXLEV];
 };
 
 // One damped Jacobi sweep on the band: Eo = Ei + omega (R - A Ei) / d.
 __device__ __forceinline__ void fast_sweep(const Band& b, const FastVec& v, int cur, float ch2, float d,
                                            float dinv, float omega, bool acc_rz, double& rz) {
-  const float* Ei = v.E[cur];
+  const int Ei = v.E[cur];
   const BArr Eo = barr(b, v.E[cur ^ 1]);
   float acc = 0.f;  // per-thread partial in FP32 (FP64 is a slow pipe here)
-  for_own(b, [&](int row, int col) {
-    const int i = bidx(b, b.r0, row, col);
-    const float e = Ei[i] + omega * (v.R[i] - band_op(b, Ei, row, col, ch2, d)) * dinv;
-    bstore(b, Eo, row, col, e);
-    if (acc_rz) acc += v.R[i] * e;
-  });
+  for (int row = b.r0 + b.warp; row < b.r1; row += b.nwarp) {
+    const int base = bidx(b, b.r0, row, 0);
+#pragma unroll
+    for (int j0 = 0; j0 < FAST_NJ; j0 += FAST_G) {
+      float ec[FAST_G], nb[FAST_G], rv[FAST_G];
+#pragma unroll
+      for (int j = j0; j < j0 + FAST_G; ++j) {
+        const int i = base + b.lane + 32 * j;
+        if (b.lane + 32 * j < b.n) {
+          ec[j - j0] = s_fb[Ei + i];
+          nb[j - j0] = bnb(b, Ei, i);
+          rv[j - j0] = s_fb[v.R + i];
+        }
+      }
+#pragma unroll
+      for (int j = j0; j < j0 + FAST_G; ++j) {
+        const int col = b.lane + 32 * j;
+        if (col < b.n) {
+          const float e = ec[j - j0] + omega * (rv[j - j0] - (d * ec[j - j0] - ch2 * nb[j - j0])) * dinv;
+          bstore(b, Eo, row, col, e);
+          if (acc_rz) acc += rv[j - j0] * e;
+        }
+      }
+    }
+  }
   rz += (double)acc;
 }
 
@@ -134,24 +181,40 @@ __device__ __forceinline__ void for_all(int n, int warp, int lane, int nwarp, F 
     for (int col = lane; col < n; col += 32) f(row, col);
 }
 
-__device__ __forceinline__ float cop(const float* A, int n, int i, float ch2, float d) {
-  return d * A[i] - ch2 * (A[i - 1] + A[i + 1] + A[i - (n + 1)] + A[i + (n + 1)]);
+__device__ __forceinline__ float cnb(int A, int n, int i) {
+  return s_fb[A + i - 1] + s_fb[A + i + 1] + s_fb[A + i - (n + 1)] + s_fb[A + i + (n + 1)];
 }
 
 // Jacobi sweep on a coarse level: eo = ei + omega (f - A ei) / d
-__device__ __forceinline__ void csweep(const Band& b, const OpLevel& lv, float* eo, const float* ei, const float* f,
-                                       float omega) {
+__device__ __forceinline__ void csweep(const Band& b, const OpLevel& lv, int eo, int ei, int f, float omega) {
   const int n = lv.n;
   const float ch2 = (float)lv.ch2, d = 1.f + 4.f * ch2, dinv = (float)lv.dinv;
-  for_all(n, b.warp, b.lane, b.nwarp, [&](int row, int col) {
-    const int i = cidx(n, row, col);
-    eo[i] = ei[i] + omega * (f[i] - cop(ei, n, i, ch2, d)) * dinv;
-  });
+  for (int row = b.warp; row < n; row += b.nwarp) {
+    const int base = cidx(n, row, 0);
+#pragma unroll
+    for (int j0 = 0; j0 < FAST_NJ; j0 += FAST_G) {
+      float ec[FAST_G], nb[FAST_G], fv[FAST_G];
+#pragma unroll
+      for (int j = j0; j < j0 + FAST_G; ++j) {
+        const int i = base + b.lane + 32 * j;
+        if (b.lane + 32 * j < n) {
+          ec[j - j0] = s_fb[ei + i];
+          nb[j - j0] = cnb(ei, n, i);
+          fv[j - j0] = s_fb[f + i];
+        }
+      }
+#pragma unroll
+      for (int j = j0; j < j0 + FAST_G; ++j)
+        if (b.lane + 32 * j < n)
+          s_fb[eo + base + b.lane + 32 * j] =
+              ec[j - j0] + omega * (fv[j - j0] - (d * ec[j - j0] - ch2 * nb[j - j0])) * dinv;
+    }
+  }
 }
 
 // Full-weighting restriction of f - A e from level lf to lc, and ec = sc fc / d
-__device__ __forceinline__ void crestrict(const Band& b, const OpLevel& lf, const OpLevel& lc, const float* ef,
-                                          const float* ff, float* fc, float* ec, float sc) {
+__device__ __forceinline__ void crestrict(const Band& b, const OpLevel& lf, const OpLevel& lc, int ef, int ff,
+                                          int fc, int ec, float sc) {
   const int nf = lf.n, nc = lc.n;
   const float ch2 = (float)lf.ch2, d = 1.f + 4.f * ch2, dinvc = (float)lc.dinv;
   for_all(nc, b.warp, b.lane, b.nwarp, [&](int J, int I) {
@@ -161,40 +224,56 @@ __device__ __forceinline__ void crestrict(const Band& b, const OpLevel& lf, cons
 #pragma unroll
       for (int dx = -1; dx <= 1; ++dx) {
         const int i = cidx(nf, 2 * J + 1 + dy, 2 * I + 1 + dx);
-        acc += (dx == 0 ? 0.5f : 0.25f) * (dy == 0 ? 0.5f : 0.25f) * (ff[i] - cop(ef, nf, i, ch2, d));
+        acc += (dx == 0 ? 0.5f : 0.25f) * (dy == 0 ? 0.5f : 0.25f) *
+               (s_fb[ff + i] - (d * s_fb[ef + i] - ch2 * cnb(ef, nf, i)));
       }
     const int k = cidx(nc, J, I);
-    fc[k] = acc;
-    ec[k] = sc * acc * dinvc;
+    s_fb[fc + k] = acc;
+    s_fb[ec + k] = sc * acc * dinvc;
   });
 }
 
 // Bilinear value of the coarse field ec (level with nc nodes, padded) at fine
 // node (row, col) of the level below it (pads give the zero boundary).
-__device__ __forceinline__ float cinterp(const float* ec, int nc, int row, int col) {
+__device__ __forceinline__ float cinterp(int ec, int nc, int row, int col) {
   const int cy0 = (row - 1) >> 1, cx0 = (col - 1) >> 1;  // floor((row-1)/2): -1 for row 0
-  const float* base = ec + cidx(nc, cy0, cx0);
+  const int base = ec + cidx(nc, cy0, cx0);
   if (row & 1) {
-    if (col & 1) return base[0];
-    return 0.5f * (base[0] + base[1]);
+    if (col & 1) return s_fb[base];
+    return 0.5f * (s_fb[base] + s_fb[base + 1]);
   }
-  if (col & 1) return 0.5f * (base[0] + base[nc + 1]);
-  return 0.25f * (base[0] + base[1] + base[nc + 1] + base[nc + 2]);
+  if (col & 1) return 0.5f * (s_fb[base] + s_fb[base + nc + 1]);
+  return 0.25f * (s_fb[base] + s_fb[base + 1] + s_fb[base + nc + 1] + s_fb[base + nc + 2]);
 }
 
 // e += P ec on a coarse level (in place)
-__device__ __forceinline__ void cprolong(const Band& b, const OpLevel& lf, const OpLevel& lc, float* ef,
-                                         const float* ec) {
+__device__ __forceinline__ void cprolong(const Band& b, const OpLevel& lf, const OpLevel& lc, int ef, int ec) {
   const int nf = lf.n, nc = lc.n;
-  for_all(nf, b.warp, b.lane, b.nwarp, [&](int row, int col) { ef[cidx(nf, row, col)] += cinterp(ec, nc, row, col); });
+  for (int row = b.warp; row < nf; row += b.nwarp) {
+    const int base = cidx(nf, row, 0);
+#pragma unroll
+    for (int j0 = 0; j0 < FAST_NJ; j0 += FAST_G) {
+      float cur[FAST_G], add[FAST_G];
+#pragma unroll
+      for (int j = j0; j < j0 + FAST_G; ++j)
+        if (b.lane + 32 * j < nf) {
+          cur[j - j0] = s_fb[ef + base + b.lane + 32 * j];
+          add[j - j0] = cinterp(ec, nc, row, b.lane + 32 * j);
+        }
+#pragma unroll
+      for (int j = j0; j < j0 + FAST_G; ++j)
+        if (b.lane + 32 * j < nf) s_fb[ef + base + b.lane + 32 * j] = cur[j - j0] + add[j - j0];
+    }
+  }
 }
 
 // Coarse rows J whose fine centre row 2J+1 lies in this band: full-weighting
 // restriction of the residual R - A E into every CTA's copy of f1 (padded
 // coarse layout).
 __device__ __forceinline__ void fast_restrict(const Band& b, const FastVec& v, int cur, float ch2, float d,
-                                              float* f1, int n1) {
-  const float* E = v.E[cur];
+                                              int f1, int n1) {
+  const int E = v.E[cur];
+  const unsigned f1loc = smem_addr(f1);
   int J0 = b.r0 / 2;  // smallest J with 2J+1 >= r0
   if (2 * J0 + 1 < b.r0) ++J0;
   for (int J = J0 + b.warp; 2 * J + 1 < b.r1 && J < n1; J += b.nwarp) {
@@ -204,35 +283,49 @@ __device__ __forceinline__ void fast_restrict(const Band& b, const FastVec& v, i
       for (int dy = -1; dy <= 1; ++dy) {
 #pragma unroll
         for (int dx = -1; dx <= 1; ++dx) {
-          const int row = 2 * J + 1 + dy, col = 2 * I + 1 + dx;
-          const float res = v.R[bidx(b, b.r0, row, col)] - band_op(b, E, row, col, ch2, d);
+          const int i = bidx(b, b.r0, 2 * J + 1 + dy, 2 * I + 1 + dx);
+          const float res = s_fb[v.R + i] - (d * s_fb[E + i] - ch2 * bnb(b, E, i));
           acc += (dx == 0 ? 0.5f : 0.25f) * (dy == 0 ? 0.5f : 0.25f) * res;
         }
       }
       const int k = cidx(n1, J, I);
       for (int r = 0; r < b.C; ++r) {
-        float* dst = (r == b.rank) ? f1 : cg::this_cluster().map_shared_rank(f1, r);
-        dst[k] = acc;
+        if (r == b.rank)
+          s_fb[f1 + k] = acc;
+        else
+          st_cluster(cluster_addr(f1loc, r) + 4u * (unsigned)k, acc);
       }
     }
   }
 }
 
 // Eo = Ei + P e1 on the band (bilinear interpolation from the padded coarse copy).
-__device__ __forceinline__ void fast_prolong(const Band& b, const FastVec& v, int cur, const float* e1,
-                                             int n1) {
-  const float* Ei = v.E[cur];
+__device__ __forceinline__ void fast_prolong(const Band& b, const FastVec& v, int cur, int e1, int n1) {
+  const int Ei = v.E[cur];
   const BArr Eo = barr(b, v.E[cur ^ 1]);
-  for_own(b, [&](int row, int col) {
-    bstore(b, Eo, row, col, Ei[bidx(b, b.r0, row, col)] + cinterp(e1, n1, row, col));
-  });
+  for (int row = b.r0 + b.warp; row < b.r1; row += b.nwarp) {
+    const int base = bidx(b, b.r0, row, 0);
+#pragma unroll
+    for (int j0 = 0; j0 < FAST_NJ; j0 += FAST_G) {
+      float cur_[FAST_G], add[FAST_G];
+#pragma unroll
+      for (int j = j0; j < j0 + FAST_G; ++j)
+        if (b.lane + 32 * j < b.n) {
+          cur_[j - j0] = s_fb[Ei + base + b.lane + 32 * j];
+          add[j - j0] = cinterp(e1, n1, row, b.lane + 32 * j);
+        }
+#pragma unroll
+      for (int j = j0; j < j0 + FAST_G; ++j)
+        if (b.lane + 32 * j < b.n) bstore(b, Eo, row, b.lane + 32 * j, cur_[j - j0] + add[j - j0]);
+    }
+  }
 }
 
 // Multigrid V-cycle z = M R on the band. Entry: R and E[0] (first smoother
 // sweep, pointwise) complete with halos. Exit: z in E[returned], r.z total in
 // slot SL_RZ.
-__device__ int fast_vcycle(const Team& t, const Band& b, const FastVec& v, const Op& op,
-                           const SmemLv<float>& sm, float omega, int nu, int nuc) {
+__device__ int fast_vcycle(const Team& t, const Band& b, const FastVec& v, const Op& op, const CLv& sm,
+                           float omega, int nu, int nuc) {
   const int L = op.L;
   if (L == 1) return 0;
   const OpLevel& l0 = op.lv[0];
@@ -259,7 +352,7 @@ __device__ int fast_vcycle(const Team& t, const Band& b, const FastVec& v, const
     const float d1inv = (float)l1.dinv;
     for_all(n1, b.warp, b.lane, b.nwarp, [&](int row, int col) {
       const int i = cidx(n1, row, col);
-      sm.e[1][0][i] = sc * sm.f[1][i] * d1inv;
+      s_fb[sm.e[1][0] + i] = sc * s_fb[sm.f[1] + i] * d1inv;
     });
     __syncthreads();
     unsigned ecur = 0;  // bit l: current smoother buffer of level l
@@ -306,8 +399,8 @@ __device__ int fast_vcycle(const Team& t, const Band& b, const FastVec& v, const
 }
 
 // FP32 PCG on the band from a prepared state (R, E[0] set), updating X.
-__device__ void fast_pcg(const Team& t, const Band& b, const FastVec& v, const Op& op, const SmemLv<float>& sm,
-                         double tol2, bool& done, const SolveCfg& cfg, Ctr& ctr) {
+__device__ void fast_pcg(const Team& t, const Band& b, const FastVec& v, const Op& op, const CLv& sm, double tol2,
+                         bool& done, const SolveCfg& cfg, Ctr& ctr) {
   const OpLevel& l0 = op.lv[0];
   const float ch2 = (float)l0.ch2, d = 1.f + 4.f * ch2, dinv = (float)l0.dinv;
   const float omega = (float)cfg.omega;
@@ -318,21 +411,44 @@ __device__ void fast_pcg(const Team& t, const Band& b, const FastVec& v, const O
   while (!all) {
     const int zc = fast_vcycle(t, b, v, op, sm, omega, cfg.nu, cfg.nu_coarse);
     SEC_T0();
-    const float* z = v.E[zc];
+    const int z = v.E[zc];
     const double rz = total(t, SL_RZ);
     SEC_ADD(SEC_REDUCE);
     const float beta = (float)((it_count == 0 || done || !(rz_old > 0.0)) ? 0.0 : rz / rz_old);
     float pqf = 0.f;
     const bool first = (it_count == 0);
-    for_own(b, [&](int row, int col) {
-      const int i = bidx(b, b.r0, row, col);
-      const float az = band_op(b, z, row, col, ch2, d);
-      const float pv = first ? z[i] : z[i] + beta * v.P[i];
-      const float qv = first ? az : az + beta * v.Q[i];
-      v.P[i] = pv;
-      v.Q[i] = qv;
-      pqf += pv * qv;
-    });
+    // phase A: p = z + beta p, q = A z + beta q (= A p), p.q
+    for (int row = b.r0 + b.warp; row < b.r1; row += b.nwarp) {
+      const int base = bidx(b, b.r0, row, 0);
+#pragma unroll
+      for (int j0 = 0; j0 < FAST_NJ; j0 += FAST_G) {
+        float zc_[FAST_G], zn[FAST_G], pp[FAST_G], qq[FAST_G];
+#pragma unroll
+        for (int j = j0; j < j0 + FAST_G; ++j) {
+          const int i = base + b.lane + 32 * j;
+          if (b.lane + 32 * j < b.n) {
+            zc_[j - j0] = s_fb[z + i];
+            zn[j - j0] = bnb(b, z, i);
+            if (!first) {
+              pp[j - j0] = s_fb[v.P + i];
+              qq[j - j0] = s_fb[v.Q + i];
+            }
+          }
+        }
+#pragma unroll
+        for (int j = j0; j < j0 + FAST_G; ++j) {
+          const int i = base + b.lane + 32 * j;
+          if (b.lane + 32 * j < b.n) {
+            const float az = d * zc_[j - j0] - ch2 * zn[j - j0];
+            const float pv = first ? zc_[j - j0] : zc_[j - j0] + beta * pp[j - j0];
+            const float qv = first ? az : az + beta * qq[j - j0];
+            s_fb[v.P + i] = pv;
+            s_fb[v.Q + i] = qv;
+            pqf += pv * qv;
+          }
+        }
+      }
+    }
     const double pq = (double)pqf;
     SEC_ADD(SEC_BAND);
     contribute(t, SL_PQ, pq);
@@ -343,20 +459,41 @@ __device__ void fast_pcg(const Team& t, const Band& b, const FastVec& v, const O
     SEC_ADD(SEC_REDUCE);
     const float alpha = (float)((done || !(pqt > 0.0)) ? 0.0 : rz / pqt);
     float rrf = 0.f, rz1f = 0.f;
-    // E[0] is written below; z may be E[0] but phase A has consumed it
+    // phase B: x += alpha p, r -= alpha q, first smoother sweep of the next
+    // V-cycle. E[0] is written here; z may be E[0] but phase A has consumed it.
     {
       const BArr Xa = barr(b, v.X), Ra = barr(b, v.R), Ea = barr(b, v.E[0]);
-      for_own(b, [&](int row, int col) {
-        const int i = bidx(b, b.r0, row, col);
-        const float xv = first ? alpha * v.P[i] : v.X[i] + alpha * v.P[i];
-        const float rv = v.R[i] - alpha * v.Q[i];
-        bstore(b, Xa, row, col, xv);
-        bstore(b, Ra, row, col, rv);
-        rrf += rv * rv;
-        const float e = scale0 * rv * dinv;
-        bstore(b, Ea, row, col, e);
-        if (op.L == 1) rz1f += rv * e;
-      });
+      for (int row = b.r0 + b.warp; row < b.r1; row += b.nwarp) {
+        const int base = bidx(b, b.r0, row, 0);
+#pragma unroll
+        for (int j0 = 0; j0 < FAST_NJ; j0 += FAST_G) {
+          float xx[FAST_G], pp[FAST_G], rr_[FAST_G], qq[FAST_G];
+#pragma unroll
+          for (int j = j0; j < j0 + FAST_G; ++j) {
+            const int i = base + b.lane + 32 * j;
+            if (b.lane + 32 * j < b.n) {
+              pp[j - j0] = s_fb[v.P + i];
+              qq[j - j0] = s_fb[v.Q + i];
+              rr_[j - j0] = s_fb[v.R + i];
+              if (!first) xx[j - j0] = s_fb[v.X + i];
+            }
+          }
+#pragma unroll
+          for (int j = j0; j < j0 + FAST_G; ++j) {
+            const int col = b.lane + 32 * j;
+            if (col < b.n) {
+              const float xv = first ? alpha * pp[j - j0] : xx[j - j0] + alpha * pp[j - j0];
+              const float rv = rr_[j - j0] - alpha * qq[j - j0];
+              bstore(b, Xa, row, col, xv);
+              bstore(b, Ra, row, col, rv);
+              rrf += rv * rv;
+              const float e = scale0 * rv * dinv;
+              bstore(b, Ea, row, col, e);
+              if (op.L == 1) rz1f += rv * e;
+            }
+          }
+        }
+      }
     }
     const double rr = (double)rrf, rz1 = (double)rz1f;
     SEC_ADD(SEC_BAND);
@@ -386,7 +523,7 @@ __device__ void fast_pcg(const Team& t, const Band& b, const FastVec& v, const O
 // refinement around the band FP32 MG-PCG; inner problems scaled by powers of
 // two as in the generic kernel.
 __device__ double* fast_solve(const Team& t, const Band& b, const SweepParams& P, const Op& op,
-                              const WSV<float>& w, const FastVec& v, const SmemLv<float>& sm, const double* bsrc,
+                              const WSV<float>& w, const FastVec& v, const CLv& sm, const double* bsrc,
                               const double* dsrc, const double* x0, double* X1, double* X2, Ctr& ctr) {
   const OpLevel& l0 = op.lv[0];
   const int n = b.n;
@@ -408,37 +545,60 @@ __device__ double* fast_solve(const Team& t, const Band& b, const SweepParams& P
     double rr = 0.0, bb = 0.0, rz1 = 0.0;
     SEC_T0();
     const BArr Ra = barr(b, v.R), Ea = barr(b, v.E[0]);
-    for_own(b, [&](int row, int col) {
-      const int p = row * n + col;
-      double bp;
-      if (first) {
-        bp = rhs_at(P, t, bsrc, dsrc, p, p);
-        if (dsrc) w.bd[p] = bp;
-        bb += bp * bp;
-      } else {
-        bp = dsrc ? w.bd[p] : (bsrc ? bsrc[p] : 0.0);
+    const bool has_x = xa || !first;
+    for (int row = b.r0 + b.warp; row < b.r1; row += b.nwarp) {
+#pragma unroll
+      for (int j0 = 0; j0 < FAST_NJ; j0 += FAST_G) {
+        // loads of the chunks first (rhs, and x + c at the node and its four
+        // neighbours, c from the band with halos), then the stores
+        double bpv[FAST_G], xcen[FAST_G], xnb[FAST_G];
+#pragma unroll
+        for (int j = j0; j < j0 + FAST_G; ++j) {
+          const int col = b.lane + 32 * j;
+          if (col < n) {
+            const int p = row * n + col;
+            if (first)
+              bpv[j - j0] = rhs_at(P, t, bsrc, dsrc, p, p);
+            else
+              bpv[j - j0] = dsrc ? w.bd[p] : (bsrc ? bsrc[p] : 0.0);
+            if (has_x) {
+              auto xc = [&](int rr_, int cc_) -> double {
+                if (rr_ < 0 || rr_ >= n || cc_ < 0 || cc_ >= n) return 0.0;
+                double s = xa ? xa[rr_ * n + cc_] : 0.0;
+                if (!first) s += (double)s_fb[v.X + bidx(b, b.r0, rr_, cc_)] * inv_sc_c;
+                return s;
+              };
+              xcen[j - j0] = xc(row, col);
+              xnb[j - j0] = xc(row, col - 1) + xc(row, col + 1) + xc(row - 1, col) + xc(row + 1, col);
+            } else {
+              xcen[j - j0] = 0.0;
+              xnb[j - j0] = 0.0;
+            }
+          }
+        }
+#pragma unroll
+        for (int j = j0; j < j0 + FAST_G; ++j) {
+          const int col = b.lane + 32 * j;
+          if (col < n) {
+            const int p = row * n + col;
+            const double bp = bpv[j - j0];
+            if (first) {
+              if (dsrc) w.bd[p] = bp;
+              bb += bp * bp;
+            }
+            const double ax = has_x ? dd * xcen[j - j0] - ch2d * xnb[j - j0] : 0.0;
+            const double rd = bp - ax;
+            tgt[p] = xcen[j - j0];
+            const float rf = (float)(rd * sc);
+            bstore(b, Ra, row, col, rf);
+            const float e = scale0 * rf * dinvf;
+            bstore(b, Ea, row, col, e);
+            rr += rd * rd;
+            if (op.L == 1) rz1 += (double)(rf * e);
+          }
+        }
       }
-      // x + c at the node and its four neighbours (c from the band, halos included)
-      auto xc = [&](int rr_, int cc_) -> double {
-        if (rr_ < 0 || rr_ >= n || cc_ < 0 || cc_ >= n) return 0.0;
-        double s = xa ? xa[rr_ * n + cc_] : 0.0;
-        if (!first) s += (double)v.X[bidx(b, b.r0, rr_, cc_)] * inv_sc_c;
-        return s;
-      };
-      double ax = 0.0, xcen = 0.0;
-      if (xa || !first) {
-        xcen = xc(row, col);
-        ax = dd * xcen - ch2d * (xc(row, col - 1) + xc(row, col + 1) + xc(row - 1, col) + xc(row + 1, col));
-      }
-      const double rd = bp - ax;
-      tgt[p] = xcen;
-      const float rf = (float)(rd * sc);
-      bstore(b, Ra, row, col, rf);
-      const float e = scale0 * rf * dinvf;
-      bstore(b, Ea, row, col, e);
-      rr += rd * rd;
-      if (op.L == 1) rz1 += (double)(rf * e);
-    });
+    }
     SEC_ADD(SEC_REFINE);
     contribute(t, SL_RRD, rr);
     if (first) contribute(t, SL_BBD, bb);
@@ -450,7 +610,8 @@ __device__ double* fast_solve(const Team& t, const Band& b, const SweepParams& P
     if (first) {
       bbt = total(t, SL_BBD);
       if (!(bbt > 0.0)) {
-        for_own(b, [&](int row, int col) { tgt[row * n + col] = 0.0; });
+        for (int row = b.r0 + b.warp; row < b.r1; row += b.nwarp)
+          for (int col = b.lane; col < n; col += 32) tgt[row * n + col] = 0.0;
         done = true;
       }
       ctr.mix_scale = pow2_inv(sqrt(bbt * inv_n));
@@ -481,10 +642,9 @@ __device__ double* fast_solve(const Team& t, const Band& b, const SweepParams& P
   return tgt;
 }
 
-__global__ void __launch_bounds__(512, 1) fast2d_kernel(const SweepParams P) {
+__global__ void __launch_bounds__(FAST_THREADS, 1) fast2d_kernel(const SweepParams P) {
   __shared__ double s_red[2 * NSLOT * LRP_MAXBV];
   __shared__ double s_redw[32 * LRP_MAXBV];
-  extern __shared__ __align__(16) unsigned char s_dyn[];
   Team t;
   t.C = P.C;
   t.rank = (P.C > 1) ? (int)cg::this_cluster().block_rank() : 0;
@@ -518,20 +678,19 @@ __global__ void __launch_bounds__(512, 1) fast2d_kernel(const SweepParams P) {
   b.nwarp = t.NT >> 5;
   // band arrays (each with one leading zero pad element) and coarse levels
   FastVec v;
-  float* fb = (float*)s_dyn;
   const int band_len = P.fast_band_len;
-  v.E[0] = fb + 0 * band_len + 1;
-  v.E[1] = fb + 1 * band_len + 1;
-  v.R = fb + 2 * band_len + 1;
-  v.P = fb + 3 * band_len + 1;
-  v.Q = fb + 4 * band_len + 1;
-  v.X = fb + 5 * band_len + 1;
-  for (size_t i = t.tid; i < P.smem_bytes / sizeof(float); i += t.NT) fb[i] = 0.f;
-  SmemLv<float> sm;
+  v.E[0] = 0 * band_len + 1;
+  v.E[1] = 1 * band_len + 1;
+  v.R = 2 * band_len + 1;
+  v.P = 3 * band_len + 1;
+  v.Q = 4 * band_len + 1;
+  v.X = 5 * band_len + 1;
+  for (int i = t.tid; i < (int)(P.smem_bytes / sizeof(float)); i += t.NT) s_fb[i] = 0.f;
+  CLv sm;
   for (int l = 0; l < LRP_MAXLEV; ++l) {
-    sm.e[l][0] = (float*)(s_dyn + P.smem_off[l][0]);
-    sm.e[l][1] = (float*)(s_dyn + P.smem_off[l][1]);
-    sm.f[l] = (float*)(s_dyn + P.smem_off[l][2]);
+    sm.e[l][0] = (int)(P.smem_off[l][0] / sizeof(float));
+    sm.e[l][1] = (int)(P.smem_off[l][1] / sizeof(float));
+    sm.f[l] = (int)(P.smem_off[l][2] / sizeof(float));
   }
   // no neighbour may write into this CTA's halos before they are zeroed
   team_sync(t);
@@ -542,11 +701,14 @@ __global__ void __launch_bounds__(512, 1) fast2d_kernel(const SweepParams P) {
   w.obs = (double*)(base + P.off_obs);
   const int gcol = team;
   const bool valid = gcol < P.nvec;
-  const int N0 = n * n;
   Ctr ctr;
   int cur = (P.stages & ST_LOAD_X) ? 0 : min(max(P.end_buf[team], 0), 2);
+  auto for_own = [&](auto f) {
+    for (int row = b.r0 + b.warp; row < b.r1; row += b.nwarp)
+      for (int col = b.lane; col < n; col += 32) f(row, col);
+  };
   if (P.stages & ST_LOAD_X) {
-    for_own(b, [&](int row, int col) {
+    for_own([&](int row, int col) {
       const int p = row * n + col;
       w.dbuf[0][p] = valid ? P.X[(size_t)gcol * P.ldx + p] : 0.0;
     });
@@ -581,7 +743,7 @@ __global__ void __launch_bounds__(512, 1) fast2d_kernel(const SweepParams P) {
       }
       if ((P.stages & ST_TRAJ) && valid) {
         double* dst = P.traj + ((size_t)gcol * P.traj_cols + (step - P.t_begin - 1)) * P.traj_ld;
-        for_own(b, [&](int row, int col) { dst[row * n + col] = res[row * n + col]; });
+        for_own([&](int row, int col) { dst[row * n + col] = res[row * n + col]; });
       }
     }
     team_sync(t);
@@ -598,7 +760,7 @@ __global__ void __launch_bounds__(512, 1) fast2d_kernel(const SweepParams P) {
     if (q) {
       cur = buf_index(w.dbuf, q);
     } else {
-      for_own(b, [&](int row, int col) { w.dbuf[cur][row * n + col] = 0.0; });
+      for_own([&](int row, int col) { w.dbuf[cur][row * n + col] = 0.0; });
       team_sync(t);
     }
   }
@@ -608,7 +770,7 @@ __global__ void __launch_bounds__(512, 1) fast2d_kernel(const SweepParams P) {
     cur = buf_index(w.dbuf, res);
   }
   if ((P.stages & ST_STORE_Y) && valid) {
-    for_own(b, [&](int row, int col) {
+    for_own([&](int row, int col) {
       const int p = row * n + col;
       P.Y[(size_t)gcol * P.ldy + p] = w.dbuf[cur][p];
     });

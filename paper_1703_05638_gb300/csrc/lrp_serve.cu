@@ -17,6 +17,10 @@
 // request's result does not depend on the batch it was served in beyond the
 // solver tolerance.
 //
+// Pointwise variance uses the prior diagonal at every node, computed once
+// per model from the sine-transform closed form of (I + alpha L0)^-2 and
+// kept with the factors.
+//
 // Memory. The server accounts every device byte it holds (factors, problem
 // handles with their workspaces, batch scratch) against hbm_budget. A model
 // whose factors are not resident is admitted by evicting the least recently
@@ -75,11 +79,6 @@ __global__ void k_add_owner_cols(int nx, int ncols, const double* M, int ldm, co
   S[(size_t)j * lds + p] += M[(size_t)owner[j] * ldm + p];
 }
 
-__global__ void k_scatter(int n, const int* idx, const double* v, double* out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[idx[i]] = v[i];
-}
-
 // var[i] = prior_diag[node_i] - sum_j d_j(s_req(i)) G[node_i, j]^2
 __global__ void k_variance_batch(int np, const int* nodes, const int* req, const double* s, const double* pdiag,
                                  int k, const double* lam, const double* G, int ldg, double* var) {
@@ -126,14 +125,13 @@ struct SlotModel {
   size_t bytes = 0;  // device bytes accounted (problem + workspace + scratch)
   int B = 0, NS = 0, NP = 0, CH = 0, nx = 0, nd = 0, k = 0;
   double *y = nullptr, *zx = nullptr, *out = nullptr, *coef = nullptr, *part = nullptr, *scal = nullptr,
-         *var = nullptr, *diag = nullptr, *norms = nullptr;
+         *var = nullptr;
   size_t part_cap = 0;
-  int *nodes = nullptr, *req = nullptr, *owner = nullptr, *miss = nullptr;
-  std::vector<char> known;  // prior diagonal already computed at this node
+  int *nodes = nullptr, *req = nullptr, *owner = nullptr;
   // pinned host staging
   double *h_y = nullptr, *h_xi = nullptr, *h_mean = nullptr, *h_samp = nullptr, *h_var = nullptr,
          *h_scal = nullptr;
-  int *h_nodes = nullptr, *h_req = nullptr, *h_owner = nullptr, *h_miss = nullptr;
+  int *h_nodes = nullptr, *h_req = nullptr, *h_owner = nullptr;
   std::vector<void*> dev, host;
 
   ~SlotModel() {
@@ -165,16 +163,16 @@ struct Model {
   int nx = 0, n_data = 0, k = 0;
   double sigma0 = 0.0;
   // pinned host copies of the factors (always kept)
-  double *h_lam = nullptr, *h_V = nullptr, *h_G = nullptr;
-  // device copies while resident
-  double *d_lam = nullptr, *d_V = nullptr, *d_G = nullptr;
+  double *h_lam = nullptr, *h_V = nullptr, *h_G = nullptr, *h_diag = nullptr;
+  // device copies while resident (d_diag: prior variance at every node)
+  double *d_lam = nullptr, *d_V = nullptr, *d_G = nullptr, *d_diag = nullptr;
   size_t factor_bytes = 0;
   size_t handle_bytes = 0;  // measured bytes of one worker handle for this model
   int in_use = 0;
   double last_used = 0.0;
   std::deque<Request*> pending;
   long long admissions = 0, evictions = 0;
-  bool resident() const { return d_V != nullptr || k == 0; }
+  bool resident() const { return d_V != nullptr; }
 };
 
 }  // namespace
@@ -232,12 +230,9 @@ lrp_status slot_model_create(lrp_server* S, cudaStream_t s, Model& m, std::uniqu
   SA(h->dalloc(&h->part, h->part_cap));
   SA(h->dalloc(&h->scal, (size_t)h->B + cols));
   SA(h->dalloc(&h->var, (size_t)h->B * h->NP));
-  SA(h->dalloc(&h->diag, (size_t)m.nx));
-  SA(h->dalloc(&h->norms, (size_t)cols));
   SA(h->dalloc(&h->nodes, (size_t)h->B * h->NP));
   SA(h->dalloc(&h->req, (size_t)h->B * h->NP));
   SA(h->dalloc(&h->owner, (size_t)cols));
-  SA(h->dalloc(&h->miss, (size_t)h->B * h->NP));
   SA(h->halloc(&h->h_y, (size_t)m.n_data * h->B));
   SA(h->halloc(&h->h_xi, (size_t)m.nx * h->B * h->NS));
   SA(h->halloc(&h->h_mean, (size_t)m.nx * h->B));
@@ -247,7 +242,6 @@ lrp_status slot_model_create(lrp_server* S, cudaStream_t s, Model& m, std::uniqu
   SA(h->halloc(&h->h_nodes, (size_t)h->B * h->NP));
   SA(h->halloc(&h->h_req, (size_t)h->B * h->NP));
   SA(h->halloc(&h->h_owner, (size_t)cols));
-  SA(h->halloc(&h->h_miss, (size_t)h->B * h->NP));
   // grow the sweep workspace to the widest batch now: a zero block solves
   // at once, and later batches never reallocate it
   SA(cudaMemsetAsync(h->zx, 0, (size_t)m.nx * cols * sizeof(double), s));
@@ -258,7 +252,6 @@ lrp_status slot_model_create(lrp_server* S, cudaStream_t s, Model& m, std::uniqu
   st = run_sweep(P, ST_LOAD_D | ST_ADJOINT | ST_PRIOR_OUT | ST_STORE_Y, h->B, nullptr, 0, h->zx, m.nx, h->y,
                  m.n_data, nullptr, 0, nullptr, false);
   if (st != LRP_OK) return st;
-  h->known.assign(m.nx, 0);
   h->bytes += P->dev_bytes + P->ws_bytes;
 #undef SA
   out = std::move(h);
@@ -269,7 +262,8 @@ void factors_free(lrp_server* S, Model& m) {
   if (m.d_V) cudaFree(m.d_V);
   if (m.d_G) cudaFree(m.d_G);
   if (m.d_lam) cudaFree(m.d_lam);
-  m.d_V = m.d_G = m.d_lam = nullptr;
+  if (m.d_diag) cudaFree(m.d_diag);
+  m.d_V = m.d_G = m.d_lam = m.d_diag = nullptr;
   S->used -= m.factor_bytes;
 }
 
@@ -307,12 +301,10 @@ bool make_room(lrp_server* S, size_t need, const Model* keep) {
 // h_scal / scal layout: [0, B) data weights 1/sigma_r^2; [B, B + R + NSt)
 // eigenvalue scalings sigma0^2/sigma^2 of the mean columns, then of the
 // sample columns.
-lrp_status serve_batch_inner(lrp_server* S, int w, Model& m, SlotModel& h, std::vector<Request*>& batch,
-                             int& nmiss) {
+lrp_status serve_batch(lrp_server* S, int w, Model& m, SlotModel& h, std::vector<Request*>& batch) {
   cudaStream_t s = S->streams[w];
   const int R = (int)batch.size(), nx = m.nx, nd = m.n_data, k = m.k, B = h.B;
   lrp_problem* P = h.P;
-  nmiss = 0;
 #define SK(x)                                                 \
   do {                                                        \
     cudaError_t e_ = (x);                                     \
@@ -394,8 +386,7 @@ lrp_status serve_batch_inner(lrp_server* S, int w, Model& m, SlotModel& h, std::
       SK(cudaMemcpyAsync(h.h_samp, h.out + (size_t)R * nx, (size_t)NSt * nx * sizeof(double),
                          cudaMemcpyDeviceToHost, s));
   }
-  // pointwise variance: prior diagonal at nodes this handle has not seen
-  // (batched unit solves), then the SMW correction
+  // pointwise variance: prior diagonal minus the low-rank correction
   int NPt = 0;
   for (int r = 0; r < R; ++r) {
     const Request* q = batch[r];
@@ -404,32 +395,13 @@ lrp_status serve_batch_inner(lrp_server* S, int w, Model& m, SlotModel& h, std::
       h.h_nodes[NPt] = v;
       h.h_req[NPt] = r;
       ++NPt;
-      if (!h.known[v]) {
-        h.known[v] = 2;  // pending in this batch
-        h.h_miss[nmiss++] = v;
-      }
     }
   }
   if (NPt > 0) {
-    if (nmiss > 0) {
-      SK(cudaMemcpyAsync(h.miss, h.h_miss, nmiss * sizeof(int), cudaMemcpyHostToDevice, s));
-      // the unit columns reuse the batch buffers, which hold no live data now
-      // (the mean and sample copies above are ordered before this on s)
-      for (int i0 = 0; i0 < nmiss; i0 += h.CH) {
-        const int nc = std::min(h.CH, nmiss - i0);
-        SK(unit_cols(s, nx, nc, h.miss, i0, h.zx, nx));
-        SS(run_sweep(P, ST_LOAD_X | ST_PRIOR_IN | ST_STORE_Y, nc, h.zx, nx, h.out, nx, nullptr, 0, nullptr, 0,
-                     nullptr, false));
-        SK(col_norm2(s, nx, nc, h.out, nx, h.norms));
-        note_launch();
-        k_scatter<<<nblk(nc), 256, 0, s>>>(nc, h.miss + i0, h.norms, h.diag);
-        SK(cudaGetLastError());
-      }
-    }
     SK(cudaMemcpyAsync(h.nodes, h.h_nodes, NPt * sizeof(int), cudaMemcpyHostToDevice, s));
     SK(cudaMemcpyAsync(h.req, h.h_req, NPt * sizeof(int), cudaMemcpyHostToDevice, s));
     note_launch();
-    k_variance_batch<<<nblk(NPt), 256, 0, s>>>(NPt, h.nodes, h.req, h.scal + B, h.diag, k, m.d_lam, m.d_G, nx,
+    k_variance_batch<<<nblk(NPt), 256, 0, s>>>(NPt, h.nodes, h.req, h.scal + B, m.d_diag, k, m.d_lam, m.d_G, nx,
                                                 h.var);
     SK(cudaGetLastError());
     SK(cudaMemcpyAsync(h.h_var, h.var, NPt * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -453,17 +425,6 @@ lrp_status serve_batch_inner(lrp_server* S, int w, Model& m, SlotModel& h, std::
 #undef SK
 #undef SS
   return LRP_OK;
-}
-
-lrp_status serve_batch(lrp_server* S, int w, Model& m, SlotModel& h, std::vector<Request*>& batch) {
-  int nmiss = 0;
-  const lrp_status st = serve_batch_inner(S, w, m, h, batch, nmiss);
-  // prior-diagonal entries computed by this batch become valid only if it
-  // completed; otherwise they are computed again next time
-  const char mark = st == LRP_OK ? 1 : 0;
-  if (st != LRP_OK) cudaStreamSynchronize(S->streams[w]);
-  for (int i = 0; i < nmiss; ++i) h.known[h.h_miss[i]] = mark;
-  return st;
 }
 
 void worker_main(lrp_server* S, int w) {
@@ -519,19 +480,23 @@ void worker_main(lrp_server* S, int w) {
     if (!m->resident()) {
       admitted = 1;
       const size_t vk = (size_t)m->nx * m->k * sizeof(double);
-      double *dV = nullptr, *dG = nullptr, *dl = nullptr;
-      cudaError_t e = cudaMalloc(&dV, vk);
-      if (e == cudaSuccess) e = cudaMalloc(&dG, vk);
-      if (e == cudaSuccess) e = cudaMalloc(&dl, m->k * sizeof(double));
+      double *dV = nullptr, *dG = nullptr, *dl = nullptr, *dd = nullptr;
+      cudaError_t e = cudaMalloc(&dV, std::max<size_t>(vk, 8));
+      if (e == cudaSuccess) e = cudaMalloc(&dG, std::max<size_t>(vk, 8));
+      if (e == cudaSuccess) e = cudaMalloc(&dl, std::max(m->k, 1) * sizeof(double));
+      if (e == cudaSuccess) e = cudaMalloc(&dd, (size_t)m->nx * sizeof(double));
       if (e == cudaSuccess) e = cudaMemcpyAsync(dV, m->h_V, vk, cudaMemcpyHostToDevice, S->streams[w]);
       if (e == cudaSuccess) e = cudaMemcpyAsync(dG, m->h_G, vk, cudaMemcpyHostToDevice, S->streams[w]);
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(dl, m->h_lam, m->k * sizeof(double), cudaMemcpyHostToDevice, S->streams[w]);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dd, m->h_diag, (size_t)m->nx * sizeof(double), cudaMemcpyHostToDevice, S->streams[w]);
       if (e == cudaSuccess) e = cudaStreamSynchronize(S->streams[w]);
       if (e == cudaSuccess) {
         m->d_V = dV;
         m->d_G = dG;
         m->d_lam = dl;
+        m->d_diag = dd;
         S->used += m->factor_bytes;
         m->admissions++;
       } else {
@@ -541,6 +506,7 @@ void worker_main(lrp_server* S, int w) {
         if (dV) cudaFree(dV);
         if (dG) cudaFree(dG);
         if (dl) cudaFree(dl);
+        if (dd) cudaFree(dd);
       }
     }
     SlotModel* h = nullptr;
@@ -686,13 +652,25 @@ lrp_status lrp_server_add_model(lrp_server* S, const lrp_problem_desc* d, int k,
   }
   m->k = post->k;
   const size_t vk = (size_t)m->nx * m->k * sizeof(double);
-  m->factor_bytes = 2 * vk + m->k * sizeof(double);
+  m->factor_bytes = 2 * std::max<size_t>(vk, 8) + std::max(m->k, 1) * sizeof(double) + (size_t)m->nx * sizeof(double);
   e = cudaMallocHost(&m->h_V, std::max<size_t>(vk, 8));
   if (e == cudaSuccess) e = cudaMallocHost(&m->h_G, std::max<size_t>(vk, 8));
   if (e == cudaSuccess) e = cudaMallocHost(&m->h_lam, std::max<size_t>(m->k, 1) * sizeof(double));
   if (e == cudaSuccess && m->k) e = cudaMemcpy(m->h_V, post->V, vk, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && m->k) e = cudaMemcpy(m->h_G, post->G, vk, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && m->k) e = cudaMemcpy(m->h_lam, post->lambda, m->k * sizeof(double), cudaMemcpyDeviceToHost);
+  // prior variance at every node (sine-transform closed form)
+  if (e == cudaSuccess) e = cudaMallocHost(&m->h_diag, (size_t)m->nx * sizeof(double));
+  if (e == cudaSuccess) {
+    double* dwork = nullptr;
+    const size_t nwork = (size_t)d->n * d->n + 3 * (size_t)m->nx;
+    e = cudaMalloc(&dwork, nwork * sizeof(double));
+    if (e == cudaSuccess) e = prior_diag_dst(s, dim, d->n, d->prior_alpha, dwork + nwork - m->nx, dwork);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(m->h_diag, dwork + nwork - m->nx, (size_t)m->nx * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (dwork) cudaFree(dwork);
+  }
   lrp_posterior_destroy(post);
   lrp_problem_destroy(P);
   if (e != cudaSuccess) {
@@ -868,6 +846,7 @@ void lrp_server_destroy(lrp_server* S) {
     if (m->h_V) cudaFreeHost(m->h_V);
     if (m->h_G) cudaFreeHost(m->h_G);
     if (m->h_lam) cudaFreeHost(m->h_lam);
+    if (m->h_diag) cudaFreeHost(m->h_diag);
   }
   for (auto& s : S->streams) cudaStreamDestroy(s);
   delete S;

@@ -153,7 +153,8 @@ lrp_status run_sweep_ex(lrp_problem* Pr, unsigned stages, int nvec, const double
   // Band kernel (2D, kappa = 1, one column per team, FP32 inner): every CTA
   // keeps its band of the finest level and all coarse levels in shared memory.
   bool fast = false;
-  if (Pr->kernel_variant != 1 && Pr->dim == 2 && mixed && BV == 1 && !Pr->step.has_kappa && Pr->L >= 2) {
+  if (Pr->kernel_variant != 1 && Pr->dim == 2 && mixed && BV == 1 && !Pr->step.has_kappa && Pr->L >= 2 &&
+      Pr->n <= 128) {
     const int n = Pr->n;
     for (int Cf = C; Cf >= 1; Cf >>= 1) {
       if (n / Cf < FAST_HALO_ROWS) continue;

@@ -62,7 +62,7 @@ struct SmemLv {
 // the prolongation back to level Ls-1 (all copies are bit-identical). On exit
 // z = e[0][returned index] and the team total r.z is in slot SL_RZ.
 template <typename T, int DIM, bool KAPPA>
-__device__ int vcycle(const Team& t, const Op& op, const WSV<T>& w, const SmemLv<T>& sm, T omega, int nu) {
+__device__ LRP_SOLVER_FN int vcycle(const Team& t, const Op& op, const WSV<T>& w, const SmemLv<T>& sm, T omega, int nu) {
   int ecur[LRP_MAXLEV];
   for (int l = 0; l < LRP_MAXLEV; ++l) ecur[l] = 0;
   const int L = op.L;
@@ -152,7 +152,7 @@ __device__ int vcycle(const Team& t, const Op& op, const WSV<T>& w, const SmemLv
 // thread's column is already converged. Updates xt (+= alpha p; = alpha p on
 // the first iteration if zero_init).
 template <typename T, typename TX, int DIM, bool KAPPA>
-__device__ void pcg_iterate(const Team& t, const Op& op, const WSV<T>& w, const SmemLv<T>& sm, TX* xt,
+__device__ LRP_SOLVER_FN void pcg_iterate(const Team& t, const Op& op, const WSV<T>& w, const SmemLv<T>& sm, TX* xt,
                             bool zero_init,
                             double tol2bb, bool& done, const SolveCfg& cfg, T omega, T scale0,
                             Ctr& ctr, double& rr_last) {
@@ -170,24 +170,31 @@ __device__ void pcg_iterate(const Team& t, const Op& op, const WSV<T>& w, const 
     double pq = 0.0;
     {
       Ld<T> ld{z, t.bvs, t.col};
-      for (int it = t.g; it < items; it += t.S) {
-        const int p = it >> t.bvs;
-        int i0, i1, i2;
-        decomp<DIM>(l0, p, i0, i1, i2);
-        T d;
-        const T az = op_at<T, DIM, KAPPA>(l0, ld, p, i0, i1, i2, d);
-        T pv, qv;
-        if (it_count == 0) {
-          pv = z[it];
-          qv = az;
-        } else {
-          pv = z[it] + beta * w.p[it];
-          qv = az + beta * w.q[it];
-        }
-        w.p[it] = pv;
-        w.q[it] = qv;
-        pq += (double)(pv * qv);
-      }
+      T pqp = T(0);  // per-thread partial in the inner type
+      batched_loop<V2<T>>(
+          t.g, items, t.S,
+          [&](int it) {
+            const int p = it >> t.bvs;
+            int i0, i1, i2;
+            decomp<DIM>(l0, p, i0, i1, i2);
+            T d;
+            const T az = op_at<T, DIM, KAPPA>(l0, ld, p, i0, i1, i2, d);
+            V2<T> r;
+            if (it_count == 0) {
+              r.a = z[it];
+              r.b = az;
+            } else {
+              r.a = z[it] + beta * w.p[it];
+              r.b = az + beta * w.q[it];
+            }
+            return r;
+          },
+          [&](int it, const V2<T>& r) {
+            w.p[it] = r.a;
+            w.q[it] = r.b;
+            pqp += r.a * r.b;
+          });
+      pq = (double)pqp;
     }
     contribute(t, SL_PQ, pq);
     team_sync(t);
@@ -195,18 +202,32 @@ __device__ void pcg_iterate(const Team& t, const Op& op, const WSV<T>& w, const 
     const T alpha = (T)((done || !(pqt > 0.0)) ? 0.0 : rz / pqt);
     // phase B: x += alpha p, r -= alpha q, first smoother sweep of the next V-cycle
     double rr = 0.0, rz1 = 0.0;
-    for (int it = t.g; it < items; it += t.S) {
-      const int p = it >> t.bvs;
-      if (zero_init && it_count == 0)
-        xt[it] = (TX)(alpha * w.p[it]);
-      else
-        xt[it] += (TX)(alpha * w.p[it]);
-      const T rv = w.f[0][it] - alpha * w.q[it];
-      w.f[0][it] = rv;
-      rr += (double)(rv * rv);
-      const T e = scale0 * rv * dinv_at<T, KAPPA>(l0, p);
-      w.e[0][0][it] = e;
-      if (op.L == 1) rz1 += (double)(rv * e);
+    {
+      T rrp = T(0), rz1p = T(0);
+      const bool fresh = zero_init && it_count == 0;
+      struct XRE {
+        TX x;
+        T r, e;
+      };
+      batched_loop<XRE>(
+          t.g, items, t.S,
+          [&](int it) {
+            const int p = it >> t.bvs;
+            XRE v;
+            v.x = fresh ? (TX)(alpha * w.p[it]) : (TX)(xt[it] + (TX)(alpha * w.p[it]));
+            v.r = w.f[0][it] - alpha * w.q[it];
+            v.e = scale0 * v.r * dinv_at<T, KAPPA>(l0, p);
+            return v;
+          },
+          [&](int it, const XRE& v) {
+            xt[it] = v.x;
+            w.f[0][it] = v.r;
+            rrp += v.r * v.r;
+            w.e[0][0][it] = v.e;
+            if (op.L == 1) rz1p += v.r * v.e;
+          });
+      rr = (double)rrp;
+      rz1 = (double)rz1p;
     }
     contribute(t, SL_RR, rr);
     if (op.L == 1) contribute(t, SL_RZ, rz1);
@@ -242,7 +263,7 @@ __device__ __forceinline__ double rhs_at(const SweepParams& P, const Team& t, co
 // Solve (I + c L) x = b in FP64 (x0 = warm start or NULL = 0). Returns the
 // index (in w.dbuf) of the solution buffer X1.
 template <int DIM, bool KAPPA>
-__device__ double* solve_fp64(const Team& t, const SweepParams& P, const Op& op,
+__device__ LRP_SOLVER_FN double* solve_fp64(const Team& t, const SweepParams& P, const Op& op,
                               const WSV<double>& w, const SmemLv<double>& sm, const double* bsrc,
                               const double* dsrc, const double* x0, double* X1, Ctr& ctr) {
   const OpLevel& l0 = op.lv[0];
@@ -298,7 +319,7 @@ __device__ double* solve_fp64(const Team& t, const SweepParams& P, const Op& op,
 // of refinement k-1 (the inner solve reduces it by about inner_rtol); that of
 // the first refinement from the previous solve's right-hand side.
 template <int DIM, bool KAPPA>
-__device__ double* solve_mixed(const Team& t, const SweepParams& P, const Op& op,
+__device__ LRP_SOLVER_FN double* solve_mixed(const Team& t, const SweepParams& P, const Op& op,
                                const WSV<float>& w, const SmemLv<float>& sm, const double* bsrc,
                                const double* dsrc, const double* x0, double* X1, double* X2,
                                Ctr& ctr) {
@@ -319,30 +340,40 @@ __device__ double* solve_mixed(const Team& t, const SweepParams& P, const Op& op
     const bool first = (ref == 0);
     double rr = 0.0, bb = 0.0, rz1 = 0.0;
     LdSum<float> ls{xa, first ? (const float*)nullptr : w.c, t.bvs, t.col, inv_sc_c};
-    for (int it = t.g; it < items; it += t.S) {
-      const int p = it >> t.bvs;
-      int i0, i1, i2;
-      decomp<DIM>(l0, p, i0, i1, i2);
-      double bp;
-      if (first) {
-        bp = rhs_at(P, t, bsrc, dsrc, p, it);
-        if (dsrc) w.bd[it] = bp;
-        bb += bp * bp;
-      } else {
-        bp = dsrc ? w.bd[it] : (bsrc ? bsrc[it] : 0.0);
-      }
-      double d, ax = 0.0;
-      if (xa || !first)
-        ax = op_at<double, DIM, KAPPA>(l0, ls, p, i0, i1, i2, d);
-      const double rd = bp - ax;
-      tgt[it] = ls(p);
-      const float rf = (float)(rd * sc);
-      w.f[0][it] = rf;
-      const float e = scale0 * rf * dinv_at<float, KAPPA>(l0, p);
-      w.e[0][0][it] = e;
-      rr += rd * rd;
-      if (op.L == 1) rz1 += (double)(rf * e);
-    }
+    struct Ref {
+      double bp, rd, x;
+    };
+    batched_loop<Ref>(
+        t.g, items, t.S,
+        [&](int it) {
+          const int p = it >> t.bvs;
+          int i0, i1, i2;
+          decomp<DIM>(l0, p, i0, i1, i2);
+          Ref v;
+          if (first)
+            v.bp = rhs_at(P, t, bsrc, dsrc, p, it);
+          else
+            v.bp = dsrc ? w.bd[it] : (bsrc ? bsrc[it] : 0.0);
+          double d, ax = 0.0;
+          if (xa || !first) ax = op_at<double, DIM, KAPPA>(l0, ls, p, i0, i1, i2, d);
+          v.rd = v.bp - ax;
+          v.x = ls(p);
+          return v;
+        },
+        [&](int it, const Ref& v) {
+          const int p = it >> t.bvs;
+          if (first) {
+            if (dsrc) w.bd[it] = v.bp;
+            bb += v.bp * v.bp;
+          }
+          tgt[it] = v.x;
+          const float rf = (float)(v.rd * sc);
+          w.f[0][it] = rf;
+          const float e = scale0 * rf * dinv_at<float, KAPPA>(l0, p);
+          w.e[0][0][it] = e;
+          rr += v.rd * v.rd;
+          if (op.L == 1) rz1 += (double)(rf * e);
+        });
     contribute(t, SL_RRD, rr);
     if (first) contribute(t, SL_BBD, bb);
     if (op.L == 1) contribute(t, SL_RZ, rz1);

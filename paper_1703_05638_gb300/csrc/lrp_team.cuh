@@ -204,6 +204,50 @@ __device__ __forceinline__ T diag_at(const OpLevel& lv, int p, int i0, int i1, i
   return T(1) + (T)lv.ch2 * kd;
 }
 
+// Grid-stride loop over items [start, items) that handles LRP_UNROLL items
+// per round: compute(it) performs every load and the arithmetic of item it
+// and returns its values, commit(it, v) performs the stores (and any
+// accumulation, in item order). All loads of a round are issued before its
+// first store, so a thread keeps several items' loads in flight (a store
+// could alias later loads, so the compiler would not overlap them itself).
+#ifndef LRP_UNROLL
+#define LRP_UNROLL 2
+#endif
+// The solver levels (V-cycle, PCG, refinement) are separate functions with
+// their own register allocation unless LRP_INLINE_SOLVER is defined: inlined
+// into the one persistent kernel they share one 128-register budget, and the
+// batched loops would spill.
+#ifdef LRP_INLINE_SOLVER
+#define LRP_SOLVER_FN
+#else
+#define LRP_SOLVER_FN __noinline__
+#endif
+template <class V, class Compute, class Commit>
+__device__ __forceinline__ void batched_loop(int start, int items, int stride, Compute compute, Commit commit) {
+  for (int it0 = start; it0 < items; it0 += LRP_UNROLL * stride) {
+    V v[LRP_UNROLL];
+#pragma unroll
+    for (int u = 0; u < LRP_UNROLL; ++u) {
+      const int it = it0 + u * stride;
+      if (it < items) v[u] = compute(it);
+    }
+#pragma unroll
+    for (int u = 0; u < LRP_UNROLL; ++u) {
+      const int it = it0 + u * stride;
+      if (it < items) commit(it, v[u]);
+    }
+  }
+}
+
+template <typename T>
+struct V2 {
+  T a, b;
+};
+template <typename T>
+struct V3 {
+  T a, b, c;
+};
+
 // ---------------------------------------------------------------------------
 // Multigrid phases. Each works over items [start, N*BV) with the given
 // stride; the caller ends the phase with a team barrier (global levels) or
@@ -222,16 +266,25 @@ __device__ __forceinline__ void mg_sweep(const OpLevel& lv, T* eo,
                                          const T* rz_r, double& rz) {
   const int items = lv.N << bvs;
   Ld<T> ld{ei, bvs, col};
-  for (int it = start; it < items; it += stride) {
-    const int p = it >> bvs;
-    int i0, i1, i2;
-    decomp<DIM>(lv, p, i0, i1, i2);
-    T d;
-    const T ae = op_at<T, DIM, KAPPA>(lv, ld, p, i0, i1, i2, d);
-    const T e = ei[it] + omega * (f[it] - ae) * dinv_at<T, KAPPA>(lv, p);
-    eo[it] = e;
-    if (rz_r) rz += (double)(rz_r[it] * e);
-  }
+  T acc = T(0);  // per-thread partial in the inner type
+  batched_loop<V2<T>>(
+      start, items, stride,
+      [&](int it) {
+        const int p = it >> bvs;
+        int i0, i1, i2;
+        decomp<DIM>(lv, p, i0, i1, i2);
+        T d;
+        const T ae = op_at<T, DIM, KAPPA>(lv, ld, p, i0, i1, i2, d);
+        V2<T> r;
+        r.a = ei[it] + omega * (f[it] - ae) * dinv_at<T, KAPPA>(lv, p);
+        r.b = rz_r ? rz_r[it] : T(0);
+        return r;
+      },
+      [&](int it, const V2<T>& r) {
+        eo[it] = r.a;
+        if (rz_r) acc += r.b * r.a;
+      });
+  if (rz_r) rz += (double)acc;
 }
 
 // Restrict the residual f - A e of level l (fine) to level l+1 (coarse) by
@@ -245,29 +298,37 @@ __device__ __forceinline__ void mg_restrict(const OpLevel& lf, const OpLevel& lc
   const int items = lc.N << bvs;
   Ld<T> ld{ef, bvs, col};
   const int nf = lf.n;
-  for (int it = start; it < items; it += stride) {
-    const int P = it >> bvs;
-    int c0, c1, c2;
-    decomp<DIM>(lc, P, c0, c1, c2);
-    T acc = T(0);
-    const int z0 = (DIM == 3) ? -1 : 0, z1 = (DIM == 3) ? 1 : 0;
-    for (int dz = z0; dz <= z1; ++dz) {
-      for (int dy = -1; dy <= 1; ++dy) {
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int F0 = 2 * c0 + 1 + dx, F1 = 2 * c1 + 1 + dy;
-          const int F2 = (DIM == 3) ? 2 * c2 + 1 + dz : 0;
-          const int pf = F0 + nf * (F1 + nf * F2);
-          T d;
-          const T res = ff[(pf << bvs) + col] - op_at<T, DIM, KAPPA>(lf, ld, pf, F0, F1, F2, d);
-          T w = (dx == 0 ? T(0.5) : T(0.25)) * (dy == 0 ? T(0.5) : T(0.25));
-          if (DIM == 3) w *= (dz == 0 ? T(0.5) : T(0.25));
-          acc += w * res;
+  batched_loop<V2<T>>(
+      start, items, stride,
+      [&](int it) {
+        const int P = it >> bvs;
+        int c0, c1, c2;
+        decomp<DIM>(lc, P, c0, c1, c2);
+        T acc = T(0);
+        const int z0 = (DIM == 3) ? -1 : 0, z1 = (DIM == 3) ? 1 : 0;
+        for (int dz = z0; dz <= z1; ++dz) {
+          for (int dy = -1; dy <= 1; ++dy) {
+            for (int dx = -1; dx <= 1; ++dx) {
+              const int F0 = 2 * c0 + 1 + dx, F1 = 2 * c1 + 1 + dy;
+              const int F2 = (DIM == 3) ? 2 * c2 + 1 + dz : 0;
+              const int pf = F0 + nf * (F1 + nf * F2);
+              T d;
+              const T res = ff[(pf << bvs) + col] - op_at<T, DIM, KAPPA>(lf, ld, pf, F0, F1, F2, d);
+              T w = (dx == 0 ? T(0.5) : T(0.25)) * (dy == 0 ? T(0.5) : T(0.25));
+              if (DIM == 3) w *= (dz == 0 ? T(0.5) : T(0.25));
+              acc += w * res;
+            }
+          }
         }
-      }
-    }
-    fc[it] = acc;
-    ec[it] = scale * acc * dinv_at<T, KAPPA>(lc, P);
-  }
+        V2<T> r;
+        r.a = acc;
+        r.b = scale * acc * dinv_at<T, KAPPA>(lc, P);
+        return r;
+      },
+      [&](int it, const V2<T>& r) {
+        fc[it] = r.a;
+        ec[it] = r.b;
+      });
 }
 
 // e_out = e_in + P e_c (bi/trilinear interpolation, zero boundary); e_out
@@ -278,7 +339,7 @@ __device__ __forceinline__ void mg_prolong(const OpLevel& lf, const OpLevel& lc,
                                            int col, const T* ein = nullptr) {
   const int items = lf.N << bvs;
   const int nc = lc.n;
-  for (int it = start; it < items; it += stride) {
+  batched_loop<T>(start, items, stride, [&](int it) {
     const int p = it >> bvs;
     int F[3];
     decomp<DIM>(lf, p, F[0], F[1], F[2]);
@@ -308,8 +369,8 @@ __device__ __forceinline__ void mg_prolong(const OpLevel& lf, const OpLevel& lc,
         }
       }
     }
-    ef[it] = (ein ? ein[it] : ef[it]) + acc;
-  }
+    return (ein ? ein[it] : ef[it]) + acc;
+  }, [&](int it, T v) { ef[it] = v; });
 }
 
 }  // namespace lrp
