@@ -157,7 +157,7 @@ def serve_bench(lrp, count: int, rate_hz: float, budget_gib: float, slots: int, 
     reqs = synth.serving_requests(count=count, rate_hz=rate_hz)
     sizes = sorted({r["size"] for r in reqs})
     srv = lrp.Server(hbm_budget=int(budget_gib * (1 << 30)), slots=slots, max_batch=max_batch, max_samples=8,
-                     max_points=1024)
+                     max_points=1024, autotune=True)
     t0 = time.perf_counter()
     mids, pools, setup = {}, {}, {}
     for size in sizes:

@@ -196,14 +196,15 @@ lrp_status lrp_hessian_apply(lrp_problem* p, int nvec, const double* X, int ldx,
 lrp_status lrp_hessian_apply_noalloc(lrp_problem* p, int nvec, const double* X, int ldx,
                                      double* Y, int ldy, lrp_apply_stats* st);
 
-/* Autotuner for blocks of nvec columns. Round 1 times, for each candidate
- * cluster size, columns per cluster, smoothing sweeps and (LRP_MIXED) inner
- * tolerance, the prior solve and the first `steps` forward implicit-Euler
- * steps (0 -> 16); round 2 times one whole Hessian apply for the three
- * fastest. The winner stays in the problem handle for later calls. All
- * candidates iterate to the same tolerances. *best_ms (may be NULL) receives
- * the winner's Hessian-apply time. Allocates two nx x nvec blocks for the
- * duration of the call. No counterpart in the paper. */
+/* Autotuner for blocks of nvec columns. Round 1 times, for each cluster size
+ * (1..8, 12, 16 CTAs), CTA size (256 or 512 threads) and columns per cluster
+ * (1, 2), the prior solve and the first `steps` forward implicit-Euler steps
+ * (0 -> 16); round 2 varies the smoothing sweeps and (LRP_MIXED) the inner
+ * tolerance on the two best shapes; round 3 times one whole Hessian apply for
+ * the three best. The winner stays in the problem handle for later calls.
+ * All candidates iterate to the same tolerances. *best_ms (may be NULL)
+ * receives the winner's Hessian-apply time. Allocates two nx x nvec blocks
+ * for the duration of the call. No counterpart in the paper. */
 lrp_status lrp_autotune(lrp_problem* p, int nvec, int steps, double* best_ms);
 
 /* D = F U (no noise weighting): forward sweep and observation.
@@ -285,6 +286,7 @@ typedef struct lrp_tuning {
   int team_ctas, team_cols, mg_nu, mg_nu_coarse;
   double inner_rtol;
   int last_kernel, last_team_ctas;
+  int threads;  /* threads per CTA */
 } lrp_tuning;
 lrp_status lrp_problem_tuning(const lrp_problem* p, lrp_tuning* out);
 
@@ -317,6 +319,7 @@ typedef struct {
   int max_batch;      /* requests per batch; 0 -> 16, <= 256 */
   int max_samples;    /* largest n_samples of a request; 0 -> 8, <= 64 */
   int max_points;     /* largest n_points of a request; 0 -> 1024 */
+  int autotune;       /* 1: run lrp_autotune for max_batch columns on every model as it is added */
 } lrp_server_config;
 
 typedef struct {

@@ -71,7 +71,7 @@ class lrp_query_result(C.Structure):
 
 class lrp_server_config(C.Structure):
     _fields_ = [("hbm_budget", C.c_size_t), ("slots", C.c_int), ("max_batch", C.c_int),
-                ("max_samples", C.c_int), ("max_points", C.c_int)]
+                ("max_samples", C.c_int), ("max_points", C.c_int), ("autotune", C.c_int)]
 
 
 class lrp_request_stats(C.Structure):
@@ -93,7 +93,8 @@ class lrp_server_stats(C.Structure):
 
 class lrp_tuning(C.Structure):
     _fields_ = [("team_ctas", C.c_int), ("team_cols", C.c_int), ("mg_nu", C.c_int), ("mg_nu_coarse", C.c_int),
-                ("inner_rtol", C.c_double), ("last_kernel", C.c_int), ("last_team_ctas", C.c_int)]
+                ("inner_rtol", C.c_double), ("last_kernel", C.c_int), ("last_team_ctas", C.c_int),
+                ("threads", C.c_int)]
 
 
 EXPORTS = {
@@ -460,8 +461,9 @@ class Server:
     GPU; see lrp_server_* in lrp.h). Results come back as NumPy arrays."""
 
     def __init__(self, hbm_budget: int = 0, slots: int = 0, max_batch: int = 0, max_samples: int = 0,
-                 max_points: int = 0):
-        cfg = lrp_server_config(int(hbm_budget), int(slots), int(max_batch), int(max_samples), int(max_points))
+                 max_points: int = 0, autotune: bool = False):
+        cfg = lrp_server_config(int(hbm_budget), int(slots), int(max_batch), int(max_samples), int(max_points),
+                                int(bool(autotune)))
         h = C.c_void_p()
         _check(load().lrp_server_create(C.byref(cfg), C.byref(h)))
         self.handle = h

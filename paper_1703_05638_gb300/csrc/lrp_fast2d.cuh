@@ -24,10 +24,8 @@
 // Addressing: every shared-memory array is an offset (in floats) into the
 // kernel's dynamic shared memory, so local accesses are 32-bit shared-window
 // accesses, and the neighbours' copies are 32-bit cluster-window addresses
-// (mapa); this keeps the register footprint small enough for the hot loops to
-// load all inputs of a group of column chunks before their first store (a
-// store could alias the next point's inputs, so the compiler would otherwise
-// issue one point's loads at a time).
+// (mapa), which keeps address arithmetic in 32-bit registers. The hot loops
+// can load the inputs of FAST_G column chunks before their first store.
 #pragma once
 
 #include "lrp_sweep_kernel.cuh"
@@ -36,10 +34,12 @@ namespace lrp {
 
 constexpr int FAST_HALO = 2;
 constexpr int FAST_NJ = 4;  // column chunks per row a lane handles (col = lane + 32 j): n <= 128
+// Chunks whose loads are issued together: 2 spills registers and measured
+// 60% slower on GB300 than 1 (127^2, 16 columns), so 1 is the default.
 #ifndef LRP_FAST_G
-#define LRP_FAST_G 2
+#define LRP_FAST_G 1
 #endif
-constexpr int FAST_G = LRP_FAST_G;  // chunks whose loads are issued together
+constexpr int FAST_G = LRP_FAST_G;
 #ifndef LRP_FAST_THREADS
 #define LRP_FAST_THREADS 512
 #endif

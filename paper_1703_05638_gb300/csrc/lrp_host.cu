@@ -426,6 +426,7 @@ lrp_status lrp_problem_tuning(const lrp_problem* P, lrp_tuning* out) {
   out->inner_rtol = P->cfg.inner_rtol;
   out->last_kernel = P->last_kernel;
   out->last_team_ctas = P->last_team_ctas;
+  out->threads = P->nthreads;
   return LRP_OK;
 }
 
@@ -573,12 +574,14 @@ static lrp_status hessian_with_factors(lrp_problem* P, int nvec, const double* X
 
 extern "C" {
 
-// Autotuner, in two rounds on a pseudo-random block of nvec columns:
-// (1) every candidate launch shape and multigrid setting times the prior
-// solve and the first `steps` implicit-Euler steps of the forward sweep
-// (the smooth start the Hessian apply sees); (2) the three fastest time one
-// whole Hessian apply each, and the fastest of those is kept. Every
-// candidate iterates to the same tolerances, so the choice changes the
+// Autotuner, on a pseudo-random block of nvec columns. Round 1 (launch
+// shape): every cluster size C, CTA size and columns per cluster times the
+// prior solve and the first `steps` implicit-Euler steps of the forward sweep
+// (the smooth start the Hessian apply sees) with the problem's multigrid
+// settings. Round 2 (solver): the two fastest shapes time the same with each
+// smoothing-sweep count and (mixed path) inner tolerance. Round 3: the three
+// fastest of round 2 time one whole Hessian apply each; the fastest is kept.
+// Every candidate iterates to the same tolerances, so the choice changes the
 // speed, not the result beyond rounding.
 lrp_status lrp_autotune(lrp_problem* P, int nvec, int steps, double* best_ms) {
   if (!P || nvec < 1 || nvec > 4096) {
@@ -598,20 +601,11 @@ lrp_status lrp_autotune(lrp_problem* P, int nvec, int steps, double* best_ms) {
     return cuda_status(e, "autotune buffers");
   }
   struct Cand {
-    int C, BV, nu;
+    int C, NT, BV, nu;
     double inner, t1, t2;
   };
-  std::vector<Cand> cands;
   const bool mixed = P->desc.precision == LRP_MIXED;
-  for (int C : {1, 2, 4, 8, 16})
-    for (int BV : {1, 2, 4}) {
-      if (BV > nvec && BV > 1) continue;
-      if (C > 1 && (long long)P->nx / C < 256) continue;
-      for (int nu : {1, 2})
-        for (double inner : (mixed ? std::vector<double>{1e-4, 1e-5} : std::vector<double>{0.0}))
-          cands.push_back({C, BV, nu, inner, 1e300, 1e300});
-    }
-  const int save_C = P->team_ctas, save_BV = P->team_cols;
+  const int save_C = P->team_ctas, save_BV = P->team_cols, save_NT = P->nthreads;
   const SolveCfg save_cfg = P->cfg;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -619,6 +613,7 @@ lrp_status lrp_autotune(lrp_problem* P, int nvec, int steps, double* best_ms) {
   auto apply_cand = [&](const Cand& c) {
     P->team_ctas = c.C;
     P->team_cols = c.BV;
+    P->nthreads = c.NT;
     P->cfg = save_cfg;
     P->cfg.nu = c.nu;
     P->cfg.nu_coarse = c.nu;
@@ -639,11 +634,37 @@ lrp_status lrp_autotune(lrp_problem* P, int nvec, int steps, double* best_ms) {
     }
     *out = best_t;
   };
-  for (Cand& c : cands) {
+  auto by_t1 = [](const Cand& a, const Cand& b) { return a.t1 < b.t1; };
+  const unsigned screen = ST_LOAD_X | ST_PRIOR_IN | ST_FORWARD;
+  // round 1: launch shape
+  std::vector<Cand> shapes;
+  for (int C : {1, 2, 3, 4, 5, 6, 7, 8, 12, 16})
+    for (int NT : {512, 256})
+      for (int BV : {1, 2}) {
+        if (BV > nvec && BV > 1) continue;
+        if (C > 1 && (long long)P->nx / C < 256) continue;
+        shapes.push_back({C, NT, BV, save_cfg.nu, save_cfg.inner_rtol, 1e300, 1e300});
+      }
+  for (Cand& c : shapes) {
     apply_cand(c);
-    time_it(ST_LOAD_X | ST_PRIOR_IN | ST_FORWARD, steps, &c.t1);
+    time_it(screen, steps, &c.t1);
   }
-  std::sort(cands.begin(), cands.end(), [](const Cand& a, const Cand& b) { return a.t1 < b.t1; });
+  std::sort(shapes.begin(), shapes.end(), by_t1);
+  // round 2: smoothing sweeps and inner tolerance on the two best shapes
+  std::vector<Cand> cands;
+  for (int i = 0; i < std::min<int>(2, (int)shapes.size()); ++i)
+    for (int nu : {1, 2})
+      for (double inner : (mixed ? std::vector<double>{1e-4, 1e-5} : std::vector<double>{save_cfg.inner_rtol})) {
+        Cand c = shapes[i];
+        c.nu = nu;
+        c.inner = inner;
+        c.t1 = 1e300;
+        apply_cand(c);
+        time_it(screen, steps, &c.t1);
+        cands.push_back(c);
+      }
+  std::sort(cands.begin(), cands.end(), by_t1);
+  // round 3: whole Hessian applies
   const unsigned hess = ST_LOAD_X | ST_PRIOR_IN | ST_FORWARD | ST_ADJOINT | ST_PRIOR_OUT | ST_STORE_Y;
   const int n2 = std::min<int>(3, (int)cands.size());
   for (int i = 0; i < n2; ++i) {
@@ -661,17 +682,22 @@ lrp_status lrp_autotune(lrp_problem* P, int nvec, int steps, double* best_ms) {
   if (bi < 0) {
     P->team_ctas = save_C;
     P->team_cols = save_BV;
+    P->nthreads = save_NT;
     P->cfg = save_cfg;
     set_error("lrp_autotune: no candidate ran");
     return LRP_ECUDA;
   }
   apply_cand(cands[bi]);
   if (best_ms) *best_ms = cands[bi].t2;
-  if (std::getenv("LRP_VERBOSE"))
+  if (std::getenv("LRP_VERBOSE")) {
+    for (int i = 0; i < std::min<int>(6, (int)shapes.size()); ++i)
+      std::fprintf(stderr, "[lrp] autotune shape C=%d NT=%d BV=%d: screen %.2f ms\n", shapes[i].C, shapes[i].NT,
+                   shapes[i].BV, shapes[i].t1);
     for (int i = 0; i < n2; ++i)
-      std::fprintf(stderr, "[lrp] autotune nvec=%d: C=%d BV=%d nu=%d inner=%.0e screen %.2f ms, apply %.2f ms%s\n",
-                   nvec, cands[i].C, cands[i].BV, cands[i].nu, cands[i].inner, cands[i].t1, cands[i].t2,
-                   i == bi ? " <- kept" : "");
+      std::fprintf(stderr, "[lrp] autotune nvec=%d: C=%d NT=%d BV=%d nu=%d inner=%.0e screen %.2f ms, apply %.2f ms%s\n",
+                   nvec, cands[i].C, cands[i].NT, cands[i].BV, cands[i].nu, cands[i].inner, cands[i].t1,
+                   cands[i].t2, i == bi ? " <- kept" : "");
+  }
   return LRP_OK;
 }
 

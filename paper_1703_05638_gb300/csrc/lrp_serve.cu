@@ -168,6 +168,10 @@ struct Model {
   double *d_lam = nullptr, *d_V = nullptr, *d_G = nullptr, *d_diag = nullptr;
   size_t factor_bytes = 0;
   size_t handle_bytes = 0;  // measured bytes of one worker handle for this model
+  // launch shape and multigrid settings every worker handle uses (autotuned)
+  bool tuned = false;
+  int team_ctas = 0, team_cols = 0, nthreads = 0;
+  SolveCfg cfg{};
   int in_use = 0;
   double last_used = 0.0;
   std::deque<Request*> pending;
@@ -209,6 +213,12 @@ lrp_status slot_model_create(lrp_server* S, cudaStream_t s, Model& m, std::uniqu
   lrp_status st = lrp_setup_problem(&d, (void*)s, &h->P);
   if (st != LRP_OK) return st;
   lrp_problem* P = h->P;
+  if (m.tuned) {
+    P->team_ctas = m.team_ctas;
+    P->team_cols = m.team_cols;
+    P->nthreads = m.nthreads;
+    P->cfg = m.cfg;
+  }
   h->nx = m.nx;
   h->nd = m.n_data;
   h->k = m.k;
@@ -672,6 +682,16 @@ lrp_status lrp_server_add_model(lrp_server* S, const lrp_problem_desc* d, int k,
     if (dwork) cudaFree(dwork);
   }
   lrp_posterior_destroy(post);
+  if (e == cudaSuccess && S->cfg.autotune) {
+    r = lrp_autotune(P, S->cfg.max_batch, 0, nullptr);
+    if (r == LRP_OK) {
+      m->tuned = true;
+      m->team_ctas = P->team_ctas;
+      m->team_cols = P->team_cols;
+      m->nthreads = P->nthreads;
+      m->cfg = P->cfg;
+    }
+  }
   lrp_problem_destroy(P);
   if (e != cudaSuccess) {
     cudaStreamDestroy(s);

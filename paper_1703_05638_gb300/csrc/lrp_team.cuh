@@ -207,20 +207,21 @@ __device__ __forceinline__ T diag_at(const OpLevel& lv, int p, int i0, int i1, i
 // Grid-stride loop over items [start, items) that handles LRP_UNROLL items
 // per round: compute(it) performs every load and the arithmetic of item it
 // and returns its values, commit(it, v) performs the stores (and any
-// accumulation, in item order). All loads of a round are issued before its
-// first store, so a thread keeps several items' loads in flight (a store
-// could alias later loads, so the compiler would not overlap them itself).
+// accumulation, in item order). With more than one item per round, all loads
+// of a round are issued before its first store (a store could alias later
+// loads, so the compiler would not overlap them itself).
+// Measured on GB300 (127^2 and 63^3 sweeps, 16 columns): 2 or 4 items per
+// round spill registers and run 5-20% slower than 1, so 1 is the default.
 #ifndef LRP_UNROLL
-#define LRP_UNROLL 2
+#define LRP_UNROLL 1
 #endif
-// The solver levels (V-cycle, PCG, refinement) are separate functions with
-// their own register allocation unless LRP_INLINE_SOLVER is defined: inlined
-// into the one persistent kernel they share one 128-register budget, and the
-// batched loops would spill.
-#ifdef LRP_INLINE_SOLVER
-#define LRP_SOLVER_FN
-#else
+// The solver levels (V-cycle, PCG, refinement) are inlined into the one
+// persistent kernel unless LRP_NOINLINE_SOLVER is defined (separate register
+// allocations; slower when measured, kept for experiments with wider rounds).
+#ifdef LRP_NOINLINE_SOLVER
 #define LRP_SOLVER_FN __noinline__
+#else
+#define LRP_SOLVER_FN
 #endif
 template <class V, class Compute, class Commit>
 __device__ __forceinline__ void batched_loop(int start, int items, int stride, Compute compute, Commit commit) {
