@@ -227,6 +227,21 @@ def serve_bench(lrp, count: int, rate_hz: float, budget_gib: float, slots: int, 
             "query": "mean + variance@1024 + 8 samples, sigma log-uniform [1e-4, 1e-2], k=50"}
 
 
+def aggregate_replicas(dist, total_ms: float, matvecs: int, device: str):
+    """Whole-job throughput of independent replicas: the matvecs of all ranks
+    over the slowest rank's time (max over ranks). dist is torch.distributed
+    or None (one process). Returns (value, total_ms, matvecs)."""
+    if dist is not None:
+        import torch
+        t = torch.tensor([total_ms], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        m = torch.tensor([float(matvecs)], device=device, dtype=torch.float64)
+        dist.all_reduce(m, op=dist.ReduceOp.SUM)
+        matvecs = int(m.item())
+    return matvecs / (total_ms / 1e3), total_ms, matvecs
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -402,14 +417,7 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = float(sum(step_ms))
     matvecs = sum(s["n_matvec"] for s in stats)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        m = torch.tensor([matvecs], device="cuda", dtype=torch.float64)
-        dist.all_reduce(m, op=dist.ReduceOp.SUM)
-        matvecs = int(m.item())
-    value = matvecs / (total_ms / 1e3)
+    value, total_ms, matvecs = aggregate_replicas(dist, total_ms, matvecs, "cuda")
 
     # end to end through the C ABI with host buffers
     e2e = None

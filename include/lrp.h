@@ -198,7 +198,8 @@ lrp_status lrp_hessian_apply_noalloc(lrp_problem* p, int nvec, const double* X, 
 
 /* Autotuner for blocks of nvec columns. Round 1 times, for each cluster size
  * (1..8, 12, 16 CTAs), CTA size (256 or 512 threads) and columns per cluster
- * (1, 2), the prior solve and the first `steps` forward implicit-Euler steps
+ * (1, 2), with or without running in several waves for clusters of 8 or
+ * more, the prior solve and the first `steps` forward implicit-Euler steps
  * (0 -> 16); round 2 varies the smoothing sweeps and (LRP_MIXED) the inner
  * tolerance on the two best shapes; round 3 times one whole Hessian apply for
  * the three best. The winner stays in the problem handle for later calls.
@@ -233,7 +234,7 @@ lrp_status lrp_trajectory_factors(lrp_problem* p, int nvec, const double* U, int
  * Low-rank posterior (Sec. 4 Algorithm 1, as block Lanczos with full
  * reorthogonalisation on the symmetric Htilde; Sec. 2 SMW form).
  * Computes the k leading eigenpairs of Htilde with blocks of `block`
- * columns (1..16) until every returned Ritz pair has
+ * columns (1..64) until every returned Ritz pair has
  * ||Htilde v - theta v|| <= eig_tol * theta_1 (eig_tol 0 -> 1e-6), or the
  * Krylov space reaches max_basis columns (0 -> min(nx, 4k+2*block)).
  * eig_threshold > 0 keeps only eigenvalues >= eig_threshold (the paper's
@@ -287,6 +288,7 @@ typedef struct lrp_tuning {
   double inner_rtol;
   int last_kernel, last_team_ctas;
   int threads;  /* threads per CTA */
+  int waves;    /* 1: clusters of the requested size even if they run in several waves */
 } lrp_tuning;
 lrp_status lrp_problem_tuning(const lrp_problem* p, lrp_tuning* out);
 

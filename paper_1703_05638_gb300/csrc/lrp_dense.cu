@@ -385,7 +385,7 @@ __global__ void k_ritz_resid(int k, int nb, const double* B, const double* Z, in
 // T[r0:r0+nb, c0:c0+nb] = S (and optionally the transpose block), S col-major nb x nb
 __global__ void k_set_block(double* T, int ldt, int r0, int c0, int nb, const double* S, int lds,
                             int symmetrize, int also_transpose) {
-  const int e = threadIdx.x;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nb * nb) return;
   const int i = e % nb, j = e / nb;
   double v = S[(size_t)j * lds + i];
@@ -396,7 +396,7 @@ __global__ void k_set_block(double* T, int ldt, int r0, int c0, int nb, const do
 
 // zero the columns c of an nb x nb col-major matrix with flags[c] != 0
 __global__ void k_zero_flagged_cols(int nb, double* M, const int* flags) {
-  const int e = threadIdx.x;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nb * nb) return;
   const int j = e / nb;
   if (flags[j]) M[e] = 0.0;
@@ -647,13 +647,14 @@ cudaError_t ritz_resid(cudaStream_t s, int k, int nb, const double* B, const dou
 cudaError_t set_block(cudaStream_t s, double* T, int ldt, int r0, int c0, int nb, const double* S, int lds,
                       bool symmetrize, bool also_transpose) {
   note_launch();
-  k_set_block<<<1, 256, 0, s>>>(T, ldt, r0, c0, nb, S, lds, symmetrize ? 1 : 0, also_transpose ? 1 : 0);
+  k_set_block<<<(nb * nb + 255) / 256, 256, 0, s>>>(T, ldt, r0, c0, nb, S, lds, symmetrize ? 1 : 0,
+                                                     also_transpose ? 1 : 0);
   return cudaGetLastError();
 }
 
 cudaError_t zero_flagged_cols(cudaStream_t s, int nb, double* M, const int* flags) {
   note_launch();
-  k_zero_flagged_cols<<<1, 256, 0, s>>>(nb, M, flags);
+  k_zero_flagged_cols<<<(nb * nb + 255) / 256, 256, 0, s>>>(nb, M, flags);
   return cudaGetLastError();
 }
 
@@ -790,6 +791,21 @@ cudaError_t prior_diag_dst(cudaStream_t s, int dim, int n, double alpha, double*
     k_dst_contract<<<(total + 255) / 256, 256, 0, s>>>(dim, n, axis, A, src, dst);
     src = dst;
   }
+  return cudaGetLastError();
+}
+
+// D[0:m, 0:n] += S[0:m, 0:n] (column-major, leading dimensions lds, ldd)
+__global__ void k_add_block(int m, int n, const double* S, int lds, double* D, int ldd) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * n) return;
+  const int i = e % m, j = e / m;
+  D[(size_t)j * ldd + i] += S[(size_t)j * lds + i];
+}
+
+cudaError_t add_block(cudaStream_t s, int m, int n, const double* S, int lds, double* D, int ldd) {
+  if (m <= 0 || n <= 0) return cudaSuccess;
+  note_launch();
+  k_add_block<<<(m * n + 255) / 256, 256, 0, s>>>(m, n, S, lds, D, ldd);
   return cudaGetLastError();
 }
 

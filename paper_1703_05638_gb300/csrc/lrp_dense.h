@@ -47,6 +47,8 @@ cudaError_t col_norm2(cudaStream_t s, int nx, int nc, const double* X, int ldx, 
 cudaError_t axpby(cudaStream_t s, size_t n, double a, const double* x, double b, double* y);
 cudaError_t add_vec_cols(cudaStream_t s, int nx, int nc, const double* m, double* Y, int ldy);
 
+// D[0:m, 0:n] += S[0:m, 0:n] (column-major).
+cudaError_t add_block(cudaStream_t s, int m, int n, const double* S, int lds, double* D, int ldd);
 // Diagonal of (I + alpha L0)^-2 on the n^dim grid (constant-coefficient
 // Laplacian, zero Dirichlet data) by the sine transform; work >= n^2 + 2 n^dim.
 cudaError_t prior_diag_dst(cudaStream_t s, int dim, int n, double alpha, double* out, double* work);

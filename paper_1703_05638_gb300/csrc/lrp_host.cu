@@ -427,6 +427,7 @@ lrp_status lrp_problem_tuning(const lrp_problem* P, lrp_tuning* out) {
   out->last_kernel = P->last_kernel;
   out->last_team_ctas = P->last_team_ctas;
   out->threads = P->nthreads;
+  out->waves = P->allow_waves;
   return LRP_OK;
 }
 
@@ -601,11 +602,11 @@ lrp_status lrp_autotune(lrp_problem* P, int nvec, int steps, double* best_ms) {
     return cuda_status(e, "autotune buffers");
   }
   struct Cand {
-    int C, NT, BV, nu;
+    int C, NT, BV, waves, nu;
     double inner, t1, t2;
   };
   const bool mixed = P->desc.precision == LRP_MIXED;
-  const int save_C = P->team_ctas, save_BV = P->team_cols, save_NT = P->nthreads;
+  const int save_C = P->team_ctas, save_BV = P->team_cols, save_NT = P->nthreads, save_W = P->allow_waves;
   const SolveCfg save_cfg = P->cfg;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -614,6 +615,7 @@ lrp_status lrp_autotune(lrp_problem* P, int nvec, int steps, double* best_ms) {
     P->team_ctas = c.C;
     P->team_cols = c.BV;
     P->nthreads = c.NT;
+    P->allow_waves = c.waves;
     P->cfg = save_cfg;
     P->cfg.nu = c.nu;
     P->cfg.nu_coarse = c.nu;
@@ -636,15 +638,25 @@ lrp_status lrp_autotune(lrp_problem* P, int nvec, int steps, double* best_ms) {
   };
   auto by_t1 = [](const Cand& a, const Cand& b) { return a.t1 < b.t1; };
   const unsigned screen = ST_LOAD_X | ST_PRIOR_IN | ST_FORWARD;
+  // keep one screen near 20 ms: fewer steps for big problems
+  {
+    Cand c0{save_C, save_NT, save_BV, save_W, save_cfg.nu, save_cfg.inner_rtol, 1e300, 1e300};
+    apply_cand(c0);
+    double t = 1e300;
+    time_it(screen, 1, &t);
+    if (t < 1e300 && t > 0) steps = std::max(2, std::min(steps, (int)(20.0 / t)));
+  }
   // round 1: launch shape
   std::vector<Cand> shapes;
   for (int C : {1, 2, 3, 4, 5, 6, 7, 8, 12, 16})
     for (int NT : {512, 256})
-      for (int BV : {1, 2}) {
-        if (BV > nvec && BV > 1) continue;
-        if (C > 1 && (long long)P->nx / C < 256) continue;
-        shapes.push_back({C, NT, BV, save_cfg.nu, save_cfg.inner_rtol, 1e300, 1e300});
-      }
+      for (int BV : {1, 2})
+        for (int waves : {0, 1}) {
+          if (BV > 1 && nvec < 32) continue;  // one column per cluster wins for Lanczos-sized blocks
+          if (C > 1 && (long long)P->nx / C < 256) continue;
+          if (waves && C < 8) continue;  // more clusters than fit at once: only worth trying for big clusters
+          shapes.push_back({C, NT, BV, waves, save_cfg.nu, save_cfg.inner_rtol, 1e300, 1e300});
+        }
   for (Cand& c : shapes) {
     apply_cand(c);
     time_it(screen, steps, &c.t1);
@@ -683,6 +695,7 @@ lrp_status lrp_autotune(lrp_problem* P, int nvec, int steps, double* best_ms) {
     P->team_ctas = save_C;
     P->team_cols = save_BV;
     P->nthreads = save_NT;
+    P->allow_waves = save_W;
     P->cfg = save_cfg;
     set_error("lrp_autotune: no candidate ran");
     return LRP_ECUDA;
@@ -691,12 +704,13 @@ lrp_status lrp_autotune(lrp_problem* P, int nvec, int steps, double* best_ms) {
   if (best_ms) *best_ms = cands[bi].t2;
   if (std::getenv("LRP_VERBOSE")) {
     for (int i = 0; i < std::min<int>(6, (int)shapes.size()); ++i)
-      std::fprintf(stderr, "[lrp] autotune shape C=%d NT=%d BV=%d: screen %.2f ms\n", shapes[i].C, shapes[i].NT,
-                   shapes[i].BV, shapes[i].t1);
+      std::fprintf(stderr, "[lrp] autotune shape C=%d NT=%d BV=%d waves=%d: screen %.2f ms\n", shapes[i].C,
+                   shapes[i].NT, shapes[i].BV, shapes[i].waves, shapes[i].t1);
     for (int i = 0; i < n2; ++i)
-      std::fprintf(stderr, "[lrp] autotune nvec=%d: C=%d NT=%d BV=%d nu=%d inner=%.0e screen %.2f ms, apply %.2f ms%s\n",
-                   nvec, cands[i].C, cands[i].NT, cands[i].BV, cands[i].nu, cands[i].inner, cands[i].t1,
-                   cands[i].t2, i == bi ? " <- kept" : "");
+      std::fprintf(stderr,
+                   "[lrp] autotune nvec=%d: C=%d NT=%d BV=%d waves=%d nu=%d inner=%.0e screen %.2f ms, apply %.2f ms%s\n",
+                   nvec, cands[i].C, cands[i].NT, cands[i].BV, cands[i].waves, cands[i].nu, cands[i].inner,
+                   cands[i].t1, cands[i].t2, i == bi ? " <- kept" : "");
   }
   return LRP_OK;
 }

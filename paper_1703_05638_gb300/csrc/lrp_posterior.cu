@@ -56,7 +56,7 @@ static const unsigned HESS_STAGES = ST_LOAD_X | ST_PRIOR_IN | ST_FORWARD | ST_AD
 
 // Scratch of one Lanczos run.
 struct LanczosWS {
-  DArr<double> part, G, R1, R2, Ri1, Ri2, R, C1, C2;
+  DArr<double> part, G, R1, R2, Ri1, Ri2, R, R16, C1, C2;
   DArr<int> flags;
   size_t part_cap = 0;
 };
@@ -74,7 +74,25 @@ static lrp_status block_orth(lrp_problem* P, int nx, int nb, double* Wn, const d
     CK(gemm_nn(s, nx, nprev, nb, -1.0, Q, nx, ws.C1.p, nprev, 1.0, Wn, nx));
     if (Cacc) CK(axpby(s, (size_t)nprev * nb, 1.0, ws.C1.p, 1.0, Cacc));
   }
-  CK(block_gs(s, 1, nx, nb, Wn, 0, nx, ws.R.p, 0, 1e-13, nullptr));
+  if (nb <= 16) {
+    CK(block_gs(s, 1, nx, nb, Wn, 0, nx, ws.R.p, 0, 1e-13, nullptr));
+    return LRP_OK;
+  }
+  // wider blocks: sub-blocks of 16 columns, each made orthogonal to the
+  // finished ones by CGS2 (coefficients into R above the diagonal block),
+  // then rank-revealing CGS2 inside the sub-block (its diagonal block of R)
+  CK(cudaMemsetAsync(ws.R.p, 0, (size_t)nb * nb * sizeof(double), s));
+  for (int c0 = 0; c0 < nb; c0 += 16) {
+    const int w = std::min(16, nb - c0);
+    double* Ws = Wn + (size_t)c0 * nx;
+    for (int pass = 0; pass < 2 && c0 > 0; ++pass) {
+      CK(gemm_tn(s, nx, c0, w, Wn, nx, Ws, nx, ws.C1.p, c0, 1.0, 0.0, ws.part.p, ws.part_cap));
+      CK(gemm_nn(s, nx, c0, w, -1.0, Wn, nx, ws.C1.p, c0, 1.0, Ws, nx));
+      CK(add_block(s, c0, w, ws.C1.p, c0, ws.R.p + (size_t)c0 * nb, nb));
+    }
+    CK(block_gs(s, 1, nx, w, Ws, 0, nx, ws.R16.p, 0, 1e-13, nullptr));
+    CK(add_block(s, w, w, ws.R16.p, w, ws.R.p + (size_t)c0 * nb + c0, nb));
+  }
   return LRP_OK;
 }
 
@@ -93,8 +111,8 @@ lrp_status lrp_lowrank_posterior(lrp_problem* P, int k, int block, double eig_to
   }
   *out = nullptr;
   const int nx = P->nx;
-  if (block < 1 || block > 16 || k < 1 || k > nx) {
-    set_error("need 1 <= block <= 16 and 1 <= k <= nx");
+  if (block < 1 || block > 64 || k < 1 || k > nx) {
+    set_error("need 1 <= block <= 64 and 1 <= k <= nx");
     return LRP_EINVAL;
   }
   cudaSetDevice(P->device);
@@ -127,6 +145,7 @@ lrp_status lrp_lowrank_posterior(lrp_problem* P, int k, int block, double eig_to
   CK(ws.Ri1.alloc(nb * nb));
   CK(ws.Ri2.alloc(nb * nb));
   CK(ws.R.alloc(nb * nb));
+  CK(ws.R16.alloc(16 * 16));
   CK(ws.C1.alloc((size_t)(mmax + nb) * nb));
   CK(ws.C2.alloc((size_t)(mmax + nb) * nb));
   CK(ws.flags.alloc(nb));

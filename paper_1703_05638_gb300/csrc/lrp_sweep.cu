@@ -169,7 +169,8 @@ lrp_status run_sweep_ex(lrp_problem* Pr, unsigned stages, int nvec, const double
           bytes += (((nl + 2) * (nl + 1) + 2) * sizeof(float) + 15) & ~(size_t)15;
         }
       if (bytes > (size_t)215 * 1024) continue;
-      if (fast2d_resident_teams(Cf, Pr->nthreads, bytes, Pr->sm_count) < n_teams && Cf > 1) continue;
+      if (!Pr->allow_waves && fast2d_resident_teams(Cf, Pr->nthreads, bytes, Pr->sm_count) < n_teams && Cf > 1)
+        continue;
       fast = true;
       C = Cf;
       prm.fast_band_len = band_len;
@@ -183,7 +184,7 @@ lrp_status run_sweep_ex(lrp_problem* Pr, unsigned stages, int nvec, const double
       return LRP_EINVAL;
     }
   }
-  if (!fast)
+  if (!fast && !Pr->allow_waves)
     while (C > 1 && resident_teams(mixed, Pr->dim, C, Pr->nthreads, soff, Pr->sm_count) < n_teams) C >>= 1;
   Pr->last_kernel = fast ? 2 : 1;
   Pr->last_team_ctas = C;

@@ -129,7 +129,7 @@ def _check_eigs(lam, lam_ref, tol, resolvable):
     assert np.max(np.abs(lam[big] - lam_ref[big]) / lam_ref[big]) <= tol
 
 
-@pytest.mark.parametrize("block", [1, 2, 4])
+@pytest.mark.parametrize("block", [1, 2, 4, 24])
 def test_lanczos_tiny_fp64(block):
     spec = synth.workload("tiny")
     P, G = _pair(spec, lrp.LRP_FP64)
