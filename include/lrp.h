@@ -247,6 +247,32 @@ lrp_status lrp_lowrank_posterior(lrp_problem* p, int k, int block, double eig_to
                                  lrp_posterior** out, lrp_lanczos_stats* st);
 void lrp_posterior_destroy(lrp_posterior* post);
 
+/* Batched low-rank posterior (no counterpart in the paper: the batching
+ * form). Runs the block Lanczos of lrp_lowrank_posterior (eig_threshold 0,
+ * default basis cap, pseudo-random start) on `count` independent problems of
+ * any sizes at once: every block step of every problem not yet converged is
+ * enqueued on that problem's own stream and, with use_graph, the whole step
+ * is captured into one CUDA graph and launched once (otherwise launched
+ * directly); problems drop out as they converge. The problems' streams must
+ * be distinct non-default streams (lrp_setup_problem's cuda_stream) and on
+ * one device. outs[i] and stats[i] (stats may be NULL) as in
+ * lrp_lowrank_posterior; *bst (may be NULL) gets totals. Each result equals
+ * that of lrp_lowrank_posterior on the same problem (same kernels in the
+ * same order on its stream). max_steps > 0 stops after that many block
+ * steps (a bounded sample: the posteriors then hold the current Ritz pairs).
+ * Returns LRP_ENOCONV if any problem stopped before converging (its
+ * posterior is still usable). */
+typedef struct {
+  int steps;             /* block steps (graph launches with use_graph) */
+  long long graph_nodes; /* nodes of all step graphs together */
+  long long n_matvec;    /* Htilde applications over all problems */
+  double ms_steps;       /* wall time of the steps */
+  double ms;             /* wall time of the call */
+} lrp_batch_stats;
+lrp_status lrp_batch_lowrank_posterior(lrp_problem* const* probs, int count, int k, int block, double eig_tol,
+                                       int use_graph, int max_steps, lrp_posterior** outs,
+                                       lrp_lanczos_stats* stats, lrp_batch_stats* bst);
+
 /* Copies the r <= k eigenvalues (decreasing) and optionally the eigenvectors
  * (nx x r column-major, ld ldv) out of a posterior. *r receives the count. */
 lrp_status lrp_posterior_eigs(const lrp_posterior* post, int* r, double* lambda,
@@ -291,6 +317,11 @@ typedef struct lrp_tuning {
   int waves;    /* 1: clusters of the requested size even if they run in several waves */
 } lrp_tuning;
 lrp_status lrp_problem_tuning(const lrp_problem* p, lrp_tuning* out);
+/* Sets a problem's launch shape and multigrid settings from t (team_ctas,
+ * team_cols, mg_nu, mg_nu_coarse, inner_rtol, threads 256 or 512, waves; the
+ * last_* fields are ignored), e.g. to reuse one autotuned setting for
+ * problems of the same size. LRP_EINVAL on values out of range. */
+lrp_status lrp_set_tuning(lrp_problem* p, const lrp_tuning* t);
 
 /* ---------------------------------------------------------------------------
  * Posterior-query server (no counterpart in the paper; it serves the

@@ -91,6 +91,14 @@ class lrp_server_stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class lrp_batch_stats(C.Structure):
+    _fields_ = [("steps", C.c_int), ("graph_nodes", C.c_longlong), ("n_matvec", C.c_longlong),
+                ("ms_steps", C.c_double), ("ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class lrp_tuning(C.Structure):
     _fields_ = [("team_ctas", C.c_int), ("team_cols", C.c_int), ("mg_nu", C.c_int), ("mg_nu_coarse", C.c_int),
                 ("inner_rtol", C.c_double), ("last_kernel", C.c_int), ("last_team_ctas", C.c_int),
@@ -126,6 +134,10 @@ EXPORTS = {
     "lrp_kernel_launches": (C.c_ulonglong, []),
     "lrp_sweep_profile": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _dp, C.POINTER(C.c_ulonglong), _dp]),
     "lrp_problem_tuning": (C.c_int, [C.c_void_p, C.POINTER(lrp_tuning)]),
+    "lrp_batch_lowrank_posterior": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.c_double, C.c_int,
+                                              C.c_int, C.POINTER(C.c_void_p), C.POINTER(lrp_lanczos_stats),
+                                              C.POINTER(lrp_batch_stats)]),
+    "lrp_set_tuning": (C.c_int, [C.c_void_p, C.POINTER(lrp_tuning)]),
     "lrp_server_create": (C.c_int, [C.POINTER(lrp_server_config), C.POINTER(C.c_void_p)]),
     "lrp_server_add_model": (C.c_int, [C.c_void_p, C.POINTER(lrp_problem_desc), C.c_int, C.c_int, C.c_double,
                                        C.c_char_p, C.POINTER(C.c_int), C.POINTER(lrp_lanczos_stats)]),
@@ -429,6 +441,21 @@ def lrp_posterior_query(post: Posterior, kind: int, y_obs=None, sigma: float = 0
     return out
 
 
+def lrp_batch_lowrank_posterior(probs, k: int, block: int = 16, eig_tol: float = 1e-6, use_graph: bool = True,
+                                max_steps: int = 0):
+    """Block Lanczos on several problems at once (each on its own stream; one
+    CUDA graph per block step with use_graph). Returns ([(Posterior, stats)],
+    batch stats)."""
+    n = len(probs)
+    hs = (C.c_void_p * n)(*[p.handle for p in probs])
+    outs = (C.c_void_p * n)()
+    sts = (lrp_lanczos_stats * n)()
+    bst = lrp_batch_stats()
+    _check(load().lrp_batch_lowrank_posterior(hs, n, int(k), int(block), float(eig_tol), int(bool(use_graph)),
+                                              int(max_steps), outs, sts, C.byref(bst)), allow=(LRP_OK, LRP_ENOCONV))
+    return [(Posterior(C.c_void_p(outs[i]), probs[i]), sts[i].as_dict()) for i in range(n)], bst.as_dict()
+
+
 def lrp_posterior_save(post: Posterior, path: str):
     _check(load().lrp_posterior_save(post.handle, path.encode()))
 
@@ -552,6 +579,15 @@ def lrp_problem_tuning(prob: "Problem") -> dict:
     t = lrp_tuning()
     _check(load().lrp_problem_tuning(prob.handle, C.byref(t)))
     return {f: getattr(t, f) for f, _ in lrp_tuning._fields_}
+
+
+def lrp_set_tuning(prob: "Problem", tuning: dict):
+    """Apply a setting read by lrp_problem_tuning (e.g. from an autotuned problem of the same size)."""
+    t = lrp_tuning()
+    for f, _ in lrp_tuning._fields_:
+        if f in tuning:
+            setattr(t, f, tuning[f])
+    _check(load().lrp_set_tuning(prob.handle, C.byref(t)))
 
 
 def lrp_kernel_launches() -> int:

@@ -431,6 +431,27 @@ lrp_status lrp_problem_tuning(const lrp_problem* P, lrp_tuning* out) {
   return LRP_OK;
 }
 
+lrp_status lrp_set_tuning(lrp_problem* P, const lrp_tuning* t) {
+  if (!P || !t) {
+    set_error("lrp_set_tuning: NULL argument");
+    return LRP_EINVAL;
+  }
+  if (t->team_ctas < 1 || t->team_ctas > 16 || t->team_cols < 1 || t->team_cols > LRP_MAXBV ||
+      (t->team_cols & (t->team_cols - 1)) || t->mg_nu < 1 || t->mg_nu > 8 || t->mg_nu_coarse < 1 ||
+      t->mg_nu_coarse > 8 || !(t->inner_rtol > 0 && t->inner_rtol < 1) || (t->threads != 256 && t->threads != 512)) {
+    set_error("lrp_set_tuning: value out of range");
+    return LRP_EINVAL;
+  }
+  P->team_ctas = t->team_ctas;
+  P->team_cols = t->team_cols;
+  P->nthreads = t->threads;
+  P->allow_waves = t->waves ? 1 : 0;
+  P->cfg.nu = t->mg_nu;
+  P->cfg.nu_coarse = t->mg_nu_coarse;
+  P->cfg.inner_rtol = t->inner_rtol;
+  return LRP_OK;
+}
+
 void lrp_problem_destroy(lrp_problem* P) {
   if (!P) return;
   if (P->stream) cudaStreamSynchronize(P->stream);

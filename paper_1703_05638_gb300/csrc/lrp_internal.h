@@ -209,6 +209,14 @@ lrp_status cuda_status(cudaError_t e, const char* where);
 bool is_device_ptr(const void* p);
 
 // sweep launcher (lrp_sweep.cu)
+struct SweepLaunch {
+  bool fast = false, mixed = false;
+  int BV = 1, n_teams = 0;
+};
+lrp_status sweep_enqueue(lrp_problem* Pr, unsigned stages, int nvec, const double* X, int ldx, double* Y, int ldy,
+                         const double* Din, int lddin, double* Dout, int lddout, int t_begin, int t_end,
+                         double* traj, int traj_cols, Stats* hs_dst, SweepLaunch* info);
+lrp_status sweep_status(const Stats& hs, const SweepLaunch& info, lrp_apply_stats* st, double ms);
 lrp_status run_sweep(lrp_problem* P, unsigned stages, int nvec, const double* X, int ldx,
                      double* Y, int ldy, const double* Din, int lddin, double* Dout,
                      int lddout, lrp_apply_stats* st, bool misfit_only);

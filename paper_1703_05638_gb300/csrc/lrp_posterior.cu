@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -96,86 +97,113 @@ static lrp_status block_orth(lrp_problem* P, int nx, int nb, double* Wn, const d
   return LRP_OK;
 }
 
-}  // namespace lrp
-
-using namespace lrp;
-
-extern "C" {
-
-lrp_status lrp_lowrank_posterior(lrp_problem* P, int k, int block, double eig_tol, double eig_threshold,
-                                 int max_basis, const double* start, lrp_posterior** out,
-                                 lrp_lanczos_stats* stats) {
-  if (!P || !out) {
-    set_error("NULL argument");
-    return LRP_EINVAL;
-  }
-  *out = nullptr;
-  const int nx = P->nx;
-  if (block < 1 || block > 64 || k < 1 || k > nx) {
-    set_error("need 1 <= block <= 64 and 1 <= k <= nx");
-    return LRP_EINVAL;
-  }
-  cudaSetDevice(P->device);
-  auto t0 = std::chrono::steady_clock::now();
-  double ms_apply = 0.0;
-  const int nb = block;
-  if (!(eig_tol > 0)) eig_tol = 1e-6;
-  int mmax = max_basis > 0 ? max_basis : std::min(nx, 3 * k + 4 * nb);
-  mmax = std::min(mmax, nx);
-  mmax = std::min(mmax, 1024);
-  mmax = std::max(nb, mmax / nb * nb);
-  cudaStream_t s = P->stream;
+// One block-Lanczos run on one problem, split so that its block steps can be
+// enqueued without host synchronisation (and captured into a CUDA graph
+// together with other problems' steps): enqueue_step() queues the Hessian
+// apply of block j, the full re-orthogonalisation, the update of the block
+// tridiagonal T and, once the basis has k columns, the eigensolve of T and
+// the Ritz residuals with their copy to pinned host memory; after_step()
+// reads them once the stream has been synchronised.
+struct LanczosRun {
+  lrp_problem* P = nullptr;
+  int k = 0, nb = 0, nx = 0, mmax = 0;
+  double eig_tol = 1e-6, eig_threshold = 0.0;
   DArr<double> Q, W, T, Tw, Z, theta, work, resid;
   DArr<int> estat;
   LanczosWS ws;
-  CK(Q.alloc((size_t)nx * (mmax + nb)));
-  CK(W.alloc((size_t)nx * nb));
-  CK(T.alloc((size_t)(mmax + nb) * (mmax + nb)));
-  CK(Tw.alloc((size_t)mmax * mmax));
-  CK(Z.alloc((size_t)mmax * mmax));
-  CK(theta.alloc(mmax));
-  CK(work.alloc(6 * (size_t)mmax + 8));
-  CK(resid.alloc(mmax));
-  CK(estat.alloc(1));
-  ws.part_cap = (size_t)std::max(mmax + nb, 16) * 16 * 128;
-  CK(ws.part.alloc(ws.part_cap));
-  CK(ws.G.alloc(nb * nb));
-  CK(ws.R1.alloc(nb * nb));
-  CK(ws.R2.alloc(nb * nb));
-  CK(ws.Ri1.alloc(nb * nb));
-  CK(ws.Ri2.alloc(nb * nb));
-  CK(ws.R.alloc(nb * nb));
-  CK(ws.R16.alloc(16 * 16));
-  CK(ws.C1.alloc((size_t)(mmax + nb) * nb));
-  CK(ws.C2.alloc((size_t)(mmax + nb) * nb));
-  CK(ws.flags.alloc(nb));
-  CK(cudaMemsetAsync(T.p, 0, T.n * sizeof(double), s));
-  // start block
-  if (start) {
-    if (is_device_ptr(start)) {
-      CK(copy_cols(s, nx, nb, start, nx, Q.p, nx));
-    } else {
-      CK(cudaMemcpyAsync(Q.p, start, (size_t)nx * nb * sizeof(double), cudaMemcpyHostToDevice, s));
-    }
-  } else {
-    CK(fill_random(s, nx, nb, Q.p, nx, nullptr, 0x5EEDull));
+  double* h_theta = nullptr;  // pinned
+  double* h_res = nullptr;    // pinned
+  Stats* h_stats = nullptr;   // pinned
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  SweepLaunch info;
+  int j = 0, cols = 0, kk = 0, n_iter = 0, n_matvec = 0;
+  bool check = false, last = false, converged = false, done = false;
+  double max_res = 0.0, ms_apply = 0.0;
+  std::chrono::steady_clock::time_point t0;
+
+  ~LanczosRun() {
+    if (h_theta) cudaFreeHost(h_theta);
+    if (h_res) cudaFreeHost(h_res);
+    if (h_stats) cudaFreeHost(h_stats);
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
   }
-  lrp_status st = block_orth(P, nx, nb, Q.p, Q.p, 0, ws, nullptr);
-  if (st != LRP_OK) return st;
-  int n_iter = 0, n_matvec = 0, cols = 0, kk = 0;
-  bool converged = false;
-  double max_res = 0.0;
-  std::vector<double> h_theta, h_res;
-  for (int j = 0;; ++j) {
+
+  lrp_status init(lrp_problem* P_, int k_, int block, double eig_tol_, double eig_threshold_, int max_basis,
+                  const double* start) {
+    P = P_;
+    nx = P->nx;
+    if (block < 1 || block > 64 || k_ < 1 || k_ > nx) {
+      set_error("need 1 <= block <= 64 and 1 <= k <= nx");
+      return LRP_EINVAL;
+    }
+    cudaSetDevice(P->device);
+    t0 = std::chrono::steady_clock::now();
+    k = k_;
+    nb = block;
+    eig_tol = eig_tol_ > 0 ? eig_tol_ : 1e-6;
+    eig_threshold = eig_threshold_;
+    mmax = max_basis > 0 ? max_basis : std::min(nx, 3 * k + 4 * nb);
+    mmax = std::min(mmax, nx);
+    mmax = std::min(mmax, 1024);
+    mmax = std::max(nb, mmax / nb * nb);
+    cudaStream_t s = P->stream;
+    CK(Q.alloc((size_t)nx * (mmax + nb)));
+    CK(W.alloc((size_t)nx * nb));
+    CK(T.alloc((size_t)(mmax + nb) * (mmax + nb)));
+    CK(Tw.alloc((size_t)mmax * mmax));
+    CK(Z.alloc((size_t)mmax * mmax));
+    CK(theta.alloc(mmax));
+    CK(work.alloc(6 * (size_t)mmax + 8));
+    CK(resid.alloc(mmax));
+    CK(estat.alloc(1));
+    ws.part_cap = (size_t)std::max(mmax + nb, 16) * 16 * 128;
+    CK(ws.part.alloc(ws.part_cap));
+    CK(ws.G.alloc(nb * nb));
+    CK(ws.R1.alloc(nb * nb));
+    CK(ws.R2.alloc(nb * nb));
+    CK(ws.Ri1.alloc(nb * nb));
+    CK(ws.Ri2.alloc(nb * nb));
+    CK(ws.R.alloc(nb * nb));
+    CK(ws.R16.alloc(16 * 16));
+    CK(ws.C1.alloc((size_t)(mmax + nb) * nb));
+    CK(ws.C2.alloc((size_t)(mmax + nb) * nb));
+    CK(ws.flags.alloc(nb));
+    CK(cudaMallocHost(&h_theta, mmax * sizeof(double)));
+    CK(cudaMallocHost(&h_res, mmax * sizeof(double)));
+    CK(cudaMallocHost(&h_stats, sizeof(Stats)));
+    CK(cudaEventCreate(&ev[0]));
+    CK(cudaEventCreate(&ev[1]));
+    CK(cudaMemsetAsync(T.p, 0, T.n * sizeof(double), s));
+    // start block
+    if (start) {
+      if (is_device_ptr(start)) {
+        CK(copy_cols(s, nx, nb, start, nx, Q.p, nx));
+      } else {
+        CK(cudaMemcpyAsync(Q.p, start, (size_t)nx * nb * sizeof(double), cudaMemcpyHostToDevice, s));
+      }
+    } else {
+      CK(fill_random(s, nx, nb, Q.p, nx, nullptr, 0x5EEDull));
+    }
+    lrp_status st = block_orth(P, nx, nb, Q.p, Q.p, 0, ws, nullptr);
+    if (st != LRP_OK) return st;
+    // grow the sweep workspace for nb columns now (an empty launch), so the
+    // block steps never reallocate it
+    st = sweep_enqueue(P, 0u, nb, nullptr, 0, nullptr, 0, nullptr, 0, nullptr, 0, 0, 0, nullptr, 0, nullptr, nullptr);
+    if (st != LRP_OK) return st;
+    CK(cudaStreamSynchronize(s));
+    return LRP_OK;
+  }
+
+  lrp_status enqueue_step() {
+    cudaStream_t s = P->stream;
     const int c0 = j * nb;
     cols = c0 + nb;
-    auto ta = std::chrono::steady_clock::now();
-    st = run_sweep(P, HESS_STAGES, nb, Q.p + (size_t)c0 * nx, nx, W.p, nx, nullptr, 0, nullptr, 0, nullptr,
-                   false);
-    ms_apply += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ta).count();
-    if (st != LRP_OK && st != LRP_ENOCONV) return st;
-    n_matvec += nb;
-    ++n_iter;
+    CK(cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal));
+    lrp_status st = sweep_enqueue(P, HESS_STAGES, nb, Q.p + (size_t)c0 * nx, nx, W.p, nx, nullptr, 0, nullptr, 0, 0,
+                                  -1, nullptr, 0, h_stats, &info);
+    if (st != LRP_OK) return st;
+    CK(cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal));
     // full re-orthogonalisation (CGS2 against the whole basis), the
     // coefficients of block j give A_j; block CGS2 of the remainder gives B_j
     CK(cudaMemsetAsync(ws.C2.p, 0, (size_t)cols * nb * sizeof(double), s));
@@ -184,19 +212,30 @@ lrp_status lrp_lowrank_posterior(lrp_problem* P, int k, int block, double eig_to
     CK(set_block(s, T.p, mmax + nb, c0, c0, nb, ws.C2.p + c0, cols, true, false));
     CK(set_block(s, T.p, mmax + nb, cols, c0, nb, ws.R.p, nb, false, true));
     if (cols < mmax) CK(copy_cols(s, nx, nb, W.p, nx, Q.p + (size_t)cols * nx, nx));
-    const bool last = cols + nb > mmax;
-    if (cols >= std::min(k, mmax) || last) {
+    last = cols + nb > mmax;
+    check = cols >= std::min(k, mmax) || last;
+    if (check) {
       kk = std::min(k, cols);
       // eigenpairs of T_j (copied: the solver destroys its input)
       CK(cudaMemcpy2DAsync(Tw.p, (size_t)cols * sizeof(double), T.p, (size_t)(mmax + nb) * sizeof(double),
                            (size_t)cols * sizeof(double), cols, cudaMemcpyDeviceToDevice, s));
       CK(eig_sym(s, cols, Tw.p, cols, Z.p, cols, theta.p, work.p, estat.p));
       CK(ritz_resid(s, kk, nb, ws.R.p, Z.p, cols, c0, resid.p));
-      h_theta.resize(kk);
-      h_res.resize(kk);
-      CK(cudaMemcpyAsync(h_theta.data(), theta.p, kk * sizeof(double), cudaMemcpyDeviceToHost, s));
-      CK(cudaMemcpyAsync(h_res.data(), resid.p, kk * sizeof(double), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
+      CK(cudaMemcpyAsync(h_theta, theta.p, kk * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(h_res, resid.p, kk * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    return LRP_OK;
+  }
+
+  // after the stream (or the graph holding the step) has completed
+  lrp_status after_step() {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess) ms_apply += ms;
+    n_matvec += nb;
+    ++n_iter;
+    lrp_status st = sweep_status(*h_stats, info, nullptr, 0.0);
+    if (st != LRP_OK && st != LRP_ENOCONV) return st;
+    if (check) {
       const double th0 = std::max(h_theta[0], 1e-300);
       if (std::getenv("LRP_VERBOSE")) {
         double mr = 0.0;
@@ -214,60 +253,227 @@ lrp_status lrp_lowrank_posterior(lrp_problem* P, int k, int block, double eig_to
       }
       if (ok) {
         converged = true;
-        break;
+        done = true;
+      } else if (last) {
+        done = true;
       }
-      if (last) break;
     }
+    ++j;
+    return LRP_OK;
   }
-  // Ritz vectors V_k = Q_m S_k, eigenvalues theta_k
-  int kout = kk;
-  if (eig_threshold > 0) {
-    kout = 0;
-    for (int i = 0; i < kk; ++i)
-      if (h_theta[i] >= eig_threshold) ++kout;
-  }
-  lrp_posterior* post = new lrp_posterior();
-  post->prob = P;
-  post->k = kout;
-  post->nx = nx;
-  post->sigma0 = P->desc.sigma;
-  post->diag = nullptr;
-  post->diag_cap = 0;
-  post->lambda_host.assign(h_theta.begin(), h_theta.begin() + kout);
-  DArr<double> V, G, lam;
-  CK(V.alloc((size_t)nx * std::max(kout, 1)));
-  CK(G.alloc((size_t)nx * std::max(kout, 1)));
-  CK(lam.alloc(std::max(kout, 1)));
-  if (kout > 0) {
-    CK(gemm_nn(s, nx, cols, kout, 1.0, Q.p, nx, Z.p, cols, 0.0, V.p, nx));
-    CK(cudaMemcpyAsync(lam.p, theta.p, kout * sizeof(double), cudaMemcpyDeviceToDevice, s));
+
+  // Ritz vectors V_k = Q_m S_k, eigenvalues theta_k, G = R^-1 V_k
+  lrp_status finish(lrp_posterior** out, lrp_lanczos_stats* stats) {
+    cudaStream_t s = P->stream;
+    int kout = kk;
+    if (eig_threshold > 0) {
+      kout = 0;
+      for (int i = 0; i < kk; ++i)
+        if (h_theta[i] >= eig_threshold) ++kout;
+    }
+    lrp_posterior* post = new lrp_posterior();
+    post->prob = P;
+    post->k = kout;
+    post->nx = nx;
+    post->sigma0 = P->desc.sigma;
+    post->diag = nullptr;
+    post->diag_cap = 0;
+    post->lambda_host.assign(h_theta, h_theta + kout);
+    DArr<double> V, G, lam;
+    CK(V.alloc((size_t)nx * std::max(kout, 1)));
+    CK(G.alloc((size_t)nx * std::max(kout, 1)));
+    CK(lam.alloc(std::max(kout, 1)));
+    if (kout > 0) {
+      CK(gemm_nn(s, nx, cols, kout, 1.0, Q.p, nx, Z.p, cols, 0.0, V.p, nx));
+      CK(cudaMemcpyAsync(lam.p, theta.p, kout * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      CK(cudaStreamSynchronize(s));
+      lrp_apply_stats ast;
+      lrp_status st = run_sweep(P, ST_LOAD_X | ST_PRIOR_IN | ST_STORE_Y, kout, V.p, nx, G.p, nx, nullptr, 0, nullptr,
+                                0, &ast, false);
+      if (st != LRP_OK && st != LRP_ENOCONV) {
+        delete post;
+        return st;
+      }
+    }
     CK(cudaStreamSynchronize(s));
-    lrp_apply_stats ast;
-    st = run_sweep(P, ST_LOAD_X | ST_PRIOR_IN | ST_STORE_Y, kout, V.p, nx, G.p, nx, nullptr, 0, nullptr, 0,
-                   &ast, false);
-    if (st != LRP_OK && st != LRP_ENOCONV) {
-      delete post;
-      return st;
+    post->V = V.release();
+    post->G = G.release();
+    post->lambda = lam.release();
+    *out = post;
+    if (stats) {
+      stats->n_iter = n_iter;
+      stats->n_matvec = n_matvec;
+      stats->k_converged = converged ? kout : 0;
+      stats->max_ritz_resid = max_res;
+      stats->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      stats->ms_apply = ms_apply;
+    }
+    if (!converged) {
+      set_error("Lanczos reached its basis cap before all Ritz pairs converged");
+      return LRP_ENOCONV;
+    }
+    return LRP_OK;
+  }
+};
+
+}  // namespace lrp
+
+using namespace lrp;
+
+extern "C" {
+
+lrp_status lrp_lowrank_posterior(lrp_problem* P, int k, int block, double eig_tol, double eig_threshold,
+                                 int max_basis, const double* start, lrp_posterior** out,
+                                 lrp_lanczos_stats* stats) {
+  if (!P || !out) {
+    set_error("NULL argument");
+    return LRP_EINVAL;
+  }
+  *out = nullptr;
+  LanczosRun run;
+  lrp_status st = run.init(P, k, block, eig_tol, eig_threshold, max_basis, start);
+  if (st != LRP_OK) return st;
+  while (!run.done) {
+    st = run.enqueue_step();
+    if (st != LRP_OK) return st;
+    CK(cudaStreamSynchronize(P->stream));
+    st = run.after_step();
+    if (st != LRP_OK) return st;
+  }
+  return run.finish(out, stats);
+}
+
+lrp_status lrp_batch_lowrank_posterior(lrp_problem* const* probs, int count, int k, int block, double eig_tol,
+                                       int use_graph, int max_steps, lrp_posterior** outs,
+                                       lrp_lanczos_stats* stats, lrp_batch_stats* bst) {
+  if (!probs || !outs || count < 1) {
+    set_error("lrp_batch_lowrank_posterior: invalid argument");
+    return LRP_EINVAL;
+  }
+  for (int i = 0; i < count; ++i) {
+    outs[i] = nullptr;
+    if (!probs[i]) {
+      set_error("lrp_batch_lowrank_posterior: NULL problem");
+      return LRP_EINVAL;
+    }
+    if (probs[i]->device != probs[0]->device) {
+      set_error("lrp_batch_lowrank_posterior: problems on different devices");
+      return LRP_EINVAL;
+    }
+    for (int j = 0; j < i; ++j)
+      if (probs[j]->stream == probs[i]->stream) {
+        set_error("lrp_batch_lowrank_posterior: the problems need distinct streams");
+        return LRP_EINVAL;
+      }
+  }
+  cudaSetDevice(probs[0]->device);
+  auto t0 = std::chrono::steady_clock::now();
+  std::vector<std::unique_ptr<LanczosRun>> runs(count);
+  for (int i = 0; i < count; ++i) {
+    runs[i].reset(new LanczosRun());
+    lrp_status st = runs[i]->init(probs[i], k, block, eig_tol, 0.0, 0, nullptr);
+    if (st != LRP_OK) return st;
+  }
+  cudaStream_t origin = nullptr;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join(count, nullptr);
+  CK(cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+  for (auto& e : join) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  auto cleanup = [&]() {
+    for (auto& e : join)
+      if (e) cudaEventDestroy(e);
+    if (fork) cudaEventDestroy(fork);
+    if (origin) cudaStreamDestroy(origin);
+  };
+  long long steps = 0, graph_nodes = 0;
+  double ms_steps = 0.0;
+  lrp_status result = LRP_OK;
+  while (true) {
+    std::vector<int> active;
+    for (int i = 0; i < count; ++i)
+      if (!runs[i]->done) active.push_back(i);
+    if (active.empty() || (max_steps > 0 && steps >= max_steps)) break;
+    auto ts = std::chrono::steady_clock::now();
+    lrp_status st = LRP_OK;
+    if (use_graph) {
+      // one CUDA graph per step: every active problem's block step on its own
+      // stream, forked from and joined back into the origin stream
+      cudaGraph_t graph = nullptr;
+      cudaGraphExec_t exec = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeRelaxed);
+      if (e == cudaSuccess) e = cudaEventRecord(fork, origin);
+      for (int i : active) {
+        if (e != cudaSuccess) break;
+        e = cudaStreamWaitEvent(probs[i]->stream, fork, 0);
+        if (e != cudaSuccess) break;
+        st = runs[i]->enqueue_step();
+        if (st != LRP_OK) break;
+        e = cudaEventRecord(join[i], probs[i]->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(origin, join[i], 0);
+      }
+      cudaError_t e2 = cudaStreamEndCapture(origin, &graph);
+      if (st != LRP_OK || e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cleanup();
+        if (st != LRP_OK) return st;
+        return cuda_status(e != cudaSuccess ? e : e2, "batched step capture");
+      }
+      size_t nn = 0;
+      cudaGraphGetNodes(graph, nullptr, &nn);
+      graph_nodes += (long long)nn;
+      e = cudaGraphInstantiate(&exec, graph, 0);
+      if (e == cudaSuccess) e = cudaGraphLaunch(exec, origin);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(origin);
+      if (exec) cudaGraphExecDestroy(exec);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        cleanup();
+        return cuda_status(e, "batched step graph");
+      }
+    } else {
+      for (int i : active) {
+        st = runs[i]->enqueue_step();
+        if (st != LRP_OK) {
+          cleanup();
+          return st;
+        }
+      }
+      for (int i : active) {
+        cudaError_t e = cudaStreamSynchronize(probs[i]->stream);
+        if (e != cudaSuccess) {
+          cleanup();
+          return cuda_status(e, "batched step");
+        }
+      }
+    }
+    ms_steps += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ts).count();
+    ++steps;
+    for (int i : active) {
+      st = runs[i]->after_step();
+      if (st != LRP_OK) {
+        cleanup();
+        return st;
+      }
     }
   }
-  CK(cudaStreamSynchronize(s));
-  post->V = V.release();
-  post->G = G.release();
-  post->lambda = lam.release();
-  *out = post;
-  if (stats) {
-    stats->n_iter = n_iter;
-    stats->n_matvec = n_matvec;
-    stats->k_converged = converged ? kout : 0;
-    stats->max_ritz_resid = max_res;
-    stats->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    stats->ms_apply = ms_apply;
+  cleanup();
+  for (int i = 0; i < count; ++i) {
+    if (!runs[i]->check) runs[i]->kk = 0;  // stopped before T had k columns: no Ritz pairs yet
+    lrp_status st = runs[i]->finish(&outs[i], stats ? &stats[i] : nullptr);
+    if (st != LRP_OK && st != LRP_ENOCONV) return st;
+    if (st == LRP_ENOCONV) result = LRP_ENOCONV;
   }
-  if (!converged) {
-    set_error("Lanczos reached its basis cap before all Ritz pairs converged");
-    return LRP_ENOCONV;
+  if (bst) {
+    bst->steps = (int)steps;
+    bst->graph_nodes = graph_nodes;
+    bst->ms_steps = ms_steps;
+    bst->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    long long mv = 0;
+    for (auto& r : runs) mv += r->n_matvec;
+    bst->n_matvec = mv;
   }
-  return LRP_OK;
+  return result;
 }
 
 void lrp_posterior_destroy(lrp_posterior* post) {

@@ -65,11 +65,15 @@ lrp_status run_sweep(lrp_problem* Pr, unsigned stages, int nvec, const double* X
   return run_sweep_ex(Pr, stages, nvec, X, ldx, Y, ldy, Din, lddin, Dout, lddout, st, 0, -1, nullptr, 0);
 }
 
-// t_end < 0: the forward sweep runs to the last observed step.
-lrp_status run_sweep_ex(lrp_problem* Pr, unsigned stages, int nvec, const double* X, int ldx,
-                        double* Y, int ldy, const double* Din, int lddin, double* Dout, int lddout,
-                        lrp_apply_stats* st, int t_begin, int t_end, double* traj, int traj_cols) {
-  auto t0 = std::chrono::steady_clock::now();
+// Enqueues one sweep launch on the problem's stream without host
+// synchronisation (so it can be captured into a CUDA graph): the stats are
+// reset before the launch and copied to *hs_dst (host memory; pinned for an
+// asynchronous copy) after it. t_end < 0: the forward sweep runs to the last
+// observed step. The workspace must already be large enough when the stream
+// is being captured (it cannot be reallocated then).
+lrp_status sweep_enqueue(lrp_problem* Pr, unsigned stages, int nvec, const double* X, int ldx, double* Y, int ldy,
+                         const double* Din, int lddin, double* Dout, int lddout, int t_begin, int t_end,
+                         double* traj, int traj_cols, Stats* hs_dst, SweepLaunch* info) {
   const bool mixed = Pr->desc.precision == LRP_MIXED;
   const int BV = Pr->team_cols;
   int bvs = 0;
@@ -118,6 +122,14 @@ lrp_status run_sweep_ex(lrp_problem* Pr, unsigned stages, int nvec, const double
     }
     prm.ws = Pr->ws_fixed;
   } else {
+    if (off * n_teams > Pr->ws_bytes) {
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      cudaStreamIsCapturing(Pr->stream, &cs);
+      if (cs != cudaStreamCaptureStatusNone) {
+        set_error("sweep workspace too small while the stream is being captured");
+        return LRP_EINVAL;
+      }
+    }
     lrp_status s = ensure_workspace(Pr, off * n_teams);
     if (s != LRP_OK) return s;
     prm.ws = Pr->ws;
@@ -225,6 +237,12 @@ lrp_status run_sweep_ex(lrp_problem* Pr, unsigned stages, int nvec, const double
   prm.stats = Pr->stats;
   cudaError_t e = cudaMemsetAsync(Pr->stats, 0, sizeof(Stats), Pr->stream);
   if (e != cudaSuccess) return cuda_status(e, "stats reset");
+  if (info) {
+    info->fast = fast;
+    info->BV = BV;
+    info->n_teams = n_teams;
+    info->mixed = mixed;
+  }
   if (Pr->prof_on) cudaEventRecord(Pr->prof_ev[0], Pr->stream);
 #ifdef LRP_SECTION_TIMERS
   static unsigned long long* sec_buf = nullptr;
@@ -244,42 +262,36 @@ lrp_status run_sweep_ex(lrp_problem* Pr, unsigned stages, int nvec, const double
   if (e != cudaSuccess) return cuda_status(e, "sweep launch");
   note_launch();
   if (Pr->prof_on) cudaEventRecord(Pr->prof_ev[1], Pr->stream);
-  Stats hs;
-  e = cudaMemcpyAsync(&hs, Pr->stats, sizeof(Stats), cudaMemcpyDeviceToHost, Pr->stream);
-  if (e != cudaSuccess) return cuda_status(e, "stats copy");
-  e = cudaStreamSynchronize(Pr->stream);
-  if (e != cudaSuccess) return cuda_status(e, "sweep");
-  if (Pr->prof_on) {
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, Pr->prof_ev[0], Pr->prof_ev[1]);
-    const double ab = algorithmic_bytes(Pr, hs, BV, mixed);
-    for (int v : {0, fast ? 2 : 1}) {
-      Pr->prof_ms[v] += ms;
-      Pr->prof_launches[v] += 1;
-      Pr->prof_bytes[v] += ab;
-    }
-  }
-  if (st) {
-    std::memset(st, 0, sizeof(*st));
-    const double nteams_cols = (double)n_teams;
-    st->n_solves = (int)(hs.solves / (unsigned long long)std::max(1, n_teams));
-    st->pcg_iters_max = hs.iters_max;
-    st->pcg_iters_mean = hs.solves ? (double)hs.iters / (double)hs.solves : 0.0;
-    (void)nteams_cols;
-    st->refine_max = hs.refine_max;
-    double mr;
-    std::memcpy(&mr, &hs.max_rel_res_bits, sizeof(double));
-    st->max_rel_residual = mr;
-    st->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (hs_dst) {
+    e = cudaMemcpyAsync(hs_dst, Pr->stats, sizeof(Stats), cudaMemcpyDeviceToHost, Pr->stream);
+    if (e != cudaSuccess) return cuda_status(e, "stats copy");
   }
 #ifdef LRP_SECTION_TIMERS
   if (fast) {
+    cudaStreamSynchronize(Pr->stream);
     unsigned long long sc[8];
     cudaMemcpy(sc, prm.section_cycles, sizeof(sc), cudaMemcpyDeviceToHost);
     std::fprintf(stderr, "[sections] band %.3e sync %.3e coarse %.3e refine %.3e reduce %.3e total %.3e cycles\n",
                  (double)sc[0], (double)sc[1], (double)sc[2], (double)sc[3], (double)sc[4], (double)sc[7]);
   }
 #endif
+  return LRP_OK;
+}
+
+// Status of a completed sweep launch from its stats (and the caller's stats
+// record, if st is not NULL).
+lrp_status sweep_status(const Stats& hs, const SweepLaunch& info, lrp_apply_stats* st, double ms) {
+  if (st) {
+    std::memset(st, 0, sizeof(*st));
+    st->n_solves = (int)(hs.solves / (unsigned long long)std::max(1, info.n_teams));
+    st->pcg_iters_max = hs.iters_max;
+    st->pcg_iters_mean = hs.solves ? (double)hs.iters / (double)hs.solves : 0.0;
+    st->refine_max = hs.refine_max;
+    double mr;
+    std::memcpy(&mr, &hs.max_rel_res_bits, sizeof(double));
+    st->max_rel_residual = mr;
+    st->ms = ms;
+  }
   if (hs.status & STAT_NONFINITE) {
     set_error("non-finite value in a spatial solve");
     return LRP_ENONFINITE;
@@ -289,6 +301,31 @@ lrp_status run_sweep_ex(lrp_problem* Pr, unsigned stages, int nvec, const double
     return LRP_ENOCONV;
   }
   return LRP_OK;
+}
+
+lrp_status run_sweep_ex(lrp_problem* Pr, unsigned stages, int nvec, const double* X, int ldx, double* Y, int ldy,
+                        const double* Din, int lddin, double* Dout, int lddout, lrp_apply_stats* st, int t_begin,
+                        int t_end, double* traj, int traj_cols) {
+  auto t0 = std::chrono::steady_clock::now();
+  Stats hs;
+  SweepLaunch info;
+  lrp_status s = sweep_enqueue(Pr, stages, nvec, X, ldx, Y, ldy, Din, lddin, Dout, lddout, t_begin, t_end, traj,
+                               traj_cols, &hs, &info);
+  if (s != LRP_OK) return s;
+  cudaError_t e = cudaStreamSynchronize(Pr->stream);
+  if (e != cudaSuccess) return cuda_status(e, "sweep");
+  if (Pr->prof_on) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, Pr->prof_ev[0], Pr->prof_ev[1]);
+    const double ab = algorithmic_bytes(Pr, hs, info.BV, info.mixed);
+    for (int v : {0, info.fast ? 2 : 1}) {
+      Pr->prof_ms[v] += ms;
+      Pr->prof_launches[v] += 1;
+      Pr->prof_bytes[v] += ab;
+    }
+  }
+  return sweep_status(hs, info, st,
+                      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
 }
 
 }  // namespace lrp

@@ -260,3 +260,27 @@ def test_autotune_keeps_results(precision):
     U = synth.normal_block(P.nx, 4, 9)
     H, st = lrp.lrp_hessian_apply(G, U)
     assert relerr(H, P.hessian_apply(U)) < TOL[precision], st
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_batched_lanczos_matches_single_runs(use_graph):
+    """Several problems of different sizes (2D mixed, 2D FP64, 3D mixed with
+    kappa) in one batched block Lanczos (one CUDA graph per block step): each
+    problem's eigenvalues equal those of its own single run and the oracle's."""
+    specs = [(synth.small_spec(dim=2, n=31, nt=16, obs_every=2, n_obs=12, sigma=1e-2, seed=51), lrp.LRP_MIXED),
+             (synth.small_spec(dim=2, n=15, nt=24, obs_every=3, n_obs=8, sigma=1e-2, seed=52), lrp.LRP_FP64),
+             (synth.small_spec(dim=3, n=7, nt=10, obs_every=2, n_obs=9, sigma=1e-2, with_kappa=True, seed=53),
+              lrp.LRP_MIXED)]
+    k = 8
+    streams = [torch.cuda.Stream() for _ in specs]
+    probs = [lrp.lrp_setup_problem(sp, precision=pr, stream=st) for (sp, pr), st in zip(specs, streams)]
+    res, bst = lrp.lrp_batch_lowrank_posterior(probs, k=k, block=4, eig_tol=1e-10, use_graph=use_graph)
+    assert bst["steps"] >= 1 and bst["n_matvec"] == sum(s["n_matvec"] for _, s in res)
+    if use_graph:
+        assert bst["graph_nodes"] > 0
+    for ((sp, pr), G, (post, st)) in zip(specs, probs, res):
+        lam = post.eigs()
+        single, _ = lrp.lrp_lowrank_posterior(G, k=k, block=4, eig_tol=1e-10)
+        np.testing.assert_allclose(lam, single.eigs(), rtol=1e-12, atol=0)
+        lam_ref = ospec.eig_dense(OProblem(sp).hessian_explicit())[0][:k]
+        _check_eigs(lam, lam_ref, TOL[pr] * 10, 1e-3)
