@@ -195,15 +195,24 @@ struct LanczosRun {
     return LRP_OK;
   }
 
+  // timing event: an event-record node when the stream is being captured
+  static cudaError_t mark(cudaEvent_t e, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t err = cudaStreamIsCapturing(s, &cs);
+    if (err != cudaSuccess) return err;
+    return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal)
+                                               : cudaEventRecord(e, s);
+  }
+
   lrp_status enqueue_step() {
     cudaStream_t s = P->stream;
     const int c0 = j * nb;
     cols = c0 + nb;
-    CK(cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal));
+    CK(mark(ev[0], s));
     lrp_status st = sweep_enqueue(P, HESS_STAGES, nb, Q.p + (size_t)c0 * nx, nx, W.p, nx, nullptr, 0, nullptr, 0, 0,
                                   -1, nullptr, 0, h_stats, &info);
     if (st != LRP_OK) return st;
-    CK(cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal));
+    CK(mark(ev[1], s));
     // full re-orthogonalisation (CGS2 against the whole basis), the
     // coefficients of block j give A_j; block CGS2 of the remainder gives B_j
     CK(cudaMemsetAsync(ws.C2.p, 0, (size_t)cols * nb * sizeof(double), s));
@@ -230,7 +239,10 @@ struct LanczosRun {
   // after the stream (or the graph holding the step) has completed
   lrp_status after_step() {
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess) ms_apply += ms;
+    if (cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess)
+      ms_apply += ms;
+    else
+      cudaGetLastError();  // no timing for this step; do not leave the error for later checks
     n_matvec += nb;
     ++n_iter;
     lrp_status st = sweep_status(*h_stats, info, nullptr, 0.0);
