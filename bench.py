@@ -235,8 +235,7 @@ def batched_bench(lrp, count: int, block: int, steps: int, use_graph: bool = Tru
     (the whole run to k=50 takes minutes). One autotune per grid size."""
     import torch
     insts = synth.batched_instances(count=count)
-    streams = [torch.cuda.Stream() for _ in insts]
-    probs = [lrp.lrp_setup_problem(sp, precision=lrp.LRP_MIXED, stream=st) for sp, st in zip(insts, streams)]
+    probs = [lrp.lrp_setup_problem(sp, precision=lrp.LRP_MIXED) for sp in insts]
     t0 = time.perf_counter()
     tuned = {}
     for sp, G in zip(insts, probs):

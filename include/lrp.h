@@ -251,11 +251,12 @@ void lrp_posterior_destroy(lrp_posterior* post);
  * form). Runs the block Lanczos of lrp_lowrank_posterior (eig_threshold 0,
  * default basis cap, pseudo-random start) on `count` independent problems of
  * any sizes at once: every block step of every problem not yet converged is
- * enqueued on that problem's own stream and, with use_graph, the whole step
- * is captured into one CUDA graph and launched once (otherwise launched
- * directly); problems drop out as they converge. The problems' streams must
- * be distinct non-default streams (lrp_setup_problem's cuda_stream) and on
- * one device. outs[i] and stats[i] (stats may be NULL) as in
+ * enqueued on a stream of that problem's own (created for the call; the
+ * problem's stream is drained first and restored at the end) and, with
+ * use_graph, the whole step is captured into one CUDA graph and launched
+ * once (otherwise launched directly); problems drop out as they converge.
+ * The problems must be distinct and on one device. outs[i] and stats[i]
+ * (stats may be NULL) as in
  * lrp_lowrank_posterior; *bst (may be NULL) gets totals. Each result equals
  * that of lrp_lowrank_posterior on the same problem (same kernels in the
  * same order on its stream). max_steps > 0 stops after that many block

@@ -506,11 +506,14 @@ __global__ void k_add_vec_cols(int nx, int nc, const double* m, double* Y, int l
 // set to zero and its diagonal entry of R is 0. Output: B = Q R with R
 // (s x s, col-major) upper triangular; zero columns of Q have zero rows in R.
 #define GS_NT 512
+#define GS_MAXC 64
 __global__ void __launch_bounds__(GS_NT) k_block_gs(int nx, int s, double* B, size_t strideB, int ldb,
                                                      double* R, size_t strideR, double drop_tol,
                                                      int* ndrop) {
   __shared__ double s_part[GS_NT / 32][17];
   __shared__ double s_tot[17];
+  __shared__ double s_h[GS_MAXC];   // projections of the current column on the previous ones
+  __shared__ double s_rc[GS_MAXC];  // their sum over the passes (column c of R)
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   double* Bb = B + blockIdx.x * strideB;
   double* Rb = R + blockIdx.x * strideR;
@@ -533,40 +536,36 @@ __global__ void __launch_bounds__(GS_NT) k_block_gs(int nx, int s, double* B, si
   int dropped = 0;
   for (int c = 0; c < s; ++c) {
     double* w = Bb + (size_t)c * ldb;
-    double rc[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) rc[i] = 0.0;
+    if (tid < GS_MAXC) s_rc[tid] = 0.0;
     double n0 = 0.0, nprev = 0.0, ncur = 0.0;
     for (int pass = 0; pass < 4; ++pass) {
-      // h = Q[:, :c]^T w and |w|^2
-      double acc[17];
+      // h = Q[:, :c]^T w in chunks of 16 previous columns, |w|^2 with the first
+      const int nchunk = c > 0 ? (c + 15) / 16 : 1;
+      for (int q = 0; q < nchunk; ++q) {
+        const int i0 = q * 16, ni = min(16, c - i0);
+        double acc[17];
 #pragma unroll
-      for (int i = 0; i < 17; ++i) acc[i] = 0.0;
-      for (int p = tid; p < nx; p += GS_NT) {
-        const double wp = w[p];
+        for (int i = 0; i < 17; ++i) acc[i] = 0.0;
+        for (int p = tid; p < nx; p += GS_NT) {
+          const double wp = w[p];
 #pragma unroll
-        for (int i = 0; i < 16; ++i)
-          if (i < c) acc[i] += Bb[(size_t)i * ldb + p] * wp;
-        acc[16] += wp * wp;
+          for (int i = 0; i < 16; ++i)
+            if (i < ni) acc[i] += Bb[(size_t)(i0 + i) * ldb + p] * wp;
+          if (q == 0) acc[16] += wp * wp;
+        }
+        reduce17(acc);
+        if (tid < ni) s_h[i0 + tid] = s_tot[tid];
+        if (q == 0) ncur = s_tot[16];
       }
-      reduce17(acc);
-      ncur = s_tot[16];
       if (pass == 0) n0 = ncur;
       // stop after two projections, or a third one if the norm collapsed
       const bool more = (c > 0) && (pass < 2 || (pass == 2 && ncur < 1e-2 * nprev));
       if (!more) break;
-      double h[16];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        h[i] = (i < c) ? s_tot[i] : 0.0;
-        rc[i] += h[i];
-      }
-      __syncthreads();
+      __syncthreads();  // every s_h entry written
+      if (tid < c) s_rc[tid] += s_h[tid];
       for (int p = tid; p < nx; p += GS_NT) {
         double v = w[p];
-#pragma unroll
-        for (int i = 0; i < 16; ++i)
-          if (i < c) v -= h[i] * Bb[(size_t)i * ldb + p];
+        for (int i = 0; i < c; ++i) v -= s_h[i] * Bb[(size_t)i * ldb + p];
         w[p] = v;
       }
       __syncthreads();
@@ -576,8 +575,9 @@ __global__ void __launch_bounds__(GS_NT) k_block_gs(int nx, int s, double* B, si
     const bool drop = !(nrm > drop_tol * sqrt(n0)) || !(nrm > 0.0);
     const double scale = drop ? 0.0 : 1.0 / nrm;
     for (int p = tid; p < nx; p += GS_NT) w[p] *= scale;
+    __syncthreads();  // s_rc complete
     if (tid == 0) {
-      for (int i = 0; i < s; ++i) Rb[(size_t)c * s + i] = (i < c) ? rc[i] : (i == c ? (drop ? 0.0 : nrm) : 0.0);
+      for (int i = 0; i < s; ++i) Rb[(size_t)c * s + i] = (i < c) ? s_rc[i] : (i == c ? (drop ? 0.0 : nrm) : 0.0);
     }
     dropped += drop ? 1 : 0;
     __syncthreads();
@@ -715,7 +715,7 @@ cudaError_t add_vec_cols(cudaStream_t s, int nx, int nc, const double* m, double
 
 cudaError_t block_gs(cudaStream_t s, int batch, int nx, int ncols, double* B, size_t strideB, int ldb, double* R,
                      size_t strideR, double drop_tol, int* ndrop) {
-  if (ncols > 16) return cudaErrorInvalidValue;
+  if (ncols > GS_MAXC) return cudaErrorInvalidValue;
   note_launch();
   k_block_gs<<<batch, GS_NT, 0, s>>>(nx, ncols, B, strideB, ldb, R, strideR, drop_tol, ndrop);
   return cudaGetLastError();

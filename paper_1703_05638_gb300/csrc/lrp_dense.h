@@ -20,7 +20,7 @@ cudaError_t small_mm(cudaStream_t s, int nb, const double* A, const double* B, d
 // theta decreasing, Z eigenvectors; A destroyed; work >= 6n doubles; n <= 1024.
 cudaError_t eig_sym(cudaStream_t s, int n, double* A, int lda, double* Z, int ldz, double* theta,
                     double* work, int* status);
-// Rank-revealing block CGS2 of `batch` matrices (nx x ncols, ncols <= 16),
+// Rank-revealing block CGS2 of `batch` matrices (nx x ncols, ncols <= 64),
 // in place; R (ncols x ncols per matrix) upper triangular; columns numerically
 // dependent on the previous ones (relative remainder <= drop_tol) become zero
 // with a zero diagonal in R; ndrop[b] (may be NULL) counts them.

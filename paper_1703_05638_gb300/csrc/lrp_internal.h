@@ -217,6 +217,7 @@ lrp_status sweep_enqueue(lrp_problem* Pr, unsigned stages, int nvec, const doubl
                          const double* Din, int lddin, double* Dout, int lddout, int t_begin, int t_end,
                          double* traj, int traj_cols, Stats* hs_dst, SweepLaunch* info);
 lrp_status sweep_status(const Stats& hs, const SweepLaunch& info, lrp_apply_stats* st, double ms);
+void ledger_add(lrp_problem* Pr, const Stats& hs, const SweepLaunch& info, double ms);
 lrp_status run_sweep(lrp_problem* P, unsigned stages, int nvec, const double* X, int ldx,
                      double* Y, int ldy, const double* Din, int lddin, double* Dout,
                      int lddout, lrp_apply_stats* st, bool misfit_only);

@@ -57,7 +57,7 @@ static const unsigned HESS_STAGES = ST_LOAD_X | ST_PRIOR_IN | ST_FORWARD | ST_AD
 
 // Scratch of one Lanczos run.
 struct LanczosWS {
-  DArr<double> part, G, R1, R2, Ri1, Ri2, R, R16, C1, C2;
+  DArr<double> part, G, R1, R2, Ri1, Ri2, R, C1, C2;
   DArr<int> flags;
   size_t part_cap = 0;
 };
@@ -75,25 +75,7 @@ static lrp_status block_orth(lrp_problem* P, int nx, int nb, double* Wn, const d
     CK(gemm_nn(s, nx, nprev, nb, -1.0, Q, nx, ws.C1.p, nprev, 1.0, Wn, nx));
     if (Cacc) CK(axpby(s, (size_t)nprev * nb, 1.0, ws.C1.p, 1.0, Cacc));
   }
-  if (nb <= 16) {
-    CK(block_gs(s, 1, nx, nb, Wn, 0, nx, ws.R.p, 0, 1e-13, nullptr));
-    return LRP_OK;
-  }
-  // wider blocks: sub-blocks of 16 columns, each made orthogonal to the
-  // finished ones by CGS2 (coefficients into R above the diagonal block),
-  // then rank-revealing CGS2 inside the sub-block (its diagonal block of R)
-  CK(cudaMemsetAsync(ws.R.p, 0, (size_t)nb * nb * sizeof(double), s));
-  for (int c0 = 0; c0 < nb; c0 += 16) {
-    const int w = std::min(16, nb - c0);
-    double* Ws = Wn + (size_t)c0 * nx;
-    for (int pass = 0; pass < 2 && c0 > 0; ++pass) {
-      CK(gemm_tn(s, nx, c0, w, Wn, nx, Ws, nx, ws.C1.p, c0, 1.0, 0.0, ws.part.p, ws.part_cap));
-      CK(gemm_nn(s, nx, c0, w, -1.0, Wn, nx, ws.C1.p, c0, 1.0, Ws, nx));
-      CK(add_block(s, c0, w, ws.C1.p, c0, ws.R.p + (size_t)c0 * nb, nb));
-    }
-    CK(block_gs(s, 1, nx, w, Ws, 0, nx, ws.R16.p, 0, 1e-13, nullptr));
-    CK(add_block(s, w, w, ws.R16.p, w, ws.R.p + (size_t)c0 * nb + c0, nb));
-  }
+  CK(block_gs(s, 1, nx, nb, Wn, 0, nx, ws.R.p, 0, 1e-13, nullptr));
   return LRP_OK;
 }
 
@@ -165,7 +147,6 @@ struct LanczosRun {
     CK(ws.Ri1.alloc(nb * nb));
     CK(ws.Ri2.alloc(nb * nb));
     CK(ws.R.alloc(nb * nb));
-    CK(ws.R16.alloc(16 * 16));
     CK(ws.C1.alloc((size_t)(mmax + nb) * nb));
     CK(ws.C2.alloc((size_t)(mmax + nb) * nb));
     CK(ws.flags.alloc(nb));
@@ -239,10 +220,12 @@ struct LanczosRun {
   // after the stream (or the graph holding the step) has completed
   lrp_status after_step() {
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess)
+    if (cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess) {
       ms_apply += ms;
-    else
+      ledger_add(P, *h_stats, info, ms);
+    } else {
       cudaGetLastError();  // no timing for this step; do not leave the error for later checks
+    }
     n_matvec += nb;
     ++n_iter;
     lrp_status st = sweep_status(*h_stats, info, nullptr, 0.0);
@@ -373,12 +356,34 @@ lrp_status lrp_batch_lowrank_posterior(lrp_problem* const* probs, int count, int
       return LRP_EINVAL;
     }
     for (int j = 0; j < i; ++j)
-      if (probs[j]->stream == probs[i]->stream) {
-        set_error("lrp_batch_lowrank_posterior: the problems need distinct streams");
+      if (probs[j] == probs[i]) {
+        set_error("lrp_batch_lowrank_posterior: a problem appears twice");
         return LRP_EINVAL;
       }
   }
   cudaSetDevice(probs[0]->device);
+  // every problem works on a private stream for the duration of the call
+  // (its own stream is drained first and restored at the end)
+  struct StreamSwap {
+    std::vector<lrp_problem*> probs;
+    std::vector<cudaStream_t> saved, own;
+    ~StreamSwap() {
+      for (size_t i = 0; i < own.size(); ++i) {
+        cudaStreamSynchronize(own[i]);
+        probs[i]->stream = saved[i];
+        cudaStreamDestroy(own[i]);
+      }
+    }
+  } swap;
+  for (int i = 0; i < count; ++i) {
+    cudaStream_t ps = nullptr;
+    CK(cudaStreamSynchronize(probs[i]->stream));
+    CK(cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking));
+    swap.probs.push_back(probs[i]);
+    swap.saved.push_back(probs[i]->stream);
+    swap.own.push_back(ps);
+    probs[i]->stream = ps;
+  }
   auto t0 = std::chrono::steady_clock::now();
   std::vector<std::unique_ptr<LanczosRun>> runs(count);
   for (int i = 0; i < count; ++i) {

@@ -278,6 +278,17 @@ lrp_status sweep_enqueue(lrp_problem* Pr, unsigned stages, int nvec, const doubl
   return LRP_OK;
 }
 
+// Adds a completed launch to the problem's sweep ledger (when recording).
+void ledger_add(lrp_problem* Pr, const Stats& hs, const SweepLaunch& info, double ms) {
+  if (!Pr->prof_on) return;
+  const double ab = algorithmic_bytes(Pr, hs, info.BV, info.mixed);
+  for (int v : {0, info.fast ? 2 : 1}) {
+    Pr->prof_ms[v] += ms;
+    Pr->prof_launches[v] += 1;
+    Pr->prof_bytes[v] += ab;
+  }
+}
+
 // Status of a completed sweep launch from its stats (and the caller's stats
 // record, if st is not NULL).
 lrp_status sweep_status(const Stats& hs, const SweepLaunch& info, lrp_apply_stats* st, double ms) {
@@ -317,12 +328,7 @@ lrp_status run_sweep_ex(lrp_problem* Pr, unsigned stages, int nvec, const double
   if (Pr->prof_on) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, Pr->prof_ev[0], Pr->prof_ev[1]);
-    const double ab = algorithmic_bytes(Pr, hs, info.BV, info.mixed);
-    for (int v : {0, info.fast ? 2 : 1}) {
-      Pr->prof_ms[v] += ms;
-      Pr->prof_launches[v] += 1;
-      Pr->prof_bytes[v] += ab;
-    }
+    ledger_add(Pr, hs, info, ms);
   }
   return sweep_status(hs, info, st,
                       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());

@@ -272,8 +272,7 @@ def test_batched_lanczos_matches_single_runs(use_graph):
              (synth.small_spec(dim=3, n=7, nt=10, obs_every=2, n_obs=9, sigma=1e-2, with_kappa=True, seed=53),
               lrp.LRP_MIXED)]
     k = 8
-    streams = [torch.cuda.Stream() for _ in specs]
-    probs = [lrp.lrp_setup_problem(sp, precision=pr, stream=st) for (sp, pr), st in zip(specs, streams)]
+    probs = [lrp.lrp_setup_problem(sp, precision=pr) for sp, pr in specs]
     res, bst = lrp.lrp_batch_lowrank_posterior(probs, k=k, block=4, eig_tol=1e-10, use_graph=use_graph)
     assert bst["steps"] >= 1 and bst["n_matvec"] == sum(s["n_matvec"] for _, s in res)
     if use_graph:
