@@ -44,9 +44,9 @@ UNIT = "matvec/s"
 # committed ncu summary (DRAM traffic per launch) for this workload.
 KERNELS = {
     1: ("sweep_kernel", "persistent cluster-team MG-PCG forward/adjoint sweeps",
-        ["lrp_sweep_kernel.cuh", "lrp_team.cuh", "lrp_sweep.cu"]),
+        ["lrp_sweep_kernel.cuh", "lrp_team.cuh"]),
     2: ("fast2d_kernel", "2D band kernel: shared-memory MG-PCG forward/adjoint sweeps",
-        ["lrp_fast2d.cuh", "lrp_team.cuh", "lrp_sweep_fast.cu", "lrp_sweep.cu"]),
+        ["lrp_fast2d.cuh", "lrp_sweep_kernel.cuh", "lrp_team.cuh", "lrp_sweep_fast.cu"]),
 }
 
 

@@ -6,7 +6,9 @@ namespace lrp {
 static cudaError_t prepare_fast2d(size_t smem) {
   cudaError_t e = cudaFuncSetAttribute(fast2d_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(fast2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int cap = smem_optin_max();  // one value for every launcher (see prepare_sweep)
+  if ((long long)smem > cap) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(fast2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
 }
 
 cudaError_t launch_fast2d(const SweepParams& prm, cudaStream_t stream) {

@@ -594,12 +594,25 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
   }
 }
 
+// The shared-memory cap of a kernel is one value per function: it is always
+// set to the device's opt-in maximum (the same value from every thread), so
+// concurrent launchers with different shared-memory sizes cannot lower it
+// under one another; each launch states its own size.
+inline int smem_optin_max() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return v;
+}
+
 template <typename T, int DIM, bool MIXED>
 static cudaError_t prepare_sweep(size_t smem) {
   auto kern = sweep_kernel<T, DIM, MIXED>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int cap = smem_optin_max();
+  if ((long long)smem > cap) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
 }
 
 template <typename T, int DIM, bool MIXED>
