@@ -509,7 +509,7 @@ __global__ void k_add_vec_cols(int nx, int nc, const double* m, double* Y, int l
 #define GS_MAXC 64
 __global__ void __launch_bounds__(GS_NT) k_block_gs(int nx, int s, double* B, size_t strideB, int ldb,
                                                      double* R, size_t strideR, double drop_tol,
-                                                     int* ndrop) {
+                                                     const double* ref_norm2, int* ndrop) {
   __shared__ double s_part[GS_NT / 32][17];
   __shared__ double s_tot[17];
   __shared__ double s_h[GS_MAXC];   // projections of the current column on the previous ones
@@ -572,7 +572,10 @@ __global__ void __launch_bounds__(GS_NT) k_block_gs(int nx, int s, double* B, si
       nprev = ncur;
     }
     const double nrm = sqrt(ncur);
-    const bool drop = !(nrm > drop_tol * sqrt(n0)) || !(nrm > 0.0);
+    // dependent: what is left is at most drop_tol of the column's norm on
+    // entry, or of its norm before the caller's earlier projections
+    const double nref = ref_norm2 ? fmax(n0, ref_norm2[(size_t)blockIdx.x * s + c]) : n0;
+    const bool drop = !(nrm > drop_tol * sqrt(nref)) || !(nrm > 0.0);
     const double scale = drop ? 0.0 : 1.0 / nrm;
     for (int p = tid; p < nx; p += GS_NT) w[p] *= scale;
     __syncthreads();  // s_rc complete
@@ -714,10 +717,10 @@ cudaError_t add_vec_cols(cudaStream_t s, int nx, int nc, const double* m, double
 }
 
 cudaError_t block_gs(cudaStream_t s, int batch, int nx, int ncols, double* B, size_t strideB, int ldb, double* R,
-                     size_t strideR, double drop_tol, int* ndrop) {
+                     size_t strideR, double drop_tol, int* ndrop, const double* ref_norm2) {
   if (ncols > GS_MAXC) return cudaErrorInvalidValue;
   note_launch();
-  k_block_gs<<<batch, GS_NT, 0, s>>>(nx, ncols, B, strideB, ldb, R, strideR, drop_tol, ndrop);
+  k_block_gs<<<batch, GS_NT, 0, s>>>(nx, ncols, B, strideB, ldb, R, strideR, drop_tol, ref_norm2, ndrop);
   return cudaGetLastError();
 }
 

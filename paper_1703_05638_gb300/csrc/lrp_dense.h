@@ -24,8 +24,11 @@ cudaError_t eig_sym(cudaStream_t s, int n, double* A, int lda, double* Z, int ld
 // in place; R (ncols x ncols per matrix) upper triangular; columns numerically
 // dependent on the previous ones (relative remainder <= drop_tol) become zero
 // with a zero diagonal in R; ndrop[b] (may be NULL) counts them.
+// ref_norm2 (may be NULL): squared column norms before the caller's earlier
+// projections ([batch][ncols]); a column is then dependent if its remainder
+// is at most drop_tol of the larger of that norm and its norm on entry.
 cudaError_t block_gs(cudaStream_t s, int batch, int nx, int ncols, double* B, size_t strideB, int ldb, double* R,
-                     size_t strideR, double drop_tol, int* ndrop);
+                     size_t strideR, double drop_tol, int* ndrop, const double* ref_norm2 = nullptr);
 // Batched eigensolver: matrix b has size n_dev[b] <= nmax, ld = its size.
 cudaError_t eig_sym_batched(cudaStream_t s, int batch, const int* n_dev, int nmax, double* A, size_t strideA,
                             double* Z, size_t strideZ, double* theta, size_t strideT, double* work,

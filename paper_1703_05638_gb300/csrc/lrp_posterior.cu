@@ -57,7 +57,7 @@ static const unsigned HESS_STAGES = ST_LOAD_X | ST_PRIOR_IN | ST_FORWARD | ST_AD
 
 // Scratch of one Lanczos run.
 struct LanczosWS {
-  DArr<double> part, G, R1, R2, Ri1, Ri2, R, C1, C2;
+  DArr<double> part, G, R1, R2, Ri1, Ri2, R, C1, C2, ref;
   DArr<int> flags;
   size_t part_cap = 0;
 };
@@ -70,12 +70,16 @@ struct LanczosWS {
 static lrp_status block_orth(lrp_problem* P, int nx, int nb, double* Wn, const double* Q, int nprev,
                              LanczosWS& ws, double* Cacc) {
   cudaStream_t s = P->stream;
+  // norms before the projection: a column whose remainder is rounding noise
+  // relative to them is dependent (deflated), even if the remainder is large
+  // relative to itself
+  if (nprev > 0) CK(col_norm2(s, nx, nb, Wn, nx, ws.ref.p));
   for (int pass = 0; pass < 2 && nprev > 0; ++pass) {
     CK(gemm_tn(s, nx, nprev, nb, Q, nx, Wn, nx, ws.C1.p, nprev, 1.0, 0.0, ws.part.p, ws.part_cap));
     CK(gemm_nn(s, nx, nprev, nb, -1.0, Q, nx, ws.C1.p, nprev, 1.0, Wn, nx));
     if (Cacc) CK(axpby(s, (size_t)nprev * nb, 1.0, ws.C1.p, 1.0, Cacc));
   }
-  CK(block_gs(s, 1, nx, nb, Wn, 0, nx, ws.R.p, 0, 1e-13, nullptr));
+  CK(block_gs(s, 1, nx, nb, Wn, 0, nx, ws.R.p, 0, 1e-13, nullptr, nprev > 0 ? ws.ref.p : nullptr));
   return LRP_OK;
 }
 
@@ -150,6 +154,7 @@ struct LanczosRun {
     CK(ws.C1.alloc((size_t)(mmax + nb) * nb));
     CK(ws.C2.alloc((size_t)(mmax + nb) * nb));
     CK(ws.flags.alloc(nb));
+    CK(ws.ref.alloc(nb));
     CK(cudaMallocHost(&h_theta, mmax * sizeof(double)));
     CK(cudaMallocHost(&h_res, mmax * sizeof(double)));
     CK(cudaMallocHost(&h_stats, sizeof(Stats)));

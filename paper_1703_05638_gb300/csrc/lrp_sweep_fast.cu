@@ -6,7 +6,7 @@ namespace lrp {
 static cudaError_t prepare_fast2d(size_t smem) {
   cudaError_t e = cudaFuncSetAttribute(fast2d_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
-  const int cap = smem_optin_max();  // one value for every launcher (see prepare_sweep)
+  const int cap = smem_dynamic_max(fast2d_kernel);  // one value for every launcher (see prepare_sweep)
   if ((long long)smem > cap) return cudaErrorInvalidValue;
   return cudaFuncSetAttribute(fast2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
 }

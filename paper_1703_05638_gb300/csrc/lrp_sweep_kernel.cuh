@@ -598,11 +598,15 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
 // set to the device's opt-in maximum (the same value from every thread), so
 // concurrent launchers with different shared-memory sizes cannot lower it
 // under one another; each launch states its own size.
-inline int smem_optin_max() {
+// (the opt-in per-block maximum less the kernel's static shared memory)
+template <class K>
+inline int smem_dynamic_max(K kern) {
   int dev = 0, v = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  return v;
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return 0;
+  return v - (int)fa.sharedSizeBytes;
 }
 
 template <typename T, int DIM, bool MIXED>
@@ -610,7 +614,7 @@ static cudaError_t prepare_sweep(size_t smem) {
   auto kern = sweep_kernel<T, DIM, MIXED>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
-  const int cap = smem_optin_max();
+  const int cap = smem_dynamic_max(kern);
   if ((long long)smem > cap) return cudaErrorInvalidValue;
   return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
 }
