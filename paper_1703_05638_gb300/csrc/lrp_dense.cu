@@ -812,4 +812,24 @@ cudaError_t add_block(cudaStream_t s, int m, int n, const double* S, int lds, do
   return cudaGetLastError();
 }
 
+// T[r0:r0+m, c0:c0+n] = S (m x n, ld lds) and, if also_transpose, the
+// mirrored block T[c0:c0+n, r0:r0+m] = S^T.
+__global__ void k_set_rect(double* T, int ldt, int r0, int c0, int m, int n, const double* S, int lds,
+                           int also_transpose) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * n) return;
+  const int i = e % m, j = e / m;
+  const double v = S[(size_t)j * lds + i];
+  T[(size_t)(c0 + j) * ldt + r0 + i] = v;
+  if (also_transpose) T[(size_t)(r0 + i) * ldt + c0 + j] = v;
+}
+
+cudaError_t set_rect(cudaStream_t s, double* T, int ldt, int r0, int c0, int m, int n, const double* S, int lds,
+                     bool also_transpose) {
+  if (m <= 0 || n <= 0) return cudaSuccess;
+  note_launch();
+  k_set_rect<<<(m * n + 255) / 256, 256, 0, s>>>(T, ldt, r0, c0, m, n, S, lds, also_transpose ? 1 : 0);
+  return cudaGetLastError();
+}
+
 }  // namespace lrp

@@ -50,6 +50,9 @@ cudaError_t col_norm2(cudaStream_t s, int nx, int nc, const double* X, int ldx, 
 cudaError_t axpby(cudaStream_t s, size_t n, double a, const double* x, double b, double* y);
 cudaError_t add_vec_cols(cudaStream_t s, int nx, int nc, const double* m, double* Y, int ldy);
 
+// T[r0:r0+m, c0:c0+n] = S (m x n, ld lds), and the mirrored block if also_transpose.
+cudaError_t set_rect(cudaStream_t s, double* T, int ldt, int r0, int c0, int m, int n, const double* S, int lds,
+                     bool also_transpose);
 // D[0:m, 0:n] += S[0:m, 0:n] (column-major).
 cudaError_t add_block(cudaStream_t s, int m, int n, const double* S, int lds, double* D, int ldd);
 // Diagonal of (I + alpha L0)^-2 on the n^dim grid (constant-coefficient

@@ -68,7 +68,7 @@ struct LanczosWS {
 // triangular in ws.R. A column numerically inside the span of the others
 // becomes zero with a zero diagonal in R (block-Lanczos deflation).
 static lrp_status block_orth(lrp_problem* P, int nx, int nb, double* Wn, const double* Q, int nprev,
-                             LanczosWS& ws, double* Cacc) {
+                             LanczosWS& ws, double* Cacc, double drop_tol) {
   cudaStream_t s = P->stream;
   // norms before the projection: a column whose remainder is rounding noise
   // relative to them is dependent (deflated), even if the remainder is large
@@ -79,7 +79,7 @@ static lrp_status block_orth(lrp_problem* P, int nx, int nb, double* Wn, const d
     CK(gemm_nn(s, nx, nprev, nb, -1.0, Q, nx, ws.C1.p, nprev, 1.0, Wn, nx));
     if (Cacc) CK(axpby(s, (size_t)nprev * nb, 1.0, ws.C1.p, 1.0, Cacc));
   }
-  CK(block_gs(s, 1, nx, nb, Wn, 0, nx, ws.R.p, 0, 1e-13, nullptr, nprev > 0 ? ws.ref.p : nullptr));
+  CK(block_gs(s, 1, nx, nb, Wn, 0, nx, ws.R.p, 0, drop_tol, nullptr, nprev > 0 ? ws.ref.p : nullptr));
   return LRP_OK;
 }
 
@@ -104,7 +104,7 @@ struct LanczosRun {
   SweepLaunch info;
   int j = 0, cols = 0, kk = 0, n_iter = 0, n_matvec = 0;
   bool check = false, last = false, converged = false, done = false;
-  double max_res = 0.0, ms_apply = 0.0;
+  double max_res = 0.0, ms_apply = 0.0, drop_tol = 1e-13;
   std::chrono::steady_clock::time_point t0;
 
   ~LanczosRun() {
@@ -171,7 +171,11 @@ struct LanczosRun {
     } else {
       CK(fill_random(s, nx, nb, Q.p, nx, nullptr, 0x5EEDull));
     }
-    lrp_status st = block_orth(P, nx, nb, Q.p, Q.p, 0, ws, nullptr);
+    // a direction whose remainder after re-orthogonalisation is below what the
+    // solves resolve (their relative tolerance, with a margin) is noise of the
+    // inexact Hessian apply, not a new Krylov direction: it is deflated
+    drop_tol = std::max(1e-13, 100.0 * P->cfg.rtol);
+    lrp_status st = block_orth(P, nx, nb, Q.p, Q.p, 0, ws, nullptr, drop_tol);
     if (st != LRP_OK) return st;
     // grow the sweep workspace for nb columns now (an empty launch), so the
     // block steps never reallocate it
@@ -202,9 +206,14 @@ struct LanczosRun {
     // full re-orthogonalisation (CGS2 against the whole basis), the
     // coefficients of block j give A_j; block CGS2 of the remainder gives B_j
     CK(cudaMemsetAsync(ws.C2.p, 0, (size_t)cols * nb * sizeof(double), s));
-    st = block_orth(P, nx, nb, W.p, Q.p, cols, ws, ws.C2.p);
+    st = block_orth(P, nx, nb, W.p, Q.p, cols, ws, ws.C2.p, drop_tol);
     if (st != LRP_OK) return st;
+    // T = Q^T Htilde Q as measured: the diagonal block A_j (symmetrised), the
+    // coupling of block j to every earlier block (the re-orthogonalisation
+    // coefficients; ~0 in exact arithmetic, kept so that T stays the exact
+    // projection when the apply is inexact), and B_j below the diagonal
     CK(set_block(s, T.p, mmax + nb, c0, c0, nb, ws.C2.p + c0, cols, true, false));
+    if (c0 > 0) CK(set_rect(s, T.p, mmax + nb, 0, c0, c0, nb, ws.C2.p, cols, true));
     CK(set_block(s, T.p, mmax + nb, cols, c0, nb, ws.R.p, nb, false, true));
     if (cols < mmax) CK(copy_cols(s, nx, nb, W.p, nx, Q.p + (size_t)cols * nx, nx));
     last = cols + nb > mmax;
