@@ -172,9 +172,10 @@ struct LanczosRun {
       CK(fill_random(s, nx, nb, Q.p, nx, nullptr, 0x5EEDull));
     }
     // a direction whose remainder after re-orthogonalisation is below what the
-    // solves resolve (their relative tolerance, with a margin) is noise of the
-    // inexact Hessian apply, not a new Krylov direction: it is deflated
-    drop_tol = std::max(1e-13, 100.0 * P->cfg.rtol);
+    // apply resolves is noise of the inexact Hessian apply (2 nt + 2 solves,
+    // each to the relative tolerance rtol), not a new Krylov direction: it is
+    // deflated. Its effect on the Ritz values would be quadratic in it.
+    drop_tol = std::max(1e-9, 1000.0 * P->cfg.rtol);
     lrp_status st = block_orth(P, nx, nb, Q.p, Q.p, 0, ws, nullptr, drop_tol);
     if (st != LRP_OK) return st;
     // grow the sweep workspace for nb columns now (an empty launch), so the
