@@ -106,7 +106,10 @@ typedef struct {
                                solved by every CTA of a team in shared memory (0 -> 1024) */
   int kernel_variant;       /* 0 auto; 1 the generic sweep kernel; 2 the band kernel (2D, kappa = 1,
                                LRP_MIXED, team_cols 1: each CTA keeps its band of rows of the finest
-                               grid in shared memory), LRP_EINVAL if it does not apply */
+                               grid in shared memory, every coarse level in every CTA); 3 the band
+                               kernel with the first coarse level split across the cluster like the
+                               finest one (each CTA owning >= 2 of its rows); LRP_EINVAL if the
+                               requested variant does not apply. Auto takes 3, else 2, else 1. */
   int mg_nu_coarse;         /* Jacobi sweeps before and after on the coarser levels of the band
                                kernel (0 -> mg_nu) */
 } lrp_problem_desc;

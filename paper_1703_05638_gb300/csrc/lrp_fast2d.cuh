@@ -321,11 +321,125 @@ __device__ __forceinline__ void fast_prolong(const Band& b, const FastVec& v, in
   }
 }
 
+// ---- level 1 split across the cluster (SweepParams::fast_split1): CTA k
+// owns the level-1 rows J whose fine centre row 2J+1 lies in its band,
+// J in [r0/2, r1/2), and keeps the full padded level-1 arrays with two halo
+// rows on each side of its own rows, written by its neighbours (the same
+// index in every CTA's copy). Every CTA owns at least two rows, so halos come
+// from the immediate neighbours only.
+struct CArr {
+  int a;
+  unsigned prev, next;
+};
+
+__device__ __forceinline__ CArr carr(const Band& b, int A) {
+  CArr r;
+  r.a = A;
+  const unsigned loc = smem_addr(A);
+  r.prev = b.rank > 0 ? cluster_addr(loc, b.rank - 1) : 0u;
+  r.next = b.rank < b.C - 1 ? cluster_addr(loc, b.rank + 1) : 0u;
+  return r;
+}
+
+// Store v at level-1 row J (owned rows [J0, J1)), and into the neighbours'
+// halo copies for the first and last two owned rows.
+__device__ __forceinline__ void cstore1(const Band& b, const CArr& A, int n1, int J0, int J1, int J, int col,
+                                        float v) {
+  const int i = cidx(n1, J, col);
+  s_fb[A.a + i] = v;
+  if (b.rank > 0 && J < J0 + 2) st_cluster(A.prev + 4u * (unsigned)i, v);
+  if (b.rank < b.C - 1 && J >= J1 - 2) st_cluster(A.next + 4u * (unsigned)i, v);
+}
+
+// Restriction of the band residual into this CTA's level-1 rows of f1, and
+// the first coarse smoother iterate e1 = sc f1 / d1, with halo copies.
+__device__ __forceinline__ void fast_restrict_split(const Band& b, const FastVec& v, int cur, float ch2, float d,
+                                                    int f1, int e1, int n1, float sc, float d1inv) {
+  const int E = v.E[cur];
+  const int J0 = b.r0 / 2, J1 = b.r1 / 2;
+  const CArr F = carr(b, f1), Ec = carr(b, e1);
+  for (int J = J0 + b.warp; J < J1; J += b.nwarp) {
+    for (int I = b.lane; I < n1; I += 32) {
+      float acc = 0.f;
+#pragma unroll
+      for (int dy = -1; dy <= 1; ++dy) {
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int i = bidx(b, b.r0, 2 * J + 1 + dy, 2 * I + 1 + dx);
+          const float res = s_fb[v.R + i] - (d * s_fb[E + i] - ch2 * bnb(b, E, i));
+          acc += (dx == 0 ? 0.5f : 0.25f) * (dy == 0 ? 0.5f : 0.25f) * res;
+        }
+      }
+      cstore1(b, F, n1, J0, J1, J, I, acc);
+      cstore1(b, Ec, n1, J0, J1, J, I, sc * acc * d1inv);
+    }
+  }
+}
+
+// Jacobi sweep on this CTA's level-1 rows (halo rows of ei read), eo with halo copies.
+__device__ __forceinline__ void csweep_split(const Band& b, const OpLevel& lv, int eo, int ei, int f, float omega) {
+  const int n = lv.n, J0 = b.r0 / 2, J1 = b.r1 / 2;
+  const float ch2 = (float)lv.ch2, d = 1.f + 4.f * ch2, dinv = (float)lv.dinv;
+  const CArr Eo = carr(b, eo);
+  for (int J = J0 + b.warp; J < J1; J += b.nwarp) {
+    const int base = cidx(n, J, 0);
+    for (int col = b.lane; col < n; col += 32) {
+      const int i = base + col;
+      const float e = s_fb[ei + i] + omega * (s_fb[f + i] - (d * s_fb[ei + i] - ch2 * cnb(ei, n, i))) * dinv;
+      cstore1(b, Eo, n, J0, J1, J, col, e);
+    }
+  }
+}
+
+// Restriction of level 1 (this CTA's rows, halos read) into the level-2 rows
+// whose centre lies in them, all-gathered into every CTA's f2 and e2.
+__device__ __forceinline__ void crestrict_split(const Band& b, const OpLevel& lf, const OpLevel& lc, int ef, int ff,
+                                                int fc, int ec, float sc) {
+  const int nf = lf.n, nc = lc.n;
+  const int J0 = b.r0 / 2, J1 = b.r1 / 2;
+  const int I0 = J0 / 2, I1 = J1 / 2;
+  const float ch2 = (float)lf.ch2, d = 1.f + 4.f * ch2, dinvc = (float)lc.dinv;
+  const unsigned fcl = smem_addr(fc), ecl = smem_addr(ec);
+  for (int I = I0 + b.warp; I < I1; I += b.nwarp) {
+    for (int K = b.lane; K < nc; K += 32) {
+      float acc = 0.f;
+#pragma unroll
+      for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int i = cidx(nf, 2 * I + 1 + dy, 2 * K + 1 + dx);
+          acc += (dx == 0 ? 0.5f : 0.25f) * (dy == 0 ? 0.5f : 0.25f) *
+                 (s_fb[ff + i] - (d * s_fb[ef + i] - ch2 * cnb(ef, nf, i)));
+        }
+      const int k = cidx(nc, I, K);
+      const float ev = sc * acc * dinvc;
+      for (int r = 0; r < b.C; ++r) {
+        if (r == b.rank) {
+          s_fb[fc + k] = acc;
+          s_fb[ec + k] = ev;
+        } else {
+          st_cluster(cluster_addr(fcl, r) + 4u * (unsigned)k, acc);
+          st_cluster(cluster_addr(ecl, r) + 4u * (unsigned)k, ev);
+        }
+      }
+    }
+  }
+}
+
+// e1 += P e2 on this CTA's level-1 rows (in place), with halo copies.
+__device__ __forceinline__ void cprolong_split(const Band& b, const OpLevel& lf, const OpLevel& lc, int ef, int ec) {
+  const int nf = lf.n, nc = lc.n, J0 = b.r0 / 2, J1 = b.r1 / 2;
+  const CArr Ef = carr(b, ef);
+  for (int J = J0 + b.warp; J < J1; J += b.nwarp)
+    for (int col = b.lane; col < nf; col += 32)
+      cstore1(b, Ef, nf, J0, J1, J, col, s_fb[ef + cidx(nf, J, col)] + cinterp(ec, nc, J, col));
+}
+
 // Multigrid V-cycle z = M R on the band. Entry: R and E[0] (first smoother
 // sweep, pointwise) complete with halos. Exit: z in E[returned], r.z total in
 // slot SL_RZ.
 __device__ int fast_vcycle(const Team& t, const Band& b, const FastVec& v, const Op& op, const CLv& sm,
-                           float omega, int nu, int nuc) {
+                           float omega, int nu, int nuc, bool split1) {
   const int L = op.L;
   if (L == 1) return 0;
   const OpLevel& l0 = op.lv[0];
@@ -341,6 +455,57 @@ __device__ int fast_vcycle(const Team& t, const Band& b, const FastVec& v, const
     SEC_ADD(SEC_SYNC);
   }
   const int n1 = op.lv[1].n;
+  if (split1 && L >= 3) {
+    // level 1 split across the cluster, levels 2.. in every CTA
+    unsigned ecur = 0;  // bit l: current smoother buffer of level l
+    auto E = [&](int l) { return sm.e[l][(ecur >> l) & 1]; };
+    auto Eo = [&](int l) { return sm.e[l][((ecur >> l) & 1) ^ 1]; };
+    fast_restrict_split(b, v, cur, ch2, d, sm.f[1], sm.e[1][0], n1, omega, (float)op.lv[1].dinv);
+    SEC_ADD(SEC_BAND);
+    team_sync(t);
+    SEC_ADD(SEC_SYNC);
+    for (int s = 1; s < nuc; ++s) {
+      csweep_split(b, op.lv[1], Eo(1), E(1), sm.f[1], omega);
+      ecur ^= 2u;
+      team_sync(t);
+    }
+    crestrict_split(b, op.lv[1], op.lv[2], E(1), sm.f[1], sm.f[2], sm.e[2][0], (L == 3) ? 1.f : omega);
+    ecur &= ~4u;
+    team_sync(t);
+    for (int c = 2; c < L - 1; ++c) {
+      for (int s = 1; s < nuc; ++s) {
+        csweep(b, op.lv[c], Eo(c), E(c), sm.f[c], omega);
+        ecur ^= 1u << c;
+        __syncthreads();
+      }
+      crestrict(b, op.lv[c], op.lv[c + 1], E(c), sm.f[c], sm.f[c + 1], sm.e[c + 1][0],
+                (c + 1 == L - 1) ? 1.f : omega);
+      ecur &= ~(1u << (c + 1));
+      __syncthreads();
+    }
+    for (int c = L - 2; c >= 2; --c) {
+      cprolong(b, op.lv[c], op.lv[c + 1], E(c), E(c + 1));
+      __syncthreads();
+      for (int s = 0; s < nuc; ++s) {
+        csweep(b, op.lv[c], Eo(c), E(c), sm.f[c], omega);
+        ecur ^= 1u << c;
+        __syncthreads();
+      }
+    }
+    cprolong_split(b, op.lv[1], op.lv[2], E(1), E(2));
+    team_sync(t);
+    for (int s = 0; s < nuc; ++s) {
+      csweep_split(b, op.lv[1], Eo(1), E(1), sm.f[1], omega);
+      ecur ^= 2u;
+      team_sync(t);
+    }
+    SEC_ADD(SEC_COARSE);
+    fast_prolong(b, v, cur, E(1), n1);
+    cur ^= 1;
+    SEC_ADD(SEC_BAND);
+    team_sync(t);
+    SEC_ADD(SEC_SYNC);
+  } else {
   fast_restrict(b, v, cur, ch2, d, sm.f[1], n1);
   SEC_ADD(SEC_BAND);
   team_sync(t);
@@ -385,6 +550,7 @@ __device__ int fast_vcycle(const Team& t, const Band& b, const FastVec& v, const
     team_sync(t);
     SEC_ADD(SEC_SYNC);
   }
+  }
   for (int s = 0; s < nu; ++s) {
     const bool last = (s == nu - 1);
     fast_sweep(b, v, cur, ch2, d, dinv, omega, last, rz);
@@ -400,7 +566,7 @@ __device__ int fast_vcycle(const Team& t, const Band& b, const FastVec& v, const
 
 // FP32 PCG on the band from a prepared state (R, E[0] set), updating X.
 __device__ void fast_pcg(const Team& t, const Band& b, const FastVec& v, const Op& op, const CLv& sm, double tol2,
-                         bool& done, const SolveCfg& cfg, Ctr& ctr) {
+                         bool& done, const SolveCfg& cfg, Ctr& ctr, bool split1) {
   const OpLevel& l0 = op.lv[0];
   const float ch2 = (float)l0.ch2, d = 1.f + 4.f * ch2, dinv = (float)l0.dinv;
   const float omega = (float)cfg.omega;
@@ -409,7 +575,7 @@ __device__ void fast_pcg(const Team& t, const Band& b, const FastVec& v, const O
   double rz_old = 0.0;
   bool all = __syncthreads_and(done);
   while (!all) {
-    const int zc = fast_vcycle(t, b, v, op, sm, omega, cfg.nu, cfg.nu_coarse);
+    const int zc = fast_vcycle(t, b, v, op, sm, omega, cfg.nu, cfg.nu_coarse, split1);
     SEC_T0();
     const int z = v.E[zc];
     const double rz = total(t, SL_RZ);
@@ -628,7 +794,8 @@ __device__ double* fast_solve(const Team& t, const Band& b, const SweepParams& P
       break;
     }
     bool idone = done;
-    fast_pcg(t, b, v, op, sm, P.cfg.inner_rtol * P.cfg.inner_rtol * rrt * sc * sc, idone, P.cfg, ctr);
+    fast_pcg(t, b, v, op, sm, P.cfg.inner_rtol * P.cfg.inner_rtol * rrt * sc * sc, idone, P.cfg, ctr,
+             P.fast_split1 != 0);
     xa = tgt;
     double* tmp = tgt;
     tgt = oth;

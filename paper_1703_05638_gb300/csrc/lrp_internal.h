@@ -127,6 +127,7 @@ struct SweepParams {
   size_t smem_off[LRP_MAXLEV][3];  // shared-memory coarse levels: e0, e1, f offsets (bytes)
   size_t smem_bytes;
   int fast_band_len;  // band kernel: floats per band array (halos and padding included)
+  int fast_split1;    // band kernel: level 1 split across the cluster (each CTA owns >= 2 of its rows)
   unsigned long long* section_cycles;  // optional section timers (LRP_SECTION_TIMERS builds)
   int poison;         // fill the dynamic shared memory with NaN first (read-before-write check)
   int start_buf;      // index of the buffer that holds the sweep state at launch

@@ -191,8 +191,23 @@ lrp_status sweep_enqueue(lrp_problem* Pr, unsigned stages, int nvec, const doubl
         for (int k = 0; k < 3; ++k) prm.smem_off[l][k] = offs[l][k];
       break;
     }
-    if (!fast && Pr->kernel_variant == 2) {
+    if (!fast && (Pr->kernel_variant == 2 || Pr->kernel_variant == 3)) {
       set_error("the band kernel does not apply to or fit this problem");
+      return LRP_EINVAL;
+    }
+    // level 1 split across the cluster: every CTA must own at least two of
+    // its rows (the rows J with 2J+1 in the CTA's band: J in [r0/2, r1/2))
+    prm.fast_split1 = 0;
+    if (fast && Pr->kernel_variant != 2 && Pr->L >= 3 && C > 1) {
+      bool ok = true;
+      for (int k = 0; k < C; ++k) {
+        const int r0 = k * n / C, r1 = (k + 1) * n / C;
+        if (r1 / 2 - r0 / 2 < 2) ok = false;
+      }
+      prm.fast_split1 = ok ? 1 : 0;
+    }
+    if (Pr->kernel_variant == 3 && !prm.fast_split1) {
+      set_error("the split-level band kernel does not apply to this problem and cluster size");
       return LRP_EINVAL;
     }
   }

@@ -247,14 +247,15 @@ def test_full_size_heat2d_sampled(precision):
     assert relerr(H, P.hessian_apply(X)) < TOL[precision], st
 
 
-@pytest.mark.parametrize("C", [1, 2, 4, 8])
-def test_band_kernel_matches_oracle(C):
+@pytest.mark.parametrize("C,variant", [(1, 2), (2, 2), (4, 2), (8, 2), (2, 3), (4, 3), (3, 3)])
+def test_band_kernel_matches_oracle(C, variant):
     """The shared-memory band kernel (2D, mixed precision, one column per
     cluster) against the oracle and against the generic kernel, for several
-    cluster sizes (bands of 31/C rows with two halo rows each)."""
+    cluster sizes (bands of 31/C rows with two halo rows each); variant 3
+    also splits the first coarse level (15 rows) across the cluster."""
     spec = synth.small_spec(dim=2, n=31, nt=24, obs_every=2, n_obs=9, sigma=0.02, seed=31)
     P = OProblem(spec)
-    Gb = lrp.lrp_setup_problem(spec, precision=lrp.LRP_MIXED, team_ctas=C, team_cols=1, kernel_variant=2)
+    Gb = lrp.lrp_setup_problem(spec, precision=lrp.LRP_MIXED, team_ctas=C, team_cols=1, kernel_variant=variant)
     Gg = lrp.lrp_setup_problem(spec, precision=lrp.LRP_MIXED, team_ctas=C, team_cols=1, kernel_variant=1)
     U = synth.normal_block(P.nx, 3, 5)
     for fn, ref in ((lrp.lrp_hessian_apply, P.hessian_apply(U)), (lrp.lrp_prior_half, P.prior_half(U)),
