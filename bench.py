@@ -55,10 +55,16 @@ def profile_summary(name: str) -> str:
 
 
 def kernel_hash(sources) -> str:
+    """Hash of the kernel's sources with comments and whitespace removed (so
+    that only a code change invalidates a committed profile)."""
+    import re
     h = hashlib.sha256()
     for f in sources:
-        with open(os.path.join(ROOT, "paper_1703_05638_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1703_05638_gb300", "csrc", f)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        h.update("".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -199,12 +199,12 @@ lrp_status lrp_hessian_apply(lrp_problem* p, int nvec, const double* X, int ldx,
 lrp_status lrp_hessian_apply_noalloc(lrp_problem* p, int nvec, const double* X, int ldx,
                                      double* Y, int ldy, lrp_apply_stats* st);
 
-/* Autotuner for blocks of nvec columns. Round 1 times, for each cluster size
+/* Autotuner for blocks of nvec columns. Stage 1 times, for each cluster size
  * (1..8, 12, 16 CTAs), CTA size (256 or 512 threads) and columns per cluster
  * (1, 2), with or without running in several waves for clusters of 8 or
  * more, the prior solve and the first `steps` forward implicit-Euler steps
- * (0 -> 16); round 2 varies the smoothing sweeps and (LRP_MIXED) the inner
- * tolerance on the two best shapes; round 3 times one whole Hessian apply for
+ * (0 -> 16); stage 2 varies the smoothing sweeps and (LRP_MIXED) the inner
+ * tolerance on the two best shapes; stage 3 times one whole Hessian apply for
  * the three best. The winner stays in the problem handle for later calls.
  * All candidates iterate to the same tolerances. *best_ms (may be NULL)
  * receives the winner's Hessian-apply time. Allocates two nx x nvec blocks

@@ -596,13 +596,13 @@ static lrp_status hessian_with_factors(lrp_problem* P, int nvec, const double* X
 
 extern "C" {
 
-// Autotuner, on a pseudo-random block of nvec columns. Round 1 (launch
+// Autotuner, on a pseudo-random block of nvec columns. Stage 1 (launch
 // shape): every cluster size C, CTA size and columns per cluster times the
 // prior solve and the first `steps` implicit-Euler steps of the forward sweep
 // (the smooth start the Hessian apply sees) with the problem's multigrid
-// settings. Round 2 (solver): the two fastest shapes time the same with each
-// smoothing-sweep count and (mixed path) inner tolerance. Round 3: the three
-// fastest of round 2 time one whole Hessian apply each; the fastest is kept.
+// settings. Stage 2 (solver): the two fastest shapes time the same with each
+// smoothing-sweep count and (mixed path) inner tolerance. Stage 3: the three
+// fastest of stage 2 time one whole Hessian apply each; the fastest is kept.
 // Every candidate iterates to the same tolerances, so the choice changes the
 // speed, not the result beyond rounding.
 lrp_status lrp_autotune(lrp_problem* P, int nvec, int steps, double* best_ms) {
@@ -667,7 +667,7 @@ lrp_status lrp_autotune(lrp_problem* P, int nvec, int steps, double* best_ms) {
     time_it(screen, 1, &t);
     if (t < 1e300 && t > 0) steps = std::max(2, std::min(steps, (int)(20.0 / t)));
   }
-  // round 1: launch shape
+  // stage 1: launch shape
   std::vector<Cand> shapes;
   for (int C : {1, 2, 3, 4, 5, 6, 7, 8, 12, 16})
     for (int NT : {512, 256})
@@ -683,7 +683,7 @@ lrp_status lrp_autotune(lrp_problem* P, int nvec, int steps, double* best_ms) {
     time_it(screen, steps, &c.t1);
   }
   std::sort(shapes.begin(), shapes.end(), by_t1);
-  // round 2: smoothing sweeps and inner tolerance on the two best shapes
+  // stage 2: smoothing sweeps and inner tolerance on the two best shapes
   std::vector<Cand> cands;
   for (int i = 0; i < std::min<int>(2, (int)shapes.size()); ++i)
     for (int nu : {1, 2})
@@ -697,7 +697,7 @@ lrp_status lrp_autotune(lrp_problem* P, int nvec, int steps, double* best_ms) {
         cands.push_back(c);
       }
   std::sort(cands.begin(), cands.end(), by_t1);
-  // round 3: whole Hessian applies
+  // stage 3: whole Hessian applies
   const unsigned hess = ST_LOAD_X | ST_PRIOR_IN | ST_FORWARD | ST_ADJOINT | ST_PRIOR_OUT | ST_STORE_Y;
   const int n2 = std::min<int>(3, (int)cands.size());
   for (int i = 0; i < n2; ++i) {

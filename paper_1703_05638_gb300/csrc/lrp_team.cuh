@@ -205,13 +205,13 @@ __device__ __forceinline__ T diag_at(const OpLevel& lv, int p, int i0, int i1, i
 }
 
 // Grid-stride loop over items [start, items) that handles LRP_UNROLL items
-// per round: compute(it) performs every load and the arithmetic of item it
+// per group: compute(it) performs every load and the arithmetic of item it
 // and returns its values, commit(it, v) performs the stores (and any
-// accumulation, in item order). With more than one item per round, all loads
-// of a round are issued before its first store (a store could alias later
+// accumulation, in item order). With more than one item per group, all loads
+// of a group are issued before its first store (a store could alias later
 // loads, so the compiler would not overlap them itself).
 // Measured on GB300 (127^2 and 63^3 sweeps, 16 columns): 2 or 4 items per
-// round spill registers and run 5-20% slower than 1, so 1 is the default.
+// group spill registers and run 5-20% slower than 1, so 1 is the default.
 #ifndef LRP_UNROLL
 #define LRP_UNROLL 1
 #endif
