@@ -438,10 +438,16 @@ def main():
         if device:
             post, st = lrp.lrp_lowrank_posterior(G, k=args.k, block=args.block, eig_tol=1e-6, start=start_d)
             out = lrp.lrp_posterior_query(post, kind, y_obs=y_obs, points=nodes_d, xi=xi_d, device=True)
+            mean = out["mean"].reshape(-1, 1)
         else:
             post, st = lrp.lrp_lowrank_posterior(G, k=args.k, block=args.block, eig_tol=1e-6, start=start_h)
             out = lrp.lrp_posterior_query(post, kind, y_obs=y_obs_h, points=nodes_h, xi=xi_h, device=False)
             out["lambda"] = post.eigs()
+            mean = out["mean"].reshape(-1, 1)
+        # the posterior mean's state trajectory in low-rank-in-time form
+        facs, tst = lrp.lrp_trajectory_factors(G, mean)
+        out["traj_rank"] = int(facs[0][0].shape[1])
+        out["traj_err"] = tst["time_trunc_err"]
         post.close()
         return st, out
 
@@ -454,6 +460,7 @@ def main():
     lrp.lrp_sweep_profile(G, 1)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     stats = []
+    traj = None
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -461,9 +468,11 @@ def main():
     for i in range(args.steps):
         flush.zero_()
         ev[i][0].record(stream)
-        st, _ = step()
+        st, out_i = step()
         ev[i][1].record(stream)
         stats.append(st)
+        if out_i is not None and "traj_rank" in out_i:
+            traj = {"rank": out_i["traj_rank"], "trunc_err_bound": out_i["traj_err"]}
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -485,8 +494,8 @@ def main():
         if args.mode == "apply":
             h2d, d2h = start_h.nbytes, start_h.nbytes
         else:
-            h2d = start_h.nbytes + y_obs_h.nbytes + nodes_h.nbytes + xi_h.nbytes
-            d2h = 8 * (args.k + nx + nodes_h.size + nx * xi_h.shape[1])
+            h2d = start_h.nbytes + y_obs_h.nbytes + nodes_h.nbytes + xi_h.nbytes + 8 * nx
+            d2h = 8 * (args.k + nx + nodes_h.size + nx * xi_h.shape[1]) + 8 * spec.time_rank_max * (nx + spec.nt)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         mv = 0
@@ -562,7 +571,8 @@ def main():
         "data": "synthetic",
         "config": {"workload": f"heat2d_127: 2D heat eq 127x127 interior (nx=16129), nt={spec.nt}, 400 uniform "
                                "sensors at every step, sigma=1e-3, prior (I-0.05 Lap)^-2",
-                   "step": ("block Lanczos to rank k + posterior factors + one query" if args.mode == "posterior"
+                   "step": ("block Lanczos to rank k + posterior factors + one query + the posterior mean's "
+                            "trajectory in low-rank-in-time form" if args.mode == "posterior"
                             else "one Hessian apply to a block of columns"),
                    "k": args.k, "block": args.block, "eig_tol": 1e-6, "query": "mean + variance@1024 + 8 samples",
                    "l2": "flushed (256 MB write) before every timed step",
@@ -573,6 +583,7 @@ def main():
         "s_to_rank_k": statistics.mean(s["ms"] for s in stats) / 1e3,
         "lanczos": {"n_iter": lan["n_iter"], "n_matvec": lan["n_matvec"], "k_converged": lan["k_converged"],
                     "max_ritz_resid": lan["max_ritz_resid"], "ms_apply": lan["ms_apply"]},
+        "trajectory": traj,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "fp64_gpu": fp64, "serve": serve,
         "gpu_launches": int(launches),
         "clocks": clocks,

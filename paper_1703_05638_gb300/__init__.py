@@ -330,10 +330,23 @@ def lrp_prior_half(prob: Problem, X):
 
 def lrp_trajectory_factors(prob: Problem, U):
     """Low-rank-in-time factors of the forward trajectories of the columns of
-    U (host arrays): returns (list of (W, V) with Y_j ~ W V^T, stats)."""
-    a = _Arg(np.asarray(U), prob.nx)
+    U (NumPy, or a CUDA torch tensor: the factors then stay on the device):
+    returns (list of (W, V) with Y_j ~ W V^T, stats)."""
     rmax = prob.desc.time_rank_max
     nt = prob.desc.nt
+    if _is_torch(U):
+        import torch
+        a = _Arg(U, prob.nx)
+        W = torch.zeros((a.ncols, rmax, prob.nx), dtype=torch.float64, device=U.device)
+        V = torch.zeros((a.ncols, rmax, nt), dtype=torch.float64, device=U.device)
+        ranks = np.zeros(a.ncols, dtype=np.int32)
+        st = lrp_apply_stats()
+        status = load().lrp_trajectory_factors(prob.handle, a.ncols, C.c_void_p(a.ptr), a.ld,
+                                               C.c_void_p(W.data_ptr()), C.c_void_p(V.data_ptr()),
+                                               C.c_void_p(ranks.ctypes.data), C.byref(st))
+        _check(status, allow=(LRP_OK, LRP_ENOCONV))
+        return [(W[j, :ranks[j]].T, V[j, :ranks[j]].T) for j in range(a.ncols)], st.as_dict()
+    a = _Arg(np.asarray(U), prob.nx)
     W = np.zeros((a.ncols, rmax, prob.nx))
     V = np.zeros((a.ncols, rmax, nt))
     ranks = np.zeros(a.ncols, dtype=np.int32)

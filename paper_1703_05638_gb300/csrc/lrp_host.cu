@@ -373,7 +373,7 @@ lrp_status lrp_setup_problem(const lrp_problem_desc* desc, void* cuda_stream, lr
   // ---- solver configuration
   SolveCfg& c = P->cfg;
   const bool mixed = d.precision == LRP_MIXED;
-  c.rtol = d.solve_rtol > 0 ? d.solve_rtol : (mixed ? 1e-11 : 1e-13);
+  c.rtol = d.solve_rtol > 0 ? d.solve_rtol : (mixed ? 1e-10 : 1e-13);
   c.inner_rtol = d.inner_rtol > 0 ? d.inner_rtol : 1e-4;
   c.maxit = d.pcg_maxit > 0 ? d.pcg_maxit : 200;
   c.maxref = 30;
