@@ -94,7 +94,7 @@ typedef struct {
   int precision;            /* LRP_FP64 or LRP_MIXED */
   double time_trunc_tol;    /* relative Frobenius tolerance of the time factors (e.g. 1e-8) */
   int time_rank_max;        /* rank cap of the time factors (e.g. 40) */
-  int time_chunk;           /* steps buffered between recompressions (0 -> 32) */
+  int time_chunk;           /* steps buffered between recompressions (0 -> 16, at most 64) */
   double solve_rtol;        /* relative residual per spatial solve (0 -> 1e-13 FP64, 1e-10 mixed) */
   int pcg_maxit;            /* PCG iteration cap per solve (0 -> 200) */
   /* tuning (0 -> autotuned or default) */

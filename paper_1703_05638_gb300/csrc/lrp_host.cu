@@ -380,7 +380,7 @@ lrp_status lrp_setup_problem(const lrp_problem_desc* desc, void* cuda_stream, lr
   c.nu = d.mg_nu > 0 ? d.mg_nu : 2;
   c.nu_coarse = d.mg_nu_coarse > 0 ? d.mg_nu_coarse : c.nu;
   c.omega = d.dim == 2 ? 0.8 : 6.0 / 7.0;
-  if (P->desc.time_chunk <= 0) P->desc.time_chunk = 32;
+  if (P->desc.time_chunk <= 0) P->desc.time_chunk = 16;
   if (P->desc.time_rank_max <= 0) P->desc.time_rank_max = 40;
   if (!(P->desc.time_trunc_tol > 0)) P->desc.time_trunc_tol = 1e-8;
   default_tuning(P);

@@ -217,7 +217,7 @@ lrp_status trajectory_factors_impl(lrp_problem* P, int nvec, const double* U, in
                                    double* Yout, int ldy) {
   auto t0 = std::chrono::steady_clock::now();
   const int nx = P->nx, nt = P->nt;
-  const int s = std::min(16, std::max(1, P->desc.time_chunk));
+  const int s = std::min(64, std::max(1, P->desc.time_chunk));  // the block QR handles up to 64 columns
   const int rmax = P->desc.time_rank_max;
   const int K = (nt + s - 1) / s;
   const double tol_k = P->desc.time_trunc_tol / K;

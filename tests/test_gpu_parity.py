@@ -341,3 +341,25 @@ def test_full_size_heat3d_properties():
     scale = np.sqrt(float(X[:, 0] @ H[:, 0]) * float(X[:, 1] @ H[:, 1]))
     assert abs(xhy - hxy) <= 1e-8 * scale, (xhy, hxy, scale)
     assert float(X[:, 0] @ H[:, 0]) >= 0 and float(X[:, 1] @ H[:, 1]) >= 0
+
+
+def test_api_limits():
+    """Empty blocks, and sizes beyond the documented limits, through the C ABI."""
+    spec = synth.small_spec(dim=2, n=7, nt=6, obs_every=2, n_obs=3)
+    P, G = _pair(spec, lrp.LRP_MIXED)
+    H, _ = lrp.lrp_hessian_apply(G, np.zeros((P.nx, 0)))
+    assert H.shape == (P.nx, 0)
+    D, _ = lrp.lrp_forward_observe(G, np.zeros((P.nx, 0)))
+    assert D.shape == (P.n_data, 0)
+    for kw in (dict(k=P.nx + 1, block=1), dict(k=4, block=65), dict(k=4, block=0), dict(k=0, block=1)):
+        with pytest.raises(lrp.LrpError) as e:
+            lrp.lrp_lowrank_posterior(G, **kw)
+        assert e.value.status == lrp.LRP_EINVAL
+    with pytest.raises(lrp.LrpError) as e:
+        lrp.lrp_setup_problem(spec, precision=lrp.LRP_MIXED, team_cols=3)  # not a power of two
+    assert e.value.status == lrp.LRP_EINVAL
+    # a kernel variant that does not apply is rejected when the sweep is set up
+    Gs = lrp.lrp_setup_problem(spec, precision=lrp.LRP_MIXED, kernel_variant=3, team_ctas=8)  # 7 rows / 8
+    with pytest.raises(lrp.LrpError) as e:
+        lrp.lrp_hessian_apply(Gs, synth.normal_block(P.nx, 1, 3))
+    assert e.value.status == lrp.LRP_EINVAL
