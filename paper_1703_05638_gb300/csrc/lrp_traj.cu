@@ -5,15 +5,15 @@
 // The forward sweep runs in chunks of s steps; each chunk's states land in a
 // buffer B (nx x s per column). Streaming recompression per column, with the
 // current factors Y_old ~ Qw diag(sig) V^T (Qw, V orthonormal columns):
-//   C = Qw^T B, B' = B - Qw C (twice: CGS2), B' = Q2 R2 (CholQR2),
-//   core = [[diag(sig), C], [0, R2]] = U S Zt (SVD),
+//   C = Qw^T B, B' = B - Qw C (twice: CGS2), B' = Q2 R2 (rank-revealing
+//   block Gram-Schmidt), core = [[diag(sig), C], [0, R2]] = U S Zt (SVD),
 //   keep the r' leading triplets whose discarded Frobenius tail is at most
 //   (tol / K) ||core||_F (K = number of chunks; by the triangle inequality the
 //   accumulated error is at most tol ||Y||_F), capped at time_rank_max,
 //   Qw <- [Qw Q2] U[:, :r'], V <- blockdiag(V, I_s) Zt^T[:, :r'], sig <- S[:r'].
-// The SVD of the small core comes from the symmetric eigenproblem of
-// [[0, core], [core^T, 0]] (eigenvalues +-s_i, eigenvectors [u; v]/sqrt 2),
-// which keeps absolute accuracy eps*||core|| without squaring the core.
+// The SVD of the small core is one-sided Jacobi in shared memory (k_core_svd),
+// which works on the core itself (no squaring) and resolves small singular
+// values to high relative accuracy.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -27,46 +27,114 @@
 
 namespace lrp {
 
-// Aug_b (2m x 2m, col-major, m = r_b + s) = [[0, core], [core^T, 0]] with
-// core = [[diag(sig_b), C_b], [0, R_b]]; one CTA per column b.
-__global__ void k_build_aug(const int* r_arr, int s, const double* sig, size_t sig_stride, const double* C,
-                            size_t c_stride, const double* R, size_t r_stride, double* Aug, size_t aug_stride) {
-  const int b = blockIdx.x;
-  const int r = r_arr[b];
-  const int m = r + s, n2 = 2 * m;
+
+// SVD of every column's core K = [[diag(sig), C], [0, R]] (m x m, m = r + s;
+// the factors' singular values, the chunk's coefficients on them and the
+// chunk's own triangular factor) by one-sided Jacobi (Hestenes): the columns
+// of A = K V are made pairwise orthogonal by plane rotations, applied to V as
+// well, in round-robin order (each round rotates m/2 disjoint column pairs in
+// parallel, one warp per pair), until a sweep rotates nothing. Then
+// sigma_j = |A e_j|, u_j = A e_j / sigma_j, v_j = V e_j. One CTA per column;
+// A and V live in shared memory. Output, sorted by decreasing sigma:
+// th[i] = sigma_i, Z = [U | V] (two m x m column-major blocks, ld m).
+__global__ void k_core_svd(const int* r_arr, int s, const double* sig, size_t sig_stride, const double* C,
+                           size_t c_stride, const double* R, size_t r_stride, double* th, size_t th_stride, double* Z,
+                           size_t z_stride, int* status) {
+  extern __shared__ double sm_svd[];
+  const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  const int r = r_arr[b], m = r + s, mp = m + (m & 1);
+  double* A = sm_svd;              // mp x mp, column-major
+  double* V = A + (size_t)mp * mp;  // mp x mp
+  double* nrm = V + (size_t)mp * mp;
+  int* order = (int*)(nrm + mp);
+  __shared__ int s_rot;
   const double* sg = sig + b * sig_stride;
   const double* Cb = C + b * c_stride;  // r x s, ld r
   const double* Rb = R + b * r_stride;  // s x s, ld s
-  double* A = Aug + b * aug_stride;
-  for (int e = threadIdx.x; e < n2 * n2; e += blockDim.x) {
-    const int i = e % n2, j = e / n2;
+  for (int e = tid; e < mp * mp; e += blockDim.x) {
+    const int i = e % mp, j = e / mp;
     double v = 0.0;
-    int a = -1, c = -1;
-    if (i < m && j >= m) {
-      a = i;
-      c = j - m;
-    } else if (i >= m && j < m) {
-      a = j;
-      c = i - m;
-    }
-    if (a >= 0) {
-      if (a < r && c < r) v = (a == c) ? sg[a] : 0.0;
-      else if (a < r && c >= r) v = Cb[(size_t)(c - r) * r + a];
-      else if (a >= r && c >= r) v = Rb[(size_t)(c - r) * s + (a - r)];
+    if (i < m && j < m) {
+      if (i < r && j < r) v = (i == j) ? sg[i] : 0.0;
+      else if (i < r && j >= r) v = Cb[(size_t)(j - r) * r + i];
+      else if (i >= r && j >= r) v = Rb[(size_t)(j - r) * s + (i - r)];
     }
     A[e] = v;
+    V[e] = (i == j) ? 1.0 : 0.0;
   }
-}
-
-// From the eigenvectors Zaug (2m x 2m, sorted decreasing) take U (m x rn) and
-// Zv (m x rn): U = sqrt2 * Zaug[0:m, 0:rn], Zv = sqrt2 * Zaug[m:2m, 0:rn].
-__global__ void k_split_uv(int m, int rn, const double* Zaug, double* U, double* Zv) {
-  const int e = threadIdx.x + blockIdx.x * blockDim.x;
-  if (e >= m * rn) return;
-  const int i = e % m, j = e / m;
-  const double sq2 = 1.4142135623730951;
-  U[(size_t)j * m + i] = sq2 * Zaug[(size_t)j * 2 * m + i];
-  Zv[(size_t)j * m + i] = sq2 * Zaug[(size_t)j * 2 * m + m + i];
+  __syncthreads();
+  // round-robin schedule: position 0 holds player 0, position q > 0 holds
+  // player ((q - 1 + round) mod (mp - 1)) + 1; positions k and mp-1-k meet
+  auto player = [&](int q, int round) { return q == 0 ? 0 : ((q - 1 + round) % (mp - 1)) + 1; };
+  int sweep = 0;
+  for (; sweep < 40; ++sweep) {
+    if (tid == 0) s_rot = 0;
+    __syncthreads();
+    for (int round = 0; round < mp - 1; ++round) {
+      for (int k = warp; k < mp / 2; k += nwarp) {
+        const int i = player(k, round), j = player(mp - 1 - k, round);
+        double a = 0.0, bb = 0.0, g = 0.0;
+        for (int row = lane; row < mp; row += 32) {
+          const double x = A[(size_t)i * mp + row], y = A[(size_t)j * mp + row];
+          a += x * x;
+          bb += y * y;
+          g += x * y;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          bb += __shfl_xor_sync(0xffffffffu, bb, o);
+          g += __shfl_xor_sync(0xffffffffu, g, o);
+        }
+        if (fabs(g) > 1e-15 * sqrt(a * bb) && fabs(g) > 1e-300) {
+          const double zeta = (bb - a) / (2.0 * g);
+          const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+          for (int row = lane; row < mp; row += 32) {
+            const double x = A[(size_t)i * mp + row], y = A[(size_t)j * mp + row];
+            A[(size_t)i * mp + row] = c * x - sn * y;
+            A[(size_t)j * mp + row] = sn * x + c * y;
+            const double vx = V[(size_t)i * mp + row], vy = V[(size_t)j * mp + row];
+            V[(size_t)i * mp + row] = c * vx - sn * vy;
+            V[(size_t)j * mp + row] = sn * vx + c * vy;
+          }
+          if (lane == 0) atomicAdd(&s_rot, 1);
+        }
+      }
+      __syncthreads();
+    }
+    if (s_rot == 0) break;
+    __syncthreads();
+  }
+  if (tid == 0 && sweep >= 40 && status) *status = 1;
+  for (int j = warp; j < mp; j += nwarp) {
+    double a = 0.0;
+    for (int row = lane; row < mp; row += 32) a += A[(size_t)j * mp + row] * A[(size_t)j * mp + row];
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) nrm[j] = sqrt(a);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int j = 0; j < mp; ++j) order[j] = j;
+    for (int j = 1; j < mp; ++j) {  // insertion sort by decreasing norm (mp <= 128)
+      const int x = order[j];
+      int q = j - 1;
+      while (q >= 0 && nrm[order[q]] < nrm[x]) {
+        order[q + 1] = order[q];
+        --q;
+      }
+      order[q + 1] = x;
+    }
+  }
+  __syncthreads();
+  double* U = Z + b * z_stride;
+  double* Vo = U + (size_t)m * m;
+  for (int e = tid; e < m * m; e += blockDim.x) {
+    const int i = e % m, jj = e / m, j = order[jj];
+    const double n_j = nrm[j];
+    U[e] = n_j > 0.0 ? A[(size_t)j * mp + i] / n_j : 0.0;
+    Vo[e] = V[(size_t)j * mp + i];
+  }
+  for (int jj = tid; jj < m; jj += blockDim.x) th[b * th_stride + jj] = nrm[order[jj]];
 }
 
 // Vn[rows n0..n0+s, :] = Zv[r:r+s, :rn]; (rows 0..n0 come from a GEMM)
@@ -116,9 +184,8 @@ struct TrajWS {
   DBuf R;                // nvec x s*s
   DBuf part;             // gemm_tn scratch
   size_t part_cap = 0;
-  DBuf Aug, Zaug;        // nvec x (2m)^2
-  DBuf th, work;         // nvec x 2m, nvec x 12m
-  DBuf U, Zv;            // m x m (per column, reused)
+  DBuf Zaug;             // nvec x 4m^2: the core's singular vectors [U | V] (2 m^2 used)
+  DBuf th;               // nvec x 2m: the core's singular values
   DBuf sig;              // nvec x rmax singular values of the current factors
   int* iarr = nullptr;   // device: [0, nvec) ranks, [nvec, 2nvec) eig sizes
   ~TrajWS() {
@@ -146,20 +213,36 @@ static lrp_status absorb_chunk(lrp_problem* P, std::vector<TrajCol>& cols, TrajW
   }
   // 2. rank-revealing thin QR of the remainders (one CTA per column)
   CKT(block_gs(st, nvec, nx, sk, ws.traj.p, (size_t)s * nx, nx, ws.R.p, (size_t)s * s, 1e-13, nullptr));
-  // 3. SVD of every column's small core via the augmented symmetric eigenproblem
+  // 3. SVD of every column's small core (one-sided Jacobi)
   std::vector<int> iarr(2 * nvec);
   for (int b = 0; b < nvec; ++b) {
     iarr[b] = cols[b].r;
     iarr[nvec + b] = 2 * (cols[b].r + sk);
   }
   CKT(cudaMemcpyAsync(ws.iarr, iarr.data(), 2 * nvec * sizeof(int), cudaMemcpyHostToDevice, st));
-  note_launch();
-  // R of a short last chunk has leading dimension sk
-  k_build_aug<<<nvec, 256, 0, st>>>(ws.iarr, sk, ws.sig.p, (size_t)rmax, ws.C.p, (size_t)rmax * s, ws.R.p, (size_t)s * s,
-                                   ws.Aug.p, (size_t)4 * M * M);
-  CKT(cudaGetLastError());
-  CKT(eig_sym_batched(st, nvec, ws.iarr + nvec, 2 * M, ws.Aug.p, (size_t)4 * M * M, ws.Zaug.p, (size_t)4 * M * M,
-                      ws.th.p, (size_t)2 * M, ws.work.p, (size_t)12 * M, nullptr));
+  {
+    // R of a short last chunk has leading dimension sk
+    const int mp = M + (M & 1);
+    const size_t smem = (2 * (size_t)mp * mp + mp) * sizeof(double) + mp * sizeof(int);
+    {
+      // one value from every caller: the device's opt-in maximum less the static part
+      int dev = 0, optin = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+      cudaFuncAttributes fa;
+      CKT(cudaFuncGetAttributes(&fa, k_core_svd));
+      const int cap = optin - (int)fa.sharedSizeBytes;
+      if ((long long)smem > cap) {
+        set_error("time_rank_max + time_chunk too large for the core SVD in shared memory");
+        return LRP_EINVAL;
+      }
+      CKT(cudaFuncSetAttribute(k_core_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    }
+    note_launch();
+    k_core_svd<<<nvec, 256, smem, st>>>(ws.iarr, sk, ws.sig.p, (size_t)rmax, ws.C.p, (size_t)rmax * s, ws.R.p,
+                                        (size_t)s * s, ws.th.p, (size_t)2 * M, ws.Zaug.p, (size_t)4 * M * M, nullptr);
+    CKT(cudaGetLastError());
+  }
   std::vector<double> th((size_t)nvec * 2 * M);
   CKT(cudaMemcpyAsync(th.data(), ws.th.p, th.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
   CKT(cudaStreamSynchronize(st));
@@ -184,24 +267,23 @@ static lrp_status absorb_chunk(lrp_problem* P, std::vector<TrajCol>& cols, TrajW
       tc.nrows += sk;
       continue;
     }
-    const double* Zb = ws.Zaug.p + (size_t)b * 4 * M * M;
-    note_launch();
-    k_split_uv<<<(m * rn + 255) / 256, 256, 0, st>>>(m, rn, Zb, ws.U.p, ws.Zv.p);
-    CKT(cudaGetLastError());
+    // left (spatial) and right (time) singular vectors of the core, ld m
+    const double* Ub = ws.Zaug.p + (size_t)b * 4 * M * M;
+    const double* Zvb = Ub + (size_t)m * m;
     // Qw <- [Qw Q2] U
     const double* Q2 = ws.traj.p + (size_t)b * s * nx;
     if (r > 0) {
-      CKT(gemm_nn(st, nx, r, rn, 1.0, tc.Qa.p, nx, ws.U.p, m, 0.0, tc.Qb.p, nx));
-      CKT(gemm_nn(st, nx, sk, rn, 1.0, Q2, nx, ws.U.p + r, m, 1.0, tc.Qb.p, nx));
+      CKT(gemm_nn(st, nx, r, rn, 1.0, tc.Qa.p, nx, Ub, m, 0.0, tc.Qb.p, nx));
+      CKT(gemm_nn(st, nx, sk, rn, 1.0, Q2, nx, Ub + r, m, 1.0, tc.Qb.p, nx));
     } else {
-      CKT(gemm_nn(st, nx, sk, rn, 1.0, Q2, nx, ws.U.p, m, 0.0, tc.Qb.p, nx));
+      CKT(gemm_nn(st, nx, sk, rn, 1.0, Q2, nx, Ub, m, 0.0, tc.Qb.p, nx));
     }
     std::swap(tc.Qa.p, tc.Qb.p);
     // V <- blockdiag(V, I) Zv
     if (r == 0 && tc.nrows > 0) CKT(cudaMemsetAsync(tc.Vn.p, 0, (size_t)nt * rn * sizeof(double), st));
-    if (r > 0) CKT(gemm_nn(st, tc.nrows, r, rn, 1.0, tc.V.p, nt, ws.Zv.p, m, 0.0, tc.Vn.p, nt));
+    if (r > 0) CKT(gemm_nn(st, tc.nrows, r, rn, 1.0, tc.V.p, nt, Zvb, m, 0.0, tc.Vn.p, nt));
     note_launch();
-    k_tail_rows<<<(sk * rn + 255) / 256, 256, 0, st>>>(tc.nrows, sk, r, m, rn, ws.Zv.p, tc.Vn.p, nt);
+    k_tail_rows<<<(sk * rn + 255) / 256, 256, 0, st>>>(tc.nrows, sk, r, m, rn, Zvb, tc.Vn.p, nt);
     CKT(cudaGetLastError());
     std::swap(tc.V.p, tc.Vn.p);
     CKT(cudaMemcpyAsync(ws.sig.p + (size_t)b * rmax, ws.th.p + (size_t)b * 2 * M, rn * sizeof(double),
@@ -240,12 +322,8 @@ lrp_status trajectory_factors_impl(lrp_problem* P, int nvec, const double* U, in
   CKT(ws.R.alloc((size_t)nvec * s * s));
   ws.part_cap = (size_t)std::max(M, 16) * 16 * 128;
   CKT(ws.part.alloc(ws.part_cap));
-  CKT(ws.Aug.alloc((size_t)nvec * 4 * M * M));
   CKT(ws.Zaug.alloc((size_t)nvec * 4 * M * M));
   CKT(ws.th.alloc((size_t)nvec * 2 * M));
-  CKT(ws.work.alloc((size_t)nvec * 12 * M + 8));
-  CKT(ws.U.alloc((size_t)M * M));
-  CKT(ws.Zv.alloc((size_t)M * M));
   CKT(ws.sig.alloc((size_t)nvec * rmax));
   CKT(cudaMalloc(&ws.iarr, 2 * nvec * sizeof(int)));
   lrp_apply_stats acc;
