@@ -832,4 +832,17 @@ cudaError_t set_rect(cudaStream_t s, double* T, int ldt, int r0, int c0, int m, 
   return cudaGetLastError();
 }
 
+// out[i] = v[idx[i]]
+__global__ void k_gather(int n, const int* idx, const double* v, double* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = v[idx[i]];
+}
+
+cudaError_t gather(cudaStream_t s, int n, const int* idx, const double* v, double* out) {
+  if (n <= 0) return cudaSuccess;
+  note_launch();
+  k_gather<<<(n + 255) / 256, 256, 0, s>>>(n, idx, v, out);
+  return cudaGetLastError();
+}
+
 }  // namespace lrp

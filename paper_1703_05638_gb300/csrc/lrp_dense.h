@@ -55,6 +55,8 @@ cudaError_t set_rect(cudaStream_t s, double* T, int ldt, int r0, int c0, int m, 
                      bool also_transpose);
 // D[0:m, 0:n] += S[0:m, 0:n] (column-major).
 cudaError_t add_block(cudaStream_t s, int m, int n, const double* S, int lds, double* D, int ldd);
+// out[i] = v[idx[i]], i < n.
+cudaError_t gather(cudaStream_t s, int n, const int* idx, const double* v, double* out);
 // Diagonal of (I + alpha L0)^-2 on the n^dim grid (constant-coefficient
 // Laplacian, zero Dirichlet data) by the sine transform; work >= n^2 + 2 n^dim.
 cudaError_t prior_diag_dst(cudaStream_t s, int dim, int n, double alpha, double* out, double* work);

@@ -197,9 +197,9 @@ struct lrp_posterior {
   double* V;         // device nx x k
   double* G;         // device nx x k, R^{-1} V
   std::vector<double> lambda_host;
-  // cached prior diagonal at the last variance node set
-  std::vector<int> diag_nodes;
-  double* diag;      // device
+  // prior variance at every node (sine-transform closed form), computed by the
+  // first variance query
+  double* diag;      // device, nx
   int diag_cap;
 };
 

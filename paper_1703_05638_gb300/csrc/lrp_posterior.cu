@@ -605,28 +605,26 @@ lrp_status lrp_posterior_query(lrp_posterior* post, const lrp_query* q, lrp_quer
     DArr<int> dnodes;
     CK(dnodes.alloc(np));
     CK(cudaMemcpyAsync(dnodes.p, nodes.data(), np * sizeof(int), cudaMemcpyHostToDevice, s));
-    if (post->diag_nodes != nodes) {
-      // prior diagonal ||R^{-1} e_i||^2 at the nodes by batched prior solves
+    if (!post->diag || post->diag_cap != nx) {
+      // prior variance at every node, (R^-2)_ii with R = I + alpha L0 (constant
+      // coefficients on the box): the sine-transform closed form, computed once
+      // per posterior
       if (post->diag) cudaFree(post->diag);
       post->diag = nullptr;
-      CK(cudaMalloc(&post->diag, np * sizeof(double)));
-      const int chunk = 256;
-      DArr<double> E, X;
-      CK(E.alloc((size_t)nx * chunk));
-      CK(X.alloc((size_t)nx * chunk));
-      for (int i0 = 0; i0 < np; i0 += chunk) {
-        const int nc = std::min(chunk, np - i0);
-        CK(unit_cols(s, nx, nc, dnodes.p, i0, E.p, nx));
-        st = run_sweep(P, ST_LOAD_X | ST_PRIOR_IN | ST_STORE_Y, nc, E.p, nx, X.p, nx, nullptr, 0, nullptr, 0,
-                       nullptr, false);
-        if (st != LRP_OK && st != LRP_ENOCONV) return st;
-        CK(col_norm2(s, nx, nc, X.p, nx, post->diag + i0));
-      }
-      post->diag_nodes = nodes;
+      CK(cudaMalloc(&post->diag, (size_t)nx * sizeof(double)));
+      post->diag_cap = nx;
+      DArr<double> dwork;
+      CK(dwork.alloc((size_t)P->n * P->n + 2 * (size_t)nx));
+      CK(prior_diag_dst(s, P->dim, P->n, P->desc.prior_alpha, post->diag, dwork.p));
+      CK(cudaStreamSynchronize(s));
     }
+    // gather the diagonal at the query nodes
+    DArr<double> pdiag;
+    CK(pdiag.alloc(np));
+    CK(gather(s, np, dnodes.p, post->diag, pdiag.p));
     DArr<double> var;
     CK(var.alloc(np));
-    CK(variance(s, np, dnodes.p, post->diag, k, post->lambda, lam_scale, post->G, nx, var.p));
+    CK(variance(s, np, dnodes.p, pdiag.p, k, post->lambda, lam_scale, post->G, nx, var.p));
     const cudaMemcpyKind k2 = is_device_ptr(r->variance) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     CK(cudaMemcpyAsync(r->variance, var.p, np * sizeof(double), k2, s));
   }
