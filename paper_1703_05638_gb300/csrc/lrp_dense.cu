@@ -13,6 +13,8 @@
 
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "lrp_dense.h"
 #include "lrp_internal.h"
 
@@ -507,6 +509,8 @@ __global__ void k_add_vec_cols(int nx, int nc, const double* m, double* Y, int l
 // (s x s, col-major) upper triangular; zero columns of Q have zero rows in R.
 #define GS_NT 512
 #define GS_MAXC 64
+#define GS_MC_MAXG 64   // CTAs of the cooperative variant
+#define GS_MC_ROWS 1024  // rows per CTA at least
 __global__ void __launch_bounds__(GS_NT) k_block_gs(int nx, int s, double* B, size_t strideB, int ldb,
                                                      double* R, size_t strideR, double drop_tol,
                                                      const double* ref_norm2, int* ndrop) {
@@ -587,6 +591,106 @@ __global__ void __launch_bounds__(GS_NT) k_block_gs(int nx, int s, double* B, si
   }
   if (tid == 0 && ndrop) ndrop[blockIdx.x] = dropped;
 }
+
+// The same rank-revealing block CGS2 of one matrix spread over the CTAs of
+// a cooperative grid: CTA g owns rows [g rows, (g+1) rows) of every column,
+// so the only cross-CTA data are the projections and norms, reduced through
+// per-CTA partial sums in `part` ([2][G][GS_MAXC + 1], the two halves used by
+// alternate passes so one grid barrier per pass suffices). Every CTA adds the
+// partials in the same order and takes identical decisions.
+__global__ void __launch_bounds__(GS_NT) k_block_gs_mc(int nx, int s, double* B, int ldb, double* R,
+                                                        double drop_tol, const double* ref_norm2, int* ndrop,
+                                                        double* part) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  __shared__ double s_part[GS_NT / 32][17];
+  __shared__ double s_tot[17];
+  __shared__ double s_h[GS_MAXC], s_rc[GS_MAXC];
+  __shared__ double s_n;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int G = gridDim.x, g = blockIdx.x;
+  const int rows = (nx + G - 1) / G, p0 = min(nx, g * rows), p1 = min(nx, p0 + rows);
+  constexpr int PW = GS_MAXC + 1;
+  auto reduce17 = [&](double* acc) {
+#pragma unroll
+    for (int i = 0; i < 17; ++i) {
+      double v = acc[i];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) s_part[wid][i] = v;
+    }
+    __syncthreads();
+    if (tid < 17) {
+      double t = 0.0;
+      for (int w = 0; w < GS_NT / 32; ++w) t += s_part[w][tid];
+      s_tot[tid] = t;
+    }
+    __syncthreads();
+  };
+  int dropped = 0, buf = 0;
+  for (int c = 0; c < s; ++c) {
+    double* w = B + (size_t)c * ldb;
+    if (tid < GS_MAXC) s_rc[tid] = 0.0;
+    double n0 = 0.0, nprev = 0.0, ncur = 0.0;
+    for (int pass = 0; pass < 4; ++pass) {
+      double* pb = part + ((size_t)buf * G + g) * PW;
+      const int nchunk = c > 0 ? (c + 15) / 16 : 1;
+      for (int q = 0; q < nchunk; ++q) {
+        const int i0 = q * 16, ni = min(16, c - i0);
+        double acc[17];
+#pragma unroll
+        for (int i = 0; i < 17; ++i) acc[i] = 0.0;
+        for (int p = p0 + tid; p < p1; p += GS_NT) {
+          const double wp = w[p];
+#pragma unroll
+          for (int i = 0; i < 16; ++i)
+            if (i < ni) acc[i] += B[(size_t)(i0 + i) * ldb + p] * wp;
+          if (q == 0) acc[16] += wp * wp;
+        }
+        reduce17(acc);
+        if (tid < ni) pb[i0 + tid] = s_tot[tid];
+        if (q == 0 && tid == 0) pb[GS_MAXC] = s_tot[16];
+      }
+      grid.sync();
+      const double* pa = part + (size_t)buf * G * PW;
+      if (tid < c) {
+        double t = 0.0;
+        for (int k = 0; k < G; ++k) t += pa[(size_t)k * PW + tid];
+        s_h[tid] = t;
+      }
+      if (tid == GS_NT - 1) {
+        double t = 0.0;
+        for (int k = 0; k < G; ++k) t += pa[(size_t)k * PW + GS_MAXC];
+        s_n = t;
+      }
+      __syncthreads();
+      ncur = s_n;
+      buf ^= 1;
+      if (pass == 0) n0 = ncur;
+      const bool more = (c > 0) && (pass < 2 || (pass == 2 && ncur < 1e-2 * nprev));
+      if (!more) break;
+      if (tid < c) s_rc[tid] += s_h[tid];
+      for (int p = p0 + tid; p < p1; p += GS_NT) {
+        double v = w[p];
+        for (int i = 0; i < c; ++i) v -= s_h[i] * B[(size_t)i * ldb + p];
+        w[p] = v;
+      }
+      nprev = ncur;
+    }
+    const double nrm = sqrt(ncur);
+    const double nref = ref_norm2 ? fmax(n0, ref_norm2[c]) : n0;
+    const bool drop = !(nrm > drop_tol * sqrt(nref)) || !(nrm > 0.0);
+    const double scale = drop ? 0.0 : 1.0 / nrm;
+    for (int p = p0 + tid; p < p1; p += GS_NT) w[p] *= scale;
+    __syncthreads();  // s_rc complete
+    if (g == 0 && tid == 0)
+      for (int i = 0; i < s; ++i) R[(size_t)c * s + i] = (i < c) ? s_rc[i] : (i == c ? (drop ? 0.0 : nrm) : 0.0);
+    dropped += drop ? 1 : 0;
+    __syncthreads();
+  }
+  if (g == 0 && tid == 0 && ndrop) *ndrop = dropped;
+}
+
+size_t block_gs_scratch_doubles() { return (size_t)2 * GS_MC_MAXG * (GS_MAXC + 1); }
 
 // --------------------------------------------------------------------------- host wrappers
 
@@ -717,8 +821,28 @@ cudaError_t add_vec_cols(cudaStream_t s, int nx, int nc, const double* m, double
 }
 
 cudaError_t block_gs(cudaStream_t s, int batch, int nx, int ncols, double* B, size_t strideB, int ldb, double* R,
-                     size_t strideR, double drop_tol, int* ndrop, const double* ref_norm2) {
+                     size_t strideR, double drop_tol, int* ndrop, const double* ref_norm2, double* coop_scratch) {
   if (ncols > GS_MAXC) return cudaErrorInvalidValue;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cs);
+  if (batch == 1 && coop_scratch && nx >= 2 * GS_MC_ROWS && cs == cudaStreamCaptureStatusNone) {
+    // one matrix: spread over a cooperative grid (co-residency checked by the launch)
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int G = std::max(1, std::min({GS_MC_MAXG, sms, nx / GS_MC_ROWS}));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(G);
+    cfg.blockDim = dim3(GS_NT);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    note_launch();
+    return cudaLaunchKernelEx(&cfg, k_block_gs_mc, nx, ncols, B, ldb, R, drop_tol, ref_norm2, ndrop, coop_scratch);
+  }
   note_launch();
   k_block_gs<<<batch, GS_NT, 0, s>>>(nx, ncols, B, strideB, ldb, R, strideR, drop_tol, ref_norm2, ndrop);
   return cudaGetLastError();

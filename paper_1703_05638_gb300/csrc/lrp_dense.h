@@ -27,8 +27,12 @@ cudaError_t eig_sym(cudaStream_t s, int n, double* A, int lda, double* Z, int ld
 // ref_norm2 (may be NULL): squared column norms before the caller's earlier
 // projections ([batch][ncols]); a column is then dependent if its remainder
 // is at most drop_tol of the larger of that norm and its norm on entry.
+// coop_scratch (may be NULL; block_gs_scratch_doubles() doubles): with one
+// matrix, the work is spread over a cooperative grid of CTAs.
 cudaError_t block_gs(cudaStream_t s, int batch, int nx, int ncols, double* B, size_t strideB, int ldb, double* R,
-                     size_t strideR, double drop_tol, int* ndrop, const double* ref_norm2 = nullptr);
+                     size_t strideR, double drop_tol, int* ndrop, const double* ref_norm2 = nullptr,
+                     double* coop_scratch = nullptr);
+size_t block_gs_scratch_doubles();
 // Batched eigensolver: matrix b has size n_dev[b] <= nmax, ld = its size.
 cudaError_t eig_sym_batched(cudaStream_t s, int batch, const int* n_dev, int nmax, double* A, size_t strideA,
                             double* Z, size_t strideZ, double* theta, size_t strideT, double* work,

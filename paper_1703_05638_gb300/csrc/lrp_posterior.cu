@@ -57,7 +57,7 @@ static const unsigned HESS_STAGES = ST_LOAD_X | ST_PRIOR_IN | ST_FORWARD | ST_AD
 
 // Scratch of one Lanczos run.
 struct LanczosWS {
-  DArr<double> part, G, R1, R2, Ri1, Ri2, R, C1, C2, ref;
+  DArr<double> part, G, R1, R2, Ri1, Ri2, R, C1, C2, ref, gs;
   DArr<int> flags;
   size_t part_cap = 0;
 };
@@ -79,7 +79,7 @@ static lrp_status block_orth(lrp_problem* P, int nx, int nb, double* Wn, const d
     CK(gemm_nn(s, nx, nprev, nb, -1.0, Q, nx, ws.C1.p, nprev, 1.0, Wn, nx));
     if (Cacc) CK(axpby(s, (size_t)nprev * nb, 1.0, ws.C1.p, 1.0, Cacc));
   }
-  CK(block_gs(s, 1, nx, nb, Wn, 0, nx, ws.R.p, 0, drop_tol, nullptr, nprev > 0 ? ws.ref.p : nullptr));
+  CK(block_gs(s, 1, nx, nb, Wn, 0, nx, ws.R.p, 0, drop_tol, nullptr, nprev > 0 ? ws.ref.p : nullptr, ws.gs.p));
   return LRP_OK;
 }
 
@@ -155,6 +155,7 @@ struct LanczosRun {
     CK(ws.C2.alloc((size_t)(mmax + nb) * nb));
     CK(ws.flags.alloc(nb));
     CK(ws.ref.alloc(nb));
+    CK(ws.gs.alloc(block_gs_scratch_doubles()));
     CK(cudaMallocHost(&h_theta, mmax * sizeof(double)));
     CK(cudaMallocHost(&h_res, mmax * sizeof(double)));
     CK(cudaMallocHost(&h_stats, sizeof(Stats)));

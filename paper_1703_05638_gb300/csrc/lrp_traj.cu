@@ -186,6 +186,7 @@ struct TrajWS {
   size_t part_cap = 0;
   DBuf Zaug;             // nvec x 4m^2: the core's singular vectors [U | V] (2 m^2 used)
   DBuf th;               // nvec x 2m: the core's singular values
+  DBuf gs;               // scratch of the cooperative block Gram-Schmidt (one column)
   DBuf sig;              // nvec x rmax singular values of the current factors
   int* iarr = nullptr;   // device: [0, nvec) ranks, [nvec, 2nvec) eig sizes
   ~TrajWS() {
@@ -212,7 +213,8 @@ static lrp_status absorb_chunk(lrp_problem* P, std::vector<TrajCol>& cols, TrajW
     }
   }
   // 2. rank-revealing thin QR of the remainders (one CTA per column)
-  CKT(block_gs(st, nvec, nx, sk, ws.traj.p, (size_t)s * nx, nx, ws.R.p, (size_t)s * s, 1e-13, nullptr));
+  CKT(block_gs(st, nvec, nx, sk, ws.traj.p, (size_t)s * nx, nx, ws.R.p, (size_t)s * s, 1e-13, nullptr, nullptr,
+               ws.gs.p));
   // 3. SVD of every column's small core (one-sided Jacobi)
   std::vector<int> iarr(2 * nvec);
   for (int b = 0; b < nvec; ++b) {
@@ -324,6 +326,7 @@ lrp_status trajectory_factors_impl(lrp_problem* P, int nvec, const double* U, in
   CKT(ws.part.alloc(ws.part_cap));
   CKT(ws.Zaug.alloc((size_t)nvec * 4 * M * M));
   CKT(ws.th.alloc((size_t)nvec * 2 * M));
+  CKT(ws.gs.alloc(block_gs_scratch_doubles()));
   CKT(ws.sig.alloc((size_t)nvec * rmax));
   CKT(cudaMalloc(&ws.iarr, 2 * nvec * sizeof(int)));
   lrp_apply_stats acc;
