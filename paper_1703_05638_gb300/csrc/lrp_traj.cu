@@ -63,6 +63,20 @@ __global__ void k_core_svd(const int* r_arr, int s, const double* sig, size_t si
     V[e] = (i == j) ? 1.0 : 0.0;
   }
   __syncthreads();
+  // columns below 1e-18 of the core's norm are noise for any truncation this
+  // serves (tolerances >= 1e-14): pairs of them are not rotated
+  __shared__ double s_f2;
+  if (tid == 0) s_f2 = 0.0;
+  __syncthreads();
+  {
+    double f2 = 0.0;
+    for (int e = tid; e < mp * mp; e += blockDim.x) f2 += A[e] * A[e];
+    for (int o = 16; o > 0; o >>= 1) f2 += __shfl_xor_sync(0xffffffffu, f2, o);
+    if (lane == 0) atomicAdd(&s_f2, f2);
+  }
+  __syncthreads();
+  const double floor2 = 1e-36 * s_f2;
+  const double tol_rot = 4.0 * mp * 2.220446049250313e-16;
   // round-robin schedule: position 0 holds player 0, position q > 0 holds
   // player ((q - 1 + round) mod (mp - 1)) + 1; positions k and mp-1-k meet
   auto player = [&](int q, int round) { return q == 0 ? 0 : ((q - 1 + round) % (mp - 1)) + 1; };
@@ -85,7 +99,9 @@ __global__ void k_core_svd(const int* r_arr, int s, const double* sig, size_t si
           bb += __shfl_xor_sync(0xffffffffu, bb, o);
           g += __shfl_xor_sync(0xffffffffu, g, o);
         }
-        if (fabs(g) > 1e-15 * sqrt(a * bb) && fabs(g) > 1e-300) {
+        // orthogonal to working accuracy once |g| is within the rounding of an
+        // mp-term dot product
+        if (fabs(g) > tol_rot * sqrt(a * bb) && fmax(a, bb) > floor2 && fabs(g) > 1e-300) {
           const double zeta = (bb - a) / (2.0 * g);
           const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
           const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
@@ -241,7 +257,7 @@ static lrp_status absorb_chunk(lrp_problem* P, std::vector<TrajCol>& cols, TrajW
       CKT(cudaFuncSetAttribute(k_core_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
     }
     note_launch();
-    k_core_svd<<<nvec, 256, smem, st>>>(ws.iarr, sk, ws.sig.p, (size_t)rmax, ws.C.p, (size_t)rmax * s, ws.R.p,
+    k_core_svd<<<nvec, 512, smem, st>>>(ws.iarr, sk, ws.sig.p, (size_t)rmax, ws.C.p, (size_t)rmax * s, ws.R.p,
                                         (size_t)s * s, ws.th.p, (size_t)2 * M, ws.Zaug.p, (size_t)4 * M * M, nullptr);
     CKT(cudaGetLastError());
   }
