@@ -104,63 +104,6 @@ __global__ void __launch_bounds__(256) k_gemm_nn(int nx, int m, int nc, double a
   }
 }
 
-// ---------------------------------------------------------------- small Cholesky
-// G (nb x nb, ld nb) -> R upper triangular with R^T R = G, Rinv = R^{-1}.
-// A pivot below tol * G_cc marks the column deficient: its R column is set
-// to the unit column (so Rinv stays finite) and flags[c] = 1.
-__global__ void k_chol_small(int nb, const double* __restrict__ G, double* __restrict__ R,
-                             double* __restrict__ Rinv, int* __restrict__ flags, double tol) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double r[16][16];
-  for (int i = 0; i < nb; ++i)
-    for (int j = 0; j < nb; ++j) r[i][j] = 0.0;
-  for (int c = 0; c < nb; ++c) {
-    double d = G[c * nb + c];
-    for (int i = 0; i < c; ++i) d -= r[i][c] * r[i][c];
-    const double gcc = G[c * nb + c];
-    if (!(d > tol * gcc) || !(gcc > 0.0) || !isfinite(d)) {
-      flags[c] = 1;
-      r[c][c] = 1.0;
-      for (int e = c + 1; e < nb; ++e) r[c][e] = 0.0;
-      continue;
-    }
-    flags[c] = 0;
-    r[c][c] = sqrt(d);
-    for (int e = c + 1; e < nb; ++e) {
-      double v = G[e * nb + c];
-      for (int i = 0; i < c; ++i) v -= r[i][c] * r[i][e];
-      r[c][e] = v / r[c][c];
-    }
-  }
-  // inverse of the upper triangular r by columns
-  double ri[16][16];
-  for (int i = 0; i < nb; ++i)
-    for (int j = 0; j < nb; ++j) ri[i][j] = 0.0;
-  for (int j = 0; j < nb; ++j) {
-    ri[j][j] = 1.0 / r[j][j];
-    for (int i = j - 1; i >= 0; --i) {
-      double s = 0.0;
-      for (int k = i + 1; k <= j; ++k) s += r[i][k] * ri[k][j];
-      ri[i][j] = -s / r[i][i];
-    }
-  }
-  // column-major outputs
-  for (int i = 0; i < nb; ++i)
-    for (int j = 0; j < nb; ++j) {
-      R[j * nb + i] = r[i][j];
-      Rinv[j * nb + i] = ri[i][j];
-    }
-}
-
-// C = A B for small upper-triangular nb x nb column-major matrices.
-__global__ void k_small_mm(int nb, const double* A, const double* B, double* C) {
-  const int e = threadIdx.x;
-  if (e >= nb * nb) return;
-  const int i = e % nb, j = e / nb;
-  double s = 0.0;
-  for (int k = 0; k < nb; ++k) s += A[k * nb + i] * B[j * nb + k];
-  C[j * nb + i] = s;
-}
 
 // ---------------------------------------------------------------- eigensolver
 // Symmetric eigendecomposition of the n x n matrix A (column-major, ld lda,
@@ -396,13 +339,6 @@ __global__ void k_set_block(double* T, int ldt, int r0, int c0, int nb, const do
   if (also_transpose) T[(size_t)(r0 + i) * ldt + c0 + j] = v;
 }
 
-// zero the columns c of an nb x nb col-major matrix with flags[c] != 0
-__global__ void k_zero_flagged_cols(int nb, double* M, const int* flags) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= nb * nb) return;
-  const int j = e / nb;
-  if (flags[j]) M[e] = 0.0;
-}
 
 // Pseudo-random values in [-1, 1) from a counter-based hash (splitmix64 of
 // seed, column and row); fills columns with flags[c] != 0 (flags NULL = all).
@@ -723,19 +659,6 @@ cudaError_t gemm_nn(cudaStream_t s, int nx, int m, int nc, double alpha, const d
   return cudaGetLastError();
 }
 
-cudaError_t chol_small(cudaStream_t s, int nb, const double* G, double* R, double* Rinv, int* flags,
-                       double tol) {
-  note_launch();
-  k_chol_small<<<1, 32, 0, s>>>(nb, G, R, Rinv, flags, tol);
-  return cudaGetLastError();
-}
-
-cudaError_t small_mm(cudaStream_t s, int nb, const double* A, const double* B, double* C) {
-  note_launch();
-  k_small_mm<<<1, 256, 0, s>>>(nb, A, B, C);
-  return cudaGetLastError();
-}
-
 cudaError_t eig_sym(cudaStream_t s, int n, double* A, int lda, double* Z, int ldz, double* theta,
                     double* work, int* status) {
   if (n > 1024) return cudaErrorInvalidValue;
@@ -756,12 +679,6 @@ cudaError_t set_block(cudaStream_t s, double* T, int ldt, int r0, int c0, int nb
   note_launch();
   k_set_block<<<(nb * nb + 255) / 256, 256, 0, s>>>(T, ldt, r0, c0, nb, S, lds, symmetrize ? 1 : 0,
                                                      also_transpose ? 1 : 0);
-  return cudaGetLastError();
-}
-
-cudaError_t zero_flagged_cols(cudaStream_t s, int nb, double* M, const int* flags) {
-  note_launch();
-  k_zero_flagged_cols<<<(nb * nb + 255) / 256, 256, 0, s>>>(nb, M, flags);
   return cudaGetLastError();
 }
 
@@ -845,16 +762,6 @@ cudaError_t block_gs(cudaStream_t s, int batch, int nx, int ncols, double* B, si
   }
   note_launch();
   k_block_gs<<<batch, GS_NT, 0, s>>>(nx, ncols, B, strideB, ldb, R, strideR, drop_tol, ref_norm2, ndrop);
-  return cudaGetLastError();
-}
-
-cudaError_t eig_sym_batched(cudaStream_t s, int batch, const int* n_dev, int nmax, double* A, size_t strideA,
-                            double* Z, size_t strideZ, double* theta, size_t strideT, double* work,
-                            size_t strideW, int* status) {
-  if (nmax > 1024) return cudaErrorInvalidValue;
-  note_launch();
-  k_eig_sym<<<batch, EIG_NT, 0, s>>>(nmax, A, nmax, Z, nmax, theta, work, status, n_dev, strideA, strideZ,
-                                     strideT, strideW);
   return cudaGetLastError();
 }
 

@@ -14,9 +14,6 @@ cudaError_t gemm_tn(cudaStream_t s, int nx, int m, int nb, const double* A, int 
 // Y (nx x nc) = beta Y + alpha A M; A: nx x m, M: m x nc. Y may alias A only if nc <= 16.
 cudaError_t gemm_nn(cudaStream_t s, int nx, int m, int nc, double alpha, const double* A, int lda,
                     const double* M, int ldm, double beta, double* Y, int ldy);
-cudaError_t chol_small(cudaStream_t s, int nb, const double* G, double* R, double* Rinv, int* flags,
-                       double tol);
-cudaError_t small_mm(cudaStream_t s, int nb, const double* A, const double* B, double* C);
 // theta decreasing, Z eigenvectors; A destroyed; work >= 6n doubles; n <= 1024.
 cudaError_t eig_sym(cudaStream_t s, int n, double* A, int lda, double* Z, int ldz, double* theta,
                     double* work, int* status);
@@ -33,15 +30,10 @@ cudaError_t block_gs(cudaStream_t s, int batch, int nx, int ncols, double* B, si
                      size_t strideR, double drop_tol, int* ndrop, const double* ref_norm2 = nullptr,
                      double* coop_scratch = nullptr);
 size_t block_gs_scratch_doubles();
-// Batched eigensolver: matrix b has size n_dev[b] <= nmax, ld = its size.
-cudaError_t eig_sym_batched(cudaStream_t s, int batch, const int* n_dev, int nmax, double* A, size_t strideA,
-                            double* Z, size_t strideZ, double* theta, size_t strideT, double* work,
-                            size_t strideW, int* status);
 cudaError_t ritz_resid(cudaStream_t s, int k, int nb, const double* B, const double* Z, int ldz, int row0,
                        double* resid);
 cudaError_t set_block(cudaStream_t s, double* T, int ldt, int r0, int c0, int nb, const double* S, int lds,
                       bool symmetrize, bool also_transpose);
-cudaError_t zero_flagged_cols(cudaStream_t s, int nb, double* M, const int* flags);
 cudaError_t fill_random(cudaStream_t s, int nx, int nb, double* W, int ldw, const int* flags,
                         unsigned long long seed);
 cudaError_t copy_cols(cudaStream_t s, int nx, int nb, const double* S, int lds, double* D, int ldd);

@@ -57,8 +57,7 @@ static const unsigned HESS_STAGES = ST_LOAD_X | ST_PRIOR_IN | ST_FORWARD | ST_AD
 
 // Scratch of one Lanczos run.
 struct LanczosWS {
-  DArr<double> part, G, R1, R2, Ri1, Ri2, R, C1, C2, ref, gs;
-  DArr<int> flags;
+  DArr<double> part, R, C1, C2, ref, gs;
   size_t part_cap = 0;
 };
 
@@ -145,15 +144,9 @@ struct LanczosRun {
     CK(estat.alloc(1));
     ws.part_cap = (size_t)std::max(mmax + nb, 16) * 16 * 128;
     CK(ws.part.alloc(ws.part_cap));
-    CK(ws.G.alloc(nb * nb));
-    CK(ws.R1.alloc(nb * nb));
-    CK(ws.R2.alloc(nb * nb));
-    CK(ws.Ri1.alloc(nb * nb));
-    CK(ws.Ri2.alloc(nb * nb));
     CK(ws.R.alloc(nb * nb));
     CK(ws.C1.alloc((size_t)(mmax + nb) * nb));
     CK(ws.C2.alloc((size_t)(mmax + nb) * nb));
-    CK(ws.flags.alloc(nb));
     CK(ws.ref.alloc(nb));
     CK(ws.gs.alloc(block_gs_scratch_doubles()));
     CK(cudaMallocHost(&h_theta, mmax * sizeof(double)));
