@@ -203,9 +203,12 @@ lrp_status lrp_hessian_apply_noalloc(lrp_problem* p, int nvec, const double* X, 
  * (1..8, 12, 16 CTAs), CTA size (256 or 512 threads) and columns per cluster
  * (1, 2), with or without running in several waves for clusters of 8 or
  * more, the prior solve and the first `steps` forward implicit-Euler steps
- * (0 -> 16); stage 2 varies the smoothing sweeps and (LRP_MIXED) the inner
+ * (0 -> 16); stage 2 varies the smoothing sweeps (finest and coarse levels,
+ * 1 or 2 each) and (LRP_MIXED) the inner
  * tolerance on the two best shapes; stage 3 times one whole Hessian apply for
- * the three best. The winner stays in the problem handle for later calls.
+ * the three best; stage 4 times the stage-1 screen for one column at larger
+ * cluster sizes (team_ctas_narrow of lrp_tuning). The winner stays in the
+ * problem handle for later calls.
  * All candidates iterate to the same tolerances. *best_ms (may be NULL)
  * receives the winner's Hessian-apply time. Allocates two nx x nvec blocks
  * for the duration of the call. No counterpart in the paper. */
@@ -319,10 +322,13 @@ typedef struct lrp_tuning {
   int last_kernel, last_team_ctas;
   int threads;  /* threads per CTA */
   int waves;    /* 1: clusters of the requested size even if they run in several waves */
+  int team_ctas_narrow; /* cluster size for launches with few columns, used when all of their
+                           clusters fit on the GPU at once at that size; 0 = team_ctas */
 } lrp_tuning;
 lrp_status lrp_problem_tuning(const lrp_problem* p, lrp_tuning* out);
 /* Sets a problem's launch shape and multigrid settings from t (team_ctas,
- * team_cols, mg_nu, mg_nu_coarse, inner_rtol, threads 256 or 512, waves; the
+ * team_cols, mg_nu, mg_nu_coarse, inner_rtol, threads 256 or 512, waves,
+ * team_ctas_narrow 0..16; the
  * last_* fields are ignored), e.g. to reuse one autotuned setting for
  * problems of the same size. LRP_EINVAL on values out of range. */
 lrp_status lrp_set_tuning(lrp_problem* p, const lrp_tuning* t);

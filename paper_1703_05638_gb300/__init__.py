@@ -102,7 +102,7 @@ class lrp_batch_stats(C.Structure):
 class lrp_tuning(C.Structure):
     _fields_ = [("team_ctas", C.c_int), ("team_cols", C.c_int), ("mg_nu", C.c_int), ("mg_nu_coarse", C.c_int),
                 ("inner_rtol", C.c_double), ("last_kernel", C.c_int), ("last_team_ctas", C.c_int),
-                ("threads", C.c_int), ("waves", C.c_int)]
+                ("threads", C.c_int), ("waves", C.c_int), ("team_ctas_narrow", C.c_int)]
 
 
 EXPORTS = {

@@ -428,6 +428,7 @@ lrp_status lrp_problem_tuning(const lrp_problem* P, lrp_tuning* out) {
   out->last_team_ctas = P->last_team_ctas;
   out->threads = P->nthreads;
   out->waves = P->allow_waves;
+  out->team_ctas_narrow = P->team_ctas_narrow;
   return LRP_OK;
 }
 
@@ -438,7 +439,8 @@ lrp_status lrp_set_tuning(lrp_problem* P, const lrp_tuning* t) {
   }
   if (t->team_ctas < 1 || t->team_ctas > 16 || t->team_cols < 1 || t->team_cols > LRP_MAXBV ||
       (t->team_cols & (t->team_cols - 1)) || t->mg_nu < 1 || t->mg_nu > 8 || t->mg_nu_coarse < 1 ||
-      t->mg_nu_coarse > 8 || !(t->inner_rtol > 0 && t->inner_rtol < 1) || (t->threads != 256 && t->threads != 512)) {
+      t->mg_nu_coarse > 8 || !(t->inner_rtol > 0 && t->inner_rtol < 1) || (t->threads != 256 && t->threads != 512) ||
+      t->team_ctas_narrow < 0 || t->team_ctas_narrow > 16) {
     set_error("lrp_set_tuning: value out of range");
     return LRP_EINVAL;
   }
@@ -446,6 +448,7 @@ lrp_status lrp_set_tuning(lrp_problem* P, const lrp_tuning* t) {
   P->team_cols = t->team_cols;
   P->nthreads = t->threads;
   P->allow_waves = t->waves ? 1 : 0;
+  P->team_ctas_narrow = t->team_ctas_narrow;
   P->cfg.nu = t->mg_nu;
   P->cfg.nu_coarse = t->mg_nu_coarse;
   P->cfg.inner_rtol = t->inner_rtol;
@@ -603,6 +606,8 @@ extern "C" {
 // settings. Stage 2 (solver): the two fastest shapes time the same with each
 // smoothing-sweep count and (mixed path) inner tolerance. Stage 3: the three
 // fastest of stage 2 time one whole Hessian apply each; the fastest is kept.
+// Stage 4: the stage-1 screen for a single column at larger cluster sizes
+// picks the size for narrow launches (team_ctas_narrow).
 // Every candidate iterates to the same tolerances, so the choice changes the
 // speed, not the result beyond rounding.
 lrp_status lrp_autotune(lrp_problem* P, int nvec, int steps, double* best_ms) {
@@ -623,12 +628,14 @@ lrp_status lrp_autotune(lrp_problem* P, int nvec, int steps, double* best_ms) {
     return cuda_status(e, "autotune buffers");
   }
   struct Cand {
-    int C, NT, BV, waves, nu;
+    int C, NT, BV, waves, nu, nuc;
     double inner, t1, t2;
   };
   const bool mixed = P->desc.precision == LRP_MIXED;
   const int save_C = P->team_ctas, save_BV = P->team_cols, save_NT = P->nthreads, save_W = P->allow_waves;
   const SolveCfg save_cfg = P->cfg;
+  const int save_narrow = P->team_ctas_narrow;
+  P->team_ctas_narrow = 0;  // stages 1-3 time nvec-column launches at the candidate's own size
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -639,14 +646,14 @@ lrp_status lrp_autotune(lrp_problem* P, int nvec, int steps, double* best_ms) {
     P->allow_waves = c.waves;
     P->cfg = save_cfg;
     P->cfg.nu = c.nu;
-    P->cfg.nu_coarse = c.nu;
+    P->cfg.nu_coarse = c.nuc;
     if (mixed) P->cfg.inner_rtol = c.inner;
   };
-  auto time_it = [&](unsigned stages, int t_end, double* out) {
+  auto time_cols = [&](int ncols, unsigned stages, int t_end, double* out) {
     double best_t = 1e300;
     for (int rep = 0; rep < 2; ++rep) {
       cudaEventRecord(e0, P->stream);
-      lrp_status st = run_sweep_ex(P, stages, nvec, X, P->nx, Y, P->nx, nullptr, 0, nullptr, 0, nullptr, 0, t_end,
+      lrp_status st = run_sweep_ex(P, stages, ncols, X, P->nx, Y, P->nx, nullptr, 0, nullptr, 0, nullptr, 0, t_end,
                                    nullptr, 0);
       cudaEventRecord(e1, P->stream);
       cudaEventSynchronize(e1);
@@ -657,11 +664,12 @@ lrp_status lrp_autotune(lrp_problem* P, int nvec, int steps, double* best_ms) {
     }
     *out = best_t;
   };
+  auto time_it = [&](unsigned stages, int t_end, double* out) { time_cols(nvec, stages, t_end, out); };
   auto by_t1 = [](const Cand& a, const Cand& b) { return a.t1 < b.t1; };
   const unsigned screen = ST_LOAD_X | ST_PRIOR_IN | ST_FORWARD;
   // keep one screen near 20 ms: fewer steps for big problems
   {
-    Cand c0{save_C, save_NT, save_BV, save_W, save_cfg.nu, save_cfg.inner_rtol, 1e300, 1e300};
+    Cand c0{save_C, save_NT, save_BV, save_W, save_cfg.nu, save_cfg.nu_coarse, save_cfg.inner_rtol, 1e300, 1e300};
     apply_cand(c0);
     double t = 1e300;
     time_it(screen, 1, &t);
@@ -676,20 +684,25 @@ lrp_status lrp_autotune(lrp_problem* P, int nvec, int steps, double* best_ms) {
           if (BV > 1 && nvec < 32) continue;  // one column per cluster wins for Lanczos-sized blocks
           if (C > 1 && (long long)P->nx / C < 256) continue;
           if (waves && C < 8) continue;  // more clusters than fit at once: only worth trying for big clusters
-          shapes.push_back({C, NT, BV, waves, save_cfg.nu, save_cfg.inner_rtol, 1e300, 1e300});
+          shapes.push_back({C, NT, BV, waves, save_cfg.nu, save_cfg.nu_coarse, save_cfg.inner_rtol, 1e300, 1e300});
         }
   for (Cand& c : shapes) {
     apply_cand(c);
     time_it(screen, steps, &c.t1);
   }
   std::sort(shapes.begin(), shapes.end(), by_t1);
-  // stage 2: smoothing sweeps and inner tolerance on the two best shapes
+  // stage 2: smoothing sweeps (finest level, coarse levels) and inner
+  // tolerance on the two best shapes
   std::vector<Cand> cands;
   for (int i = 0; i < std::min<int>(2, (int)shapes.size()); ++i)
     for (int nu : {1, 2})
+      for (int nuc : {1, 2})
       for (double inner : (mixed ? std::vector<double>{1e-4, 1e-5} : std::vector<double>{save_cfg.inner_rtol})) {
+        // only the band kernel smooths the coarse levels separately
+        if (nuc != nu && P->last_kernel != 2) continue;
         Cand c = shapes[i];
         c.nu = nu;
+        c.nuc = nuc;
         c.inner = inner;
         c.t1 = 1e300;
         apply_cand(c);
@@ -705,10 +718,6 @@ lrp_status lrp_autotune(lrp_problem* P, int nvec, int steps, double* best_ms) {
     apply_cand(cands[i]);
     time_it(hess, -1, &cands[i].t2);
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  cudaFree(X);
-  cudaFree(Y);
   int bi = -1;
   for (int i = 0; i < n2; ++i)
     if (cands[i].t2 < 1e300 && (bi < 0 || cands[i].t2 < cands[bi].t2)) bi = i;
@@ -718,19 +727,51 @@ lrp_status lrp_autotune(lrp_problem* P, int nvec, int steps, double* best_ms) {
     P->nthreads = save_NT;
     P->allow_waves = save_W;
     P->cfg = save_cfg;
+    P->team_ctas_narrow = save_narrow;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(X);
+    cudaFree(Y);
     set_error("lrp_autotune: no candidate ran");
     return LRP_ECUDA;
   }
   apply_cand(cands[bi]);
   if (best_ms) *best_ms = cands[bi].t2;
+  // stage 4: cluster size for one-column launches (a single column leaves
+  // most of the GPU idle; larger clusters shorten each step), kept only if
+  // clearly faster than the winner's own size
+  {
+    double t_base = 1e300;
+    time_cols(1, screen, steps, &t_base);
+    int best_c = 0;
+    double best_t = t_base;
+    for (int Cn : {4, 8, 12, 16}) {
+      if (Cn <= P->team_ctas || (long long)P->nx / Cn < 256) continue;
+      P->team_ctas_narrow = Cn;
+      double t = 1e300;
+      time_cols(1, screen, steps, &t);
+      if (t < 0.95 * best_t) {
+        best_t = t;
+        best_c = Cn;
+      }
+    }
+    P->team_ctas_narrow = best_c;
+    if (std::getenv("LRP_VERBOSE"))
+      std::fprintf(stderr, "[lrp] autotune one column: %.2f ms at C=%d, %.2f ms at C=%d (kept %d)\n", t_base,
+                   P->team_ctas, best_t, best_c ? best_c : P->team_ctas, best_c);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(X);
+  cudaFree(Y);
   if (std::getenv("LRP_VERBOSE")) {
     for (int i = 0; i < std::min<int>(6, (int)shapes.size()); ++i)
       std::fprintf(stderr, "[lrp] autotune shape C=%d NT=%d BV=%d waves=%d: screen %.2f ms\n", shapes[i].C,
                    shapes[i].NT, shapes[i].BV, shapes[i].waves, shapes[i].t1);
     for (int i = 0; i < n2; ++i)
       std::fprintf(stderr,
-                   "[lrp] autotune nvec=%d: C=%d NT=%d BV=%d waves=%d nu=%d inner=%.0e screen %.2f ms, apply %.2f ms%s\n",
-                   nvec, cands[i].C, cands[i].NT, cands[i].BV, cands[i].waves, cands[i].nu, cands[i].inner,
+                   "[lrp] autotune nvec=%d: C=%d NT=%d BV=%d waves=%d nu=%d/%d inner=%.0e screen %.2f ms, apply %.2f ms%s\n",
+                   nvec, cands[i].C, cands[i].NT, cands[i].BV, cands[i].waves, cands[i].nu, cands[i].nuc, cands[i].inner,
                    cands[i].t1, cands[i].t2, i == bi ? " <- kept" : "");
   }
   return LRP_OK;

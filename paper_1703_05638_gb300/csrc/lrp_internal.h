@@ -170,6 +170,10 @@ struct lrp_problem {
   int team_ctas, team_cols, nthreads, coarse_items, smem_cap, kernel_variant;
   int last_kernel = 0, last_team_ctas = 0;  // what the last sweep launch used
   int allow_waves = 0;  // 1: keep the requested cluster size even if not all teams are resident at once
+  // cluster size for launches whose teams at this size all fit on the GPU at
+  // once (few columns: a sweep is then latency-bound and more CTAs per
+  // column shorten every step); 0 = team_ctas
+  int team_ctas_narrow = 0;
   int poison;  // LRP_POISON set: new workspace and shared memory start as NaN
   // caller-provided sweep workspace (set only for the duration of an
   // allocation-free call; NULL otherwise)

@@ -170,7 +170,7 @@ struct Model {
   size_t handle_bytes = 0;  // measured bytes of one worker handle for this model
   // launch shape and multigrid settings every worker handle uses (autotuned)
   bool tuned = false;
-  int team_ctas = 0, team_cols = 0, nthreads = 0, allow_waves = 0;
+  int team_ctas = 0, team_cols = 0, nthreads = 0, allow_waves = 0, team_ctas_narrow = 0;
   SolveCfg cfg{};
   int in_use = 0;
   double last_used = 0.0;
@@ -218,6 +218,7 @@ lrp_status slot_model_create(lrp_server* S, cudaStream_t s, Model& m, std::uniqu
     P->team_cols = m.team_cols;
     P->nthreads = m.nthreads;
     P->allow_waves = m.allow_waves;
+    P->team_ctas_narrow = m.team_ctas_narrow;
     P->cfg = m.cfg;
   }
   h->nx = m.nx;
@@ -691,6 +692,7 @@ lrp_status lrp_server_add_model(lrp_server* S, const lrp_problem_desc* d, int k,
       m->team_cols = P->team_cols;
       m->nthreads = P->nthreads;
       m->allow_waves = P->allow_waves;
+      m->team_ctas_narrow = P->team_ctas_narrow;
       m->cfg = P->cfg;
     }
   }

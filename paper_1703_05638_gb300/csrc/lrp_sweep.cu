@@ -160,8 +160,11 @@ lrp_status sweep_enqueue(lrp_problem* Pr, unsigned stages, int nvec, const doubl
   prm.poison = Pr->poison;
   prm.step.Ls = Ls;
   prm.prior.Ls = Ls;
-  // team size: the largest C <= the requested one whose teams all stay resident
+  // team size: the largest C <= the requested one whose teams all stay
+  // resident; few teams take the narrow-launch size when they all fit at it
   int C = Pr->team_ctas;
+  if (Pr->team_ctas_narrow > 0 && (long long)n_teams * Pr->team_ctas_narrow <= Pr->sm_count)
+    C = Pr->team_ctas_narrow;
   // Band kernel (2D, kappa = 1, one column per team, FP32 inner): every CTA
   // keeps its band of the finest level and all coarse levels in shared memory.
   bool fast = false;

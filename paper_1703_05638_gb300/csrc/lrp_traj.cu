@@ -195,7 +195,9 @@ struct TrajCol {
 // Scratch shared by all columns (batched over columns b with fixed strides).
 struct TrajWS {
   int nvec, s, rmax, m;  // m = rmax + s
-  DBuf traj;             // nvec x s x nx: the chunk's states, orthonormalised in place
+  DBuf traj[2];          // nvec x s x nx: a chunk's states, orthonormalised in place
+                         // (two buffers: the next chunk's sweep fills one while
+                         // the other is being absorbed)
   DBuf C, C2;            // nvec x (rmax*s)
   DBuf R;                // nvec x s*s
   DBuf part;             // gemm_tn scratch
@@ -210,15 +212,18 @@ struct TrajWS {
   }
 };
 
-// Absorb one chunk (sk steps, all columns) into the factors.
-static lrp_status absorb_chunk(lrp_problem* P, std::vector<TrajCol>& cols, TrajWS& ws, int sk, double tol_k) {
-  cudaStream_t st = P->stream;
-  const int nx = P->nx, nt = P->nt, nvec = ws.nvec, s = ws.s, rmax = ws.rmax, M = ws.m;
+// Absorbing one chunk (sk steps, all columns; states in `traj`) into the
+// factors takes two parts. The head (steps 1-2) is enqueued on stream `st`
+// when no other work of the trajectory is in flight, so that a single
+// column's QR may use the cooperative grid.
+static lrp_status absorb_head(lrp_problem* P, std::vector<TrajCol>& cols, TrajWS& ws, int sk, cudaStream_t st,
+                              double* traj) {
+  const int nx = P->nx, nvec = ws.nvec, s = ws.s, rmax = ws.rmax;
   // 1. project the chunk onto the complement of each column's Qw (CGS2)
   for (int b = 0; b < nvec; ++b) {
     TrajCol& tc = cols[b];
     const int r = tc.r;
-    double* B = ws.traj.p + (size_t)b * s * nx;
+    double* B = traj + (size_t)b * s * nx;
     double* C = ws.C.p + (size_t)b * rmax * s;
     if (r == 0) continue;
     CKT(cudaMemsetAsync(C, 0, (size_t)r * sk * sizeof(double), st));
@@ -228,9 +233,17 @@ static lrp_status absorb_chunk(lrp_problem* P, std::vector<TrajCol>& cols, TrajW
       CKT(axpby(st, (size_t)r * sk, 1.0, ws.C2.p, 1.0, C));
     }
   }
-  // 2. rank-revealing thin QR of the remainders (one CTA per column)
-  CKT(block_gs(st, nvec, nx, sk, ws.traj.p, (size_t)s * nx, nx, ws.R.p, (size_t)s * s, 1e-13, nullptr, nullptr,
+  // 2. rank-revealing thin QR of the remainders
+  CKT(block_gs(st, nvec, nx, sk, traj, (size_t)s * nx, nx, ws.R.p, (size_t)s * s, 1e-13, nullptr, nullptr,
                ws.gs.p));
+  return LRP_OK;
+}
+
+// The tail (steps 3-4), on stream `st`, may overlap the next chunk's sweep;
+// the host waits for the core SVD's singular values.
+static lrp_status absorb_tail(lrp_problem* P, std::vector<TrajCol>& cols, TrajWS& ws, int sk, double tol_k,
+                              cudaStream_t st, const double* traj) {
+  const int nx = P->nx, nt = P->nt, nvec = ws.nvec, s = ws.s, rmax = ws.rmax, M = ws.m;
   // 3. SVD of every column's small core (one-sided Jacobi)
   std::vector<int> iarr(2 * nvec);
   for (int b = 0; b < nvec; ++b) {
@@ -289,7 +302,7 @@ static lrp_status absorb_chunk(lrp_problem* P, std::vector<TrajCol>& cols, TrajW
     const double* Ub = ws.Zaug.p + (size_t)b * 4 * M * M;
     const double* Zvb = Ub + (size_t)m * m;
     // Qw <- [Qw Q2] U
-    const double* Q2 = ws.traj.p + (size_t)b * s * nx;
+    const double* Q2 = traj + (size_t)b * s * nx;
     if (r > 0) {
       CKT(gemm_nn(st, nx, r, rn, 1.0, tc.Qa.p, nx, Ub, m, 0.0, tc.Qb.p, nx));
       CKT(gemm_nn(st, nx, sk, rn, 1.0, Q2, nx, Ub + r, m, 1.0, tc.Qb.p, nx));
@@ -311,6 +324,42 @@ static lrp_status absorb_chunk(lrp_problem* P, std::vector<TrajCol>& cols, TrajW
   }
   return LRP_OK;
 }
+
+// Second stream, events and pinned sweep statistics of the chunk pipeline.
+// Destruction waits for both streams, so that no buffer is freed under work
+// still in flight after an early return.
+struct TrajPipe {
+  cudaStream_t main = nullptr, s2 = nullptr;
+  cudaEvent_t sw0[2] = {}, sw1[2] = {}, head_done[2] = {}, absorbed[2] = {};
+  Stats* h_stats = nullptr;  // pinned, two
+  SweepLaunch info[2];
+  cudaError_t init(cudaStream_t m) {
+    main = m;
+    cudaError_t e = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+      e = cudaEventCreate(&sw0[i]);
+      if (e == cudaSuccess) e = cudaEventCreate(&sw1[i]);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&head_done[i], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&absorbed[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaMallocHost(&h_stats, 2 * sizeof(Stats));
+    return e;
+  }
+  ~TrajPipe() {
+    if (s2) {
+      cudaStreamSynchronize(s2);
+      cudaStreamSynchronize(main);
+      cudaStreamDestroy(s2);
+    }
+    for (int i = 0; i < 2; ++i) {
+      if (sw0[i]) cudaEventDestroy(sw0[i]);
+      if (sw1[i]) cudaEventDestroy(sw1[i]);
+      if (head_done[i]) cudaEventDestroy(head_done[i]);
+      if (absorbed[i]) cudaEventDestroy(absorbed[i]);
+    }
+    if (h_stats) cudaFreeHost(h_stats);
+  }
+};
 
 lrp_status trajectory_factors_impl(lrp_problem* P, int nvec, const double* U, int ldu, double* Wout,
                                    double* Vout, int* ranks, lrp_apply_stats* stats, bool with_hessian,
@@ -334,7 +383,8 @@ lrp_status trajectory_factors_impl(lrp_problem* P, int nvec, const double* U, in
   ws.rmax = rmax;
   ws.m = rmax + s;
   const int M = ws.m;
-  CKT(ws.traj.alloc((size_t)nvec * s * nx));
+  CKT(ws.traj[0].alloc((size_t)nvec * s * nx));
+  CKT(ws.traj[1].alloc((size_t)nvec * s * nx));
   CKT(ws.C.alloc((size_t)nvec * rmax * s));
   CKT(ws.C2.alloc((size_t)rmax * s));
   CKT(ws.R.alloc((size_t)nvec * s * s));
@@ -357,19 +407,65 @@ lrp_status trajectory_factors_impl(lrp_problem* P, int nvec, const double* U, in
     iters_sum += st.pcg_iters_mean * st.n_solves;
     solves += st.n_solves;
   };
-  for (int c0 = 0; c0 < nt; c0 += s) {
-    const int c1 = std::min(nt, c0 + s);
+  // On the problem stream, per chunk j: its sweep, then (once chunk j-1 is
+  // fully absorbed) the head of its absorption. On the second stream: the
+  // tail, which overlaps chunk j+1's sweep (the sweep only continues its own
+  // state; the tail only reads chunk j's buffer and the small factors).
+  // Chunk j+1's sweep refills the buffer of chunk j-1, whose tail the head
+  // of chunk j has waited for.
+  TrajPipe pp;
+  CKT(pp.init(P->stream));
+  auto enqueue_sweep = [&](int j) -> lrp_status {
+    const int b = j & 1, c0 = j * s, c1 = std::min(nt, c0 + s);
     unsigned stages = ST_FORWARD | ST_TRAJ;
-    if (c0 == 0) stages |= ST_LOAD_X | (with_hessian ? ST_PRIOR_IN : 0);
+    if (j == 0) stages |= ST_LOAD_X | (with_hessian ? ST_PRIOR_IN : 0);
+    CKT(cudaEventRecord(pp.sw0[b], P->stream));
+    lrp_status r = sweep_enqueue(P, stages, nvec, U, ldu, nullptr, 0, nullptr, 0, nullptr, 0, c0, c1,
+                                 ws.traj[b].p, s, pp.h_stats + b, pp.info + b);
+    if (r != LRP_OK) return r;
+    CKT(cudaEventRecord(pp.sw1[b], P->stream));
+    return LRP_OK;
+  };
+  auto enqueue_head = [&](int j) -> lrp_status {
+    const int b = j & 1, c0 = j * s, c1 = std::min(nt, c0 + s);
+    if (j > 0) CKT(cudaStreamWaitEvent(P->stream, pp.absorbed[b ^ 1], 0));
+    lrp_status r = absorb_head(P, cols, ws, c1 - c0, P->stream, ws.traj[b].p);
+    if (r != LRP_OK) return r;
+    CKT(cudaEventRecord(pp.head_done[b], P->stream));
+    return LRP_OK;
+  };
+  {
+    lrp_status r = enqueue_sweep(0);
+    if (r == LRP_OK) r = enqueue_head(0);
+    if (r != LRP_OK) return r;
+  }
+  for (int j = 0; j < K; ++j) {
+    const int b = j & 1, c0 = j * s, c1 = std::min(nt, c0 + s);
+    if (j + 1 < K) {
+      lrp_status r = enqueue_sweep(j + 1);
+      if (r != LRP_OK) return r;
+    }
+    CKT(cudaStreamWaitEvent(pp.s2, pp.head_done[b], 0));
+    lrp_status a = absorb_tail(P, cols, ws, c1 - c0, tol_k, pp.s2, ws.traj[b].p);
+    if (a != LRP_OK) return a;
+    CKT(cudaEventRecord(pp.absorbed[b], pp.s2));
+    // chunk j's sweep has completed (its head followed it)
+    CKT(cudaEventSynchronize(pp.sw1[b]));
+    float ms = 0.f;
+    CKT(cudaEventElapsedTime(&ms, pp.sw0[b], pp.sw1[b]));
+    ledger_add(P, pp.h_stats[b], pp.info[b], ms);
     lrp_apply_stats st;
-    lrp_status sres = run_sweep_ex(P, stages, nvec, U, ldu, nullptr, 0, nullptr, 0, nullptr, 0, &st, c0, c1,
-                                   ws.traj.p, s);
+    lrp_status sres = sweep_status(pp.h_stats[b], pp.info[b], &st, ms);
     if (sres != LRP_OK && sres != LRP_ENOCONV) return sres;
     if (sres == LRP_ENOCONV) result = sres;
     fold(st);
-    lrp_status a = absorb_chunk(P, cols, ws, c1 - c0, tol_k);
-    if (a != LRP_OK) return a;
+    if (j + 1 < K) {
+      lrp_status r = enqueue_head(j + 1);
+      if (r != LRP_OK) return r;
+    }
   }
+  // the trailing GEMMs of the last absorption precede everything below
+  CKT(cudaStreamWaitEvent(P->stream, pp.absorbed[(K - 1) & 1], 0));
   if (with_hessian) {
     lrp_apply_stats st;
     lrp_status sres = run_sweep_ex(P, ST_ADJOINT | ST_PRIOR_OUT | ST_STORE_Y, nvec, nullptr, 0, Yout, ldy,

@@ -26,6 +26,10 @@ pytestmark = pytest.mark.gpu
 TOL = {lrp.LRP_FP64: 1e-10, lrp.LRP_MIXED: 1e-6}
 
 
+def _sm_count():
+    return torch.cuda.get_device_properties(0).multi_processor_count
+
+
 def relerr(a, b):
     a = np.asarray(a)
     b = np.asarray(b)
@@ -151,8 +155,10 @@ def test_lanczos_tiny_wide_blocks(block, precision):
     """Blocks wider than the numerical rank of the tiny workload's Hessian
     (its spectrum falls to 1e-16 lam_1 by index 30): the Krylov space is
     exhausted after two block steps and the new directions are noise of the
-    inexact apply; they are deflated (R18) and T keeps the full measured
-    projection (R17). The leading eigenvalues then stay within 1e-8 lam_1
+    inexact apply; they are deflated (dropped when what is left after
+    re-orthogonalisation is below max(1e-9, 1000 x the solve tolerance) of the
+    column's earlier norm) and T keeps the full measured projection Q^T Htilde Q
+    (couplings to all earlier blocks). The leading eigenvalues then stay within 1e-8 lam_1
     (measured: 3e-9 at block 32 in FP64) and the top-3 projector within 1e-6."""
     spec = synth.workload("tiny")
     P, G = _pair(spec, precision)
@@ -224,6 +230,43 @@ def test_trajectory_factors(precision):
         r_opt = otf.truncate(Y, 1e-8, 40)[0].shape[1]
         assert r_opt <= W.shape[1] <= r_opt + 8
     assert st["time_trunc_err"] <= 1e-8
+
+
+def test_trajectory_one_column_narrow_cluster():
+    """One column through several chunks, at the narrow-launch cluster size
+    of 16 CTAs (the cooperative QR of a single column and the overlap of each
+    chunk's compression with the next chunk's sweep): the factors reproduce
+    the oracle's trajectory."""
+    spec = synth.small_spec(dim=2, n=63, nt=70, obs_every=5, n_obs=8, seed=8)
+    spec.time_trunc_tol = 1e-8
+    P, G = _pair(spec, lrp.LRP_MIXED)
+    t = lrp.lrp_problem_tuning(G)
+    t["team_ctas_narrow"] = 16
+    lrp.lrp_set_tuning(G, t)
+    U = P.prior_half(synth.normal_block(P.nx, 1, 9))
+    facs, st = lrp.lrp_trajectory_factors(G, U)
+    assert lrp.lrp_problem_tuning(G)["last_team_ctas"] == 16
+    W, V = facs[0]
+    Y = P.trajectory(U[:, 0])
+    err = np.linalg.norm(Y - W @ V.T) / np.linalg.norm(Y)
+    assert err <= 1e-8 + 10 * TOL[lrp.LRP_MIXED], (err, st)
+    assert np.allclose(W.T @ W, np.diag(np.sum(W * W, axis=0)), atol=1e-10 * np.linalg.norm(W) ** 2)
+
+
+def test_narrow_cluster_size_only_for_few_columns():
+    """team_ctas_narrow applies when all of a launch's clusters fit on the GPU
+    at that size; both launch forms match the oracle."""
+    spec = synth.small_spec(dim=2, n=63, nt=12, obs_every=3, n_obs=8, seed=10)
+    P, G = _pair(spec, lrp.LRP_MIXED)
+    t = lrp.lrp_problem_tuning(G)
+    t["team_ctas_narrow"] = 16
+    lrp.lrp_set_tuning(G, t)
+    for ncols in (1, 12):
+        X = synth.normal_block(P.nx, ncols, 11)
+        H, st = lrp.lrp_hessian_apply(G, X)
+        used = lrp.lrp_problem_tuning(G)["last_team_ctas"]
+        assert (used == 16) == (ncols * 16 <= _sm_count()), (ncols, used)
+        assert relerr(H, P.hessian_apply(X)) < TOL[lrp.LRP_MIXED], st
 
 
 def test_hessian_with_trajectory_factors_matches_plain():
