@@ -206,7 +206,7 @@ lrp_status lrp_hessian_apply_noalloc(lrp_problem* p, int nvec, const double* X, 
  * (0 -> 16); stage 2 varies the smoothing sweeps (finest and coarse levels,
  * 1 or 2 each) and (LRP_MIXED) the inner
  * tolerance on the two best shapes; stage 3 times one whole Hessian apply for
- * the three best; stage 4 times the stage-1 screen for one column at larger
+ * the five best; stage 4 times the stage-1 screen for one column at larger
  * cluster sizes (team_ctas_narrow of lrp_tuning). The winner stays in the
  * problem handle for later calls.
  * All candidates iterate to the same tolerances. *best_ms (may be NULL)

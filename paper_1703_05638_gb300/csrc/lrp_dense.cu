@@ -2,10 +2,10 @@
 //  * gemm_tn: C = A^T B for tall-skinny A (nx x m) and B (nx x nb), split over
 //    row chunks with a fixed-order second-stage reduction (deterministic);
 //  * gemm_nn: Y = beta Y + alpha A M for A (nx x m) and a small M (m x nc);
-//  * Cholesky of a small Gram matrix (CholQR) with a rank-deficiency test;
-//  * symmetric eigensolver for the (block) tridiagonal Lanczos matrix:
-//    Householder reduction to tridiagonal form with accumulated reflections,
-//    then implicit QL iterations with Wilkinson shifts; one CTA;
+//  * rank-revealing block Gram-Schmidt (CGS2) of up to 64 columns;
+//  * symmetric eigensolver for the projected Lanczos matrix: Householder
+//    reduction to tridiagonal form, implicit QL iterations with Wilkinson
+//    shifts, back-transformation of the eigenvectors;
 //  * small elementwise helpers (column norms, scaling, gathers, fills).
 // FP64 throughout: the Lanczos eigensolve, re-orthogonalisation and the
 // posterior factors stay in FP64.
@@ -16,6 +16,7 @@
 #include <cooperative_groups.h>
 
 #include "lrp_dense.h"
+#include "lrp_fp64.cuh"
 #include "lrp_internal.h"
 
 namespace lrp {
@@ -107,55 +108,48 @@ __global__ void __launch_bounds__(256) k_gemm_nn(int nx, int m, int nc, double a
 
 // ---------------------------------------------------------------- eigensolver
 // Symmetric eigendecomposition of the n x n matrix A (column-major, ld lda,
-// destroyed) into theta (decreasing) and Z (n x n, ld ldz), one CTA.
-// Step 1: Householder reflections H_k = I - 2 v v^T zero column k below the
-// subdiagonal; A <- H_k A H_k, Z <- Z H_k.
-// Step 2: implicit QL on the tridiagonal (d, e): repeatedly pick the
-// unreduced block [l, m], shift by the eigenvalue of the leading 2x2 closest
-// to d_l, chase the bulge with plane rotations from m-1 down to l. The
-// rotation angles depend only on (d, e): thread 0 computes a whole chase,
-// then all threads apply it to their rows of Z.
-// Step 3: sort by decreasing eigenvalue.
+// destroyed) into theta (decreasing) and Z (n x n, ld ldz), in three kernels:
+// 1. k_tridiag (one CTA): Householder reflections H_k = I - 2 v_k v_k^T zero
+//    column k below the subdiagonal, A <- H_k A H_k; the tridiagonal (d, e)
+//    and the unit vectors v_k (stored in A below the diagonal) are kept.
+// 2. k_tql (several CTAs, each owning a band of rows of Z): implicit QL on
+//    (d, e) with Wilkinson shifts: repeatedly pick the unreduced block [l, m],
+//    shift by the eigenvalue of the leading 2x2 closest to d_l and chase the
+//    bulge with plane rotations from m-1 down to l. The rotation angles depend
+//    only on (d, e): lane 0 of warp 0 computes the next chase (every CTA the
+//    same, from the same data) while the other warps apply the previous one
+//    to the CTA's rows of the tridiagonal problem's eigenvector matrix (rows
+//    of the identity at the start). Eigenvalues are then ranked (decreasing)
+//    and the rows written with their columns in that order.
+// 3. k_eig_back (one warp per column): Z <- H_0 H_1 ... H_{n-3} Z, the
+//    eigenvectors of A.
 #define EIG_NT 512
+#define TQL_NT 64      // warp 0 computes the chases, warp 1 applies them
+#define TQL_ROWS 32    // rows of Z per CTA (one per thread of warp 1)
+#define BACK_WARPS 8   // columns per CTA of the back-transformation
 
-__global__ void __launch_bounds__(EIG_NT) k_eig_sym(int n, double* A, int lda, double* Z, int ldz,
-                                                     double* theta, double* work, int* status,
-                                                     const int* n_batch, size_t strideA, size_t strideZ,
-                                                     size_t strideT, size_t strideW) {
-  // batched mode: block b works on matrix b (its size in n_batch[b])
-  if (n_batch) {
-    const int b = blockIdx.x;
-    n = n_batch[b];
-    lda = ldz = n;
-    A += b * strideA;
-    Z += b * strideZ;
-    theta += b * strideT;
-    work += b * strideW;
-    if (status) status += b;
-  }
-  __shared__ double s_red[EIG_NT / 32];
-  __shared__ double s_scal[4];
-  __shared__ double s_c[1024], s_s[1024];
-  __shared__ int s_int[4];
+__device__ __forceinline__ double eig_block_sum(double x, double* s_red) {
   const int tid = threadIdx.x;
-  double* v = work;          // n
-  double* pvec = work + n;   // n
-  double* d = work + 2 * n;  // n
-  double* e = work + 3 * n;  // n
-  auto At = [&](int i, int j) -> double& { return A[(size_t)j * lda + i]; };
-  auto Zt = [&](int i, int j) -> double& { return Z[(size_t)j * ldz + i]; };
-  auto block_sum = [&](double x) -> double {
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if ((tid & 31) == 0) s_red[tid >> 5] = x;
-    __syncthreads();
-    double s = 0.0;
-    for (int w = 0; w < EIG_NT / 32; ++w) s += s_red[w];
-    __syncthreads();
-    return s;
-  };
-  for (int i = tid; i < n * n; i += EIG_NT) Zt(i % n, i / n) = (i % n == i / n) ? 1.0 : 0.0;
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  if ((tid & 31) == 0) s_red[tid >> 5] = x;
   __syncthreads();
-  // ---- Householder tridiagonalisation
+  double s = 0.0;
+  for (int w = 0; w < EIG_NT / 32; ++w) s += s_red[w];
+  __syncthreads();
+  return s;
+}
+
+// work: d (n), e (n), tau (n; 2 for a stored reflection, 0 for none), then
+// two n-vectors of scratch.
+__global__ void __launch_bounds__(EIG_NT) k_tridiag(int n, double* A, int lda, double* work) {
+  __shared__ double s_red[EIG_NT / 32];
+  const int tid = threadIdx.x;
+  double* d = work;
+  double* e = work + n;
+  double* tau = work + 2 * n;
+  double* v = work + 3 * n;
+  double* pvec = work + 4 * n;
+  auto At = [&](int i, int j) -> double& { return A[(size_t)j * lda + i]; };
   for (int k = 0; k + 2 < n; ++k) {
     const int m0 = k + 1, len = n - m0;
     double part = 0.0;
@@ -163,27 +157,44 @@ __global__ void __launch_bounds__(EIG_NT) k_eig_sym(int n, double* A, int lda, d
       const double x = At(m0 + i, k);
       part += x * x;
     }
-    const double xnorm2 = block_sum(part);
+    const double xnorm2 = eig_block_sum(part, s_red);
     const double x0 = At(m0, k);
-    const double xnorm = sqrt(xnorm2);
     const double tail2 = xnorm2 - x0 * x0;
-    if (!(tail2 > 1e-300)) continue;  // column already reduced
+    if (!(tail2 > 1e-300)) {  // column already reduced
+      if (tid == 0) {
+        e[k] = x0;
+        tau[k] = 0.0;
+      }
+      continue;
+    }
+    const double xnorm = sqrt(xnorm2);
     const double alpha = x0 > 0 ? -xnorm : xnorm;
-    // v = x - alpha e1, normalised
+    // v = x - alpha e1, normalised, kept in column k below the diagonal
     const double v0 = x0 - alpha;
     const double vnorm = sqrt(tail2 + v0 * v0);
-    for (int i = tid; i < len; i += EIG_NT) v[i] = (i == 0 ? v0 : At(m0 + i, k)) / vnorm;
+    for (int i = tid; i < len; i += EIG_NT) {
+      const double vi = (i == 0 ? v0 : At(m0 + i, k)) / vnorm;
+      v[i] = vi;
+      At(m0 + i, k) = vi;
+    }
     __syncthreads();
     // p = 2 B v on the trailing block B = A[m0:, m0:]
     for (int i = tid; i < len; i += EIG_NT) {
-      double s = 0.0;
-      for (int j = 0; j < len; ++j) s += At(m0 + i, m0 + j) * v[j];
-      pvec[i] = 2.0 * s;
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int j = 0;
+      for (; j + 3 < len; j += 4) {
+        s0 = fma(At(m0 + i, m0 + j), v[j], s0);
+        s1 = fma(At(m0 + i, m0 + j + 1), v[j + 1], s1);
+        s2 = fma(At(m0 + i, m0 + j + 2), v[j + 2], s2);
+        s3 = fma(At(m0 + i, m0 + j + 3), v[j + 3], s3);
+      }
+      for (; j < len; ++j) s0 = fma(At(m0 + i, m0 + j), v[j], s0);
+      pvec[i] = 2.0 * ((s0 + s1) + (s2 + s3));
     }
     __syncthreads();
     double kp = 0.0;
     for (int i = tid; i < len; i += EIG_NT) kp += v[i] * pvec[i];
-    const double K = block_sum(kp);
+    const double K = eig_block_sum(kp, s_red);
     // q = p - K v; B <- B - v q^T - q v^T
     for (int i = tid; i < len; i += EIG_NT) pvec[i] -= K * v[i];
     __syncthreads();
@@ -191,126 +202,202 @@ __global__ void __launch_bounds__(EIG_NT) k_eig_sym(int n, double* A, int lda, d
       const int i = idx % len, j = idx / len;
       At(m0 + i, m0 + j) -= v[i] * pvec[j] + pvec[i] * v[j];
     }
-    for (int i = tid; i < len; i += EIG_NT) {
-      At(m0 + i, k) = (i == 0) ? alpha : 0.0;
-      At(k, m0 + i) = (i == 0) ? alpha : 0.0;
-    }
-    // Z[:, m0:] <- Z[:, m0:] (I - 2 v v^T)
-    for (int r = tid; r < n; r += EIG_NT) {
-      double s = 0.0;
-      for (int j = 0; j < len; ++j) s += Zt(r, m0 + j) * v[j];
-      s *= 2.0;
-      for (int j = 0; j < len; ++j) Zt(r, m0 + j) -= s * v[j];
+    if (tid == 0) {
+      e[k] = alpha;
+      tau[k] = 2.0;
     }
     __syncthreads();
   }
   for (int i = tid; i < n; i += EIG_NT) {
     d[i] = At(i, i);
-    e[i] = (i + 1 < n) ? At(i + 1, i) : 0.0;
+    if (i + 2 >= n) e[i] = (i + 1 < n) ? At(i + 1, i) : 0.0;
+    if (i + 2 >= n) tau[i] = 0.0;
   }
+}
+
+// Dynamic shared memory: d, e (n each), two chase buffers (c then s, n each),
+// the CTA's rows of the eigenvector matrix (rows x (n+1)), the ranking (n ints).
+__global__ void __launch_bounds__(TQL_NT) k_tql(int n, const double* work, double* Z, int ldz, double* theta,
+                                                int* status, int rows) {
+  extern __shared__ double sm_tql[];
+  double* d = sm_tql;
+  double* e = d + n;
+  double* cs = e + n;  // buffer b: c at cs + 2 n b, s at cs + 2 n b + n
+  double* Zs = cs + 4 * n;
+  const int ldzs = n + 1;
+  int* perm = (int*)(Zs + (size_t)rows * ldzs);
+  __shared__ int s_cnt[2], s_m[2], s_fail;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int r0 = blockIdx.x * rows, nr = min(rows, n - r0);
+  for (int i = tid; i < n; i += TQL_NT) {
+    d[i] = work[i];
+    e[i] = work[n + i];
+  }
+  for (int idx = tid; idx < rows * ldzs; idx += TQL_NT) {
+    const int r = idx / ldzs, c = idx % ldzs;
+    Zs[idx] = (r0 + r == c) ? 1.0 : 0.0;
+  }
+  if (tid == 0) s_fail = 0;
   __syncthreads();
-  // ---- implicit QL with Wilkinson shifts
-  if (tid == 0) s_int[0] = 0;
-  __syncthreads();
-  for (int l = 0; l < n; ++l) {
-    int iter = 0;
-    for (;;) {
-      // thread 0 finds the block end and computes the rotation chase
-      if (tid == 0) {
-        int m = l;
-        for (; m < n - 1; ++m) {
-          const double dd = fabs(d[m]) + fabs(d[m + 1]);
-          if (fabs(e[m]) <= 2.220446049250313e-16 * dd) break;
+  // producer state (warp 0, the same in every lane): current l and its iterations
+  int l = 0, iter = 0;
+  // computes the next chase into buffer b: s_cnt[b] rotations ending at
+  // column s_m[b], or s_cnt[b] = -1 once every eigenvalue has converged
+  auto produce = [&](int b) {
+    double* cb = cs + 2 * (size_t)n * b;
+    double* sb = cb + n;
+    int cnt = -1, m = l;
+    while (l < n) {
+      // block end: first m >= l with a negligible e[m] (32 candidates at a time)
+      m = n - 1;
+      for (int base = l; base < n - 1; base += 32) {
+        const int mi = base + lane;
+        bool small = false;
+        if (mi < n - 1) small = fabs(e[mi]) <= 2.220446049250313e-16 * (fabs(d[mi]) + fabs(d[mi + 1]));
+        const unsigned bal = __ballot_sync(0xffffffffu, small);
+        if (bal) {
+          m = base + __ffs(bal) - 1;
+          break;
         }
-        s_int[1] = m;
-        s_int[2] = 0;
-        if (m != l) {
-          if (iter >= 60) {
-            s_int[0] = 1;  // no convergence; leave as is
-            s_int[1] = l;
+      }
+      if (m == l) {
+        ++l;
+        iter = 0;
+        continue;
+      }
+      if (iter >= 60) {  // no convergence for this eigenvalue: leave it as is
+        if (lane == 0) s_fail = 1;
+        ++l;
+        iter = 0;
+        continue;
+      }
+      if (lane == 0) {
+        double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+        double r = hypot(g, 1.0);
+        g = d[m] - d[l] + e[l] / (g + (g >= 0 ? fabs(r) : -fabs(r)));
+        double s = 1.0, c = 1.0, p = 0.0;
+        int nrot = 0;
+        bool early = false;
+        for (int i = m - 1; i >= l; --i) {
+          const double f = s * e[i];
+          const double bb = c * e[i];
+          double ri;
+          if (sqrt_rsqrt_gs(fma(f, f, g * g), &r, &ri)) {
+            s = f * ri;
+            c = g * ri;
           } else {
-            double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-            double r = hypot(g, 1.0);
-            g = d[m] - d[l] + e[l] / (g + (g >= 0 ? fabs(r) : -fabs(r)));
-            double s = 1.0, c = 1.0, p = 0.0;
-            int i = m - 1;
-            int cnt = 0;
-            bool early = false;
-            for (; i >= l; --i) {
-              const double f = s * e[i];
-              const double b = c * e[i];
-              r = hypot(f, g);
-              e[i + 1] = r;
-              if (r == 0.0) {
-                d[i + 1] -= p;
-                e[m] = 0.0;
-                early = true;
-                break;
-              }
-              s = f / r;
-              c = g / r;
-              g = d[i + 1] - p;
-              r = (d[i] - g) * s + 2.0 * c * b;
-              p = s * r;
-              d[i + 1] = g + p;
-              g = c * r - b;
-              s_c[cnt] = c;
-              s_s[cnt] = s;
-              ++cnt;
-            }
-            if (!early) {
-              d[l] -= p;
-              e[l] = g;
+            r = hypot(f, g);
+            if (r == 0.0) {
+              e[i + 1] = 0.0;
+              d[i + 1] -= p;
               e[m] = 0.0;
+              early = true;
+              break;
             }
-            s_int[2] = cnt;
+            s = f / r;
+            c = g / r;
           }
+          e[i + 1] = r;
+          g = d[i + 1] - p;
+          r = (d[i] - g) * s + 2.0 * c * bb;
+          p = s * r;
+          d[i + 1] = g + p;
+          g = c * r - bb;
+          cb[nrot] = c;
+          sb[nrot] = s;
+          ++nrot;
         }
-      }
-      __syncthreads();
-      const int m = s_int[1];
-      const int cnt = s_int[2];
-      if (m == l) break;
-      // apply the chase to the rows of Z: rotation t acts on columns (i, i+1), i = m-1-t
-      for (int r = tid; r < n; r += EIG_NT) {
-        for (int t = 0; t < cnt; ++t) {
-          const int i = m - 1 - t;
-          const double c = s_c[t], s = s_s[t];
-          const double zi = Zt(r, i), zi1 = Zt(r, i + 1);
-          Zt(r, i + 1) = s * zi + c * zi1;
-          Zt(r, i) = c * zi - s * zi1;
+        if (!early) {
+          d[l] -= p;
+          e[l] = g;
+          e[m] = 0.0;
         }
+        cnt = nrot;
       }
-      __syncthreads();
+      cnt = __shfl_sync(0xffffffffu, cnt, 0);
       ++iter;
+      break;
     }
+    if (l >= n) cnt = -1;
+    if (lane == 0) {
+      s_cnt[b] = cnt;
+      s_m[b] = m;
+    }
+    __syncwarp();
+  };
+  if (warp == 0) produce(0);
+  __syncthreads();
+  for (int q = 0;; ++q) {
+    const int b = q & 1;
+    const int cnt = s_cnt[b];
+    if (cnt < 0) break;
+    if (warp == 0) {
+      produce(b ^ 1);
+    } else if (lane < nr && cnt > 0) {
+      // rotation t acts on columns (i, i+1), i = m-1-t; the new column i
+      // is the next rotation's column i+1, carried in a register
+      const double* cb = cs + 2 * (size_t)n * b;
+      const double* sb = cb + n;
+      const int m = s_m[b];
+      double* z = Zs + (size_t)lane * ldzs;
+      double carry = z[m];
+      for (int t = 0; t < cnt; ++t) {
+        const int i = m - 1 - t;
+        const double c = cb[t], s = sb[t], zi = z[i];
+        z[i + 1] = fma(c, carry, s * zi);
+        carry = fma(-s, carry, c * zi);
+      }
+      z[m - cnt] = carry;
+    }
+    __syncthreads();
   }
-  // ---- sort decreasing (selection sort by thread 0 on indices, then permute)
-  int* perm = (int*)(work + 4 * n);
-  if (tid == 0) {
-    for (int i = 0; i < n; ++i) perm[i] = i;
-    for (int i = 0; i < n; ++i) {
-      int best = i;
-      for (int j = i + 1; j < n; ++j)
-        if (d[perm[j]] > d[perm[best]]) best = j;
-      const int tmp = perm[i];
-      perm[i] = perm[best];
-      perm[best] = tmp;
+  // rank by decreasing eigenvalue (ties and NaN by index)
+  for (int i = tid; i < n; i += TQL_NT) {
+    const double di = isnan(d[i]) ? -INFINITY : d[i];
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      const double dj = isnan(d[j]) ? -INFINITY : d[j];
+      rank += (dj > di) || (dj == di && j < i);
     }
-    if (status) *status = s_int[0];
+    perm[rank] = i;
   }
   __syncthreads();
-  for (int i = tid; i < n; i += EIG_NT) theta[i] = d[perm[i]];
-  // permute columns of Z into A (as scratch), then copy back
-  for (int idx = tid; idx < n * n; idx += EIG_NT) {
-    const int r = idx % n, c = idx / n;
-    At(r, c) = Zt(r, perm[c]);
+  for (int idx = tid; idx < nr * n; idx += TQL_NT) {
+    const int r = idx % nr, c = idx / nr;
+    Z[(size_t)c * ldz + r0 + r] = Zs[(size_t)r * ldzs + perm[c]];
   }
-  __syncthreads();
-  for (int idx = tid; idx < n * n; idx += EIG_NT) {
-    const int r = idx % n, c = idx / n;
-    Zt(r, c) = At(r, c);
+  if (blockIdx.x == 0) {
+    for (int i = tid; i < n; i += TQL_NT) theta[i] = d[perm[i]];
+    if (tid == 0 && status) *status = s_fail;
   }
+}
+
+// Z[:, c] <- H_0 H_1 ... H_{n-3} Z[:, c], one warp per column, the column in
+// shared memory; v_k = A[k+1:, k], tau_k = work[2n + k].
+__global__ void __launch_bounds__(32 * BACK_WARPS) k_eig_back(int n, const double* A, int lda,
+                                                              const double* work, double* Z, int ldz) {
+  extern __shared__ double sm_back[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int col = blockIdx.x * BACK_WARPS + warp;
+  if (col >= n) return;
+  const double* tau = work + 2 * n;
+  double* z = sm_back + (size_t)warp * n;
+  double* zg = Z + (size_t)col * ldz;
+  for (int i = lane; i < n; i += 32) z[i] = zg[i];
+  __syncwarp();
+  for (int k = n - 3; k >= 0; --k) {
+    const double tk = tau[k];
+    if (tk == 0.0) continue;
+    const double* v = A + (size_t)k * lda + k + 1;
+    const int len = n - k - 1;
+    double part = 0.0;
+    for (int i = lane; i < len; i += 32) part = fma(v[i], z[k + 1 + i], part);
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    const double w = tk * part;
+    for (int i = lane; i < len; i += 32) z[k + 1 + i] = fma(-w, v[i], z[k + 1 + i]);
+    __syncwarp();
+  }
+  for (int i = lane; i < n; i += 32) zg[i] = z[i];
 }
 
 // resid[i] = || B (nb x nb upper, col-major) * Z[row0:row0+nb, i] ||, i < k
@@ -661,9 +748,34 @@ cudaError_t gemm_nn(cudaStream_t s, int nx, int m, int nc, double alpha, const d
 
 cudaError_t eig_sym(cudaStream_t s, int n, double* A, int lda, double* Z, int ldz, double* theta,
                     double* work, int* status) {
-  if (n > 1024) return cudaErrorInvalidValue;
+  if (n < 1 || n > 1024) return cudaErrorInvalidValue;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  // one value from every caller: the device's opt-in maximum less the static part
+  cudaFuncAttributes fa_tql, fa_back;
+  cudaError_t e = cudaFuncGetAttributes(&fa_tql, k_tql);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa_back, k_eig_back);
+  if (e != cudaSuccess) return e;
+  const size_t cap_tql = (size_t)optin - fa_tql.sharedSizeBytes;
+  const size_t cap_back = (size_t)optin - fa_back.sharedSizeBytes;
+  // rows of Z per QL CTA: at most TQL_ROWS, fewer when n is large
+  const size_t fixed = 6 * (size_t)n * sizeof(double) + (size_t)n * sizeof(int);
+  const size_t per_row = (size_t)(n + 1) * sizeof(double);
+  if (fixed + per_row > cap_tql) return cudaErrorInvalidValue;
+  const int rows = (int)std::min<size_t>(TQL_ROWS, (cap_tql - fixed) / per_row);
+  const size_t smem_tql = fixed + rows * per_row;
+  const size_t smem_back = (size_t)BACK_WARPS * n * sizeof(double);
+  if (smem_back > cap_back) return cudaErrorInvalidValue;
+  e = cudaFuncSetAttribute(k_tql, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap_tql);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eig_back, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap_back);
+  if (e != cudaSuccess) return e;
   note_launch();
-  k_eig_sym<<<1, EIG_NT, 0, s>>>(n, A, lda, Z, ldz, theta, work, status, nullptr, 0, 0, 0, 0);
+  k_tridiag<<<1, EIG_NT, 0, s>>>(n, A, lda, work);
+  note_launch();
+  k_tql<<<(n + rows - 1) / rows, TQL_NT, smem_tql, s>>>(n, work, Z, ldz, theta, status, rows);
+  note_launch();
+  k_eig_back<<<(n + BACK_WARPS - 1) / BACK_WARPS, 32 * BACK_WARPS, smem_back, s>>>(n, A, lda, work, Z, ldz);
   return cudaGetLastError();
 }
 

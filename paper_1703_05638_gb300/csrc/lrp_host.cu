@@ -604,7 +604,7 @@ extern "C" {
 // prior solve and the first `steps` implicit-Euler steps of the forward sweep
 // (the smooth start the Hessian apply sees) with the problem's multigrid
 // settings. Stage 2 (solver): the two fastest shapes time the same with each
-// smoothing-sweep count and (mixed path) inner tolerance. Stage 3: the three
+// smoothing-sweep count and (mixed path) inner tolerance. Stage 3: the five
 // fastest of stage 2 time one whole Hessian apply each; the fastest is kept.
 // Stage 4: the stage-1 screen for a single column at larger cluster sizes
 // picks the size for narrow launches (team_ctas_narrow).
@@ -710,9 +710,10 @@ lrp_status lrp_autotune(lrp_problem* P, int nvec, int steps, double* best_ms) {
         cands.push_back(c);
       }
   std::sort(cands.begin(), cands.end(), by_t1);
-  // stage 3: whole Hessian applies
+  // stage 3: whole Hessian applies for the five best screens (the screen
+  // ranks inner tolerances and smoothing counts only roughly)
   const unsigned hess = ST_LOAD_X | ST_PRIOR_IN | ST_FORWARD | ST_ADJOINT | ST_PRIOR_OUT | ST_STORE_Y;
-  const int n2 = std::min<int>(3, (int)cands.size());
+  const int n2 = std::min<int>(5, (int)cands.size());
   for (int i = 0; i < n2; ++i) {
     if (!(cands[i].t1 < 1e300)) continue;
     apply_cand(cands[i]);
