@@ -532,14 +532,19 @@ extern "C" lrp_status lrp_trajectory_factors(lrp_problem* P, int nvec, const dou
       return cuda_status(e, "trajectory staging");
     }
     const cudaMemcpyKind ku = is_device_ptr(U) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    cudaMemcpy2D(dU, nx * sizeof(double), U, (size_t)ldu * sizeof(double), nx * sizeof(double), nvec, ku);
-    cudaMemset(dW, 0, nx * rmax * nvec * sizeof(double));
-    cudaMemset(dV, 0, nt * rmax * nvec * sizeof(double));
-    lrp_status s = trajectory_factors_impl(P, nvec, dU, (int)nx, dW, dV, ranks, st, false, nullptr, 0);
-    const cudaMemcpyKind kw = is_device_ptr(W) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    const cudaMemcpyKind kv = is_device_ptr(V) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    cudaMemcpy(W, dW, nx * rmax * nvec * sizeof(double), kw);
-    cudaMemcpy(V, dV, nt * rmax * nvec * sizeof(double), kv);
+    e = cudaMemcpy2D(dU, nx * sizeof(double), U, (size_t)ldu * sizeof(double), nx * sizeof(double), nvec, ku);
+    if (e == cudaSuccess) e = cudaMemset(dW, 0, nx * rmax * nvec * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(dV, 0, nt * rmax * nvec * sizeof(double));
+    lrp_status s = e == cudaSuccess
+                       ? trajectory_factors_impl(P, nvec, dU, (int)nx, dW, dV, ranks, st, false, nullptr, 0)
+                       : cuda_status(e, "trajectory staging");
+    if (s == LRP_OK || s == LRP_ENOCONV) {
+      const cudaMemcpyKind kw = is_device_ptr(W) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+      const cudaMemcpyKind kv = is_device_ptr(V) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+      e = cudaMemcpy(W, dW, nx * rmax * nvec * sizeof(double), kw);
+      if (e == cudaSuccess) e = cudaMemcpy(V, dV, nt * rmax * nvec * sizeof(double), kv);
+      if (e != cudaSuccess) s = cuda_status(e, "trajectory results");
+    }
     cudaFree(dU);
     cudaFree(dW);
     cudaFree(dV);
