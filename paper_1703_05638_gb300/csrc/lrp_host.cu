@@ -369,7 +369,10 @@ lrp_status lrp_setup_problem(const lrp_problem_desc* desc, void* cuda_stream, lr
   if ((s = upload(P, &P->bt_w, bw)) != LRP_OK) return fail(s);
   if ((s = dev_alloc(P, &P->stats, 1)) != LRP_OK) return fail(s);
   if ((s = dev_alloc(P, &P->end_buf, 65536)) != LRP_OK) return fail(s);
-  cudaMemset(P->end_buf, 0, 65536 * sizeof(int));
+  {
+    const cudaError_t e = cudaMemset(P->end_buf, 0, 65536 * sizeof(int));
+    if (e != cudaSuccess) return fail(cuda_status(e, "end_buf"));
+  }
   // ---- solver configuration
   SolveCfg& c = P->cfg;
   const bool mixed = d.precision == LRP_MIXED;

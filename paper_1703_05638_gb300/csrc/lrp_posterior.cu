@@ -666,8 +666,12 @@ lrp_status lrp_posterior_save(const lrp_posterior* post, const char* path) {
   const size_t nx = post->nx, k = post->k;
   std::vector<double> V(nx * k), G(nx * k);
   if (k) {
-    cudaMemcpy(V.data(), post->V, V.size() * sizeof(double), cudaMemcpyDeviceToHost);
-    cudaMemcpy(G.data(), post->G, G.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaError_t e = cudaMemcpy(V.data(), post->V, V.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(G.data(), post->G, G.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+      std::fclose(f);
+      return cuda_status(e, "posterior_save");
+    }
   }
   const char magic[8] = {'L', 'R', 'P', 'O', 'S', 'T', '0', '1'};
   const uint64_t hdr[3] = {post->prob->hash, (uint64_t)nx, (uint64_t)k};
@@ -728,9 +732,9 @@ lrp_status lrp_posterior_load(lrp_problem* P, const char* path, lrp_posterior** 
   if (e == cudaSuccess) e = cudaMalloc(&post->G, std::max<size_t>(1, G.size()) * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&post->lambda, std::max<size_t>(1, k) * sizeof(double));
   if (e == cudaSuccess && k) {
-    cudaMemcpy(post->V, V.data(), V.size() * sizeof(double), cudaMemcpyHostToDevice);
-    cudaMemcpy(post->G, G.data(), G.size() * sizeof(double), cudaMemcpyHostToDevice);
-    e = cudaMemcpy(post->lambda, lam.data(), k * sizeof(double), cudaMemcpyHostToDevice);
+    e = cudaMemcpy(post->V, V.data(), V.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(post->G, G.data(), G.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(post->lambda, lam.data(), k * sizeof(double), cudaMemcpyHostToDevice);
   }
   if (e != cudaSuccess) {
     lrp_posterior_destroy(post);
