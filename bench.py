@@ -40,6 +40,12 @@ import synth  # noqa: E402
 
 METRIC = "Hessian matvecs/s (s to rank-k Gamma_post at 1e-6 rel. Ritz residual reported beside)"
 UNIT = "matvec/s"
+
+
+def heat2d_workload(nt: int) -> str:
+    """The workload name both arms report."""
+    return (f"heat2d_127: 2D heat eq 127x127 interior (nx=16129), nt={nt}, 400 uniform sensors at every step, "
+            "sigma=1e-3, prior (I-0.05 Lap)^-2")
 # The two sweep kernels, the sources their device code comes from, and the
 # committed ncu summary (DRAM traffic per launch) for this workload.
 KERNELS = {
@@ -316,8 +322,9 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "heat2d_127: 2D heat 127x127, nt=500, 400 sensors every step, sigma=1e-3, "
-                                   "prior (I-0.05 Lap)^-2, k=100", "l2": "n/a (host)"},
+            "config": {"workload": heat2d_workload(spec.nt), "k": 100,
+                       "step": "single-vector Hessian applies (the operation the matvec/s counts)",
+                       "l2": "n/a (host)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{per_step} single-vector Htilde applies per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -569,8 +576,7 @@ def main():
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32/f64" if precision == lrp.LRP_MIXED else "f64",
         "data": "synthetic",
-        "config": {"workload": f"heat2d_127: 2D heat eq 127x127 interior (nx=16129), nt={spec.nt}, 400 uniform "
-                               "sensors at every step, sigma=1e-3, prior (I-0.05 Lap)^-2",
+        "config": {"workload": heat2d_workload(spec.nt),
                    "step": ("block Lanczos to rank k + posterior factors + one query + the posterior mean's "
                             "trajectory in low-rank-in-time form" if args.mode == "posterior"
                             else "one Hessian apply to a block of columns"),
