@@ -22,18 +22,49 @@ from __future__ import annotations
 
 import numpy as np
 import scipy.sparse as sp
-from scipy.sparse.linalg import splu
+from scipy.sparse.linalg import cg, splu
 
 from .operators import laplacian, shifted
 from .observe import observation_matrix, observed_steps
 
 
+class _CGSolver:
+    """x = A^{-1} b for a symmetric positive definite sparse A by conjugate
+    gradients with the Jacobi preconditioner, to a relative residual of
+    1e-14, column by column (a plain library step in place of a sparse LU
+    whose fill-in is prohibitive on 3D grids of 63^3 nodes). Both operators
+    solved here, I + tau L and I + alpha L0, are symmetric (L is in flux
+    form), so the transposed solve is the same solve."""
+
+    RTOL = 1e-14
+
+    def __init__(self, A):
+        self.A = sp.csr_matrix(A)
+        self.M = sp.diags(1.0 / self.A.diagonal())
+
+    def solve(self, B, trans="N"):
+        B = np.asarray(B, dtype=np.float64)
+        cols = B.reshape(B.shape[0], -1)
+        out = np.empty_like(cols)
+        for j in range(cols.shape[1]):
+            if not np.any(cols[:, j]):
+                out[:, j] = 0.0
+                continue
+            x, info = cg(self.A, cols[:, j], rtol=self.RTOL, atol=0.0, M=self.M, maxiter=100000)
+            if info != 0:
+                raise RuntimeError(f"oracle CG did not reach {self.RTOL} (info {info})")
+            out[:, j] = x
+        return out.reshape(B.shape)
+
+
 class Problem:
     """All operators of one inverse problem. ``spec`` is any object with the
     attributes of ``synth.ProblemSpec`` (dim, n, nt, T, prior_alpha, sigma,
-    obs_every, sensors, kappa)."""
+    obs_every, sensors, kappa). ``solver``: "lu" (sparse LU factors of
+    I + tau L and I + alpha L0, the default) or "cg" (conjugate gradients to
+    a relative residual of 1e-14, for grids too large to factor)."""
 
-    def __init__(self, spec):
+    def __init__(self, spec, solver: str = "lu"):
         self.spec = spec
         self.dim = int(spec.dim)
         self.n = int(spec.n)
@@ -46,8 +77,14 @@ class Problem:
         self.L0 = laplacian(self.n, self.dim, None)
         self.R = shifted(self.L0, self.alpha)
         self.K = shifted(self.L, self.tau)
-        self._R_lu = splu(self.R)
-        self._K_lu = splu(self.K)
+        if solver == "lu":
+            self._R_lu = splu(self.R)
+            self._K_lu = splu(self.K)
+        elif solver == "cg":
+            self._R_lu = _CGSolver(self.R)
+            self._K_lu = _CGSolver(self.K)
+        else:
+            raise ValueError(solver)
         self.B = observation_matrix(self.n, self.dim, spec.sensors)
         self.n_obs = self.B.shape[0]
         self.steps = observed_steps(self.nt, int(spec.obs_every))

@@ -242,6 +242,22 @@ def test_arnoldi_matches_dense():
         assert np.linalg.norm(r) < 1e-8 * lam[0]
 
 
+def test_eigsh_top_matches_dense():
+    """The matrix-free ARPACK cross-check returns the leading eigenpairs of the
+    explicit Htilde (the check of Sec. 6.1 against a dense eigensolver):
+    eigenvalues to 1e-10 lam_1, eigenvectors of simple eigenvalues up to sign.
+    Catches a wrong ordering, the wrong end of the spectrum or a reshaped
+    operand."""
+    P = Problem(_spec(n=7, nt=12, obs_every=3, sensors=synth.uniform_sensors(6, 2, 5)))
+    lam, V = spectrum.eig_dense(P.hessian_explicit())
+    got, W = spectrum.eigsh_top(P.hessian_apply, P.nx, 6, tol=1e-13)
+    assert np.all(np.diff(got) <= 0)
+    assert np.max(np.abs(got - lam[:6])) <= 1e-10 * lam[0]
+    for i in range(6):
+        if min(abs(lam[i] - lam[j]) for j in range(7) if j != i) > 1e-6 * lam[0]:
+            assert abs(abs(W[:, i] @ V[:, i]) - 1.0) < 1e-8
+
+
 # ---------------------------------------------------------------- posterior
 def _tiny_problem():
     return Problem(_spec(n=5, nt=8, obs_every=2, sensors=synth.uniform_sensors(5, 2, 21),
@@ -358,3 +374,64 @@ def test_streaming_trajectory_error_bound():
     assert np.linalg.norm(Y - W @ V.T) <= tol * np.linalg.norm(Y)
     Wo, Vo, _ = timefactors.truncate(Y, tol, 40)
     assert Wo.shape[1] <= W.shape[1] <= Wo.shape[1] + 6
+
+
+@pytest.mark.parametrize("k", [None, 6])
+def test_sigma_override_equals_problem_at_that_sigma(k):
+    """Gamma_noise = sigma^2 I (Sec. 2): the posterior queries of a problem
+    set up at sigma0 and asked at sigma (eigenvalues rescaled by
+    sigma0^2/sigma^2, data weighted by 1/sigma^2) equal those of the same
+    problem set up at sigma with its own eigenpairs. k = None uses every
+    eigenpair (then the mean is also the exact posterior mean at sigma);
+    k = 6 sits at a spectral gap (lam_6 / lam_7 ~ 100), so the rank-k projector is unique. Catches a
+    swapped sigma0/sigma in the rescaling or the data weighted at sigma0."""
+    s0, s1 = 0.02, 0.005
+    sens = synth.uniform_sensors(5, 2, 21)
+    P0 = Problem(_spec(n=5, nt=8, obs_every=2, sensors=sens, sigma=s0, prior_alpha=0.05))
+    P1 = Problem(_spec(n=5, nt=8, obs_every=2, sensors=sens, sigma=s1, prior_alpha=0.05))
+    l0, V0 = spectrum.eig_dense(P0.hessian_explicit())
+    l1, V1 = spectrum.eig_dense(P1.hessian_explicit())
+    if k is not None:
+        assert l0[k - 1] > 10 * l0[k]
+        l0, V0, l1, V1 = l0[:k], V0[:, :k], l1[:k], V1[:, :k]
+    np.testing.assert_allclose(posterior.rescale_eigs(l0, s0, s1), l1, rtol=1e-9, atol=1e-12 * l1[0])
+    y = synth.normal_block(P0.n_data, 1, 4)[:, 0]
+    m0 = posterior.mean_lowrank(P0, l0, V0, y, sigma=s1)
+    m1 = posterior.mean_lowrank(P1, l1, V1, y)
+    np.testing.assert_allclose(m0, m1, rtol=0, atol=1e-9 * np.abs(m1).max())
+    if k is None:
+        me = posterior.mean_exact(P1, y)
+        np.testing.assert_allclose(m0, me, rtol=0, atol=1e-8 * np.abs(me).max())
+    nodes = np.array([0, 6, 12, 18, 24])
+    v0 = posterior.variance_lowrank(P0, l0, V0, nodes, sigma=s1)
+    v1 = posterior.variance_lowrank(P1, l1, V1, nodes)
+    np.testing.assert_allclose(v0, v1, rtol=1e-9)
+    # samples: the maps xi -> sample agree through their covariance (the
+    # eigenvector bases differ by rotations inside degenerate spaces)
+    E = np.eye(P0.nx)
+    S0 = posterior.samples_lowrank(P0, l0, V0, np.zeros(P0.nx), E, sigma=s1)
+    S1 = posterior.samples_lowrank(P1, l1, V1, np.zeros(P1.nx), E)
+    np.testing.assert_allclose(S0 @ S0.T, S1 @ S1.T, rtol=0, atol=1e-9 * np.abs(S1 @ S1.T).max())
+    # and the sample map at the override is the low-rank covariance at sigma
+    C1 = posterior.post_cov_lowrank(P1, l1, V1)
+    np.testing.assert_allclose(S0 @ S0.T, C1, rtol=0, atol=1e-9 * np.abs(C1).max())
+
+
+def test_cg_solver_matches_lu():
+    """The oracle's CG solves (used where sparse LU fill-in is prohibitive)
+    reach the stated relative residual 1e-14 of the operator itself, and give
+    the same forward map, adjoint and Hessian as the LU solves on a 3D
+    problem with a variable kappa."""
+    spec = synth.small_spec(dim=3, n=7, nt=6, obs_every=2, n_obs=6, with_kappa=True, seed=12)
+    Pl, Pc = Problem(spec), Problem(spec, solver="cg")
+    b = synth.normal_block(Pl.nx, 2, 3)
+    for A, solver in ((Pl.K, Pc._K_lu), (Pl.R, Pc._R_lu)):
+        x = solver.solve(b)
+        assert np.max(np.linalg.norm(b - A @ x, axis=0) / np.linalg.norm(b, axis=0)) <= 2e-14
+    X = synth.normal_block(Pl.nx, 2, 5)
+    for f in ("forward", "hessian_apply"):
+        want = getattr(Pl, f)(X)
+        np.testing.assert_allclose(getattr(Pc, f)(X), want, rtol=0, atol=1e-11 * np.abs(want).max())
+    W = synth.normal_block(Pl.n_data, 2, 6)
+    want = Pl.adjoint(W)
+    np.testing.assert_allclose(Pc.adjoint(W), want, rtol=0, atol=1e-11 * np.abs(want).max())
