@@ -29,7 +29,8 @@
  *  - Array arguments may be host or device pointers; the library detects
  *    which with cudaPointerGetAttributes and stages host arrays through the
  *    device. The caller owns every array it passes. Device arrays must be
- *    on the problem's device.
+ *    on the problem's device; device memory of another GPU is rejected with
+ *    LRP_EINVAL (managed memory is accepted).
  *  - All work is ordered on the problem's CUDA stream; every call returns
  *    after that work has completed (synchronous).
  *  - Errors: a call returns a status; on error the outputs are undefined and
@@ -247,7 +248,8 @@ lrp_status lrp_trajectory_factors(lrp_problem* p, int nvec, const double* U, int
  * threshold epsilon) among the k. start: optional nx x block start block
  * (host or device), NULL -> a fixed pseudo-random block.
  * The posterior keeps V_k, G = R^{-1} V_k and lambda on the device.
- * Returns LRP_ENOCONV (with a usable posterior) if the basis cap is hit. */
+ * Returns LRP_ENOCONV (with a usable posterior) if the basis cap is hit or a
+ * solve of a Hessian apply missed its tolerance within pcg_maxit. */
 lrp_status lrp_lowrank_posterior(lrp_problem* p, int k, int block, double eig_tol,
                                  double eig_threshold, int max_basis, const double* start,
                                  lrp_posterior** out, lrp_lanczos_stats* st);
@@ -288,10 +290,15 @@ lrp_status lrp_posterior_eigs(const lrp_posterior* post, int* r, double* lambda,
 /* Posterior queries (Sec. 2: posterior mean = MAP point, pointwise variance
  * diag(Gamma_post), samples u_mean + R^{-1}(I + V Lambda V^T)^{-1/2} xi),
  * with the eigenvalues rescaled to the request's sigma
- * (lambda(sigma) = lambda(sigma0) sigma0^2 / sigma^2). */
+ * (lambda(sigma) = lambda(sigma0) sigma0^2 / sigma^2). If a solve of the
+ * query misses its tolerance within pcg_maxit, the outputs are still written
+ * and the call returns LRP_ENOCONV. */
 lrp_status lrp_posterior_query(lrp_posterior* post, const lrp_query* q, lrp_query_result* r);
 
-/* Checkpoint: write / read the posterior factors and a hash of the problem. */
+/* Checkpoint: write / read the posterior factors and a hash of the problem.
+ * Save writes `path`.tmp and renames it to `path` when complete (a failed
+ * save leaves no partial file). Load rejects (LRP_EINVAL) a file of another
+ * problem, a header whose rank exceeds nx and a truncated file. */
 lrp_status lrp_posterior_save(const lrp_posterior* post, const char* path);
 lrp_status lrp_posterior_load(lrp_problem* p, const char* path, lrp_posterior** out);
 
@@ -391,7 +398,9 @@ lrp_status lrp_server_add_model(lrp_server* s, const lrp_problem_desc* d, int k,
 lrp_status lrp_server_submit(lrp_server* s, int model, const lrp_query* q, unsigned long long* ticket);
 /* Waits for a request (timeout_s <= 0: no limit; LRP_ETIMEOUT otherwise),
  * copies its results into r's HOST buffers (each may be NULL) and releases
- * the ticket. Returns the request's own status. */
+ * the ticket. Returns the request's own status; LRP_ENOCONV means a solve of
+ * the batch the request was served in missed its tolerance within pcg_maxit
+ * (every request of that batch gets it), and the results are still copied. */
 lrp_status lrp_server_wait(lrp_server* s, unsigned long long ticket, double timeout_s, lrp_query_result* r,
                            lrp_request_stats* st);
 lrp_status lrp_server_info(lrp_server* s, lrp_server_stats* out);
@@ -401,6 +410,13 @@ void lrp_server_destroy(lrp_server* s);
 /* Diagnostics: number of CUDA kernels this library has launched in this
  * process so far (all problems, all threads). */
 unsigned long long lrp_kernel_launches(void);
+
+/* Test hook (failure injection on the host, no counterpart in the paper):
+ * after `after` further successful device allocations by this library, the
+ * next one fails as if the device were out of memory (once, in any thread);
+ * after < 0 disarms it. The call that meets the failure returns LRP_ENOMEM
+ * and releases what it had allocated. */
+void lrp_debug_fail_alloc(long long after);
 
 #ifdef __cplusplus
 }

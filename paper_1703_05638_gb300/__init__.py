@@ -132,6 +132,7 @@ EXPORTS = {
     "lrp_last_error": (C.c_char_p, []),
     "lrp_version": (C.c_char_p, []),
     "lrp_kernel_launches": (C.c_ulonglong, []),
+    "lrp_debug_fail_alloc": (None, [C.c_longlong]),
     "lrp_sweep_profile": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _dp, C.POINTER(C.c_ulonglong), _dp]),
     "lrp_problem_tuning": (C.c_int, [C.c_void_p, C.POINTER(lrp_tuning)]),
     "lrp_batch_lowrank_posterior": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.c_double, C.c_int,
@@ -286,7 +287,9 @@ def _sweep(fn, prob: Problem, X, rows_in, rows_out, *extra):
     st = lrp_apply_stats()
     status = fn(prob.handle, a.ncols, C.c_void_p(a.ptr), a.ld, C.c_void_p(optr), rows_out, *extra, C.byref(st))
     _check(status, allow=(LRP_OK, LRP_ENOCONV))
-    return view(), st.as_dict()
+    d = st.as_dict()
+    d["status"] = status
+    return view(), d
 
 
 def lrp_hessian_apply(prob: Problem, X, flags: int = 0):
@@ -398,7 +401,9 @@ def lrp_lowrank_posterior(prob: Problem, k: int, block: int = 1, eig_tol: float 
                                        int(max_basis), C.c_void_p(a.ptr) if a else None, C.byref(h),
                                        C.byref(st))
     _check(status, allow=(LRP_OK, LRP_ENOCONV))
-    return Posterior(h, prob), st.as_dict()
+    d = st.as_dict()
+    d["status"] = status
+    return Posterior(h, prob), d
 
 
 def lrp_posterior_query(post: Posterior, kind: int, y_obs=None, sigma: float = 0.0, points=None, xi=None,
@@ -449,7 +454,8 @@ def lrp_posterior_query(post: Posterior, kind: int, y_obs=None, sigma: float = 0
             keep.append(x)
             q.xi, q.n_samples = x.ctypes.data, x.shape[1]
         out["samples"], res.samples = alloc((nx, q.n_samples))
-    _check(lib.lrp_posterior_query(post.handle, C.byref(q), C.byref(res)), allow=(LRP_OK, LRP_ENOCONV))
+    out["status"] = _check(lib.lrp_posterior_query(post.handle, C.byref(q), C.byref(res)),
+                           allow=(LRP_OK, LRP_ENOCONV))
     out["ms"] = res.ms
     return out
 
@@ -550,7 +556,9 @@ class Server:
         return t.value
 
     def wait(self, ticket: int, timeout: float = 0.0) -> dict:
-        kind, nx, npts, ns = self._shape.pop(ticket)
+        """Results of a request (NumPy arrays) with its stats and status
+        (LRP_OK or LRP_ENOCONV); LRP_ETIMEOUT raises and keeps the ticket."""
+        kind, nx, npts, ns = self._shape[ticket]
         res = lrp_query_result()
         out = {}
         if kind & (LRP_Q_MEAN | LRP_Q_SAMPLES):
@@ -563,8 +571,11 @@ class Server:
             out["samples"] = np.zeros((nx, ns), order="F")
             res.samples = out["samples"].ctypes.data
         st = lrp_request_stats()
-        _check(load().lrp_server_wait(self.handle, C.c_ulonglong(ticket), float(timeout), C.byref(res),
-                                      C.byref(st)))
+        status = load().lrp_server_wait(self.handle, C.c_ulonglong(ticket), float(timeout), C.byref(res),
+                                        C.byref(st))
+        if status != LRP_ETIMEOUT:
+            self._shape.pop(ticket, None)
+        out["status"] = _check(status, allow=(LRP_OK, LRP_ENOCONV))
         out["stats"] = st.as_dict()
         out["latency_ms"] = st.t_done_ms - st.t_submit_ms
         return out
@@ -605,3 +616,9 @@ def lrp_set_tuning(prob: "Problem", tuning: dict):
 
 def lrp_kernel_launches() -> int:
     return int(load().lrp_kernel_launches())
+
+
+def lrp_debug_fail_alloc(after: int):
+    """Test hook: the device allocation after `after` more successful ones
+    fails as if the device were full (once); after < 0 disarms it."""
+    load().lrp_debug_fail_alloc(int(after))

@@ -31,6 +31,25 @@ lrp_status cuda_status(cudaError_t e, const char* where) {
   return e == cudaErrorMemoryAllocation ? LRP_ENOMEM : LRP_ECUDA;
 }
 
+// Allocation-failure injection (lrp_debug_fail_alloc): when armed, the
+// allocation after `fail_after` further successful ones returns
+// cudaErrorMemoryAllocation once, as a full device would.
+static std::atomic<long long> g_fail_after{-1};
+
+cudaError_t dev_malloc_raw(void** p, size_t bytes) {
+  long long n = g_fail_after.load();
+  while (n >= 0) {
+    if (g_fail_after.compare_exchange_weak(n, n - 1)) {
+      if (n == 0) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+      }
+      break;
+    }
+  }
+  return cudaMalloc(p, bytes);
+}
+
 bool is_device_ptr(const void* p) {
   if (!p) return false;
   cudaPointerAttributes a;
@@ -41,10 +60,29 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Device arrays must live on the problem's device: the kernels read them
+// directly, and memory of another GPU without peer access would fault. NULL,
+// host and managed memory pass; device memory of another device is
+// LRP_EINVAL.
+lrp_status check_on_device(int device, const void* p, const char* what) {
+  if (!p) return LRP_OK;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return LRP_OK;
+  }
+  if (a.type == cudaMemoryTypeDevice && a.device != device) {
+    set_error(std::string(what) + ": device array on device " + std::to_string(a.device) +
+              ", the problem is on device " + std::to_string(device));
+    return LRP_EINVAL;
+  }
+  return LRP_OK;
+}
+
 template <typename T>
 static lrp_status dev_alloc(lrp_problem* P, T** out, size_t count) {
   void* p = nullptr;
-  cudaError_t e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
+  cudaError_t e = lrp::dev_malloc(&p, std::max<size_t>(count, 1) * sizeof(T));
   if (e != cudaSuccess) return cuda_status(e, "cudaMalloc");
   P->allocs.push_back(p);
   P->dev_bytes += std::max<size_t>(count, 1) * sizeof(T);
@@ -72,7 +110,7 @@ lrp_status ensure_workspace(lrp_problem* P, size_t bytes) {
     P->ws_bytes = 0;
   }
   size_t want = bytes + bytes / 8;
-  cudaError_t e = cudaMalloc((void**)&P->ws, want);
+  cudaError_t e = lrp::dev_malloc((void**)&P->ws, want);
   if (e != cudaSuccess) return cuda_status(e, "workspace cudaMalloc");
   P->ws_bytes = want;
   if (P->poison) cudaMemset(P->ws, P->poison & 0xFF, want);  // 0xFF bytes: NaN in FP32 and FP64
@@ -147,6 +185,8 @@ const char* lrp_last_error(void) { return g_err.c_str(); }
 const char* lrp_version(void) { return "lrpost-gb300 0.1"; }
 
 unsigned long long lrp_kernel_launches(void) { return g_launches.load(); }
+
+void lrp_debug_fail_alloc(long long after) { lrp::g_fail_after.store(after < 0 ? -1 : after); }
 
 lrp_status lrp_setup_problem(const lrp_problem_desc* desc, void* cuda_stream, lrp_problem** out) {
   if (!desc || !out) {
@@ -501,7 +541,7 @@ static lrp_status stage_in(lrp_problem* P, const double* src, int rows, int cols
     *dld = ld;
     return LRP_OK;
   }
-  cudaError_t e = cudaMalloc(&st.tmp, (size_t)rows * cols * sizeof(double) + 8);
+  cudaError_t e = lrp::dev_malloc(&st.tmp, (size_t)rows * cols * sizeof(double) + 8);
   if (e != cudaSuccess) return cuda_status(e, "staging cudaMalloc");
   e = cudaMemcpy2DAsync(st.tmp, (size_t)rows * sizeof(double), src, (size_t)ld * sizeof(double),
                         (size_t)rows * sizeof(double), cols, cudaMemcpyHostToDevice, P->stream);
@@ -519,7 +559,7 @@ static lrp_status stage_out_alloc(lrp_problem* P, double* dst, int rows, int col
     *dld = ld;
     return LRP_OK;
   }
-  cudaError_t e = cudaMalloc(&st.tmp, (size_t)rows * cols * sizeof(double) + 8);
+  cudaError_t e = lrp::dev_malloc(&st.tmp, (size_t)rows * cols * sizeof(double) + 8);
   if (e != cudaSuccess) return cuda_status(e, "staging cudaMalloc");
   *dev = (double*)st.tmp;
   *dld = rows;
@@ -547,6 +587,9 @@ static lrp_status check_common(lrp_problem* P, int nvec, int ld_in, int rows_in,
     set_error("invalid nvec or leading dimension");
     return LRP_EINVAL;
   }
+  lrp_status s = check_on_device(P->device, in, "input");
+  if (s == LRP_OK) s = check_on_device(P->device, out, "output");
+  if (s != LRP_OK) return s;
   cudaSetDevice(P->device);
   return LRP_OK;
 }
@@ -622,8 +665,8 @@ lrp_status lrp_autotune(lrp_problem* P, int nvec, int steps, double* best_ms) {
   if (steps < 1) steps = 16;
   steps = std::min(steps, P->nt);
   double *X = nullptr, *Y = nullptr;
-  cudaError_t e = cudaMalloc(&X, (size_t)P->nx * nvec * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&Y, (size_t)P->nx * nvec * sizeof(double));
+  cudaError_t e = lrp::dev_malloc(&X, (size_t)P->nx * nvec * sizeof(double));
+  if (e == cudaSuccess) e = lrp::dev_malloc(&Y, (size_t)P->nx * nvec * sizeof(double));
   if (e == cudaSuccess) e = fill_random(P->stream, P->nx, nvec, X, P->nx, nullptr, 0xA070ull);
   if (e != cudaSuccess) {
     cudaFree(X);

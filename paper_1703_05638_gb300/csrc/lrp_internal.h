@@ -212,6 +212,14 @@ void note_launch(unsigned n = 1);
 void set_error(const std::string& msg);
 lrp_status cuda_status(cudaError_t e, const char* where);
 bool is_device_ptr(const void* p);
+// Every device allocation of the library goes through here (cudaMalloc, plus
+// the failure injection of lrp_debug_fail_alloc).
+cudaError_t dev_malloc_raw(void** p, size_t bytes);
+template <class T>
+inline cudaError_t dev_malloc(T** p, size_t bytes) {
+  return dev_malloc_raw((void**)p, bytes);
+}
+lrp_status check_on_device(int device, const void* p, const char* what);
 
 // sweep launcher (lrp_sweep.cu)
 struct SweepLaunch {

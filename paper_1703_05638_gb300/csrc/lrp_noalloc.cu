@@ -74,6 +74,11 @@ extern "C" lrp_status lrp_hessian_apply_noalloc(lrp_problem* P, int nvec, const 
     set_error("lrp_hessian_apply_noalloc: X and Y must be device arrays");
     return LRP_EINVAL;
   }
+  {
+    lrp_status sd = check_on_device(P->device, X, "lrp_hessian_apply_noalloc X");
+    if (sd == LRP_OK) sd = check_on_device(P->device, Y, "lrp_hessian_apply_noalloc Y");
+    if (sd != LRP_OK) return sd;
+  }
   auto t0 = std::chrono::steady_clock::now();
   cudaError_t e = cudaSetDevice(P->device);
   if (e != cudaSuccess) return cuda_status(e, "cudaSetDevice");

@@ -13,6 +13,7 @@
 #include <cstring>
 #include <memory>
 #include <string>
+#include <new>
 #include <vector>
 
 #include "lrp_dense.h"
@@ -38,7 +39,7 @@ struct DArr {
     if (p) cudaFree(p);
     p = nullptr;
     n = count;
-    return cudaMalloc((void**)&p, std::max<size_t>(count, 1) * sizeof(T));
+    return lrp::dev_malloc((void**)&p, std::max<size_t>(count, 1) * sizeof(T));
   }
   T* release() {
     T* r = p;
@@ -92,6 +93,7 @@ static lrp_status block_orth(lrp_problem* P, int nx, int nb, double* Wn, const d
 struct LanczosRun {
   lrp_problem* P = nullptr;
   int k = 0, nb = 0, nx = 0, mmax = 0;
+  bool apply_noconv = false;  // a solve of some Hessian apply missed its tolerance
   double eig_tol = 1e-6, eig_threshold = 0.0;
   DArr<double> Q, W, T, Tw, Z, theta, work, resid;
   DArr<int> estat;
@@ -239,6 +241,7 @@ struct LanczosRun {
     ++n_iter;
     lrp_status st = sweep_status(*h_stats, info, nullptr, 0.0);
     if (st != LRP_OK && st != LRP_ENOCONV) return st;
+    if (st == LRP_ENOCONV) apply_noconv = true;
     if (check) {
       const double th0 = std::max(h_theta[0], 1e-300);
       if (std::getenv("LRP_VERBOSE")) {
@@ -316,6 +319,10 @@ struct LanczosRun {
       set_error("Lanczos reached its basis cap before all Ritz pairs converged");
       return LRP_ENOCONV;
     }
+    if (apply_noconv) {
+      set_error("a solve of a Hessian apply missed its tolerance within pcg_maxit");
+      return LRP_ENOCONV;
+    }
     return LRP_OK;
   }
 };
@@ -334,8 +341,10 @@ lrp_status lrp_lowrank_posterior(lrp_problem* P, int k, int block, double eig_to
     return LRP_EINVAL;
   }
   *out = nullptr;
+  lrp_status st = check_on_device(P->device, start, "lrp_lowrank_posterior start");
+  if (st != LRP_OK) return st;
   LanczosRun run;
-  lrp_status st = run.init(P, k, block, eig_tol, eig_threshold, max_basis, start);
+  st = run.init(P, k, block, eig_tol, eig_threshold, max_basis, start);
   if (st != LRP_OK) return st;
   while (!run.done) {
     st = run.enqueue_step();
@@ -516,6 +525,10 @@ lrp_status lrp_posterior_eigs(const lrp_posterior* post, int* r, double* lambda,
     set_error("NULL argument");
     return LRP_EINVAL;
   }
+  {
+    lrp_status sd = check_on_device(post->prob->device, V, "lrp_posterior_eigs V");
+    if (sd != LRP_OK) return sd;
+  }
   *r = post->k;
   if (lambda) std::memcpy(lambda, post->lambda_host.data(), post->k * sizeof(double));
   if (V && post->k > 0) {
@@ -537,6 +550,11 @@ lrp_status lrp_posterior_query(lrp_posterior* post, const lrp_query* q, lrp_quer
     return LRP_EINVAL;
   }
   lrp_problem* P = post->prob;
+  for (const void* a : {(const void*)q->y_obs, (const void*)q->points, (const void*)q->xi, (const void*)r->mean,
+                        (const void*)r->variance, (const void*)r->samples}) {
+    lrp_status sd = check_on_device(P->device, a, "lrp_posterior_query");
+    if (sd != LRP_OK) return sd;
+  }
   cudaSetDevice(P->device);
   cudaStream_t s = P->stream;
   auto t0 = std::chrono::steady_clock::now();
@@ -545,6 +563,9 @@ lrp_status lrp_posterior_query(lrp_posterior* post, const lrp_query* q, lrp_quer
   const double lam_scale = (post->sigma0 * post->sigma0) / (sigma * sigma);
   const bool want_mean = (q->kind & (LRP_Q_MEAN | LRP_Q_SAMPLES)) != 0;
   lrp_status st;
+  // a sweep whose solves miss their tolerance still fills its output: the
+  // query completes and reports LRP_ENOCONV at the end
+  lrp_status result = LRP_OK;
   DArr<double> mean, tmp, coef;
   if (want_mean) {
     if (!q->y_obs) {
@@ -562,6 +583,7 @@ lrp_status lrp_posterior_query(lrp_posterior* post, const lrp_query* q, lrp_quer
     st = run_sweep(P, ST_LOAD_D | ST_ADJOINT | ST_PRIOR_OUT | ST_STORE_Y, 1, nullptr, 0, tmp.p, nx, y.p,
                    P->n_data, nullptr, 0, nullptr, false);
     if (st != LRP_OK && st != LRP_ENOCONV) return st;
+    if (st == LRP_ENOCONV) result = LRP_ENOCONV;
     // z <- z - V (d .* V^T z)
     if (k > 0) {
       CK(coef.alloc(k));
@@ -574,6 +596,7 @@ lrp_status lrp_posterior_query(lrp_posterior* post, const lrp_query* q, lrp_quer
     st = run_sweep(P, ST_LOAD_X | ST_PRIOR_IN | ST_STORE_Y, 1, tmp.p, nx, mean.p, nx, nullptr, 0, nullptr, 0,
                    nullptr, false);
     if (st != LRP_OK && st != LRP_ENOCONV) return st;
+    if (st == LRP_ENOCONV) result = LRP_ENOCONV;
     if (r->mean) {
       const cudaMemcpyKind k2 = is_device_ptr(r->mean) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
       CK(cudaMemcpyAsync(r->mean, mean.p, nx * sizeof(double), k2, s));
@@ -605,7 +628,7 @@ lrp_status lrp_posterior_query(lrp_posterior* post, const lrp_query* q, lrp_quer
       // per posterior
       if (post->diag) cudaFree(post->diag);
       post->diag = nullptr;
-      CK(cudaMalloc(&post->diag, (size_t)nx * sizeof(double)));
+      CK(lrp::dev_malloc(&post->diag, (size_t)nx * sizeof(double)));
       post->diag_cap = nx;
       DArr<double> dwork;
       CK(dwork.alloc((size_t)P->n * P->n + 2 * (size_t)nx));
@@ -644,13 +667,15 @@ lrp_status lrp_posterior_query(lrp_posterior* post, const lrp_query* q, lrp_quer
     st = run_sweep(P, ST_LOAD_X | ST_PRIOR_IN | ST_STORE_Y, ns, Xi.p, nx, Sm.p, nx, nullptr, 0, nullptr, 0,
                    nullptr, false);
     if (st != LRP_OK && st != LRP_ENOCONV) return st;
+    if (st == LRP_ENOCONV) result = LRP_ENOCONV;
     CK(add_vec_cols(s, nx, ns, mean.p, Sm.p, nx));
     const cudaMemcpyKind k2 = is_device_ptr(r->samples) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     CK(cudaMemcpyAsync(r->samples, Sm.p, (size_t)nx * ns * sizeof(double), k2, s));
   }
   CK(cudaStreamSynchronize(s));
   r->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-  return LRP_OK;
+  if (result == LRP_ENOCONV) set_error("query: a solve missed its tolerance within pcg_maxit");
+  return result;
 }
 
 lrp_status lrp_posterior_save(const lrp_posterior* post, const char* path) {
@@ -658,20 +683,27 @@ lrp_status lrp_posterior_save(const lrp_posterior* post, const char* path) {
     set_error("NULL argument");
     return LRP_EINVAL;
   }
-  FILE* f = std::fopen(path, "wb");
-  if (!f) {
-    set_error(std::string("cannot open ") + path);
-    return LRP_EINVAL;
-  }
   const size_t nx = post->nx, k = post->k;
-  std::vector<double> V(nx * k), G(nx * k);
+  std::vector<double> V, G;
+  try {
+    V.resize(nx * k);
+    G.resize(nx * k);
+  } catch (const std::bad_alloc&) {
+    set_error("posterior_save: host allocation failed");
+    return LRP_ENOMEM;
+  }
   if (k) {
     cudaError_t e = cudaMemcpy(V.data(), post->V, V.size() * sizeof(double), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(G.data(), post->G, G.size() * sizeof(double), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) {
-      std::fclose(f);
-      return cuda_status(e, "posterior_save");
-    }
+    if (e != cudaSuccess) return cuda_status(e, "posterior_save");
+  }
+  // written to a temporary name and renamed at the end: a failed save leaves
+  // no partial checkpoint under `path`
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE* f = std::fopen(tmp.c_str(), "wb");
+  if (!f) {
+    set_error(std::string("cannot open ") + tmp);
+    return LRP_EINVAL;
   }
   const char magic[8] = {'L', 'R', 'P', 'O', 'S', 'T', '0', '1'};
   const uint64_t hdr[3] = {post->prob->hash, (uint64_t)nx, (uint64_t)k};
@@ -681,7 +713,8 @@ lrp_status lrp_posterior_save(const lrp_posterior* post, const char* path) {
             std::fwrite(V.data(), sizeof(double), V.size(), f) == V.size() &&
             std::fwrite(G.data(), sizeof(double), G.size(), f) == G.size();
   ok = (std::fclose(f) == 0) && ok;
-  if (!ok) {
+  if (!ok || std::rename(tmp.c_str(), path) != 0) {
+    std::remove(tmp.c_str());
     set_error("write failed");
     return LRP_EINVAL;
   }
@@ -709,8 +742,24 @@ lrp_status lrp_posterior_load(lrp_problem* P, const char* path, lrp_posterior** 
     set_error("checkpoint does not match this problem");
     return LRP_EINVAL;
   }
+  // the rank can be at most nx: a larger value is a corrupt header, rejected
+  // before anything is sized from it
+  if (hdr[2] > hdr[1]) {
+    std::fclose(f);
+    set_error("corrupt checkpoint header (rank > nx)");
+    return LRP_EINVAL;
+  }
   const size_t nx = hdr[1], k = hdr[2];
-  std::vector<double> lam(k), V(nx * k), G(nx * k);
+  std::vector<double> lam, V, G;
+  try {
+    lam.resize(k);
+    V.resize(nx * k);
+    G.resize(nx * k);
+  } catch (const std::bad_alloc&) {
+    std::fclose(f);
+    set_error("posterior_load: host allocation failed");
+    return LRP_ENOMEM;
+  }
   ok = std::fread(lam.data(), sizeof(double), k, f) == k && std::fread(V.data(), sizeof(double), V.size(), f) == V.size() &&
        std::fread(G.data(), sizeof(double), G.size(), f) == G.size();
   std::fclose(f);
@@ -728,9 +777,9 @@ lrp_status lrp_posterior_load(lrp_problem* P, const char* path, lrp_posterior** 
   post->diag = nullptr;
   post->diag_cap = 0;
   post->V = post->G = post->lambda = nullptr;
-  cudaError_t e = cudaMalloc(&post->V, std::max<size_t>(1, V.size()) * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&post->G, std::max<size_t>(1, G.size()) * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&post->lambda, std::max<size_t>(1, k) * sizeof(double));
+  cudaError_t e = lrp::dev_malloc(&post->V, std::max<size_t>(1, V.size()) * sizeof(double));
+  if (e == cudaSuccess) e = lrp::dev_malloc(&post->G, std::max<size_t>(1, G.size()) * sizeof(double));
+  if (e == cudaSuccess) e = lrp::dev_malloc(&post->lambda, std::max<size_t>(1, k) * sizeof(double));
   if (e == cudaSuccess && k) {
     e = cudaMemcpy(post->V, V.data(), V.size() * sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(post->G, G.data(), G.size() * sizeof(double), cudaMemcpyHostToDevice);

@@ -141,7 +141,7 @@ struct SlotModel {
   }
   template <typename T>
   cudaError_t dalloc(T** p, size_t n) {
-    cudaError_t e = cudaMalloc((void**)p, std::max<size_t>(n, 1) * sizeof(T));
+    cudaError_t e = lrp::dev_malloc((void**)p, std::max<size_t>(n, 1) * sizeof(T));
     if (e == cudaSuccess) {
       dev.push_back(*p);
       bytes += std::max<size_t>(n, 1) * sizeof(T);
@@ -322,10 +322,14 @@ lrp_status serve_batch(lrp_server* S, int w, Model& m, SlotModel& h, std::vector
     cudaError_t e_ = (x);                                     \
     if (e_ != cudaSuccess) return cuda_status(e_, #x);        \
   } while (0)
+  // a sweep whose solves miss their tolerance still fills its output: the
+  // batch completes and every request of it reports LRP_ENOCONV
+  bool noconv = false;
 #define SS(x)                                                 \
   do {                                                        \
     lrp_status s_ = (x);                                      \
     if (s_ != LRP_OK && s_ != LRP_ENOCONV) return s_;         \
+    if (s_ == LRP_ENOCONV) noconv = true;                     \
   } while (0)
   // column layout of zx/out: [0, R) mean columns, [R, R+NSt) sample columns
   int NSt = 0;
@@ -436,6 +440,10 @@ lrp_status serve_batch(lrp_server* S, int w, Model& m, SlotModel& h, std::vector
   }
 #undef SK
 #undef SS
+  if (noconv) {
+    set_error("a solve of this batch missed its tolerance within pcg_maxit");
+    return LRP_ENOCONV;
+  }
   return LRP_OK;
 }
 
@@ -493,10 +501,10 @@ void worker_main(lrp_server* S, int w) {
       admitted = 1;
       const size_t vk = (size_t)m->nx * m->k * sizeof(double);
       double *dV = nullptr, *dG = nullptr, *dl = nullptr, *dd = nullptr;
-      cudaError_t e = cudaMalloc(&dV, std::max<size_t>(vk, 8));
-      if (e == cudaSuccess) e = cudaMalloc(&dG, std::max<size_t>(vk, 8));
-      if (e == cudaSuccess) e = cudaMalloc(&dl, std::max(m->k, 1) * sizeof(double));
-      if (e == cudaSuccess) e = cudaMalloc(&dd, (size_t)m->nx * sizeof(double));
+      cudaError_t e = lrp::dev_malloc(&dV, std::max<size_t>(vk, 8));
+      if (e == cudaSuccess) e = lrp::dev_malloc(&dG, std::max<size_t>(vk, 8));
+      if (e == cudaSuccess) e = lrp::dev_malloc(&dl, std::max(m->k, 1) * sizeof(double));
+      if (e == cudaSuccess) e = lrp::dev_malloc(&dd, (size_t)m->nx * sizeof(double));
       if (e == cudaSuccess) e = cudaMemcpyAsync(dV, m->h_V, vk, cudaMemcpyHostToDevice, S->streams[w]);
       if (e == cudaSuccess) e = cudaMemcpyAsync(dG, m->h_G, vk, cudaMemcpyHostToDevice, S->streams[w]);
       if (e == cudaSuccess)
@@ -676,7 +684,7 @@ lrp_status lrp_server_add_model(lrp_server* S, const lrp_problem_desc* d, int k,
   if (e == cudaSuccess) {
     double* dwork = nullptr;
     const size_t nwork = (size_t)d->n * d->n + 3 * (size_t)m->nx;
-    e = cudaMalloc(&dwork, nwork * sizeof(double));
+    e = lrp::dev_malloc(&dwork, nwork * sizeof(double));
     if (e == cudaSuccess) e = prior_diag_dst(s, dim, d->n, d->prior_alpha, dwork + nwork - m->nx, dwork);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(m->h_diag, dwork + nwork - m->nx, (size_t)m->nx * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -821,10 +829,13 @@ lrp_status lrp_server_wait(lrp_server* S, unsigned long long ticket, double time
   S->reqs.erase(it);
   lk.unlock();
   if (st) *st = own->st;
-  if (own->status != LRP_OK) {
+  if (own->status != LRP_OK && own->status != LRP_ENOCONV) {
     set_error(own->err);
     return own->status;
   }
+  // LRP_ENOCONV: the results are filled (a solve of the request's batch
+  // missed its tolerance); they are copied out and the status returned
+  if (own->status == LRP_ENOCONV) set_error(own->err);
   if (res) {
     if (res->mean && !own->mean.empty()) std::memcpy(res->mean, own->mean.data(), own->mean.size() * sizeof(double));
     if (res->variance && !own->var.empty())
@@ -833,7 +844,7 @@ lrp_status lrp_server_wait(lrp_server* S, unsigned long long ticket, double time
       std::memcpy(res->samples, own->samples.data(), own->samples.size() * sizeof(double));
     res->ms = own->st.t_done_ms - own->st.t_submit_ms;
   }
-  return LRP_OK;
+  return own->status;
 }
 
 lrp_status lrp_server_info(lrp_server* S, lrp_server_stats* out) {

@@ -264,7 +264,7 @@ lrp_status sweep_enqueue(lrp_problem* Pr, unsigned stages, int nvec, const doubl
   if (Pr->prof_on) cudaEventRecord(Pr->prof_ev[0], Pr->stream);
 #ifdef LRP_SECTION_TIMERS
   static unsigned long long* sec_buf = nullptr;
-  if (!sec_buf) cudaMalloc(&sec_buf, 8 * sizeof(unsigned long long));
+  if (!sec_buf) lrp::dev_malloc(&sec_buf, 8 * sizeof(unsigned long long));
   cudaMemsetAsync(sec_buf, 0, 8 * sizeof(unsigned long long), Pr->stream);
   prm.section_cycles = sec_buf;
 #endif

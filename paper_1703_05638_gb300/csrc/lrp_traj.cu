@@ -179,7 +179,7 @@ struct DBuf {
   ~DBuf() {
     if (p) cudaFree(p);
   }
-  cudaError_t alloc(size_t n) { return cudaMalloc((void**)&p, std::max<size_t>(n, 1) * sizeof(double)); }
+  cudaError_t alloc(size_t n) { return lrp::dev_malloc((void**)&p, std::max<size_t>(n, 1) * sizeof(double)); }
 };
 
 // Factor state of one column: Y_absorbed ~ Qw diag(sig) V^T.
@@ -394,7 +394,7 @@ lrp_status trajectory_factors_impl(lrp_problem* P, int nvec, const double* U, in
   CKT(ws.th.alloc((size_t)nvec * 2 * M));
   CKT(ws.gs.alloc(block_gs_scratch_doubles()));
   CKT(ws.sig.alloc((size_t)nvec * rmax));
-  CKT(cudaMalloc(&ws.iarr, 2 * nvec * sizeof(int)));
+  CKT(lrp::dev_malloc(&ws.iarr, 2 * nvec * sizeof(int)));
   lrp_apply_stats acc;
   std::memset(&acc, 0, sizeof(acc));
   lrp_status result = LRP_OK;
@@ -517,14 +517,18 @@ extern "C" lrp_status lrp_trajectory_factors(lrp_problem* P, int nvec, const dou
     return LRP_EINVAL;
   }
   if (nvec == 0) return LRP_OK;
+  for (const void* a : {(const void*)U, (const void*)W, (const void*)V}) {
+    lrp_status sd = check_on_device(P->device, a, "lrp_trajectory_factors");
+    if (sd != LRP_OK) return sd;
+  }
   cudaSetDevice(P->device);
   if (!is_device_ptr(U) || !is_device_ptr(W) || !is_device_ptr(V)) {
     // stage through the device
     const size_t nx = P->nx, nt = P->nt, rmax = P->desc.time_rank_max;
     double *dU = nullptr, *dW = nullptr, *dV = nullptr;
-    cudaError_t e = cudaMalloc(&dU, nx * nvec * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&dW, nx * rmax * nvec * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&dV, nt * rmax * nvec * sizeof(double));
+    cudaError_t e = lrp::dev_malloc(&dU, nx * nvec * sizeof(double));
+    if (e == cudaSuccess) e = lrp::dev_malloc(&dW, nx * rmax * nvec * sizeof(double));
+    if (e == cudaSuccess) e = lrp::dev_malloc(&dV, nt * rmax * nvec * sizeof(double));
     if (e != cudaSuccess) {
       cudaFree(dU);
       cudaFree(dW);

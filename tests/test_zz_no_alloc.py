@@ -36,6 +36,24 @@ def test_noalloc_matches_hessian_apply(precision, tol):
         assert err < tol, (err, st)
 
 
+def test_noalloc_band_kernel():
+    """A 2D problem with kappa = 1 in the mixed path and one column per
+    cluster runs the shared-memory band kernel; on the fixed workspace it
+    gives the same result as the ordinary apply, call after call."""
+    spec = synth.small_spec(dim=2, n=63, nt=12, obs_every=2, n_obs=10, seed=19)
+    G = lrp.lrp_setup_problem(spec, precision=1, team_ctas=4, team_cols=1)
+    X = torch.from_numpy(synth.normal_block(G.nx, 3, 7)).cuda()
+    ref, _ = lrp.lrp_hessian_apply(G, X)
+    assert lrp.lrp_problem_tuning(G)["last_kernel"] == 2
+    ref = ref.cpu().numpy()
+    scale = np.abs(ref).max()
+    for _ in range(2):
+        Y, st = lrp.lrp_hessian_apply_noalloc(G, X)
+        assert lrp.lrp_problem_tuning(G)["last_kernel"] == 2
+        err = np.abs(Y.cpu().numpy() - ref).max() / scale
+        assert err < 1e-6, (err, st)
+
+
 def test_noalloc_rejects_host_arrays_and_oversize():
     spec = synth.small_spec(dim=2, n=15, nt=8, obs_every=2, n_obs=4, seed=2)
     G = lrp.lrp_setup_problem(spec, precision=1)
