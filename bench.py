@@ -42,10 +42,17 @@ METRIC = "Hessian matvecs/s (s to rank-k Gamma_post at 1e-6 rel. Ritz residual r
 UNIT = "matvec/s"
 
 
-def heat2d_workload(nt: int) -> str:
-    """The workload name both arms report."""
+def workload_name(name: str, nt: int) -> str:
+    """The workload description both arms report."""
+    if name == "heat3d_63":
+        return (f"heat3d_63: 3D heat eq 63^3 interior (nx=250047), kappa=exp(g) field, nt={nt}, 400 uniform "
+                "sensors every 10th step, sigma=1e-3, prior (I-0.05 Lap)^-2")
     return (f"heat2d_127: 2D heat eq 127x127 interior (nx=16129), nt={nt}, 400 uniform sensors at every step, "
             "sigma=1e-3, prior (I-0.05 Lap)^-2")
+
+
+# rank and Lanczos block per workload (the benchmark configurations)
+WORKLOAD_DEFAULTS = {"heat2d_127": (100, 32), "heat3d_63": (200, 16)}
 # The two sweep kernels, the sources their device code comes from, and the
 # committed ncu summary (DRAM traffic per launch) for this workload.
 KERNELS = {
@@ -56,8 +63,8 @@ KERNELS = {
 }
 
 
-def profile_summary(name: str) -> str:
-    return os.path.join(ROOT, "profiles", f"{name}_heat2d_127.json")
+def profile_summary(name: str, workload: str = "heat2d_127") -> str:
+    return os.path.join(ROOT, "profiles", f"{name}_{workload}.json")
 
 
 def kernel_hash(sources) -> str:
@@ -139,23 +146,130 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(seconds: float = 15.0):
-    """The FP64 oracle (SciPy sparse LU per operator, single-threaded
-    triangular solves) applying Htilde to single vectors on this host."""
+# ---------------------------------------------------------------- the oracle on the host cores
+# One process per host core, each holding its own oracle problem (sparse LU
+# factors for 2D, CG solves for the 3D grid whose LU fill-in is prohibitive),
+# applying Htilde to its own columns: a block of `cores` columns per round.
+# On the 3D workload a full apply (2 nt + 2 solves) takes tens of minutes per
+# column, so each worker times `sample_steps` forward and adjoint steps plus
+# the two prior solves and scales the steps to nt (labelled as extrapolated).
+_ORACLE = None
+
+
+def _oracle_init(workload: str, nt: int):
+    global _ORACLE
     from oracle.problem import Problem as OProblem
-    spec = synth.workload("heat2d_127")
-    P = OProblem(spec)
-    x = synth.normal_block(P.nx, 1, 77)[:, 0]
-    n = 0
-    t0 = time.perf_counter()
-    while True:
+    spec = synth.workload(workload)
+    if nt:
+        spec.T, spec.nt = spec.T * nt / spec.nt, nt
+    _ORACLE = OProblem(spec, solver="cg" if spec.dim == 3 else "lu")
+
+
+def _oracle_apply_time(arg):
+    """Seconds of one Htilde apply to one column on this worker (sampled and
+    extrapolated when sample_steps > 0)."""
+    seed, sample_steps = arg
+    P = _ORACLE
+    x = synth.normal_block(P.nx, 1, seed)[:, 0]
+    if not sample_steps:
+        t0 = time.perf_counter()
         P.hessian_apply(x)
-        n += 1
-        dt = time.perf_counter() - t0
-        if dt >= seconds:
-            break
-    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} single-vector Htilde applies on heat2d_127 (nx=16129, nt=500) in {dt:.1f} s"}
+        return time.perf_counter() - t0
+    t0 = time.perf_counter()
+    z = P.prior_half(x)
+    t_prior = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    y = z
+    for _ in range(sample_steps):
+        y = P.step(y)
+    for _ in range(sample_steps):
+        y = P.step_adjoint(y)
+    t_steps = time.perf_counter() - t0
+    return 2 * t_prior + t_steps * P.nt / sample_steps
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+class OraclePool:
+    """The oracle on all host cores (spawned processes: safe after CUDA is
+    initialised in the parent)."""
+
+    def __init__(self, workload: str, nt: int = 0):
+        import multiprocessing as mp
+        self.cores = host_cores()
+        self.workload = workload
+        self.dim = 3 if workload.startswith("heat3d") else 2
+        self.sample_steps = 10 if self.dim == 3 else 0
+        env = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in env:
+            os.environ[k] = "1"  # one thread per worker process: cores = processes
+        try:
+            self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_oracle_init, initargs=(workload, nt))
+        finally:
+            for k, v in env.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        self.seed = 770
+
+    def block(self):
+        """Apply Htilde to one block of `cores` columns (one per process).
+        Returns (wall seconds, columns), extrapolated on the 3D workload."""
+        args = [(self.seed + j, self.sample_steps) for j in range(self.cores)]
+        self.seed += self.cores
+        t0 = time.perf_counter()
+        per = self.pool.map(_oracle_apply_time, args, chunksize=1)
+        wall = time.perf_counter() - t0
+        if self.sample_steps:
+            # the block's time is that of its slowest column at full length
+            return max(per), len(per)
+        return wall, len(per)
+
+    def sample_text(self, blocks: int, seconds: float) -> str:
+        if self.sample_steps:
+            return (f"{blocks} blocks of {self.cores} single-column Htilde applies (one per core) on {self.workload}, "
+                    f"each timed over 2 prior solves + {self.sample_steps} forward + {self.sample_steps} adjoint "
+                    f"steps and extrapolated to nt steps; {seconds:.1f} s of sampled work")
+        return (f"{blocks} blocks of {self.cores} single-column Htilde applies (one per core, sparse LU solves) "
+                f"on {self.workload} in {seconds:.1f} s")
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_baseline(workload: str, nt: int, n_matvec_to_k: int, seconds: float = 20.0):
+    """The FP64 oracle on this host's cores: matvec/s over blocks of one
+    column per core, and the time to rank k extrapolated from it with the
+    GPU run's matvec count (the oracle's own eigensolver is not run)."""
+    pool = OraclePool(workload, nt)
+    try:
+        pool.block()  # warm-up (factorisations, page-in)
+        t_tot, cols, blocks = 0.0, 0, 0
+        t0 = time.perf_counter()
+        while True:
+            dt, c = pool.block()
+            t_tot += dt
+            cols += c
+            blocks += 1
+            if time.perf_counter() - t0 >= seconds:
+                break
+        value = cols / t_tot
+        out = {"value": value, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+               "sample": pool.sample_text(blocks, time.perf_counter() - t0)}
+        if n_matvec_to_k:
+            out["s_to_rank_k_extrapolated"] = n_matvec_to_k / value
+            out["s_to_rank_k_basis"] = (f"{n_matvec_to_k} matvecs (the GPU Lanczos run's count) at the oracle's "
+                                        "matvec rate; extrapolated, not run")
+        return out
+    finally:
+        pool.close()
 
 
 def serve_bench(lrp, count: int, rate_hz: float, budget_gib: float, slots: int, max_batch: int):
@@ -301,32 +415,89 @@ def dist_env():
     return ws, rank, local
 
 
+def roofline_object(kdom, workload, ledger, unit, peaks, peak_kind, dev, block):
+    """Roofline figures of the dominant sweep kernel, per launch of the
+    Lanczos block apply (`block` columns, a whole Hessian apply): algorithmic
+    bytes (the sweep ledger: passes over the solver's fine-level vectors
+    implied by the iteration counts) / CUDA-event time, against the bound
+    that applies. The band kernel keeps those vectors in shared memory, so
+    its bound is shared-memory bandwidth (measured live by the library's own
+    kernel) and its DRAM traffic is a side figure; the generic kernel moves
+    its vectors through L2/HBM and is set against the HBM copy bandwidth."""
+    kname, kdesc, ksources = KERNELS[kdom]
+    ms, launches, algo = unit
+    achieved = (algo / launches) / (ms / launches / 1e3) / 1e9 if ms > 0 else 0.0
+    prof = {}
+    try:
+        with open(profile_summary(kname, workload)) as f:
+            prof = json.load(f)
+        if prof.get("kernel_hash") != kernel_hash(ksources):
+            prof = {"stale": True}
+    except (OSError, ValueError):
+        prof = {}
+    traffic = prof.get("dram_bytes_per_launch_full")
+    hbm = peaks["hbm_gbs"]
+    if kdom == 2:
+        obj = {"bound": "smem", "achieved": achieved, "peak": dev["smem_gbs"], "unit": "GB/s",
+               "frac": achieved / dev["smem_gbs"], "traffic": traffic,
+               "peak_kind": "shared-memory bandwidth measured live by lrp_measure_device_peaks (own kernel)"}
+        if traffic:
+            dram = traffic / (ms / launches / 1e3) / 1e9
+            obj["hbm_side_note"] = {"dram_gbs": dram, "frac_of_hbm": dram / hbm,
+                                    "hbm_peak_gbs": hbm, "hbm_peak_kind": f"{peak_kind} copy bandwidth"}
+    else:
+        obj = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+               "traffic": traffic, "peak_kind": f"{peak_kind} copy bandwidth"}
+    obj.update({"kernel": f"{kname} ({kdesc})", "kernel_hash": kernel_hash(ksources),
+                "unit_of_launch": f"one {block}-column Hessian apply (a Lanczos block step)",
+                "algo_bytes_per_launch": algo / max(launches, 1), "ms_per_launch": ms / max(launches, 1),
+                "launches": launches,
+                "sweep_ms_by_kernel": {KERNELS[kv][0]: ledger[kv][0] for kv in (1, 2)},
+                "device_peaks_live": dev})
+    if prof.get("ncu"):
+        obj["ncu"] = prof["ncu"]
+    return obj
+
+
+def config_dict(args, nt: int, ws: int = 1) -> dict:
+    """The workload configuration both arms print (identical dicts)."""
+    return {"workload": workload_name(args.workload, nt),
+            "step": ("block Lanczos to rank k + posterior factors + one query + the posterior mean's trajectory "
+                     "in low-rank-in-time form" if args.mode == "posterior"
+                     else "one Hessian apply to a block of columns"),
+            "k": args.k, "block": args.block, "eig_tol": 1e-6, "query": "mean + variance@1024 + 8 samples",
+            "parallelism": f"replicas x{max(ws, 1)}"}
+
+
 def run_reference(args):
+    """The oracle (FP64 SciPy, sparse LU or CG solves) timed on this host's
+    cores: every step applies Htilde to one block of columns, one column per
+    core (a bounded sample of the workload's matvecs; on the 3D workload each
+    column is itself sampled over 10 steps and extrapolated)."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    from oracle.problem import Problem as OProblem
-    spec = synth.workload("heat2d_127")
-    P = OProblem(spec)
-    x = synth.normal_block(P.nx, 1, 77)[:, 0]
-    per_step = 2  # a bounded sample per step: two single-vector applies
-    for _ in range(args.warmup):
-        P.hessian_apply(x)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        for _ in range(per_step):
-            P.hessian_apply(x)
-    dt = time.perf_counter() - t0
-    value = args.steps * per_step / dt
+    nt = args.nt or {"heat2d_127": 500, "heat3d_63": 1000}[args.workload]
+    pool = OraclePool(args.workload, args.nt)
+    try:
+        for _ in range(args.warmup):
+            pool.block()
+        t_tot, cols = 0.0, 0
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            dt, c = pool.block()
+            t_tot += dt
+            cols += c
+        wall = time.perf_counter() - t0
+    finally:
+        pool.close()
+    value = cols / t_tot
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": heat2d_workload(spec.nt), "k": 100,
-                       "step": "single-vector Hessian applies (the operation the matvec/s counts)",
-                       "l2": "n/a (host)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{per_step} single-vector Htilde applies per step"},
+            "data": "synthetic", "config": config_dict(args, nt, ws),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+                             "sample": pool.sample_text(args.steps, wall)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -339,8 +510,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--k", type=int, default=100)
-    ap.add_argument("--block", type=int, default=32)
+    ap.add_argument("--workload", default="heat2d_127", choices=sorted(WORKLOAD_DEFAULTS))
+    ap.add_argument("--k", type=int, default=0, help="rank (0: the workload's)")
+    ap.add_argument("--block", type=int, default=0, help="Lanczos block (0: the workload's)")
     ap.add_argument("--nt", type=int, default=0, help="override nt (profiling of small cases only)")
     ap.add_argument("--team-ctas", type=int, default=0)
     ap.add_argument("--team-cols", type=int, default=0)
@@ -361,6 +533,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
+    k0, b0 = WORKLOAD_DEFAULTS[args.workload]
+    args.k = args.k or k0
+    args.block = args.block or b0
     if args.impl == "reference":
         return run_reference(args)
 
@@ -403,8 +578,10 @@ def main():
         if dist:
             dist.destroy_process_group()
         return 0
-    spec = synth.workload("heat2d_127")
+    spec = synth.workload(args.workload)
     if args.nt:
+        # a shorter horizon with the workload's step size (profiling of small cases)
+        spec.T = spec.T * args.nt / spec.nt
         spec.nt = args.nt
     precision = lrp.LRP_MIXED if args.precision == "mixed" else lrp.LRP_FP64
     stream = torch.cuda.current_stream()
@@ -484,11 +661,16 @@ def main():
     if dist:
         dist.barrier()
     clocks = sampler.stop()
-    ledger = {kv: lrp.lrp_sweep_profile(G, -1, kv) for kv in (1, 2)}
+    # ledger: every sweep launch per kernel (1 generic, 2 band) and, per
+    # kernel, the launches that run a whole Hessian apply (3, 4): the
+    # Lanczos block applies, the unit of the roofline figures
+    ledger = {kv: lrp.lrp_sweep_profile(G, -1, kv) for kv in (1, 2, 3, 4)}
     lrp.lrp_sweep_profile(G, 0)
     # the dominant sweep kernel of the timed region (most device time)
-    kdom = max(ledger, key=lambda kv: ledger[kv][0])
-    sweep_ms, sweep_launches, sweep_bytes = ledger[kdom]
+    kdom = max((1, 2), key=lambda kv: ledger[kv][0])
+    sweep_ms, sweep_launches, sweep_bytes = ledger[kdom + 2]
+    if sweep_launches == 0:  # no whole-apply launch of it: all its launches
+        sweep_ms, sweep_launches, sweep_bytes = ledger[kdom]
     launches = lrp.lrp_kernel_launches() - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = float(sum(step_ms))
@@ -519,6 +701,8 @@ def main():
     fp64 = None
     if not args.no_fp64_compare and precision == lrp.LRP_MIXED and rank == 0 and args.mode == "posterior":
         G64 = lrp.lrp_setup_problem(spec, precision=lrp.LRP_FP64, stream=stream)
+        if not args.no_autotune and not tuning:
+            lrp.lrp_autotune(G64, args.block)  # tuned like the mixed path
         lrp.lrp_hessian_apply(G64, start_d[:, :2])
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -548,44 +732,25 @@ def main():
             dist.destroy_process_group()
         return 0
     peaks, peak_kind = measured_peaks()
+    dev = lrp.lrp_measure_device_peaks()
     tune = lrp.lrp_problem_tuning(G)
-    kname, kdesc, ksources = KERNELS[kdom]
-    achieved = (sweep_bytes / sweep_launches) / (sweep_ms / sweep_launches / 1e3) / 1e9 if sweep_ms > 0 else 0.0
-    traffic = None
-    try:
-        with open(profile_summary(kname)) as f:
-            prof = json.load(f)
-        if prof.get("kernel_hash") == kernel_hash(ksources) and prof.get("dram_bytes_per_launch_full"):
-            traffic = prof["dram_bytes_per_launch_full"]
-    except (OSError, ValueError):
-        pass
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                "kernel": f"{kname} ({kdesc})", "kernel_hash": kernel_hash(ksources),
-                "peak_kind": f"{peak_kind} copy bandwidth",
-                "algo_bytes_per_launch": sweep_bytes / max(sweep_launches, 1),
-                "ms_per_launch": sweep_ms / max(sweep_launches, 1), "launches": sweep_launches,
-                "sweep_ms_by_kernel": {KERNELS[kv][0]: ledger[kv][0] for kv in ledger}}
+    roofline = roofline_object(kdom, args.workload, ledger, (sweep_ms, sweep_launches, sweep_bytes), peaks,
+                               peak_kind, dev, args.block)
+    lan = stats[-1]
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
-        cpu = cpu_baseline()
-    lan = stats[-1]
+        cpu = cpu_baseline(args.workload, args.nt, lan["n_matvec"] if args.mode == "posterior" else 0)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": max(ws, 1), "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32/f64" if precision == lrp.LRP_MIXED else "f64",
         "data": "synthetic",
-        "config": {"workload": heat2d_workload(spec.nt),
-                   "step": ("block Lanczos to rank k + posterior factors + one query + the posterior mean's "
-                            "trajectory in low-rank-in-time form" if args.mode == "posterior"
-                            else "one Hessian apply to a block of columns"),
-                   "k": args.k, "block": args.block, "eig_tol": 1e-6, "query": "mean + variance@1024 + 8 samples",
-                   "l2": "flushed (256 MB write) before every timed step",
-                   "precision": "f32 MG-PCG inside f64 iterative refinement; f64 Lanczos, re-orthogonalisation, "
-                                "eigensolve and posterior" if precision == lrp.LRP_MIXED else "f64 throughout",
-                   "launch": tune, "autotuned": not args.no_autotune and not tuning,
-                   "parallelism": f"replicas x{max(ws, 1)}"},
+        "config": config_dict(args, spec.nt, ws),
+        "l2": "flushed (256 MB write) before every timed step",
+        "precision": ("f32 MG-PCG inside f64 iterative refinement; f64 Lanczos, re-orthogonalisation, "
+                      "eigensolve and posterior" if precision == lrp.LRP_MIXED else "f64 throughout"),
+        "launch": tune, "autotuned": not args.no_autotune and not tuning,
         "s_to_rank_k": statistics.mean(s["ms"] for s in stats) / 1e3,
         "lanczos": {"n_iter": lan["n_iter"], "n_matvec": lan["n_matvec"], "k_converged": lan["k_converged"],
                     "max_ritz_resid": lan["max_ritz_resid"], "ms_apply": lan["ms_apply"]},

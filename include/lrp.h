@@ -15,7 +15,8 @@
  *   observed steps obs_every, 2*obs_every, ..., nt (Sec. 6 Eq. (obj),
  *   Eq. (dis_obj)). Gamma_noise = sigma^2 I.
  *   Prior: Gamma_prior = R^-2, R = I + alpha L0 (L0 the constant-coefficient
- *   Laplacian), so Gamma_prior^{1/2} = R^{-1}.
+ *   Laplacian), so Gamma_prior^{1/2} = R^{-1}; or Gamma_prior = gamma I
+ *   (R^{-1} = sqrt(gamma) I, prior_kind LRP_PRIOR_IDENTITY).
  *   F = parameter-to-observable map; H_mis = F^T F / sigma^2;
  *   Htilde = R^{-1} H_mis R^{-1}  (Sec. 2 Eq. (prior_pre), Sec. 6.1 Eq. (misfit)).
  *
@@ -63,6 +64,12 @@ typedef enum {
 enum {
   LRP_FP64 = 0,  /* everything in FP64 */
   LRP_MIXED = 1  /* FP32 multigrid-PCG corrections inside FP64 iterative refinement */
+};
+
+/* prior covariance (lrp_problem_desc.prior_kind) */
+enum {
+  LRP_PRIOR_LAPLACE = 0,  /* Gamma_prior = (I + alpha L0)^-2, Gamma_prior^{1/2} = (I + alpha L0)^-1 */
+  LRP_PRIOR_IDENTITY = 1  /* Gamma_prior = gamma I, Gamma_prior^{1/2} = sqrt(gamma) I */
 };
 
 /* flags of lrp_hessian_apply */
@@ -113,6 +120,10 @@ typedef struct {
                                requested variant does not apply. Auto takes 3, else 2, else 1. */
   int mg_nu_coarse;         /* Jacobi sweeps before and after on the coarser levels of the band
                                kernel (0 -> mg_nu) */
+  int prior_kind;           /* LRP_PRIOR_LAPLACE: Gamma_prior = (I + prior_alpha L0)^-2 (the default);
+                               LRP_PRIOR_IDENTITY: Gamma_prior = prior_gamma I (the paper's
+                               experiments, Sec. 6.1: Gamma_prior = 10 I) */
+  double prior_gamma;       /* LRP_PRIOR_IDENTITY: the prior variance (> 0) */
 } lrp_problem_desc;
 
 typedef struct {
@@ -245,7 +256,9 @@ lrp_status lrp_trajectory_factors(lrp_problem* p, int nvec, const double* U, int
  * ||Htilde v - theta v|| <= eig_tol * theta_1 (eig_tol 0 -> 1e-6), or the
  * Krylov space reaches max_basis columns (0 -> min(nx, 4k+2*block)).
  * eig_threshold > 0 keeps only eigenvalues >= eig_threshold (the paper's
- * threshold epsilon) among the k. start: optional nx x block start block
+ * threshold epsilon, Sec. 6.1) among the k, and the iteration stops as soon
+ * as every Ritz value above the threshold meets the residual test and some
+ * Ritz value lies below it (k is then a cap). start: optional nx x block start block
  * (host or device), NULL -> a fixed pseudo-random block.
  * The posterior keeps V_k, G = R^{-1} V_k and lambda on the device.
  * Returns LRP_ENOCONV (with a usable posterior) if the basis cap is hit or a
@@ -314,7 +327,10 @@ const char* lrp_version(void);
  * solver's iteration counts); mode 0: reset and stop; mode -1: read only.
  * kernel selects what is returned: 0 all sweep launches, 1 the generic team
  * kernel, 2 the 2D band kernel. The accumulated values before the reset are
- * returned in *ms, *launches and *algo_bytes (each may be NULL). */
+ * returned in *ms, *launches and *algo_bytes (each may be NULL). kernel 3
+ * (generic) and 4 (band) select the launches that run a whole Hessian apply
+ * (prior solve, forward sweep, adjoint sweep, prior solve), e.g. the block
+ * applies of the Lanczos iteration. */
 lrp_status lrp_sweep_profile(lrp_problem* p, int mode, int kernel, double* ms, unsigned long long* launches,
                              double* algo_bytes);
 
@@ -410,6 +426,21 @@ void lrp_server_destroy(lrp_server* s);
 /* Diagnostics: number of CUDA kernels this library has launched in this
  * process so far (all problems, all threads). */
 unsigned long long lrp_kernel_launches(void);
+
+/* Peak rates of the current device measured with the library's own kernels
+ * (no counterpart in the paper; the denominators of the roofline figures of
+ * kernels not bound by HBM bandwidth): shared-memory bandwidth over all SMs
+ * (16-byte loads and stores, conflict-free), FP64 and FP32 FMA throughput
+ * (8 independent chains per thread). Each is the best of three timed
+ * launches; the call takes well under a second. */
+typedef struct {
+  double smem_gbs;         /* shared-memory bytes loaded + stored per second / 1e9 */
+  double fp64_fma_tflops;  /* 2 x FP64 FMAs per second / 1e12 */
+  double fp32_fma_tflops;  /* 2 x FP32 FMAs per second / 1e12 */
+  int sm_count;
+  double clock_mhz;        /* the device's nominal SM clock */
+} lrp_device_peaks;
+lrp_status lrp_measure_device_peaks(lrp_device_peaks* out);
 
 /* Test hook (failure injection on the host, no counterpart in the paper):
  * after `after` further successful device allocations by this library, the

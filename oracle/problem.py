@@ -11,7 +11,9 @@ y_n = S^n u with S = (I + tau L)^{-1}.
   q_{nt+1} = 0, q_n = (I + tau L)^{-T} (q_{n+1} + B^T w_n), F^T w = q_1
   (w_n = 0 at unobserved steps)
 * Gamma_noise = sigma^2 I, Gamma_prior = R^{-2} with R = I + alpha L0
-  (L0: the constant-coefficient Laplacian), so Gamma_prior^{1/2} = R^{-1}
+  (L0: the constant-coefficient Laplacian), so Gamma_prior^{1/2} = R^{-1};
+  or (prior_kind 1, the prior of the experiments of Sec. 6.1) Gamma_prior =
+  gamma I, i.e. R = gamma^{-1/2} I
 * H_mis = F^T F / sigma^2,  Htilde = R^{-1} H_mis R^{-1}
   (Sec. 2 Eq. (prior_pre); Sec. 6.1 Eq. (misfit))
 
@@ -57,6 +59,16 @@ class _CGSolver:
         return out.reshape(B.shape)
 
 
+class _ScaledIdentity:
+    """x = s b (Gamma_prior^{1/2} = sqrt(gamma) I)."""
+
+    def __init__(self, s):
+        self.s = float(s)
+
+    def solve(self, B, trans="N"):
+        return self.s * np.asarray(B, dtype=np.float64)
+
+
 class Problem:
     """All operators of one inverse problem. ``spec`` is any object with the
     attributes of ``synth.ProblemSpec`` (dim, n, nt, T, prior_alpha, sigma,
@@ -75,7 +87,12 @@ class Problem:
         self.sigma = float(spec.sigma)
         self.L = laplacian(self.n, self.dim, spec.kappa)
         self.L0 = laplacian(self.n, self.dim, None)
-        self.R = shifted(self.L0, self.alpha)
+        self.prior_kind = int(getattr(spec, "prior_kind", 0) or 0)
+        if self.prior_kind == 1:
+            self.gamma = float(spec.prior_gamma)
+            self.R = (sp.identity(self.nx, format="csc") / np.sqrt(self.gamma)).tocsc()
+        else:
+            self.R = shifted(self.L0, self.alpha)
         self.K = shifted(self.L, self.tau)
         if solver == "lu":
             self._R_lu = splu(self.R)
@@ -85,6 +102,8 @@ class Problem:
             self._K_lu = _CGSolver(self.K)
         else:
             raise ValueError(solver)
+        if self.prior_kind == 1:
+            self._R_lu = _ScaledIdentity(np.sqrt(self.gamma))
         self.B = observation_matrix(self.n, self.dim, spec.sensors)
         self.n_obs = self.B.shape[0]
         self.steps = observed_steps(self.nt, int(spec.obs_every))

@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_HERE, "liblrp.so")
 
 LRP_OK, LRP_EINVAL, LRP_ENOMEM, LRP_ENOCONV, LRP_ENONFINITE, LRP_ETIMEOUT, LRP_EBUDGET, LRP_ECUDA = range(8)
 LRP_FP64, LRP_MIXED = 0, 1
+LRP_PRIOR_LAPLACE, LRP_PRIOR_IDENTITY = 0, 1
 LRP_PRIOR_PRECOND, LRP_MISFIT_ONLY, LRP_KEEP_TRAJ_FACTORS = 0, 1, 2
 LRP_Q_MEAN, LRP_Q_VARIANCE, LRP_Q_SAMPLES = 1, 2, 4
 STATUS_NAMES = {0: "LRP_OK", 1: "LRP_EINVAL", 2: "LRP_ENOMEM", 3: "LRP_ENOCONV", 4: "LRP_ENONFINITE",
@@ -40,7 +41,7 @@ class lrp_problem_desc(C.Structure):
                 ("time_chunk", C.c_int), ("solve_rtol", C.c_double), ("pcg_maxit", C.c_int),
                 ("team_ctas", C.c_int), ("team_cols", C.c_int), ("mg_nu", C.c_int),
                 ("inner_rtol", C.c_double), ("coarse_items", C.c_int), ("kernel_variant", C.c_int),
-                ("mg_nu_coarse", C.c_int)]
+                ("mg_nu_coarse", C.c_int), ("prior_kind", C.c_int), ("prior_gamma", C.c_double)]
 
 
 class lrp_apply_stats(C.Structure):
@@ -99,6 +100,11 @@ class lrp_batch_stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class lrp_device_peaks(C.Structure):
+    _fields_ = [("smem_gbs", C.c_double), ("fp64_fma_tflops", C.c_double), ("fp32_fma_tflops", C.c_double),
+                ("sm_count", C.c_int), ("clock_mhz", C.c_double)]
+
+
 class lrp_tuning(C.Structure):
     _fields_ = [("team_ctas", C.c_int), ("team_cols", C.c_int), ("mg_nu", C.c_int), ("mg_nu_coarse", C.c_int),
                 ("inner_rtol", C.c_double), ("last_kernel", C.c_int), ("last_team_ctas", C.c_int),
@@ -133,6 +139,7 @@ EXPORTS = {
     "lrp_version": (C.c_char_p, []),
     "lrp_kernel_launches": (C.c_ulonglong, []),
     "lrp_debug_fail_alloc": (None, [C.c_longlong]),
+    "lrp_measure_device_peaks": (C.c_int, [C.POINTER(lrp_device_peaks)]),
     "lrp_sweep_profile": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _dp, C.POINTER(C.c_ulonglong), _dp]),
     "lrp_problem_tuning": (C.c_int, [C.c_void_p, C.POINTER(lrp_tuning)]),
     "lrp_batch_lowrank_posterior": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.c_double, C.c_int,
@@ -255,6 +262,8 @@ def _desc(spec, precision, tuning, keep):
         keep.append(k)
         d.kappa_faces = k.ctypes.data
     d.prior_alpha = float(spec.prior_alpha)
+    d.prior_kind = int(getattr(spec, "prior_kind", 0) or 0)
+    d.prior_gamma = float(getattr(spec, "prior_gamma", 0.0) or 0.0)
     sens = np.ascontiguousarray(np.asarray(spec.sensors, dtype=np.float64))
     keep.append(sens)
     d.n_obs = sens.shape[0]
@@ -616,6 +625,14 @@ def lrp_set_tuning(prob: "Problem", tuning: dict):
 
 def lrp_kernel_launches() -> int:
     return int(load().lrp_kernel_launches())
+
+
+def lrp_measure_device_peaks() -> dict:
+    """Shared-memory bandwidth and FP64/FP32 FMA throughput of the current
+    device, measured with the library's own kernels."""
+    pk = lrp_device_peaks()
+    _check(load().lrp_measure_device_peaks(C.byref(pk)))
+    return {f: getattr(pk, f) for f, _ in lrp_device_peaks._fields_}
 
 
 def lrp_debug_fail_alloc(after: int):

@@ -940,6 +940,21 @@ cudaError_t prior_diag_dst(cudaStream_t s, int dim, int n, double alpha, double*
   return cudaGetLastError();
 }
 
+__global__ void k_fill_const(size_t n, double v, double* out) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = v;
+}
+
+cudaError_t prior_diag(cudaStream_t s, const lrp_problem_desc& d, double* out, double* work) {
+  if (d.prior_kind == LRP_PRIOR_IDENTITY) {
+    const size_t total = d.dim == 2 ? (size_t)d.n * d.n : (size_t)d.n * d.n * d.n;
+    note_launch();
+    k_fill_const<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(total, d.prior_gamma, out);
+    return cudaGetLastError();
+  }
+  return prior_diag_dst(s, d.dim, d.n, d.prior_alpha, out, work);
+}
+
 // D[0:m, 0:n] += S[0:m, 0:n] (column-major, leading dimensions lds, ldd)
 __global__ void k_add_block(int m, int n, const double* S, int lds, double* D, int ldd) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;

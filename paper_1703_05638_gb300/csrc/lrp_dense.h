@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include "lrp.h"
+
 namespace lrp {
 
 // C (m x nb, ld ldc) = alpha * A^T B + beta * C; A: nx x m (lda), B: nx x nb (ldb).
@@ -56,5 +58,7 @@ cudaError_t gather(cudaStream_t s, int n, const int* idx, const double* v, doubl
 // Diagonal of (I + alpha L0)^-2 on the n^dim grid (constant-coefficient
 // Laplacian, zero Dirichlet data) by the sine transform; work >= n^2 + 2 n^dim.
 cudaError_t prior_diag_dst(cudaStream_t s, int dim, int n, double alpha, double* out, double* work);
+// (Gamma_prior)_ii at every node for either prior kind (work as prior_diag_dst)
+cudaError_t prior_diag(cudaStream_t s, const lrp_problem_desc& d, double* out, double* work);
 
 }  // namespace lrp

@@ -678,8 +678,9 @@ __device__ void fast_pcg(const Team& t, const Band& b, const FastVec& v, const O
     ++it_count;
     rz_old = rz;
     const bool capped = it_count >= cfg.maxit;
+    // an inner solve that stops at its cap is not a failure: the FP64
+    // refinement around it decides convergence (and flags its own cap)
     all = __syncthreads_and(done) || capped;
-    if (capped && !__syncthreads_and(done)) ctr.status |= STAT_NOCONV;
   }
   ctr.iters += it_count;
   ctr.iters_max = max(ctr.iters_max, it_count);
@@ -790,6 +791,8 @@ __device__ double* fast_solve(const Team& t, const Band& b, const SweepParams& P
     if (done) ctr.max_res = fmax(ctr.max_res, bbt > 0.0 ? sqrt(rrt / bbt) : 0.0);
     if (__syncthreads_and(done)) break;
     if (ref >= P.cfg.maxref) {
+      // the refinement cap: the residual reached is reported with the status
+      if (!done) ctr.max_res = fmax(ctr.max_res, bbt > 0.0 ? sqrt(rrt / bbt) : 0.0);
       ctr.status |= STAT_NOCONV;
       break;
     }
@@ -887,9 +890,17 @@ __global__ void __launch_bounds__(FAST_THREADS, 1) fast2d_kernel(const SweepPara
     team_sync(t);
   }
   if (P.stages & ST_PRIOR_IN) {
-    double* res = fast_solve(t, b, P, P.prior, w, v, sm, w.dbuf[cur], nullptr, nullptr, w.dbuf[(cur + 1) % 3],
-                             w.dbuf[(cur + 2) % 3], ctr);
-    cur = buf_index(w.dbuf, res);
+    if (P.prior_scale > 0.0) {
+      // identity prior: Gamma_prior^{1/2} x = sqrt(gamma) x
+      const int nxt = (cur + 1) % 3;
+      for_own([&](int row, int col) { w.dbuf[nxt][row * n + col] = P.prior_scale * w.dbuf[cur][row * n + col]; });
+      team_sync(t);
+      cur = nxt;
+    } else {
+      double* res = fast_solve(t, b, P, P.prior, w, v, sm, w.dbuf[cur], nullptr, nullptr, w.dbuf[(cur + 1) % 3],
+                               w.dbuf[(cur + 2) % 3], ctr);
+      cur = buf_index(w.dbuf, res);
+    }
   }
   if (P.stages & ST_FORWARD) {
     for (int step = P.t_begin + 1; step <= P.t_end; ++step) {
@@ -932,9 +943,17 @@ __global__ void __launch_bounds__(FAST_THREADS, 1) fast2d_kernel(const SweepPara
     }
   }
   if (P.stages & ST_PRIOR_OUT) {
-    double* res = fast_solve(t, b, P, P.prior, w, v, sm, w.dbuf[cur], nullptr, nullptr, w.dbuf[(cur + 1) % 3],
-                             w.dbuf[(cur + 2) % 3], ctr);
-    cur = buf_index(w.dbuf, res);
+    if (P.prior_scale > 0.0) {
+      // identity prior: Gamma_prior^{1/2} x = sqrt(gamma) x
+      const int nxt = (cur + 1) % 3;
+      for_own([&](int row, int col) { w.dbuf[nxt][row * n + col] = P.prior_scale * w.dbuf[cur][row * n + col]; });
+      team_sync(t);
+      cur = nxt;
+    } else {
+      double* res = fast_solve(t, b, P, P.prior, w, v, sm, w.dbuf[cur], nullptr, nullptr, w.dbuf[(cur + 1) % 3],
+                               w.dbuf[(cur + 2) % 3], ctr);
+      cur = buf_index(w.dbuf, res);
+    }
   }
   if ((P.stages & ST_STORE_Y) && valid) {
     for_own([&](int row, int col) {

@@ -219,6 +219,14 @@ lrp_status lrp_setup_problem(const lrp_problem_desc* desc, void* cuda_stream, lr
     set_error("precision must be LRP_FP64 or LRP_MIXED");
     return LRP_EINVAL;
   }
+  if (d.prior_kind != LRP_PRIOR_LAPLACE && d.prior_kind != LRP_PRIOR_IDENTITY) {
+    set_error("prior_kind must be LRP_PRIOR_LAPLACE or LRP_PRIOR_IDENTITY");
+    return LRP_EINVAL;
+  }
+  if (d.prior_kind == LRP_PRIOR_IDENTITY && !(d.prior_gamma > 0 && std::isfinite(d.prior_gamma))) {
+    set_error("LRP_PRIOR_IDENTITY needs a finite prior_gamma > 0");
+    return LRP_EINVAL;
+  }
   if (d.team_cols != 0 && (d.team_cols < 1 || d.team_cols > LRP_MAXBV || (d.team_cols & (d.team_cols - 1)))) {
     set_error("team_cols must be a power of two <= 16");
     return LRP_EINVAL;
@@ -294,6 +302,8 @@ lrp_status lrp_setup_problem(const lrp_problem_desc* desc, void* cuda_stream, lr
   hash = fnv1a(hash, &d.nt, sizeof(int));
   hash = fnv1a(hash, &d.T, sizeof(double));
   hash = fnv1a(hash, &d.prior_alpha, sizeof(double));
+  hash = fnv1a(hash, &d.prior_kind, sizeof(int));
+  if (d.prior_kind == LRP_PRIOR_IDENTITY) hash = fnv1a(hash, &d.prior_gamma, sizeof(double));
   hash = fnv1a(hash, &d.obs_every, sizeof(int));
   hash = fnv1a(hash, d.obs_xyz, sizeof(double) * d.n_obs * d.dim);
   for (int l = 0; l < L; ++l) {
@@ -435,8 +445,8 @@ lrp_status lrp_setup_problem(const lrp_problem_desc* desc, void* cuda_stream, lr
 
 lrp_status lrp_sweep_profile(lrp_problem* P, int mode, int kernel, double* ms, unsigned long long* launches,
                              double* algo_bytes) {
-  if (!P || kernel < 0 || kernel > 2) {
-    set_error("lrp_sweep_profile: NULL problem or kernel not in 0..2");
+  if (!P || kernel < 0 || kernel > 4) {
+    set_error("lrp_sweep_profile: NULL problem or kernel not in 0..4");
     return LRP_EINVAL;
   }
   if (ms) *ms = P->prof_ms[kernel];
@@ -448,7 +458,7 @@ lrp_status lrp_sweep_profile(lrp_problem* P, int mode, int kernel, double* ms, u
       cudaEventCreate(&P->prof_ev[1]);
     }
     P->prof_on = (mode == 1) && P->prof_ev[0];
-    for (int v = 0; v < 3; ++v) {
+    for (int v = 0; v < 5; ++v) {
       P->prof_ms[v] = 0.0;
       P->prof_bytes[v] = 0.0;
       P->prof_launches[v] = 0;

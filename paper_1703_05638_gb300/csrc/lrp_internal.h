@@ -104,6 +104,7 @@ struct SweepParams {
   int adj_begin;      // adjoint: first (largest) step
   int obs_every, n_obs, n_steps;
   double inv_sigma2;
+  double prior_scale;      // > 0: Gamma_prior^{1/2} = prior_scale I (no prior solve); 0: MG solve with I + alpha L0
   const int* obs_node;     // [n_obs][8]
   const double* obs_w;     // [n_obs][8]
   const int* bt_ptr;       // [N0+1]
@@ -186,9 +187,11 @@ struct lrp_problem {
   // (index 0: all launches; 1: generic team kernel; 2: band kernel)
   int prof_on;
   cudaEvent_t prof_ev[2];
-  double prof_ms[3];
-  double prof_bytes[3];
-  unsigned long long prof_launches[3];
+  // (3: generic kernel, 4: band kernel, launches that run a whole Hessian
+  // apply: both prior solves, the forward and the adjoint sweep)
+  double prof_ms[5];
+  double prof_bytes[5];
+  unsigned long long prof_launches[5];
   size_t dev_bytes = 0;  // device bytes of the problem's own arrays (not the workspace)
 };
 
@@ -225,6 +228,7 @@ lrp_status check_on_device(int device, const void* p, const char* what);
 struct SweepLaunch {
   bool fast = false, mixed = false;
   int BV = 1, n_teams = 0;
+  unsigned stages = 0;
 };
 lrp_status sweep_enqueue(lrp_problem* Pr, unsigned stages, int nvec, const double* X, int ldx, double* Y, int ldy,
                          const double* Din, int lddin, double* Dout, int lddout, int t_begin, int t_end,

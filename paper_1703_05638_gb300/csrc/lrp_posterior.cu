@@ -214,7 +214,9 @@ struct LanczosRun {
     CK(set_block(s, T.p, mmax + nb, cols, c0, nb, ws.R.p, nb, false, true));
     if (cols < mmax) CK(copy_cols(s, nx, nb, W.p, nx, Q.p + (size_t)cols * nx, nx));
     last = cols + nb > mmax;
-    check = cols >= std::min(k, mmax) || last;
+    // with a threshold the number of pairs is not known in advance: every
+    // block step checks whether the Ritz values have crossed it
+    check = cols >= std::min(k, mmax) || last || (eig_threshold > 0 && cols >= nb);
     if (check) {
       kk = std::min(k, cols);
       // eigenpairs of T_j (copied: the solver destroys its input)
@@ -252,6 +254,12 @@ struct LanczosRun {
                      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
       }
       bool ok = kk == k || cols >= nx;
+      if (eig_threshold > 0) {
+        // done once some Ritz value lies below the threshold (the kept ones
+        // still have to meet the residual test below)
+        for (int i = 0; i < kk; ++i)
+          if (h_theta[i] < eig_threshold) ok = true;
+      }
       max_res = 0.0;
       for (int i = 0; i < kk; ++i) {
         if (eig_threshold > 0 && h_theta[i] < eig_threshold) continue;
@@ -623,16 +631,16 @@ lrp_status lrp_posterior_query(lrp_posterior* post, const lrp_query* q, lrp_quer
     CK(dnodes.alloc(np));
     CK(cudaMemcpyAsync(dnodes.p, nodes.data(), np * sizeof(int), cudaMemcpyHostToDevice, s));
     if (!post->diag || post->diag_cap != nx) {
-      // prior variance at every node, (R^-2)_ii with R = I + alpha L0 (constant
-      // coefficients on the box): the sine-transform closed form, computed once
-      // per posterior
+      // prior variance at every node: (R^-2)_ii with R = I + alpha L0 (constant
+      // coefficients on the box) by the sine-transform closed form, or gamma
+      // for the identity prior; computed once per posterior
       if (post->diag) cudaFree(post->diag);
       post->diag = nullptr;
       CK(lrp::dev_malloc(&post->diag, (size_t)nx * sizeof(double)));
       post->diag_cap = nx;
       DArr<double> dwork;
       CK(dwork.alloc((size_t)P->n * P->n + 2 * (size_t)nx));
-      CK(prior_diag_dst(s, P->dim, P->n, P->desc.prior_alpha, post->diag, dwork.p));
+      CK(prior_diag(s, P->desc, post->diag, dwork.p));
       CK(cudaStreamSynchronize(s));
     }
     // gather the diagonal at the query nodes

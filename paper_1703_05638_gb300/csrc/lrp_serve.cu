@@ -685,7 +685,7 @@ lrp_status lrp_server_add_model(lrp_server* S, const lrp_problem_desc* d, int k,
     double* dwork = nullptr;
     const size_t nwork = (size_t)d->n * d->n + 3 * (size_t)m->nx;
     e = lrp::dev_malloc(&dwork, nwork * sizeof(double));
-    if (e == cudaSuccess) e = prior_diag_dst(s, dim, d->n, d->prior_alpha, dwork + nwork - m->nx, dwork);
+    if (e == cudaSuccess) e = prior_diag(s, *d, dwork + nwork - m->nx, dwork);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(m->h_diag, dwork + nwork - m->nx, (size_t)m->nx * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

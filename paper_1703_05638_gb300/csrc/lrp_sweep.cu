@@ -230,6 +230,7 @@ lrp_status sweep_enqueue(lrp_problem* Pr, unsigned stages, int nvec, const doubl
   prm.n_obs = Pr->n_obs;
   prm.n_steps = Pr->n_steps;
   prm.inv_sigma2 = 1.0 / (Pr->desc.sigma * Pr->desc.sigma);
+  prm.prior_scale = Pr->desc.prior_kind == LRP_PRIOR_IDENTITY ? std::sqrt(Pr->desc.prior_gamma) : 0.0;
   prm.obs_node = Pr->obs_node;
   prm.obs_w = Pr->obs_w;
   prm.bt_ptr = Pr->bt_ptr;
@@ -257,6 +258,7 @@ lrp_status sweep_enqueue(lrp_problem* Pr, unsigned stages, int nvec, const doubl
   if (e != cudaSuccess) return cuda_status(e, "stats reset");
   if (info) {
     info->fast = fast;
+    info->stages = stages;
     info->BV = BV;
     info->n_teams = n_teams;
     info->mixed = mixed;
@@ -300,7 +302,10 @@ lrp_status sweep_enqueue(lrp_problem* Pr, unsigned stages, int nvec, const doubl
 void ledger_add(lrp_problem* Pr, const Stats& hs, const SweepLaunch& info, double ms) {
   if (!Pr->prof_on) return;
   const double ab = algorithmic_bytes(Pr, hs, info.BV, info.mixed);
-  for (int v : {0, info.fast ? 2 : 1}) {
+  const unsigned hess = ST_PRIOR_IN | ST_FORWARD | ST_ADJOINT | ST_PRIOR_OUT;
+  const bool whole = (info.stages & hess) == hess;
+  for (int v : {0, info.fast ? 2 : 1, whole ? (info.fast ? 4 : 3) : -1}) {
+    if (v < 0) continue;
     Pr->prof_ms[v] += ms;
     Pr->prof_launches[v] += 1;
     Pr->prof_bytes[v] += ab;

@@ -243,7 +243,9 @@ __device__ LRP_SOLVER_FN void pcg_iterate(const Team& t, const Op& op, const WSV
     rz_old = rz;
     const bool capped = it_count >= cfg.maxit;
     all = __syncthreads_and(done) || capped;
-    if (capped && !__syncthreads_and(done)) ctr.status |= STAT_NOCONV;
+    // the cap is a failure of the FP64 solve; an FP32 inner solve that stops
+    // at it leaves the decision to the FP64 refinement around it
+    if (capped && sizeof(TX) == sizeof(double) && !__syncthreads_and(done)) ctr.status |= STAT_NOCONV;
   }
   ctr.iters += it_count;
   ctr.iters_max = max(ctr.iters_max, it_count);
@@ -396,6 +398,8 @@ __device__ LRP_SOLVER_FN double* solve_mixed(const Team& t, const SweepParams& P
     const bool all = __syncthreads_and(done);
     if (all) break;
     if (ref >= P.cfg.maxref) {
+      // the refinement cap: the residual reached is reported with the status
+      if (!done) ctr.max_res = fmax(ctr.max_res, bbt > 0.0 ? sqrt(rrt / bbt) : 0.0);
       ctr.status |= STAT_NOCONV;
       break;
     }
@@ -434,6 +438,16 @@ __device__ __forceinline__ double* solve_any(const Team& t, const SweepParams& P
 
 __device__ __forceinline__ int buf_index(const double* const* b, const double* x) {
   return x == b[0] ? 0 : (x == b[1] ? 1 : 2);
+}
+
+// Gamma_prior^{1/2} x = sqrt(gamma) x for the identity prior: the next state
+// buffer receives the scaled copy; returns its index.
+__device__ __forceinline__ int prior_scale_copy(const Team& t, const SweepParams& P, double* const* dbuf, int cur,
+                                                int items) {
+  const int nxt = (cur + 1) % 3;
+  for (int it = t.g; it < items; it += t.S) dbuf[nxt][it] = P.prior_scale * dbuf[cur][it];
+  team_sync(t);
+  return nxt;
 }
 
 template <typename T, int DIM, bool MIXED>
@@ -507,9 +521,13 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
   if (P.stages & ST_PRIOR_IN) {
     double* X1 = w.dbuf[(cur + 1) % 3];
     double* X2 = w.dbuf[(cur + 2) % 3];
-    double* res = solve_any<T, DIM, MIXED>(t, P, P.prior, w, sm, w.dbuf[cur], nullptr, nullptr, X1,
-                                           X2, ctr);
-    cur = buf_index(w.dbuf, res);
+    if (P.prior_scale > 0.0) {
+      cur = prior_scale_copy(t, P, w.dbuf, cur, items0);
+    } else {
+      double* res = solve_any<T, DIM, MIXED>(t, P, P.prior, w, sm, w.dbuf[cur], nullptr, nullptr, X1,
+                                             X2, ctr);
+      cur = buf_index(w.dbuf, res);
+    }
   }
   if (P.stages & ST_FORWARD) {
     for (int n = P.t_begin + 1; n <= P.t_end; ++n) {
@@ -571,9 +589,13 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
   if (P.stages & ST_PRIOR_OUT) {
     double* X1 = w.dbuf[(cur + 1) % 3];
     double* X2 = w.dbuf[(cur + 2) % 3];
-    double* res = solve_any<T, DIM, MIXED>(t, P, P.prior, w, sm, w.dbuf[cur], nullptr, nullptr, X1,
-                                           X2, ctr);
-    cur = buf_index(w.dbuf, res);
+    if (P.prior_scale > 0.0) {
+      cur = prior_scale_copy(t, P, w.dbuf, cur, items0);
+    } else {
+      double* res = solve_any<T, DIM, MIXED>(t, P, P.prior, w, sm, w.dbuf[cur], nullptr, nullptr, X1,
+                                             X2, ctr);
+      cur = buf_index(w.dbuf, res);
+    }
   }
   if ((P.stages & ST_STORE_Y) && valid) {
     for (int it = t.g; it < items0; it += t.S) P.Y[(size_t)gcol * P.ldy + (it >> t.bvs)] = w.dbuf[cur][it];

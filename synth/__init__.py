@@ -131,6 +131,8 @@ class ProblemSpec:
     time_trunc_tol: float = 1e-8
     time_rank_max: int = 40
     seed: int = 0
+    prior_kind: int = 0       # 0: (I + alpha L0)^-2; 1: gamma I
+    prior_gamma: float = 0.0
 
     @property
     def nx(self) -> int:
@@ -166,6 +168,32 @@ def workload(name: str, **overrides) -> ProblemSpec:
     for k, v in overrides.items():
         setattr(spec, k, v)
     return spec
+
+
+def paper_heat_spec(ratio: float, nt: int = 30) -> ProblemSpec:
+    """The 2D heat experiment of the paper's numerical section on finite
+    differences: 64 x 64 cells (63^2 interior nodes), nt = 30, T = 1; 9
+    square sensor patches of side 1/16 (1/256 of the domain) centred at
+    (i/4, j/4), i, j = 1..3, every node of a patch (4 x 4 nodes: the half-open
+    square [c - 1/32, c + 1/32)^2) a point sensor, observed at every step;
+    Gamma_prior = 10 I; noise level for beta_noise = ratio * beta_prior:
+    sigma^2 = 10 / (ratio * tau) (the misfit integral weighs each node and
+    step by tau h^2 and the prior term each node by h^2, so Gamma_prior =
+    10 I fixes beta_prior h^2 = 0.1 and Gamma_noise^-1 = 0.1 ratio tau)."""
+    n = 63
+    h = 1.0 / (n + 1)
+    pts = []
+    for cj in (1, 2, 3):
+        for ci in (1, 2, 3):
+            base_i, base_j = 16 * ci - 2, 16 * cj - 2  # node positions (i+1)h in [c - 2h, c + 2h)
+            for dj in range(4):
+                for di in range(4):
+                    pts.append(((base_i + di) * h, (base_j + dj) * h))
+    tau = 1.0 / nt
+    sigma = math.sqrt(10.0 / (ratio * tau))
+    return ProblemSpec(name=f"paper_heat_r{ratio:g}", dim=2, n=n, nt=nt, T=1.0, prior_alpha=0.0, sigma=sigma,
+                       obs_every=1, sensors=np.asarray(pts), k=50, block=1, seed=1000 + 5,
+                       prior_kind=1, prior_gamma=10.0)
 
 
 def small_spec(dim: int = 2, n: int = 7, nt: int = 12, obs_every: int = 3,

@@ -206,6 +206,31 @@ def test_hessian_modal_closed_form():
         np.testing.assert_allclose(P.hessian_apply(phi), lam * phi, rtol=1e-11, atol=1e-14)
 
 
+def test_identity_prior_modal_closed_form():
+    """The prior of the experiments of Sec. 6.1, Gamma_prior = gamma I: with
+    full observation a sine mode is an eigenvector of Htilde with eigenvalue
+    gamma sigma^-2 sum_n (1+tau mu)^-2n; the exact posterior covariance is
+    (H_mis + I/gamma)^-1 and the prior variance is gamma at every node.
+    Catches sqrt(gamma) applied once instead of twice, or 1/gamma in place of
+    gamma."""
+    n = 7
+    spec = _spec(n=n, nt=10, obs_every=1, sensors=synth.lattice_sensors(n, 2), sigma=0.3,
+                 prior_kind=1, prior_gamma=10.0)
+    P = Problem(spec)
+    for modes in [(1, 1), (2, 3), (5, 2)]:
+        phi = operators.sine_mode(n, 2, modes)
+        mu = operators.sine_eigenvalue(n, modes)
+        lam = 10.0 / P.sigma ** 2 * sum((1 + P.tau * mu) ** (-2 * k) for k in range(1, P.nt + 1))
+        np.testing.assert_allclose(P.hessian_apply(phi), lam * phi, rtol=1e-11, atol=1e-14)
+    Hm = P.misfit_explicit()
+    want = np.linalg.inv(Hm + np.eye(P.nx) / 10.0)
+    np.testing.assert_allclose(posterior.post_cov_exact(P), want, rtol=1e-10, atol=1e-14)
+    np.testing.assert_allclose(posterior.prior_diag(P, np.arange(P.nx)), 10.0, rtol=1e-15)
+    lam, V = spectrum.eig_dense(P.hessian_explicit())
+    G_lr = posterior.post_cov_lowrank(P, lam, V)
+    assert np.max(np.abs(G_lr - want)) <= 1e-10 * np.max(np.abs(want))
+
+
 def test_one_node_golden():
     rows = {r[0]: Fraction(r[1]) for r in _read_golden("one_node_problem.txt")}
     spec = _spec(n=1, nt=2, prior_alpha=1 / 16, sigma=1.0, obs_every=1,
