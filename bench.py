@@ -393,6 +393,40 @@ def batched_bench(lrp, count: int, block: int, steps: int, use_graph: bool = Tru
     return out
 
 
+# Arnoldi iteration counts printed by the paper for its Q1 finite-element
+# version of this experiment (MATLAB, one CPU core): context, not a target
+PAPER_ARNOLDI_ITERATIONS = {(1e6, 1.0): 72, (1e6, 0.1): 163, (1e8, 1.0): 347, (1e8, 0.1): 470}
+
+
+def paper_bench(lrp, precision):
+    """The heat experiment of the paper's numerical section on finite
+    differences (63^2 nodes, nt = 30, 9 sensor patches, Gamma_prior = 10 I)
+    for beta_noise / beta_prior in {1e4, 1e6, 1e8} and thresholds epsilon in
+    {1, 0.1}: single-vector Lanczos until every eigenvalue above epsilon is
+    resolved (Ritz residual 1e-6 theta_1); Lanczos steps, eigenvalues kept,
+    time, and the posterior variance over the grid (min / mean / max)."""
+    import torch
+    out = []
+    for ratio in (1e4, 1e6, 1e8):
+        spec = synth.paper_heat_spec(ratio)
+        G = lrp.lrp_setup_problem(spec, precision=precision)
+        nodes = np.arange(G.nx, dtype=np.int32)
+        for eps in (1.0, 0.1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            post, st = lrp.lrp_lowrank_posterior(G, k=1000, block=1, eig_tol=1e-6, eig_threshold=eps)
+            dt = time.perf_counter() - t0
+            lam = post.eigs()
+            var = lrp.lrp_posterior_query(post, lrp.LRP_Q_VARIANCE, points=nodes)["variance"]
+            out.append({"ratio": ratio, "epsilon": eps, "lanczos_steps": st["n_matvec"], "kept": int(len(lam)),
+                        "lambda_1": float(lam[0]) if len(lam) else None, "s": dt, "status": st["status"],
+                        "variance_min_mean_max": [float(var.min()), float(var.mean()), float(var.max())],
+                        "paper_arnoldi_iterations": PAPER_ARNOLDI_ITERATIONS.get((ratio, eps))})
+            post.close()
+        G.close()
+    return out
+
+
 def aggregate_replicas(dist, total_ms: float, matvecs: int, device: str):
     """Whole-job throughput of independent replicas: the matvecs of all ranks
     over the slowest rank's time (max over ranks). dist is torch.distributed
@@ -517,7 +551,7 @@ def main():
     ap.add_argument("--team-ctas", type=int, default=0)
     ap.add_argument("--team-cols", type=int, default=0)
     ap.add_argument("--mg-nu", type=int, default=0)
-    ap.add_argument("--mode", default="posterior", choices=["posterior", "apply", "serve", "batched"],
+    ap.add_argument("--mode", default="posterior", choices=["posterior", "apply", "serve", "batched", "paper"],
                     help="posterior: the whole hot path per step; apply: one Hessian apply per step "
                          "(kernel-level measurement and profiling); serve: the serving workload alone")
     ap.add_argument("--instances", type=int, default=64)
@@ -564,6 +598,18 @@ def main():
                               "config": {"workload": f"batched: {args.instances} 2D instances, grids 63/127/255, "
                                                      "nt 200-2000, k=50, block 16"},
                               "batched": bt}), flush=True)
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    if args.mode == "paper":
+        if rank == 0:
+            prec = lrp.LRP_MIXED if args.precision == "mixed" else lrp.LRP_FP64
+            runs = paper_bench(lrp, prec)
+            print(json.dumps({"metric": "Lanczos steps to resolve every eigenvalue above epsilon",
+                              "unit": "steps", "n_gpus": 1, "data": "synthetic", "dtype": args.precision,
+                              "config": {"workload": "paper heat experiment (Sec. 6.1) on FD: 63^2 nodes, nt=30, "
+                                                     "9 sensor patches, Gamma_prior=10 I"},
+                              "runs": runs}), flush=True)
         if dist:
             dist.destroy_process_group()
         return 0

@@ -28,6 +28,7 @@
 // can load the inputs of FAST_G column chunks before their first store.
 #pragma once
 
+#include "lrp_df64.cuh"
 #include "lrp_sweep_kernel.cuh"
 
 namespace lrp {
@@ -686,86 +687,98 @@ __device__ void fast_pcg(const Team& t, const Band& b, const FastVec& v, const O
   ctr.iters_max = max(ctr.iters_max, it_count);
 }
 
-// Solve (I + c L) x = b (FP64 state in global memory) by FP64 iterative
-// refinement around the band FP32 MG-PCG; inner problems scaled by powers of
-// two as in the generic kernel.
-__device__ double* fast_solve(const Team& t, const Band& b, const SweepParams& P, const Op& op,
-                              const WSV<float>& w, const FastVec& v, const CLv& sm, const double* bsrc,
-                              const double* dsrc, const double* x0, double* X1, double* X2, Ctr& ctr) {
+// Right-hand side at node p: the previous state (double-float) plus the
+// adjoint source B^T d (an FP64 sum over the sensors next to the node).
+__device__ __forceinline__ df fast_rhs(const SweepParams& P, const float2* bsrc, const double* dsrc, int p) {
+  df bv = bsrc ? df_load(bsrc + p) : df{0.f, 0.f};
+  if (dsrc) {
+    const int e0 = P.bt_ptr[p], e1 = P.bt_ptr[p + 1];
+    if (e1 > e0) {
+      double s = 0.0;
+      for (int e = e0; e < e1; ++e) s += P.bt_w[e] * dsrc[P.bt_idx[e]];
+      bv = df_add(bv, df_from_double(s));
+    }
+  }
+  return bv;
+}
+
+// Solve (I + c L) x = b by iterative refinement around the band FP32
+// MG-PCG; inner problems scaled by powers of two as in the generic kernel.
+// The state x, the right-hand side b and the refinement residual
+// r = b - (I + c L)(x + correction) are double-floats (about 48 bits: the
+// residual of the outer tolerance 1e-10 is resolved with a wide margin);
+// FP32 arithmetic runs at 64 times the FP64 rate here, and this pass was the
+// FP64-bound fifth of the kernel. x and b live in global memory as float2
+// (hi, lo) pairs.
+__device__ float2* fast_solve(const Team& t, const Band& b, const SweepParams& P, const Op& op, float2* bd,
+                              const FastVec& v, const CLv& sm, const float2* bsrc, const double* dsrc,
+                              const float2* x0, float2* X1, float2* X2, Ctr& ctr) {
   const OpLevel& l0 = op.lv[0];
   const int n = b.n;
-  const double ch2d = l0.ch2, dd = 1.0 + 4.0 * ch2d;
+  const df ch2 = df_from_double(l0.ch2);
+  const df dd = df_from_double(1.0 + 4.0 * l0.ch2);
   const float dinvf = (float)l0.dinv;
   const float omega = (float)P.cfg.omega;
   const float scale0 = (op.L == 1) ? 1.f : omega;
-  const double* xa = x0;
-  double* tgt = X1;
-  double* oth = X2;
+  const float2* xa = x0;
+  float2* tgt = X1;
+  float2* oth = X2;
   bool done = false;
   double bbt = 0.0;
   int ref = 0;
   const double inv_n = 1.0 / (double)l0.N;
   double sc = ctr.mix_scale;
-  double inv_sc_c = 1.0;
+  float isc_c = 1.f;  // 1 / scale of the current inner correction (a power of two)
   for (;; ++ref) {
     const bool first = (ref == 0);
-    double rr = 0.0, bb = 0.0, rz1 = 0.0;
+    // sc is a power of two chosen so that the FP32 residual is O(1); the
+    // scaled residual's squares are summed in FP32 and unscaled once
+    const float scf = (float)sc;
+    float rrs = 0.f;
+    double bb = 0.0, rz1 = 0.0;
     SEC_T0();
     const BArr Ra = barr(b, v.R), Ea = barr(b, v.E[0]);
     const bool has_x = xa || !first;
     for (int row = b.r0 + b.warp; row < b.r1; row += b.nwarp) {
 #pragma unroll
-      for (int j0 = 0; j0 < FAST_NJ; j0 += FAST_G) {
-        // loads of the chunks first (rhs, and x + c at the node and its four
-        // neighbours, c from the band with halos), then the stores
-        double bpv[FAST_G], xcen[FAST_G], xnb[FAST_G];
-#pragma unroll
-        for (int j = j0; j < j0 + FAST_G; ++j) {
-          const int col = b.lane + 32 * j;
-          if (col < n) {
-            const int p = row * n + col;
-            if (first)
-              bpv[j - j0] = rhs_at(P, t, bsrc, dsrc, p, p);
-            else
-              bpv[j - j0] = dsrc ? w.bd[p] : (bsrc ? bsrc[p] : 0.0);
-            if (has_x) {
-              auto xc = [&](int rr_, int cc_) -> double {
-                if (rr_ < 0 || rr_ >= n || cc_ < 0 || cc_ >= n) return 0.0;
-                double s = xa ? xa[rr_ * n + cc_] : 0.0;
-                if (!first) s += (double)s_fb[v.X + bidx(b, b.r0, rr_, cc_)] * inv_sc_c;
-                return s;
-              };
-              xcen[j - j0] = xc(row, col);
-              xnb[j - j0] = xc(row, col - 1) + xc(row, col + 1) + xc(row - 1, col) + xc(row + 1, col);
-            } else {
-              xcen[j - j0] = 0.0;
-              xnb[j - j0] = 0.0;
-            }
-          }
+      for (int j0 = 0; j0 < FAST_NJ; ++j0) {
+        const int col = b.lane + 32 * j0;
+        if (col >= n) continue;
+        const int p = row * n + col;
+        df bp;
+        if (first)
+          bp = fast_rhs(P, bsrc, dsrc, p);
+        else
+          bp = dsrc ? df_load(bd + p) : (bsrc ? df_load(bsrc + p) : df{0.f, 0.f});
+        df xcen = {0.f, 0.f}, ax = {0.f, 0.f};
+        if (has_x) {
+          // x + c / sc at the node and its four neighbours (c from the band
+          // with halos; zero outside the grid)
+          auto xc = [&](int rr_, int cc_) -> df {
+            if (rr_ < 0 || rr_ >= n || cc_ < 0 || cc_ >= n) return df{0.f, 0.f};
+            df s = xa ? df_load(xa + rr_ * n + cc_) : df{0.f, 0.f};
+            if (!first) s = df_add_f(s, s_fb[v.X + bidx(b, b.r0, rr_, cc_)] * isc_c);
+            return s;
+          };
+          xcen = xc(row, col);
+          const df nb = df_add(df_add(xc(row, col - 1), xc(row, col + 1)), df_add(xc(row - 1, col), xc(row + 1, col)));
+          ax = df_sub(df_mul(dd, xcen), df_mul(ch2, nb));
         }
-#pragma unroll
-        for (int j = j0; j < j0 + FAST_G; ++j) {
-          const int col = b.lane + 32 * j;
-          if (col < n) {
-            const int p = row * n + col;
-            const double bp = bpv[j - j0];
-            if (first) {
-              if (dsrc) w.bd[p] = bp;
-              bb += bp * bp;
-            }
-            const double ax = has_x ? dd * xcen[j - j0] - ch2d * xnb[j - j0] : 0.0;
-            const double rd = bp - ax;
-            tgt[p] = xcen[j - j0];
-            const float rf = (float)(rd * sc);
-            bstore(b, Ra, row, col, rf);
-            const float e = scale0 * rf * dinvf;
-            bstore(b, Ea, row, col, e);
-            rr += rd * rd;
-            if (op.L == 1) rz1 += (double)(rf * e);
-          }
+        const df rd = df_sub(bp, ax);
+        if (first) {
+          if (dsrc) df_store(bd + p, bp);
+          bb += (double)bp.hi * (double)bp.hi;
         }
+        df_store(tgt + p, xcen);
+        const float rf = rd.hi * scf;
+        bstore(b, Ra, row, col, rf);
+        const float e = scale0 * rf * dinvf;
+        bstore(b, Ea, row, col, e);
+        rrs = __fmaf_rn(rf, rf, rrs);
+        if (op.L == 1) rz1 += (double)(rf * e);
       }
     }
+    const double rr = (double)rrs / (sc * sc);
     SEC_ADD(SEC_REFINE);
     contribute(t, SL_RRD, rr);
     if (first) contribute(t, SL_BBD, bb);
@@ -778,7 +791,7 @@ __device__ double* fast_solve(const Team& t, const Band& b, const SweepParams& P
       bbt = total(t, SL_BBD);
       if (!(bbt > 0.0)) {
         for (int row = b.r0 + b.warp; row < b.r1; row += b.nwarp)
-          for (int col = b.lane; col < n; col += 32) tgt[row * n + col] = 0.0;
+          for (int col = b.lane; col < n; col += 32) tgt[row * n + col] = make_float2(0.f, 0.f);
         done = true;
       }
       ctr.mix_scale = pow2_inv(sqrt(bbt * inv_n));
@@ -800,10 +813,10 @@ __device__ double* fast_solve(const Team& t, const Band& b, const SweepParams& P
     fast_pcg(t, b, v, op, sm, P.cfg.inner_rtol * P.cfg.inner_rtol * rrt * sc * sc, idone, P.cfg, ctr,
              P.fast_split1 != 0);
     xa = tgt;
-    double* tmp = tgt;
+    float2* tmp = tgt;
     tgt = oth;
     oth = tmp;
-    inv_sc_c = 1.0 / sc;
+    isc_c = (float)(1.0 / sc);
     sc = pow2_inv(P.cfg.inner_rtol * sqrt(rrt * inv_n));
   }
   ctr.refines += ref;
@@ -865,10 +878,13 @@ __global__ void __launch_bounds__(FAST_THREADS, 1) fast2d_kernel(const SweepPara
   // no neighbour may write into this CTA's halos before they are zeroed
   team_sync(t);
   char* base = P.ws + (size_t)team * P.team_bytes;
-  WSV<float> w;
-  for (int k = 0; k < 3; ++k) w.dbuf[k] = (double*)(base + P.off_dbuf[k]);
-  w.bd = (double*)(base + P.off_bd);
-  w.obs = (double*)(base + P.off_obs);
+  // the implicit-Euler state buffers and the saved right-hand side hold
+  // double-floats (hi, lo) in the space of the FP64 vectors
+  float2* db[3];
+  for (int k = 0; k < 3; ++k) db[k] = (float2*)(base + P.off_dbuf[k]);
+  float2* bd = (float2*)(base + P.off_bd);
+  double* obs = (double*)(base + P.off_obs);
+  auto db_index = [&](const float2* x) { return x == db[0] ? 0 : (x == db[1] ? 1 : 2); };
   const int gcol = team;
   const bool valid = gcol < P.nvec;
   Ctr ctr;
@@ -877,88 +893,88 @@ __global__ void __launch_bounds__(FAST_THREADS, 1) fast2d_kernel(const SweepPara
     for (int row = b.r0 + b.warp; row < b.r1; row += b.nwarp)
       for (int col = b.lane; col < n; col += 32) f(row, col);
   };
+  // identity prior: Gamma_prior^{1/2} x = sqrt(gamma) x into the next buffer
+  auto prior_scale = [&]() {
+    const int nxt = (cur + 1) % 3;
+    const df s = df_from_double(P.prior_scale);
+    for_own([&](int row, int col) { df_store(db[nxt] + row * n + col, df_mul(s, df_load(db[cur] + row * n + col))); });
+    team_sync(t);
+    cur = nxt;
+  };
   if (P.stages & ST_LOAD_X) {
     for_own([&](int row, int col) {
       const int p = row * n + col;
-      w.dbuf[0][p] = valid ? P.X[(size_t)gcol * P.ldx + p] : 0.0;
+      df_store(db[0] + p, df_from_double(valid ? P.X[(size_t)gcol * P.ldx + p] : 0.0));
     });
     team_sync(t);
   }
   if (P.stages & ST_LOAD_D) {
     const int nd = P.n_obs * P.n_steps;
-    for (int it = t.g; it < nd; it += t.S) w.obs[it] = valid ? P.Din[(size_t)gcol * P.lddin + it] : 0.0;
+    for (int it = t.g; it < nd; it += t.S) obs[it] = valid ? P.Din[(size_t)gcol * P.lddin + it] : 0.0;
     team_sync(t);
   }
   if (P.stages & ST_PRIOR_IN) {
     if (P.prior_scale > 0.0) {
-      // identity prior: Gamma_prior^{1/2} x = sqrt(gamma) x
-      const int nxt = (cur + 1) % 3;
-      for_own([&](int row, int col) { w.dbuf[nxt][row * n + col] = P.prior_scale * w.dbuf[cur][row * n + col]; });
-      team_sync(t);
-      cur = nxt;
+      prior_scale();
     } else {
-      double* res = fast_solve(t, b, P, P.prior, w, v, sm, w.dbuf[cur], nullptr, nullptr, w.dbuf[(cur + 1) % 3],
-                               w.dbuf[(cur + 2) % 3], ctr);
-      cur = buf_index(w.dbuf, res);
+      float2* res = fast_solve(t, b, P, P.prior, bd, v, sm, db[cur], nullptr, nullptr, db[(cur + 1) % 3],
+                               db[(cur + 2) % 3], ctr);
+      cur = db_index(res);
     }
   }
   if (P.stages & ST_FORWARD) {
     for (int step = P.t_begin + 1; step <= P.t_end; ++step) {
-      double* res = fast_solve(t, b, P, P.step, w, v, sm, w.dbuf[cur], nullptr, w.dbuf[cur],
-                               w.dbuf[(cur + 1) % 3], w.dbuf[(cur + 2) % 3], ctr);
-      cur = buf_index(w.dbuf, res);
+      float2* res = fast_solve(t, b, P, P.step, bd, v, sm, db[cur], nullptr, db[cur], db[(cur + 1) % 3],
+                               db[(cur + 2) % 3], ctr);
+      cur = db_index(res);
       if (P.n_steps > 0 && (step % P.obs_every) == 0 && step / P.obs_every <= P.n_steps) {
         const int k = step / P.obs_every - 1;
         for (int s = t.g; s < P.n_obs; s += t.S) {
           double y = 0.0;
           for (int c = 0; c < 8; ++c) {
             const int node = P.obs_node[s * 8 + c];
-            if (node >= 0) y += P.obs_w[s * 8 + c] * res[node];
+            if (node >= 0) y += P.obs_w[s * 8 + c] * df_to_double(df_load(res + node));
           }
-          w.obs[(size_t)k * P.n_obs + s] = y * P.inv_sigma2;
+          obs[(size_t)k * P.n_obs + s] = y * P.inv_sigma2;
           if ((P.stages & ST_STORE_D) && valid) P.Dout[(size_t)gcol * P.lddout + k * P.n_obs + s] = y;
         }
       }
       if ((P.stages & ST_TRAJ) && valid) {
         double* dst = P.traj + ((size_t)gcol * P.traj_cols + (step - P.t_begin - 1)) * P.traj_ld;
-        for_own([&](int row, int col) { dst[row * n + col] = res[row * n + col]; });
+        for_own([&](int row, int col) { dst[row * n + col] = df_to_double(df_load(res + row * n + col)); });
       }
     }
     team_sync(t);
   }
   if (P.stages & ST_ADJOINT) {
-    const double* q = nullptr;
+    const float2* q = nullptr;
     for (int step = P.adj_begin; step >= 1; --step) {
-      const bool obs = (step % P.obs_every) == 0 && step / P.obs_every <= P.n_steps;
-      if (!q && !obs) continue;
-      const double* dsrc = obs ? w.obs + (size_t)(step / P.obs_every - 1) * P.n_obs : nullptr;
-      const int qi = q ? buf_index(w.dbuf, q) : cur;
-      q = fast_solve(t, b, P, P.step, w, v, sm, q, dsrc, q, w.dbuf[(qi + 1) % 3], w.dbuf[(qi + 2) % 3], ctr);
+      const bool is_obs = (step % P.obs_every) == 0 && step / P.obs_every <= P.n_steps;
+      if (!q && !is_obs) continue;
+      const double* dsrc = is_obs ? obs + (size_t)(step / P.obs_every - 1) * P.n_obs : nullptr;
+      const int qi = q ? db_index(q) : cur;
+      q = fast_solve(t, b, P, P.step, bd, v, sm, q, dsrc, q, db[(qi + 1) % 3], db[(qi + 2) % 3], ctr);
     }
     if (q) {
-      cur = buf_index(w.dbuf, q);
+      cur = db_index(q);
     } else {
-      for_own([&](int row, int col) { w.dbuf[cur][row * n + col] = 0.0; });
+      for_own([&](int row, int col) { db[cur][row * n + col] = make_float2(0.f, 0.f); });
       team_sync(t);
     }
   }
   if (P.stages & ST_PRIOR_OUT) {
     if (P.prior_scale > 0.0) {
-      // identity prior: Gamma_prior^{1/2} x = sqrt(gamma) x
-      const int nxt = (cur + 1) % 3;
-      for_own([&](int row, int col) { w.dbuf[nxt][row * n + col] = P.prior_scale * w.dbuf[cur][row * n + col]; });
-      team_sync(t);
-      cur = nxt;
+      prior_scale();
     } else {
-      double* res = fast_solve(t, b, P, P.prior, w, v, sm, w.dbuf[cur], nullptr, nullptr, w.dbuf[(cur + 1) % 3],
-                               w.dbuf[(cur + 2) % 3], ctr);
-      cur = buf_index(w.dbuf, res);
+      float2* res = fast_solve(t, b, P, P.prior, bd, v, sm, db[cur], nullptr, nullptr, db[(cur + 1) % 3],
+                               db[(cur + 2) % 3], ctr);
+      cur = db_index(res);
     }
   }
   if ((P.stages & ST_STORE_Y) && valid) {
     for_own([&](int row, int col) {
       const int p = row * n + col;
-      P.Y[(size_t)gcol * P.ldy + p] = w.dbuf[cur][p];
+      P.Y[(size_t)gcol * P.ldy + p] = df_to_double(df_load(db[cur] + p));
     });
   }
   team_sync(t);

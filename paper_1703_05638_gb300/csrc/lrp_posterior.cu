@@ -215,8 +215,9 @@ struct LanczosRun {
     if (cols < mmax) CK(copy_cols(s, nx, nb, W.p, nx, Q.p + (size_t)cols * nx, nx));
     last = cols + nb > mmax;
     // with a threshold the number of pairs is not known in advance: every
-    // block step checks whether the Ritz values have crossed it
-    check = cols >= std::min(k, mmax) || last || (eig_threshold > 0 && cols >= nb);
+    // block step (every 8 columns for narrower blocks) checks whether the
+    // Ritz values have crossed it
+    check = cols >= std::min(k, mmax) || last || (eig_threshold > 0 && cols % std::max(nb, 8) == 0);
     if (check) {
       kk = std::min(k, cols);
       // eigenpairs of T_j (copied: the solver destroys its input)
