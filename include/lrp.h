@@ -124,6 +124,13 @@ typedef struct {
                                LRP_PRIOR_IDENTITY: Gamma_prior = prior_gamma I (the paper's
                                experiments, Sec. 6.1: Gamma_prior = 10 I) */
   double prior_gamma;       /* LRP_PRIOR_IDENTITY: the prior variance (> 0) */
+  int mg_levels;            /* multigrid levels of the time-step operator I + tau L: 0 = down to one
+                               node; 3..L cuts the hierarchy there, and the coarsest kept level is
+                               smoothed by 2 mg_nu_coarse damped Jacobi sweeps (a fixed symmetric
+                               polynomial, so PCG stays valid) instead of solved exactly. On the
+                               coarse levels of a time step the operator is close to the identity
+                               (c/h^2 small), so the deep levels cost latency and add little. The
+                               prior operator always keeps the whole hierarchy. 0 -> autotuned or 0 */
 } lrp_problem_desc;
 
 typedef struct {
@@ -347,11 +354,12 @@ typedef struct lrp_tuning {
   int waves;    /* 1: clusters of the requested size even if they run in several waves */
   int team_ctas_narrow; /* cluster size for launches with few columns, used when all of their
                            clusters fit on the GPU at once at that size; 0 = team_ctas */
+  int mg_levels;        /* time-step operator's multigrid levels (0 = all; see lrp_problem_desc) */
 } lrp_tuning;
 lrp_status lrp_problem_tuning(const lrp_problem* p, lrp_tuning* out);
 /* Sets a problem's launch shape and multigrid settings from t (team_ctas,
  * team_cols, mg_nu, mg_nu_coarse, inner_rtol, threads 256 or 512, waves,
- * team_ctas_narrow 0..16; the
+ * team_ctas_narrow 0..16, mg_levels 0 or 3..levels; the
  * last_* fields are ignored), e.g. to reuse one autotuned setting for
  * problems of the same size. LRP_EINVAL on values out of range. */
 lrp_status lrp_set_tuning(lrp_problem* p, const lrp_tuning* t);

@@ -41,7 +41,8 @@ class lrp_problem_desc(C.Structure):
                 ("time_chunk", C.c_int), ("solve_rtol", C.c_double), ("pcg_maxit", C.c_int),
                 ("team_ctas", C.c_int), ("team_cols", C.c_int), ("mg_nu", C.c_int),
                 ("inner_rtol", C.c_double), ("coarse_items", C.c_int), ("kernel_variant", C.c_int),
-                ("mg_nu_coarse", C.c_int), ("prior_kind", C.c_int), ("prior_gamma", C.c_double)]
+                ("mg_nu_coarse", C.c_int), ("prior_kind", C.c_int), ("prior_gamma", C.c_double),
+                ("mg_levels", C.c_int)]
 
 
 class lrp_apply_stats(C.Structure):
@@ -108,7 +109,7 @@ class lrp_device_peaks(C.Structure):
 class lrp_tuning(C.Structure):
     _fields_ = [("team_ctas", C.c_int), ("team_cols", C.c_int), ("mg_nu", C.c_int), ("mg_nu_coarse", C.c_int),
                 ("inner_rtol", C.c_double), ("last_kernel", C.c_int), ("last_team_ctas", C.c_int),
-                ("threads", C.c_int), ("waves", C.c_int), ("team_ctas_narrow", C.c_int)]
+                ("threads", C.c_int), ("waves", C.c_int), ("team_ctas_narrow", C.c_int), ("mg_levels", C.c_int)]
 
 
 EXPORTS = {

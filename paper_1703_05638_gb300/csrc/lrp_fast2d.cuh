@@ -61,6 +61,40 @@ __device__ __forceinline__ void st_cluster(unsigned addr, float v) {
   asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
 }
 
+// Team reductions of the inner FP32 PCG (one column per team): the same
+// deterministic order as contribute()/total() of the generic kernel (warp
+// tree, warp 0 over the warps, lane r reading rank r, one fixed tree), but
+// summed in FP32: the FP64 pipe's dependent-add latency (~64 cycles) made
+// these trees a seventh of the kernel, and the inner solve needs its dot
+// products to FP32 accuracy only. The totals are kept as doubles in the
+// same slots.
+__device__ __forceinline__ void contribute_f(const Team& t, int slot, float v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  const int lane = t.tid & 31, w = t.tid >> 5;
+  float* redw = (float*)t.redw;
+  if (lane == 0) redw[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    float s = lane < (t.NT >> 5) ? redw[lane] : 0.f;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) ((float*)t.red)[(t.phase & 1) * NSLOT + slot] = s;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ double total_f(const Team& t, int slot) {
+  const int idx = ((t.phase - 1) & 1) * NSLOT + slot;
+  const float* red = (const float*)t.red;
+  if (t.C == 1) return (double)red[idx];
+  const int lane = t.tid & 31;
+  float s = lane < t.C ? *cg::this_cluster().map_shared_rank(red + idx, lane) : 0.f;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  return (double)s;
+}
+
 // Optional section timers (build with -DLRP_SECTION_TIMERS): thread 0 of each
 // CTA accumulates clock64() cycles per section into shared memory; CTA 0 of
 // team 0 writes them to SweepParams::section_cycles at exit.
@@ -81,7 +115,7 @@ __shared__ unsigned long long s_sec[8];
 #define SEC_ADD(k)
 #define SEC_RESET()
 #endif
-enum { SEC_BAND = 0, SEC_SYNC = 1, SEC_COARSE = 2, SEC_REFINE = 3, SEC_REDUCE = 4, SEC_OTHER = 5 };
+enum { SEC_BAND = 0, SEC_SYNC = 1, SEC_COARSE = 2, SEC_REFINE = 3, SEC_REDUCE = 4, SEC_OTHER = 5, SEC_COARSE2 = 6 };
 
 struct Band {
   int n, r0, r1, pitch;  // grid size, own rows, row pitch (n + 1)
@@ -456,6 +490,10 @@ __device__ int fast_vcycle(const Team& t, const Band& b, const FastVec& v, const
     SEC_ADD(SEC_SYNC);
   }
   const int n1 = op.lv[1].n;
+  // the coarsest level: one node is solved exactly (e = f / d); a hierarchy
+  // cut above it smooths its coarsest level by 2 nuc damped Jacobi sweeps
+  // from zero instead (a fixed symmetric polynomial)
+  const bool exact = op.lv[L - 1].n == 1;
   if (split1 && L >= 3) {
     // level 1 split across the cluster, levels 2.. in every CTA
     unsigned ecur = 0;  // bit l: current smoother buffer of level l
@@ -470,9 +508,10 @@ __device__ int fast_vcycle(const Team& t, const Band& b, const FastVec& v, const
       ecur ^= 2u;
       team_sync(t);
     }
-    crestrict_split(b, op.lv[1], op.lv[2], E(1), sm.f[1], sm.f[2], sm.e[2][0], (L == 3) ? 1.f : omega);
+    crestrict_split(b, op.lv[1], op.lv[2], E(1), sm.f[1], sm.f[2], sm.e[2][0], (L == 3 && exact) ? 1.f : omega);
     ecur &= ~4u;
     team_sync(t);
+    SEC_ADD(SEC_COARSE);
     for (int c = 2; c < L - 1; ++c) {
       for (int s = 1; s < nuc; ++s) {
         csweep(b, op.lv[c], Eo(c), E(c), sm.f[c], omega);
@@ -480,9 +519,16 @@ __device__ int fast_vcycle(const Team& t, const Band& b, const FastVec& v, const
         __syncthreads();
       }
       crestrict(b, op.lv[c], op.lv[c + 1], E(c), sm.f[c], sm.f[c + 1], sm.e[c + 1][0],
-                (c + 1 == L - 1) ? 1.f : omega);
+                (c + 1 == L - 1 && exact) ? 1.f : omega);
       ecur &= ~(1u << (c + 1));
       __syncthreads();
+    }
+    if (!exact) {
+      for (int s = 1; s < 2 * nuc; ++s) {
+        csweep(b, op.lv[L - 1], Eo(L - 1), E(L - 1), sm.f[L - 1], omega);
+        ecur ^= 1u << (L - 1);
+        __syncthreads();
+      }
     }
     for (int c = L - 2; c >= 2; --c) {
       cprolong(b, op.lv[c], op.lv[c + 1], E(c), E(c + 1));
@@ -493,6 +539,7 @@ __device__ int fast_vcycle(const Team& t, const Band& b, const FastVec& v, const
         __syncthreads();
       }
     }
+    SEC_ADD(SEC_COARSE2);
     cprolong_split(b, op.lv[1], op.lv[2], E(1), E(2));
     team_sync(t);
     for (int s = 0; s < nuc; ++s) {
@@ -514,7 +561,7 @@ __device__ int fast_vcycle(const Team& t, const Band& b, const FastVec& v, const
   // every CTA: the coarse levels in its own shared memory
   {
     const OpLevel& l1 = op.lv[1];
-    const float sc = (L == 2) ? 1.f : omega;
+    const float sc = (L == 2 && exact) ? 1.f : omega;
     const float d1inv = (float)l1.dinv;
     for_all(n1, b.warp, b.lane, b.nwarp, [&](int row, int col) {
       const int i = cidx(n1, row, col);
@@ -531,9 +578,16 @@ __device__ int fast_vcycle(const Team& t, const Band& b, const FastVec& v, const
         __syncthreads();
       }
       crestrict(b, op.lv[c], op.lv[c + 1], E(c), sm.f[c], sm.f[c + 1], sm.e[c + 1][0],
-                (c + 1 == L - 1) ? 1.f : omega);
+                (c + 1 == L - 1 && exact) ? 1.f : omega);
       ecur &= ~(1u << (c + 1));
       __syncthreads();
+    }
+    if (!exact) {
+      for (int s = 1; s < 2 * nuc; ++s) {
+        csweep(b, op.lv[L - 1], Eo(L - 1), E(L - 1), sm.f[L - 1], omega);
+        ecur ^= 1u << (L - 1);
+        __syncthreads();
+      }
     }
     for (int c = L - 2; c >= 1; --c) {
       cprolong(b, op.lv[c], op.lv[c + 1], E(c), E(c + 1));
@@ -557,7 +611,7 @@ __device__ int fast_vcycle(const Team& t, const Band& b, const FastVec& v, const
     fast_sweep(b, v, cur, ch2, d, dinv, omega, last, rz);
     cur ^= 1;
     SEC_ADD(SEC_BAND);
-    if (last) contribute(t, SL_RZ, rz);
+    if (last) contribute_f(t, SL_RZ, (float)rz);
     SEC_ADD(SEC_REDUCE);
     team_sync(t);
     SEC_ADD(SEC_SYNC);
@@ -579,7 +633,7 @@ __device__ void fast_pcg(const Team& t, const Band& b, const FastVec& v, const O
     const int zc = fast_vcycle(t, b, v, op, sm, omega, cfg.nu, cfg.nu_coarse, split1);
     SEC_T0();
     const int z = v.E[zc];
-    const double rz = total(t, SL_RZ);
+    const double rz = total_f(t, SL_RZ);
     SEC_ADD(SEC_REDUCE);
     const float beta = (float)((it_count == 0 || done || !(rz_old > 0.0)) ? 0.0 : rz / rz_old);
     float pqf = 0.f;
@@ -616,13 +670,12 @@ __device__ void fast_pcg(const Team& t, const Band& b, const FastVec& v, const O
         }
       }
     }
-    const double pq = (double)pqf;
     SEC_ADD(SEC_BAND);
-    contribute(t, SL_PQ, pq);
+    contribute_f(t, SL_PQ, pqf);
     SEC_ADD(SEC_REDUCE);
     team_sync(t);
     SEC_ADD(SEC_SYNC);
-    const double pqt = total(t, SL_PQ);
+    const double pqt = total_f(t, SL_PQ);
     SEC_ADD(SEC_REDUCE);
     const float alpha = (float)((done || !(pqt > 0.0)) ? 0.0 : rz / pqt);
     float rrf = 0.f, rz1f = 0.f;
@@ -662,14 +715,13 @@ __device__ void fast_pcg(const Team& t, const Band& b, const FastVec& v, const O
         }
       }
     }
-    const double rr = (double)rrf, rz1 = (double)rz1f;
     SEC_ADD(SEC_BAND);
-    contribute(t, SL_RR, rr);
-    if (op.L == 1) contribute(t, SL_RZ, rz1);
+    contribute_f(t, SL_RR, rrf);
+    if (op.L == 1) contribute_f(t, SL_RZ, rz1f);
     SEC_ADD(SEC_REDUCE);
     team_sync(t);
     SEC_ADD(SEC_SYNC);
-    const double rrt = total(t, SL_RR);
+    const double rrt = total_f(t, SL_RR);
     SEC_ADD(SEC_REDUCE);
     if (!isfinite(rrt)) {
       ctr.status |= STAT_NONFINITE;
@@ -782,7 +834,7 @@ __device__ float2* fast_solve(const Team& t, const Band& b, const SweepParams& P
     SEC_ADD(SEC_REFINE);
     contribute(t, SL_RRD, rr);
     if (first) contribute(t, SL_BBD, bb);
-    if (op.L == 1) contribute(t, SL_RZ, rz1);
+    if (op.L == 1) contribute_f(t, SL_RZ, (float)rz1);
     SEC_ADD(SEC_REDUCE);
     team_sync(t);
     SEC_ADD(SEC_SYNC);
@@ -991,7 +1043,7 @@ __global__ void __launch_bounds__(FAST_THREADS, 1) fast2d_kernel(const SweepPara
     atomicMax(&P.stats->max_rel_res_bits, (unsigned long long)__double_as_longlong(ctr.max_res));
 #ifdef LRP_SECTION_TIMERS
   if (team == 0 && t.rank == 0 && t.tid == 0 && P.section_cycles) {
-    for (int k = 0; k < 6; ++k) P.section_cycles[k] = s_sec[k];
+    for (int k = 0; k < 7; ++k) P.section_cycles[k] = s_sec[k];
     P.section_cycles[7] = (unsigned long long)(clock64() - k_t0);
   }
 #endif

@@ -433,6 +433,11 @@ lrp_status lrp_setup_problem(const lrp_problem_desc* desc, void* cuda_stream, lr
   c.nu = d.mg_nu > 0 ? d.mg_nu : 2;
   c.nu_coarse = d.mg_nu_coarse > 0 ? d.mg_nu_coarse : c.nu;
   c.omega = d.dim == 2 ? 0.8 : 6.0 / 7.0;
+  if (d.mg_levels != 0 && (d.mg_levels < 3 || d.mg_levels > L)) {
+    set_error("mg_levels must be 0 or in 3..levels of the grid");
+    return fail(LRP_EINVAL);
+  }
+  c.mg_levels = d.mg_levels;
   if (P->desc.time_chunk <= 0) P->desc.time_chunk = 16;
   if (P->desc.time_rank_max <= 0) P->desc.time_rank_max = 40;
   if (!(P->desc.time_trunc_tol > 0)) P->desc.time_trunc_tol = 1e-8;
@@ -482,6 +487,7 @@ lrp_status lrp_problem_tuning(const lrp_problem* P, lrp_tuning* out) {
   out->threads = P->nthreads;
   out->waves = P->allow_waves;
   out->team_ctas_narrow = P->team_ctas_narrow;
+  out->mg_levels = P->cfg.mg_levels;
   return LRP_OK;
 }
 
@@ -493,7 +499,8 @@ lrp_status lrp_set_tuning(lrp_problem* P, const lrp_tuning* t) {
   if (t->team_ctas < 1 || t->team_ctas > 16 || t->team_cols < 1 || t->team_cols > LRP_MAXBV ||
       (t->team_cols & (t->team_cols - 1)) || t->mg_nu < 1 || t->mg_nu > 8 || t->mg_nu_coarse < 1 ||
       t->mg_nu_coarse > 8 || !(t->inner_rtol > 0 && t->inner_rtol < 1) || (t->threads != 256 && t->threads != 512) ||
-      t->team_ctas_narrow < 0 || t->team_ctas_narrow > 16) {
+      t->team_ctas_narrow < 0 || t->team_ctas_narrow > 16 ||
+      (t->mg_levels != 0 && (t->mg_levels < 3 || t->mg_levels > P->L))) {
     set_error("lrp_set_tuning: value out of range");
     return LRP_EINVAL;
   }
@@ -505,6 +512,7 @@ lrp_status lrp_set_tuning(lrp_problem* P, const lrp_tuning* t) {
   P->cfg.nu = t->mg_nu;
   P->cfg.nu_coarse = t->mg_nu_coarse;
   P->cfg.inner_rtol = t->inner_rtol;
+  P->cfg.mg_levels = t->mg_levels;
   return LRP_OK;
 }
 
@@ -686,6 +694,7 @@ lrp_status lrp_autotune(lrp_problem* P, int nvec, int steps, double* best_ms) {
   struct Cand {
     int C, NT, BV, waves, nu, nuc;
     double inner, t1, t2;
+    int levels;
   };
   const bool mixed = P->desc.precision == LRP_MIXED;
   const int save_C = P->team_ctas, save_BV = P->team_cols, save_NT = P->nthreads, save_W = P->allow_waves;
@@ -703,6 +712,7 @@ lrp_status lrp_autotune(lrp_problem* P, int nvec, int steps, double* best_ms) {
     P->cfg = save_cfg;
     P->cfg.nu = c.nu;
     P->cfg.nu_coarse = c.nuc;
+    P->cfg.mg_levels = c.levels;
     if (mixed) P->cfg.inner_rtol = c.inner;
   };
   auto time_cols = [&](int ncols, unsigned stages, int t_end, double* out) {
@@ -725,7 +735,8 @@ lrp_status lrp_autotune(lrp_problem* P, int nvec, int steps, double* best_ms) {
   const unsigned screen = ST_LOAD_X | ST_PRIOR_IN | ST_FORWARD;
   // keep one screen near 20 ms: fewer steps for big problems
   {
-    Cand c0{save_C, save_NT, save_BV, save_W, save_cfg.nu, save_cfg.nu_coarse, save_cfg.inner_rtol, 1e300, 1e300};
+    Cand c0{save_C,    save_NT, save_BV, save_W, save_cfg.nu, save_cfg.nu_coarse, save_cfg.inner_rtol,
+            1e300,     1e300,   save_cfg.mg_levels};
     apply_cand(c0);
     double t = 1e300;
     time_it(screen, 1, &t);
@@ -740,31 +751,37 @@ lrp_status lrp_autotune(lrp_problem* P, int nvec, int steps, double* best_ms) {
           if (BV > 1 && nvec < 32) continue;  // one column per cluster wins for Lanczos-sized blocks
           if (C > 1 && (long long)P->nx / C < 256) continue;
           if (waves && C < 8) continue;  // more clusters than fit at once: only worth trying for big clusters
-          shapes.push_back({C, NT, BV, waves, save_cfg.nu, save_cfg.nu_coarse, save_cfg.inner_rtol, 1e300, 1e300});
+          shapes.push_back({C, NT, BV, waves, save_cfg.nu, save_cfg.nu_coarse, save_cfg.inner_rtol, 1e300, 1e300,
+                            save_cfg.mg_levels});
         }
   for (Cand& c : shapes) {
     apply_cand(c);
     time_it(screen, steps, &c.t1);
   }
   std::sort(shapes.begin(), shapes.end(), by_t1);
-  // stage 2: smoothing sweeps (finest level, coarse levels) and inner
-  // tolerance on the two best shapes
+  // stage 2: smoothing sweeps (finest level, coarse levels), inner
+  // tolerance and depth of the time-step operator's hierarchy on the two
+  // best shapes
+  std::vector<int> depths{0};
+  for (int lv = P->L - 1; lv >= std::max(3, P->L - 3); --lv) depths.push_back(lv);
   std::vector<Cand> cands;
   for (int i = 0; i < std::min<int>(2, (int)shapes.size()); ++i)
     for (int nu : {1, 2})
       for (int nuc : {1, 2})
-      for (double inner : (mixed ? std::vector<double>{1e-4, 1e-5} : std::vector<double>{save_cfg.inner_rtol})) {
-        // only the band kernel smooths the coarse levels separately
-        if (nuc != nu && P->last_kernel != 2) continue;
-        Cand c = shapes[i];
-        c.nu = nu;
-        c.nuc = nuc;
-        c.inner = inner;
-        c.t1 = 1e300;
-        apply_cand(c);
-        time_it(screen, steps, &c.t1);
-        cands.push_back(c);
-      }
+        for (double inner : (mixed ? std::vector<double>{1e-4, 1e-5} : std::vector<double>{save_cfg.inner_rtol}))
+          for (int levels : depths) {
+            // only the band kernel smooths the coarse levels separately
+            if (nuc != nu && P->last_kernel != 2) continue;
+            Cand c = shapes[i];
+            c.nu = nu;
+            c.nuc = nuc;
+            c.inner = inner;
+            c.levels = levels;
+            c.t1 = 1e300;
+            apply_cand(c);
+            time_it(screen, steps, &c.t1);
+            cands.push_back(c);
+          }
   std::sort(cands.begin(), cands.end(), by_t1);
   // stage 3: whole Hessian applies for the five best screens (the screen
   // ranks inner tolerances and smoothing counts only roughly)
@@ -827,9 +844,10 @@ lrp_status lrp_autotune(lrp_problem* P, int nvec, int steps, double* best_ms) {
                    shapes[i].NT, shapes[i].BV, shapes[i].waves, shapes[i].t1);
     for (int i = 0; i < n2; ++i)
       std::fprintf(stderr,
-                   "[lrp] autotune nvec=%d: C=%d NT=%d BV=%d waves=%d nu=%d/%d inner=%.0e screen %.2f ms, apply %.2f ms%s\n",
+                   "[lrp] autotune nvec=%d: C=%d NT=%d BV=%d waves=%d nu=%d/%d inner=%.0e levels=%d screen %.2f ms, "
+                   "apply %.2f ms%s\n",
                    nvec, cands[i].C, cands[i].NT, cands[i].BV, cands[i].waves, cands[i].nu, cands[i].nuc, cands[i].inner,
-                   cands[i].t1, cands[i].t2, i == bi ? " <- kept" : "");
+                   cands[i].levels, cands[i].t1, cands[i].t2, i == bi ? " <- kept" : "");
   }
   return LRP_OK;
 }

@@ -84,6 +84,7 @@ struct SolveCfg {
   int nu;             // Jacobi sweeps pre and post (finest level)
   int nu_coarse;      // Jacobi sweeps pre and post on the coarser levels
   double omega;       // Jacobi damping
+  int mg_levels;      // levels of the time-step operator's hierarchy (0 = all)
 };
 
 struct Stats {

@@ -145,10 +145,24 @@ lrp_status sweep_enqueue(lrp_problem* Pr, unsigned stages, int nvec, const doubl
     for (int c = l; c < Pr->L; ++c) bytes += 3 * (((size_t)Pr->step.lv[c].N * BV * tsz + 15) & ~(size_t)15);
     if ((long long)Pr->step.lv[l].N * BV <= Pr->coarse_items && bytes <= (size_t)Pr->smem_cap) Ls = l;
   }
+  // the time-step operator's hierarchy may stop above the one-node level;
+  // its coarsest kept level then lives in shared memory too (if it fits)
+  int Ls_step = Ls;
+  if (Pr->cfg.mg_levels >= 3 && Pr->cfg.mg_levels < Pr->L) {
+    const int Lst = Pr->cfg.mg_levels;
+    const int cand = std::min(Ls, Lst - 1);
+    size_t bytes = 0;
+    for (int c = cand; c < Pr->L; ++c) bytes += 3 * (((size_t)Pr->step.lv[c].N * BV * tsz + 15) & ~(size_t)15);
+    if (bytes <= (size_t)Pr->smem_cap) {
+      prm.step.L = Lst;
+      Ls_step = cand;
+    }
+  }
+  const int Ls_all = std::min(Ls, Ls_step);
   size_t soff = 0;
   for (int l = 0; l < LRP_MAXLEV; ++l) {
     for (int k = 0; k < 3; ++k) prm.smem_off[l][k] = 0;
-    if (l >= Ls && l < Pr->L) {
+    if (l >= Ls_all && l < Pr->L) {
       const size_t b = ((size_t)Pr->step.lv[l].N * BV * tsz + 15) & ~(size_t)15;
       for (int k = 0; k < 3; ++k) {
         prm.smem_off[l][k] = soff;
@@ -158,7 +172,7 @@ lrp_status sweep_enqueue(lrp_problem* Pr, unsigned stages, int nvec, const doubl
   }
   prm.smem_bytes = soff;
   prm.poison = Pr->poison;
-  prm.step.Ls = Ls;
+  prm.step.Ls = Ls_step;
   prm.prior.Ls = Ls;
   // team size: the largest C <= the requested one whose teams all stay
   // resident; few teams take the narrow-launch size when they all fit at it
@@ -291,8 +305,11 @@ lrp_status sweep_enqueue(lrp_problem* Pr, unsigned stages, int nvec, const doubl
     cudaStreamSynchronize(Pr->stream);
     unsigned long long sc[8];
     cudaMemcpy(sc, prm.section_cycles, sizeof(sc), cudaMemcpyDeviceToHost);
-    std::fprintf(stderr, "[sections] band %.3e sync %.3e coarse %.3e refine %.3e reduce %.3e total %.3e cycles\n",
-                 (double)sc[0], (double)sc[1], (double)sc[2], (double)sc[3], (double)sc[4], (double)sc[7]);
+    std::fprintf(stderr,
+                 "[sections] band %.3e sync %.3e coarse-level1 %.3e coarse-levels2+ %.3e refine %.3e reduce %.3e "
+                 "total %.3e cycles\n",
+                 (double)sc[0], (double)sc[1], (double)sc[2], (double)sc[6], (double)sc[3], (double)sc[4],
+                 (double)sc[7]);
   }
 #endif
   return LRP_OK;

@@ -94,9 +94,13 @@ __device__ LRP_SOLVER_FN int vcycle(const Team& t, const Op& op, const WSV<T>& w
   }
   // every CTA: restriction into its shared-memory level Ls, coarse cycle there
   {
+    // the coarsest level: one node is solved exactly (e = f / d); a
+    // hierarchy cut above it smooths its coarsest level by 2 nu damped
+    // Jacobi sweeps from zero instead (a fixed symmetric polynomial)
+    const bool exact = op.lv[L - 1].n == 1;
     const int l = Ls - 1;
     mg_restrict<T, DIM, KAPPA>(op.lv[l], op.lv[Ls], w.e[l][ecur[l]], w.f[l], sm.f[Ls], sm.e[Ls][0], t.tid,
-                               t.NT, t.bvs, t.col, (Ls == L - 1) ? T(1) : omega);
+                               t.NT, t.bvs, t.col, (Ls == L - 1 && exact) ? T(1) : omega);
     ecur[Ls] = 0;
     __syncthreads();
     for (int c = Ls; c < L - 1; ++c) {
@@ -107,9 +111,18 @@ __device__ LRP_SOLVER_FN int vcycle(const Team& t, const Op& op, const WSV<T>& w
         __syncthreads();
       }
       mg_restrict<T, DIM, KAPPA>(op.lv[c], op.lv[c + 1], sm.e[c][ecur[c]], sm.f[c], sm.f[c + 1],
-                                 sm.e[c + 1][0], t.tid, t.NT, t.bvs, t.col, (c + 1 == L - 1) ? T(1) : omega);
+                                 sm.e[c + 1][0], t.tid, t.NT, t.bvs, t.col, (c + 1 == L - 1 && exact) ? T(1) : omega);
       ecur[c + 1] = 0;
       __syncthreads();
+    }
+    if (!exact) {
+      const int c = L - 1;
+      for (int s = 1; s < 2 * nu; ++s) {
+        mg_sweep<T, DIM, KAPPA>(op.lv[c], sm.e[c][ecur[c] ^ 1], sm.e[c][ecur[c]], sm.f[c], t.tid, t.NT,
+                                t.bvs, t.col, omega, (const T*)nullptr, rz);
+        ecur[c] ^= 1;
+        __syncthreads();
+      }
     }
     for (int c = L - 2; c >= Ls; --c) {
       mg_prolong<T, DIM>(op.lv[c], op.lv[c + 1], sm.e[c][ecur[c]], sm.e[c + 1][ecur[c + 1]], t.tid, t.NT,

@@ -343,6 +343,28 @@ def test_band_kernel_matches_oracle(C, variant):
     assert np.all(Z == 0.0)
 
 
+@pytest.mark.parametrize("precision,kappa,variant", [(lrp.LRP_FP64, True, 0), (lrp.LRP_MIXED, True, 0),
+                                                     (lrp.LRP_MIXED, False, 2), (lrp.LRP_MIXED, False, 3)])
+@pytest.mark.parametrize("levels", [3, 4])
+def test_cut_hierarchy_keeps_results(precision, kappa, variant, levels):
+    """The time-step operator's multigrid hierarchy cut at 3 or 4 levels (the
+    coarsest kept level smoothed instead of solved) is still a fixed SPD
+    preconditioner: the solves reach the same tolerance and the Hessian apply
+    matches the oracle, on the generic kernel (with kappa) and on both band
+    kernel variants."""
+    spec = synth.small_spec(dim=2, n=63, nt=12, obs_every=2, n_obs=9, with_kappa=kappa, seed=37)
+    P = OProblem(spec)
+    G = lrp.lrp_setup_problem(spec, precision=precision, mg_levels=levels, team_ctas=4, team_cols=1,
+                              kernel_variant=variant)
+    U = synth.normal_block(P.nx, 3, 8)
+    H, st = lrp.lrp_hessian_apply(G, U)
+    assert st["status"] == lrp.LRP_OK, st
+    assert lrp.lrp_problem_tuning(G)["mg_levels"] == levels
+    assert relerr(H, P.hessian_apply(U)) < TOL[precision], st
+    D, st = lrp.lrp_forward_observe(G, U)
+    assert relerr(D, P.forward(U)) < TOL[precision], st
+
+
 @pytest.mark.parametrize("precision", [lrp.LRP_FP64, lrp.LRP_MIXED])
 def test_autotune_keeps_results(precision):
     """Whatever launch shape and multigrid setting the autotuner picks, the
