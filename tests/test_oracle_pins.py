@@ -460,3 +460,19 @@ def test_cg_solver_matches_lu():
     W = synth.normal_block(Pl.n_data, 2, 6)
     want = Pl.adjoint(W)
     np.testing.assert_allclose(Pc.adjoint(W), want, rtol=0, atol=1e-11 * np.abs(want).max())
+
+
+def test_golden_files_are_consistent():
+    """The oracle-written full-size reference values (tests/golden/make_spectra.py)
+    are what their headers say: decreasing eigenvalues with explicit residuals
+    far below the compared tolerances, and the sampled apply at the seeded
+    nodes of the 63^3 grid."""
+    for name, k in (("spectrum_heat2d_127.txt", 110), ("spectrum_heat3d_63_nt20.txt", 24)):
+        rows = _read_golden(name)
+        lam = np.array([float(r[1]) for r in rows])
+        res = np.array([float(r[2]) for r in rows])
+        assert len(lam) == k and np.all(np.diff(lam) <= 0) and lam[-1] > 0
+        assert np.max(res) < 1e-12
+    rows = _read_golden("apply_heat3d_63.txt")
+    nodes = np.array([int(r[0]) for r in rows])
+    assert np.array_equal(nodes, synth.query_nodes(63 ** 3, 256, 2028))
