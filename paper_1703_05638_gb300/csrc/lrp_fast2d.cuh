@@ -95,27 +95,6 @@ __device__ __forceinline__ double total_f(const Team& t, int slot) {
   return (double)s;
 }
 
-// Optional section timers (build with -DLRP_SECTION_TIMERS): thread 0 of each
-// CTA accumulates clock64() cycles per section into shared memory; CTA 0 of
-// team 0 writes them to SweepParams::section_cycles at exit.
-#ifdef LRP_SECTION_TIMERS
-__shared__ unsigned long long s_sec[8];
-#define SEC_T0() long long _sec_t0 = clock64()
-#define SEC_ADD(k)                                   \
-  do {                                               \
-    if (threadIdx.x == 0) {                          \
-      long long _t = clock64();                      \
-      s_sec[k] += (unsigned long long)(_t - _sec_t0); \
-      _sec_t0 = _t;                                  \
-    }                                                \
-  } while (0)
-#define SEC_RESET() _sec_t0 = clock64()
-#else
-#define SEC_T0()
-#define SEC_ADD(k)
-#define SEC_RESET()
-#endif
-enum { SEC_BAND = 0, SEC_SYNC = 1, SEC_COARSE = 2, SEC_REFINE = 3, SEC_REDUCE = 4, SEC_OTHER = 5, SEC_COARSE2 = 6 };
 
 struct Band {
   int n, r0, r1, pitch;  // grid size, own rows, row pitch (n + 1)
@@ -896,7 +875,7 @@ __global__ void __launch_bounds__(FAST_THREADS, 1) fast2d_kernel(const SweepPara
   const int team = blockIdx.x / P.C;
   const int n = P.step.lv[0].n;
 #ifdef LRP_SECTION_TIMERS
-  if (threadIdx.x < 8) s_sec[threadIdx.x] = 0;
+  if (threadIdx.x < 12) s_sec[threadIdx.x] = 0;
   const long long k_t0 = clock64();
 #endif
   Band b;
@@ -1043,8 +1022,8 @@ __global__ void __launch_bounds__(FAST_THREADS, 1) fast2d_kernel(const SweepPara
     atomicMax(&P.stats->max_rel_res_bits, (unsigned long long)__double_as_longlong(ctr.max_res));
 #ifdef LRP_SECTION_TIMERS
   if (team == 0 && t.rank == 0 && t.tid == 0 && P.section_cycles) {
-    for (int k = 0; k < 7; ++k) P.section_cycles[k] = s_sec[k];
-    P.section_cycles[7] = (unsigned long long)(clock64() - k_t0);
+    for (int k = 0; k < 11; ++k) P.section_cycles[k] = s_sec[k];
+    P.section_cycles[11] = (unsigned long long)(clock64() - k_t0);
   }
 #endif
 }

@@ -280,8 +280,8 @@ lrp_status sweep_enqueue(lrp_problem* Pr, unsigned stages, int nvec, const doubl
   if (Pr->prof_on) cudaEventRecord(Pr->prof_ev[0], Pr->stream);
 #ifdef LRP_SECTION_TIMERS
   static unsigned long long* sec_buf = nullptr;
-  if (!sec_buf) lrp::dev_malloc(&sec_buf, 8 * sizeof(unsigned long long));
-  cudaMemsetAsync(sec_buf, 0, 8 * sizeof(unsigned long long), Pr->stream);
+  if (!sec_buf) lrp::dev_malloc(&sec_buf, 12 * sizeof(unsigned long long));
+  cudaMemsetAsync(sec_buf, 0, 12 * sizeof(unsigned long long), Pr->stream);
   prm.section_cycles = sec_buf;
 #endif
   if (fast) {
@@ -301,15 +301,15 @@ lrp_status sweep_enqueue(lrp_problem* Pr, unsigned stages, int nvec, const doubl
     if (e != cudaSuccess) return cuda_status(e, "stats copy");
   }
 #ifdef LRP_SECTION_TIMERS
-  if (fast) {
+  {
     cudaStreamSynchronize(Pr->stream);
-    unsigned long long sc[8];
+    unsigned long long sc[12];
     cudaMemcpy(sc, prm.section_cycles, sizeof(sc), cudaMemcpyDeviceToHost);
     std::fprintf(stderr,
-                 "[sections] band %.3e sync %.3e coarse-level1 %.3e coarse-levels2+ %.3e refine %.3e reduce %.3e "
-                 "total %.3e cycles\n",
-                 (double)sc[0], (double)sc[1], (double)sc[2], (double)sc[6], (double)sc[3], (double)sc[4],
-                 (double)sc[7]);
+                 "[sections %s] finest %.3e sync %.3e coarse %.3e coarse2/smem %.3e restrict0 %.3e refine %.3e "
+                 "reduce %.3e pcg-vectors %.3e total %.3e cycles\n",
+                 fast ? "band" : "generic", (double)sc[0], (double)sc[1], (double)sc[2], (double)sc[6],
+                 (double)sc[7], (double)sc[3], (double)sc[4], (double)sc[5], (double)sc[11]);
   }
 #endif
   return LRP_OK;

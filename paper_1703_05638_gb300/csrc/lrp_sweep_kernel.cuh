@@ -69,18 +69,23 @@ __device__ LRP_SOLVER_FN int vcycle(const Team& t, const Op& op, const WSV<T>& w
   if (L == 1) return 0;  // z = r/d was formed exactly in the fused phase (rz too)
   const int Ls = op.Ls;  // 1 <= Ls <= L-1
   double rz = 0.0;
+  SEC_T0();
   // down: team levels 0..Ls-2 (pre-smoothing, restriction in global memory)
   for (int l = 0; l < Ls - 1; ++l) {
     for (int s = 1; s < nu; ++s) {
       mg_sweep<T, DIM, KAPPA>(op.lv[l], w.e[l][ecur[l] ^ 1], w.e[l][ecur[l]], w.f[l], t.g, t.S,
                               t.bvs, t.col, omega, (const T*)nullptr, rz);
       ecur[l] ^= 1;
+      SEC_ADD(l == 0 ? SEC_BAND : SEC_COARSE);
       team_sync(t);
+      SEC_ADD(SEC_SYNC);
     }
     mg_restrict<T, DIM, KAPPA>(op.lv[l], op.lv[l + 1], w.e[l][ecur[l]], w.f[l], w.f[l + 1],
                                w.e[l + 1][0], t.g, t.S, t.bvs, t.col, omega);
     ecur[l + 1] = 0;
+    SEC_ADD(l == 0 ? SEC_RESTRICT : SEC_COARSE);
     team_sync(t);
+    SEC_ADD(SEC_SYNC);
   }
   // level Ls-1: pre-smoothing by the team
   {
@@ -89,7 +94,9 @@ __device__ LRP_SOLVER_FN int vcycle(const Team& t, const Op& op, const WSV<T>& w
       mg_sweep<T, DIM, KAPPA>(op.lv[l], w.e[l][ecur[l] ^ 1], w.e[l][ecur[l]], w.f[l], t.g, t.S,
                               t.bvs, t.col, omega, (const T*)nullptr, rz);
       ecur[l] ^= 1;
+      SEC_ADD(l == 0 ? SEC_BAND : SEC_COARSE);
       team_sync(t);
+      SEC_ADD(SEC_SYNC);
     }
   }
   // every CTA: restriction into its shared-memory level Ls, coarse cycle there
@@ -136,6 +143,7 @@ __device__ LRP_SOLVER_FN int vcycle(const Team& t, const Op& op, const WSV<T>& w
       }
     }
   }
+  SEC_ADD(Ls == 1 ? SEC_RESTRICT : SEC_COARSE2);
   // up: prolongation from the CTA's own shared-memory level Ls, then the team levels
   for (int l = Ls - 1; l >= 0; --l) {
     if (l == Ls - 1) {
@@ -147,14 +155,19 @@ __device__ LRP_SOLVER_FN int vcycle(const Team& t, const Op& op, const WSV<T>& w
       mg_prolong<T, DIM>(op.lv[l], op.lv[l + 1], w.e[l][ecur[l]], w.e[l + 1][ecur[l + 1]], t.g, t.S, t.bvs,
                          t.col);
     }
+    SEC_ADD(l == 0 ? SEC_BAND : SEC_COARSE);
     team_sync(t);
+    SEC_ADD(SEC_SYNC);
     for (int s = 0; s < nu; ++s) {
       const bool last = (l == 0 && s == nu - 1);
       mg_sweep<T, DIM, KAPPA>(op.lv[l], w.e[l][ecur[l] ^ 1], w.e[l][ecur[l]], w.f[l], t.g, t.S,
                               t.bvs, t.col, omega, last ? (const T*)w.f[0] : (const T*)nullptr, rz);
       ecur[l] ^= 1;
+      SEC_ADD(l == 0 ? SEC_BAND : SEC_COARSE);
       if (last) contribute(t, SL_RZ, rz);
+      SEC_ADD(SEC_REDUCE);
       team_sync(t);
+      SEC_ADD(SEC_SYNC);
     }
   }
   return ecur[0];
@@ -176,8 +189,10 @@ __device__ LRP_SOLVER_FN void pcg_iterate(const Team& t, const Op& op, const WSV
   bool all = __syncthreads_and(done);
   while (!all) {
     const int zc = vcycle<T, DIM, KAPPA>(t, op, w, sm, omega, cfg.nu);
+    SEC_T0();
     const T* z = w.e[0][zc];
     const double rz = total(t, SL_RZ);
+    SEC_ADD(SEC_REDUCE);
     const T beta = (T)((it_count == 0 || done || !(rz_old > 0.0)) ? 0.0 : rz / rz_old);
     // phase A: p = z + beta p, q = A z + beta q, accumulate p.q
     double pq = 0.0;
@@ -209,9 +224,13 @@ __device__ LRP_SOLVER_FN void pcg_iterate(const Team& t, const Op& op, const WSV
           });
       pq = (double)pqp;
     }
+    SEC_ADD(SEC_OTHER);
     contribute(t, SL_PQ, pq);
+    SEC_ADD(SEC_REDUCE);
     team_sync(t);
+    SEC_ADD(SEC_SYNC);
     const double pqt = total(t, SL_PQ);
+    SEC_ADD(SEC_REDUCE);
     const T alpha = (T)((done || !(pqt > 0.0)) ? 0.0 : rz / pqt);
     // phase B: x += alpha p, r -= alpha q, first smoother sweep of the next V-cycle
     double rr = 0.0, rz1 = 0.0;
@@ -242,10 +261,14 @@ __device__ LRP_SOLVER_FN void pcg_iterate(const Team& t, const Op& op, const WSV
       rr = (double)rrp;
       rz1 = (double)rz1p;
     }
+    SEC_ADD(SEC_OTHER);
     contribute(t, SL_RR, rr);
     if (op.L == 1) contribute(t, SL_RZ, rz1);
+    SEC_ADD(SEC_REDUCE);
     team_sync(t);
+    SEC_ADD(SEC_SYNC);
     const double rrt = total(t, SL_RR);
+    SEC_ADD(SEC_REDUCE);
     if (!isfinite(rrt)) {
       ctr.status |= STAT_NONFINITE;
       done = true;
@@ -354,6 +377,7 @@ __device__ LRP_SOLVER_FN double* solve_mixed(const Team& t, const SweepParams& P
   for (;; ++ref) {
     const bool first = (ref == 0);
     double rr = 0.0, bb = 0.0, rz1 = 0.0;
+    SEC_T0();
     LdSum<float> ls{xa, first ? (const float*)nullptr : w.c, t.bvs, t.col, inv_sc_c};
     struct Ref {
       double bp, rd, x;
@@ -389,10 +413,13 @@ __device__ LRP_SOLVER_FN double* solve_mixed(const Team& t, const SweepParams& P
           rr += v.rd * v.rd;
           if (op.L == 1) rz1 += (double)(rf * e);
         });
+    SEC_ADD(SEC_REFINE);
     contribute(t, SL_RRD, rr);
     if (first) contribute(t, SL_BBD, bb);
     if (op.L == 1) contribute(t, SL_RZ, rz1);
+    SEC_ADD(SEC_REDUCE);
     team_sync(t);
+    SEC_ADD(SEC_SYNC);
     const double rrt = total(t, SL_RRD);
     if (first) {
       bbt = total(t, SL_BBD);
@@ -482,6 +509,10 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
   t.redw = s_redw;
   t.phase = 0;
   const int team = blockIdx.x / P.C;
+#ifdef LRP_SECTION_TIMERS
+  if (threadIdx.x < 12) s_sec[threadIdx.x] = 0;
+  const long long k_t0 = clock64();
+#endif
   char* base = P.ws + (size_t)team * P.team_bytes;
   WSV<T> w;
   for (int k = 0; k < 3; ++k) w.dbuf[k] = (double*)(base + P.off_dbuf[k]);
@@ -627,6 +658,12 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
   if (t.rank == 0 && t.tid < t.BV && valid) {
     atomicMax(&P.stats->max_rel_res_bits, (unsigned long long)__double_as_longlong(ctr.max_res));
   }
+#ifdef LRP_SECTION_TIMERS
+  if (team == 0 && t.rank == 0 && t.tid == 0 && P.section_cycles) {
+    for (int k = 0; k < 11; ++k) P.section_cycles[k] = s_sec[k];
+    P.section_cycles[11] = (unsigned long long)(clock64() - k_t0);
+  }
+#endif
 }
 
 // The shared-memory cap of a kernel is one value per function: it is always

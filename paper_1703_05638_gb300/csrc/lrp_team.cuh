@@ -21,6 +21,36 @@ namespace cg = cooperative_groups;
 
 namespace lrp {
 
+// Optional section timers (build with -DLRP_SECTION_TIMERS): thread 0 of each
+// CTA accumulates clock64() cycles per section into shared memory; CTA 0 of
+// team 0 writes them to SweepParams::section_cycles at exit (slot 11: the
+// whole kernel). Sections: 0 finest-level phases (band kernel: the band;
+// generic kernel: level-0 smoothing and prolongation), 1 team barriers,
+// 2 coarse level 1 (band) / global coarse levels (generic), 3 refinement,
+// 4 reductions, 5 PCG vector phases (generic), 6 coarse levels >= 2 (band) /
+// shared-memory levels (generic), 7 level-0 restriction (generic).
+#ifdef LRP_SECTION_TIMERS
+__shared__ unsigned long long s_sec[12];
+#define SEC_T0() long long _sec_t0 = clock64()
+#define SEC_ADD(k)                                   \
+  do {                                               \
+    if (threadIdx.x == 0) {                          \
+      long long _t = clock64();                      \
+      s_sec[k] += (unsigned long long)(_t - _sec_t0); \
+      _sec_t0 = _t;                                  \
+    }                                                \
+  } while (0)
+#define SEC_RESET() _sec_t0 = clock64()
+#else
+#define SEC_T0()
+#define SEC_ADD(k)
+#define SEC_RESET()
+#endif
+enum {
+  SEC_BAND = 0, SEC_SYNC = 1, SEC_COARSE = 2, SEC_REFINE = 3, SEC_REDUCE = 4, SEC_OTHER = 5, SEC_COARSE2 = 6,
+  SEC_RESTRICT = 7
+};
+
 enum { SL_RR = 0, SL_BB = 1, SL_RZ = 2, SL_PQ = 3, SL_RRD = 4, SL_BBD = 5, NSLOT = 8 };
 
 struct Team {
