@@ -396,6 +396,8 @@ def batched_bench(lrp, count: int, block: int, steps: int, use_graph: bool = Tru
 # Arnoldi iteration counts printed by the paper for its Q1 finite-element
 # version of this experiment (MATLAB, one CPU core): context, not a target
 PAPER_ARNOLDI_ITERATIONS = {(1e6, 1.0): 72, (1e6, 0.1): 163, (1e8, 1.0): 347, (1e8, 0.1): 470}
+# the same for its convection-diffusion experiment, by (nu, epsilon)
+PAPER_CD_ARNOLDI_ITERATIONS = {(1e-2, 10.0): 17, (1e-2, 1.0): 121, (1e-3, 10.0): 52, (1e-3, 1.0): 131}
 
 
 def paper_bench(lrp, precision):
@@ -422,6 +424,26 @@ def paper_bench(lrp, precision):
                         "lambda_1": float(lam[0]) if len(lam) else None, "s": dt, "status": st["status"],
                         "variance_min_mean_max": [float(var.min()), float(var.mean()), float(var.max())],
                         "paper_arnoldi_iterations": PAPER_ARNOLDI_ITERATIONS.get((ratio, eps))})
+            post.close()
+        G.close()
+    # the convection-diffusion experiment (FP64 path: the nonsymmetric steps
+    # are solved by BiCGStab)
+    for nu in (1e-2, 1e-3):
+        spec = synth.paper_convdiff_spec(nu)
+        G = lrp.lrp_setup_problem(spec, precision=lrp.LRP_FP64)
+        nodes = np.arange(G.nx, dtype=np.int32)
+        for eps in (10.0, 1.0):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            post, st = lrp.lrp_lowrank_posterior(G, k=min(1000, G.nx), block=1, eig_tol=1e-6, eig_threshold=eps)
+            dt = time.perf_counter() - t0
+            lam = post.eigs()
+            var = lrp.lrp_posterior_query(post, lrp.LRP_Q_VARIANCE, points=nodes)["variance"]
+            out.append({"pde": "convdiff", "nu": nu, "ratio": 1e4, "epsilon": eps, "lanczos_steps": st["n_matvec"],
+                        "kept": int(len(lam)), "lambda_1": float(lam[0]) if len(lam) else None, "s": dt,
+                        "status": st["status"],
+                        "variance_min_mean_max": [float(var.min()), float(var.mean()), float(var.max())],
+                        "paper_arnoldi_iterations": PAPER_CD_ARNOLDI_ITERATIONS.get((nu, eps))})
             post.close()
         G.close()
     return out
@@ -608,7 +630,8 @@ def main():
             print(json.dumps({"metric": "Lanczos steps to resolve every eigenvalue above epsilon",
                               "unit": "steps", "n_gpus": 1, "data": "synthetic", "dtype": args.precision,
                               "config": {"workload": "paper heat experiment (Sec. 6.1) on FD: 63^2 nodes, nt=30, "
-                                                     "9 sensor patches, Gamma_prior=10 I"},
+                                                     "9 sensor patches, Gamma_prior=10 I; convection-diffusion "
+                                                     "experiment (Sec. 6.2): 31^2 nodes, nt=90, upwind, FP64"},
                               "runs": runs}), flush=True)
         if dist:
             dist.destroy_process_group()

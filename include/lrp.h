@@ -7,8 +7,10 @@
  * "Low-rank computation of posterior covariance matrices in Bayesian inverse
  * problems", Sec. 6 Eq. (pde)):
  *
- *   y_t - div(kappa grad y) = 0 on the unit square/cube, y = 0 on the
- *   boundary, y(0) = u; finite differences with n interior nodes per axis
+ *   y_t - div(kappa grad y) = 0 (or the convection-diffusion equation
+ *   y_t - nu Laplace y + w . grad y = 0 of Sec. 6.2, upwind) on the unit
+ *   square/cube, y = 0 on the boundary, y(0) = u; finite differences with
+ *   n interior nodes per axis
  *   (h = 1/(n+1)), implicit Euler with tau = T/nt:
  *   (I + tau L) y_n = y_{n-1}  (block row of Sec. 6.1 Eq. (st_pde), M = I).
  *   Data: point sensors read the bilinear/trilinear interpolant of y at the
@@ -65,6 +67,9 @@ enum {
   LRP_FP64 = 0,  /* everything in FP64 */
   LRP_MIXED = 1  /* FP32 multigrid-PCG corrections inside FP64 iterative refinement */
 };
+
+/* PDE operator (lrp_problem_desc.pde) */
+enum { LRP_PDE_HEAT = 0, LRP_PDE_CONVDIFF = 1 };
 
 /* prior covariance (lrp_problem_desc.prior_kind) */
 enum {
@@ -124,6 +129,13 @@ typedef struct {
                                LRP_PRIOR_IDENTITY: Gamma_prior = prior_gamma I (the paper's
                                experiments, Sec. 6.1: Gamma_prior = 10 I) */
   double prior_gamma;       /* LRP_PRIOR_IDENTITY: the prior variance (> 0) */
+  int pde;                  /* LRP_PDE_HEAT (L = -div(kappa grad)) or LRP_PDE_CONVDIFF (L = -conv_nu
+                               Laplace + wind . grad with first-order upwind differences: the
+                               convection-diffusion operator of Sec. 6.2; not symmetric, so every
+                               implicit-Euler step is solved by Jacobi-preconditioned BiCGStab and
+                               the adjoint sweep solves with (I + tau L)^T; LRP_FP64 only, kappa NULL) */
+  double conv_nu;           /* LRP_PDE_CONVDIFF: diffusivity nu (>= 0) */
+  double wind[3];           /* LRP_PDE_CONVDIFF: constant wind vector w (dim entries used) */
   int mg_levels;            /* multigrid levels of the time-step operator I + tau L: 0 = down to one
                                node; 3..L cuts the hierarchy there, and the coarsest kept level is
                                smoothed by 2 mg_nu_coarse damped Jacobi sweeps (a fixed symmetric

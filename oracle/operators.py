@@ -73,6 +73,50 @@ def laplacian(n: int, dim: int, kappa=None) -> sp.csr_matrix:
     return A.tocsr()
 
 
+def upwind_convection(n: int, dim: int, wind) -> sp.csr_matrix:
+    """W = w . grad_h by first-order upwind differences with zero Dirichlet
+    data: for w_a > 0, (W y)_p += w_a (y_p - y_{p - e_a}) / h (the upstream
+    neighbour is the one on the low side); for w_a < 0, w_a (y_{p + e_a} -
+    y_p) / h. Upwinding replaces the paper's SUPG stabilisation of the
+    convection-diffusion experiment (Sec. 6.2); W is not symmetric."""
+    nx = n ** dim
+    hinv = float(n + 1)
+    rows, cols, vals = [], [], []
+    idx = np.arange(nx)
+    coords = []
+    rem = idx.copy()
+    for a in range(dim):
+        coords.append(rem % n)
+        rem = rem // n
+    for a in range(dim):
+        wa = float(wind[a])
+        if wa == 0.0:
+            continue
+        stride = n ** a
+        c = abs(wa) * hinv
+        rows.append(idx)
+        cols.append(idx)
+        vals.append(np.full(nx, c))
+        if wa > 0:
+            has = coords[a] > 0          # upstream neighbour p - e_a inside the grid
+            rows.append(idx[has])
+            cols.append(idx[has] - stride)
+        else:
+            has = coords[a] < n - 1      # upstream neighbour p + e_a inside the grid
+            rows.append(idx[has])
+            cols.append(idx[has] + stride)
+        vals.append(np.full(int(has.sum()), -c))
+    if not rows:
+        return sp.csr_matrix((nx, nx))
+    return sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(nx, nx)).tocsr()
+
+
+def convection_diffusion(n: int, dim: int, nu: float, wind) -> sp.csr_matrix:
+    """L = -nu Laplace_h + w . grad_h (Sec. 6.2's operator, upwind convection)."""
+    return (nu * laplacian(n, dim, None) + upwind_convection(n, dim, wind)).tocsr()
+
+
 def shifted(L: sp.spmatrix, c: float) -> sp.csc_matrix:
     """I + c*L: the implicit-Euler step matrix (c = tau, Sec. 6.1, block row
     of Eq. (st_pde) with M = I) or the prior root R (c = alpha)."""

@@ -1,6 +1,9 @@
 """Forward map, adjoint and prior-preconditioned misfit Hessian (FP64).
 
-The parameter u is the initial condition of y_t + L y = 0 (Sec. 6, Eq. (pde)).
+The parameter u is the initial condition of y_t + L y = 0 (Sec. 6, Eq. (pde));
+L = -div(kappa grad) (the heat equation) or -nu Laplace + w . grad (the
+convection-diffusion equation of Sec. 6.2, upwind; not symmetric, so the
+adjoint steps solve with (I + tau L)^T).
 Implicit Euler with tau = T/nt gives (I + tau L) y_n = y_{n-1}, y_0 = u
 (one block row of the space-time system Eq. (st_pde) with M = I), so
 y_n = S^n u with S = (I + tau L)^{-1}.
@@ -26,7 +29,7 @@ import numpy as np
 import scipy.sparse as sp
 from scipy.sparse.linalg import cg, splu
 
-from .operators import laplacian, shifted
+from .operators import convection_diffusion, laplacian, shifted
 from .observe import observation_matrix, observed_steps
 
 
@@ -85,7 +88,12 @@ class Problem:
         self.tau = float(spec.T) / self.nt
         self.alpha = float(spec.prior_alpha)
         self.sigma = float(spec.sigma)
-        self.L = laplacian(self.n, self.dim, spec.kappa)
+        self.pde = str(getattr(spec, "pde", "heat") or "heat")
+        if self.pde == "convdiff":
+            # Sec. 6.2: L = -nu Laplace + w . grad (upwind); not symmetric
+            self.L = convection_diffusion(self.n, self.dim, float(spec.conv_nu), spec.wind)
+        else:
+            self.L = laplacian(self.n, self.dim, spec.kappa)
         self.L0 = laplacian(self.n, self.dim, None)
         self.prior_kind = int(getattr(spec, "prior_kind", 0) or 0)
         if self.prior_kind == 1:
@@ -98,6 +106,8 @@ class Problem:
             self._R_lu = splu(self.R)
             self._K_lu = splu(self.K)
         elif solver == "cg":
+            if self.pde != "heat":
+                raise ValueError("the CG solves need a symmetric operator")
             self._R_lu = _CGSolver(self.R)
             self._K_lu = _CGSolver(self.K)
         else:

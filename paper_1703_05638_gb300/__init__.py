@@ -24,6 +24,7 @@ LIB_PATH = os.path.join(_HERE, "liblrp.so")
 LRP_OK, LRP_EINVAL, LRP_ENOMEM, LRP_ENOCONV, LRP_ENONFINITE, LRP_ETIMEOUT, LRP_EBUDGET, LRP_ECUDA = range(8)
 LRP_FP64, LRP_MIXED = 0, 1
 LRP_PRIOR_LAPLACE, LRP_PRIOR_IDENTITY = 0, 1
+LRP_PDE_HEAT, LRP_PDE_CONVDIFF = 0, 1
 LRP_PRIOR_PRECOND, LRP_MISFIT_ONLY, LRP_KEEP_TRAJ_FACTORS = 0, 1, 2
 LRP_Q_MEAN, LRP_Q_VARIANCE, LRP_Q_SAMPLES = 1, 2, 4
 STATUS_NAMES = {0: "LRP_OK", 1: "LRP_EINVAL", 2: "LRP_ENOMEM", 3: "LRP_ENOCONV", 4: "LRP_ENONFINITE",
@@ -42,7 +43,7 @@ class lrp_problem_desc(C.Structure):
                 ("team_ctas", C.c_int), ("team_cols", C.c_int), ("mg_nu", C.c_int),
                 ("inner_rtol", C.c_double), ("coarse_items", C.c_int), ("kernel_variant", C.c_int),
                 ("mg_nu_coarse", C.c_int), ("prior_kind", C.c_int), ("prior_gamma", C.c_double),
-                ("mg_levels", C.c_int)]
+                ("pde", C.c_int), ("conv_nu", C.c_double), ("wind", C.c_double * 3), ("mg_levels", C.c_int)]
 
 
 class lrp_apply_stats(C.Structure):
@@ -265,6 +266,11 @@ def _desc(spec, precision, tuning, keep):
     d.prior_alpha = float(spec.prior_alpha)
     d.prior_kind = int(getattr(spec, "prior_kind", 0) or 0)
     d.prior_gamma = float(getattr(spec, "prior_gamma", 0.0) or 0.0)
+    if (getattr(spec, "pde", "heat") or "heat") == "convdiff":
+        d.pde = LRP_PDE_CONVDIFF
+        d.conv_nu = float(spec.conv_nu)
+        for a, v in enumerate(spec.wind):
+            d.wind[a] = float(v)
     sens = np.ascontiguousarray(np.asarray(spec.sensors, dtype=np.float64))
     keep.append(sens)
     d.n_obs = sens.shape[0]

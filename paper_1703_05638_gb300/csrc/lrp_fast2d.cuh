@@ -61,39 +61,6 @@ __device__ __forceinline__ void st_cluster(unsigned addr, float v) {
   asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
 }
 
-// Team reductions of the inner FP32 PCG (one column per team): the same
-// deterministic order as contribute()/total() of the generic kernel (warp
-// tree, warp 0 over the warps, lane r reading rank r, one fixed tree), but
-// summed in FP32: the FP64 pipe's dependent-add latency (~64 cycles) made
-// these trees a seventh of the kernel, and the inner solve needs its dot
-// products to FP32 accuracy only. The totals are kept as doubles in the
-// same slots.
-__device__ __forceinline__ void contribute_f(const Team& t, int slot, float v) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  const int lane = t.tid & 31, w = t.tid >> 5;
-  float* redw = (float*)t.redw;
-  if (lane == 0) redw[w] = v;
-  __syncthreads();
-  if (w == 0) {
-    float s = lane < (t.NT >> 5) ? redw[lane] : 0.f;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if (lane == 0) ((float*)t.red)[(t.phase & 1) * NSLOT + slot] = s;
-  }
-  __syncthreads();
-}
-
-__device__ __forceinline__ double total_f(const Team& t, int slot) {
-  const int idx = ((t.phase - 1) & 1) * NSLOT + slot;
-  const float* red = (const float*)t.red;
-  if (t.C == 1) return (double)red[idx];
-  const int lane = t.tid & 31;
-  float s = lane < t.C ? *cg::this_cluster().map_shared_rank(red + idx, lane) : 0.f;
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-  return (double)s;
-}
 
 
 struct Band {
@@ -590,7 +557,7 @@ __device__ int fast_vcycle(const Team& t, const Band& b, const FastVec& v, const
     fast_sweep(b, v, cur, ch2, d, dinv, omega, last, rz);
     cur ^= 1;
     SEC_ADD(SEC_BAND);
-    if (last) contribute_f(t, SL_RZ, (float)rz);
+    if (last) contribute(t, SL_RZ, (float)rz);
     SEC_ADD(SEC_REDUCE);
     team_sync(t);
     SEC_ADD(SEC_SYNC);
@@ -650,7 +617,7 @@ __device__ void fast_pcg(const Team& t, const Band& b, const FastVec& v, const O
       }
     }
     SEC_ADD(SEC_BAND);
-    contribute_f(t, SL_PQ, pqf);
+    contribute(t, SL_PQ, (float)pqf);
     SEC_ADD(SEC_REDUCE);
     team_sync(t);
     SEC_ADD(SEC_SYNC);
@@ -695,8 +662,8 @@ __device__ void fast_pcg(const Team& t, const Band& b, const FastVec& v, const O
       }
     }
     SEC_ADD(SEC_BAND);
-    contribute_f(t, SL_RR, rrf);
-    if (op.L == 1) contribute_f(t, SL_RZ, rz1f);
+    contribute(t, SL_RR, (float)rrf);
+    if (op.L == 1) contribute(t, SL_RZ, (float)rz1f);
     SEC_ADD(SEC_REDUCE);
     team_sync(t);
     SEC_ADD(SEC_SYNC);
@@ -813,7 +780,7 @@ __device__ float2* fast_solve(const Team& t, const Band& b, const SweepParams& P
     SEC_ADD(SEC_REFINE);
     contribute(t, SL_RRD, rr);
     if (first) contribute(t, SL_BBD, bb);
-    if (op.L == 1) contribute_f(t, SL_RZ, (float)rz1);
+    if (op.L == 1) contribute(t, SL_RZ, (float)rz1);
     SEC_ADD(SEC_REDUCE);
     team_sync(t);
     SEC_ADD(SEC_SYNC);
@@ -859,6 +826,8 @@ __device__ float2* fast_solve(const Team& t, const Band& b, const SweepParams& P
 __global__ void __launch_bounds__(FAST_THREADS, 1) fast2d_kernel(const SweepParams P) {
   __shared__ double s_red[2 * NSLOT * LRP_MAXBV];
   __shared__ double s_redw[32 * LRP_MAXBV];
+  __shared__ float s_redf[2 * NSLOT * LRP_MAXBV];
+  __shared__ float s_redwf[32 * LRP_MAXBV];
   Team t;
   t.C = P.C;
   t.rank = (P.C > 1) ? (int)cg::this_cluster().block_rank() : 0;
@@ -871,6 +840,8 @@ __global__ void __launch_bounds__(FAST_THREADS, 1) fast2d_kernel(const SweepPara
   t.col = 0;
   t.red = s_red;
   t.redw = s_redw;
+  t.redf = s_redf;
+  t.redwf = s_redwf;
   t.phase = 0;
   const int team = blockIdx.x / P.C;
   const int n = P.step.lv[0].n;

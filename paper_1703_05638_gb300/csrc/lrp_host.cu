@@ -219,6 +219,18 @@ lrp_status lrp_setup_problem(const lrp_problem_desc* desc, void* cuda_stream, lr
     set_error("precision must be LRP_FP64 or LRP_MIXED");
     return LRP_EINVAL;
   }
+  if (d.pde != LRP_PDE_HEAT && d.pde != LRP_PDE_CONVDIFF) {
+    set_error("pde must be LRP_PDE_HEAT or LRP_PDE_CONVDIFF");
+    return LRP_EINVAL;
+  }
+  if (d.pde == LRP_PDE_CONVDIFF) {
+    bool ok = d.precision == LRP_FP64 && !d.kappa_faces && d.conv_nu >= 0 && std::isfinite(d.conv_nu);
+    for (int a = 0; a < d.dim; ++a) ok = ok && std::isfinite(d.wind[a]);
+    if (!ok) {
+      set_error("LRP_PDE_CONVDIFF needs LRP_FP64, no kappa field, a finite conv_nu >= 0 and a finite wind");
+      return LRP_EINVAL;
+    }
+  }
   if (d.prior_kind != LRP_PRIOR_LAPLACE && d.prior_kind != LRP_PRIOR_IDENTITY) {
     set_error("prior_kind must be LRP_PRIOR_LAPLACE or LRP_PRIOR_IDENTITY");
     return LRP_EINVAL;
@@ -282,6 +294,8 @@ lrp_status lrp_setup_problem(const lrp_problem_desc* desc, void* cuda_stream, lr
   P->step.L = P->prior.L = L;
   P->step.has_kappa = has_kappa ? 1 : 0;
   P->prior.has_kappa = 0;
+  P->step.conv = d.pde == LRP_PDE_CONVDIFF ? 1 : 0;
+  P->prior.conv = 0;
   std::vector<std::vector<double>> kcur(d.dim);
   if (has_kappa) {
     size_t off = 0;
@@ -305,6 +319,11 @@ lrp_status lrp_setup_problem(const lrp_problem_desc* desc, void* cuda_stream, lr
   hash = fnv1a(hash, &d.prior_kind, sizeof(int));
   if (d.prior_kind == LRP_PRIOR_IDENTITY) hash = fnv1a(hash, &d.prior_gamma, sizeof(double));
   hash = fnv1a(hash, &d.obs_every, sizeof(int));
+  hash = fnv1a(hash, &d.pde, sizeof(int));
+  if (d.pde == LRP_PDE_CONVDIFF) {
+    hash = fnv1a(hash, &d.conv_nu, sizeof(double));
+    hash = fnv1a(hash, d.wind, sizeof(double) * d.dim);
+  }
   hash = fnv1a(hash, d.obs_xyz, sizeof(double) * d.n_obs * d.dim);
   for (int l = 0; l < L; ++l) {
     const int nl = ((d.n + 1) >> l) - 1;
@@ -322,6 +341,17 @@ lrp_status lrp_setup_problem(const lrp_problem_desc* desc, void* cuda_stream, lr
     P->step.lv[l].ch2 = P->tau * h2inv;
     P->prior.lv[l].ch2 = d.prior_alpha * h2inv;
     P->step.lv[l].dinv = 1.0 / (1.0 + P->step.lv[l].ch2 * 2 * d.dim);
+    for (int a = 0; a < 3; ++a) P->step.lv[l].cw[a] = P->prior.lv[l].cw[a] = 0.0;
+    if (d.pde == LRP_PDE_CONVDIFF) {
+      // I + tau (nu (-Laplace) + w . grad): diffusion in ch2, upwind convection in cw
+      P->step.lv[l].ch2 = P->tau * d.conv_nu * h2inv;
+      double cs = 0.0;
+      for (int a = 0; a < d.dim; ++a) {
+        P->step.lv[l].cw[a] = P->tau * d.wind[a] * (double)(nl + 1);
+        cs += std::fabs(P->step.lv[l].cw[a]);
+      }
+      P->step.lv[l].dinv = 1.0 / (1.0 + P->step.lv[l].ch2 * 2 * d.dim + cs);
+    }
     P->prior.lv[l].dinv = 1.0 / (1.0 + P->prior.lv[l].ch2 * 2 * d.dim);
     P->step.lv[l].dinvd = P->prior.lv[l].dinvd = nullptr;
     P->step.lv[l].dinvf = P->prior.lv[l].dinvf = nullptr;

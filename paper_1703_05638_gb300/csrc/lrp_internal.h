@@ -52,12 +52,14 @@ struct OpLevel {
   const float* kf[3];
   const double* dinvd;  // per-node 1 / diagonal when kappa is given
   const float* dinvf;
+  double cw[3];         // convection-diffusion: c w_a / h (signed; the diffusion part is in ch2)
 };
 
 struct Op {
   int L;        // number of levels
   int Ls;       // levels Ls..L-1 are solved by every CTA of a team in its shared memory
   int has_kappa;
+  int conv;     // 1: the convection-diffusion operator (not symmetric; BiCGStab, FP64)
   OpLevel lv[LRP_MAXLEV];
 };
 

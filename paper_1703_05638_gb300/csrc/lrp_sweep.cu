@@ -99,7 +99,8 @@ lrp_status sweep_enqueue(lrp_problem* Pr, unsigned stages, int nvec, const doubl
   prm.off_q = off;
   off = align_up(off + N0 * BV * tsz);
   prm.off_c = off;
-  off = align_up(off + (mixed ? N0 * BV * tsz : 0));
+  // mixed: the inner correction; convection-diffusion: BiCGStab's shadow residual
+  off = align_up(off + ((mixed || Pr->step.conv) ? N0 * BV * tsz : 0));
   prm.off_e0[0] = off;
   off = align_up(off + N0 * BV * tsz);
   prm.off_e0[1] = off;
@@ -182,7 +183,8 @@ lrp_status sweep_enqueue(lrp_problem* Pr, unsigned stages, int nvec, const doubl
   // Band kernel (2D, kappa = 1, one column per team, FP32 inner): every CTA
   // keeps its band of the finest level and all coarse levels in shared memory.
   bool fast = false;
-  if (Pr->kernel_variant != 1 && Pr->dim == 2 && mixed && BV == 1 && !Pr->step.has_kappa && Pr->L >= 2 &&
+  if (Pr->kernel_variant != 1 && Pr->dim == 2 && mixed && BV == 1 && !Pr->step.has_kappa && !Pr->step.conv &&
+      Pr->L >= 2 &&
       Pr->n <= 128) {
     const int n = Pr->n;
     for (int Cf = C; Cf >= 1; Cf >>= 1) {

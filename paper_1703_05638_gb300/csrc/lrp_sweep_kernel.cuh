@@ -164,7 +164,7 @@ __device__ LRP_SOLVER_FN int vcycle(const Team& t, const Op& op, const WSV<T>& w
                               t.bvs, t.col, omega, last ? (const T*)w.f[0] : (const T*)nullptr, rz);
       ecur[l] ^= 1;
       SEC_ADD(l == 0 ? SEC_BAND : SEC_COARSE);
-      if (last) contribute(t, SL_RZ, rz);
+      if (last) contribute(t, SL_RZ, (T)rz);
       SEC_ADD(SEC_REDUCE);
       team_sync(t);
       SEC_ADD(SEC_SYNC);
@@ -191,7 +191,7 @@ __device__ LRP_SOLVER_FN void pcg_iterate(const Team& t, const Op& op, const WSV
     const int zc = vcycle<T, DIM, KAPPA>(t, op, w, sm, omega, cfg.nu);
     SEC_T0();
     const T* z = w.e[0][zc];
-    const double rz = total(t, SL_RZ);
+    const double rz = total_t<T>(t, SL_RZ);
     SEC_ADD(SEC_REDUCE);
     const T beta = (T)((it_count == 0 || done || !(rz_old > 0.0)) ? 0.0 : rz / rz_old);
     // phase A: p = z + beta p, q = A z + beta q, accumulate p.q
@@ -225,11 +225,11 @@ __device__ LRP_SOLVER_FN void pcg_iterate(const Team& t, const Op& op, const WSV
       pq = (double)pqp;
     }
     SEC_ADD(SEC_OTHER);
-    contribute(t, SL_PQ, pq);
+    contribute(t, SL_PQ, (T)pq);
     SEC_ADD(SEC_REDUCE);
     team_sync(t);
     SEC_ADD(SEC_SYNC);
-    const double pqt = total(t, SL_PQ);
+    const double pqt = total_t<T>(t, SL_PQ);
     SEC_ADD(SEC_REDUCE);
     const T alpha = (T)((done || !(pqt > 0.0)) ? 0.0 : rz / pqt);
     // phase B: x += alpha p, r -= alpha q, first smoother sweep of the next V-cycle
@@ -262,12 +262,12 @@ __device__ LRP_SOLVER_FN void pcg_iterate(const Team& t, const Op& op, const WSV
       rz1 = (double)rz1p;
     }
     SEC_ADD(SEC_OTHER);
-    contribute(t, SL_RR, rr);
-    if (op.L == 1) contribute(t, SL_RZ, rz1);
+    contribute(t, SL_RR, (T)rr);
+    if (op.L == 1) contribute(t, SL_RZ, (T)rz1);
     SEC_ADD(SEC_REDUCE);
     team_sync(t);
     SEC_ADD(SEC_SYNC);
-    const double rrt = total(t, SL_RR);
+    const double rrt = total_t<T>(t, SL_RR);
     SEC_ADD(SEC_REDUCE);
     if (!isfinite(rrt)) {
       ctr.status |= STAT_NONFINITE;
@@ -416,7 +416,7 @@ __device__ LRP_SOLVER_FN double* solve_mixed(const Team& t, const SweepParams& P
     SEC_ADD(SEC_REFINE);
     contribute(t, SL_RRD, rr);
     if (first) contribute(t, SL_BBD, bb);
-    if (op.L == 1) contribute(t, SL_RZ, rz1);
+    if (op.L == 1) contribute(t, SL_RZ, (float)rz1);
     SEC_ADD(SEC_REDUCE);
     team_sync(t);
     SEC_ADD(SEC_SYNC);
@@ -461,16 +461,203 @@ __device__ LRP_SOLVER_FN double* solve_mixed(const Team& t, const SweepParams& P
   return tgt;
 }
 
+// ((I + c L) v)_p for the convection-diffusion operator, L = nu (-Laplace) +
+// w . grad with first-order upwind differences (Sec. 6.2, upwind in place of
+// the paper's SUPG): the diffusion part as op_at (ch2 = c nu / h^2), and per
+// axis with wind, |c w_a / h| on the diagonal and -|c w_a / h| at the
+// upstream neighbour (the low side for w_a > 0). transpose: (I + c L)^T, the
+// same coefficient at the downstream neighbour (the adjoint sweep).
+template <int DIM, class LD>
+__device__ __forceinline__ double op_conv_at(const OpLevel& lv, const LD& ld, int p, int i0, int i1, int i2,
+                                             bool transpose, double& diag) {
+  double v = op_at<double, DIM, false>(lv, ld, p, i0, i1, i2, diag);
+  const int n = lv.n;
+  const int ii[3] = {i0, i1, i2};
+  int stride = 1;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    const double cw = lv.cw[a];
+    if (cw != 0.0) {
+      const double c = fabs(cw);
+      // upstream side: low (-1) for w_a > 0; the transpose reads the other side
+      const bool low = (cw > 0.0) != transpose;
+      const bool inside = low ? ii[a] > 0 : ii[a] < n - 1;
+      v += c * ld(p) - (inside ? c * ld(low ? p - stride : p + stride) : 0.0);
+      diag += c;
+    }
+    stride *= n;
+  }
+  return v;
+}
+
+// Solve (I + c L) x = b for the nonsymmetric convection-diffusion step by
+// BiCGStab (van der Vorst, 1992) with the Jacobi preconditioner applied on
+// the right, in FP64: five phases and team barriers per iteration (the two
+// operator applications need their input's neighbours). Vectors: x in X1,
+// r in w.f[0], shadow residual r^ = r_0 in w.c, p in w.p, v in w.q,
+// D^-1 p and D^-1 s in the two finest smoother buffers, s in place of r,
+// t in X2.
+template <int DIM>
+__device__ LRP_SOLVER_FN double* solve_bicgstab(const Team& t, const SweepParams& P, const Op& op,
+                                                const WSV<double>& w, const double* bsrc, const double* dsrc,
+                                                const double* x0, double* X1, double* X2, bool transpose,
+                                                Ctr& ctr) {
+  const OpLevel& l0 = op.lv[0];
+  const int items = l0.N << t.bvs;
+  const double dinv = l0.dinv;
+  double* r = w.f[0];
+  double* rh = w.c;
+  double* pv = w.p;
+  double* vv = w.q;
+  double* ph = w.e[0][0];
+  double* sh = w.e[0][1];
+  double* tv = X2;
+  auto decomp_at = [&](int it, int& p, int& i0, int& i1, int& i2) {
+    p = it >> t.bvs;
+    decomp<DIM>(l0, p, i0, i1, i2);
+  };
+  // r0 = b - A x0, r^ = r0, x = x0
+  double rr = 0.0, bb = 0.0;
+  {
+    Ld<double> ld{x0, t.bvs, t.col};
+    for (int it = t.g; it < items; it += t.S) {
+      int p, i0, i1, i2;
+      decomp_at(it, p, i0, i1, i2);
+      const double bp = rhs_at(P, t, bsrc, dsrc, p, it);
+      double d, ax = 0.0;
+      if (x0) ax = op_conv_at<DIM>(l0, ld, p, i0, i1, i2, transpose, d);
+      const double rv = bp - ax;
+      r[it] = rv;
+      rh[it] = rv;
+      X1[it] = x0 ? x0[it] : 0.0;
+      pv[it] = 0.0;
+      vv[it] = 0.0;
+      rr += rv * rv;
+      bb += bp * bp;
+    }
+  }
+  contribute(t, SL_RR, rr);
+  contribute(t, SL_BBD, bb);
+  team_sync(t);
+  double rrt = total(t, SL_RR);
+  const double bbt = total(t, SL_BBD);
+  const double tol2 = P.cfg.rtol * P.cfg.rtol * bbt;
+  bool done = !(bbt > 0.0) || rrt <= tol2;
+  if (!isfinite(rrt) || !isfinite(bbt)) {
+    ctr.status |= STAT_NONFINITE;
+    done = true;
+  }
+  double rho = rrt;  // (r^, r0) = ||r0||^2
+  double alpha = 1.0, omg = 1.0, rho_old = 1.0;
+  int it_count = 0;
+  bool all = __syncthreads_and(done);
+  while (!all) {
+    const double beta = (it_count == 0 || done) ? 0.0 : (rho / rho_old) * (alpha / omg);
+    const double omg_p = (it_count == 0 || done) ? 0.0 : omg;
+    // phase A: p = r + beta (p - omega v); p^ = D^-1 p
+    for (int it = t.g; it < items; it += t.S) {
+      const double pn = r[it] + beta * (pv[it] - omg_p * vv[it]);
+      pv[it] = pn;
+      ph[it] = dinv * pn;
+    }
+    team_sync(t);
+    // phase B: v = A p^, (r^, v)
+    double rhv = 0.0;
+    {
+      Ld<double> ld{ph, t.bvs, t.col};
+      for (int it = t.g; it < items; it += t.S) {
+        int p, i0, i1, i2;
+        decomp_at(it, p, i0, i1, i2);
+        double d;
+        const double v = op_conv_at<DIM>(l0, ld, p, i0, i1, i2, transpose, d);
+        vv[it] = v;
+        rhv += rh[it] * v;
+      }
+    }
+    contribute(t, SL_PQ, rhv);
+    team_sync(t);
+    const double rhvt = total(t, SL_PQ);
+    if (!done && !(fabs(rhvt) > 0.0)) {  // breakdown
+      ctr.status |= STAT_NOCONV;
+      done = true;
+    }
+    alpha = done ? 0.0 : rho / rhvt;
+    // phase C: s = r - alpha v (in place of r); s^ = D^-1 s
+    for (int it = t.g; it < items; it += t.S) {
+      const double sv = r[it] - alpha * vv[it];
+      r[it] = sv;
+      sh[it] = dinv * sv;
+    }
+    team_sync(t);
+    // phase D: t = A s^, (t, s), (t, t)
+    double ts = 0.0, tt = 0.0;
+    {
+      Ld<double> ld{sh, t.bvs, t.col};
+      for (int it = t.g; it < items; it += t.S) {
+        int p, i0, i1, i2;
+        decomp_at(it, p, i0, i1, i2);
+        double d;
+        const double tvv = op_conv_at<DIM>(l0, ld, p, i0, i1, i2, transpose, d);
+        tv[it] = tvv;
+        ts += tvv * r[it];
+        tt += tvv * tvv;
+      }
+    }
+    contribute(t, 6, ts);
+    contribute(t, 7, tt);
+    team_sync(t);
+    const double tst = total(t, 6), ttt = total(t, 7);
+    omg = (done || !(ttt > 0.0)) ? 0.0 : tst / ttt;
+    // phase E: x += alpha p^ + omega s^, r = s - omega t, (r^, r), (r, r)
+    double rhr = 0.0;
+    rr = 0.0;
+    for (int it = t.g; it < items; it += t.S) {
+      X1[it] += alpha * ph[it] + omg * sh[it];
+      const double rn = r[it] - omg * tv[it];
+      r[it] = rn;
+      rhr += rh[it] * rn;
+      rr += rn * rn;
+    }
+    contribute(t, SL_RZ, rhr);
+    contribute(t, SL_RR, rr);
+    team_sync(t);
+    const double rhrt = total(t, SL_RZ);
+    rrt = total(t, SL_RR);
+    if (!isfinite(rrt)) {
+      ctr.status |= STAT_NONFINITE;
+      done = true;
+    }
+    const bool conv = rrt <= tol2;
+    if (!done && !conv && !(omg != 0.0 && fabs(rhrt) > 0.0)) {  // breakdown
+      ctr.status |= STAT_NOCONV;
+      done = true;
+    }
+    done = done || conv;
+    rho_old = rho;
+    rho = rhrt;
+    ++it_count;
+    const bool capped = it_count >= P.cfg.maxit;
+    all = __syncthreads_and(done) || capped;
+    if (capped && !__syncthreads_and(done)) ctr.status |= STAT_NOCONV;
+  }
+  ctr.iters += it_count;
+  ctr.iters_max = max(ctr.iters_max, it_count);
+  ctr.max_res = fmax(ctr.max_res, bbt > 0.0 ? sqrt(rrt / bbt) : 0.0);
+  ctr.solves += 1;
+  return X1;
+}
+
 template <typename T, int DIM, bool MIXED>
 __device__ __forceinline__ double* solve_any(const Team& t, const SweepParams& P, const Op& op,
                                              const WSV<T>& w, const SmemLv<T>& sm, const double* bsrc,
                                              const double* dsrc, const double* x0, double* X1,
-                                             double* X2, Ctr& ctr) {
+                                             double* X2, Ctr& ctr, bool transpose = false) {
   if constexpr (MIXED) {
     if (op.has_kappa)
       return solve_mixed<DIM, true>(t, P, op, w, sm, bsrc, dsrc, x0, X1, X2, ctr);
     return solve_mixed<DIM, false>(t, P, op, w, sm, bsrc, dsrc, x0, X1, X2, ctr);
   } else {
+    if (op.conv) return solve_bicgstab<DIM>(t, P, op, w, bsrc, dsrc, x0, X1, X2, transpose, ctr);
     if (op.has_kappa) return solve_fp64<DIM, true>(t, P, op, w, sm, bsrc, dsrc, x0, X1, ctr);
     return solve_fp64<DIM, false>(t, P, op, w, sm, bsrc, dsrc, x0, X1, ctr);
   }
@@ -494,6 +681,8 @@ template <typename T, int DIM, bool MIXED>
 __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
   __shared__ double s_red[2 * NSLOT * LRP_MAXBV];
   __shared__ double s_redw[32 * LRP_MAXBV];
+  __shared__ float s_redf[2 * NSLOT * LRP_MAXBV];
+  __shared__ float s_redwf[32 * LRP_MAXBV];
   extern __shared__ __align__(16) unsigned char s_dyn[];
   Team t;
   t.C = P.C;
@@ -507,6 +696,8 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
   t.col = t.g & (P.BV - 1);
   t.red = s_red;
   t.redw = s_redw;
+  t.redf = s_redf;
+  t.redwf = s_redwf;
   t.phase = 0;
   const int team = blockIdx.x / P.C;
 #ifdef LRP_SECTION_TIMERS
@@ -620,7 +811,7 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
       const int qi = q ? buf_index(w.dbuf, q) : cur;
       double* X1 = w.dbuf[(qi + 1) % 3];
       double* X2 = w.dbuf[(qi + 2) % 3];
-      double* res = solve_any<T, DIM, MIXED>(t, P, P.step, w, sm, q, dsrc, q, X1, X2, ctr);
+      double* res = solve_any<T, DIM, MIXED>(t, P, P.step, w, sm, q, dsrc, q, X1, X2, ctr, true);
       q = res;
     }
     if (q) {

@@ -57,6 +57,8 @@ struct Team {
   int C, rank, NT, tid, g, S, BV, bvs, col;
   double* red;   // [2][NSLOT][LRP_MAXBV] CTA totals, two banks (shared memory)
   double* redw;  // [32][LRP_MAXBV] warp partials (shared memory)
+  float* redf;   // the same for the FP32 reductions of the inner PCG (separate
+  float* redwf;  //   arrays: no aliasing with FP64 totals other CTAs still read)
   // Team barriers passed so far (identical in every thread of the team).
   // A total is contributed before barrier k into bank k&1 and read after it;
   // its bank is next written before barrier k+2, which no CTA reaches before
@@ -96,6 +98,49 @@ __device__ __forceinline__ void contribute(const Team& t, int slot, double v) {
   __syncthreads();
 }
 
+// FP32 version for the inner PCG's dot products (the FP64 pipe's ~64-cycle
+// dependent adds made the FP64 trees a large part of a PCG iteration; the
+// inner solve needs its dot products to FP32 accuracy only). Same
+// deterministic order and bank protocol as the FP64 version.
+__device__ __forceinline__ void contribute(const Team& t, int slot, float v) {
+  for (int off = 16; off >= t.BV; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  const int lane = t.tid & 31, w = t.tid >> 5;
+  if (lane < t.BV) t.redwf[w * LRP_MAXBV + lane] = v;
+  __syncthreads();
+  const int nw = t.NT >> 5;
+  if (t.BV == 1) {
+    if (w == 0) {
+      float s = lane < nw ? t.redwf[lane * LRP_MAXBV] : 0.f;
+      for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+      if (lane == 0) t.redf[((t.phase & 1) * NSLOT + slot) * LRP_MAXBV] = s;
+    }
+  } else if (t.tid < t.BV) {
+    float s = 0.f;
+    for (int i = 0; i < nw; ++i) s += t.redwf[i * LRP_MAXBV + t.tid];
+    t.redf[((t.phase & 1) * NSLOT + slot) * LRP_MAXBV + t.tid] = s;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ double total_f(const Team& t, int slot) {
+  const int idx = (((t.phase - 1) & 1) * NSLOT + slot) * LRP_MAXBV + t.col;
+  if (t.C == 1) return (double)t.redf[idx];
+  cg::cluster_group cl = cg::this_cluster();
+  if (t.BV == 1) {
+    const int lane = t.tid & 31;
+    float s = lane < t.C ? *cl.map_shared_rank(t.redf + idx, lane) : 0.f;
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    return (double)s;
+  }
+  float s = 0.f;
+  for (int r = 0; r < t.C; ++r) s += *cl.map_shared_rank(t.redf + idx, r);
+  return (double)s;
+}
+
+// total of a slot contributed in the inner type T (float: total_f)
+template <typename T>
+__device__ __forceinline__ double total_t(const Team& t, int slot);
+
 // Team-wide total of slot for this thread's column; valid after a team_sync
 // that followed the contribute. Every CTA sums the ranks in the same order,
 // so all CTAs obtain bit-identical totals (and take identical branches).
@@ -114,6 +159,15 @@ __device__ __forceinline__ double total(const Team& t, int slot) {
   double s = 0.0;
   for (int r = 0; r < t.C; ++r) s += *cl.map_shared_rank(t.red + idx, r);
   return s;
+}
+
+template <>
+__device__ __forceinline__ double total_t<double>(const Team& t, int slot) {
+  return total(t, slot);
+}
+template <>
+__device__ __forceinline__ double total_t<float>(const Team& t, int slot) {
+  return total_f(t, slot);
 }
 
 __device__ __forceinline__ uint32_t fdiv(uint32_t x, const FastDiv& f) {
@@ -290,31 +344,44 @@ struct V3 {
 // One damped Jacobi sweep e_out = e_in + omega (f - A e_in) / d. If rz_r is
 // non-NULL, accumulates rz_r * e_out into rz (used for r.z after the last
 // post-smoothing sweep on the finest level).
+// The item loop of a Jacobi sweep with the output marked __restrict__ (it
+// is a different array from the inputs): the compiler may then issue the
+// loads of the next SWEEP_UNROLL items before the stores of the earlier
+// ones, which the ordinary loop (a store could alias a later load) forbids.
+#ifndef LRP_SWEEP_UNROLL
+#define LRP_SWEEP_UNROLL 1
+#endif
 template <typename T, int DIM, bool KAPPA>
-__device__ __forceinline__ void mg_sweep(const OpLevel& lv, T* eo,
-                                         const T* ei, const T* f,
-                                         int start, int stride, int bvs, int col, T omega,
-                                         const T* rz_r, double& rz) {
+__device__ __forceinline__ T mg_sweep_items(const OpLevel& lv, T* __restrict__ eo, const T* ei, const T* f,
+                                            int start, int stride, int bvs, int col, T omega, const T* rz_r) {
   const int items = lv.N << bvs;
   Ld<T> ld{ei, bvs, col};
   T acc = T(0);  // per-thread partial in the inner type
-  batched_loop<V2<T>>(
-      start, items, stride,
-      [&](int it) {
+  for (int it0 = start; it0 < items; it0 += LRP_SWEEP_UNROLL * stride) {
+#pragma unroll
+    for (int u = 0; u < LRP_SWEEP_UNROLL; ++u) {
+      const int it = it0 + u * stride;
+      if (it < items) {
         const int p = it >> bvs;
         int i0, i1, i2;
         decomp<DIM>(lv, p, i0, i1, i2);
         T d;
         const T ae = op_at<T, DIM, KAPPA>(lv, ld, p, i0, i1, i2, d);
-        V2<T> r;
-        r.a = ei[it] + omega * (f[it] - ae) * dinv_at<T, KAPPA>(lv, p);
-        r.b = rz_r ? rz_r[it] : T(0);
-        return r;
-      },
-      [&](int it, const V2<T>& r) {
-        eo[it] = r.a;
-        if (rz_r) acc += r.b * r.a;
-      });
+        const T e = ei[it] + omega * (f[it] - ae) * dinv_at<T, KAPPA>(lv, p);
+        eo[it] = e;
+        if (rz_r) acc += rz_r[it] * e;
+      }
+    }
+  }
+  return acc;
+}
+
+template <typename T, int DIM, bool KAPPA>
+__device__ __forceinline__ void mg_sweep(const OpLevel& lv, T* eo,
+                                         const T* ei, const T* f,
+                                         int start, int stride, int bvs, int col, T omega,
+                                         const T* rz_r, double& rz) {
+  const T acc = mg_sweep_items<T, DIM, KAPPA>(lv, eo, ei, f, start, stride, bvs, col, omega, rz_r);
   if (rz_r) rz += (double)acc;
 }
 

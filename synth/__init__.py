@@ -133,6 +133,9 @@ class ProblemSpec:
     seed: int = 0
     prior_kind: int = 0       # 0: (I + alpha L0)^-2; 1: gamma I
     prior_gamma: float = 0.0
+    pde: str = "heat"         # "heat" or "convdiff" (-nu Laplace + wind . grad)
+    conv_nu: float = 0.0
+    wind: tuple = (0.0, 0.0, 0.0)
 
     @property
     def nx(self) -> int:
@@ -170,6 +173,22 @@ def workload(name: str, **overrides) -> ProblemSpec:
     return spec
 
 
+def _patch_sensors(n: int):
+    """Point sensors on every node of the 9 square patches of side 1/16
+    (1/256 of the domain) centred at (i/4, j/4), i, j = 1..3: the nodes whose
+    coordinates lie in the half-open square [c - 1/32, c + 1/32)^2."""
+    h = 1.0 / (n + 1)
+    half = (n + 1) // 32  # nodes on each side of a centre (n + 1 a multiple of 32)
+    pts = []
+    for cj in (1, 2, 3):
+        for ci in (1, 2, 3):
+            bi, bj = ci * (n + 1) // 4 - half, cj * (n + 1) // 4 - half
+            for dj in range(2 * half):
+                for di in range(2 * half):
+                    pts.append(((bi + di) * h, (bj + dj) * h))
+    return np.asarray(pts)
+
+
 def paper_heat_spec(ratio: float, nt: int = 30) -> ProblemSpec:
     """The 2D heat experiment of the paper's numerical section on finite
     differences: 64 x 64 cells (63^2 interior nodes), nt = 30, T = 1; 9
@@ -181,19 +200,28 @@ def paper_heat_spec(ratio: float, nt: int = 30) -> ProblemSpec:
     step by tau h^2 and the prior term each node by h^2, so Gamma_prior =
     10 I fixes beta_prior h^2 = 0.1 and Gamma_noise^-1 = 0.1 ratio tau)."""
     n = 63
-    h = 1.0 / (n + 1)
-    pts = []
-    for cj in (1, 2, 3):
-        for ci in (1, 2, 3):
-            base_i, base_j = 16 * ci - 2, 16 * cj - 2  # node positions (i+1)h in [c - 2h, c + 2h)
-            for dj in range(4):
-                for di in range(4):
-                    pts.append(((base_i + di) * h, (base_j + dj) * h))
     tau = 1.0 / nt
     sigma = math.sqrt(10.0 / (ratio * tau))
     return ProblemSpec(name=f"paper_heat_r{ratio:g}", dim=2, n=n, nt=nt, T=1.0, prior_alpha=0.0, sigma=sigma,
-                       obs_every=1, sensors=np.asarray(pts), k=50, block=1, seed=1000 + 5,
+                       obs_every=1, sensors=_patch_sensors(n), k=50, block=1, seed=1000 + 5,
                        prior_kind=1, prior_gamma=10.0)
+
+
+def paper_convdiff_spec(nu: float, ratio: float = 1e4, nt: int = 90) -> ProblemSpec:
+    """The convection-diffusion experiment of the paper's numerical section on
+    finite differences: 32 x 32 cells (31^2 interior nodes), L = -nu Laplace
+    + w . grad with w = (0, 1) (upwind differences in place of SUPG), zero
+    Dirichlet data (the perturbation problem: the inflow data of the paper's
+    example only shift the state and leave the Hessian unchanged), nt = 90,
+    T = 1, the 9 sensor patches of the heat experiment (2 x 2 nodes each on
+    this grid), Gamma_prior = 10 I and beta_noise = ratio * beta_prior
+    (sigma^2 = 10 / (ratio * tau), as for the heat experiment)."""
+    n = 31
+    tau = 1.0 / nt
+    sigma = math.sqrt(10.0 / (ratio * tau))
+    return ProblemSpec(name=f"paper_convdiff_nu{nu:g}", dim=2, n=n, nt=nt, T=1.0, prior_alpha=0.0, sigma=sigma,
+                       obs_every=1, sensors=_patch_sensors(n), k=50, block=1, seed=1000 + 6,
+                       prior_kind=1, prior_gamma=10.0, pde="convdiff", conv_nu=nu, wind=(0.0, 1.0, 0.0))
 
 
 def small_spec(dim: int = 2, n: int = 7, nt: int = 12, obs_every: int = 3,

@@ -476,3 +476,76 @@ def test_golden_files_are_consistent():
     rows = _read_golden("apply_heat3d_63.txt")
     nodes = np.array([int(r[0]) for r in rows])
     assert np.array_equal(nodes, synth.query_nodes(63 ** 3, 256, 2028))
+
+
+# ------------------------------------------------- convection-diffusion (Sec. 6.2)
+@pytest.mark.parametrize("wind", [(0.0, 1.0), (-1.0, 0.5)])
+def test_upwind_convection_linear_field(wind):
+    """Upwind w . grad_h of the coordinate field x_a is w_a at every node whose
+    upstream neighbour is inside the grid or the inflow boundary (where the
+    Dirichlet value 0 equals x_a); the upwind direction is the low side for
+    w_a > 0. Catches a downwind stencil, a wrong sign or a missing 1/h."""
+    n = 9
+    W = operators.upwind_convection(n, 2, wind)
+    x = (np.arange(n) + 1.0) / (n + 1)
+    for a in range(2):
+        field = np.kron(np.ones(n), x) if a == 0 else np.kron(x, np.ones(n))  # x_0 fastest
+        got = (W @ field).reshape(n, n)  # [i1, i0]
+        other = 1 - a
+        want_part = wind[a]
+        # contributions of the other axis vanish on this field except at its
+        # outflow/inflow nodes; compare where both axes see interior upstream data
+        if wind[a] > 0:
+            sl_a = slice(0, n)
+        else:
+            sl_a = slice(0, n - 1)
+        if wind[other] == 0:
+            sl_o = slice(0, n)
+        elif wind[other] > 0:
+            sl_o = slice(1, n)
+        else:
+            sl_o = slice(0, n - 1)
+        sub = got[sl_a, sl_o] if a == 1 else got[sl_o, sl_a]
+        np.testing.assert_allclose(sub, want_part, rtol=1e-12, atol=1e-12)
+
+
+def test_upwind_step_closed_form():
+    """Pure advection (nu = 0) in 1D: one implicit-Euler upwind step
+    (1 + c) y_i - c y_{i-1} = y0_i, c = tau w / h, from a unit pulse at j has
+    y_i = c^(i-j) / (1 + c)^(i-j+1) for i >= j and 0 upstream of j."""
+    n, j, tau, w = 15, 4, 0.05, 1.0
+    A = operators.convection_diffusion(n, 1, 0.0, (w,)).toarray()
+    y0 = np.zeros(n)
+    y0[j] = 1.0
+    y = np.linalg.solve(np.eye(n) + tau * A, y0)
+    c = tau * w * (n + 1)
+    want = np.array([c ** (i - j) / (1 + c) ** (i - j + 1) if i >= j else 0.0 for i in range(n)])
+    np.testing.assert_allclose(y, want, rtol=1e-12, atol=1e-15)
+
+
+def _convdiff_spec(**kw):
+    base = dict(dim=2, n=7, nt=10, obs_every=2, sensors=synth.uniform_sensors(6, 2, 2),
+                pde="convdiff", conv_nu=1e-2, wind=(0.0, 1.0))
+    base.update(kw)
+    return _spec(**base)
+
+
+def test_convdiff_adjoint_and_brute_force():
+    """The nonsymmetric operator: <F u, w> = <u, F^T w> to 1e-12 (the adjoint
+    steps solve with the transpose), F equals dense powers B (I + tau L)^-n,
+    and the explicit F^T equals the transpose of the explicit F. Catches a
+    forgotten transpose in the adjoint sweep."""
+    P = Problem(_convdiff_spec())
+    assert abs(P.L - P.L.T).max() > 1.0  # genuinely nonsymmetric
+    r = synth.rng(19)
+    u = r.standard_normal((P.nx, 3))
+    w = r.standard_normal((P.n_data, 3))
+    np.testing.assert_allclose(np.sum(P.forward(u) * w, axis=0), np.sum(u * P.adjoint(w), axis=0), rtol=1e-12)
+    Sinv = np.linalg.inv(np.eye(P.nx) + P.tau * P.L.toarray())
+    B = P.B.toarray()
+    rows = [B @ np.linalg.matrix_power(Sinv, s) for s in P.steps]
+    F = P.forward_explicit()
+    np.testing.assert_allclose(F, np.vstack(rows), rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(P.adjoint(np.eye(P.n_data)), F.T, rtol=1e-12, atol=1e-15)
+    H = P.hessian_apply(np.eye(P.nx))
+    assert np.max(np.abs(H - H.T)) <= 1e-12 * np.max(np.abs(H))
