@@ -573,6 +573,8 @@ def main():
     ap.add_argument("--team-ctas", type=int, default=0)
     ap.add_argument("--team-cols", type=int, default=0)
     ap.add_argument("--mg-nu", type=int, default=0)
+    ap.add_argument("--threads", type=int, default=0, help="threads per CTA (256 or 512; profiling)")
+    ap.add_argument("--mg-levels", type=int, default=0, help="time-step hierarchy depth (profiling)")
     ap.add_argument("--mode", default="posterior", choices=["posterior", "apply", "serve", "batched", "paper"],
                     help="posterior: the whole hot path per step; apply: one Hessian apply per step "
                          "(kernel-level measurement and profiling); serve: the serving workload alone")
@@ -661,7 +663,13 @@ def main():
         tuning["team_cols"] = args.team_cols
     if args.mg_nu:
         tuning["mg_nu"] = args.mg_nu
+    if args.mg_levels:
+        tuning["mg_levels"] = args.mg_levels
     G = lrp.lrp_setup_problem(spec, precision=precision, stream=stream, **tuning)
+    if args.threads:
+        t = lrp.lrp_problem_tuning(G)
+        t["threads"] = args.threads
+        lrp.lrp_set_tuning(G, t)
     if not args.no_autotune and not tuning:
         lrp.lrp_autotune(G, args.block)
     nx = G.nx
