@@ -23,6 +23,10 @@ Modules and the passages they follow:
 * ``posterior``  — exact posterior covariance (Sec. 2 Eq. (postcov1); Sec. 6
   Eq. (postvar)), the Sherman-Morrison-Woodbury low-rank form (Sec. 2), the
   posterior mean, pointwise variance and samples.
+* ``lowrank``    — the low-rank matrix-vector product of Sec. 4
+  Algorithm 1 (state and adjoint trajectories truncated to eps_0, the
+  adjoint's data observed from the truncated state), the Ritz values of a
+  nonsymmetric Hessenberg matrix and the threshold-stopped Arnoldi run.
 * ``timefactors``— the low-rank-in-time factorisation Y ~ W V^T (Sec. 3) by
   truncated SVD of the full trajectory, and the streaming recompression the
   GPU uses (thin QR of [W | new columns], small SVD, truncation; Sec. 4).

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import synth
-from oracle import operators, observe, posterior, spectrum, timefactors
+from oracle import lowrank, operators, observe, posterior, spectrum, timefactors
 from oracle.problem import Problem
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -549,3 +549,117 @@ def test_convdiff_adjoint_and_brute_force():
     np.testing.assert_allclose(P.adjoint(np.eye(P.n_data)), F.T, rtol=1e-12, atol=1e-15)
     H = P.hessian_apply(np.eye(P.nx))
     assert np.max(np.abs(H - H.T)) <= 1e-12 * np.max(np.abs(H))
+
+
+# ---------------------------------------------------------------- low-rank product, Arnoldi (Sec. 4)
+def _norm2(A):
+    return float(np.linalg.norm(np.asarray(A), 2))
+
+
+@pytest.mark.parametrize("pde", ["heat", "convdiff"])
+def test_lowrank_apply_exact_without_truncation(pde):
+    """Sec. 4 Algorithm 1's product with nothing discarded (eps_0 = 0, no
+    rank cap) is the exact Htilde x and H_mis x (Sec. 2 Eq. (prior_pre)).
+    Catches a wrong step of the pipeline: an off-by-one time index in the
+    observed rows of the truncated trajectory, the wrong column of the
+    adjoint trajectory, a missing 1/sigma^2 or prior factor."""
+    P = Problem(_convdiff_spec() if pde == "convdiff" else _spec(n=7, nt=12, obs_every=3))
+    x = synth.normal_block(P.nx, 1, 41)[:, 0]
+    got, info = lowrank.lowrank_hessian_apply(P, x, 0.0, 10 ** 6, 5)
+    want = P.hessian_apply(x)
+    assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
+    assert info["err_y"] <= 1e-14 and info["err_q"] <= 1e-14
+    got_m, _ = lowrank.lowrank_hessian_apply(P, x, 0.0, 10 ** 6, 4, misfit_only=True)
+    want_m = P.misfit_apply(x)
+    assert np.max(np.abs(got_m - want_m)) <= 1e-12 * np.max(np.abs(want_m))
+
+
+def test_adjoint_trajectory_first_column_is_adjoint():
+    """q_1 of the backward recursion is F^T d (Sec. 6 Eq. (postvar) with
+    K^{-T}), and the columns past the last observed step are zero."""
+    P = Problem(_spec(n=7, nt=13, obs_every=3))
+    d = synth.normal_block(P.n_data, 1, 42)[:, 0]
+    Q = lowrank.adjoint_trajectory(P, d)
+    np.testing.assert_allclose(Q[:, 0], P.adjoint(d), rtol=1e-13, atol=1e-15)
+    assert not np.any(Q[:, P.steps[-1]:])
+    assert np.all(np.linalg.norm(Q[:, :P.steps[-1]], axis=0) > 0)
+
+
+@pytest.mark.parametrize("tol", [1e-4, 1e-6])
+def test_lowrank_apply_error_bound(tol):
+    """With truncation the product differs from Htilde x by at most
+    ||R^-1|| (||F|| ||B|| tol ||Y||_F / sigma^2 + tol ||Q||_F) (the streaming
+    truncation keeps ||Y - W V^T||_F <= tol ||Y||_F for both trajectories;
+    ||Q||_F of the truncated data is within O(tol) of the exact one, a 1 %
+    margin). The error is genuinely there, and the product is no longer
+    symmetric (the reason for Arnoldi in Sec. 4), by at most twice the bound.
+    An off-by-one time index in the adjoint's data or a wrong row of V makes
+    the error O(||Htilde x||) and fails the bound."""
+    P = Problem(_spec(n=7, nt=40, obs_every=2, sensors=synth.uniform_sensors(8, 2, 4)))
+    x = synth.normal_block(P.nx, 2, 43)
+    got, info = lowrank.lowrank_hessian_apply(P, x[:, 0], tol, 40, 8)
+    want = P.hessian_apply(x[:, 0])
+    z = P.prior_half(x[:, 0])
+    Y = P.trajectory(z)
+    Q = lowrank.adjoint_trajectory(P, P.forward(z) / P.sigma ** 2)
+    Rinv = P.prior_half(np.eye(P.nx))
+    F = P.forward_explicit()
+    bound = _norm2(Rinv) * (_norm2(F) * _norm2(P.B.toarray()) * tol * np.linalg.norm(Y) / P.sigma ** 2
+                            + 1.01 * tol * np.linalg.norm(Q))
+    err = np.linalg.norm(got - want)
+    assert 0.0 < err <= bound, (err, bound)
+    assert info["err_y"] <= tol and info["err_q"] <= tol and info["rank_y"] < P.nx
+    got2, _ = lowrank.lowrank_hessian_apply(P, x[:, 1], tol, 40, 8)
+    asym = abs(x[:, 1] @ got - x[:, 0] @ got2)
+    assert 0.0 < asym <= 2 * bound * max(np.linalg.norm(x[:, 0]), np.linalg.norm(x[:, 1])) * 1.5
+
+
+def test_ritz_nonsym_known_spectrum_and_residual_estimate():
+    """Algorithm 1 on a nonsymmetric matrix with a prescribed spectrum (a
+    complex pair included): after n steps the Ritz values are that spectrum;
+    after m < n steps the estimate |h_{m+1,m}| |e_m^T y| equals the true
+    residual ||A V_m y - theta V_m y|| of every real Ritz pair (the Arnoldi
+    relation A V_m = V_{m+1} H). Catches a transposed H, a wrong row of the
+    estimate or an unsorted spectrum."""
+    r = synth.rng(44)
+    n = 12
+    lam = np.array([9.0, 7.5, 6.0, 4.0, 3.0, 2.0, 1.0, 0.5, 0.25, 0.125])
+    T = np.zeros((n, n))
+    T[:10, :10] = np.diag(lam)
+    T[10:, 10:] = [[-1.0, 2.0], [-2.0, -1.0]]  # eigenvalues -1 +- 2i
+    S = r.standard_normal((n, n)) + 3 * np.eye(n)
+    A = S @ T @ np.linalg.inv(S)
+    v1 = r.standard_normal(n)
+    V, H = spectrum.arnoldi_mgs(lambda v: A @ v, v1, n)
+    got, _, _ = lowrank.ritz_nonsym(H, n)
+    want = np.concatenate([lam, [-1 + 2j, -1 - 2j]])
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-8)
+    m = 6
+    V, H = spectrum.arnoldi_mgs(lambda v: A @ v, v1, m)
+    theta, Yv, res = lowrank.ritz_nonsym(H, m)
+    for i in range(m):
+        if abs(theta[i].imag) > 0:
+            continue
+        y = V[:, :m] @ Yv[:, i].real
+        true = np.linalg.norm(A @ y - theta[i].real * y)
+        assert abs(true - res[i]) <= 1e-9 * np.abs(A).max()
+
+
+def test_arnoldi_threshold_rule_symmetric_operator():
+    """The threshold stop of Sec. 6.1 on the exact (symmetric) Htilde: the
+    Ritz values above eps are the eigenvalues above eps of the explicit
+    matrix, in number and value, every Ritz value is real, and the Arnoldi
+    relation Htilde V_m = V_{m+1} H holds."""
+    P = Problem(_spec(n=7, nt=12, obs_every=3, sensors=synth.uniform_sensors(6, 2, 5)))
+    lam, _ = spectrum.eig_dense(P.hessian_explicit())
+    eps = lam[4] * 0.5 + lam[5] * 0.5  # between the 5th and 6th eigenvalue
+    v1 = synth.normal_block(P.nx, 1, 45)[:, 0]
+    m, V, H, theta, res = lowrank.arnoldi_threshold(P.hessian_apply, v1, eps, 1e-10, 40)
+    above = theta.real >= eps
+    assert m < 40 and int(np.sum(above)) == 5
+    np.testing.assert_allclose(theta.real[above], lam[:5], rtol=1e-9)
+    assert np.max(np.abs(theta.imag)) <= 1e-10 * lam[0]
+    # the Arnoldi relation holds to rounding (single MGS lets orthogonality
+    # decay as Ritz values converge; the relation does not depend on it)
+    AV = np.column_stack([P.hessian_apply(V[:, j]) for j in range(m)])
+    assert np.max(np.abs(AV - V @ H)) <= 1e-12 * lam[0]
