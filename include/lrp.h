@@ -81,9 +81,21 @@ enum {
 enum {
   LRP_PRIOR_PRECOND = 0,      /* default: Y = Htilde X */
   LRP_MISFIT_ONLY = 1u << 0,  /* Y = H_mis X (no prior factors) */
-  LRP_KEEP_TRAJ_FACTORS = 1u << 1 /* also compress the forward trajectory of
-                                     each column to low-rank-in-time factors
-                                     Y ~ W V^T (Sec. 3); ranks in the stats */
+  LRP_KEEP_TRAJ_FACTORS = 1u << 1, /* also compress the forward trajectory of
+                                      each column to low-rank-in-time factors
+                                      Y ~ W V^T (Sec. 3); ranks in the stats */
+  LRP_LOWRANK_SOURCE = 1u << 2     /* the product of Sec. 4 Algorithm 1 "up to the
+                                      truncation tolerance": the state trajectory
+                                      and the adjoint trajectory are kept as
+                                      W V^T truncated to time_trunc_tol (rank cap
+                                      time_rank_max), the adjoint's data are the
+                                      observations of the truncated state and the
+                                      result is the truncated adjoint's first
+                                      step (then the prior factor). No longer
+                                      exactly symmetric: the operator of
+                                      lrp_arnoldi. Ranks and truncation errors of
+                                      both trajectories in the stats. Not with
+                                      LRP_KEEP_TRAJ_FACTORS. */
 };
 
 typedef struct lrp_problem lrp_problem;     /* opaque, library-owned */
@@ -154,6 +166,8 @@ typedef struct {
   int time_rank_max;        /* largest time rank of the kept trajectory factors (0 if not kept) */
   double time_trunc_err;    /* largest certified relative truncation error bound of the factors */
   double ms;                /* wall time of the call */
+  int adj_rank_max;         /* LRP_LOWRANK_SOURCE: largest time rank of the adjoint trajectory factors */
+  double adj_trunc_err;     /* LRP_LOWRANK_SOURCE: their largest certified relative truncation error */
 } lrp_apply_stats;
 
 typedef struct {
@@ -313,6 +327,70 @@ typedef struct {
 lrp_status lrp_batch_lowrank_posterior(lrp_problem* const* probs, int count, int k, int block, double eig_tol,
                                        int use_graph, int max_steps, lrp_posterior** outs,
                                        lrp_lanczos_stats* stats, lrp_batch_stats* bst);
+
+/* ---------------------------------------------------------------------------
+ * Arnoldi process of Sec. 4 Algorithm 1, as printed: single vectors; step j
+ * applies the operator to v_j, orthogonalises the result against v_1 .. v_j
+ * one at a time (modified Gram-Schmidt; the coefficients are column j of the
+ * Hessenberg matrix H), H_{j+1,j} = its norm, v_{j+1} = it / H_{j+1,j}.
+ * The operator is Htilde (flags 0), H_mis (LRP_MISFIT_ONLY) or the truncated
+ * product of Algorithm 1 (LRP_LOWRANK_SOURCE, see lrp_hessian_apply), which
+ * is not exactly symmetric: hence Arnoldi rather than Lanczos (Sec. 4).
+ * Ritz values: the eigenvalues of the leading m x m block of H
+ * (lrp_hessenberg_eig), possibly complex. Ritz vectors of the real ones by
+ * back substitution on the Schur factor; residual estimate
+ * |H_{m+1,m}| |e_m^T y| (||y|| = 1).
+ * Stops after max_steps steps, on an invariant subspace, or once the wanted
+ * Ritz values all have residual estimates <= eig_tol |theta_1| (eig_tol 0 ->
+ * 1e-6): with eig_threshold > 0 (the threshold epsilon of Sec. 6.1) the
+ * wanted ones are those with real part >= eig_threshold, and some Ritz value
+ * must lie below it; otherwise the k leading ones. A complex Ritz value
+ * among the wanted ones keeps the run going. The test runs after every step
+ * up to 32 steps, then every floor(m/16)-th step.
+ * Outputs (each may be NULL; host or device):
+ *   theta_re, theta_im [max_steps]: the m Ritz values of the last H_m by
+ *     decreasing real part;
+ *   H [(max_steps+1) x max_steps], column-major, ld max_steps+1 (zero beyond
+ *     column m);
+ *   ranks_y, ranks_q [max_steps] (host): with LRP_LOWRANK_SOURCE, the time
+ *     ranks of the state and adjoint trajectory factors at each step
+ *     (0 otherwise);
+ *   out: a posterior from the wanted real Ritz pairs with theta > 0, the
+ *     Ritz vectors orthonormalised (block CGS2) in order of decreasing theta
+ *     (not with LRP_MISFIT_ONLY).
+ * start: nx vector (host or device) or NULL (a fixed pseudo-random vector).
+ * Returns LRP_ENOCONV (outputs written) if max_steps is reached first or a
+ * solve missed its tolerance; LRP_EINVAL for max_steps outside
+ * 1..min(nx, 2048), k < 1 without a threshold, or LRP_KEEP_TRAJ_FACTORS. */
+typedef struct {
+  int n_steps;           /* Arnoldi steps m (Hessian applications) */
+  int k_converged;       /* wanted real Ritz values that met the test (0 if it failed) */
+  int n_complex;         /* Ritz values of H_m with nonzero imaginary part */
+  double max_imag;       /* largest |Im theta| / |theta_1| */
+  double hess_asym;      /* ||H_m - H_m^T||_F / ||H_m||_F */
+  double max_ritz_resid; /* largest residual estimate of the wanted pairs / |theta_1| */
+  int time_rank_max;     /* LRP_LOWRANK_SOURCE: largest state-trajectory rank over the steps */
+  int adj_rank_max;      /* LRP_LOWRANK_SOURCE: largest adjoint-trajectory rank over the steps */
+  double ms;             /* wall time of the call */
+  double ms_apply;       /* wall time of the operator applications */
+} lrp_arnoldi_stats;
+lrp_status lrp_arnoldi(lrp_problem* p, int max_steps, int k, double eig_tol, double eig_threshold,
+                       unsigned flags, const double* start, double* theta_re, double* theta_im,
+                       double* H, int* ranks_y, int* ranks_q, lrp_posterior** out,
+                       lrp_arnoldi_stats* st);
+
+/* Eigenvalues of a real upper Hessenberg matrix by the Francis double-shift
+ * QR iteration (the eigensolver of lrp_arnoldi; Golub & Van Loan Sec. 7.5),
+ * on the current device, synchronously. H: m x m column-major (ld ldh >= m),
+ * host or device; entries below the first subdiagonal are ignored.
+ * wr, wi (host, m): the eigenvalues in the order of the diagonal of the real
+ * Schur form (a complex pair adjacent, positive imaginary part first).
+ * T, Z (each may be NULL; host or device, m x m, ld m): the quasi-upper-
+ * triangular Schur factor and the orthogonal Schur vectors, H = Z T Z^T.
+ * LRP_ENOCONV if the iteration used 30 m double-shift steps without
+ * finishing (outputs as far as reached); LRP_EINVAL for m outside 1..4096. */
+lrp_status lrp_hessenberg_eig(int m, const double* H, int ldh, double* wr, double* wi,
+                              double* T, double* Z);
 
 /* Copies the r <= k eigenvalues (decreasing) and optionally the eigenvectors
  * (nx x r column-major, ld ldv) out of a posterior. *r receives the count. */

@@ -25,7 +25,7 @@ LRP_OK, LRP_EINVAL, LRP_ENOMEM, LRP_ENOCONV, LRP_ENONFINITE, LRP_ETIMEOUT, LRP_E
 LRP_FP64, LRP_MIXED = 0, 1
 LRP_PRIOR_LAPLACE, LRP_PRIOR_IDENTITY = 0, 1
 LRP_PDE_HEAT, LRP_PDE_CONVDIFF = 0, 1
-LRP_PRIOR_PRECOND, LRP_MISFIT_ONLY, LRP_KEEP_TRAJ_FACTORS = 0, 1, 2
+LRP_PRIOR_PRECOND, LRP_MISFIT_ONLY, LRP_KEEP_TRAJ_FACTORS, LRP_LOWRANK_SOURCE = 0, 1, 2, 4
 LRP_Q_MEAN, LRP_Q_VARIANCE, LRP_Q_SAMPLES = 1, 2, 4
 STATUS_NAMES = {0: "LRP_OK", 1: "LRP_EINVAL", 2: "LRP_ENOMEM", 3: "LRP_ENOCONV", 4: "LRP_ENONFINITE",
                 5: "LRP_ETIMEOUT", 6: "LRP_EBUDGET", 7: "LRP_ECUDA"}
@@ -49,7 +49,8 @@ class lrp_problem_desc(C.Structure):
 class lrp_apply_stats(C.Structure):
     _fields_ = [("n_solves", C.c_int), ("pcg_iters_max", C.c_int), ("pcg_iters_mean", C.c_double),
                 ("refine_max", C.c_int), ("max_rel_residual", C.c_double), ("time_rank_max", C.c_int),
-                ("time_trunc_err", C.c_double), ("ms", C.c_double)]
+                ("time_trunc_err", C.c_double), ("ms", C.c_double), ("adj_rank_max", C.c_int),
+                ("adj_trunc_err", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -102,6 +103,15 @@ class lrp_batch_stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class lrp_arnoldi_stats(C.Structure):
+    _fields_ = [("n_steps", C.c_int), ("k_converged", C.c_int), ("n_complex", C.c_int), ("max_imag", C.c_double),
+                ("hess_asym", C.c_double), ("max_ritz_resid", C.c_double), ("time_rank_max", C.c_int),
+                ("adj_rank_max", C.c_int), ("ms", C.c_double), ("ms_apply", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class lrp_device_peaks(C.Structure):
     _fields_ = [("smem_gbs", C.c_double), ("fp64_fma_tflops", C.c_double), ("fp32_fma_tflops", C.c_double),
                 ("sm_count", C.c_int), ("clock_mhz", C.c_double)]
@@ -132,6 +142,11 @@ EXPORTS = {
                                          C.c_void_p, C.POINTER(lrp_apply_stats)]),
     "lrp_lowrank_posterior": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
                                         C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(lrp_lanczos_stats)]),
+    "lrp_arnoldi": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_double, C.c_uint, C.c_void_p,
+                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p),
+                              C.POINTER(lrp_arnoldi_stats)]),
+    "lrp_hessenberg_eig": (C.c_int, [C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_void_p]),
     "lrp_posterior_destroy": (None, [C.c_void_p]),
     "lrp_posterior_eigs": (C.c_int, [C.c_void_p, _ip, C.c_void_p, C.c_void_p, C.c_int]),
     "lrp_posterior_query": (C.c_int, [C.c_void_p, C.POINTER(lrp_query), C.POINTER(lrp_query_result)]),
@@ -420,6 +435,59 @@ def lrp_lowrank_posterior(prob: Problem, k: int, block: int = 1, eig_tol: float 
     d = st.as_dict()
     d["status"] = status
     return Posterior(h, prob), d
+
+
+def lrp_arnoldi(prob: Problem, max_steps: int, k: int = 0, eig_tol: float = 1e-6, eig_threshold: float = 0.0,
+                flags: int = 0, start=None, posterior: bool = False):
+    """Arnoldi process of Algorithm 1 (modified Gram-Schmidt, Hessenberg H)
+    on Htilde, H_mis (LRP_MISFIT_ONLY) or the truncated product
+    (LRP_LOWRANK_SOURCE). Returns a dict: 'theta' (complex Ritz values by
+    decreasing real part), 'H' ((m+1) x m), 'ranks_y', 'ranks_q' (per step),
+    'posterior' (a Posterior or None), 'stats' (with 'status')."""
+    mmax = int(max_steps)
+    re = np.zeros(mmax)
+    im = np.zeros(mmax)
+    H = np.zeros((mmax + 1, mmax), order="F")
+    ry = np.zeros(mmax, dtype=np.int32)
+    rq = np.zeros(mmax, dtype=np.int32)
+    keep = []
+    sp = None
+    if start is not None:
+        if _is_torch(start):
+            t = start.contiguous()
+            keep.append(t)
+            sp = t.data_ptr()
+        else:
+            a = np.ascontiguousarray(np.asarray(start, dtype=np.float64).ravel())
+            keep.append(a)
+            sp = a.ctypes.data
+    h = C.c_void_p()
+    st = lrp_arnoldi_stats()
+    status = load().lrp_arnoldi(prob.handle, mmax, int(k), float(eig_tol), float(eig_threshold), C.c_uint(flags),
+                                sp, re.ctypes.data, im.ctypes.data, H.ctypes.data, ry.ctypes.data, rq.ctypes.data,
+                                C.byref(h) if posterior else None, C.byref(st))
+    _check(status, allow=(LRP_OK, LRP_ENOCONV))
+    m = st.n_steps
+    d = st.as_dict()
+    d["status"] = status
+    return {"theta": re[:m] + 1j * im[:m], "H": np.array(H[:m + 1, :m]), "ranks_y": ry[:m].copy(),
+            "ranks_q": rq[:m].copy(), "posterior": Posterior(h, prob) if posterior else None, "stats": d}
+
+
+def lrp_hessenberg_eig(H, want_schur: bool = False):
+    """Eigenvalues of an upper Hessenberg matrix (Francis double-shift QR on
+    the GPU). Returns (wr + i wi in Schur-diagonal order) or, with want_schur,
+    (eigenvalues, T, Z) with H = Z T Z^T."""
+    A = np.asfortranarray(np.asarray(H, dtype=np.float64))
+    m = A.shape[0]
+    wr = np.zeros(m)
+    wi = np.zeros(m)
+    T = np.zeros((m, m), order="F") if want_schur else None
+    Z = np.zeros((m, m), order="F") if want_schur else None
+    _check(load().lrp_hessenberg_eig(m, A.ctypes.data, m, wr.ctypes.data, wi.ctypes.data,
+                                     T.ctypes.data if want_schur else None, Z.ctypes.data if want_schur else None))
+    lam = wr + 1j * wi
+    return (lam, T, Z) if want_schur else lam
 
 
 def lrp_posterior_query(post: Posterior, kind: int, y_obs=None, sigma: float = 0.0, points=None, xi=None,

@@ -956,6 +956,10 @@ __global__ void __launch_bounds__(FAST_THREADS, 1) fast2d_kernel(const SweepPara
       const double* dsrc = is_obs ? obs + (size_t)(step / P.obs_every - 1) * P.n_obs : nullptr;
       const int qi = q ? db_index(q) : cur;
       q = fast_solve(t, b, P, P.step, bd, v, sm, q, dsrc, q, db[(qi + 1) % 3], db[(qi + 2) % 3], ctr);
+      if ((P.stages & ST_TRAJ_ADJ) && valid) {
+        double* dst = P.traj + ((size_t)gcol * P.traj_cols + (step - 1)) * P.traj_ld;
+        for_own([&](int row, int col) { dst[row * n + col] = df_to_double(df_load(q + row * n + col)); });
+      }
     }
     if (q) {
       cur = db_index(q);

@@ -689,6 +689,26 @@ static lrp_status hessian_with_factors(lrp_problem* P, int nvec, const double* X
   return s2 != LRP_OK ? s2 : s;
 }
 
+// The truncated product of Algorithm 1 (LRP_LOWRANK_SOURCE), staged like
+// the other calls.
+static lrp_status hessian_lowrank_source(lrp_problem* P, int nvec, const double* X, int ldx, double* Y, int ldy,
+                                         bool misfit, lrp_apply_stats* st) {
+  lrp_status s = check_common(P, nvec, ldx, P->nx, ldy, P->nx, X, Y);
+  if (s != LRP_OK) return s;
+  if (nvec == 0) return LRP_OK;
+  Staged sin, sout;
+  const double* din;
+  int dldin;
+  double* dout;
+  int dldout;
+  if ((s = stage_in(P, X, P->nx, nvec, ldx, &din, &dldin, sin)) != LRP_OK) return s;
+  if ((s = stage_out_alloc(P, Y, P->nx, nvec, ldy, &dout, &dldout, sout)) != LRP_OK) return s;
+  s = lowrank_hessian_impl(P, nvec, din, dldin, dout, dldout, misfit, st);
+  if (s != LRP_OK && s != LRP_ENOCONV) return s;
+  lrp_status s2 = stage_out_copy(P, Y, P->nx, nvec, ldy, dout, dldout);
+  return s2 != LRP_OK ? s2 : s;
+}
+
 }  // namespace lrp
 
 extern "C" {
@@ -889,6 +909,11 @@ lrp_status lrp_hessian_apply(lrp_problem* P, int nvec, const double* X, int ldx,
     return LRP_EINVAL;
   }
   const bool misfit = (flags & LRP_MISFIT_ONLY) != 0;
+  if ((flags & LRP_KEEP_TRAJ_FACTORS) && (flags & LRP_LOWRANK_SOURCE)) {
+    set_error("LRP_KEEP_TRAJ_FACTORS and LRP_LOWRANK_SOURCE are exclusive");
+    return LRP_EINVAL;
+  }
+  if (flags & LRP_LOWRANK_SOURCE) return hessian_lowrank_source(P, nvec, X, ldx, Y, ldy, misfit, st);
   if (flags & LRP_KEEP_TRAJ_FACTORS) return hessian_with_factors(P, nvec, X, ldx, Y, ldy, misfit, st);
   unsigned stages = ST_LOAD_X | ST_FORWARD | ST_ADJOINT | ST_STORE_Y;
   if (!misfit) stages |= ST_PRIOR_IN | ST_PRIOR_OUT;

@@ -73,7 +73,8 @@ enum : unsigned {
   ST_PRIOR_OUT = 1u << 5,   // solve (I + alpha L0) y = q
   ST_STORE_Y = 1u << 6,     // store the result buffer to column-major Y
   ST_STORE_D = 1u << 7,     // store the observations (unweighted) to column-major D
-  ST_TRAJ = 1u << 8         // copy every forward state into the trajectory chunk buffer
+  ST_TRAJ = 1u << 8,        // copy every forward state into the trajectory chunk buffer
+  ST_TRAJ_ADJ = 1u << 9     // copy every adjoint state q_n into column n-1 of the trajectory buffer
 };
 
 enum : int { STAT_NOCONV = 1, STAT_NONFINITE = 2 };
@@ -121,7 +122,7 @@ struct SweepParams {
   double* Y; int ldy;
   const double* Din; int lddin;
   double* Dout; int lddout;
-  double* traj; int traj_ld; int traj_cols;  // trajectory chunk buffer: [team col][step in chunk][nx]
+  double* traj; int traj_ld; int traj_cols;  // trajectory buffer: [team col][step in chunk (forward) or step-1 (adjoint)][nx]
   // workspace
   char* ws;
   size_t team_bytes;
@@ -248,4 +249,7 @@ lrp_status trajectory_factors_impl(lrp_problem* P, int nvec, const double* U, in
                                    double* Vout, int* ranks, lrp_apply_stats* stats, bool with_hessian,
                                    double* Yout, int ldy);
 lrp_status ensure_workspace(lrp_problem* P, size_t bytes);
+// Y = the truncated product of Algorithm 1 (LRP_LOWRANK_SOURCE); X, Y device arrays.
+lrp_status lowrank_hessian_impl(lrp_problem* P, int nvec, const double* X, int ldx, double* Y, int ldy,
+                                bool misfit, lrp_apply_stats* stats);
 }  // namespace lrp

@@ -813,6 +813,11 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
       double* X2 = w.dbuf[(qi + 2) % 3];
       double* res = solve_any<T, DIM, MIXED>(t, P, P.step, w, sm, q, dsrc, q, X1, X2, ctr, true);
       q = res;
+      if ((P.stages & ST_TRAJ_ADJ) && valid) {
+        // steps after the last observation hold q_n = 0: the caller zeroes the buffer
+        double* dst = P.traj + ((size_t)gcol * P.traj_cols + (n - 1)) * P.traj_ld;
+        for (int it = t.g; it < items0; it += t.S) dst[it >> t.bvs] = res[it];
+      }
     }
     if (q) {
       cur = buf_index(w.dbuf, q);

@@ -168,6 +168,38 @@ __global__ void k_scale_cols(int nx, int r, const double* sig, double* W, int ld
   W[(size_t)c * ldw + p] *= sig[c];
 }
 
+// One time column of factored trajectory Qw diag(sig) V^T:
+// out[p] = sum_i Qw[p, i] sig[i] V[row, i] (row = step - 1).
+__global__ void k_factor_col(int nx, int r, const double* Qw, const double* sig, const double* V, int ldv,
+                             int row, double* out) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nx) return;
+  double acc = 0.0;
+  for (int i = 0; i < r; ++i) acc += Qw[(size_t)i * nx + p] * (sig[i] * V[(size_t)i * ldv + row]);
+  out[p] = acc;
+}
+
+// Observations of a factored trajectory (the adjoint's data of the truncated
+// product): D[k*n_obs + s] = inv_sigma2 * sum_c w_sc (Qw diag(sig) V^T)[node_sc, n_k - 1]
+// at the observed steps n_k = (k+1) obs_every, k < n_steps (8 taps per sensor).
+__global__ void k_observe_factors(int nx, int r, const double* Qw, const double* sig, const double* V, int ldv,
+                                  int n_obs, int n_steps, int obs_every, const int* obs_node, const double* obs_w,
+                                  double inv_sigma2, double* D) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_obs * n_steps) return;
+  const int k = e / n_obs, so = e % n_obs;
+  const int row = (k + 1) * obs_every - 1;
+  double y = 0.0;
+  for (int c = 0; c < 8; ++c) {
+    const int node = obs_node[so * 8 + c];
+    if (node < 0) continue;
+    double v = 0.0;
+    for (int i = 0; i < r; ++i) v += Qw[(size_t)i * nx + node] * (sig[i] * V[(size_t)i * ldv + row]);
+    y += obs_w[so * 8 + c] * v;
+  }
+  D[e] = y * inv_sigma2;
+}
+
 #define CKT(call)                                          \
   do {                                                     \
     cudaError_t _e = (call);                               \
@@ -361,23 +393,18 @@ struct TrajPipe {
   }
 };
 
-lrp_status trajectory_factors_impl(lrp_problem* P, int nvec, const double* U, int ldu, double* Wout,
-                                   double* Vout, int* ranks, lrp_apply_stats* stats, bool with_hessian,
-                                   double* Yout, int ldy) {
-  auto t0 = std::chrono::steady_clock::now();
+// Factors and scratch of one streamed compression of nvec trajectories.
+static lrp_status traj_alloc(lrp_problem* P, int nvec, std::vector<TrajCol>& cols, TrajWS& ws) {
   const int nx = P->nx, nt = P->nt;
   const int s = std::min(64, std::max(1, P->desc.time_chunk));  // the block QR handles up to 64 columns
   const int rmax = P->desc.time_rank_max;
-  const int K = (nt + s - 1) / s;
-  const double tol_k = P->desc.time_trunc_tol / K;
-  std::vector<TrajCol> cols(nvec);
+  cols.resize(nvec);
   for (auto& c : cols) {
     CKT(c.Qa.alloc((size_t)nx * rmax));
     CKT(c.Qb.alloc((size_t)nx * rmax));
     CKT(c.V.alloc((size_t)nt * rmax));
     CKT(c.Vn.alloc((size_t)nt * rmax));
   }
-  TrajWS ws;
   ws.nvec = nvec;
   ws.s = s;
   ws.rmax = rmax;
@@ -395,30 +422,55 @@ lrp_status trajectory_factors_impl(lrp_problem* P, int nvec, const double* U, in
   CKT(ws.gs.alloc(block_gs_scratch_doubles()));
   CKT(ws.sig.alloc((size_t)nvec * rmax));
   CKT(lrp::dev_malloc(&ws.iarr, 2 * nvec * sizeof(int)));
+  return LRP_OK;
+}
+
+// Statistics of the sweeps of one call, folded launch by launch.
+struct SweepAcc {
   lrp_apply_stats acc;
-  std::memset(&acc, 0, sizeof(acc));
-  lrp_status result = LRP_OK;
   double iters_sum = 0.0;
   long long solves = 0;
-  auto fold = [&](const lrp_apply_stats& st) {
+  lrp_status result = LRP_OK;
+  SweepAcc() { std::memset(&acc, 0, sizeof(acc)); }
+  // folds one launch's statistics; returns its status unless it is LRP_ENOCONV
+  // (kept as the call's result: the outputs are still written)
+  lrp_status fold(lrp_status sres, const lrp_apply_stats& st) {
+    if (sres != LRP_OK && sres != LRP_ENOCONV) return sres;
+    if (sres == LRP_ENOCONV) result = sres;
     acc.pcg_iters_max = std::max(acc.pcg_iters_max, st.pcg_iters_max);
     acc.refine_max = std::max(acc.refine_max, st.refine_max);
     acc.max_rel_residual = std::max(acc.max_rel_residual, st.max_rel_residual);
     iters_sum += st.pcg_iters_mean * st.n_solves;
     solves += st.n_solves;
-  };
-  // On the problem stream, per chunk j: its sweep, then (once chunk j-1 is
-  // fully absorbed) the head of its absorption. On the second stream: the
-  // tail, which overlaps chunk j+1's sweep (the sweep only continues its own
-  // state; the tail only reads chunk j's buffer and the small factors).
-  // Chunk j+1's sweep refills the buffer of chunk j-1, whose tail the head
-  // of chunk j has waited for.
+    return LRP_OK;
+  }
+  void fill(lrp_apply_stats* out) const {
+    *out = acc;
+    out->n_solves = (int)solves;
+    out->pcg_iters_mean = solves ? iters_sum / solves : 0.0;
+  }
+};
+
+// The forward sweep of nvec columns (optionally after the prior solve) in
+// chunks of s steps over all nt steps, every chunk absorbed into the
+// columns' factors.
+// On the problem stream, per chunk j: its sweep, then (once chunk j-1 is
+// fully absorbed) the head of its absorption. On the second stream: the
+// tail, which overlaps chunk j+1's sweep (the sweep only continues its own
+// state; the tail only reads chunk j's buffer and the small factors).
+// Chunk j+1's sweep refills the buffer of chunk j-1, whose tail the head
+// of chunk j has waited for. Returns with the problem stream ordered after
+// the last absorption.
+static lrp_status stream_forward(lrp_problem* P, int nvec, const double* U, int ldu, bool prior_in,
+                                 std::vector<TrajCol>& cols, TrajWS& ws, double tol_k, SweepAcc& sa) {
+  const int nt = P->nt, s = ws.s;
+  const int K = (nt + s - 1) / s;
   TrajPipe pp;
   CKT(pp.init(P->stream));
   auto enqueue_sweep = [&](int j) -> lrp_status {
     const int b = j & 1, c0 = j * s, c1 = std::min(nt, c0 + s);
     unsigned stages = ST_FORWARD | ST_TRAJ;
-    if (j == 0) stages |= ST_LOAD_X | (with_hessian ? ST_PRIOR_IN : 0);
+    if (j == 0) stages |= ST_LOAD_X | (prior_in ? ST_PRIOR_IN : 0);
     CKT(cudaEventRecord(pp.sw0[b], P->stream));
     lrp_status r = sweep_enqueue(P, stages, nvec, U, ldu, nullptr, 0, nullptr, 0, nullptr, 0, c0, c1,
                                  ws.traj[b].p, s, pp.h_stats + b, pp.info + b);
@@ -456,32 +508,80 @@ lrp_status trajectory_factors_impl(lrp_problem* P, int nvec, const double* U, in
     ledger_add(P, pp.h_stats[b], pp.info[b], ms);
     lrp_apply_stats st;
     lrp_status sres = sweep_status(pp.h_stats[b], pp.info[b], &st, ms);
-    if (sres != LRP_OK && sres != LRP_ENOCONV) return sres;
-    if (sres == LRP_ENOCONV) result = sres;
-    fold(st);
+    if ((sres = sa.fold(sres, st)) != LRP_OK) return sres;
     if (j + 1 < K) {
       lrp_status r = enqueue_head(j + 1);
       if (r != LRP_OK) return r;
     }
   }
-  // the trailing GEMMs of the last absorption precede everything below
+  // the trailing GEMMs of the last absorption precede everything after
   CKT(cudaStreamWaitEvent(P->stream, pp.absorbed[(K - 1) & 1], 0));
+  return LRP_OK;
+}
+
+// Absorbs a stored trajectory (nvec x nt x nx: column b's step n at
+// traj + (b*nt + n-1)*nx) into cols, chunk by chunk in time order, on the
+// problem stream.
+static lrp_status absorb_stored(lrp_problem* P, int nvec, const double* traj, std::vector<TrajCol>& cols,
+                                TrajWS& ws, double tol_k) {
+  const size_t nx = P->nx, nt = P->nt;
+  const int s = ws.s;
+  for (int c0 = 0; c0 < (int)nt; c0 += s) {
+    const int sk = std::min<int>(s, (int)nt - c0);
+    // chunk buffer layout: [column][step in chunk][nx] (absorb_head works on it in place)
+    CKT(cudaMemcpy2DAsync(ws.traj[0].p, (size_t)s * nx * sizeof(double), traj + (size_t)c0 * nx,
+                          nt * nx * sizeof(double), (size_t)sk * nx * sizeof(double), nvec,
+                          cudaMemcpyDeviceToDevice, P->stream));
+    lrp_status r = absorb_head(P, cols, ws, sk, P->stream, ws.traj[0].p);
+    if (r == LRP_OK) r = absorb_tail(P, cols, ws, sk, tol_k, P->stream, ws.traj[0].p);
+    if (r != LRP_OK) return r;
+  }
+  return LRP_OK;
+}
+
+// Largest rank and largest certified relative truncation error of the factors.
+static void factor_summary(const std::vector<TrajCol>& cols, int* rank_max, double* err_max, int* ranks) {
+  *rank_max = 0;
+  *err_max = 0.0;
+  for (size_t j = 0; j < cols.size(); ++j) {
+    const TrajCol& tc = cols[j];
+    *rank_max = std::max(*rank_max, tc.r);
+    const double fro = std::sqrt(tc.fro2);
+    *err_max = std::max(*err_max, fro > 0 ? tc.err_abs / fro : 0.0);
+    if (ranks) ranks[j] = tc.r;
+  }
+}
+
+lrp_status trajectory_factors_impl(lrp_problem* P, int nvec, const double* U, int ldu, double* Wout,
+                                   double* Vout, int* ranks, lrp_apply_stats* stats, bool with_hessian,
+                                   double* Yout, int ldy) {
+  auto t0 = std::chrono::steady_clock::now();
+  const int nx = P->nx, nt = P->nt;
+  std::vector<TrajCol> cols;
+  TrajWS ws;
+  {
+    lrp_status r = traj_alloc(P, nvec, cols, ws);
+    if (r != LRP_OK) return r;
+  }
+  const int rmax = ws.rmax;
+  const int K = (nt + ws.s - 1) / ws.s;
+  const double tol_k = P->desc.time_trunc_tol / K;
+  SweepAcc sa;
+  {
+    lrp_status r = stream_forward(P, nvec, U, ldu, with_hessian, cols, ws, tol_k, sa);
+    if (r != LRP_OK) return r;
+  }
   if (with_hessian) {
     lrp_apply_stats st;
     lrp_status sres = run_sweep_ex(P, ST_ADJOINT | ST_PRIOR_OUT | ST_STORE_Y, nvec, nullptr, 0, Yout, ldy,
                                    nullptr, 0, nullptr, 0, &st, 0, 0, nullptr, 0);
-    if (sres != LRP_OK && sres != LRP_ENOCONV) return sres;
-    if (sres == LRP_ENOCONV) result = sres;
-    fold(st);
+    if ((sres = sa.fold(sres, st)) != LRP_OK) return sres;
   }
   int rank_max = 0;
   double err_max = 0.0;
+  factor_summary(cols, &rank_max, &err_max, ranks);
   for (int j = 0; j < nvec; ++j) {
     TrajCol& tc = cols[j];
-    rank_max = std::max(rank_max, tc.r);
-    const double fro = std::sqrt(tc.fro2);
-    err_max = std::max(err_max, fro > 0 ? tc.err_abs / fro : 0.0);
-    if (ranks) ranks[j] = tc.r;
     if (Wout && tc.r > 0) {
       double* W = Wout + (size_t)j * nx * rmax;
       CKT(cudaMemcpyAsync(W, tc.Qa.p, (size_t)nx * tc.r * sizeof(double), cudaMemcpyDeviceToDevice, P->stream));
@@ -496,14 +596,116 @@ lrp_status trajectory_factors_impl(lrp_problem* P, int nvec, const double* U, in
   }
   CKT(cudaStreamSynchronize(P->stream));
   if (stats) {
-    *stats = acc;
-    stats->n_solves = (int)solves;
-    stats->pcg_iters_mean = solves ? iters_sum / solves : 0.0;
+    sa.fill(stats);
     stats->time_rank_max = rank_max;
     stats->time_trunc_err = err_max;
     stats->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
-  return result;
+  return sa.result;
+}
+
+// The matrix-vector product of Sec. 4 Algorithm 1 "up to the truncation
+// tolerance", with the initial condition as parameter: the space-time
+// solutions it passes through (the state and the adjoint trajectory) are
+// kept in low-rank-in-time form truncated to time_trunc_tol (rank cap
+// time_rank_max), and every later step uses the truncated form:
+//   z = Gamma_prior^{1/2} x (not for H_mis); Y = [y_1 .. y_nt] of z ~ W_Y V_Y^T
+//   (chunked forward sweep, streaming recompression); d_n = B (W_Y V_Y^T) e_n
+//   / sigma^2 at the observed steps; adjoint sweep with that source, storing
+//   Q = [q_1 .. q_nt] ~ W_Q V_Q^T (same recompression); result
+//   Gamma_prior^{1/2} (W_Q V_Q^T) e_1.
+// The product is then no longer symmetric (by about the tolerance), which is
+// why Algorithm 1 is an Arnoldi process. X and Y are device arrays.
+lrp_status lowrank_hessian_impl(lrp_problem* P, int nvec, const double* X, int ldx, double* Y, int ldy,
+                                bool misfit, lrp_apply_stats* stats) {
+  auto t0 = std::chrono::steady_clock::now();
+  const int nx = P->nx, nt = P->nt;
+  std::vector<TrajCol> cy, cq;
+  TrajWS ws;
+  {
+    lrp_status r = traj_alloc(P, nvec, cy, ws);
+    if (r != LRP_OK) return r;
+  }
+  cq.resize(nvec);
+  for (auto& c : cq) {
+    CKT(c.Qa.alloc((size_t)nx * ws.rmax));
+    CKT(c.Qb.alloc((size_t)nx * ws.rmax));
+    CKT(c.V.alloc((size_t)nt * ws.rmax));
+    CKT(c.Vn.alloc((size_t)nt * ws.rmax));
+  }
+  const int rmax = ws.rmax;
+  const int K = (nt + ws.s - 1) / ws.s;
+  const double tol_k = P->desc.time_trunc_tol / K;
+  DBuf D, Q, Z;
+  CKT(D.alloc((size_t)nvec * std::max(1, P->n_data)));
+  CKT(Q.alloc((size_t)nvec * nt * nx));
+  CKT(Z.alloc((size_t)nvec * nx));
+  SweepAcc sa;
+  // 1-2: (prior solve and) forward sweep, state factors
+  {
+    lrp_status r = stream_forward(P, nvec, X, ldx, !misfit, cy, ws, tol_k, sa);
+    if (r != LRP_OK) return r;
+  }
+  // 3: the adjoint's data from the truncated state
+  CKT(cudaMemsetAsync(D.p, 0, (size_t)nvec * std::max(1, P->n_data) * sizeof(double), P->stream));
+  const double inv_s2 = 1.0 / (P->desc.sigma * P->desc.sigma);
+  for (int b = 0; b < nvec; ++b) {
+    if (cy[b].r == 0 || P->n_data == 0) continue;
+    note_launch();
+    k_observe_factors<<<(P->n_data + 127) / 128, 128, 0, P->stream>>>(
+        nx, cy[b].r, cy[b].Qa.p, ws.sig.p + (size_t)b * rmax, cy[b].V.p, nt, P->n_obs, P->n_steps,
+        P->desc.obs_every, P->obs_node, P->obs_w, inv_s2, D.p + (size_t)b * P->n_data);
+    CKT(cudaGetLastError());
+  }
+  // 4: adjoint sweep storing its trajectory (q_n = 0 after the last observation)
+  CKT(cudaMemsetAsync(Q.p, 0, (size_t)nvec * nt * nx * sizeof(double), P->stream));
+  {
+    lrp_apply_stats st;
+    lrp_status sres = run_sweep_ex(P, ST_LOAD_D | ST_ADJOINT | ST_TRAJ_ADJ, nvec, nullptr, 0, nullptr, 0, D.p,
+                                   std::max(1, P->n_data), nullptr, 0, &st, 0, 0, Q.p, nt);
+    if ((sres = sa.fold(sres, st)) != LRP_OK) return sres;
+  }
+  int rank_y = 0, rank_q = 0;
+  double err_y = 0.0, err_q = 0.0;
+  factor_summary(cy, &rank_y, &err_y, nullptr);
+  // the state's singular values in ws.sig are no longer needed: the adjoint's
+  // compression reuses the scratch
+  {
+    lrp_status r = absorb_stored(P, nvec, Q.p, cq, ws, tol_k);
+    if (r != LRP_OK) return r;
+  }
+  factor_summary(cq, &rank_q, &err_q, nullptr);
+  // 5: the truncated q_1, then the prior factor
+  for (int b = 0; b < nvec; ++b) {
+    double* zb = Z.p + (size_t)b * nx;
+    if (cq[b].r == 0) {
+      CKT(cudaMemsetAsync(zb, 0, (size_t)nx * sizeof(double), P->stream));
+      continue;
+    }
+    note_launch();
+    k_factor_col<<<(nx + 255) / 256, 256, 0, P->stream>>>(nx, cq[b].r, cq[b].Qa.p, ws.sig.p + (size_t)b * rmax,
+                                                         cq[b].V.p, nt, 0, zb);
+    CKT(cudaGetLastError());
+  }
+  if (misfit) {
+    CKT(cudaMemcpy2DAsync(Y, (size_t)ldy * sizeof(double), Z.p, (size_t)nx * sizeof(double),
+                          (size_t)nx * sizeof(double), nvec, cudaMemcpyDeviceToDevice, P->stream));
+  } else {
+    lrp_apply_stats st;
+    lrp_status sres = run_sweep_ex(P, ST_LOAD_X | ST_PRIOR_OUT | ST_STORE_Y, nvec, Z.p, nx, Y, ldy, nullptr, 0,
+                                   nullptr, 0, &st, 0, 0, nullptr, 0);
+    if ((sres = sa.fold(sres, st)) != LRP_OK) return sres;
+  }
+  CKT(cudaStreamSynchronize(P->stream));
+  if (stats) {
+    sa.fill(stats);
+    stats->time_rank_max = rank_y;
+    stats->time_trunc_err = err_y;
+    stats->adj_rank_max = rank_q;
+    stats->adj_trunc_err = err_q;
+    stats->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return sa.result;
 }
 
 }  // namespace lrp
