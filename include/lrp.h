@@ -346,7 +346,8 @@ lrp_status lrp_batch_lowrank_posterior(lrp_problem* const* probs, int count, int
  * wanted ones are those with real part >= eig_threshold, and some Ritz value
  * must lie below it; otherwise the k leading ones. A complex Ritz value
  * among the wanted ones keeps the run going. The test runs after every step
- * up to 32 steps, then every floor(m/16)-th step.
+ * up to 32 steps, then every floor(m/16)-th step; with a threshold, not
+ * before step 8.
  * Outputs (each may be NULL; host or device):
  *   theta_re, theta_im [max_steps]: the m Ritz values of the last H_m by
  *     decreasing real part;

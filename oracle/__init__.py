@@ -27,6 +27,9 @@ Modules and the passages they follow:
   Algorithm 1 (state and adjoint trajectories truncated to eps_0, the
   adjoint's data observed from the truncated state), the Ritz values of a
   nonsymmetric Hessenberg matrix and the threshold-stopped Arnoldi run.
+* ``spacetime``  — a space-time source as the parameter (Sec. 4): its
+  forward map, adjoint and Hessian, low-rank space-time vectors (truncation,
+  inner product) and Algorithm 1 on them (Eq. (lanczos1)-(lanczos2)).
 * ``timefactors``— the low-rank-in-time factorisation Y ~ W V^T (Sec. 3) by
   truncated SVD of the full trajectory, and the streaming recompression the
   GPU uses (thin QR of [W | new columns], small SVD, truncation; Sec. 4).

@@ -32,7 +32,8 @@ With eps_0 = 0 (nothing discarded) every step is exact and the result is
 * ``arnoldi_threshold`` — Algorithm 1 (``spectrum.arnoldi_mgs`` one step at
   a time) stopped by the threshold rule of Sec. 6.1: once every Ritz value
   whose real part is at least eps has a residual estimate of at most
-  tol * |theta_1| and some Ritz value lies below eps (or m_max steps).
+  tol * |theta_1| and some Ritz value lies below eps, from step 8 on (or
+  m_max steps).
 """
 from __future__ import annotations
 
@@ -111,6 +112,8 @@ def arnoldi_threshold(apply, v1, eps, tol, m_max):
         if H[j + 1, j] == 0.0:
             break
         V[:, j + 1] = w / H[j + 1, j]
+        if m < 8:
+            continue  # a short Krylov space has not found the dominant eigenvalues yet
         lam, _, res = ritz_nonsym(H[:m + 1, :m], m)
         above = lam.real >= eps
         if np.any(~above) and np.all(res[above] <= tol * abs(lam[0])):

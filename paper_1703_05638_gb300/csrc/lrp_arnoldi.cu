@@ -654,7 +654,10 @@ extern "C" lrp_status lrp_arnoldi(lrp_problem* P, int max_steps, int k, double e
     breakdown = A.hH[(size_t)j * ldh + j + 1] <= 1e-14 * hnorm;
     const int mm = A.m;
     const bool due = mm <= 32 || mm % std::max(1, mm / 16) == 0;
-    const bool enough = A.eig_threshold > 0.0 || mm >= A.k;
+    // with a threshold: not before 8 steps (a short Krylov space from a
+    // random start has not found the dominant eigenvalues yet, and every
+    // Ritz value may still lie below the threshold)
+    const bool enough = A.eig_threshold > 0.0 ? mm >= 8 : mm >= A.k;
     if ((due && enough) || breakdown || j + 1 == mmax) {
       bool ok = false;
       lrp_status c = arnoldi_check(A, &ok);

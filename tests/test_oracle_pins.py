@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import synth
-from oracle import lowrank, operators, observe, posterior, spectrum, timefactors
+from oracle import lowrank, operators, observe, posterior, spacetime, spectrum, timefactors
 from oracle.problem import Problem
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -663,3 +663,115 @@ def test_arnoldi_threshold_rule_symmetric_operator():
     # decay as Ritz values converge; the relation does not depend on it)
     AV = np.column_stack([P.hessian_apply(V[:, j]) for j in range(m)])
     assert np.max(np.abs(AV - V @ H)) <= 1e-12 * lam[0]
+
+
+# ---------------------------------------------------------------- space-time parameter (Sec. 4)
+def _st_problem(**kw):
+    base = dict(n=3, nt=5, obs_every=2, sensors=synth.uniform_sensors(4, 2, 31), sigma=0.05, prior_alpha=0.1)
+    base.update(kw)
+    return Problem(_spec(**base))
+
+
+@pytest.mark.parametrize("pde", ["heat", "convdiff"])
+def test_source_forward_brute_force_and_adjoint(pde):
+    """y_n = sum_{m<=n} S^{n-m+1} tau u_m: the explicit F of the source map
+    equals the block matrix [tau B S^{n_k - m + 1}] (m <= n_k), and
+    <F U, d> = <U, F^T d>. Catches a source added after the solve, a wrong
+    tau, or an adjoint trajectory shifted by one step."""
+    kw = dict(pde="convdiff", conv_nu=1e-2, wind=(0.0, 1.0)) if pde == "convdiff" else {}
+    P = _st_problem(**kw)
+    S = np.linalg.inv(np.eye(P.nx) + P.tau * P.L.toarray())
+    B = P.B.toarray()
+    F = np.zeros((P.n_data, P.nx * P.nt))
+    for k, nk in enumerate(P.steps):
+        for m in range(1, nk + 1):
+            F[k * P.n_obs:(k + 1) * P.n_obs, (m - 1) * P.nx:m * P.nx] = P.tau * B @ np.linalg.matrix_power(S, nk - m + 1)
+    Fo = np.column_stack([spacetime.forward_source(P, np.eye(P.nx * P.nt)[:, c].reshape(P.nt, P.nx).T)
+                          for c in range(P.nx * P.nt)])
+    np.testing.assert_allclose(Fo, F, rtol=1e-12, atol=1e-15)
+    r = synth.rng(32)
+    U = r.standard_normal((P.nx, P.nt))
+    d = r.standard_normal(P.n_data)
+    lhs = spacetime.forward_source(P, U) @ d
+    rhs = np.sum(U * spacetime.adjoint_source(P, d))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+    np.testing.assert_allclose(np.column_stack([spacetime.vec(spacetime.adjoint_source(P, e))
+                                                for e in np.eye(P.n_data)]), F.T, rtol=1e-12, atol=1e-15)
+
+
+def test_spacetime_hessian_symmetric_psd():
+    """Htilde = R^-1 F^T F R^-1 / sigma^2 on vec(U) is symmetric positive
+    semi-definite (before the symmetrisation of the explicit matrix) and
+    equals the product of its explicit factors."""
+    P = _st_problem()
+    N = P.nx * P.nt
+    cols = [spacetime.vec(spacetime.hessian_st(P, e.reshape(P.nt, P.nx).T)) for e in np.eye(N)]
+    H = np.column_stack(cols)
+    assert np.max(np.abs(H - H.T)) <= 1e-12 * np.abs(H).max()
+    assert np.linalg.eigvalsh(0.5 * (H + H.T)).min() >= -1e-12 * np.abs(H).max()
+    F = np.column_stack([spacetime.forward_source(P, e.reshape(P.nt, P.nx).T) for e in np.eye(N)])
+    Rinv = np.kron(np.eye(P.nt), P.prior_half(np.eye(P.nx)))
+    np.testing.assert_allclose(H, Rinv @ F.T @ F @ Rinv / P.sigma ** 2, rtol=1e-11, atol=1e-12 * np.abs(H).max())
+
+
+def test_lowrank_vector_ops():
+    """Truncation of a factored matrix: exact without a tolerance; with
+    prescribed singular values it keeps the smallest rank meeting the
+    Frobenius tail bound (Eckart-Young); the factored inner product equals the
+    dense one."""
+    r = synth.rng(33)
+    A = r.standard_normal((30, 7))
+    B = r.standard_normal((20, 7))
+    A2, B2 = spacetime.truncate(A, B, 0.0, 100)
+    np.testing.assert_allclose(A2 @ B2.T, A @ B.T, rtol=0, atol=1e-12 * np.abs(A @ B.T).max())
+    U, _ = np.linalg.qr(r.standard_normal((30, 8)))
+    Z, _ = np.linalg.qr(r.standard_normal((20, 8)))
+    s = 10.0 ** -np.arange(8)
+    # split into two factored terms that sum to U diag(s) Z^T
+    A = np.hstack([U[:, :4] * s[:4], U[:, 4:] * s[4:]])
+    B = np.hstack([Z[:, :4], Z[:, 4:]])
+    At, Bt = spacetime.truncate(A, B, 3e-4, 100)
+    assert At.shape[1] == 4  # tail from s_4 = 1e-4 is ~1.005e-4 <= 3e-4 ||.||; from s_3 it is 1e-3
+    err = np.linalg.norm(A @ B.T - At @ Bt.T)
+    assert abs(err - np.sqrt(np.sum(s[4:] ** 2))) < 1e-13
+    X = (r.standard_normal((30, 3)), r.standard_normal((20, 3)))
+    Y = (r.standard_normal((30, 5)), r.standard_normal((20, 5)))
+    assert abs(spacetime.dot(X, Y) - np.sum((X[0] @ X[1].T) * (Y[0] @ Y[1].T))) < 1e-10
+
+
+def test_lr_hessian_apply_exact_without_truncation():
+    P = _st_problem(n=7, nt=12, obs_every=3)
+    r = synth.rng(34)
+    A = r.standard_normal((P.nx, 3))
+    B = r.standard_normal((P.nt, 3))
+    Ao, Bo = spacetime.lr_hessian_apply(P, A, B, 0.0, 100, 5)
+    want = spacetime.hessian_st(P, A @ B.T)
+    assert np.max(np.abs(Ao @ Bo.T - want)) <= 1e-12 * np.abs(want).max()
+
+
+def test_lr_arnoldi_equals_dense_arnoldi():
+    """Algorithm 1 on factored vectors with nothing truncated is Algorithm 1
+    on vec(U) with the explicit space-time Htilde: the same Hessenberg matrix
+    from the same start vector, and its Ritz values converge to the dense
+    eigenvalues. With the paper's truncation (1e-8) the leading Ritz values
+    stay within 1e-7 of them and every vector keeps unit norm."""
+    P = _st_problem(n=7, nt=16, obs_every=2, sensors=synth.uniform_sensors(6, 2, 35))
+    Hd = spacetime.hessian_st_explicit(P)
+    lam = np.sort(np.linalg.eigvalsh(Hd))[::-1]
+    r = synth.rng(36)
+    A0 = r.standard_normal((P.nx, 2))
+    B0 = r.standard_normal((P.nt, 2))
+    m = 24
+    H, ranks, _ = spacetime.lr_arnoldi(P, A0, B0, m, 0.0, 1000, 4)
+    v1 = spacetime.vec(A0 @ B0.T)
+    _, Hdense = spectrum.arnoldi_mgs(lambda x: Hd @ x, v1, m)
+    # the leading columns (later ones amplify rounding once the fast-decaying
+    # spectrum is resolved, in either form)
+    assert np.max(np.abs(H[:9, :8] - Hdense[:9, :8])) <= 1e-10 * lam[0]
+    theta, _, _ = lowrank.ritz_nonsym(H, m)
+    np.testing.assert_allclose(theta.real[:4], lam[:4], rtol=1e-9)
+    Ht, ranks_t, basis = spacetime.lr_arnoldi(P, A0, B0, m, 1e-8, 40, 4)
+    th_t, _, _ = lowrank.ritz_nonsym(Ht, m)
+    np.testing.assert_allclose(th_t.real[:4], lam[:4], rtol=1e-7)
+    assert max(ranks_t) <= min(P.nx, P.nt, 40)
+    assert abs(spacetime.dot(basis[3], basis[3]) - 1.0) < 1e-12
