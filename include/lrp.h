@@ -380,6 +380,44 @@ lrp_status lrp_arnoldi(lrp_problem* p, int max_steps, int k, double eig_tol, dou
                        double* H, int* ranks_y, int* ranks_q, lrp_posterior** out,
                        lrp_arnoldi_stats* st);
 
+/* ---------------------------------------------------------------------------
+ * A space-time parameter (Sec. 4: a distributed source u(x, t) as the
+ * uncertain quantity, the case the low-rank Krylov vectors are made for):
+ * y_t + L y = u, y(0) = 0, implicit Euler (I + tau L) y_n = y_{n-1} + tau u_n;
+ * U = [u_1 .. u_nt] (nx x nt). Observations, noise and the spatial prior as
+ * for the initial condition; Gamma_prior = I_nt (x) Gamma_x. Then
+ * F^T d = tau [q_1 .. q_nt] (the adjoint recursion's whole trajectory) and
+ * Htilde U = Gamma_x^{1/2} F^T F Gamma_x^{1/2} U / sigma^2.
+ * Low-rank vectors U = W V^T (W: nx x r, V: nt x r, column-major).
+ *
+ * lrp_st_hessian_apply: Htilde (W V^T) as factors: the prior factor on the r
+ * columns of W, one forward sweep with the factored source added before each
+ * step's solve and the fused observation, the adjoint sweep storing its
+ * trajectory, the streaming truncation of that trajectory (time_trunc_tol,
+ * time_rank_max, time_chunk), the prior factor on its space factor. Wout
+ * (nx x time_rank_max, ld nx) and Vout (nt x time_rank_max, ld nt) receive
+ * the *r_out result columns; host or device arrays. Stats: adj_rank_max and
+ * adj_trunc_err describe the truncation. */
+lrp_status lrp_st_hessian_apply(lrp_problem* p, int r, const double* W, int ldw, const double* V, int ldv,
+                                double* Wout, double* Vout, int* r_out, lrp_apply_stats* st);
+
+/* Algorithm 1 on low-rank space-time vectors (Sec. 4, Eq. (lanczos1)-
+ * (lanczos2)): w = Htilde v_j (lrp_st_hessian_apply); for i = 1..j:
+ * h_ij = <w, v_i> (trace of the factor products), w <- round(w - h_ij v_i)
+ * (factors concatenated, then rounded: thin QR of both factors, SVD of the
+ * small core, smallest rank whose discarded Frobenius tail is at most
+ * time_trunc_tol ||w||_F, capped at time_rank_max); h_{j+1,j} = ||w||_F,
+ * v_{j+1} = w / h_{j+1,j}. Ritz values, the stopping rule, theta_re/theta_im
+ * and H as in lrp_arnoldi. Start: r0 factor columns W0 (nx x r0), V0
+ * (nt x r0) (host or device; rounded and normalised), or r0 = 0 for a fixed
+ * pseudo-random rank-1 start. ranks [max_steps] (host, may be NULL): the rank
+ * of v_{j+1}. Stats: time_rank_max = the largest rank of a Krylov vector,
+ * adj_rank_max = the largest rank of a product Htilde v_j. Needs
+ * time_rank_max <= 56; LRP_EINVAL otherwise. */
+lrp_status lrp_st_arnoldi(lrp_problem* p, int max_steps, int k, double eig_tol, double eig_threshold, int r0,
+                          const double* W0, const double* V0, double* theta_re, double* theta_im, double* H,
+                          int* ranks, lrp_arnoldi_stats* st);
+
 /* Eigenvalues of a real upper Hessenberg matrix by the Francis double-shift
  * QR iteration (the eigensolver of lrp_arnoldi; Golub & Van Loan Sec. 7.5),
  * on the current device, synchronously. H: m x m column-major (ld ldh >= m),

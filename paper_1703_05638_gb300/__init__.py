@@ -147,6 +147,11 @@ EXPORTS = {
                               C.POINTER(lrp_arnoldi_stats)]),
     "lrp_hessenberg_eig": (C.c_int, [C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p]),
+    "lrp_st_hessian_apply": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p,
+                                       C.c_void_p, _ip, C.POINTER(lrp_apply_stats)]),
+    "lrp_st_arnoldi": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, C.c_void_p,
+                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.POINTER(lrp_arnoldi_stats)]),
     "lrp_posterior_destroy": (None, [C.c_void_p]),
     "lrp_posterior_eigs": (C.c_int, [C.c_void_p, _ip, C.c_void_p, C.c_void_p, C.c_int]),
     "lrp_posterior_query": (C.c_int, [C.c_void_p, C.POINTER(lrp_query), C.POINTER(lrp_query_result)]),
@@ -257,6 +262,7 @@ class Problem:
         nx, no, ns, nd = C.c_int(), C.c_int(), C.c_int(), C.c_int()
         _check(load().lrp_problem_sizes(handle, C.byref(nx), C.byref(no), C.byref(ns), C.byref(nd)))
         self.nx, self.n_obs, self.n_steps, self.n_data = nx.value, no.value, ns.value, nd.value
+        self.nt = int(desc.nt)
 
     def close(self):
         if self.handle:
@@ -472,6 +478,49 @@ def lrp_arnoldi(prob: Problem, max_steps: int, k: int = 0, eig_tol: float = 1e-6
     d["status"] = status
     return {"theta": re[:m] + 1j * im[:m], "H": np.array(H[:m + 1, :m]), "ranks_y": ry[:m].copy(),
             "ranks_q": rq[:m].copy(), "posterior": Posterior(h, prob) if posterior else None, "stats": d}
+
+
+def lrp_st_hessian_apply(prob: Problem, W, V):
+    """Htilde (W V^T) for the space-time source parameter; returns
+    (Wout, Vout, stats) with Wout Vout^T the truncated product."""
+    Wa = np.asfortranarray(np.asarray(W, dtype=np.float64).reshape(prob.nx, -1))
+    Va = np.asfortranarray(np.asarray(V, dtype=np.float64).reshape(prob.nt, -1))
+    rmax = prob.desc.time_rank_max
+    Wo = np.zeros((prob.nx, rmax), order="F")
+    Vo = np.zeros((prob.nt, rmax), order="F")
+    r = C.c_int()
+    st = lrp_apply_stats()
+    status = load().lrp_st_hessian_apply(prob.handle, Wa.shape[1], Wa.ctypes.data, prob.nx, Va.ctypes.data, prob.nt,
+                                         Wo.ctypes.data, Vo.ctypes.data, C.byref(r), C.byref(st))
+    _check(status, allow=(LRP_OK, LRP_ENOCONV))
+    d = st.as_dict()
+    d["status"] = status
+    return Wo[:, :r.value].copy(), Vo[:, :r.value].copy(), d
+
+
+def lrp_st_arnoldi(prob: Problem, max_steps: int, k: int = 0, eig_tol: float = 1e-6, eig_threshold: float = 0.0,
+                   W0=None, V0=None):
+    """Algorithm 1 on low-rank space-time vectors. Returns a dict: 'theta',
+    'H', 'ranks' (rank of each new Krylov vector), 'stats'."""
+    mmax = int(max_steps)
+    re = np.zeros(mmax)
+    im = np.zeros(mmax)
+    H = np.zeros((mmax + 1, mmax), order="F")
+    rk = np.zeros(mmax, dtype=np.int32)
+    r0, wp, vp, keep = 0, None, None, []
+    if W0 is not None:
+        Wa = np.asfortranarray(np.asarray(W0, dtype=np.float64).reshape(prob.nx, -1))
+        Va = np.asfortranarray(np.asarray(V0, dtype=np.float64).reshape(prob.nt, -1))
+        keep += [Wa, Va]
+        r0, wp, vp = Wa.shape[1], Wa.ctypes.data, Va.ctypes.data
+    st = lrp_arnoldi_stats()
+    status = load().lrp_st_arnoldi(prob.handle, mmax, int(k), float(eig_tol), float(eig_threshold), r0, wp, vp,
+                                   re.ctypes.data, im.ctypes.data, H.ctypes.data, rk.ctypes.data, C.byref(st))
+    _check(status, allow=(LRP_OK, LRP_ENOCONV))
+    m = st.n_steps
+    d = st.as_dict()
+    d["status"] = status
+    return {"theta": re[:m] + 1j * im[:m], "H": np.array(H[:m + 1, :m]), "ranks": rk[:m].copy(), "stats": d}
 
 
 def lrp_hessenberg_eig(H, want_schur: bool = False):

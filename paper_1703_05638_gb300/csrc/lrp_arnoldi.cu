@@ -780,3 +780,361 @@ extern "C" lrp_status lrp_arnoldi(lrp_problem* P, int max_steps, int k, double e
   }
   return result;
 }
+
+// ---------------------------------------------------------------------------
+// Low-rank space-time vectors (Sec. 4): X = A B^T with A: nx x r, B: nt x r.
+
+namespace lrp {
+namespace {
+
+// out = sum_ij Ga[i, j] Gb[i, j] (Ga, Gb: n entries); one CTA.
+__global__ void k_frob_dot(int n, const double* Ga, const double* Gb, double* out) {
+  __shared__ double red[32];
+  double d = 0.0;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) d += Ga[e] * Gb[e];
+  const double s = block_sum(d, red);
+  if (threadIdx.x == 0) *out = s;
+}
+
+// M = Ra Rb^T (R x R, all column-major, ld R)
+__global__ void k_small_abt(int R, const double* Ra, const double* Rb, double* M) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= R * R) return;
+  const int i = e % R, j = e / R;
+  double acc = 0.0;
+  for (int k = 0; k < R; ++k) acc += Ra[(size_t)k * R + i] * Rb[(size_t)k * R + j];
+  M[e] = acc;
+}
+
+// Scratch of the low-rank vector operations (sized for R <= kStMaxCols).
+constexpr int kStMaxCols = 112;
+struct StWS {
+  Buf<double> part, C, Csum, Rblk, Ra, Rb, M, th, Zaug, gs, scal, cat_a, cat_b;
+  Buf<int> iarr, stat;
+  size_t part_cap = 0;
+  int nx = 0, nt = 0;
+  cudaError_t init(int nx_, int nt_) {
+    nx = nx_;
+    nt = nt_;
+    const int R = kStMaxCols;
+    part_cap = (size_t)std::max(R, 16) * 16 * 128;
+    cudaError_t e = part.alloc(part_cap);
+    if (e == cudaSuccess) e = C.alloc((size_t)R * 64);
+    if (e == cudaSuccess) e = Csum.alloc((size_t)R * 64);
+    if (e == cudaSuccess) e = Rblk.alloc(64 * 64);
+    if (e == cudaSuccess) e = Ra.alloc((size_t)R * R);
+    if (e == cudaSuccess) e = Rb.alloc((size_t)R * R);
+    if (e == cudaSuccess) e = M.alloc((size_t)R * R);
+    if (e == cudaSuccess) e = th.alloc(2 * (size_t)R);
+    if (e == cudaSuccess) e = Zaug.alloc(4 * (size_t)R * R);
+    if (e == cudaSuccess) e = gs.alloc(block_gs_scratch_doubles());
+    if (e == cudaSuccess) e = scal.alloc(4);
+    if (e == cudaSuccess) e = cat_a.alloc((size_t)nx * R);
+    if (e == cudaSuccess) e = cat_b.alloc((size_t)nt * R);
+    if (e == cudaSuccess) e = iarr.alloc(2);
+    if (e == cudaSuccess) e = stat.alloc(1);
+    return e;
+  }
+};
+
+// Thin QR of the rows x R matrix A (in place: A <- Q) with R <= kStMaxCols:
+// blocks of up to 64 columns, each projected on the previous blocks twice
+// (block CGS2; coefficients into the upper blocks of Rout) and then
+// factorised by the rank-revealing block Gram-Schmidt. Rout: R x R, ld R.
+cudaError_t qr_tall(cudaStream_t s, StWS& w, int rows, int R, double* A, double* Rout) {
+  cudaError_t e = cudaMemsetAsync(Rout, 0, (size_t)R * R * sizeof(double), s);
+  for (int c0 = 0; c0 < R && e == cudaSuccess; c0 += 64) {
+    const int nb = std::min(64, R - c0);
+    double* B = A + (size_t)c0 * rows;
+    if (c0 > 0) {
+      e = cudaMemsetAsync(w.Csum.p, 0, (size_t)c0 * nb * sizeof(double), s);
+      for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
+        e = gemm_tn(s, rows, c0, nb, A, rows, B, rows, w.C.p, c0, 1.0, 0.0, w.part.p, w.part_cap);
+        if (e == cudaSuccess) e = gemm_nn(s, rows, c0, nb, -1.0, A, rows, w.C.p, c0, 1.0, B, rows);
+        if (e == cudaSuccess) e = axpby(s, (size_t)c0 * nb, 1.0, w.C.p, 1.0, w.Csum.p);
+      }
+      if (e == cudaSuccess) e = set_rect(s, Rout, R, 0, c0, c0, nb, w.Csum.p, c0, false);
+    }
+    if (e == cudaSuccess) e = block_gs(s, 1, rows, nb, B, 0, rows, w.Rblk.p, 0, 1e-14, nullptr, nullptr, w.gs.p);
+    if (e == cudaSuccess) e = set_rect(s, Rout, R, c0, c0, nb, nb, w.Rblk.p, nb, false);
+  }
+  return e;
+}
+
+// <X, Y> = sum (A_X^T A_Y) .* (B_X^T B_Y); result on the host.
+lrp_status lr_dot(cudaStream_t s, StWS& w, int rx, const double* Ax, const double* Bx, int ry, const double* Ay,
+                  const double* By, double* out) {
+  if (rx == 0 || ry == 0) {
+    *out = 0.0;
+    return LRP_OK;
+  }
+  CKA(gemm_tn(s, w.nx, rx, ry, Ax, w.nx, Ay, w.nx, w.Ra.p, rx, 1.0, 0.0, w.part.p, w.part_cap));
+  CKA(gemm_tn(s, w.nt, rx, ry, Bx, w.nt, By, w.nt, w.Rb.p, rx, 1.0, 0.0, w.part.p, w.part_cap));
+  note_launch();
+  k_frob_dot<<<1, 256, 0, s>>>(rx * ry, w.Ra.p, w.Rb.p, w.scal.p);
+  CKA(cudaGetLastError());
+  CKA(cudaMemcpyAsync(out, w.scal.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CKA(cudaStreamSynchronize(s));
+  return LRP_OK;
+}
+
+// Rounds A B^T (R columns in w.cat_a / w.cat_b, destroyed) to the smallest
+// rank whose discarded Frobenius tail is at most tol ||A B^T||_F, capped at
+// rmax: thin QR of both factors, SVD of the R x R core Ra Rb^T (one-sided
+// Jacobi), A' = Q_A U_r S_r, B' = Q_B Z_r into Aout, Bout. *norm = ||A' B'^T||_F.
+lrp_status lr_round(cudaStream_t s, StWS& w, int R, double tol, int rmax, double* Aout, double* Bout, int* r_out,
+                    double* norm, double* err) {
+  *r_out = 0;
+  *norm = 0.0;
+  *err = 0.0;
+  if (R == 0) return LRP_OK;
+  if (R > kStMaxCols) {
+    set_error("low-rank vector rounding: more than 112 columns");
+    return LRP_EINVAL;
+  }
+  CKA(qr_tall(s, w, w.nx, R, w.cat_a.p, w.Ra.p));
+  CKA(qr_tall(s, w, w.nt, R, w.cat_b.p, w.Rb.p));
+  note_launch();
+  k_small_abt<<<(R * R + 255) / 256, 256, 0, s>>>(R, w.Ra.p, w.Rb.p, w.M.p);
+  CKA(cudaGetLastError());
+  std::vector<double> th;
+  {
+    lrp_status r = core_svd(s, R, w.M.p, w.th.p, w.Zaug.p, w.iarr.p, w.stat.p, &th);
+    if (r != LRP_OK) return r;
+  }
+  double fro2 = 0.0;
+  for (double x : th) fro2 += x * x;
+  std::vector<double> tail(R + 1, 0.0);
+  for (int i = R - 1; i >= 0; --i) tail[i] = tail[i + 1] + th[i] * th[i];
+  int rn = 0;
+  while (rn < R && tail[rn] > tol * tol * fro2) ++rn;
+  if (rn == 0 && R > 0 && th[0] > 0) rn = 1;
+  rn = std::min(rn, rmax);
+  *err = fro2 > 0 ? std::sqrt(tail[rn] / fro2) : 0.0;
+  *norm = std::sqrt(std::max(fro2 - tail[rn], 0.0));
+  *r_out = rn;
+  if (rn == 0) return LRP_OK;
+  const double* U = w.Zaug.p;
+  const double* Zv = U + (size_t)R * R;
+  CKA(gemm_nn(s, w.nx, R, rn, 1.0, w.cat_a.p, w.nx, U, R, 0.0, Aout, w.nx));
+  CKA(scale_cols(s, w.nx, rn, w.th.p, Aout, w.nx));
+  CKA(gemm_nn(s, w.nt, R, rn, 1.0, w.cat_b.p, w.nt, Zv, R, 0.0, Bout, w.nt));
+  return LRP_OK;
+}
+
+}  // namespace
+}  // namespace lrp
+
+extern "C" lrp_status lrp_st_hessian_apply(lrp_problem* P, int r, const double* W, int ldw, const double* V, int ldv,
+                                           double* Wout, double* Vout, int* r_out, lrp_apply_stats* st) {
+  if (!P || r < 0 || r > 4096 || (r > 0 && (!W || !V || ldw < P->nx || ldv < P->nt)) || !Wout || !Vout || !r_out) {
+    set_error("lrp_st_hessian_apply: invalid argument");
+    return LRP_EINVAL;
+  }
+  for (const void* a : {(const void*)W, (const void*)V, (const void*)Wout, (const void*)Vout}) {
+    if (!a) continue;
+    lrp_status sd = check_on_device(P->device, a, "lrp_st_hessian_apply");
+    if (sd != LRP_OK) return sd;
+  }
+  cudaSetDevice(P->device);
+  const int nx = P->nx, nt = P->nt, rmax = P->desc.time_rank_max;
+  cudaStream_t s = P->stream;
+  Buf<double> dW, dV, oW, oV;
+  CKA(dW.alloc((size_t)nx * std::max(r, 1)));
+  CKA(dV.alloc((size_t)nt * std::max(r, 1)));
+  CKA(oW.alloc((size_t)nx * rmax));
+  CKA(oV.alloc((size_t)nt * rmax));
+  if (r > 0) {
+    CKA(cudaMemcpy2DAsync(dW.p, (size_t)nx * sizeof(double), W, (size_t)ldw * sizeof(double), (size_t)nx * sizeof(double),
+                          r, cudaMemcpyDefault, s));
+    CKA(cudaMemcpy2DAsync(dV.p, (size_t)nt * sizeof(double), V, (size_t)ldv * sizeof(double), (size_t)nt * sizeof(double),
+                          r, cudaMemcpyDefault, s));
+  }
+  int ro = 0;
+  lrp_status res = st_hessian_impl(P, r, dW.p, nx, dV.p, nt, oW.p, oV.p, &ro, st);
+  if (res != LRP_OK && res != LRP_ENOCONV) return res;
+  if (ro > 0) {
+    CKA(cudaMemcpyAsync(Wout, oW.p, (size_t)nx * ro * sizeof(double), cudaMemcpyDefault, s));
+    CKA(cudaMemcpyAsync(Vout, oV.p, (size_t)nt * ro * sizeof(double), cudaMemcpyDefault, s));
+  }
+  CKA(cudaStreamSynchronize(s));
+  *r_out = ro;
+  return res;
+}
+
+extern "C" lrp_status lrp_st_arnoldi(lrp_problem* P, int max_steps, int k, double eig_tol, double eig_threshold, int r0,
+                                     const double* W0, const double* V0, double* theta_re, double* theta_im,
+                                     double* H_out, int* ranks, lrp_arnoldi_stats* stats) {
+  if (!P || max_steps < 1 || max_steps > 2048 || (long long)max_steps > (long long)P->nx * P->nt || k < 0 ||
+      eig_threshold < 0.0 || (eig_threshold == 0.0 && k < 1) || r0 < 0 || r0 > kStMaxCols ||
+      (r0 > 0 && (!W0 || !V0)) || P->desc.time_rank_max > kStMaxCols / 2) {
+    set_error("lrp_st_arnoldi: need 1 <= max_steps <= min(nx nt, 2048), k >= 1 without a threshold, "
+              "0 <= r0 <= 112 with start factors, time_rank_max <= 56");
+    return LRP_EINVAL;
+  }
+  for (const void* a : {(const void*)W0, (const void*)V0}) {
+    if (!a) continue;
+    lrp_status sd = check_on_device(P->device, a, "lrp_st_arnoldi");
+    if (sd != LRP_OK) return sd;
+  }
+  cudaSetDevice(P->device);
+  auto t0 = std::chrono::steady_clock::now();
+  const int nx = P->nx, nt = P->nt, rmax = P->desc.time_rank_max, mmax = max_steps, ldh = mmax + 1;
+  const double tol = P->desc.time_trunc_tol;
+  cudaStream_t s = P->stream;
+  ArnoldiRun A;
+  A.P = P;
+  A.nx = nx;
+  A.mmax = mmax;
+  A.k = k;
+  A.eig_tol = eig_tol > 0.0 ? eig_tol : 1e-6;
+  A.eig_threshold = eig_threshold;
+  CKA(A.H.alloc((size_t)ldh * mmax));
+  CKA(A.Hm.alloc((size_t)mmax * mmax));
+  CKA(A.Zm.alloc((size_t)mmax * mmax));
+  CKA(A.wbuf.alloc(2 * (size_t)mmax));
+  CKA(A.X.alloc((size_t)mmax * mmax));
+  CKA(A.Y.alloc((size_t)mmax * mmax));
+  CKA(A.res.alloc(mmax));
+  CKA(A.pos.alloc(mmax));
+  CKA(A.hstat.alloc(1));
+  A.hH.assign((size_t)ldh * mmax, 0.0);
+  CKA(cudaMemsetAsync(A.H.p, 0, (size_t)ldh * mmax * sizeof(double), s));
+  StWS w;
+  CKA(w.init(nx, nt));
+  // the basis: factors of v_1 .. v_{m+1}
+  Buf<double> BA, BB, Aw, Bw;
+  CKA(BA.alloc((size_t)(mmax + 1) * nx * rmax));
+  CKA(BB.alloc((size_t)(mmax + 1) * nt * rmax));
+  CKA(Aw.alloc((size_t)nx * rmax));
+  CKA(Bw.alloc((size_t)nt * rmax));
+  std::vector<int> rv(mmax + 1, 0);
+  auto fa = [&](int j) { return BA.p + (size_t)j * nx * rmax; };
+  auto fb = [&](int j) { return BB.p + (size_t)j * nt * rmax; };
+  // start: the given factors (or one pseudo-random rank-1 pair), rounded and normalised
+  int rs = r0;
+  if (r0 > 0) {
+    CKA(cudaMemcpyAsync(w.cat_a.p, W0, (size_t)nx * r0 * sizeof(double), cudaMemcpyDefault, s));
+    CKA(cudaMemcpyAsync(w.cat_b.p, V0, (size_t)nt * r0 * sizeof(double), cudaMemcpyDefault, s));
+  } else {
+    rs = 1;
+    CKA(fill_random(s, nx, 1, w.cat_a.p, nx, nullptr, 0x57A7ull));
+    CKA(fill_random(s, nt, 1, w.cat_b.p, nt, nullptr, 0x57A8ull));
+  }
+  double nrm = 0.0, err = 0.0;
+  {
+    lrp_status r = lr_round(s, w, rs, 0.0, rmax, fa(0), fb(0), &rv[0], &nrm, &err);
+    if (r != LRP_OK) return r;
+  }
+  if (nrm <= 0.0) {
+    set_error("lrp_st_arnoldi: zero start vector");
+    return LRP_EINVAL;
+  }
+  CKA(axpby(s, (size_t)nx * rv[0], 0.0, fa(0), 1.0 / nrm, fa(0)));
+  bool converged = false, breakdown = false;
+  int rank_v_max = rv[0], rank_q_max = 0;
+  double ms_apply = 0.0;
+  for (int j = 0; j < mmax; ++j) {
+    lrp_apply_stats ast;
+    std::memset(&ast, 0, sizeof(ast));
+    int rw = 0;
+    auto ta = std::chrono::steady_clock::now();
+    lrp_status r = st_hessian_impl(P, rv[j], fa(j), nx, fb(j), nt, Aw.p, Bw.p, &rw, &ast);
+    ms_apply += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ta).count();
+    if (r == LRP_ENOCONV)
+      A.apply_noconv = true;
+    else if (r != LRP_OK)
+      return r;
+    rank_q_max = std::max(rank_q_max, rw);
+    // modified Gram-Schmidt on factored vectors, rounding after every update
+    for (int i = 0; i <= j; ++i) {
+      double h = 0.0;
+      lrp_status d = lr_dot(s, w, rw, Aw.p, Bw.p, rv[i], fa(i), fb(i), &h);
+      if (d != LRP_OK) return d;
+      A.hH[(size_t)j * ldh + i] = h;
+      const int ri = rv[i];
+      if (rw > 0) {
+        CKA(cudaMemcpyAsync(w.cat_a.p, Aw.p, (size_t)nx * rw * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CKA(cudaMemcpyAsync(w.cat_b.p, Bw.p, (size_t)nt * rw * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      }
+      if (ri > 0) {
+        double* ca = w.cat_a.p + (size_t)nx * rw;
+        CKA(cudaMemcpyAsync(ca, fa(i), (size_t)nx * ri * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CKA(axpby(s, (size_t)nx * ri, 0.0, ca, -h, ca));
+        CKA(cudaMemcpyAsync(w.cat_b.p + (size_t)nt * rw, fb(i), (size_t)nt * ri * sizeof(double),
+                            cudaMemcpyDeviceToDevice, s));
+      }
+      lrp_status rr = lr_round(s, w, rw + ri, tol, rmax, Aw.p, Bw.p, &rw, &nrm, &err);
+      if (rr != LRP_OK) return rr;
+    }
+    A.hH[(size_t)j * ldh + j + 1] = nrm;
+    if (ranks) ranks[j] = rw;
+    rank_v_max = std::max(rank_v_max, rw);
+    rv[j + 1] = rw;
+    if (rw > 0) {
+      CKA(cudaMemcpyAsync(fa(j + 1), Aw.p, (size_t)nx * rw * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      CKA(axpby(s, (size_t)nx * rw, 0.0, fa(j + 1), nrm > 0.0 ? 1.0 / nrm : 0.0, fa(j + 1)));
+      CKA(cudaMemcpyAsync(fb(j + 1), Bw.p, (size_t)nt * rw * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    CKA(cudaMemcpyAsync(A.H.p + (size_t)j * ldh, A.hH.data() + (size_t)j * ldh, (size_t)(j + 2) * sizeof(double),
+                        cudaMemcpyHostToDevice, s));
+    A.m = j + 1;
+    double hnorm = 0.0;
+    for (int i = 0; i <= j; ++i) hnorm = std::max(hnorm, std::fabs(A.hH[(size_t)j * ldh + i]));
+    breakdown = nrm <= 1e-14 * hnorm;
+    const int mm = A.m;
+    const bool due = mm <= 32 || mm % std::max(1, mm / 16) == 0;
+    const bool enough = A.eig_threshold > 0.0 ? mm >= 8 : mm >= A.k;
+    if ((due && enough) || breakdown || j + 1 == mmax) {
+      bool ok = false;
+      lrp_status c = arnoldi_check(A, &ok);
+      if (c != LRP_OK) return c;
+      if (ok || breakdown) {
+        converged = true;
+        break;
+      }
+    }
+  }
+  const int m = A.m;
+  for (int q = 0; q < m; ++q) {
+    if (theta_re) theta_re[q] = A.wr[A.order[q]];
+    if (theta_im) theta_im[q] = A.wi[A.order[q]];
+  }
+  if (H_out) CKA(cudaMemcpy(H_out, A.hH.data(), A.hH.size() * sizeof(double), cudaMemcpyDefault));
+  if (stats) {
+    double asym = 0.0, hf = 0.0, max_imag = 0.0, max_res = 0.0;
+    int n_complex = 0;
+    for (int c = 0; c < m; ++c)
+      for (int r = 0; r < m; ++r) {
+        const double a = A.hH[(size_t)c * ldh + r], b = A.hH[(size_t)r * ldh + c];
+        asym += (a - b) * (a - b);
+        hf += a * a;
+      }
+    for (int q = 0; q < m; ++q) {
+      if (A.wi[q] != 0.0) ++n_complex;
+      max_imag = std::max(max_imag, std::fabs(A.wi[q]));
+    }
+    for (double x : A.rres) max_res = std::max(max_res, x);
+    const double th1 = A.theta1 > 0.0 ? A.theta1 : 1.0;
+    std::memset(stats, 0, sizeof(*stats));
+    stats->n_steps = m;
+    stats->k_converged = converged ? (int)A.sel.size() : 0;
+    stats->n_complex = n_complex;
+    stats->max_imag = max_imag / th1;
+    stats->hess_asym = hf > 0.0 ? std::sqrt(asym / hf) : 0.0;
+    stats->max_ritz_resid = max_res / th1;
+    stats->time_rank_max = rank_v_max;
+    stats->adj_rank_max = rank_q_max;
+    stats->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    stats->ms_apply = ms_apply;
+  }
+  if (!converged) {
+    set_error("Arnoldi reached max_steps before the wanted Ritz values converged");
+    return LRP_ENOCONV;
+  }
+  if (A.apply_noconv) {
+    set_error("a solve of a Hessian apply missed its tolerance within pcg_maxit");
+    return LRP_ENOCONV;
+  }
+  return LRP_OK;
+}

@@ -74,7 +74,8 @@ enum : unsigned {
   ST_STORE_Y = 1u << 6,     // store the result buffer to column-major Y
   ST_STORE_D = 1u << 7,     // store the observations (unweighted) to column-major D
   ST_TRAJ = 1u << 8,        // copy every forward state into the trajectory chunk buffer
-  ST_TRAJ_ADJ = 1u << 9     // copy every adjoint state q_n into column n-1 of the trajectory buffer
+  ST_TRAJ_ADJ = 1u << 9,    // copy every adjoint state q_n into column n-1 of the trajectory buffer
+  ST_SOURCE = 1u << 10      // forward steps solve (I + tau L) y_n = y_{n-1} + s_scale W V[n-1, :]^T (one column)
 };
 
 enum : int { STAT_NOCONV = 1, STAT_NONFINITE = 2 };
@@ -122,6 +123,7 @@ struct SweepParams {
   double* Y; int ldy;
   const double* Din; int lddin;
   double* Dout; int lddout;
+  const double* src_W; const double* src_V; int src_r, src_ldw, src_ldv; double src_scale;  // ST_SOURCE factors
   double* traj; int traj_ld; int traj_cols;  // trajectory buffer: [team col][step in chunk (forward) or step-1 (adjoint)][nx]
   // workspace
   char* ws;
@@ -184,6 +186,11 @@ struct lrp_problem {
   // allocation-free call; NULL otherwise)
   char* ws_fixed;
   size_t ws_fixed_bytes;
+  // factored source of the forward sweep (set only for the duration of a
+  // space-time Hessian product; NULL otherwise)
+  const double* src_W = nullptr;
+  const double* src_V = nullptr;
+  int src_r = 0, src_ldv = 0;
   lrp::SolveCfg cfg;
   uint64_t hash;
   // sweep-kernel ledger (lrp_sweep_profile): CUDA-event time and algorithmic
@@ -252,4 +259,14 @@ lrp_status ensure_workspace(lrp_problem* P, size_t bytes);
 // Y = the truncated product of Algorithm 1 (LRP_LOWRANK_SOURCE); X, Y device arrays.
 lrp_status lowrank_hessian_impl(lrp_problem* P, int nvec, const double* X, int ldx, double* Y, int ldy,
                                 bool misfit, lrp_apply_stats* stats);
+// Stored one-column trajectory -> W diag(sig), V (streaming truncation).
+lrp_status compress_trajectory(lrp_problem* P, const double* traj, double* Wout, double* Vout, int* r_out,
+                               double* err);
+// The space-time parameter's Hessian on factors (W, V) -> (Wout, Vout, *r_out).
+lrp_status st_hessian_impl(lrp_problem* P, int r, const double* W, int ldw, const double* V, int ldv, double* Wout,
+                           double* Vout, int* r_out, lrp_apply_stats* stats);
+// General m x m SVD by one-sided Jacobi (th: singular values, Z = [U | V]).
+lrp_status core_svd(cudaStream_t s, int m, const double* M, double* th, double* Z, int* iarr, int* stat,
+                    std::vector<double>* th_host);
+cudaError_t scale_cols(cudaStream_t s, int nx, int r, const double* sig, double* W, int ldw);
 }  // namespace lrp

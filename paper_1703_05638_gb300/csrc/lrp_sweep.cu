@@ -183,7 +183,8 @@ lrp_status sweep_enqueue(lrp_problem* Pr, unsigned stages, int nvec, const doubl
   // Band kernel (2D, kappa = 1, one column per team, FP32 inner): every CTA
   // keeps its band of the finest level and all coarse levels in shared memory.
   bool fast = false;
-  if (Pr->kernel_variant != 1 && Pr->dim == 2 && mixed && BV == 1 && !Pr->step.has_kappa && !Pr->step.conv &&
+  if (Pr->kernel_variant != 1 && !(stages & ST_SOURCE) && Pr->dim == 2 && mixed && BV == 1 && !Pr->step.has_kappa &&
+      !Pr->step.conv &&
       Pr->L >= 2 &&
       Pr->n <= 128) {
     const int n = Pr->n;
@@ -240,6 +241,12 @@ lrp_status sweep_enqueue(lrp_problem* Pr, unsigned stages, int nvec, const doubl
   prm.t_end = t_end >= 0 ? t_end : Pr->last_obs;
   prm.traj = traj;
   prm.traj_ld = Pr->nx;
+  prm.src_W = Pr->src_W;
+  prm.src_V = Pr->src_V;
+  prm.src_r = (stages & ST_SOURCE) ? Pr->src_r : 0;
+  prm.src_ldw = Pr->nx;
+  prm.src_ldv = Pr->src_ldv;
+  prm.src_scale = Pr->tau;
   prm.traj_cols = traj_cols;
   prm.adj_begin = Pr->last_obs;
   prm.obs_every = Pr->desc.obs_every;

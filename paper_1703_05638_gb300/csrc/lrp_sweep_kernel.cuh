@@ -766,6 +766,17 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
   }
   if (P.stages & ST_FORWARD) {
     for (int n = P.t_begin + 1; n <= P.t_end; ++n) {
+      if (P.stages & ST_SOURCE) {
+        // y_{n-1} + tau u_n with u_n = W V[n-1, :]^T (also the solve's start)
+        for (int it = t.g; it < items0; it += t.S) {
+          const int p = it >> t.bvs;
+          double u = 0.0;
+          for (int i = 0; i < P.src_r; ++i)
+            u += P.src_W[(size_t)i * P.src_ldw + p] * P.src_V[(size_t)i * P.src_ldv + n - 1];
+          w.dbuf[cur][it] += P.src_scale * u;
+        }
+        team_sync(t);
+      }
       double* X1 = w.dbuf[(cur + 1) % 3];
       double* X2 = w.dbuf[(cur + 2) % 3];
       double* res = solve_any<T, DIM, MIXED>(t, P, P.step, w, sm, w.dbuf[cur], nullptr, w.dbuf[cur],

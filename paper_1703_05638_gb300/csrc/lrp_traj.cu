@@ -708,6 +708,143 @@ lrp_status lowrank_hessian_impl(lrp_problem* P, int nvec, const double* X, int l
   return sa.result;
 }
 
+
+// SVD of a general m x m matrix M (column-major, ld m; 1 <= m <= 112) by the
+// one-sided Jacobi kernel of the trajectory compression (a core with no
+// carried singular values): th (device, >= 2m) gets the singular values in
+// decreasing order, Z (device, >= 4 m^2) = [U | V] (two m x m blocks, ld m).
+// The values are also returned on the host (the stream is synchronised).
+lrp_status core_svd(cudaStream_t s, int m, const double* M, double* th, double* Z, int* iarr, int* stat,
+                    std::vector<double>* th_host) {
+  const int mp = m + (m & 1);
+  const size_t smem = (2 * (size_t)mp * mp + mp) * sizeof(double) + mp * sizeof(int);
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  CKT(cudaFuncGetAttributes(&fa, k_core_svd));
+  const int cap = optin - (int)fa.sharedSizeBytes;
+  if ((long long)smem > cap) {
+    set_error("core SVD larger than shared memory");
+    return LRP_EINVAL;
+  }
+  CKT(cudaFuncSetAttribute(k_core_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+  CKT(cudaMemsetAsync(iarr, 0, sizeof(int), s));
+  CKT(cudaMemsetAsync(stat, 0, sizeof(int), s));
+  note_launch();
+  k_core_svd<<<1, 512, smem, s>>>(iarr, m, nullptr, 0, nullptr, 0, M, 0, th, 0, Z, 0, stat);
+  CKT(cudaGetLastError());
+  th_host->assign(m, 0.0);
+  CKT(cudaMemcpyAsync(th_host->data(), th, m * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CKT(cudaStreamSynchronize(s));
+  for (double& x : *th_host) x = std::max(x, 0.0);
+  return LRP_OK;
+}
+
+cudaError_t scale_cols(cudaStream_t s, int nx, int r, const double* sig, double* W, int ldw) {
+  if (r <= 0) return cudaSuccess;
+  dim3 grid((nx + 255) / 256, r);
+  note_launch();
+  k_scale_cols<<<grid, 256, 0, s>>>(nx, r, sig, W, ldw);
+  return cudaGetLastError();
+}
+
+// Compresses a stored trajectory of one column (nt x nx, step n at
+// traj + (n-1)*nx) into W diag(sig) V^T by the streaming recompression;
+// writes W diag(sig) (nx x r, ld nx) to Wout and V (nt x r, ld nt) to Vout,
+// *r_out = r, *err = the certified relative truncation error bound.
+lrp_status compress_trajectory(lrp_problem* P, const double* traj, double* Wout, double* Vout, int* r_out,
+                               double* err) {
+  std::vector<TrajCol> cols;
+  TrajWS ws;
+  {
+    lrp_status r = traj_alloc(P, 1, cols, ws);
+    if (r != LRP_OK) return r;
+  }
+  const int nx = P->nx, nt = P->nt;
+  const int K = (nt + ws.s - 1) / ws.s;
+  {
+    lrp_status r = absorb_stored(P, 1, traj, cols, ws, P->desc.time_trunc_tol / K);
+    if (r != LRP_OK) return r;
+  }
+  int rank = 0;
+  factor_summary(cols, &rank, err, nullptr);
+  const TrajCol& tc = cols[0];
+  if (tc.r > 0) {
+    CKT(cudaMemcpyAsync(Wout, tc.Qa.p, (size_t)nx * tc.r * sizeof(double), cudaMemcpyDeviceToDevice, P->stream));
+    dim3 grid((nx + 255) / 256, tc.r);
+    note_launch();
+    k_scale_cols<<<grid, 256, 0, P->stream>>>(nx, tc.r, ws.sig.p, Wout, nx);
+    CKT(cudaGetLastError());
+    CKT(cudaMemcpyAsync(Vout, tc.V.p, (size_t)nt * tc.r * sizeof(double), cudaMemcpyDeviceToDevice, P->stream));
+  }
+  CKT(cudaStreamSynchronize(P->stream));
+  *r_out = tc.r;
+  return LRP_OK;
+}
+
+// The space-time parameter's Hessian on a factored vector U = W V^T
+// (W: nx x r, V: nt x r; device): Z = Gamma_x^{1/2} W (prior solves on the
+// r columns), the forward sweep with the source tau u_n = tau Z V[n-1, :]^T
+// added before each step's solve (y_0 = 0) and the fused observation, the
+// adjoint sweep storing q_1 .. q_nt, its streaming truncation W_Q V_Q^T,
+// and the result factors (tau Gamma_x^{1/2} W_Q, V_Q). Wout: nx x
+// time_rank_max, Vout: nt x time_rank_max (device).
+lrp_status st_hessian_impl(lrp_problem* P, int r, const double* W, int ldw, const double* V, int ldv, double* Wout,
+                           double* Vout, int* r_out, lrp_apply_stats* stats) {
+  auto t0 = std::chrono::steady_clock::now();
+  const int nx = P->nx, nt = P->nt;
+  DBuf Z, Q, X0, Wq;
+  CKT(Z.alloc((size_t)nx * std::max(r, 1)));
+  CKT(Q.alloc((size_t)nt * nx));
+  CKT(X0.alloc(nx));
+  CKT(Wq.alloc((size_t)nx * P->desc.time_rank_max));
+  SweepAcc sa;
+  if (r > 0) {
+    lrp_apply_stats st;
+    lrp_status sres = run_sweep_ex(P, ST_LOAD_X | ST_PRIOR_IN | ST_STORE_Y, r, W, ldw, Z.p, nx, nullptr, 0, nullptr,
+                                   0, &st, 0, 0, nullptr, 0);
+    if ((sres = sa.fold(sres, st)) != LRP_OK) return sres;
+  }
+  CKT(cudaMemsetAsync(X0.p, 0, (size_t)nx * sizeof(double), P->stream));
+  CKT(cudaMemsetAsync(Q.p, 0, (size_t)nt * nx * sizeof(double), P->stream));
+  P->src_W = Z.p;
+  P->src_V = V;
+  P->src_r = r;
+  P->src_ldv = ldv;
+  {
+    lrp_apply_stats st;
+    lrp_status sres = run_sweep_ex(P, ST_LOAD_X | ST_SOURCE | ST_FORWARD | ST_ADJOINT | ST_TRAJ_ADJ, 1, X0.p, nx,
+                                   nullptr, 0, nullptr, 0, nullptr, 0, &st, 0, -1, Q.p, nt);
+    P->src_W = nullptr;
+    P->src_V = nullptr;
+    P->src_r = 0;
+    if ((sres = sa.fold(sres, st)) != LRP_OK) return sres;
+  }
+  int rq = 0;
+  double err = 0.0;
+  {
+    lrp_status c = compress_trajectory(P, Q.p, Wq.p, Vout, &rq, &err);
+    if (c != LRP_OK) return c;
+  }
+  if (rq > 0) {
+    lrp_apply_stats st;
+    lrp_status sres = run_sweep_ex(P, ST_LOAD_X | ST_PRIOR_IN | ST_STORE_Y, rq, Wq.p, nx, Wout, nx, nullptr, 0,
+                                   nullptr, 0, &st, 0, 0, nullptr, 0);
+    if ((sres = sa.fold(sres, st)) != LRP_OK) return sres;
+    CKT(axpby(P->stream, (size_t)nx * rq, 0.0, Wout, P->tau, Wout));
+  }
+  CKT(cudaStreamSynchronize(P->stream));
+  *r_out = rq;
+  if (stats) {
+    sa.fill(stats);
+    stats->adj_rank_max = rq;
+    stats->adj_trunc_err = err;
+    stats->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return sa.result;
+}
+
 }  // namespace lrp
 
 using namespace lrp;
