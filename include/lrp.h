@@ -117,7 +117,7 @@ typedef struct {
   int obs_every;            /* observed steps obs_every, 2*obs_every, ..., <= nt */
   double sigma;             /* noise standard deviation */
   int precision;            /* LRP_FP64 or LRP_MIXED */
-  double time_trunc_tol;    /* relative Frobenius tolerance of the time factors (e.g. 1e-8) */
+  double time_trunc_tol;    /* relative Frobenius tolerance of the time factors (<= 0 -> 1e-8) */
   int time_rank_max;        /* rank cap of the time factors (e.g. 40) */
   int time_chunk;           /* steps buffered between recompressions (0 -> 16, at most 64) */
   double solve_rtol;        /* relative residual per spatial solve (0 -> 1e-13 FP64, 1e-10 mixed) */

@@ -767,7 +767,10 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
   if (P.stages & ST_FORWARD) {
     for (int n = P.t_begin + 1; n <= P.t_end; ++n) {
       if (P.stages & ST_SOURCE) {
-        // y_{n-1} + tau u_n with u_n = W V[n-1, :]^T (also the solve's start)
+        // y_{n-1} + tau u_n with u_n = W V[n-1, :]^T (also the solve's
+        // start). The previous step's fused observation reads y_{n-1} with no
+        // barrier after it: wait for it before y_{n-1} is overwritten.
+        team_sync(t);
         for (int it = t.g; it < items0; it += t.S) {
           const int p = it >> t.bvs;
           double u = 0.0;

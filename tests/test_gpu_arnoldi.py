@@ -124,11 +124,12 @@ def test_lowrank_source_apply_matches_oracle(precision, pde):
 
 @pytest.mark.parametrize("precision", [lrp.LRP_FP64, lrp.LRP_MIXED])
 def test_lowrank_source_without_truncation_is_exact(precision):
-    """time_trunc_tol = 0 and a rank cap above nt: nothing is discarded and
-    the truncated product is the exact Hessian apply."""
+    """time_trunc_tol = 1e-15 and a rank cap above nt: nothing of
+    significance is discarded and the truncated product is the exact Hessian
+    apply."""
     spec = synth.small_spec(dim=2, n=15, nt=12, obs_every=3, n_obs=8, sigma=1e-2, seed=83)
     P = OProblem(spec)
-    G = lrp.lrp_setup_problem(spec, precision=precision, time_trunc_tol=0.0, time_rank_max=16, time_chunk=5)
+    G = lrp.lrp_setup_problem(spec, precision=precision, time_trunc_tol=1e-15, time_rank_max=16, time_chunk=5)
     X = synth.normal_block(P.nx, 3, 84)
     Y, st = lrp.lrp_hessian_apply(G, X, lrp.LRP_LOWRANK_SOURCE)
     assert relerr(Y, P.hessian_apply(X)) < TOL[precision], st
