@@ -30,6 +30,10 @@ Modules and the passages they follow:
 * ``spacetime``  — a space-time source as the parameter (Sec. 4): its
   forward map, adjoint and Hessian, low-rank space-time vectors (truncation,
   inner product) and Algorithm 1 on them (Eq. (lanczos1)-(lanczos2)).
+* ``als``        — the alternating low-rank solve of the space-time system
+  (Sec. 6.1, Eq. (st_pde), (amen_1), (amen_2)): space steps by Galerkin
+  projection in time (a Sylvester equation), time steps by Galerkin
+  projection in space (block forward substitution).
 * ``timefactors``— the low-rank-in-time factorisation Y ~ W V^T (Sec. 3) by
   truncated SVD of the full trajectory, and the streaming recompression the
   GPU uses (thin QR of [W | new columns], small SVD, truncation; Sec. 4).

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import synth
-from oracle import lowrank, operators, observe, posterior, spacetime, spectrum, timefactors
+from oracle import als, lowrank, operators, observe, posterior, spacetime, spectrum, timefactors
 from oracle.problem import Problem
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -775,3 +775,84 @@ def test_lr_arnoldi_equals_dense_arnoldi():
     np.testing.assert_allclose(th_t.real[:4], lam[:4], rtol=1e-7)
     assert max(ranks_t) <= min(P.nx, P.nt, 40)
     assert abs(spacetime.dot(basis[3], basis[3]) - 1.0) < 1e-12
+
+
+# ---------------------------------------------------------------- alternating space-time solve (Sec. 6.1)
+def _als_setup(n=7, nt=20, dim=2):
+    P = Problem(_spec(n=n, nt=nt, dim=dim))
+    A = P.K.toarray()
+    return P, A
+
+
+def test_als_full_rank_is_time_stepping():
+    """With r = nt the time basis spans everything: one sweep solves the
+    space-time system (Eq. (st_pde)) exactly and reproduces the
+    implicit-Euler trajectory of the initial condition (f_1 = u)."""
+    P, A = _als_setup()
+    u = synth.normal_block(P.nx, 1, 51)[:, 0]
+    Wf = u[:, None]
+    Vf = np.zeros((P.nt, 1))
+    Vf[0, 0] = 1.0
+    V0, _ = np.linalg.qr(synth.normal_block(P.nt, P.nt, 52))
+    W, V, res = als.als_solve(A, Wf, Vf, V0, 1)
+    Y = P.trajectory(u)
+    assert res[0] < 1e-12
+    assert np.max(np.abs(W @ V.T - Y)) <= 1e-12 * np.abs(Y).max()
+
+
+@pytest.mark.parametrize("modes", [[(1, 1)], [(1, 1), (2, 3)]])
+def test_als_recovers_exact_low_rank_solution(modes):
+    """u a sum of k sine modes (eigenvectors of the Dirichlet Laplacian,
+    Sec. 5): y_n = sum_k (1 + tau mu_k)^-n u_k has rank k, and the
+    alternating solve with r = k from a random start converges to it."""
+    P, A = _als_setup(n=15, nt=40)
+    n = P.n
+    x = np.arange(1, n + 1) / (n + 1)
+    u = np.zeros(P.nx)
+    for a, b in modes:
+        u += np.kron(np.sin(b * np.pi * x), np.sin(a * np.pi * x))
+    Wf = u[:, None]
+    Vf = np.zeros((P.nt, 1))
+    Vf[0, 0] = 1.0
+    V0, _ = np.linalg.qr(synth.normal_block(P.nt, len(modes), 53))
+    W, V, res = als.als_solve(A, Wf, Vf, V0, 6)
+    Y = P.trajectory(u)
+    assert res[-1] < 1e-12, res
+    assert np.max(np.abs(W @ V.T - Y)) <= 1e-11 * np.abs(Y).max()
+
+
+def test_als_galerkin_conditions():
+    """The two half steps are Galerkin projections: after the time step the
+    residual R = A Y - Y S^T - F is orthogonal to the space basis (Q^T R = 0);
+    after the space step it is orthogonal to the time basis (R V = 0). A
+    transposed T or a shift in the wrong direction breaks one of them. The
+    block forward substitution equals the dense block-bidiagonal solve."""
+    P, A = _als_setup(n=7, nt=16)
+    r = synth.rng(54)
+    Wf = r.standard_normal((P.nx, 2))
+    Vf = r.standard_normal((P.nt, 2))
+    V, _ = np.linalg.qr(r.standard_normal((P.nt, 3)))
+    F = Wf @ Vf.T
+
+    def R_of(Y):
+        YS = np.zeros_like(Y)
+        YS[:, 1:] = Y[:, :-1]
+        return A @ Y - YS - F
+
+    T = als.shift_gram(V)
+    W = sla_solve_sylvester(A, -T, Wf @ (Vf.T @ V))
+    assert np.max(np.abs(R_of(W @ V.T) @ V)) <= 1e-12 * np.abs(F).max()
+    Q, _ = np.linalg.qr(W)
+    G = (Q.T @ Wf) @ Vf.T
+    Z = als.time_step(Q.T @ A @ Q, G)
+    assert np.max(np.abs(Q.T @ R_of(Q @ Z.T))) <= 1e-12 * np.abs(F).max()
+    k = Q.shape[1]
+    Ah = Q.T @ A @ Q
+    big = np.kron(np.eye(P.nt), Ah) - np.kron(np.eye(P.nt, k=-1), np.eye(k))
+    z = np.linalg.solve(big, G.T.reshape(-1))
+    np.testing.assert_allclose(Z.reshape(-1), z, rtol=1e-12, atol=1e-14)
+
+
+def sla_solve_sylvester(A, B, C):
+    import scipy.linalg
+    return scipy.linalg.solve_sylvester(A, B, C)
