@@ -442,6 +442,85 @@ def spacetime_leg(lrp, spec, precision, eps, max_steps=300):
             "s": dt, "ms_apply": st["ms_apply"], "status": st["status"], "nx_nt": G.nx * spec.nt}
 
 
+def als_bench(lrp, spec, precision, ranks=(12, 16, 20), sweeps=3, ncols=4, prec=((0.0, 2), (0.0, 1), (1e-4, 0))):
+    """The Hessian product with both space-time systems solved by the
+    alternating low-rank solver (Sec. 6.1, Eq. (amen_1)-(pre_1);
+    LRP_ALS_SOLVES) beside the time-stepping product on the same columns:
+    wall time per column (one column at a time, the ALS form's unit; and the
+    time-stepping block of ncols columns in one launch), the relative
+    difference to the time-stepping result, and the solver's own counts for
+    one forward solve of the initial condition (GMRES iterations, time in
+    the space and the time steps). prec: (als_prec_rtol, als_prec_its)
+    pairs of the preconditioner (the first for every rank, the others at the
+    second rank)."""
+    import torch
+    G = lrp.lrp_setup_problem(spec, precision=precision)
+    X = synth.normal_block(G.nx, ncols, 1000 + 17)
+    Xd = torch.from_numpy(X).cuda()
+    ref, _ = lrp.lrp_hessian_apply(G, Xd)          # warm-up and reference
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ref, st_ts = lrp.lrp_hessian_apply(G, Xd)
+    torch.cuda.synchronize()
+    ms_block = (time.perf_counter() - t0) * 1e3
+    t0 = time.perf_counter()
+    one, _ = lrp.lrp_hessian_apply(G, Xd[:, :1])
+    torch.cuda.synchronize()
+    ms_one = (time.perf_counter() - t0) * 1e3
+    refn = ref.cpu().numpy()
+    out = {"workload": f"{spec.dim}D n={spec.n} nt={spec.nt}", "precision": int(precision),
+           "time_stepping": {"ms_per_column_alone": ms_one, "ms_block": ms_block, "block": ncols,
+                             "solves_per_column": st_ts["n_solves"]},
+           "als": []}
+    for r, (prt, pits) in [(r, prec[0]) for r in ranks] + [(ranks[1], p) for p in prec[1:]]:
+        G.close()
+        G = lrp.lrp_setup_problem(spec, precision=precision, als_rank=r, als_sweeps=sweeps, als_prec_rtol=prt,
+                                  als_prec_its=pits)
+        lrp.lrp_hessian_apply(G, Xd[:, :1], flags=lrp.LRP_ALS_SOLVES)   # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Y, st = lrp.lrp_hessian_apply(G, Xd, flags=lrp.LRP_ALS_SOLVES)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3
+        Yn = Y.cpu().numpy()
+        rel = float(np.max(np.linalg.norm(Yn - refn, axis=0) / np.linalg.norm(refn, axis=0)))
+        e1 = np.zeros((G.nt, 1))
+        e1[0, 0] = 1.0
+        W, V, res, ast = lrp.lrp_als_solve(G, X[:, :1], e1, np.eye(G.nt)[:, :r], sweeps)
+        out["als"].append({"rank": r, "sweeps": sweeps, "prec_rtol": prt, "prec_its": pits, "ms_per_column": ms / ncols,
+                           "status": st["status"],
+                           "max_rel_diff_vs_time_stepping": rel, "residual_forward": st["time_trunc_err"],
+                           "residual_adjoint": st["adj_trunc_err"],
+                           "precond_solves_per_column": st["n_solves"],
+                           "forward_solve": {"gmres_iters": ast["gmres_iters"], "ms": ast["ms"],
+                                             "ms_space": ast["ms_space"], "ms_time": ast["ms_time"],
+                                             "residuals": [float(v) for v in res]}})
+    G.close()
+    return out
+
+
+def als_arnoldi_leg(lrp, spec, precision, eps, lam_lanczos, rank=16, sweeps=3):
+    """Algorithm 1 in the paper's arrangement: Arnoldi outside, the forward
+    and adjoint space-time systems of every product solved by the
+    alternating low-rank solver (LRP_ALS_SOLVES) inside; steps, Ritz values
+    kept and their largest difference from the Lanczos eigenvalues."""
+    import torch
+    G = lrp.lrp_setup_problem(spec, precision=precision, als_rank=rank, als_sweeps=sweeps)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = lrp.lrp_arnoldi(G, min(1000, G.nx), eig_tol=1e-6, eig_threshold=eps, flags=lrp.LRP_ALS_SOLVES)
+    dt = time.perf_counter() - t0
+    G.close()
+    st = res["stats"]
+    th = res["theta"]
+    kept = np.sort(th.real[(th.real >= eps) & (th.imag == 0)])[::-1]
+    n = min(len(kept), len(lam_lanczos))
+    diff = float(np.max(np.abs(kept[:n] - lam_lanczos[:n])) / lam_lanczos[0]) if n else None
+    return {"rank": rank, "sweeps": sweeps, "arnoldi_steps": st["n_steps"], "kept": int(len(kept)), "s": dt,
+            "status": st["status"], "hess_asym": st["hess_asym"], "n_complex": st["n_complex"],
+            "max_rel_diff_vs_lanczos": diff, "ms_apply": st["ms_apply"]}
+
+
 def paper_bench(lrp, precision):
     """The heat experiment of the paper's numerical section on finite
     differences (63^2 nodes, nt = 30, 9 sensor patches, Gamma_prior = 10 I)
@@ -469,6 +548,8 @@ def paper_bench(lrp, precision):
                         "variance_min_mean_max": [float(var.min()), float(var.mean()), float(var.max())],
                         "paper_arnoldi_iterations": PAPER_ARNOLDI_ITERATIONS.get((ratio, eps)),
                         "arnoldi": arnoldi_leg(lrp, G, eps, lam)})
+            if ratio == 1e6:
+                out[-1]["arnoldi_als"] = als_arnoldi_leg(lrp, spec, precision, eps, lam)
             post.close()
         G.close()
     # the space-time parameter on the heat experiment's setting
@@ -623,7 +704,7 @@ def main():
     ap.add_argument("--mg-nu", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0, help="threads per CTA (256 or 512; profiling)")
     ap.add_argument("--mg-levels", type=int, default=0, help="time-step hierarchy depth (profiling)")
-    ap.add_argument("--mode", default="posterior", choices=["posterior", "apply", "serve", "batched", "paper"],
+    ap.add_argument("--mode", default="posterior", choices=["posterior", "apply", "serve", "batched", "paper", "als"],
                     help="posterior: the whole hot path per step; apply: one Hessian apply per step "
                          "(kernel-level measurement and profiling); serve: the serving workload alone")
     ap.add_argument("--instances", type=int, default=64)
@@ -682,6 +763,21 @@ def main():
                               "config": {"workload": "paper heat experiment (Sec. 6.1) on FD: 63^2 nodes, nt=30, "
                                                      "9 sensor patches, Gamma_prior=10 I; convection-diffusion "
                                                      "experiment (Sec. 6.2): 31^2 nodes, nt=90, upwind, FP64"},
+                              "runs": runs}), flush=True)
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    if args.mode == "als":
+        if rank == 0:
+            prec = lrp.LRP_MIXED if args.precision == "mixed" else lrp.LRP_FP64
+            spec = synth.workload(args.workload)
+            if args.nt:
+                spec.nt, spec.T = args.nt, args.nt * spec.T / spec.nt
+            runs = [als_bench(lrp, spec, prec), als_bench(lrp, synth.paper_heat_spec(1e6), prec)]
+            print(json.dumps({"metric": "Hessian apply ms per column: alternating low-rank space-time solves "
+                                        "vs time stepping", "unit": "ms", "n_gpus": 1, "data": "synthetic",
+                              "dtype": args.precision, "higher_is_better": False,
+                              "config": {"workload": f"{args.workload} and the paper heat experiment (63^2, nt=30)"},
                               "runs": runs}), flush=True)
         if dist:
             dist.destroy_process_group()

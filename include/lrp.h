@@ -84,7 +84,7 @@ enum {
   LRP_KEEP_TRAJ_FACTORS = 1u << 1, /* also compress the forward trajectory of
                                       each column to low-rank-in-time factors
                                       Y ~ W V^T (Sec. 3); ranks in the stats */
-  LRP_LOWRANK_SOURCE = 1u << 2     /* the product of Sec. 4 Algorithm 1 "up to the
+  LRP_LOWRANK_SOURCE = 1u << 2,    /* the product of Sec. 4 Algorithm 1 "up to the
                                       truncation tolerance": the state trajectory
                                       and the adjoint trajectory are kept as
                                       W V^T truncated to time_trunc_tol (rank cap
@@ -96,6 +96,23 @@ enum {
                                       lrp_arnoldi. Ranks and truncation errors of
                                       both trajectories in the stats. Not with
                                       LRP_KEEP_TRAJ_FACTORS. */
+  LRP_ALS_SOLVES = 1u << 3         /* the forward and the adjoint space-time systems
+                                      (Sec. 6.1, Eq. (st_pde)) are solved by the
+                                      alternating low-rank solver of lrp_als_solve
+                                      (rank als_rank, als_sweeps sweeps from the
+                                      first als_rank unit time vectors) instead of
+                                      time stepping: the state Y ~ W_Y V_Y^T, the
+                                      adjoint's source B^T B W_Y V_Y^T / sigma^2 at
+                                      the observed steps, the result the adjoint
+                                      solution's first step (then the prior
+                                      factor). Equals Htilde X up to the solver's
+                                      residual. Stats: time_rank_max / adj_rank_max
+                                      = the rank, time_trunc_err / adj_trunc_err =
+                                      the largest final relative residual of the
+                                      forward / adjoint solves, n_solves = the
+                                      preconditioner's spatial solves per column.
+                                      Not with LRP_KEEP_TRAJ_FACTORS or
+                                      LRP_LOWRANK_SOURCE; also a flag of lrp_arnoldi. */
 };
 
 typedef struct lrp_problem lrp_problem;     /* opaque, library-owned */
@@ -155,6 +172,17 @@ typedef struct {
                                coarse levels of a time step the operator is close to the identity
                                (c/h^2 small), so the deep levels cost latency and add little. The
                                prior operator always keeps the whole hierarchy. 0 -> autotuned or 0 */
+  int als_rank;             /* LRP_ALS_SOLVES: rank of the alternating solves (0 -> 16; capped at
+                               min(64, nt, nx)) */
+  int als_sweeps;           /* LRP_ALS_SOLVES: sweeps per solve (0 -> 3) */
+  double als_tol;           /* LRP_ALS_SOLVES: stop a solve once its relative residual is <= als_tol
+                               (0 -> always als_sweeps sweeps) */
+  double als_prec_rtol;     /* alternating solves (lrp_als_solve, LRP_ALS_SOLVES): > 0 -> the spatial
+                               solves that apply the space step's preconditioner run to this relative
+                               residual (never below solve_rtol); 0 -> als_prec_its iterations each */
+  int als_prec_its;         /* alternating solves: multigrid-preconditioned CG iterations per
+                               preconditioner solve, from zero (LRP_MIXED: one FP32 inner solve and one
+                               FP64 residual update), when als_prec_rtol is 0 (0 -> 2) */
 } lrp_problem_desc;
 
 typedef struct {
@@ -417,6 +445,56 @@ lrp_status lrp_st_hessian_apply(lrp_problem* p, int r, const double* W, int ldw,
 lrp_status lrp_st_arnoldi(lrp_problem* p, int max_steps, int k, double eig_tol, double eig_threshold, int r0,
                           const double* W0, const double* V0, double* theta_re, double* theta_im, double* H,
                           int* ranks, lrp_arnoldi_stats* st);
+
+/* ---------------------------------------------------------------------------
+ * Alternating low-rank solver of the space-time system (Sec. 6.1: the
+ * all-at-once system Eq. (st_pde), solved in low-rank form by alternating
+ * Galerkin projections, Eq. (amen_1) and Eq. (amen_2), the first by a Krylov
+ * method with the preconditioner of Eq. (pre_1)). With A = I + tau L the
+ * problem's time-step operator, the forward system (transpose = 0) is
+ *   A y_n = y_{n-1} + f_n, n = 1..nt, y_0 = 0, i.e. A Y - Y S^T = F,
+ * and the adjoint system (transpose = 1) is
+ *   A^T q_n = q_{n+1} + f_n, n = nt..1, q_{nt+1} = 0,
+ * with Y = [y_1 .. y_nt] (nx x nt) and the source F = Wf Vf^T given as
+ * factors Wf (nx x rf, ld ldwf), Vf (nt x rf, ld ldvf; row n-1 = step n).
+ * An initial condition u is the source u e_1^T (rf = 1, Vf = e_1).
+ * The solution is returned as Y ~ W V^T, W: nx x r (ld ldw), V: nt x r
+ * (ld ldv, orthonormal columns, row n-1 = step n). One sweep is
+ *  - the space step: V fixed, the Galerkin projection onto span(V) in time,
+ *    A W - W T = F V with T = V^T S^T V (T[i, j] = sum_n V[n-1, i] V[n, j];
+ *    the adjoint uses the same with time reversed), an nx r system solved by
+ *    flexible GMRES to a relative residual of max(10 solve_rtol, 1e-12),
+ *    right-preconditioned by blockdiag(A - T_jj I), each block applied by
+ *    als_prec_its (0 -> 2) multigrid-preconditioned CG iterations from zero
+ *    (the problem's solver and precision), or a solve to als_prec_rtol if
+ *    that is > 0 (the GMRES is flexible: the preconditioner may change from
+ *    one iteration to the next);
+ *  - the time step: W orthonormalised to Q, the Galerkin projection onto
+ *    span(Q) in space, Q^T A Q z_n - z_{n-1} = Q^T f_n (r x r, direct),
+ *    then V = the orthonormalised Z and W = Q R_Z^T.
+ * V0 (nt x r, ld ldv0): the start (orthonormalised first). The rank is fixed
+ * (AMEn's residual-based enrichment is not done); basis directions that
+ * become numerically dependent are dropped (zero columns). Runs `sweeps`
+ * sweeps, or stops after the first whose relative residual
+ * ||A Y - Y S^T - F||_F / ||F||_F (A^T Q - Q S - F for the adjoint) is
+ * <= tol (tol > 0). res (host, may be NULL): that residual after each sweep
+ * (0 past the last one taken). All arrays host or device.
+ * Errors: LRP_EINVAL for r outside 1..min(64, nt, nx), rf outside 0..64,
+ * sweeps < 1, short leading dimensions; LRP_ENOCONV (outputs written) if a
+ * GMRES space step or a spatial solve missed its tolerance. */
+typedef struct {
+  int sweeps;           /* sweeps taken */
+  int gmres_iters;      /* GMRES iterations over all space steps */
+  int gmres_iters_max;  /* largest count of one space step */
+  int precond_solves;   /* spatial solves of the preconditioner, per column */
+  double residual;      /* relative residual after the last sweep */
+  double ms;            /* wall time */
+  double ms_space;      /* of which space steps */
+  double ms_time;       /* of which time steps and residuals */
+} lrp_als_stats;
+lrp_status lrp_als_solve(lrp_problem* p, int transpose, int rf, const double* Wf, int ldwf, const double* Vf,
+                         int ldvf, int r, const double* V0, int ldv0, int sweeps, double tol, double* W, int ldw,
+                         double* V, int ldv, double* res, lrp_als_stats* st);
 
 /* Eigenvalues of a real upper Hessenberg matrix by the Francis double-shift
  * QR iteration (the eigensolver of lrp_arnoldi; Golub & Van Loan Sec. 7.5),

@@ -22,6 +22,18 @@ Y ~ W V^T (nx x r, nt x r) the alternating solve takes, in turn:
 ``als_solve`` runs a fixed number of such sweeps from a given orthonormal
 start V0 and returns the factors and the relative residual
 ||A Y - Y S^T - F||_F / ||F||_F after each sweep.
+
+``als_adjoint`` solves the adjoint system A^T q_n = q_{n+1} + f_n,
+n = nt..1, q_{nt+1} = 0 (the backward recursion of the Hessian's adjoint
+sweep) as the same system with A^T in reversed time.
+
+``als_hessian_apply`` is the prior-preconditioned Hessian product (Sec. 2
+Eq. (prior_pre), Sec. 6.1 Eq. (misfit)) with both space-time solves done by
+``als_solve`` at rank r from the first r unit time vectors:
+z = Gamma_prior^{1/2} x; the state Y ~ W_Y V_Y^T of A Y - Y S^T = z e_1^T;
+the adjoint's source at the observed steps n, B^T B y_n / sigma^2, i.e. the
+factors (B^T B W_Y / sigma^2, V_Y with the unobserved rows zeroed); the
+adjoint solution's first step q_1; the result Gamma_prior^{1/2} q_1.
 """
 from __future__ import annotations
 
@@ -74,3 +86,37 @@ def als_solve(A, Wf, Vf, V0, sweeps):
         V = Vn
         res.append(residual(A, W, V, Wf, Vf))
     return W, V, res
+
+
+def als_adjoint(A, Wf, Vf, V0, sweeps):
+    """A^T q_n = q_{n+1} + f_n (n = nt..1, q_{nt+1} = 0), F = Wf Vf^T with
+    row n-1 of Vf and V0 = step n. Returns (W, V, residuals), Q ~ W V^T in
+    natural time order."""
+    W, Vr, res = als_solve(A.T.copy(), Wf, Vf[::-1].copy(), V0[::-1].copy(), sweeps)
+    return W, Vr[::-1].copy(), res
+
+
+def als_hessian_apply(P, x, r, sweeps, A=None, misfit_only=False):
+    """Htilde x (H_mis x) with both solves by ``als_solve`` at rank r and
+    ``sweeps`` sweeps from the unit vectors e_1..e_r in each solve's own
+    time direction. P: an oracle Problem; A: its dense time-step matrix
+    (built if None). Returns (result, info) with the final residuals."""
+    A = P.K.toarray() if A is None else A
+    x = np.asarray(x, dtype=np.float64).reshape(-1)
+    nt = P.nt
+    z = x if misfit_only else P.prior_half(x)
+    start = np.eye(nt)[:, :r]
+    e1 = np.zeros((nt, 1))
+    e1[0, 0] = 1.0
+    Wy, Vy, res_f = als_solve(A, z[:, None], e1, start, sweeps)
+    B = P.B.toarray()
+    Wa = B.T @ (B @ Wy) / P.sigma ** 2
+    mask = np.zeros((nt, 1))
+    for n in P.steps:
+        mask[n - 1, 0] = 1.0
+    Va = Vy * mask
+    # the adjoint starts from e_1..e_r of its own (reversed) time
+    Wq, Vq, res_a = als_adjoint(A, Wa, Va, start[::-1].copy(), sweeps)
+    q1 = Wq @ Vq[0, :]
+    out = q1 if misfit_only else P.prior_half(q1)
+    return out, dict(res_f=res_f, res_a=res_a)

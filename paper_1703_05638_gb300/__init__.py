@@ -25,7 +25,7 @@ LRP_OK, LRP_EINVAL, LRP_ENOMEM, LRP_ENOCONV, LRP_ENONFINITE, LRP_ETIMEOUT, LRP_E
 LRP_FP64, LRP_MIXED = 0, 1
 LRP_PRIOR_LAPLACE, LRP_PRIOR_IDENTITY = 0, 1
 LRP_PDE_HEAT, LRP_PDE_CONVDIFF = 0, 1
-LRP_PRIOR_PRECOND, LRP_MISFIT_ONLY, LRP_KEEP_TRAJ_FACTORS, LRP_LOWRANK_SOURCE = 0, 1, 2, 4
+LRP_PRIOR_PRECOND, LRP_MISFIT_ONLY, LRP_KEEP_TRAJ_FACTORS, LRP_LOWRANK_SOURCE, LRP_ALS_SOLVES = 0, 1, 2, 4, 8
 LRP_Q_MEAN, LRP_Q_VARIANCE, LRP_Q_SAMPLES = 1, 2, 4
 STATUS_NAMES = {0: "LRP_OK", 1: "LRP_EINVAL", 2: "LRP_ENOMEM", 3: "LRP_ENOCONV", 4: "LRP_ENONFINITE",
                 5: "LRP_ETIMEOUT", 6: "LRP_EBUDGET", 7: "LRP_ECUDA"}
@@ -43,7 +43,9 @@ class lrp_problem_desc(C.Structure):
                 ("team_ctas", C.c_int), ("team_cols", C.c_int), ("mg_nu", C.c_int),
                 ("inner_rtol", C.c_double), ("coarse_items", C.c_int), ("kernel_variant", C.c_int),
                 ("mg_nu_coarse", C.c_int), ("prior_kind", C.c_int), ("prior_gamma", C.c_double),
-                ("pde", C.c_int), ("conv_nu", C.c_double), ("wind", C.c_double * 3), ("mg_levels", C.c_int)]
+                ("pde", C.c_int), ("conv_nu", C.c_double), ("wind", C.c_double * 3), ("mg_levels", C.c_int),
+                ("als_rank", C.c_int), ("als_sweeps", C.c_int), ("als_tol", C.c_double),
+                ("als_prec_rtol", C.c_double), ("als_prec_its", C.c_int)]
 
 
 class lrp_apply_stats(C.Structure):
@@ -112,6 +114,15 @@ class lrp_arnoldi_stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class lrp_als_stats(C.Structure):
+    _fields_ = [("sweeps", C.c_int), ("gmres_iters", C.c_int), ("gmres_iters_max", C.c_int),
+                ("precond_solves", C.c_int), ("residual", C.c_double), ("ms", C.c_double), ("ms_space", C.c_double),
+                ("ms_time", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class lrp_device_peaks(C.Structure):
     _fields_ = [("smem_gbs", C.c_double), ("fp64_fma_tflops", C.c_double), ("fp32_fma_tflops", C.c_double),
                 ("sm_count", C.c_int), ("clock_mhz", C.c_double)]
@@ -147,6 +158,9 @@ EXPORTS = {
                               C.POINTER(lrp_arnoldi_stats)]),
     "lrp_hessenberg_eig": (C.c_int, [C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p]),
+    "lrp_als_solve": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int,
+                                C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_void_p, C.c_int, C.c_void_p, C.c_int,
+                                C.c_void_p, C.POINTER(lrp_als_stats)]),
     "lrp_st_hessian_apply": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p,
                                        C.c_void_p, _ip, C.POINTER(lrp_apply_stats)]),
     "lrp_st_arnoldi": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, C.c_void_p,
@@ -496,6 +510,27 @@ def lrp_st_hessian_apply(prob: Problem, W, V):
     d = st.as_dict()
     d["status"] = status
     return Wo[:, :r.value].copy(), Vo[:, :r.value].copy(), d
+
+
+def lrp_als_solve(prob: Problem, Wf, Vf, V0, sweeps: int, tol: float = 0.0, transpose: bool = False):
+    """Alternating low-rank solve of the space-time system with the source
+    Wf Vf^T (Wf: nx x rf, Vf: nt x rf) from the start V0 (nt x r). Returns
+    (W, V, residuals, stats) with Y ~ W V^T. NumPy arrays (host)."""
+    Wa = np.asfortranarray(np.asarray(Wf, dtype=np.float64).reshape(prob.nx, -1))
+    Va = np.asfortranarray(np.asarray(Vf, dtype=np.float64).reshape(prob.nt, -1))
+    V0a = np.asfortranarray(np.asarray(V0, dtype=np.float64).reshape(prob.nt, -1))
+    rf, r = Wa.shape[1], V0a.shape[1]
+    W = np.zeros((prob.nx, r), order="F")
+    V = np.zeros((prob.nt, r), order="F")
+    res = np.zeros(int(sweeps))
+    st = lrp_als_stats()
+    status = load().lrp_als_solve(prob.handle, int(bool(transpose)), rf, Wa.ctypes.data, prob.nx, Va.ctypes.data,
+                                  prob.nt, r, V0a.ctypes.data, prob.nt, int(sweeps), float(tol), W.ctypes.data,
+                                  prob.nx, V.ctypes.data, prob.nt, res.ctypes.data, C.byref(st))
+    _check(status, allow=(LRP_OK, LRP_ENOCONV))
+    d = st.as_dict()
+    d["status"] = status
+    return W, V, res[:st.sweeps].copy(), d
 
 
 def lrp_st_arnoldi(prob: Problem, max_steps: int, k: int = 0, eig_tol: float = 1e-6, eig_threshold: float = 0.0,

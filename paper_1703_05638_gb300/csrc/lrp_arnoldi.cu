@@ -506,6 +506,7 @@ struct ArnoldiRun {
 
 lrp_status arnoldi_apply(ArnoldiRun& A, const double* x, double* y, lrp_apply_stats* st) {
   const bool misfit = (A.flags & LRP_MISFIT_ONLY) != 0;
+  if (A.flags & LRP_ALS_SOLVES) return als_hessian_impl(A.P, 1, x, A.nx, y, A.nx, misfit, st);
   if (A.flags & LRP_LOWRANK_SOURCE) return lowrank_hessian_impl(A.P, 1, x, A.nx, y, A.nx, misfit, st);
   unsigned stages = ST_LOAD_X | ST_FORWARD | ST_ADJOINT | ST_STORE_Y;
   if (!misfit) stages |= ST_PRIOR_IN | ST_PRIOR_OUT;

@@ -709,6 +709,26 @@ static lrp_status hessian_lowrank_source(lrp_problem* P, int nvec, const double*
   return s2 != LRP_OK ? s2 : s;
 }
 
+// The product with both space-time solves by the alternating low-rank
+// solver (LRP_ALS_SOLVES), staged like the other calls.
+static lrp_status hessian_als(lrp_problem* P, int nvec, const double* X, int ldx, double* Y, int ldy, bool misfit,
+                              lrp_apply_stats* st) {
+  lrp_status s = check_common(P, nvec, ldx, P->nx, ldy, P->nx, X, Y);
+  if (s != LRP_OK) return s;
+  if (nvec == 0) return LRP_OK;
+  Staged sin, sout;
+  const double* din;
+  int dldin;
+  double* dout;
+  int dldout;
+  if ((s = stage_in(P, X, P->nx, nvec, ldx, &din, &dldin, sin)) != LRP_OK) return s;
+  if ((s = stage_out_alloc(P, Y, P->nx, nvec, ldy, &dout, &dldout, sout)) != LRP_OK) return s;
+  s = als_hessian_impl(P, nvec, din, dldin, dout, dldout, misfit, st);
+  if (s != LRP_OK && s != LRP_ENOCONV) return s;
+  lrp_status s2 = stage_out_copy(P, Y, P->nx, nvec, ldy, dout, dldout);
+  return s2 != LRP_OK ? s2 : s;
+}
+
 }  // namespace lrp
 
 extern "C" {
@@ -913,6 +933,11 @@ lrp_status lrp_hessian_apply(lrp_problem* P, int nvec, const double* X, int ldx,
     set_error("LRP_KEEP_TRAJ_FACTORS and LRP_LOWRANK_SOURCE are exclusive");
     return LRP_EINVAL;
   }
+  if ((flags & LRP_ALS_SOLVES) && (flags & (LRP_KEEP_TRAJ_FACTORS | LRP_LOWRANK_SOURCE))) {
+    set_error("LRP_ALS_SOLVES excludes LRP_KEEP_TRAJ_FACTORS and LRP_LOWRANK_SOURCE");
+    return LRP_EINVAL;
+  }
+  if (flags & LRP_ALS_SOLVES) return hessian_als(P, nvec, X, ldx, Y, ldy, misfit, st);
   if (flags & LRP_LOWRANK_SOURCE) return hessian_lowrank_source(P, nvec, X, ldx, Y, ldy, misfit, st);
   if (flags & LRP_KEEP_TRAJ_FACTORS) return hessian_with_factors(P, nvec, X, ldx, Y, ldy, misfit, st);
   unsigned stages = ST_LOAD_X | ST_FORWARD | ST_ADJOINT | ST_STORE_Y;

@@ -75,7 +75,8 @@ enum : unsigned {
   ST_STORE_D = 1u << 7,     // store the observations (unweighted) to column-major D
   ST_TRAJ = 1u << 8,        // copy every forward state into the trajectory chunk buffer
   ST_TRAJ_ADJ = 1u << 9,    // copy every adjoint state q_n into column n-1 of the trajectory buffer
-  ST_SOURCE = 1u << 10      // forward steps solve (I + tau L) y_n = y_{n-1} + s_scale W V[n-1, :]^T (one column)
+  ST_SOURCE = 1u << 10,     // forward steps solve (I + tau L) y_n = y_{n-1} + s_scale W V[n-1, :]^T (one column)
+  ST_SHIFTED = 1u << 11     // one solve per column with that column's operator team_ops[team] (one column per team)
 };
 
 enum : int { STAT_NOCONV = 1, STAT_NONFINITE = 2 };
@@ -124,6 +125,7 @@ struct SweepParams {
   const double* Din; int lddin;
   double* Dout; int lddout;
   const double* src_W; const double* src_V; int src_r, src_ldw, src_ldv; double src_scale;  // ST_SOURCE factors
+  const Op* team_ops; int shift_transpose;    // ST_SHIFTED: per-column operators (device), solve with the transpose
   double* traj; int traj_ld; int traj_cols;  // trajectory buffer: [team col][step in chunk (forward) or step-1 (adjoint)][nx]
   // workspace
   char* ws;
@@ -191,6 +193,12 @@ struct lrp_problem {
   const double* src_W = nullptr;
   const double* src_V = nullptr;
   int src_r = 0, src_ldv = 0;
+  // per-column operators of an ST_SHIFTED launch (set only for the duration
+  // of an alternating space-time solve): host templates (one per column;
+  // the launcher sets their shared-memory level split) and their device copy
+  std::vector<lrp::Op> shift_ops;
+  lrp::Op* shift_ops_dev = nullptr;
+  int shift_transpose = 0;
   lrp::SolveCfg cfg;
   uint64_t hash;
   // sweep-kernel ledger (lrp_sweep_profile): CUDA-event time and algorithmic
@@ -259,6 +267,11 @@ lrp_status ensure_workspace(lrp_problem* P, size_t bytes);
 // Y = the truncated product of Algorithm 1 (LRP_LOWRANK_SOURCE); X, Y device arrays.
 lrp_status lowrank_hessian_impl(lrp_problem* P, int nvec, const double* X, int ldx, double* Y, int ldy,
                                 bool misfit, lrp_apply_stats* stats);
+// Y = Htilde X (H_mis X if misfit) with the forward and adjoint space-time
+// systems solved by the alternating low-rank solver (LRP_ALS_SOLVES); X, Y
+// device arrays.
+lrp_status als_hessian_impl(lrp_problem* P, int nvec, const double* X, int ldx, double* Y, int ldy, bool misfit,
+                            lrp_apply_stats* stats);
 // Stored one-column trajectory -> W diag(sig), V (streaming truncation).
 lrp_status compress_trajectory(lrp_problem* P, const double* traj, double* Wout, double* Vout, int* r_out,
                                double* err);

@@ -75,7 +75,12 @@ lrp_status sweep_enqueue(lrp_problem* Pr, unsigned stages, int nvec, const doubl
                          const double* Din, int lddin, double* Dout, int lddout, int t_begin, int t_end,
                          double* traj, int traj_cols, Stats* hs_dst, SweepLaunch* info) {
   const bool mixed = Pr->desc.precision == LRP_MIXED;
-  const int BV = Pr->team_cols;
+  // per-column operators: one column per team
+  const int BV = (stages & ST_SHIFTED) ? 1 : Pr->team_cols;
+  if ((stages & ST_SHIFTED) && ((int)Pr->shift_ops.size() < nvec || !Pr->shift_ops_dev)) {
+    set_error("shifted solves without per-column operators");
+    return LRP_EINVAL;
+  }
   int bvs = 0;
   while ((1 << bvs) < BV) ++bvs;
   const int n_teams = (nvec + BV - 1) / BV;
@@ -83,6 +88,7 @@ lrp_status sweep_enqueue(lrp_problem* Pr, unsigned stages, int nvec, const doubl
   const size_t N0 = (size_t)Pr->nx;
   SweepParams prm;
   std::memset(&prm, 0, sizeof(prm));
+  cudaError_t e0 = cudaSuccess;
   size_t off = 0;
   for (int k = 0; k < 3; ++k) {
     prm.off_dbuf[k] = off;
@@ -183,7 +189,7 @@ lrp_status sweep_enqueue(lrp_problem* Pr, unsigned stages, int nvec, const doubl
   // Band kernel (2D, kappa = 1, one column per team, FP32 inner): every CTA
   // keeps its band of the finest level and all coarse levels in shared memory.
   bool fast = false;
-  if (Pr->kernel_variant != 1 && !(stages & ST_SOURCE) && Pr->dim == 2 && mixed && BV == 1 && !Pr->step.has_kappa &&
+  if (Pr->kernel_variant != 1 && !(stages & (ST_SOURCE | ST_SHIFTED)) && Pr->dim == 2 && mixed && BV == 1 && !Pr->step.has_kappa &&
       !Pr->step.conv &&
       Pr->L >= 2 &&
       Pr->n <= 128) {
@@ -248,6 +254,19 @@ lrp_status sweep_enqueue(lrp_problem* Pr, unsigned stages, int nvec, const doubl
   prm.src_ldv = Pr->src_ldv;
   prm.src_scale = Pr->tau;
   prm.traj_cols = traj_cols;
+  if (stages & ST_SHIFTED) {
+    // the per-column operators keep the whole hierarchy (their coefficient
+    // can be much larger than tau) with the prior's shared-memory split
+    for (int j = 0; j < nvec; ++j) {
+      Pr->shift_ops[j].L = Pr->L;
+      Pr->shift_ops[j].Ls = Ls;
+    }
+    e0 = cudaMemcpyAsync(Pr->shift_ops_dev, Pr->shift_ops.data(), sizeof(Op) * nvec, cudaMemcpyHostToDevice,
+                         Pr->stream);
+    if (e0 != cudaSuccess) return cuda_status(e0, "per-column operators");
+    prm.team_ops = Pr->shift_ops_dev;
+    prm.shift_transpose = Pr->shift_transpose;
+  }
   prm.adj_begin = Pr->last_obs;
   prm.obs_every = Pr->desc.obs_every;
   prm.n_obs = Pr->n_obs;

@@ -764,6 +764,15 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
       cur = buf_index(w.dbuf, res);
     }
   }
+  if (P.stages & ST_SHIFTED) {
+    // one solve with this column's own operator (one column per team): the
+    // block-diagonal preconditioner of the alternating space-time solver
+    double* X1 = w.dbuf[(cur + 1) % 3];
+    double* X2 = w.dbuf[(cur + 2) % 3];
+    double* res = solve_any<T, DIM, MIXED>(t, P, P.team_ops[team], w, sm, w.dbuf[cur], nullptr, nullptr, X1, X2,
+                                           ctr, P.shift_transpose != 0);
+    cur = buf_index(w.dbuf, res);
+  }
   if (P.stages & ST_FORWARD) {
     for (int n = P.t_begin + 1; n <= P.t_end; ++n) {
       if (P.stages & ST_SOURCE) {

@@ -68,7 +68,8 @@ def test_sources_have_no_host_fallback():
 
 
 def test_server_struct_layouts_match_c(tmp_path):
-    names = ["lrp_server_config", "lrp_request_stats", "lrp_server_stats", "lrp_tuning"]
+    names = ["lrp_server_config", "lrp_request_stats", "lrp_server_stats", "lrp_tuning", "lrp_als_stats",
+             "lrp_arnoldi_stats", "lrp_problem_desc"]
     src = tmp_path / "sz2.c"
     body = "".join(f'printf("%zu\\n", sizeof({n}));' for n in names)
     src.write_text('#include <stdio.h>\n#include "lrp.h"\nint main(void){' + body + 'return 0;}\n')

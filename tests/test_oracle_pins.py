@@ -856,3 +856,38 @@ def test_als_galerkin_conditions():
 def sla_solve_sylvester(A, B, C):
     import scipy.linalg
     return scipy.linalg.solve_sylvester(A, B, C)
+
+
+def test_als_adjoint_full_rank_is_backward_recursion():
+    """The adjoint system A^T q_n = q_{n+1} + f_n in reversed time: with
+    r = nt one sweep reproduces the backward recursion of the Hessian's
+    adjoint sweep (lowrank.adjoint_trajectory, itself pinned to F^T d)."""
+    P, A = _als_setup(n=7, nt=12)
+    r = synth.rng(55)
+    D = r.standard_normal(P.n_data)
+    Q = lowrank.adjoint_trajectory(P, D)
+    F = np.zeros((P.nx, P.nt))
+    Bt = P.B.T.toarray()
+    for k, n in enumerate(P.steps):
+        F[:, n - 1] = Bt @ D[k * P.n_obs:(k + 1) * P.n_obs]
+    U, s, Vt = np.linalg.svd(F, full_matrices=False)
+    V0, _ = np.linalg.qr(r.standard_normal((P.nt, P.nt)))
+    W, V, res = als.als_adjoint(A, U * s, Vt.T, V0, 1)
+    assert res[0] < 1e-12
+    assert np.max(np.abs(W @ V.T - Q)) <= 1e-12 * np.abs(Q).max()
+
+
+@pytest.mark.parametrize("misfit", [False, True])
+def test_als_hessian_full_rank_is_exact(misfit):
+    """With r = nt both alternating solves are exact after one sweep, so the
+    product is Htilde x (H_mis x) of the time-stepping oracle; with r below
+    nt it differs by about the solves' residuals."""
+    P, A = _als_setup(n=7, nt=12)
+    x = synth.normal_block(P.nx, 1, 56)[:, 0]
+    ref = P.misfit_apply(x) if misfit else P.hessian_apply(x)
+    out, info = als.als_hessian_apply(P, x, P.nt, 1, A=A, misfit_only=misfit)
+    assert info["res_f"][0] < 1e-12 and info["res_a"][0] < 1e-12
+    assert np.max(np.abs(out - ref)) <= 1e-11 * np.abs(ref).max()
+    out4, info4 = als.als_hessian_apply(P, x, 4, 3, A=A, misfit_only=misfit)
+    err = np.linalg.norm(out4 - ref) / np.linalg.norm(ref)
+    assert 0 < err < 1e-2
