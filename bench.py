@@ -472,7 +472,7 @@ def als_bench(lrp, spec, precision, ranks=(12, 16, 20), sweeps=3, ncols=4, prec=
            "time_stepping": {"ms_per_column_alone": ms_one, "ms_block": ms_block, "block": ncols,
                              "solves_per_column": st_ts["n_solves"]},
            "als": []}
-    for r, (prt, pits) in [(r, prec[0]) for r in ranks] + [(ranks[1], p) for p in prec[1:]]:
+    for r, (prt, pits) in [(r, prec[0]) for r in ranks] + [(ranks[min(1, len(ranks) - 1)], p) for p in prec[1:]]:
         G.close()
         G = lrp.lrp_setup_problem(spec, precision=precision, als_rank=r, als_sweeps=sweeps, als_prec_rtol=prt,
                                   als_prec_its=pits)
@@ -707,6 +707,8 @@ def main():
     ap.add_argument("--mode", default="posterior", choices=["posterior", "apply", "serve", "batched", "paper", "als"],
                     help="posterior: the whole hot path per step; apply: one Hessian apply per step "
                          "(kernel-level measurement and profiling); serve: the serving workload alone")
+    ap.add_argument("--als-rank", type=int, default=0,
+                    help="--mode als: only this rank, the default preconditioner and --workload (profiling)")
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=2)
     ap.add_argument("--no-autotune", action="store_true")
@@ -773,7 +775,10 @@ def main():
             spec = synth.workload(args.workload)
             if args.nt:
                 spec.nt, spec.T = args.nt, args.nt * spec.T / spec.nt
-            runs = [als_bench(lrp, spec, prec), als_bench(lrp, synth.paper_heat_spec(1e6), prec)]
+            if args.als_rank:
+                runs = [als_bench(lrp, spec, prec, ranks=(args.als_rank,), prec=((0.0, 2),))]
+            else:
+                runs = [als_bench(lrp, spec, prec), als_bench(lrp, synth.paper_heat_spec(1e6), prec)]
             print(json.dumps({"metric": "Hessian apply ms per column: alternating low-rank space-time solves "
                                         "vs time stepping", "unit": "ms", "n_gpus": 1, "data": "synthetic",
                               "dtype": args.precision, "higher_is_better": False,
