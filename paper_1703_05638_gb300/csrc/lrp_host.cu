@@ -854,9 +854,32 @@ lrp_status lrp_autotune(lrp_problem* P, int nvec, int steps, double* best_ms) {
           }
   std::sort(cands.begin(), cands.end(), by_t1);
   // stage 3: whole Hessian applies for the five best screens (the screen
-  // ranks inner tolerances and smoothing counts only roughly)
+  // ranks inner tolerances and smoothing counts only roughly), and for the
+  // two best also their counterparts with the other inner tolerance: a
+  // tighter inner tolerance screens faster (the screen's first steps start
+  // from rough data) but can apply slower (measured on the 127^2 workload:
+  // 1e-4 applied in 246 ms against 277 ms for 1e-5 with the same shape,
+  // and was never among the five best screens)
   const unsigned hess = ST_LOAD_X | ST_PRIOR_IN | ST_FORWARD | ST_ADJOINT | ST_PRIOR_OUT | ST_STORE_Y;
-  const int n2 = std::min<int>(5, (int)cands.size());
+  {
+    const int top = std::min<int>(5, (int)cands.size());
+    std::vector<Cand> sel(cands.begin(), cands.begin() + top);
+    for (int i = 0; i < std::min(2, top) && mixed; ++i) {
+      for (const Cand& o : cands) {
+        const bool twin = o.C == sel[i].C && o.NT == sel[i].NT && o.BV == sel[i].BV && o.waves == sel[i].waves &&
+                          o.nu == sel[i].nu && o.nuc == sel[i].nuc && o.levels == sel[i].levels &&
+                          o.inner != sel[i].inner;
+        if (!twin) continue;
+        bool have = false;
+        for (const Cand& q : sel)
+          have = have || (q.C == o.C && q.NT == o.NT && q.BV == o.BV && q.waves == o.waves && q.nu == o.nu &&
+                          q.nuc == o.nuc && q.levels == o.levels && q.inner == o.inner);
+        if (!have) sel.push_back(o);
+      }
+    }
+    cands = sel;
+  }
+  const int n2 = (int)cands.size();
   for (int i = 0; i < n2; ++i) {
     if (!(cands[i].t1 < 1e300)) continue;
     apply_cand(cands[i]);
