@@ -30,7 +30,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "lrp_dense.h"
@@ -910,8 +912,148 @@ lrp_status als_run(lrp_problem* P, AlsWS& w, int transpose, const double* Wf, co
 
 }  // namespace
 
+namespace {
+
+// Work arrays of the product for one column at a time.
+struct ColWS {
+  AlsWS fw, aw;
+  Buf<double> z, e1, Wa, Va, D, q1;
+  std::vector<double> start, hist;
+  cudaError_t init(lrp_problem* P, int r, int sweeps) {
+    const int nx = P->nx, nt = P->nt;
+    cudaError_t e = fw.init(P, r, 1);
+    if (e == cudaSuccess) e = aw.init(P, r, r);
+    if (e == cudaSuccess) e = z.alloc(nx);
+    if (e == cudaSuccess) e = e1.alloc(nt);
+    if (e == cudaSuccess) e = Wa.alloc((size_t)nx * r);
+    if (e == cudaSuccess) e = Va.alloc((size_t)nt * r);
+    if (e == cudaSuccess) e = D.alloc((size_t)P->n_obs * r);
+    if (e == cudaSuccess) e = q1.alloc(nx);
+    std::vector<double> unit(nt, 0.0);
+    unit[0] = 1.0;
+    if (e == cudaSuccess) e = cudaMemcpy(e1.p, unit.data(), nt * sizeof(double), cudaMemcpyHostToDevice);
+    // start: the first r time steps (unit vectors), for both solves
+    start.assign((size_t)nt * r, 0.0);
+    for (int j = 0; j < r; ++j) start[(size_t)j * nt + j] = 1.0;
+    hist.assign(sweeps, 0.0);
+    return e;
+  }
+};
+
+struct ColResult {
+  double res_f = 0.0, res_a = 0.0;
+  bool noconv = false;
+  AlsCounters c;
+};
+
+// y = Htilde x (H_mis x) for one column with both space-time systems solved
+// by the alternating solver; x, y device vectors.
+lrp_status als_column(lrp_problem* P, ColWS& w, int r, int sweeps, double tol, bool misfit, const double* x,
+                      double* y, ColResult& cr) {
+  const int nx = P->nx, nt = P->nt;
+  cudaStream_t s = P->stream;
+  const unsigned prior_st = ST_LOAD_X | ST_PRIOR_IN | ST_STORE_Y;
+  lrp_apply_stats pst;
+  if (misfit) {
+    CKL(cudaMemcpyAsync(w.z.p, x, nx * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  } else {
+    lrp_status pr = run_sweep_ex(P, prior_st, 1, x, nx, w.z.p, nx, nullptr, 0, nullptr, 0, &pst, 0, 0, nullptr, 0);
+    if (pr == LRP_ENOCONV)
+      cr.noconv = true;
+    else if (pr != LRP_OK)
+      return pr;
+  }
+  // forward: A Y - Y S^T = z e_1^T
+  CKL(cudaMemcpyAsync(w.fw.V.p, w.start.data(), w.start.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  int done = 0;
+  CKS(als_run(P, w.fw, 0, w.z.p, w.e1.p, sweeps, tol, w.hist.data(), &done, cr.c));
+  cr.res_f = std::max(cr.res_f, done > 0 ? w.hist[done - 1] : 0.0);
+  // adjoint source: f_n = B^T B y_n / sigma^2 at the observed steps, as
+  // factors (B^T B W / sigma^2) (mask V)^T, in reversed time
+  {
+    dim3 go((P->n_obs + 255) / 256, r);
+    note_launch();
+    k_observe_cols<<<go, 256, 0, s>>>(P->n_obs, r, P->obs_node, P->obs_w, w.fw.W.p, nx, w.D.p);
+    CKL(cudaGetLastError());
+    dim3 gb(grid1(nx), r);
+    const double is2 = 1.0 / (P->desc.sigma * P->desc.sigma);
+    note_launch();
+    k_bt_cols<<<gb, 256, 0, s>>>(nx, r, P->bt_ptr, P->bt_idx, P->bt_w, w.D.p, P->n_obs, is2, w.Wa.p);
+    CKL(cudaGetLastError());
+    dim3 gr(grid1(nt), r);
+    note_launch();
+    k_rows_reverse<<<gr, 256, 0, s>>>(nt, r, w.fw.V.p, nt, w.Va.p, P->desc.obs_every, P->n_steps);
+    CKL(cudaGetLastError());
+  }
+  CKL(cudaMemcpyAsync(w.aw.V.p, w.start.data(), w.start.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  CKS(als_run(P, w.aw, 1, w.Wa.p, w.Va.p, sweeps, tol, w.hist.data(), &done, cr.c));
+  cr.res_a = std::max(cr.res_a, done > 0 ? w.hist[done - 1] : 0.0);
+  // q_1 = the last column of the reversed solution
+  note_launch();
+  k_factor_row<<<grid1(nx), 256, 0, s>>>(nx, r, w.aw.W.p, w.aw.V.p, nt, nt - 1, w.q1.p);
+  CKL(cudaGetLastError());
+  if (misfit) {
+    CKL(cudaMemcpyAsync(y, w.q1.p, nx * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  } else {
+    lrp_status pr = run_sweep_ex(P, prior_st, 1, w.q1.p, nx, y, nx, nullptr, 0, nullptr, 0, &pst, 0, 0, nullptr, 0);
+    if (pr == LRP_ENOCONV)
+      cr.noconv = true;
+    else if (pr != LRP_OK)
+      return pr;
+  }
+  CKL(cudaStreamSynchronize(s));
+  return LRP_OK;
+}
+
+// A handle that shares the problem's operators, sensors and settings (all
+// read-only in a solve) but has its own stream, sweep workspace, statistics
+// and per-column operators, so that independent columns can run from
+// separate host threads at the same time.
+struct SideHandle {
+  lrp_problem* h = nullptr;
+  lrp_status make(const lrp_problem* P) {
+    h = new lrp_problem(*P);
+    h->allocs.clear();  // owns none of the problem's arrays
+    h->stream = nullptr;
+    h->ws = nullptr;
+    h->ws_bytes = 0;
+    h->ws_fixed = nullptr;
+    h->ws_fixed_bytes = 0;
+    h->stats = nullptr;
+    h->end_buf = nullptr;
+    h->prof_on = 0;
+    h->prof_ev[0] = h->prof_ev[1] = nullptr;
+    h->shift_ops.clear();
+    h->shift_ops_dev = nullptr;
+    h->src_W = h->src_V = nullptr;
+    CKL(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    CKL(dev_malloc(&h->stats, sizeof(Stats)));
+    CKL(dev_malloc(&h->end_buf, 65536 * sizeof(int)));
+    CKL(cudaMemset(h->end_buf, 0, 65536 * sizeof(int)));
+    return LRP_OK;
+  }
+  ~SideHandle() {
+    if (!h) return;
+    if (h->stream) {
+      cudaStreamSynchronize(h->stream);
+      cudaStreamDestroy(h->stream);
+    }
+    if (h->ws) cudaFree(h->ws);
+    if (h->stats) cudaFree(h->stats);
+    if (h->end_buf) cudaFree(h->end_buf);
+    delete h;
+  }
+};
+
+constexpr int kAlsStreams = 8;  // columns of a product solved at the same time
+
+}  // namespace
+
 // The Hessian product with both space-time solves by the alternating solver
-// (flag LRP_ALS_SOLVES of lrp_hessian_apply; X, Y device arrays).
+// (flag LRP_ALS_SOLVES of lrp_hessian_apply; X, Y device arrays). One
+// column is one chain of small, synchronising steps (GMRES iterations), so
+// up to kAlsStreams columns run at once, each from its own host thread on a
+// side handle with its own stream; the results do not depend on this.
 lrp_status als_hessian_impl(lrp_problem* P, int nvec, const double* X, int ldx, double* Y, int ldy, bool misfit,
                             lrp_apply_stats* stats) {
   auto t0 = std::chrono::steady_clock::now();
@@ -919,82 +1061,62 @@ lrp_status als_hessian_impl(lrp_problem* P, int nvec, const double* X, int ldx, 
   const int r = std::min({P->desc.als_rank > 0 ? P->desc.als_rank : 16, nt, nx, kMaxRank});
   const int sweeps = P->desc.als_sweeps > 0 ? P->desc.als_sweeps : 3;
   const double tol = P->desc.als_tol;
-  cudaStream_t s = P->stream;
-  AlsWS fw, aw;
-  CKL(fw.init(P, r, 1));
-  CKL(aw.init(P, r, r));
-  Buf<double> z, e1, Wa, Va, D, q1;
-  CKL(z.alloc(nx));
-  CKL(e1.alloc(nt));
-  CKL(Wa.alloc((size_t)nx * r));
-  CKL(Va.alloc((size_t)nt * r));
-  CKL(D.alloc((size_t)P->n_obs * r));
-  CKL(q1.alloc(nx));
+  const int nw = std::max(1, std::min(nvec, kAlsStreams));
+  CKL(cudaStreamSynchronize(P->stream));  // X is ready
+  std::vector<std::unique_ptr<SideHandle>> side(nw);
+  std::vector<ColResult> res(nw);
+  std::vector<lrp_status> st(nw, LRP_OK);
+  std::vector<std::string> msg(nw);
+  // the side handles are copies of P made before any worker runs (the
+  // workers change P's per-call state: its settings during a preconditioner
+  // solve and its per-column operators)
+  for (int wi = 1; wi < nw; ++wi) {
+    side[wi].reset(new SideHandle());
+    lrp_status sm = side[wi]->make(P);
+    if (sm != LRP_OK) return sm;
+  }
+  auto worker = [&](int wi) {
+    cudaSetDevice(P->device);
+    lrp_problem* H = wi > 0 ? side[wi]->h : P;
+    ColWS w;
+    cudaError_t e = w.init(H, r, sweeps);
+    if (e != cudaSuccess) {
+      st[wi] = cuda_status(e, "alternating solve work arrays");
+      msg[wi] = lrp_last_error();
+      return;
+    }
+    ShiftOpsGuard guard{H};
+    for (int col = wi; col < nvec; col += nw) {
+      st[wi] = als_column(H, w, r, sweeps, tol, misfit, X + (size_t)col * ldx, Y + (size_t)col * ldy, res[wi]);
+      if (st[wi] != LRP_OK) {
+        msg[wi] = lrp_last_error();
+        return;
+      }
+    }
+  };
+  {
+    std::vector<std::thread> threads;
+    for (int wi = 1; wi < nw; ++wi) threads.emplace_back(worker, wi);
+    worker(0);
+    for (auto& t : threads) t.join();
+  }
+  side.clear();
+  for (int wi = 0; wi < nw; ++wi)
+    if (st[wi] != LRP_OK) {
+      set_error(msg[wi]);
+      return st[wi];
+    }
   AlsCounters c;
-  ShiftOpsGuard guard{P};
   double res_f = 0.0, res_a = 0.0;
   bool noconv = false;
-  std::vector<double> hist(sweeps);
-  std::vector<double> unit(nt, 0.0);
-  unit[0] = 1.0;
-  CKL(cudaMemcpyAsync(e1.p, unit.data(), nt * sizeof(double), cudaMemcpyHostToDevice, s));
-  // start: the first r time steps (unit vectors), for both solves
-  std::vector<double> start((size_t)nt * r, 0.0);
-  for (int j = 0; j < r; ++j) start[(size_t)j * nt + j] = 1.0;
-  const unsigned prior_st = ST_LOAD_X | ST_PRIOR_IN | ST_STORE_Y;
-  for (int col = 0; col < nvec; ++col) {
-    const double* x = X + (size_t)col * ldx;
-    lrp_apply_stats pst;
-    if (misfit) {
-      CKL(cudaMemcpyAsync(z.p, x, nx * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    } else {
-      lrp_status pr = run_sweep_ex(P, prior_st, 1, x, ldx, z.p, nx, nullptr, 0, nullptr, 0, &pst, 0, 0, nullptr, 0);
-      if (pr == LRP_ENOCONV)
-        noconv = true;
-      else if (pr != LRP_OK)
-        return pr;
-    }
-    // forward: A Y - Y S^T = z e_1^T
-    CKL(cudaMemcpyAsync(fw.V.p, start.data(), start.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-    int done = 0;
-    CKS(als_run(P, fw, 0, z.p, e1.p, sweeps, tol, hist.data(), &done, c));
-    res_f = std::max(res_f, done > 0 ? hist[done - 1] : 0.0);
-    // adjoint source: f_n = B^T B y_n / sigma^2 at the observed steps, as
-    // factors (B^T B W / sigma^2) (mask V)^T, in reversed time
-    {
-      dim3 go((P->n_obs + 255) / 256, r);
-      note_launch();
-      k_observe_cols<<<go, 256, 0, s>>>(P->n_obs, r, P->obs_node, P->obs_w, fw.W.p, nx, D.p);
-      CKL(cudaGetLastError());
-      dim3 gb(grid1(nx), r);
-      const double is2 = 1.0 / (P->desc.sigma * P->desc.sigma);
-      note_launch();
-      k_bt_cols<<<gb, 256, 0, s>>>(nx, r, P->bt_ptr, P->bt_idx, P->bt_w, D.p, P->n_obs, is2, Wa.p);
-      CKL(cudaGetLastError());
-      dim3 gr(grid1(nt), r);
-      note_launch();
-      k_rows_reverse<<<gr, 256, 0, s>>>(nt, r, fw.V.p, nt, Va.p, P->desc.obs_every, P->n_steps);
-      CKL(cudaGetLastError());
-    }
-    CKL(cudaMemcpyAsync(aw.V.p, start.data(), start.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-    CKS(als_run(P, aw, 1, Wa.p, Va.p, sweeps, tol, hist.data(), &done, c));
-    res_a = std::max(res_a, done > 0 ? hist[done - 1] : 0.0);
-    // q_1 = the last column of the reversed solution
-    note_launch();
-    k_factor_row<<<grid1(nx), 256, 0, s>>>(nx, r, aw.W.p, aw.V.p, nt, nt - 1, q1.p);
-    CKL(cudaGetLastError());
-    double* y = Y + (size_t)col * ldy;
-    if (misfit) {
-      CKL(cudaMemcpyAsync(y, q1.p, nx * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    } else {
-      lrp_status pr = run_sweep_ex(P, prior_st, 1, q1.p, nx, y, ldy, nullptr, 0, nullptr, 0, &pst, 0, 0, nullptr, 0);
-      if (pr == LRP_ENOCONV)
-        noconv = true;
-      else if (pr != LRP_OK)
-        return pr;
-    }
+  for (const ColResult& cr : res) {
+    res_f = std::max(res_f, cr.res_f);
+    res_a = std::max(res_a, cr.res_a);
+    noconv = noconv || cr.noconv;
+    c.noconv = c.noconv || cr.c.noconv;
+    c.precond_solves += cr.c.precond_solves;
+    c.gmres_worst = std::max(c.gmres_worst, cr.c.gmres_worst);
   }
-  CKL(cudaStreamSynchronize(s));
   if (stats) {
     std::memset(stats, 0, sizeof(*stats));
     stats->n_solves = nvec > 0 ? c.precond_solves / nvec : 0;
