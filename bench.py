@@ -644,6 +644,35 @@ def roofline_object(kdom, workload, ledger, unit, peaks, peak_kind, dev, block):
     return obj
 
 
+def config3_leg(lrp, stream, peaks, peak_kind, dev):
+    """The 3D workload (63^3 with the kappa field, nt = 1000, 400 sensors
+    every 10th step) beside the headline: one 16-column Hessian apply (its
+    Lanczos block) on the mixed path in the launch shape the autotuner picks
+    for it (12-CTA clusters of 256 threads, time-step hierarchy cut at 4
+    levels; fixed here to keep the bench short), timed by the sweep ledger's
+    CUDA events, and its roofline object (generic kernel: HBM bound)."""
+    import torch
+    spec = synth.workload("heat3d_63")
+    G = lrp.lrp_setup_problem(spec, precision=lrp.LRP_MIXED, stream=stream, team_ctas=12, team_cols=1, mg_levels=4)
+    t = lrp.lrp_problem_tuning(G)
+    t["threads"] = 256
+    lrp.lrp_set_tuning(G, t)
+    X = torch.from_numpy(synth.normal_block(G.nx, 16, spec.seed + 31)).cuda()
+    lrp.lrp_sweep_profile(G, 1)
+    Y, st = lrp.lrp_hessian_apply(G, X)
+    torch.cuda.synchronize()
+    ledger = {kv: lrp.lrp_sweep_profile(G, -1, kv) for kv in (1, 2, 3, 4)}
+    lrp.lrp_sweep_profile(G, 0)
+    ms, n, algo = ledger[3]
+    roof = roofline_object(1, "heat3d_63", ledger, (ms, n, algo), peaks, peak_kind, dev, 16)
+    out = {"workload": "heat3d_63: 3D 63^3 (250047 dofs), kappa field, nt=1000, 400 sensors every 10th step, "
+                        "sigma=1e-3; one 16-column Hessian apply (mixed)",
+            "matvec_per_s": 16 / (ms / 1e3) if ms > 0 else None, "ms_apply": ms, "status": st["status"],
+            "pcg_iters_mean": st["pcg_iters_mean"], "launch": lrp.lrp_problem_tuning(G), "roofline": roof}
+    G.close()
+    return out
+
+
 def config_dict(args, nt: int, ws: int = 1) -> dict:
     """The workload configuration both arms print (identical dicts)."""
     return {"workload": workload_name(args.workload, nt),
@@ -720,6 +749,7 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-batch", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-config3", action="store_true", help="skip the 3D workload's block apply beside the headline")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     k0, b0 = WORKLOAD_DEFAULTS[args.workload]
@@ -963,6 +993,9 @@ def main():
     roofline = roofline_object(kdom, args.workload, ledger, (sweep_ms, sweep_launches, sweep_bytes), peaks,
                                peak_kind, dev, args.block)
     lan = stats[-1]
+    cfg3 = None
+    if not args.no_config3 and args.mode == "posterior" and args.workload == "heat2d_127":
+        cfg3 = config3_leg(lrp, stream, peaks, peak_kind, dev)
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         cpu = cpu_baseline(args.workload, args.nt, lan["n_matvec"] if args.mode == "posterior" else 0)
@@ -982,6 +1015,7 @@ def main():
                     "max_ritz_resid": lan["max_ritz_resid"], "ms_apply": lan["ms_apply"]},
         "trajectory": traj,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "fp64_gpu": fp64, "serve": serve,
+        "heat3d_63": cfg3,
         "gpu_launches": int(launches),
         "clocks": clocks,
     }

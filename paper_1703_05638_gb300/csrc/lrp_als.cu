@@ -441,6 +441,75 @@ __global__ void k_tn_small_sum(int nblk, int m, int nb, const double* part, doub
   *c = alpha * t + (beta == 0.0 ? 0.0 : beta * *c);
 }
 
+// Cholesky factor and its inverse for Cholesky QR (one CTA, r <= 64): with
+// M = G + shift_rel trace(G) I, M = R^T R (R upper triangular, column
+// oriented right-looking elimination), then Rinv = R^{-1} by backward
+// elimination on [R | I]. A pivot d <= floor_rel trace(G) (a column of the factored
+// matrix that is zero, or dependent to rounding) marks a vanished direction:
+// its row of R and column of Rinv are zero, so A Rinv has a zero column there.
+// Rinv: r x r column-major.
+__global__ void __launch_bounds__(256) k_chol_inv_rel(int r, const double* G, double shift_rel, double floor_rel,
+                                                      double* Rinv) {
+  extern __shared__ double sh_chol[];
+  double* M = sh_chol;          // M[i + r j]: R (upper triangle)
+  double* X = sh_chol + r * r;  // the right half of [R | I]: Rinv
+  __shared__ double s_tr;
+  __shared__ int s_dead;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  for (int e = tid; e < r * r; e += nthr) {
+    const int i = e % r, j = e / r;
+    M[i + r * j] = G[e];
+    X[i + r * j] = i == j ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double tr = 0.0;
+    for (int i = 0; i < r; ++i) tr += M[i + r * i];
+    s_tr = tr;
+  }
+  __syncthreads();
+  const double floor_abs = floor_rel * s_tr;
+  for (int i = tid; i < r; i += nthr) M[i + r * i] += shift_rel * s_tr;
+  __syncthreads();
+  for (int k = 0; k < r; ++k) {
+    if (tid == 0) {
+      const double d = M[k + r * k];
+      const bool dead = !(d > floor_abs);
+      s_dead = dead;
+      M[k + r * k] = dead ? 0.0 : sqrt(d);
+    }
+    __syncthreads();
+    const double rkk = M[k + r * k];
+    const bool dead = s_dead != 0;
+    for (int j = k + 1 + tid; j < r; j += nthr) M[k + r * j] = dead ? 0.0 : M[k + r * j] / rkk;
+    __syncthreads();
+    // trailing update of the upper triangle: M[i][j] -= R[k][i] R[k][j], k < i <= j
+    const int m = r - k - 1;
+    for (int e = tid; e < m * m; e += nthr) {
+      const int i = k + 1 + e % m, j = k + 1 + e / m;
+      if (i <= j) M[i + r * j] -= M[k + r * i] * M[k + r * j];
+    }
+    __syncthreads();
+  }
+  // R^{-1}: rows k = r-1 .. 0 of [R | I]: scale row k by 1 / R_kk, then
+  // eliminate column k from the rows above (their right halves)
+  for (int k = r - 1; k >= 0; --k) {
+    const double rkk = M[k + r * k];
+    const double inv = rkk > 0.0 ? 1.0 / rkk : 0.0;
+    for (int j = tid; j < r; j += nthr) X[k + r * j] *= inv;
+    __syncthreads();
+    for (int e = tid; e < k * r; e += nthr) {
+      const int i = e % k, j = e / k;
+      X[i + r * j] -= M[i + r * k] * X[k + r * j];
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < r * r; e += nthr) {
+    const int i = e % r, j = e / r;
+    Rinv[e] = j >= i ? X[i + r * j] : 0.0;
+  }
+}
+
 // out = sum_ij Ga[i, j] Gb[i, j]; one CTA.
 __global__ void k_frob(int n, const double* Ga, const double* Gb, double* out) {
   __shared__ double red[32];
@@ -493,6 +562,7 @@ struct AlsWS {
   Buf<double> V, W, Q, G, Tm, inv_s, Ahat, Gt, Z, Rz, M1, AQ, part, gs, scal;
   Buf<double> Vb, Zb, H, cs, sn, g, y, hv;  // GMRES
   Buf<double> Xc, Yc, Gx, Gy;                 // residual
+  Buf<double> Gq, Rq;                         // Cholesky QR: Gram matrix and inverse factor
   Buf<double> tn;                             // partials of the thin products
   size_t tn_cap = 0;
   Buf<double> dinv;                           // per-column shifted inverse diagonals (kappa), FP64 then FP32
@@ -538,6 +608,8 @@ struct AlsWS {
     if (e == cudaSuccess) e = Gy.alloc((size_t)rc * rc);
     if (e == cudaSuccess) e = stat.alloc(1);
     if (e == cudaSuccess) e = ops.alloc(r);
+    if (e == cudaSuccess) e = Gq.alloc((size_t)r * r);
+    if (e == cudaSuccess) e = Rq.alloc((size_t)r * r);
     tn_cap = (size_t)512 * kTnMaxEntries;
     if (e == cudaSuccess) e = tn.alloc(tn_cap);
     lev_nodes = 0;
@@ -692,6 +764,42 @@ cudaError_t small_tn(cudaStream_t s, AlsWS& w, int nx, int m, int nb, const doub
   return cudaGetLastError();
 }
 
+// A (rows x r, ld rows; r <= 64) <- an orthonormal basis of its columns by
+// shifted Cholesky QR followed by two Cholesky QR passes (Fukaya, Kannan,
+// Nakatsukasa, Yamamoto, Yanagisawa, "Shifted Cholesky QR for computing the
+// QR factorization of ill-conditioned matrices", SIAM J. Sci. Comput. 2020):
+// the shift 11 (rows r + r (r + 1)) u ||A||_F^2 makes the first factorisation
+// succeed for condition numbers up to about 1/u, after which the basis is
+// well conditioned and CholeskyQR2 restores orthogonality to rounding. Each
+// pass is a thin Gram product, one small CTA and one tall product (no
+// cooperative launch). tmp: rows x r scratch. Columns that vanish (zero,
+// or dependent to rounding) come out as zero columns.
+cudaError_t orth_cholqr(cudaStream_t s, AlsWS& w, int rows, int r, double* A, double* tmp) {
+  const double u = 1.1102230246251565e-16;  // unit roundoff 2^-53
+  double* src = A;
+  double* dst = tmp;
+  for (int pass = 0; pass < 3; ++pass) {
+    cudaError_t e = small_tn(s, w, rows, r, r, src, rows, src, rows, w.Gq.p, r, 1.0, 0.0);
+    if (e != cudaSuccess) return e;
+    // shift relative to ||A||_F^2 = trace(G): applied inside k_chol_inv
+    const double shift_rel = pass == 0 ? 11.0 * ((double)rows * r + (double)r * (r + 1)) * u : 0.0;
+    const size_t smem = 2 * (size_t)r * r * sizeof(double);
+    if (smem > 48 * 1024) {
+      e = cudaFuncSetAttribute(k_chol_inv_rel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    note_launch();
+    k_chol_inv_rel<<<1, 256, smem, s>>>(r, w.Gq.p, shift_rel, 64.0 * u, w.Rq.p);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = gemm_nn(s, rows, r, r, 1.0, src, rows, w.Rq.p, r, 0.0, dst, rows);
+    if (e != cudaSuccess) return e;
+    std::swap(src, dst);
+  }
+  // three passes: the result is in tmp
+  return cudaMemcpyAsync(A, src, (size_t)rows * r * sizeof(double), cudaMemcpyDeviceToDevice, s);
+}
+
 // <a, b> over n entries into dst (device)
 cudaError_t dot_into(cudaStream_t s, AlsWS& w, size_t n, const double* a, const double* b, double* dst, double beta) {
   return mdot(s, w, n, 1, a, b, dst, beta);
@@ -817,7 +925,7 @@ lrp_status als_run(lrp_problem* P, AlsWS& w, int transpose, const double* Wf, co
     CKL(cudaStreamSynchronize(s));
   }
   // orthonormal start
-  CKL(block_gs(s, 1, nt, r, w.V.p, 0, nt, w.Rz.p, 0, 1e-14, nullptr, nullptr, w.gs.p));
+  CKL(orth_cholqr(s, w, nt, r, w.V.p, w.Gt.p));
   *done_sweeps = 0;
   if (!(f2 > 0.0)) {
     CKL(cudaMemsetAsync(w.W.p, 0, (size_t)nx * r * sizeof(double), s));
@@ -847,7 +955,7 @@ lrp_status als_run(lrp_problem* P, AlsWS& w, int transpose, const double* Wf, co
     c.ms_space += std::chrono::duration<double, std::milli>(t1 - t0).count();
     // ---- time step
     CKL(cudaMemcpyAsync(w.Q.p, w.W.p, (size_t)nx * r * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    CKL(block_gs(s, 1, nx, r, w.Q.p, 0, nx, w.Rz.p, 0, 1e-14, nullptr, nullptr, w.gs.p));
+    CKL(orth_cholqr(s, w, nx, r, w.Q.p, w.AQ.p));
     CKS(kron_apply(P, r, w.Q.p, nullptr, transpose, w.AQ.p));
     CKL(small_tn(s, w, nx, r, r, w.Q.p, nx, w.AQ.p, nx, w.Ahat.p, r, 1.0, 0.0));
     // Gt (nt x r) = Vf (Wf^T Q)
@@ -860,7 +968,7 @@ lrp_status als_run(lrp_problem* P, AlsWS& w, int transpose, const double* Wf, co
     CKL(cudaGetLastError());
     // V, R_Z = qr(Z); W = Q R_Z^T = Q (Z^T V)
     CKL(cudaMemcpyAsync(w.V.p, w.Z.p, (size_t)nt * r * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    CKL(block_gs(s, 1, nt, r, w.V.p, 0, nt, w.Rz.p, 0, 1e-14, nullptr, nullptr, w.gs.p));
+    CKL(orth_cholqr(s, w, nt, r, w.V.p, w.Gt.p));
     CKL(small_tn(s, w, nt, r, r, w.Z.p, nt, w.V.p, nt, w.M1.p, r, 1.0, 0.0));
     CKL(gemm_nn(s, nx, r, r, 1.0, w.Q.p, nx, w.M1.p, r, 0.0, w.W.p, nx));
     // ---- residual. After the time step Q^T R = 0, so with X1 = (I - Q Q^T) A W,
