@@ -653,23 +653,37 @@ def config3_leg(lrp, stream, peaks, peak_kind, dev):
     CUDA events, and its roofline object (generic kernel: HBM bound)."""
     import torch
     spec = synth.workload("heat3d_63")
-    G = lrp.lrp_setup_problem(spec, precision=lrp.LRP_MIXED, stream=stream, team_ctas=12, team_cols=1, mg_levels=4)
-    t = lrp.lrp_problem_tuning(G)
-    t["threads"] = 256
-    lrp.lrp_set_tuning(G, t)
-    X = torch.from_numpy(synth.normal_block(G.nx, 16, spec.seed + 31)).cuda()
-    lrp.lrp_sweep_profile(G, 1)
-    Y, st = lrp.lrp_hessian_apply(G, X)
-    torch.cuda.synchronize()
-    ledger = {kv: lrp.lrp_sweep_profile(G, -1, kv) for kv in (1, 2, 3, 4)}
-    lrp.lrp_sweep_profile(G, 0)
-    ms, n, algo = ledger[3]
-    roof = roofline_object(1, "heat3d_63", ledger, (ms, n, algo), peaks, peak_kind, dev, 16)
+    X = torch.from_numpy(synth.normal_block(spec.nx, 16, spec.seed + 31)).cuda()
+    res = {}
+    for bf in (0, 1):
+        G = lrp.lrp_setup_problem(spec, precision=lrp.LRP_MIXED, stream=stream, team_ctas=12, team_cols=1,
+                                  mg_levels=4, mg_bf16=bf)
+        t = lrp.lrp_problem_tuning(G)
+        t["threads"] = 256
+        lrp.lrp_set_tuning(G, t)
+        lrp.lrp_sweep_profile(G, 1)
+        Y, st = lrp.lrp_hessian_apply(G, X)
+        torch.cuda.synchronize()
+        ledger = {kv: lrp.lrp_sweep_profile(G, -1, kv) for kv in (1, 2, 3, 4)}
+        lrp.lrp_sweep_profile(G, 0)
+        ms, n, algo = ledger[3]
+        res[bf] = (Y.cpu().numpy(), st, ms, ledger, lrp.lrp_problem_tuning(G))
+        G.close()
+    Y0, st, ms, ledger, tune = res[0]
+    roof = roofline_object(1, "heat3d_63", ledger, ledger[3], peaks, peak_kind, dev, 16)
     out = {"workload": "heat3d_63: 3D 63^3 (250047 dofs), kappa field, nt=1000, 400 sensors every 10th step, "
                         "sigma=1e-3; one 16-column Hessian apply (mixed)",
-            "matvec_per_s": 16 / (ms / 1e3) if ms > 0 else None, "ms_apply": ms, "status": st["status"],
-            "pcg_iters_mean": st["pcg_iters_mean"], "launch": lrp.lrp_problem_tuning(G), "roofline": roof}
-    G.close()
+           "matvec_per_s": 16 / (ms / 1e3) if ms > 0 else None, "ms_apply": ms, "status": st["status"],
+           "pcg_iters_mean": st["pcg_iters_mean"], "launch": tune, "roofline": roof}
+    Y1, st1, ms1, ledger1, _ = res[1]
+    ms_b, n_b, algo_b = ledger1[3]
+    out["bf16_smoothing"] = {
+        "what": "the same apply with the multigrid vectors of the global-memory levels stored in BF16 (mg_bf16)",
+        "matvec_per_s": 16 / (ms1 / 1e3) if ms1 > 0 else None, "ms_apply": ms1, "status": st1["status"],
+        "converged": st1["status"] == 0, "pcg_iters_mean": st1["pcg_iters_mean"],
+        "max_rel_residual": st1["max_rel_residual"],
+        "max_rel_diff_vs_fp32_smoothing": float(np.max(np.abs(Y1 - Y0)) / np.max(np.abs(Y0))),
+        "algo_gbs": (algo_b / n_b) / (ms_b / n_b / 1e3) / 1e9 if ms_b > 0 else None}
     return out
 
 

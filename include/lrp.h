@@ -183,6 +183,14 @@ typedef struct {
   int als_prec_its;         /* alternating solves: multigrid-preconditioned CG iterations per
                                preconditioner solve, from zero (LRP_MIXED: one FP32 inner solve and one
                                FP64 residual update), when als_prec_rtol is 0 (0 -> 2) */
+  int mg_bf16;              /* LRP_MIXED: 1 -> the multigrid smoother iterates and coarse right-hand sides
+                               of the levels held in global memory are stored in BF16 (rounded to
+                               nearest even; the arithmetic stays FP32, the PCG vectors FP32, the
+                               refinement FP64). Runs the generic sweep kernel (the 2D band kernel keeps
+                               its vectors in shared memory in FP32 and has no BF16 form). The V-cycle
+                               is then not exactly the same operator in every application; the FP64
+                               refinement keeps the result at the solve tolerance, and a solve that
+                               does not converge returns LRP_ENOCONV. 0 -> FP32 storage */
 } lrp_problem_desc;
 
 typedef struct {

@@ -45,7 +45,7 @@ class lrp_problem_desc(C.Structure):
                 ("mg_nu_coarse", C.c_int), ("prior_kind", C.c_int), ("prior_gamma", C.c_double),
                 ("pde", C.c_int), ("conv_nu", C.c_double), ("wind", C.c_double * 3), ("mg_levels", C.c_int),
                 ("als_rank", C.c_int), ("als_sweeps", C.c_int), ("als_tol", C.c_double),
-                ("als_prec_rtol", C.c_double), ("als_prec_its", C.c_int)]
+                ("als_prec_rtol", C.c_double), ("als_prec_its", C.c_int), ("mg_bf16", C.c_int)]
 
 
 class lrp_apply_stats(C.Structure):

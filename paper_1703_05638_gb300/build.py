@@ -19,7 +19,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblrp.so")
 
-SOURCES = ["lrp_sweep_d2.cu", "lrp_sweep_d3.cu", "lrp_sweep_f2.cu", "lrp_sweep_f3.cu", "lrp_sweep.cu",
+SOURCES = ["lrp_sweep_d2.cu", "lrp_sweep_d3.cu", "lrp_sweep_f2.cu", "lrp_sweep_f3.cu", "lrp_sweep_b2.cu",
+           "lrp_sweep_b3.cu", "lrp_sweep.cu",
            "lrp_host.cu", "lrp_dense.cu", "lrp_posterior.cu", "lrp_traj.cu", "lrp_noalloc.cu",
            "lrp_sweep_fast.cu", "lrp_serve.cu", "lrp_peaks.cu", "lrp_arnoldi.cu", "lrp_als.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

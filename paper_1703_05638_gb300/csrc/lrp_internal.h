@@ -245,7 +245,7 @@ lrp_status check_on_device(int device, const void* p, const char* what);
 
 // sweep launcher (lrp_sweep.cu)
 struct SweepLaunch {
-  bool fast = false, mixed = false;
+  bool fast = false, mixed = false, bf16 = false;
   int BV = 1, n_teams = 0;
   unsigned stages = 0;
 };

@@ -1,5 +1,6 @@
 // Host launcher of the persistent sweep kernel (lrp_sweep_kernel.cuh): team
 // workspace layout, levels worked by the whole team, cluster launch, stats.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -14,23 +15,30 @@ namespace lrp {
 
 constexpr int FAST_HALO_ROWS = 2;  // halo rows of the band kernel
 
-template <typename T, int DIM, bool MIXED>
+template <typename T, int DIM, bool MIXED, typename ES = T>
 cudaError_t launch_sweep(const SweepParams& prm, cudaStream_t stream);
 extern template cudaError_t launch_sweep<double, 2, false>(const SweepParams&, cudaStream_t);
 extern template cudaError_t launch_sweep<double, 3, false>(const SweepParams&, cudaStream_t);
 extern template cudaError_t launch_sweep<float, 2, true>(const SweepParams&, cudaStream_t);
 extern template cudaError_t launch_sweep<float, 3, true>(const SweepParams&, cudaStream_t);
-template <typename T, int DIM, bool MIXED>
+extern template cudaError_t launch_sweep<float, 2, true, __nv_bfloat16>(const SweepParams&, cudaStream_t);
+extern template cudaError_t launch_sweep<float, 3, true, __nv_bfloat16>(const SweepParams&, cudaStream_t);
+template <typename T, int DIM, bool MIXED, typename ES = T>
 int max_resident_teams(int C, int NT, size_t smem, int sm_count);
 extern template int max_resident_teams<double, 2, false>(int, int, size_t, int);
 extern template int max_resident_teams<double, 3, false>(int, int, size_t, int);
 extern template int max_resident_teams<float, 2, true>(int, int, size_t, int);
 extern template int max_resident_teams<float, 3, true>(int, int, size_t, int);
+extern template int max_resident_teams<float, 2, true, __nv_bfloat16>(int, int, size_t, int);
+extern template int max_resident_teams<float, 3, true, __nv_bfloat16>(int, int, size_t, int);
 
 cudaError_t launch_fast2d(const SweepParams& prm, cudaStream_t stream);
 int fast2d_resident_teams(int C, int NT, size_t smem, int sm_count);
 
-static int resident_teams(bool mixed, int dim, int C, int NT, size_t smem, int sm_count) {
+static int resident_teams(bool mixed, bool bf16, int dim, int C, int NT, size_t smem, int sm_count) {
+  if (mixed && bf16)
+    return dim == 2 ? max_resident_teams<float, 2, true, __nv_bfloat16>(C, NT, smem, sm_count)
+                    : max_resident_teams<float, 3, true, __nv_bfloat16>(C, NT, smem, sm_count);
   if (dim == 2)
     return mixed ? max_resident_teams<float, 2, true>(C, NT, smem, sm_count)
                  : max_resident_teams<double, 2, false>(C, NT, smem, sm_count);
@@ -48,12 +56,16 @@ static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 //     2.5 restriction + 2.25 prolongation + 3 nu post-sweeps + 1 (r.z),
 //     in words of the inner type;
 //   solve set-up: 3 FP64 + 2 inner words; FP64 refinement: 3 FP64 + 3 inner.
-double algorithmic_bytes(const lrp_problem* Pr, const Stats& hs, int BV, bool mixed) {
+double algorithmic_bytes(const lrp_problem* Pr, const Stats& hs, int BV, bool mixed, bool bf16) {
   const double T = mixed ? 4.0 : 8.0, D = 8.0;
+  const double E = bf16 ? 2.0 : T;  // multigrid vectors of the global-memory levels
   const double nu = Pr->cfg.nu;
   const double g = Pr->dim == 2 ? 4.0 / 3.0 : 8.0 / 7.0;
-  const double c_it = 12.0 + (3.0 * (nu - 1.0) + 2.5 + 2.25 + 3.0 * nu + 1.0) * g;
-  const double per_point = (double)hs.iters * c_it * T + (double)hs.refines * (3.0 * D + 3.0 * T) +
+  // phases A and B: 10 words of PCG vectors, 2 of multigrid vectors (z read,
+  // the first smoother iterate written); the V-cycle: multigrid vectors
+  // (r, read once, counted in T)
+  const double c_it_bytes = 10.0 * T + 2.0 * E + (3.0 * (nu - 1.0) + 2.5 + 2.25 + 3.0 * nu) * g * E + g * T;
+  const double per_point = (double)hs.iters * c_it_bytes + (double)hs.refines * (3.0 * D + 3.0 * T) +
                            (double)hs.solves * (3.0 * D + 2.0 * T);
   return per_point * (double)Pr->nx * BV;
 }
@@ -85,6 +97,10 @@ lrp_status sweep_enqueue(lrp_problem* Pr, unsigned stages, int nvec, const doubl
   while ((1 << bvs) < BV) ++bvs;
   const int n_teams = (nvec + BV - 1) / BV;
   const size_t tsz = mixed ? sizeof(float) : sizeof(double);
+  // BF16 storage of the multigrid vectors: the generic kernel only (the band
+  // kernel keeps its vectors in shared memory in FP32); decided with the
+  // kernel below, the workspace is laid out for the larger element size
+  const bool bf16_req = mixed && Pr->desc.mg_bf16 != 0;
   const size_t N0 = (size_t)Pr->nx;
   SweepParams prm;
   std::memset(&prm, 0, sizeof(prm));
@@ -107,18 +123,19 @@ lrp_status sweep_enqueue(lrp_problem* Pr, unsigned stages, int nvec, const doubl
   prm.off_c = off;
   // mixed: the inner correction; convection-diffusion: BiCGStab's shadow residual
   off = align_up(off + ((mixed || Pr->step.conv) ? N0 * BV * tsz : 0));
+  const size_t esz = bf16_req ? sizeof(__nv_bfloat16) : tsz;
   prm.off_e0[0] = off;
-  off = align_up(off + N0 * BV * tsz);
+  off = align_up(off + N0 * BV * esz);
   prm.off_e0[1] = off;
-  off = align_up(off + N0 * BV * tsz);
+  off = align_up(off + N0 * BV * esz);
   for (int l = 1; l < Pr->L; ++l) {
     const size_t Nl = (size_t)Pr->step.lv[l].N;
     prm.off_e[l][0] = off;
-    off = align_up(off + Nl * BV * tsz);
+    off = align_up(off + Nl * BV * esz);
     prm.off_e[l][1] = off;
-    off = align_up(off + Nl * BV * tsz);
+    off = align_up(off + Nl * BV * esz);
     prm.off_f[l] = off;
-    off = align_up(off + Nl * BV * tsz);
+    off = align_up(off + Nl * BV * esz);
   }
   prm.team_bytes = off;
   if (Pr->ws_fixed) {
@@ -189,7 +206,7 @@ lrp_status sweep_enqueue(lrp_problem* Pr, unsigned stages, int nvec, const doubl
   // Band kernel (2D, kappa = 1, one column per team, FP32 inner): every CTA
   // keeps its band of the finest level and all coarse levels in shared memory.
   bool fast = false;
-  if (Pr->kernel_variant != 1 && !(stages & (ST_SOURCE | ST_SHIFTED)) && Pr->dim == 2 && mixed && BV == 1 && !Pr->step.has_kappa &&
+  if (Pr->kernel_variant != 1 && !bf16_req && !(stages & (ST_SOURCE | ST_SHIFTED)) && Pr->dim == 2 && mixed && BV == 1 && !Pr->step.has_kappa &&
       !Pr->step.conv &&
       Pr->L >= 2 &&
       Pr->n <= 128) {
@@ -238,7 +255,7 @@ lrp_status sweep_enqueue(lrp_problem* Pr, unsigned stages, int nvec, const doubl
     }
   }
   if (!fast && !Pr->allow_waves)
-    while (C > 1 && resident_teams(mixed, Pr->dim, C, Pr->nthreads, soff, Pr->sm_count) < n_teams) C >>= 1;
+    while (C > 1 && resident_teams(mixed, bf16_req, Pr->dim, C, Pr->nthreads, soff, Pr->sm_count) < n_teams) C >>= 1;
   Pr->last_kernel = fast ? 2 : 1;
   Pr->last_team_ctas = C;
   prm.dim = Pr->dim;
@@ -304,6 +321,7 @@ lrp_status sweep_enqueue(lrp_problem* Pr, unsigned stages, int nvec, const doubl
     info->BV = BV;
     info->n_teams = n_teams;
     info->mixed = mixed;
+    info->bf16 = bf16_req && !fast;
   }
   if (Pr->prof_on) cudaEventRecord(Pr->prof_ev[0], Pr->stream);
 #ifdef LRP_SECTION_TIMERS
@@ -314,6 +332,9 @@ lrp_status sweep_enqueue(lrp_problem* Pr, unsigned stages, int nvec, const doubl
 #endif
   if (fast) {
     e = launch_fast2d(prm, Pr->stream);
+  } else if (bf16_req) {
+    e = Pr->dim == 2 ? launch_sweep<float, 2, true, __nv_bfloat16>(prm, Pr->stream)
+                     : launch_sweep<float, 3, true, __nv_bfloat16>(prm, Pr->stream);
   } else if (Pr->dim == 2) {
     e = mixed ? launch_sweep<float, 2, true>(prm, Pr->stream)
               : launch_sweep<double, 2, false>(prm, Pr->stream);
@@ -346,7 +367,7 @@ lrp_status sweep_enqueue(lrp_problem* Pr, unsigned stages, int nvec, const doubl
 // Adds a completed launch to the problem's sweep ledger (when recording).
 void ledger_add(lrp_problem* Pr, const Stats& hs, const SweepLaunch& info, double ms) {
   if (!Pr->prof_on) return;
-  const double ab = algorithmic_bytes(Pr, hs, info.BV, info.mixed);
+  const double ab = algorithmic_bytes(Pr, hs, info.BV, info.mixed, info.bf16);
   const unsigned hess = ST_PRIOR_IN | ST_FORWARD | ST_ADJOINT | ST_PRIOR_OUT;
   const bool whole = (info.stages & hess) == hess;
   for (int v : {0, info.fast ? 2 : 1, whole ? (info.fast ? 4 : 3) : -1}) {

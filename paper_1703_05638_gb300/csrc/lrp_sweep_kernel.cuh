@@ -13,11 +13,17 @@
 // refinement (residual and solution in FP64).
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "lrp_team.cuh"
 
 namespace lrp {
 
-template <typename T>
+// Team vectors. The multigrid vectors on the levels held in global memory
+// (smoother iterates e, coarse right-hand sides f) are stored as ES (T, or
+// BF16 with arithmetic in FP32); level 0's right-hand side is the PCG
+// residual r (T).
+template <typename T, typename ES = T>
 struct WSV {
   double* dbuf[3];
   double* bd;
@@ -26,8 +32,8 @@ struct WSV {
   T* p;
   T* q;
   T* c;
-  T* e[LRP_MAXLEV][2];  // level 0: the two finest smoother buffers
-  T* f[LRP_MAXLEV];     // level 0: r
+  ES* e[LRP_MAXLEV][2];  // level 0: the two finest smoother buffers
+  ES* f[LRP_MAXLEV];     // levels >= 1 (level 0: r)
 };
 
 struct Ctr {
@@ -53,6 +59,22 @@ struct SmemLv {
   T* f[LRP_MAXLEV];
 };
 
+// Calls fn with level l's right-hand side: w.f[l], which for level 0 is r
+// itself when the multigrid vectors have the arithmetic type (one code path,
+// as before BF16 storage existed); with BF16 storage level 0's is r (T) and
+// the others' are BF16, two instantiations of the phase.
+template <typename T, typename ES, class Fn>
+__device__ __forceinline__ void with_rhs(const WSV<T, ES>& w, int l, Fn&& fn) {
+  if constexpr (std::is_same<ES, T>::value) {
+    fn(w.f[l]);
+  } else {
+    if (l == 0)
+      fn((const T*)w.r);
+    else
+      fn((const ES*)w.f[l]);
+  }
+}
+
 // V-cycle: z = M r. On entry f[0] = r is complete and e[0][0] holds the first
 // (pointwise) smoother sweep of level 0. Levels 0..Ls-1 live in global memory
 // and are worked by the whole team (phases separated by team barriers);
@@ -61,8 +83,9 @@ struct SmemLv {
 // block barriers only, so no CTA idles and no team barrier is needed before
 // the prolongation back to level Ls-1 (all copies are bit-identical). On exit
 // z = e[0][returned index] and the team total r.z is in slot SL_RZ.
-template <typename T, int DIM, bool KAPPA>
-__device__ LRP_SOLVER_FN int vcycle(const Team& t, const Op& op, const WSV<T>& w, const SmemLv<T>& sm, T omega, int nu) {
+template <typename T, typename ES, int DIM, bool KAPPA>
+__device__ LRP_SOLVER_FN int vcycle(const Team& t, const Op& op, const WSV<T, ES>& w, const SmemLv<T>& sm, T omega,
+                                    int nu) {
   int ecur[LRP_MAXLEV];
   for (int l = 0; l < LRP_MAXLEV; ++l) ecur[l] = 0;
   const int L = op.L;
@@ -73,15 +96,19 @@ __device__ LRP_SOLVER_FN int vcycle(const Team& t, const Op& op, const WSV<T>& w
   // down: team levels 0..Ls-2 (pre-smoothing, restriction in global memory)
   for (int l = 0; l < Ls - 1; ++l) {
     for (int s = 1; s < nu; ++s) {
-      mg_sweep<T, DIM, KAPPA>(op.lv[l], w.e[l][ecur[l] ^ 1], w.e[l][ecur[l]], w.f[l], t.g, t.S,
-                              t.bvs, t.col, omega, (const T*)nullptr, rz);
+      with_rhs(w, l, [&](auto fl) {
+        mg_sweep<T, DIM, KAPPA>(op.lv[l], w.e[l][ecur[l] ^ 1], w.e[l][ecur[l]], fl, t.g, t.S, t.bvs, t.col, omega,
+                                (const T*)nullptr, rz);
+      });
       ecur[l] ^= 1;
       SEC_ADD(l == 0 ? SEC_BAND : SEC_COARSE);
       team_sync(t);
       SEC_ADD(SEC_SYNC);
     }
-    mg_restrict<T, DIM, KAPPA>(op.lv[l], op.lv[l + 1], w.e[l][ecur[l]], w.f[l], w.f[l + 1],
-                               w.e[l + 1][0], t.g, t.S, t.bvs, t.col, omega);
+    with_rhs(w, l, [&](auto fl) {
+      mg_restrict<T, DIM, KAPPA>(op.lv[l], op.lv[l + 1], w.e[l][ecur[l]], fl, w.f[l + 1], w.e[l + 1][0], t.g, t.S,
+                                 t.bvs, t.col, omega);
+    });
     ecur[l + 1] = 0;
     SEC_ADD(l == 0 ? SEC_RESTRICT : SEC_COARSE);
     team_sync(t);
@@ -91,8 +118,10 @@ __device__ LRP_SOLVER_FN int vcycle(const Team& t, const Op& op, const WSV<T>& w
   {
     const int l = Ls - 1;
     for (int s = 1; s < nu; ++s) {
-      mg_sweep<T, DIM, KAPPA>(op.lv[l], w.e[l][ecur[l] ^ 1], w.e[l][ecur[l]], w.f[l], t.g, t.S,
-                              t.bvs, t.col, omega, (const T*)nullptr, rz);
+      with_rhs(w, l, [&](auto fl) {
+        mg_sweep<T, DIM, KAPPA>(op.lv[l], w.e[l][ecur[l] ^ 1], w.e[l][ecur[l]], fl, t.g, t.S, t.bvs, t.col, omega,
+                                (const T*)nullptr, rz);
+      });
       ecur[l] ^= 1;
       SEC_ADD(l == 0 ? SEC_BAND : SEC_COARSE);
       team_sync(t);
@@ -106,8 +135,11 @@ __device__ LRP_SOLVER_FN int vcycle(const Team& t, const Op& op, const WSV<T>& w
     // Jacobi sweeps from zero instead (a fixed symmetric polynomial)
     const bool exact = op.lv[L - 1].n == 1;
     const int l = Ls - 1;
-    mg_restrict<T, DIM, KAPPA>(op.lv[l], op.lv[Ls], w.e[l][ecur[l]], w.f[l], sm.f[Ls], sm.e[Ls][0], t.tid,
-                               t.NT, t.bvs, t.col, (Ls == L - 1 && exact) ? T(1) : omega);
+    const T sc_ls = (Ls == L - 1 && exact) ? T(1) : omega;
+    with_rhs(w, l, [&](auto fl) {
+      mg_restrict<T, DIM, KAPPA>(op.lv[l], op.lv[Ls], w.e[l][ecur[l]], fl, sm.f[Ls], sm.e[Ls][0], t.tid, t.NT,
+                                 t.bvs, t.col, sc_ls);
+    });
     ecur[Ls] = 0;
     __syncthreads();
     for (int c = Ls; c < L - 1; ++c) {
@@ -160,8 +192,10 @@ __device__ LRP_SOLVER_FN int vcycle(const Team& t, const Op& op, const WSV<T>& w
     SEC_ADD(SEC_SYNC);
     for (int s = 0; s < nu; ++s) {
       const bool last = (l == 0 && s == nu - 1);
-      mg_sweep<T, DIM, KAPPA>(op.lv[l], w.e[l][ecur[l] ^ 1], w.e[l][ecur[l]], w.f[l], t.g, t.S,
-                              t.bvs, t.col, omega, last ? (const T*)w.f[0] : (const T*)nullptr, rz);
+      with_rhs(w, l, [&](auto fl) {
+        mg_sweep<T, DIM, KAPPA>(op.lv[l], w.e[l][ecur[l] ^ 1], w.e[l][ecur[l]], fl, t.g, t.S, t.bvs, t.col, omega,
+                                last ? (const T*)w.r : (const T*)nullptr, rz);
+      });
       ecur[l] ^= 1;
       SEC_ADD(l == 0 ? SEC_BAND : SEC_COARSE);
       if (last) contribute(t, SL_RZ, (T)rz);
@@ -177,8 +211,8 @@ __device__ LRP_SOLVER_FN int vcycle(const Team& t, const Op& op, const WSV<T>& w
 // initial residual, e[0][0] its first smoother sweep, `done` whether this
 // thread's column is already converged. Updates xt (+= alpha p; = alpha p on
 // the first iteration if zero_init).
-template <typename T, typename TX, int DIM, bool KAPPA>
-__device__ LRP_SOLVER_FN void pcg_iterate(const Team& t, const Op& op, const WSV<T>& w, const SmemLv<T>& sm, TX* xt,
+template <typename T, typename ES, typename TX, int DIM, bool KAPPA>
+__device__ LRP_SOLVER_FN void pcg_iterate(const Team& t, const Op& op, const WSV<T, ES>& w, const SmemLv<T>& sm, TX* xt,
                             bool zero_init,
                             double tol2bb, bool& done, const SolveCfg& cfg, T omega, T scale0,
                             Ctr& ctr, double& rr_last) {
@@ -188,16 +222,16 @@ __device__ LRP_SOLVER_FN void pcg_iterate(const Team& t, const Op& op, const WSV
   double rz_old = 0.0;
   bool all = __syncthreads_and(done);
   while (!all) {
-    const int zc = vcycle<T, DIM, KAPPA>(t, op, w, sm, omega, cfg.nu);
+    const int zc = vcycle<T, ES, DIM, KAPPA>(t, op, w, sm, omega, cfg.nu);
     SEC_T0();
-    const T* z = w.e[0][zc];
+    const ES* z = w.e[0][zc];
     const double rz = total_t<T>(t, SL_RZ);
     SEC_ADD(SEC_REDUCE);
     const T beta = (T)((it_count == 0 || done || !(rz_old > 0.0)) ? 0.0 : rz / rz_old);
     // phase A: p = z + beta p, q = A z + beta q, accumulate p.q
     double pq = 0.0;
     {
-      Ld<T> ld{z, t.bvs, t.col};
+      LdT<ES, T> ld{z, t.bvs, t.col};
       T pqp = T(0);  // per-thread partial in the inner type
       batched_loop<V2<T>>(
           t.g, items, t.S,
@@ -209,10 +243,10 @@ __device__ LRP_SOLVER_FN void pcg_iterate(const Team& t, const Op& op, const WSV
             const T az = op_at<T, DIM, KAPPA>(l0, ld, p, i0, i1, i2, d);
             V2<T> r;
             if (it_count == 0) {
-              r.a = z[it];
+              r.a = cvt<T>(z[it]);
               r.b = az;
             } else {
-              r.a = z[it] + beta * w.p[it];
+              r.a = cvt<T>(z[it]) + beta * w.p[it];
               r.b = az + beta * w.q[it];
             }
             return r;
@@ -247,15 +281,15 @@ __device__ LRP_SOLVER_FN void pcg_iterate(const Team& t, const Op& op, const WSV
             const int p = it >> t.bvs;
             XRE v;
             v.x = fresh ? (TX)(alpha * w.p[it]) : (TX)(xt[it] + (TX)(alpha * w.p[it]));
-            v.r = w.f[0][it] - alpha * w.q[it];
+            v.r = w.r[it] - alpha * w.q[it];
             v.e = scale0 * v.r * dinv_at<T, KAPPA>(l0, p);
             return v;
           },
           [&](int it, const XRE& v) {
             xt[it] = v.x;
-            w.f[0][it] = v.r;
+            w.r[it] = v.r;
             rrp += v.r * v.r;
-            w.e[0][0][it] = v.e;
+            w.e[0][0][it] = cst<ES>(v.e);
             if (op.L == 1) rz1p += v.r * v.e;
           });
       rr = (double)rrp;
@@ -318,7 +352,7 @@ __device__ LRP_SOLVER_FN double* solve_fp64(const Team& t, const SweepParams& P,
     double d, ax = 0.0;
     if (x0) ax = op_at<double, DIM, KAPPA>(l0, ld, p, i0, i1, i2, d);
     const double rv = bp - ax;
-    w.f[0][it] = rv;
+    w.r[it] = rv;
     X1[it] = x0 ? x0[it] : 0.0;
     const double e = scale0 * rv * dinv_at<double, KAPPA>(l0, p);
     w.e[0][0][it] = e;
@@ -342,7 +376,7 @@ __device__ LRP_SOLVER_FN double* solve_fp64(const Team& t, const SweepParams& P,
     done = true;
   }
   double rr_last = rrt;
-  pcg_iterate<double, double, DIM, KAPPA>(t, op, w, sm, X1, false, tol2bb, done, P.cfg, omega,
+  pcg_iterate<double, double, double, DIM, KAPPA>(t, op, w, sm, X1, false, tol2bb, done, P.cfg, omega,
                                           scale0, ctr, rr_last);
   ctr.max_res = fmax(ctr.max_res, bbt > 0.0 ? sqrt(rr_last / bbt) : 0.0);
   ctr.solves += 1;
@@ -356,9 +390,9 @@ __device__ LRP_SOLVER_FN double* solve_fp64(const Team& t, const SweepParams& P,
 // values underflow. The scale of refinement k is predicted from the residual
 // of refinement k-1 (the inner solve reduces it by about inner_rtol); that of
 // the first refinement from the previous solve's right-hand side.
-template <int DIM, bool KAPPA>
+template <int DIM, bool KAPPA, typename ES>
 __device__ LRP_SOLVER_FN double* solve_mixed(const Team& t, const SweepParams& P, const Op& op,
-                               const WSV<float>& w, const SmemLv<float>& sm, const double* bsrc,
+                               const WSV<float, ES>& w, const SmemLv<float>& sm, const double* bsrc,
                                const double* dsrc, const double* x0, double* X1, double* X2,
                                Ctr& ctr) {
   const OpLevel& l0 = op.lv[0];
@@ -407,9 +441,9 @@ __device__ LRP_SOLVER_FN double* solve_mixed(const Team& t, const SweepParams& P
           }
           tgt[it] = v.x;
           const float rf = (float)(v.rd * sc);
-          w.f[0][it] = rf;
+          w.r[it] = rf;
           const float e = scale0 * rf * dinv_at<float, KAPPA>(l0, p);
-          w.e[0][0][it] = e;
+          w.e[0][0][it] = cst<ES>(e);
           rr += v.rd * v.rd;
           if (op.L == 1) rz1 += (double)(rf * e);
         });
@@ -446,7 +480,7 @@ __device__ LRP_SOLVER_FN double* solve_mixed(const Team& t, const SweepParams& P
     bool idone = done;
     const double itol2 = P.cfg.inner_rtol * P.cfg.inner_rtol * rrt * sc * sc;
     double rr_in = rrt * sc * sc;
-    pcg_iterate<float, float, DIM, KAPPA>(t, op, w, sm, w.c, true, itol2, idone, P.cfg, omega, scale0,
+    pcg_iterate<float, ES, float, DIM, KAPPA>(t, op, w, sm, w.c, true, itol2, idone, P.cfg, omega, scale0,
                                           ctr, rr_in);
     xa = tgt;
     double* tmp = tgt;
@@ -494,7 +528,7 @@ __device__ __forceinline__ double op_conv_at(const OpLevel& lv, const LD& ld, in
 // BiCGStab (van der Vorst, 1992) with the Jacobi preconditioner applied on
 // the right, in FP64: five phases and team barriers per iteration (the two
 // operator applications need their input's neighbours). Vectors: x in X1,
-// r in w.f[0], shadow residual r^ = r_0 in w.c, p in w.p, v in w.q,
+// r in w.r, shadow residual r^ = r_0 in w.c, p in w.p, v in w.q,
 // D^-1 p and D^-1 s in the two finest smoother buffers, s in place of r,
 // t in X2.
 template <int DIM>
@@ -505,7 +539,7 @@ __device__ LRP_SOLVER_FN double* solve_bicgstab(const Team& t, const SweepParams
   const OpLevel& l0 = op.lv[0];
   const int items = l0.N << t.bvs;
   const double dinv = l0.dinv;
-  double* r = w.f[0];
+  double* r = w.r;
   double* rh = w.c;
   double* pv = w.p;
   double* vv = w.q;
@@ -647,15 +681,15 @@ __device__ LRP_SOLVER_FN double* solve_bicgstab(const Team& t, const SweepParams
   return X1;
 }
 
-template <typename T, int DIM, bool MIXED>
+template <typename T, int DIM, bool MIXED, typename ES>
 __device__ __forceinline__ double* solve_any(const Team& t, const SweepParams& P, const Op& op,
-                                             const WSV<T>& w, const SmemLv<T>& sm, const double* bsrc,
+                                             const WSV<T, ES>& w, const SmemLv<T>& sm, const double* bsrc,
                                              const double* dsrc, const double* x0, double* X1,
                                              double* X2, Ctr& ctr, bool transpose = false) {
   if constexpr (MIXED) {
     if (op.has_kappa)
-      return solve_mixed<DIM, true>(t, P, op, w, sm, bsrc, dsrc, x0, X1, X2, ctr);
-    return solve_mixed<DIM, false>(t, P, op, w, sm, bsrc, dsrc, x0, X1, X2, ctr);
+      return solve_mixed<DIM, true, ES>(t, P, op, w, sm, bsrc, dsrc, x0, X1, X2, ctr);
+    return solve_mixed<DIM, false, ES>(t, P, op, w, sm, bsrc, dsrc, x0, X1, X2, ctr);
   } else {
     if (op.conv) return solve_bicgstab<DIM>(t, P, op, w, bsrc, dsrc, x0, X1, X2, transpose, ctr);
     if (op.has_kappa) return solve_fp64<DIM, true>(t, P, op, w, sm, bsrc, dsrc, x0, X1, ctr);
@@ -677,7 +711,7 @@ __device__ __forceinline__ int prior_scale_copy(const Team& t, const SweepParams
   return nxt;
 }
 
-template <typename T, int DIM, bool MIXED>
+template <typename T, int DIM, bool MIXED, typename ES = T>
 __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
   __shared__ double s_red[2 * NSLOT * LRP_MAXBV];
   __shared__ double s_redw[32 * LRP_MAXBV];
@@ -705,7 +739,7 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
   const long long k_t0 = clock64();
 #endif
   char* base = P.ws + (size_t)team * P.team_bytes;
-  WSV<T> w;
+  WSV<T, ES> w;
   for (int k = 0; k < 3; ++k) w.dbuf[k] = (double*)(base + P.off_dbuf[k]);
   w.bd = (double*)(base + P.off_bd);
   w.obs = (double*)(base + P.off_obs);
@@ -713,13 +747,16 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
   w.p = (T*)(base + P.off_p);
   w.q = (T*)(base + P.off_q);
   w.c = (T*)(base + P.off_c);
-  w.e[0][0] = (T*)(base + P.off_e0[0]);
-  w.e[0][1] = (T*)(base + P.off_e0[1]);
-  w.f[0] = w.r;
+  w.e[0][0] = (ES*)(base + P.off_e0[0]);
+  w.e[0][1] = (ES*)(base + P.off_e0[1]);
+  if constexpr (std::is_same<ES, T>::value)
+    w.f[0] = w.r;  // level 0's right-hand side is r
+  else
+    w.f[0] = nullptr;
   for (int l = 1; l < LRP_MAXLEV; ++l) {
-    w.e[l][0] = (T*)(base + P.off_e[l][0]);
-    w.e[l][1] = (T*)(base + P.off_e[l][1]);
-    w.f[l] = (T*)(base + P.off_f[l]);
+    w.e[l][0] = (ES*)(base + P.off_e[l][0]);
+    w.e[l][1] = (ES*)(base + P.off_e[l][1]);
+    w.f[l] = (ES*)(base + P.off_f[l]);
   }
   if (P.poison) {
     for (size_t i = t.tid; i < P.smem_bytes / sizeof(T); i += t.NT) ((T*)s_dyn)[i] = T(NAN);
@@ -759,7 +796,7 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
     if (P.prior_scale > 0.0) {
       cur = prior_scale_copy(t, P, w.dbuf, cur, items0);
     } else {
-      double* res = solve_any<T, DIM, MIXED>(t, P, P.prior, w, sm, w.dbuf[cur], nullptr, nullptr, X1,
+      double* res = solve_any<T, DIM, MIXED, ES>(t, P, P.prior, w, sm, w.dbuf[cur], nullptr, nullptr, X1,
                                              X2, ctr);
       cur = buf_index(w.dbuf, res);
     }
@@ -769,7 +806,7 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
     // block-diagonal preconditioner of the alternating space-time solver
     double* X1 = w.dbuf[(cur + 1) % 3];
     double* X2 = w.dbuf[(cur + 2) % 3];
-    double* res = solve_any<T, DIM, MIXED>(t, P, P.team_ops[team], w, sm, w.dbuf[cur], nullptr, nullptr, X1, X2,
+    double* res = solve_any<T, DIM, MIXED, ES>(t, P, P.team_ops[team], w, sm, w.dbuf[cur], nullptr, nullptr, X1, X2,
                                            ctr, P.shift_transpose != 0);
     cur = buf_index(w.dbuf, res);
   }
@@ -791,7 +828,7 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
       }
       double* X1 = w.dbuf[(cur + 1) % 3];
       double* X2 = w.dbuf[(cur + 2) % 3];
-      double* res = solve_any<T, DIM, MIXED>(t, P, P.step, w, sm, w.dbuf[cur], nullptr, w.dbuf[cur],
+      double* res = solve_any<T, DIM, MIXED, ES>(t, P, P.step, w, sm, w.dbuf[cur], nullptr, w.dbuf[cur],
                                              X1, X2, ctr);
       cur = buf_index(w.dbuf, res);
       // fused observation d_n = B y_n (/ sigma^2 for the Hessian); no barrier
@@ -834,7 +871,7 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
       const int qi = q ? buf_index(w.dbuf, q) : cur;
       double* X1 = w.dbuf[(qi + 1) % 3];
       double* X2 = w.dbuf[(qi + 2) % 3];
-      double* res = solve_any<T, DIM, MIXED>(t, P, P.step, w, sm, q, dsrc, q, X1, X2, ctr, true);
+      double* res = solve_any<T, DIM, MIXED, ES>(t, P, P.step, w, sm, q, dsrc, q, X1, X2, ctr, true);
       q = res;
       if ((P.stages & ST_TRAJ_ADJ) && valid) {
         // steps after the last observation hold q_n = 0: the caller zeroes the buffer
@@ -855,7 +892,7 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepParams P) {
     if (P.prior_scale > 0.0) {
       cur = prior_scale_copy(t, P, w.dbuf, cur, items0);
     } else {
-      double* res = solve_any<T, DIM, MIXED>(t, P, P.prior, w, sm, w.dbuf[cur], nullptr, nullptr, X1,
+      double* res = solve_any<T, DIM, MIXED, ES>(t, P, P.prior, w, sm, w.dbuf[cur], nullptr, nullptr, X1,
                                              X2, ctr);
       cur = buf_index(w.dbuf, res);
     }
@@ -900,9 +937,9 @@ inline int smem_dynamic_max(K kern) {
   return v - (int)fa.sharedSizeBytes;
 }
 
-template <typename T, int DIM, bool MIXED>
+template <typename T, int DIM, bool MIXED, typename ES = T>
 static cudaError_t prepare_sweep(size_t smem) {
-  auto kern = sweep_kernel<T, DIM, MIXED>;
+  auto kern = sweep_kernel<T, DIM, MIXED, ES>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
   const int cap = smem_dynamic_max(kern);
@@ -910,10 +947,10 @@ static cudaError_t prepare_sweep(size_t smem) {
   return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
 }
 
-template <typename T, int DIM, bool MIXED>
+template <typename T, int DIM, bool MIXED, typename ES = T>
 cudaError_t launch_sweep(const SweepParams& prm, cudaStream_t stream) {
-  auto kern = sweep_kernel<T, DIM, MIXED>;
-  cudaError_t e = prepare_sweep<T, DIM, MIXED>(prm.smem_bytes);
+  auto kern = sweep_kernel<T, DIM, MIXED, ES>;
+  cudaError_t e = prepare_sweep<T, DIM, MIXED, ES>(prm.smem_bytes);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(prm.n_teams * prm.C);
@@ -937,10 +974,10 @@ cudaError_t launch_sweep(const SweepParams& prm, cudaStream_t stream) {
 // How many teams of C CTAs (NT threads, smem dynamic bytes each) can be
 // resident at once: the sweep keeps every team resident for its whole
 // lifetime, so a launch with more teams than this runs in waves.
-template <typename T, int DIM, bool MIXED>
+template <typename T, int DIM, bool MIXED, typename ES = T>
 int max_resident_teams(int C, int NT, size_t smem, int sm_count) {
-  auto kern = sweep_kernel<T, DIM, MIXED>;
-  if (prepare_sweep<T, DIM, MIXED>(smem) != cudaSuccess) {
+  auto kern = sweep_kernel<T, DIM, MIXED, ES>;
+  if (prepare_sweep<T, DIM, MIXED, ES>(smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }

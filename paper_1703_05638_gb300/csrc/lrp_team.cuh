@@ -14,6 +14,7 @@
 #pragma once
 
 #include <cooperative_groups.h>
+#include <cuda_bf16.h>
 
 #include "lrp_internal.h"
 
@@ -195,6 +196,33 @@ __device__ __forceinline__ const double* kap<double>(const OpLevel& lv, int a) {
 template <>
 __device__ __forceinline__ const float* kap<float>(const OpLevel& lv, int a) { return lv.kf[a]; }
 
+// Conversions between the arithmetic type and a storage type (BF16
+// storage of the multigrid vectors: round to nearest even on store).
+template <typename T, typename S>
+__device__ __forceinline__ T cvt(S x) {
+  return (T)x;
+}
+template <>
+__device__ __forceinline__ float cvt<float, __nv_bfloat16>(__nv_bfloat16 x) {
+  return __bfloat162float(x);
+}
+template <typename S, typename T>
+__device__ __forceinline__ S cst(T x) {
+  return (S)x;
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 cst<__nv_bfloat16, float>(float x) {
+  return __float2bfloat16_rn(x);
+}
+
+// Loader of one interleaved column of a team vector stored as S, read as T.
+template <typename S, typename T>
+struct LdT {
+  const S* v;
+  int bvs, col;
+  __device__ __forceinline__ T operator()(int q) const { return cvt<T>(v[(q << bvs) + col]); }
+};
+
 // Loader of one interleaved column of a team vector.
 template <typename T>
 struct Ld {
@@ -351,11 +379,13 @@ struct V3 {
 #ifndef LRP_SWEEP_UNROLL
 #define LRP_SWEEP_UNROLL 1
 #endif
-template <typename T, int DIM, bool KAPPA>
-__device__ __forceinline__ T mg_sweep_items(const OpLevel& lv, T* __restrict__ eo, const T* ei, const T* f,
+// (eo, ei: the level's smoother iterates, f: its right-hand side, each in
+// its storage type; arithmetic in T)
+template <typename T, int DIM, bool KAPPA, typename EO, typename EI, typename FF>
+__device__ __forceinline__ T mg_sweep_items(const OpLevel& lv, EO* __restrict__ eo, const EI* ei, const FF* f,
                                             int start, int stride, int bvs, int col, T omega, const T* rz_r) {
   const int items = lv.N << bvs;
-  Ld<T> ld{ei, bvs, col};
+  LdT<EI, T> ld{ei, bvs, col};
   T acc = T(0);  // per-thread partial in the inner type
   for (int it0 = start; it0 < items; it0 += LRP_SWEEP_UNROLL * stride) {
 #pragma unroll
@@ -367,8 +397,8 @@ __device__ __forceinline__ T mg_sweep_items(const OpLevel& lv, T* __restrict__ e
         decomp<DIM>(lv, p, i0, i1, i2);
         T d;
         const T ae = op_at<T, DIM, KAPPA>(lv, ld, p, i0, i1, i2, d);
-        const T e = ei[it] + omega * (f[it] - ae) * dinv_at<T, KAPPA>(lv, p);
-        eo[it] = e;
+        const T e = cvt<T>(ei[it]) + omega * (cvt<T>(f[it]) - ae) * dinv_at<T, KAPPA>(lv, p);
+        eo[it] = cst<EO>(e);
         if (rz_r) acc += rz_r[it] * e;
       }
     }
@@ -376,9 +406,9 @@ __device__ __forceinline__ T mg_sweep_items(const OpLevel& lv, T* __restrict__ e
   return acc;
 }
 
-template <typename T, int DIM, bool KAPPA>
-__device__ __forceinline__ void mg_sweep(const OpLevel& lv, T* eo,
-                                         const T* ei, const T* f,
+template <typename T, int DIM, bool KAPPA, typename EO, typename EI, typename FF>
+__device__ __forceinline__ void mg_sweep(const OpLevel& lv, EO* eo,
+                                         const EI* ei, const FF* f,
                                          int start, int stride, int bvs, int col, T omega,
                                          const T* rz_r, double& rz) {
   const T acc = mg_sweep_items<T, DIM, KAPPA>(lv, eo, ei, f, start, stride, bvs, col, omega, rz_r);
@@ -388,13 +418,13 @@ __device__ __forceinline__ void mg_sweep(const OpLevel& lv, T* eo,
 // Restrict the residual f - A e of level l (fine) to level l+1 (coarse) by
 // full weighting, and start the coarse smoother: e_c = scale * f_c / d_c
 // (scale = omega, or 1 on the single-node coarsest level: exact solve).
-template <typename T, int DIM, bool KAPPA>
+template <typename T, int DIM, bool KAPPA, typename EF, typename FF, typename FC, typename EC>
 __device__ __forceinline__ void mg_restrict(const OpLevel& lf, const OpLevel& lc,
-                                            const T* ef, const T* ff,
-                                            T* fc, T* ec, int start,
+                                            const EF* ef, const FF* ff,
+                                            FC* fc, EC* ec, int start,
                                             int stride, int bvs, int col, T scale) {
   const int items = lc.N << bvs;
-  Ld<T> ld{ef, bvs, col};
+  LdT<EF, T> ld{ef, bvs, col};
   const int nf = lf.n;
   batched_loop<V2<T>>(
       start, items, stride,
@@ -411,7 +441,7 @@ __device__ __forceinline__ void mg_restrict(const OpLevel& lf, const OpLevel& lc
               const int F2 = (DIM == 3) ? 2 * c2 + 1 + dz : 0;
               const int pf = F0 + nf * (F1 + nf * F2);
               T d;
-              const T res = ff[(pf << bvs) + col] - op_at<T, DIM, KAPPA>(lf, ld, pf, F0, F1, F2, d);
+              const T res = cvt<T>(ff[(pf << bvs) + col]) - op_at<T, DIM, KAPPA>(lf, ld, pf, F0, F1, F2, d);
               T w = (dx == 0 ? T(0.5) : T(0.25)) * (dy == 0 ? T(0.5) : T(0.25));
               if (DIM == 3) w *= (dz == 0 ? T(0.5) : T(0.25));
               acc += w * res;
@@ -424,17 +454,17 @@ __device__ __forceinline__ void mg_restrict(const OpLevel& lf, const OpLevel& lc
         return r;
       },
       [&](int it, const V2<T>& r) {
-        fc[it] = r.a;
-        ec[it] = r.b;
+        fc[it] = cst<FC>(r.a);
+        ec[it] = cst<EC>(r.b);
       });
 }
 
 // e_out = e_in + P e_c (bi/trilinear interpolation, zero boundary); e_out
 // may equal e_in (in place).
-template <typename T, int DIM>
-__device__ __forceinline__ void mg_prolong(const OpLevel& lf, const OpLevel& lc, T* ef,
-                                           const T* ec, int start, int stride, int bvs,
-                                           int col, const T* ein = nullptr) {
+template <typename T, int DIM, typename EF, typename EC>
+__device__ __forceinline__ void mg_prolong(const OpLevel& lf, const OpLevel& lc, EF* ef,
+                                           const EC* ec, int start, int stride, int bvs,
+                                           int col, const EF* ein = nullptr) {
   const int items = lf.N << bvs;
   const int nc = lc.n;
   batched_loop<T>(start, items, stride, [&](int it) {
@@ -463,12 +493,12 @@ __device__ __forceinline__ void mg_prolong(const OpLevel& lf, const OpLevel& lc,
       for (int b = 0; b < cnt[1]; ++b) {
         for (int a = 0; a < cnt[0]; ++a) {
           const int P = ci[0][a] + nc * (ci[1][b] + nc * z);
-          acc += wz * cw[1][b] * cw[0][a] * ec[(P << bvs) + col];
+          acc += wz * cw[1][b] * cw[0][a] * cvt<T>(ec[(P << bvs) + col]);
         }
       }
     }
-    return (ein ? ein[it] : ef[it]) + acc;
-  }, [&](int it, T v) { ef[it] = v; });
+    return cvt<T>(ein ? ein[it] : ef[it]) + acc;
+  }, [&](int it, T v) { ef[it] = cst<EF>(v); });
 }
 
 }  // namespace lrp
