@@ -178,3 +178,21 @@ def test_als_argument_checks_and_degenerate_source():
     assert st["sweeps"] == 2 and res[-1] <= 5e-8, (res, st)
     assert np.all(res[:-1] > 5e-8)
     G.close()
+
+
+def test_als_hessian_many_columns_equal_single_column_calls():
+    """A block of 11 columns runs on 8 side handles at once (three of them
+    take two columns); every column equals the same column applied alone,
+    to the solves' accuracy (the side handles share the operators and the
+    settings, not the solver state)."""
+    spec = _spec("heat2d")
+    P = OProblem(spec)
+    X = synth.normal_block(P.nx, 11, 113)
+    G = lrp.lrp_setup_problem(spec, precision=lrp.LRP_FP64, als_rank=8, als_sweeps=3)
+    Y, st = lrp.lrp_hessian_apply(G, X, flags=lrp.LRP_ALS_SOLVES)
+    assert st["status"] == lrp.LRP_OK, (st, lrp.lrp_last_error())
+    for j in (0, 5, 8, 10):
+        y1, st1 = lrp.lrp_hessian_apply(G, X[:, j:j + 1], flags=lrp.LRP_ALS_SOLVES)
+        assert st1["status"] == lrp.LRP_OK
+        assert relerr(Y[:, j], y1[:, 0]) < 1e-10, j
+    G.close()
