@@ -375,6 +375,23 @@ __global__ void __launch_bounds__(256) k_mdot(size_t n, int m, const double* V, 
   }
 }
 
+// w[i] += alpha sum_k h[k] V[k n + i], i < n (m <= kGmresMax + 1 vectors of
+// n entries, coefficients on the device): the Gram-Schmidt update of GMRES
+// and its final combination, streaming the basis once with many loads in
+// flight per thread.
+__global__ void __launch_bounds__(256) k_mupdate(size_t n, int m, const double* V, const double* h, double alpha,
+                                                 double* w) {
+  __shared__ double sh[64];
+  if (threadIdx.x < m && threadIdx.x < 64) sh[threadIdx.x] = h[threadIdx.x];
+  __syncthreads();
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+#pragma unroll 8
+    for (int k = 0; k < m; ++k) acc += sh[k] * V[(size_t)k * n + i];
+    w[i] += alpha * acc;
+  }
+}
+
 // out[k] = beta out[k] + sum_b part[b * m + k] (fixed order); one warp per k.
 __global__ void k_mdot_sum(int nb, int m, const double* part, double* out, double beta) {
   const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -800,6 +817,15 @@ cudaError_t orth_cholqr(cudaStream_t s, AlsWS& w, int rows, int r, double* A, do
   return cudaMemcpyAsync(A, src, (size_t)rows * r * sizeof(double), cudaMemcpyDeviceToDevice, s);
 }
 
+// w += alpha V h (V: m vectors of n entries, ld n; h: m device coefficients)
+cudaError_t mupdate(cudaStream_t s, size_t n, int m, const double* V, const double* h, double alpha, double* w) {
+  if (m <= 0) return cudaSuccess;
+  const unsigned grid = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 8);
+  note_launch();
+  k_mupdate<<<grid, 256, 0, s>>>(n, m, V, h, alpha, w);
+  return cudaGetLastError();
+}
+
 // <a, b> over n entries into dst (device)
 cudaError_t dot_into(cudaStream_t s, AlsWS& w, size_t n, const double* a, const double* b, double* dst, double beta) {
   return mdot(s, w, n, 1, a, b, dst, beta);
@@ -862,7 +888,7 @@ lrp_status space_step(lrp_problem* P, AlsWS& w, int transpose, bool warm, double
       double* hcol = w.H.p + (size_t)j * ldh;
       for (int pass = 0; pass < 2; ++pass) {
         CKL(mdot(s, w, n, j + 1, w.Vb.p, wv, w.hv.p, 0.0));
-        CKL(gemm_nn(s, (int)n, j + 1, 1, -1.0, w.Vb.p, (int)n, w.hv.p, j + 1, 1.0, wv, (int)n));
+        CKL(mupdate(s, n, j + 1, w.Vb.p, w.hv.p, -1.0, wv));
         CKL(axpby(s, (size_t)(j + 1), 1.0, w.hv.p, 1.0, hcol));
       }
       CKL(dot_into(s, w, n, wv, wv, w.scal.p + 4, 0.0));
@@ -889,7 +915,7 @@ lrp_status space_step(lrp_problem* P, AlsWS& w, int transpose, bool warm, double
     note_launch();
     k_backsolve<<<1, 1, 0, s>>>(m, w.H.p, ldh, w.g.p, w.y.p);
     CKL(cudaGetLastError());
-    CKL(gemm_nn(s, (int)n, m, 1, 1.0, w.Zb.p, (int)n, w.y.p, m, 1.0, w.W.p, (int)n));
+    CKL(mupdate(s, n, m, w.Zb.p, w.y.p, 1.0, w.W.p));
     warm = true;
     if (rnorm <= target) break;
     if (cyc == kGmresCycles - 1) {
