@@ -101,6 +101,10 @@ lrp_status sweep_enqueue(lrp_problem* Pr, unsigned stages, int nvec, const doubl
   // kernel keeps its vectors in shared memory in FP32); decided with the
   // kernel below, the workspace is laid out for the larger element size
   const bool bf16_req = mixed && Pr->desc.mg_bf16 != 0;
+  if (bf16_req && (Pr->kernel_variant == 2 || Pr->kernel_variant == 3)) {
+    set_error("the band kernel has no BF16 form (mg_bf16 runs the generic kernel)");
+    return LRP_EINVAL;
+  }
   const size_t N0 = (size_t)Pr->nx;
   SweepParams prm;
   std::memset(&prm, 0, sizeof(prm));
