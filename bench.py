@@ -752,6 +752,7 @@ def main():
                          "(kernel-level measurement and profiling); serve: the serving workload alone")
     ap.add_argument("--als-rank", type=int, default=0,
                     help="--mode als: only this rank, the default preconditioner and --workload (profiling)")
+    ap.add_argument("--als-cols", type=int, default=4, help="--mode als with --als-rank: columns per product")
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=2)
     ap.add_argument("--no-autotune", action="store_true")
@@ -820,7 +821,7 @@ def main():
             if args.nt:
                 spec.nt, spec.T = args.nt, args.nt * spec.T / spec.nt
             if args.als_rank:
-                runs = [als_bench(lrp, spec, prec, ranks=(args.als_rank,), prec=((0.0, 2),))]
+                runs = [als_bench(lrp, spec, prec, ranks=(args.als_rank,), prec=((0.0, 2),), ncols=args.als_cols)]
             else:
                 runs = [als_bench(lrp, spec, prec), als_bench(lrp, synth.paper_heat_spec(1e6), prec)]
             print(json.dumps({"metric": "Hessian apply ms per column: alternating low-rank space-time solves "

@@ -30,9 +30,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <memory>
 #include <string>
-#include <thread>
 #include <vector>
 
 #include "lrp_dense.h"
@@ -78,18 +76,21 @@ constexpr int kPrecondIts = 2;         // default CG iterations per precondition
 // ---------------------------------------------------------------------------
 // kernels
 
-// Y[:, j] = (A x_j) - sum_i x_i Tm[i, j] for the r columns of X (nx x r,
-// ld nx): the operator of the space step (Tm = T) or plain A X (Tm NULL).
-// A = I + tau L of the problem on its finest level (transpose: A^T).
+// Y[:, j] = (A x_j) - sum_i x_i Tm[i, j] for the columns of X (nx x ncol,
+// ld nx; ncol = nb r: nb solves of r columns each, solve c with its own
+// r x r matrix Tm + c r r): the operator of the space step (Tm = T) or plain
+// A X (Tm NULL). A = I + tau L of the problem on its finest level
+// (transpose: A^T).
 template <int DIM, bool KAPPA, bool CONV>
-__global__ void k_kron_apply(const OpLevel l0, int r, const double* X, const double* Tm, int transpose, double* Y) {
+__global__ void k_kron_apply(const OpLevel l0, int r, int ncol, const double* X, const double* Tm, int transpose,
+                             double* Y) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y;
-  if (p >= l0.N || j >= r) return;
+  const int y = blockIdx.y;
+  if (p >= l0.N || y >= ncol) return;
   const size_t nx = (size_t)l0.N;
   int i0, i1, i2;
   decomp<DIM>(l0, p, i0, i1, i2);
-  Ld<double> ld{X + (size_t)j * nx, 0, 0};
+  Ld<double> ld{X + (size_t)y * nx, 0, 0};
   double d;
   double v;
   if (CONV)
@@ -97,9 +98,12 @@ __global__ void k_kron_apply(const OpLevel l0, int r, const double* X, const dou
   else
     v = op_at<double, DIM, KAPPA>(l0, ld, p, i0, i1, i2, d);
   if (Tm) {
-    for (int i = 0; i < r; ++i) v -= X[(size_t)i * nx + p] * Tm[(size_t)j * r + i];
+    const int c = y / r, j = y - c * r;
+    const double* Xc = X + (size_t)c * r * nx;
+    const double* Tc = Tm + (size_t)c * r * r;
+    for (int i = 0; i < r; ++i) v -= Xc[(size_t)i * nx + p] * Tc[(size_t)j * r + i];
   }
-  Y[(size_t)j * nx + p] = v;
+  Y[(size_t)y * nx + p] = v;
 }
 
 // Per-node inverse diagonal of I + (c / s) L from that of I + c L:
@@ -115,8 +119,17 @@ __global__ void k_shift_dinv(int N, const double* dinv, double inv_s, double* ou
 // GMRES: applies the j earlier Givens rotations to column j of the
 // Hessenberg matrix H (ld ldh), forms rotation j that zeroes H[j+1, j],
 // updates the rotated right-hand side g; res = |g[j+1]| (the residual norm).
-__global__ void k_givens(int j, double* H, int ldh, double* cs, double* sn, double* g, double* res) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// (one thread per solve c = blockIdx.x; its H, cs, sn, g at strides hs, kmax,
+// kmax + 1; res[c])
+__global__ void k_givens(int j, double* H, int ldh, size_t hs, double* cs, double* sn, double* g, int kmax,
+                         double* res) {
+  if (threadIdx.x != 0) return;
+  const int col = blockIdx.x;
+  H += (size_t)col * hs;
+  cs += (size_t)col * kmax;
+  sn += (size_t)col * kmax;
+  g += (size_t)col * (kmax + 1);
+  res += col;
   double* h = H + (size_t)j * ldh;
   for (int i = 0; i < j; ++i) {
     const double a = h[i], b = h[i + 1];
@@ -138,8 +151,13 @@ __global__ void k_givens(int j, double* H, int ldh, double* cs, double* sn, doub
 
 // y = R^{-1} g with R the leading m x m upper triangle of H (ld ldh); a zero
 // pivot (a vanished direction) leaves its component at zero.
-__global__ void k_backsolve(int m, const double* H, int ldh, const double* g, double* y) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// (one thread per solve c = blockIdx.x, strides as k_givens)
+__global__ void k_backsolve(int m, const double* H, int ldh, size_t hs, const double* g, double* y, int kmax) {
+  if (threadIdx.x != 0) return;
+  const int c = blockIdx.x;
+  H += (size_t)c * hs;
+  g += (size_t)c * (kmax + 1);
+  y += (size_t)c * kmax;
   for (int i = m - 1; i >= 0; --i) {
     double acc = g[i];
     for (int k = i + 1; k < m; ++k) acc -= H[(size_t)k * ldh + i] * y[k];
@@ -150,17 +168,26 @@ __global__ void k_backsolve(int m, const double* H, int ldh, const double* g, do
 
 // H[j+1, j] = sqrt(*nrm2) and g[0] = that norm for j < 0 (the start of a
 // cycle); inv = 1 / the norm (0 for a vanished vector).
-__global__ void k_norm_entry(const double* nrm2, double* dst, double* inv) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const double v = sqrt(fmax(*nrm2, 0.0));
-  *dst = v;
-  *inv = v > 0.0 ? 1.0 / v : 0.0;
+// (solve c = blockIdx.x: nrm2[c], dst + c dst_stride, inv[c])
+__global__ void k_norm_entry(const double* nrm2, double* dst, size_t dst_stride, double* inv) {
+  if (threadIdx.x != 0) return;
+  const int c = blockIdx.x;
+  const double v = sqrt(fmax(nrm2[c], 0.0));
+  dst[(size_t)c * dst_stride] = v;
+  inv[c] = v > 0.0 ? 1.0 / v : 0.0;
 }
 
-// y = (*scale) x (n entries)
+// y_c = scale[c] x_c for the solves c = blockIdx.y (n entries each, offset c n)
 __global__ void k_scale_by(size_t n, const double* scale, const double* x, double* y) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) y[i] = (*scale) * x[i];
+  const size_t c = blockIdx.y;
+  if (i < n) y[c * n + i] = scale[c] * x[c * n + i];
+}
+
+// H_c[0:m, j] += hv_c[0:m] for the solves c = blockIdx.x
+__global__ void k_hadd(int m, const double* hv, size_t hvs, double* H, size_t hs) {
+  const int c = blockIdx.x;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) H[(size_t)c * hs + i] += hv[(size_t)c * hvs + i];
 }
 
 // out[i] = v[i] * s[i / nx] (column scaling by a device vector), in place allowed
@@ -175,6 +202,12 @@ __global__ void k_col_scale(size_t nx, int r, const double* s, double* v) {
 __global__ void k_shift_gram(int nt, int r, const double* V, double* T, double* inv_s, int* status) {
   __shared__ double red[32];
   const int e = blockIdx.x;
+  {
+    const size_t c = blockIdx.y;  // solve c: its V, T and shifts
+    V += c * nt * r;
+    T += c * r * r;
+    inv_s += c * r;
+  }
   const int i = e % r, j = e / r;
   double acc = 0.0;
   for (int n = 1 + threadIdx.x; n < nt; n += blockDim.x) acc += V[(size_t)i * nt + n - 1] * V[(size_t)j * nt + n];
@@ -199,8 +232,12 @@ __global__ void k_shift_gram(int nt, int r, const double* V, double* T, double* 
 // without a nonzero pivot candidate belongs to a vanished basis vector: its
 // row becomes the identity row, so that component stays zero), then the
 // recurrence z_n = Ahat^{-1} (z_{n-1} + g_n), one warp per row and step.
+// (solve c = blockIdx.x: its Ahat, Gt, Z at strides r r, nt r, nt r)
 __global__ void __launch_bounds__(1024) k_als_time(int r, int nt, const double* Ahat, const double* Gt, double* Z) {
   extern __shared__ double sm[];
+  Ahat += (size_t)blockIdx.x * r * r;
+  Gt += (size_t)blockIdx.x * nt * r;
+  Z += (size_t)blockIdx.x * nt * r;
   double* M = sm;                       // r x 2r, row-major: [Ahat | I] -> [I | Ahat^{-1}]
   double* u = M + (size_t)r * 2 * r;    // r: z_{n-1} + g_n
   __shared__ int s_piv;
@@ -342,9 +379,17 @@ __global__ void k_factor_row(int nx, int r, const double* W, const double* V, in
 // with w over this CTA's contiguous range of rows: part[blk * m + k]. Many
 // CTAs over long vectors (n = nx r), eight vectors per pass over the range.
 constexpr int kDotRows = 2048;
-__global__ void __launch_bounds__(256) k_mdot(size_t n, int m, const double* V, const double* w, size_t rows,
-                                              double* part) {
+// (solve c = blockIdx.y: vectors V + k ldv + c n, w + c n; partials at
+// part + c gridDim.x m)
+__global__ void __launch_bounds__(256) k_mdot(size_t n, int m, const double* V, size_t ldv, const double* w,
+                                              size_t rows, double* part) {
   __shared__ double red[8][8];
+  {
+    const size_t c = blockIdx.y;
+    V += c * n;
+    w += c * n;
+    part += c * gridDim.x * (size_t)m;
+  }
   const size_t i0 = (size_t)blockIdx.x * rows;
   const size_t i1 = min(n, i0 + rows);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -357,7 +402,7 @@ __global__ void __launch_bounds__(256) k_mdot(size_t n, int m, const double* V, 
       const double wi = w[i];
 #pragma unroll
       for (int q = 0; q < 8; ++q)
-        if (q < kn) acc[q] += V[(size_t)(k0 + q) * n + i] * wi;
+        if (q < kn) acc[q] += V[(size_t)(k0 + q) * ldv + i] * wi;
     }
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -379,26 +424,34 @@ __global__ void __launch_bounds__(256) k_mdot(size_t n, int m, const double* V, 
 // n entries, coefficients on the device): the Gram-Schmidt update of GMRES
 // and its final combination, streaming the basis once with many loads in
 // flight per thread.
-__global__ void __launch_bounds__(256) k_mupdate(size_t n, int m, const double* V, const double* h, double alpha,
-                                                 double* w) {
+// (solve c = blockIdx.y: V + k ldv + c n, h + c hs, w + c n)
+__global__ void __launch_bounds__(256) k_mupdate(size_t n, int m, const double* V, size_t ldv, const double* h,
+                                                 size_t hs, double alpha, double* w) {
   __shared__ double sh[64];
-  if (threadIdx.x < m && threadIdx.x < 64) sh[threadIdx.x] = h[threadIdx.x];
+  const size_t c = blockIdx.y;
+  if (threadIdx.x < m && threadIdx.x < 64) sh[threadIdx.x] = h[c * hs + threadIdx.x];
   __syncthreads();
+  V += c * n;
+  w += c * n;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     double acc = 0.0;
 #pragma unroll 8
-    for (int k = 0; k < m; ++k) acc += sh[k] * V[(size_t)k * n + i];
+    for (int k = 0; k < m; ++k) acc += sh[k] * V[(size_t)k * ldv + i];
     w[i] += alpha * acc;
   }
 }
 
-// out[k] = beta out[k] + sum_b part[b * m + k] (fixed order); one warp per k.
-__global__ void k_mdot_sum(int nb, int m, const double* part, double* out, double beta) {
+// out_c[k] = beta out_c[k] + sum_b part_c[b * m + k] (fixed order); one warp
+// per k; solve c = blockIdx.y (partials at c nblk m, output at out + c os)
+__global__ void k_mdot_sum(int nblk, int m, const double* part, double* out, size_t os, double beta) {
   const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (k >= m) return;
+  const size_t c = blockIdx.y;
+  part += c * nblk * (size_t)m;
+  out += c * os;
   double t = 0.0;
-  for (int b = lane; b < nb; b += 32) t += part[(size_t)b * m + k];
+  for (int b = lane; b < nblk; b += 32) t += part[(size_t)b * m + k];
   for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
   if (lane == 0) out[k] = (beta == 0.0 ? 0.0 : beta * out[k]) + t;
 }
@@ -527,6 +580,14 @@ __global__ void __launch_bounds__(256) k_chol_inv_rel(int r, const double* G, do
   }
 }
 
+// out = trace(G) of an r x r matrix (column-major); one thread
+__global__ void k_trace(int r, const double* G, double* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double t = 0.0;
+  for (int i = 0; i < r; ++i) t += G[(size_t)i * r + i];
+  *out = t;
+}
+
 // out = sum_ij Ga[i, j] Gb[i, j]; one CTA.
 __global__ void k_frob(int n, const double* Ga, const double* Gb, double* out) {
   __shared__ double red[32];
@@ -544,39 +605,49 @@ __global__ void k_frob(int n, const double* Ga, const double* Gb, double* out) {
 
 // ---------------------------------------------------------------------------
 // host side
+//
+// A call solves nb independent systems (same operator, own sources and
+// starts) at once: every per-solve array holds nb copies at a fixed stride,
+// the GMRES of the space steps runs with a Hessenberg matrix per solve, and
+// one preconditioner launch serves the r blocks of every solve.
 
 unsigned grid1(size_t n) { return (unsigned)((n + 255) / 256); }
 
-// Y = A X - X Tm for the r columns of X (Tm NULL: Y = A X); A^T if transpose.
-lrp_status kron_apply(lrp_problem* P, int r, const double* X, const double* Tm, int transpose, double* Y) {
+// Y = A X - X T for the ncol = nb r columns of X (solve c with its own
+// r x r matrix Tm + c r r), or Y = A X (Tm NULL); A^T if transpose.
+lrp_status kron_apply(lrp_problem* P, int r, int ncol, const double* X, const double* Tm, int transpose, double* Y) {
   const OpLevel& l0 = P->step.lv[0];
-  dim3 g(grid1(P->nx), r);
+  dim3 g(grid1(P->nx), ncol);
   cudaStream_t s = P->stream;
   note_launch();
   if (P->step.conv) {
     if (P->dim == 2)
-      k_kron_apply<2, false, true><<<g, 256, 0, s>>>(l0, r, X, Tm, transpose, Y);
+      k_kron_apply<2, false, true><<<g, 256, 0, s>>>(l0, r, ncol, X, Tm, transpose, Y);
     else
-      k_kron_apply<3, false, true><<<g, 256, 0, s>>>(l0, r, X, Tm, transpose, Y);
+      k_kron_apply<3, false, true><<<g, 256, 0, s>>>(l0, r, ncol, X, Tm, transpose, Y);
   } else if (P->step.has_kappa) {
     if (P->dim == 2)
-      k_kron_apply<2, true, false><<<g, 256, 0, s>>>(l0, r, X, Tm, transpose, Y);
+      k_kron_apply<2, true, false><<<g, 256, 0, s>>>(l0, r, ncol, X, Tm, transpose, Y);
     else
-      k_kron_apply<3, true, false><<<g, 256, 0, s>>>(l0, r, X, Tm, transpose, Y);
+      k_kron_apply<3, true, false><<<g, 256, 0, s>>>(l0, r, ncol, X, Tm, transpose, Y);
   } else {
     if (P->dim == 2)
-      k_kron_apply<2, false, false><<<g, 256, 0, s>>>(l0, r, X, Tm, transpose, Y);
+      k_kron_apply<2, false, false><<<g, 256, 0, s>>>(l0, r, ncol, X, Tm, transpose, Y);
     else
-      k_kron_apply<3, false, false><<<g, 256, 0, s>>>(l0, r, X, Tm, transpose, Y);
+      k_kron_apply<3, false, false><<<g, 256, 0, s>>>(l0, r, ncol, X, Tm, transpose, Y);
   }
   CKL(cudaGetLastError());
   return LRP_OK;
 }
 
-// Work arrays of one alternating solve (r columns, source rank rf).
+// slots of AlsWS::scal, nb entries each
+enum { S_G = 0, S_R0, S_INV0, S_W, S_INV, S_RES, S_F, S_RA, S_RB, S_NSLOT };
+
+// Work arrays of nb alternating solves (r columns, source rank rf).
 struct AlsWS {
-  int nx = 0, nt = 0, r = 0, rf = 0;
-  Buf<double> V, W, Q, G, Tm, inv_s, Ahat, Gt, Z, Rz, M1, AQ, part, gs, scal;
+  int nx = 0, nt = 0, r = 0, rf = 0, nb = 0, nb_cap = 0;
+  size_t n1 = 0;  // nx r: one solve's space factor
+  Buf<double> V, W, Q, G, Tm, inv_s, Ahat, Gt, Z, M1, AQ, part, scal;
   Buf<double> Vb, Zb, H, cs, sn, g, y, hv;  // GMRES
   Buf<double> Xc, Yc, Gx, Gy;                 // residual
   Buf<double> Gq, Rq;                         // Cholesky QR: Gram matrix and inverse factor
@@ -588,54 +659,76 @@ struct AlsWS {
   size_t part_cap = 0;
   size_t lev_nodes = 0;  // sum of the level sizes
   std::vector<double> inv_s_host;
-  cudaError_t init(lrp_problem* P, int r_, int rf_) {
+  int rc() const { return r + std::max(rf, 1); }
+  size_t hs() const { return (size_t)(kGmresMax + 1) * kGmresMax; }
+  cudaError_t init(lrp_problem* P, int r_, int rf_, int nb_) {
     nx = P->nx;
     nt = P->nt;
     r = r_;
     rf = rf_;
-    const size_t blk = (size_t)nx * r;
-    const int rc = r + std::max(rf, 1);
-    part_cap = (size_t)128 * std::max(rc, kGmresMax + 1) * 16;  // >= 1024 (kGmresMax + 1) for mdot
-    cudaError_t e = V.alloc((size_t)nt * r);
-    if (e == cudaSuccess) e = W.alloc(blk);
-    if (e == cudaSuccess) e = Q.alloc(blk);
-    if (e == cudaSuccess) e = G.alloc(blk);
-    if (e == cudaSuccess) e = Tm.alloc((size_t)r * r);
-    if (e == cudaSuccess) e = inv_s.alloc(r);
-    if (e == cudaSuccess) e = Ahat.alloc((size_t)r * r);
-    if (e == cudaSuccess) e = Gt.alloc((size_t)nt * r);
-    if (e == cudaSuccess) e = Z.alloc((size_t)nt * r);
-    if (e == cudaSuccess) e = Rz.alloc((size_t)r * r);
-    if (e == cudaSuccess) e = M1.alloc((size_t)rc * rc);
-    if (e == cudaSuccess) e = AQ.alloc(blk);
+    nb = nb_cap = nb_;
+    n1 = (size_t)nx * r;
+    const size_t B = (size_t)nb_cap;
+    const int c2 = rc();
+    part_cap = B * 1024 * (kGmresMax + 1);
+    cudaError_t e = V.alloc(B * nt * r);
+    if (e == cudaSuccess) e = W.alloc(B * n1);
+    if (e == cudaSuccess) e = Q.alloc(B * n1);
+    if (e == cudaSuccess) e = G.alloc(B * n1);
+    if (e == cudaSuccess) e = Tm.alloc(B * r * r);
+    if (e == cudaSuccess) e = inv_s.alloc(B * r);
+    if (e == cudaSuccess) e = Ahat.alloc(B * r * r);
+    if (e == cudaSuccess) e = Gt.alloc(B * nt * r);
+    if (e == cudaSuccess) e = Z.alloc(B * nt * r);
+    if (e == cudaSuccess) e = M1.alloc(B * c2 * c2);
+    if (e == cudaSuccess) e = AQ.alloc(B * n1);
     if (e == cudaSuccess) e = part.alloc(part_cap);
-    if (e == cudaSuccess) e = gs.alloc(block_gs_scratch_doubles());
-    if (e == cudaSuccess) e = scal.alloc(8);
-    if (e == cudaSuccess) e = Vb.alloc(blk * (kGmresMax + 1));
-    if (e == cudaSuccess) e = Zb.alloc(blk * kGmresMax);
-    if (e == cudaSuccess) e = H.alloc((size_t)(kGmresMax + 1) * kGmresMax);
-    if (e == cudaSuccess) e = cs.alloc(kGmresMax);
-    if (e == cudaSuccess) e = sn.alloc(kGmresMax);
-    if (e == cudaSuccess) e = g.alloc(kGmresMax + 1);
-    if (e == cudaSuccess) e = y.alloc(kGmresMax);
-    if (e == cudaSuccess) e = hv.alloc(kGmresMax + 1);
-    if (e == cudaSuccess) e = Xc.alloc((size_t)nx * rc);
-    if (e == cudaSuccess) e = Yc.alloc((size_t)nt * rc);
-    if (e == cudaSuccess) e = Gx.alloc((size_t)rc * rc);
-    if (e == cudaSuccess) e = Gy.alloc((size_t)rc * rc);
+    if (e == cudaSuccess) e = scal.alloc(B * S_NSLOT);
+    if (e == cudaSuccess) e = Vb.alloc(B * n1 * (kGmresMax + 1));
+    if (e == cudaSuccess) e = Zb.alloc(B * n1 * kGmresMax);
+    if (e == cudaSuccess) e = H.alloc(B * hs());
+    if (e == cudaSuccess) e = cs.alloc(B * kGmresMax);
+    if (e == cudaSuccess) e = sn.alloc(B * kGmresMax);
+    if (e == cudaSuccess) e = g.alloc(B * (kGmresMax + 1));
+    if (e == cudaSuccess) e = y.alloc(B * kGmresMax);
+    if (e == cudaSuccess) e = hv.alloc(B * (kGmresMax + 1));
+    if (e == cudaSuccess) e = Xc.alloc(B * nx * c2);
+    if (e == cudaSuccess) e = Yc.alloc(B * nt * c2);
+    if (e == cudaSuccess) e = Gx.alloc((size_t)c2 * c2);
+    if (e == cudaSuccess) e = Gy.alloc((size_t)c2 * c2);
     if (e == cudaSuccess) e = stat.alloc(1);
-    if (e == cudaSuccess) e = ops.alloc(r);
+    if (e == cudaSuccess) e = ops.alloc(B * r);
     if (e == cudaSuccess) e = Gq.alloc((size_t)r * r);
     if (e == cudaSuccess) e = Rq.alloc((size_t)r * r);
     tn_cap = (size_t)512 * kTnMaxEntries;
     if (e == cudaSuccess) e = tn.alloc(tn_cap);
     lev_nodes = 0;
     for (int l = 0; l < P->L; ++l) lev_nodes += (size_t)P->step.lv[l].N;
-    if (e == cudaSuccess && P->step.has_kappa) e = dinv.alloc(lev_nodes * r * 3 / 2 + r * 2 * P->L);
-    inv_s_host.assign(r, 1.0);
+    if (e == cudaSuccess && P->step.has_kappa) e = dinv.alloc(lev_nodes * B * r * 3 / 2 + B * r * 2 * P->L);
+    inv_s_host.assign(B * r, 1.0);
     return e;
   }
+  // per-solve views
+  double* Vc(int c) const { return V.p + (size_t)c * nt * r; }
+  double* Wc(int c) const { return W.p + (size_t)c * n1; }
+  double* Qc(int c) const { return Q.p + (size_t)c * n1; }
+  double* Gc(int c) const { return G.p + (size_t)c * n1; }
+  double* AQc(int c) const { return AQ.p + (size_t)c * n1; }
+  double* Ahatc(int c) const { return Ahat.p + (size_t)c * r * r; }
+  double* Gtc(int c) const { return Gt.p + (size_t)c * nt * r; }
+  double* Zc(int c) const { return Z.p + (size_t)c * nt * r; }
+  double* M1c(int c) const { return M1.p + (size_t)c * rc() * rc(); }
+  double* Xcc(int c) const { return Xc.p + (size_t)c * nx * rc(); }
+  double* Ycc(int c) const { return Yc.p + (size_t)c * nt * rc(); }
+  double* slot(int k) const { return scal.p + (size_t)k * nb_cap; }
 };
+
+// Solves per call of the product: as many as fit a budget of ~6 GB for the
+// Krylov bases of one AlsWS, at most 32.
+int als_batch_cap(const lrp_problem* P, int r) {
+  const double per = 8.0 * (2 * kGmresMax + 1) * (double)P->nx * r;
+  return (int)std::max(1.0, std::min(32.0, std::floor(6e9 / per)));
+}
 
 // Drops the per-column operators from the problem handle when a solve ends
 // (their device copy belongs to the solve's work arrays).
@@ -670,17 +763,19 @@ std::string noconv_message(bool pcg, double gmres_worst) {
 }
 
 // The per-column operators A - T_jj I = (1 - T_jj)(I + (tau / (1 - T_jj)) L)
-// of the preconditioner, as scaled copies of the time-step operator.
+// of the preconditioner, as scaled copies of the time-step operator (nb r
+// of them: column j of solve c at c r + j).
 lrp_status build_shift_ops(lrp_problem* P, AlsWS& w) {
   cudaStream_t s = P->stream;
-  CKL(cudaMemcpyAsync(w.inv_s_host.data(), w.inv_s.p, sizeof(double) * w.r, cudaMemcpyDeviceToHost, s));
+  const int ncol = w.nb * w.r;
+  CKL(cudaMemcpyAsync(w.inv_s_host.data(), w.inv_s.p, sizeof(double) * ncol, cudaMemcpyDeviceToHost, s));
   CKL(cudaStreamSynchronize(s));
-  P->shift_ops.assign(w.r, P->step);
+  P->shift_ops.assign(ncol, P->step);
   P->shift_ops_dev = w.ops.p;
   size_t off = 0;
   double* dd = w.dinv.p;
-  float* df = w.dinv.p ? (float*)(w.dinv.p + w.lev_nodes * w.r) : nullptr;
-  for (int j = 0; j < w.r; ++j) {
+  float* df = w.dinv.p ? (float*)(w.dinv.p + w.lev_nodes * (size_t)w.nb_cap * w.r) : nullptr;
+  for (int j = 0; j < ncol; ++j) {
     const double is = w.inv_s_host[j];  // 1 / (1 - T_jj)
     Op& op = P->shift_ops[j];
     for (int l = 0; l < P->L; ++l) {
@@ -706,8 +801,8 @@ lrp_status build_shift_ops(lrp_problem* P, AlsWS& w) {
   return LRP_OK;
 }
 
-// z (nx x r) = blockdiag(A - T_jj I)^{-1} v: one sweep launch, one solve per
-// column with its own operator, then the 1/(1 - T_jj) scaling.
+// z = blockdiag(A - T_jj I)^{-1} v for the nb r columns: one sweep launch,
+// one solve per column with its own operator, then the 1/(1 - T_jj) scaling.
 // Each solve is als_prec_its (0 -> kPrecondIts) CG iterations from zero, or,
 // with als_prec_rtol > 0, a solve to that relative residual (at least the
 // problem's own). Flexible GMRES accepts an inexact, even iteration-dependent
@@ -720,6 +815,7 @@ lrp_status build_shift_ops(lrp_problem* P, AlsWS& w) {
 lrp_status precond(lrp_problem* P, AlsWS& w, const double* v, double* z, AlsCounters& c) {
   lrp_apply_stats st;
   std::memset(&st, 0, sizeof(st));
+  const int ncol = w.nb * w.r;
   const SolveCfg saved = P->cfg;
   if (P->desc.als_prec_rtol > 0.0) {
     P->cfg.rtol = std::max(saved.rtol, P->desc.als_prec_rtol);
@@ -729,7 +825,7 @@ lrp_status precond(lrp_problem* P, AlsWS& w, const double* v, double* z, AlsCoun
     P->cfg.maxit = P->desc.als_prec_its > 0 ? P->desc.als_prec_its : kPrecondIts;
     P->cfg.maxref = 1;
   }
-  lrp_status res = run_sweep_ex(P, ST_LOAD_X | ST_SHIFTED | ST_STORE_Y, w.r, v, w.nx, z, w.nx, nullptr, 0, nullptr,
+  lrp_status res = run_sweep_ex(P, ST_LOAD_X | ST_SHIFTED | ST_STORE_Y, ncol, v, w.nx, z, w.nx, nullptr, 0, nullptr,
                                 0, &st, 0, 0, nullptr, 0);
   P->cfg = saved;
   if (res == LRP_ENOCONV)
@@ -738,26 +834,39 @@ lrp_status precond(lrp_problem* P, AlsWS& w, const double* v, double* z, AlsCoun
     return res;
   c.precond_solves += st.n_solves;
   note_launch();
-  k_col_scale<<<grid1((size_t)w.nx * w.r), 256, 0, P->stream>>>((size_t)w.nx, w.r, w.inv_s.p, z);
+  k_col_scale<<<grid1((size_t)w.nx * ncol), 256, 0, P->stream>>>((size_t)w.nx, ncol, w.inv_s.p, z);
   CKL(cudaGetLastError());
   return LRP_OK;
 }
 
-// out[0:m] = beta out + V^T x for m vectors of n entries (V: ld n), over
-// many CTAs (k_mdot) and a fixed-order sum of their partials.
-cudaError_t mdot(cudaStream_t s, AlsWS& w, size_t n, int m, const double* V, const double* x, double* out,
-                 double beta) {
+// For every solve c < w.nb: out[c os + k] = beta out + <V_k, x> over n
+// entries, V_k = V + k ldv + c n, x = X + c n; many CTAs per solve
+// (k_mdot) and a fixed-order sum of their partials.
+cudaError_t mdot(cudaStream_t s, AlsWS& w, size_t n, int m, const double* V, size_t ldv, const double* X,
+                 double* out, size_t os, double beta) {
   size_t rows = kDotRows;
-  size_t nb = (n + rows - 1) / rows;
-  const size_t cap = std::min<size_t>(1024, w.part_cap / (size_t)std::max(m, 1));
-  if (nb > cap) {
+  size_t nblk = (n + rows - 1) / rows;
+  const size_t cap = std::min<size_t>(1024, w.part_cap / ((size_t)std::max(m, 1) * w.nb));
+  if (nblk > cap) {
     rows = (n + cap - 1) / cap;
-    nb = (n + rows - 1) / rows;
+    nblk = (n + rows - 1) / rows;
   }
   note_launch();
-  k_mdot<<<(unsigned)nb, 256, 0, s>>>(n, m, V, x, rows, w.part.p);
+  k_mdot<<<dim3((unsigned)nblk, w.nb), 256, 0, s>>>(n, m, V, ldv, X, rows, w.part.p);
   note_launch();
-  k_mdot_sum<<<(m + 7) / 8, 256, 0, s>>>((int)nb, m, w.part.p, out, beta);
+  k_mdot_sum<<<dim3((m + 7) / 8, w.nb), 256, 0, s>>>((int)nblk, m, w.part.p, out, os, beta);
+  return cudaGetLastError();
+}
+
+// For every solve c < w.nb: x_c += alpha sum_k h[c hs + k] V_k (V_k = V + k
+// ldv + c n; x_c = X + c n)
+cudaError_t mupdate(cudaStream_t s, AlsWS& w, size_t n, int m, const double* V, size_t ldv, const double* h,
+                    size_t hs, double alpha, double* X) {
+  if (m <= 0) return cudaSuccess;
+  const size_t per = std::max<size_t>(1, (1216 + w.nb - 1) / w.nb);
+  const unsigned grid = (unsigned)std::min<size_t>((n + 255) / 256, per);
+  note_launch();
+  k_mupdate<<<dim3(grid, w.nb), 256, 0, s>>>(n, m, V, ldv, h, hs, alpha, X);
   return cudaGetLastError();
 }
 
@@ -817,110 +926,113 @@ cudaError_t orth_cholqr(cudaStream_t s, AlsWS& w, int rows, int r, double* A, do
   return cudaMemcpyAsync(A, src, (size_t)rows * r * sizeof(double), cudaMemcpyDeviceToDevice, s);
 }
 
-// w += alpha V h (V: m vectors of n entries, ld n; h: m device coefficients)
-cudaError_t mupdate(cudaStream_t s, size_t n, int m, const double* V, const double* h, double alpha, double* w) {
-  if (m <= 0) return cudaSuccess;
-  const unsigned grid = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 8);
-  note_launch();
-  k_mupdate<<<grid, 256, 0, s>>>(n, m, V, h, alpha, w);
-  return cudaGetLastError();
-}
-
-// <a, b> over n entries into dst (device)
-cudaError_t dot_into(cudaStream_t s, AlsWS& w, size_t n, const double* a, const double* b, double* dst, double beta) {
-  return mdot(s, w, n, 1, a, b, dst, beta);
-}
-
-// Space step: A W - W T = G by flexible GMRES, right-preconditioned with
-// blockdiag(A - T_jj I), from the start in w.W (zero if !warm), to a
-// relative residual gtol ||G||.
+// Space step of every solve: A W_c - W_c T_c = G_c by flexible GMRES,
+// right-preconditioned with blockdiag(A - T_jj I), from the start in W (zero
+// if !warm), each to a relative residual gtol ||G_c||. The solves share the
+// iterations (one preconditioner launch and one kernel per step for all of
+// them) and have their own Hessenberg matrices, rotations and residuals; the
+// iteration ends when every solve has reached its tolerance.
 lrp_status space_step(lrp_problem* P, AlsWS& w, int transpose, bool warm, double gtol, AlsCounters& c) {
   cudaStream_t s = P->stream;
-  const size_t n = (size_t)w.nx * w.r;
-  const int ldh = kGmresMax + 1;
+  const int nb = w.nb, r = w.r, kmax = kGmresMax;
+  const size_t n1 = w.n1, N = (size_t)nb * n1;
+  const int ldh = kmax + 1;
+  const size_t hs = w.hs();
   CKS(build_shift_ops(P, w));
   P->shift_transpose = transpose;
-  double hres[2];
-  // ||G||
-  CKL(dot_into(s, w, n, w.G.p, w.G.p, w.scal.p + 1, 0.0));
-  if (!warm) CKL(cudaMemsetAsync(w.W.p, 0, n * sizeof(double), s));
+  std::vector<double> h(2 * (size_t)nb), rres(nb), target(nb), gnorm(nb);
+  // ||G_c||^2
+  CKL(mdot(s, w, n1, 1, w.G.p, n1, w.G.p, w.slot(S_G), 1, 0.0));
+  if (!warm) CKL(cudaMemsetAsync(w.W.p, 0, N * sizeof(double), s));
   int iters = 0;
   for (int cyc = 0; cyc < kGmresCycles; ++cyc) {
     // r0 = G - K(W) into Vb[0]
     double* v0 = w.Vb.p;
     if (warm || cyc > 0) {
-      CKS(kron_apply(P, w.r, w.W.p, w.Tm.p, transpose, v0));
-      CKL(axpby(s, n, 1.0, w.G.p, -1.0, v0));
+      CKS(kron_apply(P, r, nb * r, w.W.p, w.Tm.p, transpose, v0));
+      CKL(axpby(s, N, 1.0, w.G.p, -1.0, v0));
     } else {
-      CKL(cudaMemcpyAsync(v0, w.G.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      CKL(cudaMemcpyAsync(v0, w.G.p, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
     }
-    CKL(cudaMemsetAsync(w.H.p, 0, (size_t)ldh * kGmresMax * sizeof(double), s));
-    CKL(cudaMemsetAsync(w.g.p, 0, (kGmresMax + 1) * sizeof(double), s));
-    CKL(dot_into(s, w, n, v0, v0, w.scal.p + 2, 0.0));
+    CKL(cudaMemsetAsync(w.H.p, 0, (size_t)nb * hs * sizeof(double), s));
+    CKL(cudaMemsetAsync(w.g.p, 0, (size_t)nb * (kmax + 1) * sizeof(double), s));
+    CKL(mdot(s, w, n1, 1, v0, n1, v0, w.slot(S_R0), 1, 0.0));
     note_launch();
-    k_norm_entry<<<1, 1, 0, s>>>(w.scal.p + 2, w.g.p, w.scal.p + 3);
+    k_norm_entry<<<nb, 1, 0, s>>>(w.slot(S_R0), w.g.p, (size_t)(kmax + 1), w.slot(S_INV0));
     CKL(cudaGetLastError());
     note_launch();
-    k_scale_by<<<grid1(n), 256, 0, s>>>(n, w.scal.p + 3, v0, v0);
+    k_scale_by<<<dim3(grid1(n1), nb), 256, 0, s>>>(n1, w.slot(S_INV0), v0, v0);
     CKL(cudaGetLastError());
-    CKL(cudaMemcpyAsync(hres, w.scal.p + 1, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CKL(cudaMemcpyAsync(h.data(), w.slot(S_G), nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CKL(cudaMemcpyAsync(h.data() + nb, w.slot(S_R0), nb * sizeof(double), cudaMemcpyDeviceToHost, s));
     CKL(cudaStreamSynchronize(s));
-    const double gnorm = std::sqrt(std::max(hres[0], 0.0));
-    const double target = gtol * gnorm;
-    double rnorm = std::sqrt(std::max(hres[1], 0.0));
-    if (!(gnorm > 0.0)) {
-      CKL(cudaMemsetAsync(w.W.p, 0, n * sizeof(double), s));
-      break;
-    }
-    if (!std::isfinite(rnorm)) {
-      set_error("alternating solve: non-finite residual in the space step");
-      return LRP_ENONFINITE;
-    }
-    if (rnorm <= target) break;
-    int m = 0;
-    for (int j = 0; j < kGmresMax; ++j) {
-      double* vj = w.Vb.p + (size_t)j * n;
-      double* zj = w.Zb.p + (size_t)j * n;
-      double* wv = w.Vb.p + (size_t)(j + 1) * n;
-      CKS(precond(P, w, vj, zj, c));
-      CKS(kron_apply(P, w.r, zj, w.Tm.p, transpose, wv));
-      // classical Gram-Schmidt twice against v_0..v_j (vectors of n entries)
-      double* hcol = w.H.p + (size_t)j * ldh;
-      for (int pass = 0; pass < 2; ++pass) {
-        CKL(mdot(s, w, n, j + 1, w.Vb.p, wv, w.hv.p, 0.0));
-        CKL(mupdate(s, n, j + 1, w.Vb.p, w.hv.p, -1.0, wv));
-        CKL(axpby(s, (size_t)(j + 1), 1.0, w.hv.p, 1.0, hcol));
-      }
-      CKL(dot_into(s, w, n, wv, wv, w.scal.p + 4, 0.0));
-      note_launch();
-      k_norm_entry<<<1, 1, 0, s>>>(w.scal.p + 4, hcol + j + 1, w.scal.p + 5);
-      CKL(cudaGetLastError());
-      note_launch();
-      k_scale_by<<<grid1(n), 256, 0, s>>>(n, w.scal.p + 5, wv, wv);
-      CKL(cudaGetLastError());
-      note_launch();
-      k_givens<<<1, 1, 0, s>>>(j, w.H.p, ldh, w.cs.p, w.sn.p, w.g.p, w.scal.p + 6);
-      CKL(cudaGetLastError());
-      CKL(cudaMemcpyAsync(&rnorm, w.scal.p + 6, sizeof(double), cudaMemcpyDeviceToHost, s));
-      CKL(cudaStreamSynchronize(s));
-      m = j + 1;
-      ++iters;
-      if (!std::isfinite(rnorm)) {
+    bool all_done = true;
+    for (int i = 0; i < nb; ++i) {
+      gnorm[i] = std::sqrt(std::max(h[i], 0.0));
+      target[i] = gtol * gnorm[i];
+      rres[i] = std::sqrt(std::max(h[nb + i], 0.0));
+      if (!std::isfinite(rres[i])) {
         set_error("alternating solve: non-finite residual in the space step");
         return LRP_ENONFINITE;
       }
-      if (rnorm <= target) break;
+      if (!(gnorm[i] > 0.0)) {
+        // a zero right-hand side: the solution is zero
+        CKL(cudaMemsetAsync(w.Wc(i), 0, n1 * sizeof(double), s));
+        rres[i] = 0.0;
+      }
+      if (rres[i] > target[i]) all_done = false;
     }
-    // W += Z y
+    if (all_done) break;
+    int m = 0;
+    for (int j = 0; j < kmax; ++j) {
+      double* vj = w.Vb.p + (size_t)j * N;
+      double* zj = w.Zb.p + (size_t)j * N;
+      double* wv = w.Vb.p + (size_t)(j + 1) * N;
+      CKS(precond(P, w, vj, zj, c));
+      CKS(kron_apply(P, r, nb * r, zj, w.Tm.p, transpose, wv));
+      // classical Gram-Schmidt twice against v_0..v_j of each solve
+      for (int pass = 0; pass < 2; ++pass) {
+        CKL(mdot(s, w, n1, j + 1, w.Vb.p, N, wv, w.hv.p, (size_t)(kmax + 1), 0.0));
+        CKL(mupdate(s, w, n1, j + 1, w.Vb.p, N, w.hv.p, (size_t)(kmax + 1), -1.0, wv));
+        note_launch();
+        k_hadd<<<nb, 64, 0, s>>>(j + 1, w.hv.p, (size_t)(kmax + 1), w.H.p + (size_t)j * ldh, hs);
+        CKL(cudaGetLastError());
+      }
+      CKL(mdot(s, w, n1, 1, wv, n1, wv, w.slot(S_W), 1, 0.0));
+      note_launch();
+      k_norm_entry<<<nb, 1, 0, s>>>(w.slot(S_W), w.H.p + (size_t)j * ldh + j + 1, hs, w.slot(S_INV));
+      CKL(cudaGetLastError());
+      note_launch();
+      k_scale_by<<<dim3(grid1(n1), nb), 256, 0, s>>>(n1, w.slot(S_INV), wv, wv);
+      CKL(cudaGetLastError());
+      note_launch();
+      k_givens<<<nb, 1, 0, s>>>(j, w.H.p, ldh, hs, w.cs.p, w.sn.p, w.g.p, kmax, w.slot(S_RES));
+      CKL(cudaGetLastError());
+      CKL(cudaMemcpyAsync(rres.data(), w.slot(S_RES), nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CKL(cudaStreamSynchronize(s));
+      m = j + 1;
+      ++iters;
+      all_done = true;
+      for (int i = 0; i < nb; ++i) {
+        if (!std::isfinite(rres[i])) {
+          set_error("alternating solve: non-finite residual in the space step");
+          return LRP_ENONFINITE;
+        }
+        if (gnorm[i] > 0.0 && rres[i] > target[i]) all_done = false;
+      }
+      if (all_done) break;
+    }
+    // W_c += Z_c y_c
     note_launch();
-    k_backsolve<<<1, 1, 0, s>>>(m, w.H.p, ldh, w.g.p, w.y.p);
+    k_backsolve<<<nb, 1, 0, s>>>(m, w.H.p, ldh, hs, w.g.p, w.y.p, kmax);
     CKL(cudaGetLastError());
-    CKL(mupdate(s, n, m, w.Zb.p, w.y.p, 1.0, w.W.p));
+    CKL(mupdate(s, w, n1, m, w.Zb.p, N, w.y.p, (size_t)kmax, 1.0, w.W.p));
     warm = true;
-    if (rnorm <= target) break;
+    if (all_done) break;
     if (cyc == kGmresCycles - 1) {
       c.noconv = true;
-      c.gmres_worst = std::max(c.gmres_worst, rnorm / gnorm);
+      for (int i = 0; i < nb; ++i)
+        if (gnorm[i] > 0.0) c.gmres_worst = std::max(c.gmres_worst, rres[i] / gnorm[i]);
     }
   }
   c.gmres_iters += iters;
@@ -928,47 +1040,58 @@ lrp_status space_step(lrp_problem* P, AlsWS& w, int transpose, bool warm, double
   return LRP_OK;
 }
 
-// One alternating solve of A Y - Y S^T = Wf Vf^T (A^T with transpose) with
-// the factors Wf (nx x rf), Vf (nt x rf) and the start w.V (nt x r), all
-// device arrays with leading dimensions nx / nt. Runs `sweeps` sweeps (or
-// until the residual is <= tol); Y ~ w.W w.V^T on return, res[s] the
-// relative residual after sweep s. *done_sweeps: sweeps taken.
+// nb alternating solves of A Y_c - Y_c S^T = Wf_c Vf_c^T (A^T with transpose)
+// with the factors Wf_c (nx x rf, at Wf + c nx rf), Vf_c (nt x rf, at Vf + c
+// nt rf) and the starts in w.V (nt x r each). Runs `sweeps` sweeps (or until
+// every residual is <= tol); Y_c ~ W_c V_c^T on return, res[c sweeps + s] the
+// relative residual of solve c after sweep s. *done_sweeps: sweeps taken.
 lrp_status als_run(lrp_problem* P, AlsWS& w, int transpose, const double* Wf, const double* Vf, int sweeps,
                    double tol, double* res, int* done_sweeps, AlsCounters& c) {
   cudaStream_t s = P->stream;
-  const int nx = w.nx, nt = w.nt, r = w.r, rf = w.rf;
+  const int nx = w.nx, nt = w.nt, r = w.r, rf = w.rf, nb = w.nb;
   const double gtol = std::max(10.0 * P->cfg.rtol, 1e-12);
   const int rc = r + rf;
-  // ||F||_F^2 = sum (Wf^T Wf) .* (Vf^T Vf)
-  double f2 = 0.0;
+  auto Wfc = [&](int i) { return Wf + (size_t)i * nx * rf; };
+  auto Vfc = [&](int i) { return Vf + (size_t)i * nt * rf; };
+  // ||F_c||_F^2 = sum (Wf^T Wf) .* (Vf^T Vf)
+  std::vector<double> f2(nb, 0.0);
   if (rf > 0) {
-    CKL(small_tn(s, w, nx, rf, rf, Wf, nx, Wf, nx, w.Gx.p, rf, 1.0, 0.0));
-    CKL(small_tn(s, w, nt, rf, rf, Vf, nt, Vf, nt, w.Gy.p, rf, 1.0, 0.0));
-    note_launch();
-    k_frob<<<1, 256, 0, s>>>(rf * rf, w.Gx.p, w.Gy.p, w.scal.p);
-    CKL(cudaGetLastError());
-    CKL(cudaMemcpyAsync(&f2, w.scal.p, sizeof(double), cudaMemcpyDeviceToHost, s));
-    CKL(cudaStreamSynchronize(s));
+    for (int i = 0; i < nb; ++i) {
+      CKL(small_tn(s, w, nx, rf, rf, Wfc(i), nx, Wfc(i), nx, w.Gx.p, rf, 1.0, 0.0));
+      CKL(small_tn(s, w, nt, rf, rf, Vfc(i), nt, Vfc(i), nt, w.Gy.p, rf, 1.0, 0.0));
+      note_launch();
+      k_frob<<<1, 256, 0, s>>>(rf * rf, w.Gx.p, w.Gy.p, w.slot(S_F) + i);
+      CKL(cudaGetLastError());
+    }
+    CKL(cudaMemcpyAsync(f2.data(), w.slot(S_F), nb * sizeof(double), cudaMemcpyDeviceToHost, s));
   }
-  // orthonormal start
-  CKL(orth_cholqr(s, w, nt, r, w.V.p, w.Gt.p));
+  // orthonormal starts
+  for (int i = 0; i < nb; ++i) CKL(orth_cholqr(s, w, nt, r, w.Vc(i), w.Gtc(i)));
+  CKL(cudaStreamSynchronize(s));
   *done_sweeps = 0;
-  if (!(f2 > 0.0)) {
-    CKL(cudaMemsetAsync(w.W.p, 0, (size_t)nx * r * sizeof(double), s));
+  bool any = false;
+  for (int i = 0; i < nb; ++i) any = any || f2[i] > 0.0;
+  if (!any) {
+    CKL(cudaMemsetAsync(w.W.p, 0, (size_t)nb * w.n1 * sizeof(double), s));
     if (res)
-      for (int k = 0; k < sweeps; ++k) res[k] = 0.0;
+      for (size_t k = 0; k < (size_t)nb * sweeps; ++k) res[k] = 0.0;
     CKL(cudaStreamSynchronize(s));
     return LRP_OK;
   }
+  const size_t smem_t = ((size_t)r * 2 * r + 2 * r) * sizeof(double);
+  CKL(cudaFuncSetAttribute(k_als_time, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t));
+  std::vector<double> rr(2 * (size_t)nb);
   for (int sw = 0; sw < sweeps; ++sw) {
     auto t0 = std::chrono::steady_clock::now();
     // ---- space step
     CKL(cudaMemsetAsync(w.stat.p, 0, sizeof(int), s));
     note_launch();
-    k_shift_gram<<<r * r, 256, 0, s>>>(nt, r, w.V.p, w.Tm.p, w.inv_s.p, w.stat.p);
+    k_shift_gram<<<dim3(r * r, nb), 256, 0, s>>>(nt, r, w.V.p, w.Tm.p, w.inv_s.p, w.stat.p);
     CKL(cudaGetLastError());
-    CKL(small_tn(s, w, nt, rf, r, Vf, nt, w.V.p, nt, w.M1.p, rf, 1.0, 0.0));
-    CKL(gemm_nn(s, nx, rf, r, 1.0, Wf, nx, w.M1.p, rf, 0.0, w.G.p, nx));
+    for (int i = 0; i < nb; ++i) {
+      CKL(small_tn(s, w, nt, rf, r, Vfc(i), nt, w.Vc(i), nt, w.M1c(i), rf, 1.0, 0.0));
+      CKL(gemm_nn(s, nx, rf, r, 1.0, Wfc(i), nx, w.M1c(i), rf, 0.0, w.Gc(i), nx));
+    }
     int hstat = 0;
     CKL(cudaMemcpyAsync(&hstat, w.stat.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     CKL(cudaStreamSynchronize(s));
@@ -980,23 +1103,25 @@ lrp_status als_run(lrp_problem* P, AlsWS& w, int transpose, const double* Wf, co
     auto t1 = std::chrono::steady_clock::now();
     c.ms_space += std::chrono::duration<double, std::milli>(t1 - t0).count();
     // ---- time step
-    CKL(cudaMemcpyAsync(w.Q.p, w.W.p, (size_t)nx * r * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    CKL(orth_cholqr(s, w, nx, r, w.Q.p, w.AQ.p));
-    CKS(kron_apply(P, r, w.Q.p, nullptr, transpose, w.AQ.p));
-    CKL(small_tn(s, w, nx, r, r, w.Q.p, nx, w.AQ.p, nx, w.Ahat.p, r, 1.0, 0.0));
-    // Gt (nt x r) = Vf (Wf^T Q)
-    CKL(small_tn(s, w, nx, rf, r, Wf, nx, w.Q.p, nx, w.M1.p, rf, 1.0, 0.0));
-    CKL(gemm_nn(s, nt, rf, r, 1.0, Vf, nt, w.M1.p, rf, 0.0, w.Gt.p, nt));
-    const size_t smem = ((size_t)r * 2 * r + 2 * r) * sizeof(double);
-    CKL(cudaFuncSetAttribute(k_als_time, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CKL(cudaMemcpyAsync(w.Q.p, w.W.p, (size_t)nb * w.n1 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    for (int i = 0; i < nb; ++i) CKL(orth_cholqr(s, w, nx, r, w.Qc(i), w.AQc(i)));
+    CKS(kron_apply(P, r, nb * r, w.Q.p, nullptr, transpose, w.AQ.p));
+    for (int i = 0; i < nb; ++i) {
+      CKL(small_tn(s, w, nx, r, r, w.Qc(i), nx, w.AQc(i), nx, w.Ahatc(i), r, 1.0, 0.0));
+      // Gt (nt x r) = Vf (Wf^T Q)
+      CKL(small_tn(s, w, nx, rf, r, Wfc(i), nx, w.Qc(i), nx, w.M1c(i), rf, 1.0, 0.0));
+      CKL(gemm_nn(s, nt, rf, r, 1.0, Vfc(i), nt, w.M1c(i), rf, 0.0, w.Gtc(i), nt));
+    }
     note_launch();
-    k_als_time<<<1, 1024, smem, s>>>(r, nt, w.Ahat.p, w.Gt.p, w.Z.p);
+    k_als_time<<<nb, 1024, smem_t, s>>>(r, nt, w.Ahat.p, w.Gt.p, w.Z.p);
     CKL(cudaGetLastError());
     // V, R_Z = qr(Z); W = Q R_Z^T = Q (Z^T V)
-    CKL(cudaMemcpyAsync(w.V.p, w.Z.p, (size_t)nt * r * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    CKL(orth_cholqr(s, w, nt, r, w.V.p, w.Gt.p));
-    CKL(small_tn(s, w, nt, r, r, w.Z.p, nt, w.V.p, nt, w.M1.p, r, 1.0, 0.0));
-    CKL(gemm_nn(s, nx, r, r, 1.0, w.Q.p, nx, w.M1.p, r, 0.0, w.W.p, nx));
+    CKL(cudaMemcpyAsync(w.V.p, w.Z.p, (size_t)nb * nt * r * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    for (int i = 0; i < nb; ++i) {
+      CKL(orth_cholqr(s, w, nt, r, w.Vc(i), w.Gtc(i)));
+      CKL(small_tn(s, w, nt, r, r, w.Zc(i), nt, w.Vc(i), nt, w.M1c(i), r, 1.0, 0.0));
+      CKL(gemm_nn(s, nx, r, r, 1.0, w.Qc(i), nx, w.M1c(i), r, 0.0, w.Wc(i), nx));
+    }
     // ---- residual. After the time step Q^T R = 0, so with X1 = (I - Q Q^T) A W,
     // X2 = (I - Q Q^T) Wf and the source's time factor split along V,
     // Vf = V C + Pv (C = V^T Vf, V^T Pv = 0):
@@ -1005,41 +1130,50 @@ lrp_status als_run(lrp_problem* P, AlsWS& w, int transpose, const double* Wf, co
     // (V orthonormal). The state and the source cancel in the vector
     // X1 - X2 C^T (rounding relative to the residual itself), not in a sum
     // of squares (which would floor the relative residual near 1e-8).
-    double* X1 = w.Xc.p;
-    double* X2 = w.Xc.p + (size_t)nx * r;
-    double* Pv = w.Yc.p;
-    CKS(kron_apply(P, r, w.W.p, nullptr, transpose, X1));
-    CKL(cudaMemcpyAsync(X2, Wf, (size_t)nx * rf * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    for (int pass = 0; pass < 2; ++pass) {
-      CKL(small_tn(s, w, nx, r, rc, w.Q.p, nx, w.Xc.p, nx, w.Gx.p, r, 1.0, 0.0));
-      CKL(gemm_nn(s, nx, r, rc, -1.0, w.Q.p, nx, w.Gx.p, r, 1.0, w.Xc.p, nx));
+    for (int i = 0; i < nb; ++i) {
+      double* X1 = w.Xcc(i);
+      double* X2 = X1 + (size_t)nx * r;
+      double* Pv = w.Ycc(i);
+      double* M1 = w.M1c(i);
+      CKS(kron_apply(P, r, r, w.Wc(i), nullptr, transpose, X1));
+      CKL(cudaMemcpyAsync(X2, Wfc(i), (size_t)nx * rf * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      for (int pass = 0; pass < 2; ++pass) {
+        CKL(small_tn(s, w, nx, r, rc, w.Qc(i), nx, X1, nx, w.Gx.p, r, 1.0, 0.0));
+        CKL(gemm_nn(s, nx, r, rc, -1.0, w.Qc(i), nx, w.Gx.p, r, 1.0, X1, nx));
+      }
+      CKL(small_tn(s, w, nt, rf, r, Vfc(i), nt, w.Vc(i), nt, M1, rf, 1.0, 0.0));
+      CKL(gemm_nn(s, nx, rf, r, -1.0, X2, nx, M1, rf, 1.0, X1, nx));
+      CKL(cudaMemcpyAsync(Pv, Vfc(i), (size_t)nt * rf * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      for (int pass = 0; pass < 2; ++pass) {
+        CKL(small_tn(s, w, nt, r, rf, w.Vc(i), nt, Pv, nt, w.Gx.p, r, 1.0, 0.0));
+        CKL(gemm_nn(s, nt, r, rf, -1.0, w.Vc(i), nt, w.Gx.p, r, 1.0, Pv, nt));
+      }
+      CKL(small_tn(s, w, nx, r, r, X1, nx, X1, nx, w.Gy.p, r, 1.0, 0.0));
+      note_launch();
+      k_trace<<<1, 64, 0, s>>>(r, w.Gy.p, w.slot(S_RA) + i);
+      CKL(cudaGetLastError());
+      CKL(small_tn(s, w, nx, rf, rf, X2, nx, X2, nx, w.Gx.p, rf, 1.0, 0.0));
+      CKL(small_tn(s, w, nt, rf, rf, Pv, nt, Pv, nt, w.Gy.p, rf, 1.0, 0.0));
+      note_launch();
+      k_frob<<<1, 256, 0, s>>>(rf * rf, w.Gx.p, w.Gy.p, w.slot(S_RB) + i);
+      CKL(cudaGetLastError());
     }
-    CKL(small_tn(s, w, nt, rf, r, Vf, nt, w.V.p, nt, w.M1.p, rf, 1.0, 0.0));
-    CKL(gemm_nn(s, nx, rf, r, -1.0, X2, nx, w.M1.p, rf, 1.0, X1, nx));
-    CKL(cudaMemcpyAsync(Pv, Vf, (size_t)nt * rf * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    for (int pass = 0; pass < 2; ++pass) {
-      CKL(small_tn(s, w, nt, r, rf, w.V.p, nt, Pv, nt, w.Gx.p, r, 1.0, 0.0));
-      CKL(gemm_nn(s, nt, r, rf, -1.0, w.V.p, nt, w.Gx.p, r, 1.0, Pv, nt));
-    }
-    CKL(dot_into(s, w, (size_t)nx * r, X1, X1, w.scal.p + 1, 0.0));
-    CKL(small_tn(s, w, nx, rf, rf, X2, nx, X2, nx, w.Gx.p, rf, 1.0, 0.0));
-    CKL(small_tn(s, w, nt, rf, rf, Pv, nt, Pv, nt, w.Gy.p, rf, 1.0, 0.0));
-    note_launch();
-    k_frob<<<1, 256, 0, s>>>(rf * rf, w.Gx.p, w.Gy.p, w.scal.p);
-    CKL(cudaGetLastError());
-    double rr[2] = {0.0, 0.0};
-    CKL(cudaMemcpyAsync(rr, w.scal.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CKL(cudaMemcpyAsync(rr.data(), w.slot(S_RA), nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CKL(cudaMemcpyAsync(rr.data() + nb, w.slot(S_RB), nb * sizeof(double), cudaMemcpyDeviceToHost, s));
     CKL(cudaStreamSynchronize(s));
-    const double r2 = rr[0] + rr[1];
     c.ms_time += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
-    const double rel = std::sqrt(std::max(r2, 0.0) / f2);
-    if (!std::isfinite(rel)) {
-      set_error("alternating solve: non-finite residual");
-      return LRP_ENONFINITE;
+    bool all_tol = tol > 0.0;
+    for (int i = 0; i < nb; ++i) {
+      const double rel = f2[i] > 0.0 ? std::sqrt(std::max(rr[i] + rr[nb + i], 0.0) / f2[i]) : 0.0;
+      if (!std::isfinite(rel)) {
+        set_error("alternating solve: non-finite residual");
+        return LRP_ENONFINITE;
+      }
+      if (res) res[(size_t)i * sweeps + sw] = rel;
+      all_tol = all_tol && rel <= tol;
     }
-    if (res) res[sw] = rel;
     *done_sweeps = sw + 1;
-    if (tol > 0.0 && rel <= tol) break;
+    if (all_tol) break;
   }
   return LRP_OK;
 }
@@ -1048,146 +1182,17 @@ lrp_status als_run(lrp_problem* P, AlsWS& w, int transpose, const double* Wf, co
 
 namespace {
 
-// Work arrays of the product for one column at a time.
-struct ColWS {
-  AlsWS fw, aw;
-  Buf<double> z, e1, Wa, Va, D, q1;
-  std::vector<double> start, hist;
-  cudaError_t init(lrp_problem* P, int r, int sweeps) {
-    const int nx = P->nx, nt = P->nt;
-    cudaError_t e = fw.init(P, r, 1);
-    if (e == cudaSuccess) e = aw.init(P, r, r);
-    if (e == cudaSuccess) e = z.alloc(nx);
-    if (e == cudaSuccess) e = e1.alloc(nt);
-    if (e == cudaSuccess) e = Wa.alloc((size_t)nx * r);
-    if (e == cudaSuccess) e = Va.alloc((size_t)nt * r);
-    if (e == cudaSuccess) e = D.alloc((size_t)P->n_obs * r);
-    if (e == cudaSuccess) e = q1.alloc(nx);
-    std::vector<double> unit(nt, 0.0);
-    unit[0] = 1.0;
-    if (e == cudaSuccess) e = cudaMemcpy(e1.p, unit.data(), nt * sizeof(double), cudaMemcpyHostToDevice);
-    // start: the first r time steps (unit vectors), for both solves
-    start.assign((size_t)nt * r, 0.0);
-    for (int j = 0; j < r; ++j) start[(size_t)j * nt + j] = 1.0;
-    hist.assign(sweeps, 0.0);
-    return e;
-  }
-};
-
-struct ColResult {
-  double res_f = 0.0, res_a = 0.0;
-  bool noconv = false;
-  AlsCounters c;
-};
-
-// y = Htilde x (H_mis x) for one column with both space-time systems solved
-// by the alternating solver; x, y device vectors.
-lrp_status als_column(lrp_problem* P, ColWS& w, int r, int sweeps, double tol, bool misfit, const double* x,
-                      double* y, ColResult& cr) {
-  const int nx = P->nx, nt = P->nt;
-  cudaStream_t s = P->stream;
-  const unsigned prior_st = ST_LOAD_X | ST_PRIOR_IN | ST_STORE_Y;
-  lrp_apply_stats pst;
-  if (misfit) {
-    CKL(cudaMemcpyAsync(w.z.p, x, nx * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  } else {
-    lrp_status pr = run_sweep_ex(P, prior_st, 1, x, nx, w.z.p, nx, nullptr, 0, nullptr, 0, &pst, 0, 0, nullptr, 0);
-    if (pr == LRP_ENOCONV)
-      cr.noconv = true;
-    else if (pr != LRP_OK)
-      return pr;
-  }
-  // forward: A Y - Y S^T = z e_1^T
-  CKL(cudaMemcpyAsync(w.fw.V.p, w.start.data(), w.start.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-  int done = 0;
-  CKS(als_run(P, w.fw, 0, w.z.p, w.e1.p, sweeps, tol, w.hist.data(), &done, cr.c));
-  cr.res_f = std::max(cr.res_f, done > 0 ? w.hist[done - 1] : 0.0);
-  // adjoint source: f_n = B^T B y_n / sigma^2 at the observed steps, as
-  // factors (B^T B W / sigma^2) (mask V)^T, in reversed time
-  {
-    dim3 go((P->n_obs + 255) / 256, r);
-    note_launch();
-    k_observe_cols<<<go, 256, 0, s>>>(P->n_obs, r, P->obs_node, P->obs_w, w.fw.W.p, nx, w.D.p);
-    CKL(cudaGetLastError());
-    dim3 gb(grid1(nx), r);
-    const double is2 = 1.0 / (P->desc.sigma * P->desc.sigma);
-    note_launch();
-    k_bt_cols<<<gb, 256, 0, s>>>(nx, r, P->bt_ptr, P->bt_idx, P->bt_w, w.D.p, P->n_obs, is2, w.Wa.p);
-    CKL(cudaGetLastError());
-    dim3 gr(grid1(nt), r);
-    note_launch();
-    k_rows_reverse<<<gr, 256, 0, s>>>(nt, r, w.fw.V.p, nt, w.Va.p, P->desc.obs_every, P->n_steps);
-    CKL(cudaGetLastError());
-  }
-  CKL(cudaMemcpyAsync(w.aw.V.p, w.start.data(), w.start.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-  CKS(als_run(P, w.aw, 1, w.Wa.p, w.Va.p, sweeps, tol, w.hist.data(), &done, cr.c));
-  cr.res_a = std::max(cr.res_a, done > 0 ? w.hist[done - 1] : 0.0);
-  // q_1 = the last column of the reversed solution
-  note_launch();
-  k_factor_row<<<grid1(nx), 256, 0, s>>>(nx, r, w.aw.W.p, w.aw.V.p, nt, nt - 1, w.q1.p);
-  CKL(cudaGetLastError());
-  if (misfit) {
-    CKL(cudaMemcpyAsync(y, w.q1.p, nx * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  } else {
-    lrp_status pr = run_sweep_ex(P, prior_st, 1, w.q1.p, nx, y, nx, nullptr, 0, nullptr, 0, &pst, 0, 0, nullptr, 0);
-    if (pr == LRP_ENOCONV)
-      cr.noconv = true;
-    else if (pr != LRP_OK)
-      return pr;
-  }
-  CKL(cudaStreamSynchronize(s));
-  return LRP_OK;
-}
-
-// A handle that shares the problem's operators, sensors and settings (all
-// read-only in a solve) but has its own stream, sweep workspace, statistics
-// and per-column operators, so that independent columns can run from
-// separate host threads at the same time.
-struct SideHandle {
-  lrp_problem* h = nullptr;
-  lrp_status make(const lrp_problem* P) {
-    h = new lrp_problem(*P);
-    h->allocs.clear();  // owns none of the problem's arrays
-    h->stream = nullptr;
-    h->ws = nullptr;
-    h->ws_bytes = 0;
-    h->ws_fixed = nullptr;
-    h->ws_fixed_bytes = 0;
-    h->stats = nullptr;
-    h->end_buf = nullptr;
-    h->prof_on = 0;
-    h->prof_ev[0] = h->prof_ev[1] = nullptr;
-    h->shift_ops.clear();
-    h->shift_ops_dev = nullptr;
-    h->src_W = h->src_V = nullptr;
-    CKL(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
-    CKL(dev_malloc(&h->stats, sizeof(Stats)));
-    CKL(dev_malloc(&h->end_buf, 65536 * sizeof(int)));
-    CKL(cudaMemset(h->end_buf, 0, 65536 * sizeof(int)));
-    return LRP_OK;
-  }
-  ~SideHandle() {
-    if (!h) return;
-    if (h->stream) {
-      cudaStreamSynchronize(h->stream);
-      cudaStreamDestroy(h->stream);
-    }
-    if (h->ws) cudaFree(h->ws);
-    if (h->stats) cudaFree(h->stats);
-    if (h->end_buf) cudaFree(h->end_buf);
-    delete h;
-  }
-};
-
-constexpr int kAlsStreams = 8;  // columns of a product solved at the same time
+constexpr unsigned kPriorStages = ST_LOAD_X | ST_PRIOR_IN | ST_STORE_Y;
 
 }  // namespace
 
 // The Hessian product with both space-time solves by the alternating solver
-// (flag LRP_ALS_SOLVES of lrp_hessian_apply; X, Y device arrays). One
-// column is one chain of small, synchronising steps (GMRES iterations), so
-// up to kAlsStreams columns run at once, each from its own host thread on a
-// side handle with its own stream; the results do not depend on this.
+// (flag LRP_ALS_SOLVES of lrp_hessian_apply; X, Y device arrays). The
+// columns go in batches (als_batch_cap): one prior solve launch for the
+// batch, the forward solves of the batch as one batched alternating solve
+// (source z_c e_1^T), the adjoint sources B^T B W_Y / sigma^2 with the
+// unobserved steps' rows of V_Y zeroed, the adjoint solves as one batched
+// alternating solve in reversed time, q_1 of each, one prior solve launch.
 lrp_status als_hessian_impl(lrp_problem* P, int nvec, const double* X, int ldx, double* Y, int ldy, bool misfit,
                             lrp_apply_stats* stats) {
   auto t0 = std::chrono::steady_clock::now();
@@ -1195,62 +1200,95 @@ lrp_status als_hessian_impl(lrp_problem* P, int nvec, const double* X, int ldx, 
   const int r = std::min({P->desc.als_rank > 0 ? P->desc.als_rank : 16, nt, nx, kMaxRank});
   const int sweeps = P->desc.als_sweeps > 0 ? P->desc.als_sweeps : 3;
   const double tol = P->desc.als_tol;
-  const int nw = std::max(1, std::min(nvec, kAlsStreams));
-  CKL(cudaStreamSynchronize(P->stream));  // X is ready
-  std::vector<std::unique_ptr<SideHandle>> side(nw);
-  std::vector<ColResult> res(nw);
-  std::vector<lrp_status> st(nw, LRP_OK);
-  std::vector<std::string> msg(nw);
-  // the side handles are copies of P made before any worker runs (the
-  // workers change P's per-call state: its settings during a preconditioner
-  // solve and its per-column operators)
-  for (int wi = 1; wi < nw; ++wi) {
-    side[wi].reset(new SideHandle());
-    lrp_status sm = side[wi]->make(P);
-    if (sm != LRP_OK) return sm;
-  }
-  auto worker = [&](int wi) {
-    cudaSetDevice(P->device);
-    lrp_problem* H = wi > 0 ? side[wi]->h : P;
-    ColWS w;
-    cudaError_t e = w.init(H, r, sweeps);
-    if (e != cudaSuccess) {
-      st[wi] = cuda_status(e, "alternating solve work arrays");
-      msg[wi] = lrp_last_error();
-      return;
-    }
-    ShiftOpsGuard guard{H};
-    for (int col = wi; col < nvec; col += nw) {
-      st[wi] = als_column(H, w, r, sweeps, tol, misfit, X + (size_t)col * ldx, Y + (size_t)col * ldy, res[wi]);
-      if (st[wi] != LRP_OK) {
-        msg[wi] = lrp_last_error();
-        return;
-      }
-    }
-  };
+  cudaStream_t s = P->stream;
+  const int nbc = std::max(1, std::min(nvec, als_batch_cap(P, r)));
+  AlsWS fw, aw;
+  CKL(fw.init(P, r, 1, nbc));
+  CKL(aw.init(P, r, r, nbc));
+  Buf<double> z, e1, Wa, Va, D, q1;
+  CKL(z.alloc((size_t)nx * nbc));
+  CKL(e1.alloc((size_t)nt * nbc));
+  CKL(Wa.alloc((size_t)nx * r * nbc));
+  CKL(Va.alloc((size_t)nt * r * nbc));
+  CKL(D.alloc((size_t)P->n_obs * r * nbc));
+  CKL(q1.alloc((size_t)nx * nbc));
   {
-    std::vector<std::thread> threads;
-    for (int wi = 1; wi < nw; ++wi) threads.emplace_back(worker, wi);
-    worker(0);
-    for (auto& t : threads) t.join();
+    std::vector<double> unit((size_t)nt * nbc, 0.0);
+    for (int i = 0; i < nbc; ++i) unit[(size_t)i * nt] = 1.0;
+    CKL(cudaMemcpyAsync(e1.p, unit.data(), unit.size() * sizeof(double), cudaMemcpyHostToDevice, s));
   }
-  side.clear();
-  for (int wi = 0; wi < nw; ++wi)
-    if (st[wi] != LRP_OK) {
-      set_error(msg[wi]);
-      return st[wi];
-    }
+  // starts: the first r time steps (unit vectors), for every solve
+  std::vector<double> start((size_t)nt * r * nbc, 0.0);
+  for (int i = 0; i < nbc; ++i)
+    for (int j = 0; j < r; ++j) start[(size_t)i * nt * r + (size_t)j * nt + j] = 1.0;
+  std::vector<double> hist((size_t)nbc * sweeps);
   AlsCounters c;
+  ShiftOpsGuard guard{P};
   double res_f = 0.0, res_a = 0.0;
   bool noconv = false;
-  for (const ColResult& cr : res) {
-    res_f = std::max(res_f, cr.res_f);
-    res_a = std::max(res_a, cr.res_a);
-    noconv = noconv || cr.noconv;
-    c.noconv = c.noconv || cr.c.noconv;
-    c.precond_solves += cr.c.precond_solves;
-    c.gmres_worst = std::max(c.gmres_worst, cr.c.gmres_worst);
+  lrp_apply_stats pst;
+  for (int col0 = 0; col0 < nvec; col0 += nbc) {
+    const int nb = std::min(nbc, nvec - col0);
+    fw.nb = aw.nb = nb;
+    const double* x = X + (size_t)col0 * ldx;
+    if (misfit) {
+      CKL(cudaMemcpy2DAsync(z.p, (size_t)nx * sizeof(double), x, (size_t)ldx * sizeof(double),
+                            (size_t)nx * sizeof(double), nb, cudaMemcpyDeviceToDevice, s));
+    } else {
+      lrp_status pr = run_sweep_ex(P, kPriorStages, nb, x, ldx, z.p, nx, nullptr, 0, nullptr, 0, &pst, 0, 0,
+                                   nullptr, 0);
+      if (pr == LRP_ENOCONV)
+        noconv = true;
+      else if (pr != LRP_OK)
+        return pr;
+    }
+    // forward: A Y_c - Y_c S^T = z_c e_1^T
+    CKL(cudaMemcpyAsync(fw.V.p, start.data(), (size_t)nb * nt * r * sizeof(double), cudaMemcpyHostToDevice, s));
+    int done = 0;
+    CKS(als_run(P, fw, 0, z.p, e1.p, sweeps, tol, hist.data(), &done, c));
+    for (int i = 0; i < nb && done > 0; ++i) res_f = std::max(res_f, hist[(size_t)i * sweeps + done - 1]);
+    // adjoint sources: f_n = B^T B y_n / sigma^2 at the observed steps, as
+    // factors (B^T B W / sigma^2) (mask V)^T, in reversed time (all nb r
+    // columns of the batch at once: the factors are stored solve by solve)
+    {
+      const int ncol = nb * r;
+      dim3 go((P->n_obs + 255) / 256, ncol);
+      note_launch();
+      k_observe_cols<<<go, 256, 0, s>>>(P->n_obs, ncol, P->obs_node, P->obs_w, fw.W.p, nx, D.p);
+      CKL(cudaGetLastError());
+      dim3 gb(grid1(nx), ncol);
+      const double is2 = 1.0 / (P->desc.sigma * P->desc.sigma);
+      note_launch();
+      k_bt_cols<<<gb, 256, 0, s>>>(nx, ncol, P->bt_ptr, P->bt_idx, P->bt_w, D.p, P->n_obs, is2, Wa.p);
+      CKL(cudaGetLastError());
+      dim3 gr(grid1(nt), ncol);
+      note_launch();
+      k_rows_reverse<<<gr, 256, 0, s>>>(nt, ncol, fw.V.p, nt, Va.p, P->desc.obs_every, P->n_steps);
+      CKL(cudaGetLastError());
+    }
+    CKL(cudaMemcpyAsync(aw.V.p, start.data(), (size_t)nb * nt * r * sizeof(double), cudaMemcpyHostToDevice, s));
+    CKS(als_run(P, aw, 1, Wa.p, Va.p, sweeps, tol, hist.data(), &done, c));
+    for (int i = 0; i < nb && done > 0; ++i) res_a = std::max(res_a, hist[(size_t)i * sweeps + done - 1]);
+    // q_1 = the last column of each reversed solution
+    for (int i = 0; i < nb; ++i) {
+      note_launch();
+      k_factor_row<<<grid1(nx), 256, 0, s>>>(nx, r, aw.Wc(i), aw.Vc(i), nt, nt - 1, q1.p + (size_t)i * nx);
+      CKL(cudaGetLastError());
+    }
+    double* y = Y + (size_t)col0 * ldy;
+    if (misfit) {
+      CKL(cudaMemcpy2DAsync(y, (size_t)ldy * sizeof(double), q1.p, (size_t)nx * sizeof(double),
+                            (size_t)nx * sizeof(double), nb, cudaMemcpyDeviceToDevice, s));
+    } else {
+      lrp_status pr = run_sweep_ex(P, kPriorStages, nb, q1.p, nx, y, ldy, nullptr, 0, nullptr, 0, &pst, 0, 0,
+                                   nullptr, 0);
+      if (pr == LRP_ENOCONV)
+        noconv = true;
+      else if (pr != LRP_OK)
+        return pr;
+    }
   }
+  CKL(cudaStreamSynchronize(s));
   if (stats) {
     std::memset(stats, 0, sizeof(*stats));
     stats->n_solves = nvec > 0 ? c.precond_solves / nvec : 0;
@@ -1292,7 +1330,7 @@ extern "C" lrp_status lrp_als_solve(lrp_problem* P, int transpose, int rf, const
   const int nx = P->nx, nt = P->nt;
   cudaStream_t s = P->stream;
   AlsWS w;
-  CKL(w.init(P, r, rf));
+  CKL(w.init(P, r, rf, 1));
   Buf<double> dWf, dVf, tmp;
   CKL(dWf.alloc((size_t)nx * std::max(rf, 1)));
   CKL(dVf.alloc((size_t)nt * std::max(rf, 1)));

@@ -181,10 +181,14 @@ def test_als_argument_checks_and_degenerate_source():
 
 
 def test_als_hessian_many_columns_equal_single_column_calls():
-    """A block of 11 columns runs on 8 side handles at once (three of them
-    take two columns); every column equals the same column applied alone,
-    to the solves' accuracy (the side handles share the operators and the
-    settings, not the solver state)."""
+    """A block of 11 columns is solved as one batch (one preconditioner
+    launch per GMRES iteration for all of them, a Hessenberg matrix per
+    column); every column equals the same column applied alone to the
+    solves' accuracy. The batch keeps iterating a column's GMRES until every
+    column has converged, so a column can take more iterations than alone:
+    the difference is of the order of the space step's GMRES tolerance
+    propagated through the sweeps (~1e-11 relative), hence 1e-9 here; the
+    comparisons with the oracle keep 1e-10."""
     spec = _spec("heat2d")
     P = OProblem(spec)
     X = synth.normal_block(P.nx, 11, 113)
@@ -194,5 +198,5 @@ def test_als_hessian_many_columns_equal_single_column_calls():
     for j in (0, 5, 8, 10):
         y1, st1 = lrp.lrp_hessian_apply(G, X[:, j:j + 1], flags=lrp.LRP_ALS_SOLVES)
         assert st1["status"] == lrp.LRP_OK
-        assert relerr(Y[:, j], y1[:, 0]) < 1e-10, j
+        assert relerr(Y[:, j], y1[:, 0]) < 1e-9, (j, relerr(Y[:, j], y1[:, 0]))
     G.close()
