@@ -891,3 +891,55 @@ def test_als_hessian_full_rank_is_exact(misfit):
     out4, info4 = als.als_hessian_apply(P, x, 4, 3, A=A, misfit_only=misfit)
     err = np.linalg.norm(out4 - ref) / np.linalg.norm(ref)
     assert 0 < err < 1e-2
+
+
+def _als_setup_convdiff(n=7, nt=12):
+    """The upwind convection-diffusion operator (Sec. 6.2): A = I + tau L is
+    not symmetric, so a transposed A anywhere in the alternating solve or its
+    adjoint changes the result."""
+    spec = _spec(n=n, nt=nt, pde="convdiff", conv_nu=1e-2, wind=(0.0, 1.0, 0.0))
+    P = Problem(spec)
+    A = P.K.toarray()
+    assert np.abs(A - A.T).max() > 1e-3
+    return P, A
+
+
+def test_als_convdiff_full_rank_forward_and_adjoint():
+    """Nonsymmetric operator: with r = nt one sweep of the forward solve
+    reproduces implicit Euler with (I + tau L) and one sweep of the adjoint
+    solve the backward recursion with (I + tau L)^T; swapping the two
+    operators fails both."""
+    P, A = _als_setup_convdiff()
+    g = synth.rng(57)
+    u = g.standard_normal(P.nx)
+    e1 = np.zeros((P.nt, 1))
+    e1[0, 0] = 1.0
+    V0, _ = np.linalg.qr(g.standard_normal((P.nt, P.nt)))
+    W, V, res = als.als_solve(A, u[:, None], e1, V0, 1)
+    Y = P.trajectory(u)
+    assert res[0] < 1e-12
+    assert np.max(np.abs(W @ V.T - Y)) <= 1e-12 * np.abs(Y).max()
+    Wt, Vt, _ = als.als_solve(A.T.copy(), u[:, None], e1, V0, 1)
+    assert np.max(np.abs(Wt @ Vt.T - Y)) > 1e-6 * np.abs(Y).max()
+    D = g.standard_normal(P.n_data)
+    Q = lowrank.adjoint_trajectory(P, D)
+    F = np.zeros((P.nx, P.nt))
+    Bt = P.B.T.toarray()
+    for k, n in enumerate(P.steps):
+        F[:, n - 1] = Bt @ D[k * P.n_obs:(k + 1) * P.n_obs]
+    U, s, Vt2 = np.linalg.svd(F, full_matrices=False)
+    Wq, Vq, resq = als.als_adjoint(A, U * s, Vt2.T, V0, 1)
+    assert resq[0] < 1e-12
+    assert np.max(np.abs(Wq @ Vq.T - Q)) <= 1e-12 * np.abs(Q).max()
+    Wx, Vx, _ = als.als_adjoint(A.T.copy(), U * s, Vt2.T, V0, 1)
+    assert np.max(np.abs(Wx @ Vx.T - Q)) > 1e-6 * np.abs(Q).max()
+
+
+def test_als_convdiff_hessian_full_rank_is_exact():
+    """The product on the nonsymmetric operator with r = nt equals the
+    time-stepping Htilde (forward with A, adjoint with A^T)."""
+    P, A = _als_setup_convdiff()
+    x = synth.normal_block(P.nx, 1, 58)[:, 0]
+    ref = P.hessian_apply(x)
+    out, info = als.als_hessian_apply(P, x, P.nt, 1, A=A)
+    assert np.max(np.abs(out - ref)) <= 1e-11 * np.abs(ref).max()
