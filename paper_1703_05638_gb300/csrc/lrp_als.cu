@@ -13,10 +13,14 @@
 //    preconditioner of Eq. (pre_1): blocks A - T_jj I, each applied by one
 //    multigrid-preconditioned solve of the sweep kernel (stage ST_SHIFTED,
 //    one column per team, all r columns in one launch);
-//  * the time step (Eq. (amen_2)): W orthonormalised to Q, the Galerkin
-//    projection onto span(Q) in space, Ahat z_n - z_{n-1} = Q^T f_n with
-//    Ahat = Q^T A Q (r x r), solved directly (one CTA: Gauss-Jordan inverse,
-//    then the nt-step recurrence), Y = Q Z^T, V = orth(Z), W = Q R_Z^T.
+//  * the time step (Eq. (amen_2)): W orthonormalised to Q (Cholesky QR),
+//    the Galerkin projection onto span(Q) in space,
+//    Ahat z_n - z_{n-1} = Q^T f_n with Ahat = Q^T A Q (r x r), solved
+//    directly (one CTA: Gauss-Jordan inverse, then the nt-step recurrence),
+//    Y = Q Z^T, V = orth(Z), W = Q R_Z^T.
+// Several independent solves (the columns of a Hessian product) run as one
+// batch: their GMRES iterations are shared (one preconditioner launch for
+// all their columns), each with its own Hessenberg matrix.
 // The adjoint system A^T q_n = q_{n+1} + f_n (n = nt..1) is the same system
 // with A^T in reversed time.
 //
@@ -67,7 +71,7 @@ struct Buf {
     if (_s != LRP_OK) return _s;  \
   } while (0)
 
-constexpr int kMaxRank = 64;     // block Gram-Schmidt limit (columns of W and of Z)
+constexpr int kMaxRank = 64;     // rank limit: the Cholesky QR's and the GMRES update's small tiles
 constexpr int kGmresMax = 40;    // Krylov vectors per GMRES cycle
 constexpr int kGmresCycles = 6;  // restarts per space step
 constexpr double kPrecondRtol = 1e-8;  // stop of a preconditioner solve before its iteration cap
