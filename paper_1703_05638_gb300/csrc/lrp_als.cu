@@ -980,8 +980,12 @@ lrp_status space_step(lrp_problem* P, AlsWS& w, int transpose, bool warm, double
         return LRP_ENONFINITE;
       }
       if (!(gnorm[i] > 0.0)) {
-        // a zero right-hand side: the solution is zero
+        // a zero right-hand side: the solution is zero, and the solve's
+        // Krylov start and rotated right-hand side are zeroed so that the
+        // shared iterations leave it at zero
         CKL(cudaMemsetAsync(w.Wc(i), 0, n1 * sizeof(double), s));
+        CKL(cudaMemsetAsync(v0 + (size_t)i * n1, 0, n1 * sizeof(double), s));
+        CKL(cudaMemsetAsync(w.g.p + (size_t)i * (kmax + 1), 0, (kmax + 1) * sizeof(double), s));
         rres[i] = 0.0;
       }
       if (rres[i] > target[i]) all_done = false;
